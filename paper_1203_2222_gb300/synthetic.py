@@ -1,0 +1,103 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the oracle.
+
+This module holds leg structures (charges or doubled spins, degeneracies,
+directions) and seeded N(0,1) draws only -- none of the method's arithmetic.
+Each side builds its own tensors from these plain tuples and asks for as many
+random values as its own sector enumeration says the tensor holds.
+
+A leg spec is ``(labels, degens, dir)`` with ``dir = +1`` ('out') or ``-1``
+('in'); U(1) labels are charges, SU(2) labels are doubled spins 2j.
+
+Workload shapes (all seeds are ``1234 + index``):
+
+* ``u1_pairwise``   two rank-4 U(1) tensors, charges -2..2, degeneracies
+  uniform in 1..4 per leg, total charge 0; contract A's legs 2,3 with B's
+  legs 0,1 (B's first two legs are A's last two, reversed).
+* ``u1_mps_heff``   MPS effective-Hamiltonian apply (L.A).W.R with bond
+  D = 2048 over charges -20..20 (Gaussian degeneracy profile, sigma 6),
+  physical leg {0:1, 1:1}, MPO leg {-1:1, 0:3, +1:1}.
+* ``su2_recouple``  rank-4 SU(2) tensors, every leg with 2j = 0..8 and
+  degeneracies uniform in 1..dmax (32 at full size); A has all legs out in
+  the comb tree, is permuted (0,2,1,3) into the matrix tree and its legs 1,3
+  are contracted with a tensor B whose first two legs are their duals.
+"""
+import math
+
+import numpy as np
+
+
+def normal(seed, n, stream=0):
+    """n draws of N(0,1) in float64 from PCG64(seed), sub-stream ``stream``."""
+    ss = np.random.SeedSequence([int(seed), int(stream)])
+    return np.random.Generator(np.random.PCG64(ss)).standard_normal(int(n))
+
+
+def uniform_int(seed, lo, hi, n, stream=0):
+    ss = np.random.SeedSequence([int(seed), int(stream), 7])
+    return np.random.Generator(np.random.PCG64(ss)).integers(lo, hi + 1, size=n).tolist()
+
+
+def gaussian_degeneracies(D, qmin, qmax, sigma):
+    """Degeneracies over charges qmin..qmax summing to D, profile exp(-q^2/(2 sigma^2)).
+
+    d_q = max(1, round-half-even(D g_q / sum g)); the remainder is fixed by
+    +-1 steps on charges in order of increasing |q|, negative first.
+    """
+    qs = list(range(qmin, qmax + 1))
+    g = [math.exp(-q * q / (2.0 * sigma * sigma)) for q in qs]
+    sg = sum(g)
+    d = [max(1, int(round(D * gi / sg))) for gi in g]
+    order = sorted(range(len(qs)), key=lambda i: (abs(qs[i]), qs[i]))
+    rem = D - sum(d)
+    i = 0
+    while rem != 0:
+        j = order[i % len(order)]
+        step = 1 if rem > 0 else -1
+        if d[j] + step >= 1:
+            d[j] += step
+            rem -= step
+        i += 1
+    return qs, d
+
+
+def u1_pairwise(seed=1234):
+    """Two rank-4 U(1) tensors and the contracted pairs (dense dim per leg <= 20)."""
+    qs = [-2, -1, 0, 1, 2]
+    dl = [uniform_int(seed, 1, 4, 5, stream=l) for l in range(6)]
+    A = [(qs, dl[0], 1), (qs, dl[1], 1), (qs, dl[2], -1), (qs, dl[3], -1)]
+    B = [(qs, dl[2], 1), (qs, dl[3], 1), (qs, dl[4], -1), (qs, dl[5], -1)]
+    return {"group": "u1", "A": A, "QA": 0, "B": B, "QB": 0,
+            "pairsA": [2, 3], "pairsB": [0, 1], "seedA": seed, "seedB": seed + 1}
+
+
+def u1_mps_heff(D=2048, qmax=20, sigma=6.0, seed=1235):
+    """Legs of L[a,w,a'], A[a',s',b'], W[w,s,s',w2], R[b,w2,b'] (all total charge 0).
+
+    Directions: A (in, in, out); L (in, in, out); W (out, in, out, in);
+    R (out, out, in).  Contraction order ((L.A).W).R:
+      L.A    over L2 <-> A0            -> T1[a, w, s', b']   (in, in, in, out)
+      T1.W   over T1(1,2) <-> W(0,2)   -> T2[a, b', s, w2]   (in, out, in, in)
+      T2.R   over T2(1,3) <-> R(2,1)   -> Y[a, s, b]         (in, in, out)
+    """
+    qs, d = gaussian_degeneracies(D, -qmax, qmax, sigma)
+    bond_in, bond_out = (qs, d, -1), (qs, d, 1)
+    wq, wd = [-1, 0, 1], [1, 3, 1]
+    phys_in, phys_out = ([0, 1], [1, 1], -1), ([0, 1], [1, 1], 1)
+    L = [bond_in, (wq, wd, -1), bond_out]
+    A = [bond_in, phys_in, bond_out]
+    W = [(wq, wd, 1), phys_in, phys_out, (wq, wd, -1)]
+    R = [bond_out, (wq, wd, 1), bond_in]
+    return {"group": "u1", "L": L, "A": A, "W": W, "R": R,
+            "steps": [((1, 2), (0, 2)), ((1, 3), (2, 1))],
+            "seeds": {"L": seed, "A": seed + 100, "W": seed + 200, "R": seed + 300},
+            "D": D}
+
+
+def su2_recouple(dmax=32, jmax2=8, seed=1236):
+    """Legs of the SU(2) recoupling contraction (A all out; B = duals + 2 out legs)."""
+    spins = list(range(0, jmax2 + 1))
+    dl = [uniform_int(seed, 1, dmax, len(spins), stream=l) for l in range(6)]
+    A = [(spins, dl[l], 1) for l in range(4)]
+    B = [(spins, dl[1], -1), (spins, dl[3], -1), (spins, dl[4], 1), (spins, dl[5], 1)]
+    return {"group": "su2", "A": A, "B": B, "perm": [0, 2, 1, 3],
+            "pairsA": [1, 3], "pairsB": [0, 1], "seedA": seed, "seedB": seed + 1}
