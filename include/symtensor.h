@@ -1,0 +1,194 @@
+/*
+ * symtensor.h -- C ABI of the GB300 symmetric block-sparse contraction library.
+ *
+ * A symmetric tensor (S. Singh, arXiv:1203.2222) is stored as its degeneracy
+ * blocks only.  This library builds the integer sector tables of such tensors
+ * on the host and moves, recouples and multiplies the blocks on one GPU.
+ *
+ * Data model (Ch. 5 "Tensors as linear maps", Ch. 6 "Tree decompositions"):
+ *   - A leg is a list of n labels with degeneracies and a direction
+ *     (+1 'out', -1 'in').  U(1): labels are integer charges.  SU(2): labels
+ *     are doubled spins 2j.  Labels are strictly increasing.
+ *   - U(1): a block (sector) is one charge per leg with
+ *       sum_out q - sum_in q == total   (charge conservation).
+ *   - SU(2): the tensor is a tree decomposition; a sector is one spin per leg
+ *     plus one spin per non-root node of the fusion tree, every node obeying
+ *     the fusion rule |ja-jb| <= jc <= ja+jb (Ch. 5, Eq. fusionrules) and the
+ *     root carrying spin 0 (the vector v of Ch. 6 is invariant).  Incoming
+ *     legs carry a cup (Ch. 6); reversal of a leg is metadata only.
+ *   - A tree over k legs is given as k-1 nodes (left, right): ids 0..k-1 are
+ *     legs, node n has id k+n, the last node is the root and every node joins
+ *     two adjacent leg ranges, left first.  NULL means the left comb
+ *     ((0,1),2),...
+ *   - Sectors are ordered lexicographically by leg label positions (leg 0
+ *     slowest), then by node spins in node order.  Each block is a dense
+ *     d_1 x ... x d_k array, row-major (last leg fastest); blocks are
+ *     concatenated in sector order.  Block data lives in caller-owned device
+ *     buffers of numel elements (float for SYM_PREC_BF16X3 plans, double for
+ *     SYM_PREC_FP64 plans); the library never frees them.
+ *
+ * Handles (sym_tensor, sym_plan) are owned by the caller and freed with the
+ * matching destroy call.  A sym_tensor holds structure only (host tables).
+ * A sym_plan holds the precomputed tables of one operation (uploaded to the
+ * device) and its scratch operand buffers; it is the precomputation of
+ * symmetry-only data the thesis recommends reusing across iterations
+ * (Ch. 6, "Discussion on computational performance").
+ *
+ * Environment: SYM_PLAN_DRYRUN=1 makes the *_plan calls build and
+ * bounds-check their work lists on the host without touching the GPU; such
+ * plans report statistics but refuse to execute (SYM_ERR_UNSUPPORTED).
+ *
+ * Errors: every call returns SYM_OK (0) or a negative SYM_ERR_* code;
+ * sym_last_error() returns a thread-local message for the last failure.
+ * Execution calls are asynchronous on the given CUDA stream (a cudaStream_t
+ * passed as void*, NULL = legacy default stream); they return SYM_ERR_CUDA if
+ * a launch fails.  Device-side bounded waits that expire set a device error
+ * word that sym_device_status() reports as SYM_ERR_TIMEOUT.
+ */
+#ifndef SYMTENSOR_H
+#define SYMTENSOR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SYM_OK 0
+#define SYM_ERR_ARG (-1)               /* malformed argument */
+#define SYM_ERR_INCOMPATIBLE_LEGS (-2) /* contracted legs differ or share a direction */
+#define SYM_ERR_CUDA (-4)              /* a CUDA call failed */
+#define SYM_ERR_TIMEOUT (-5)           /* a device-side bounded wait expired */
+#define SYM_ERR_OOM (-6)               /* host or device allocation failed */
+#define SYM_ERR_UNSUPPORTED (-7)       /* valid request outside what is built */
+
+#define SYM_U1 1
+#define SYM_SU2 2
+
+/* Precision of a plan (the storage dtype follows from it). */
+#define SYM_PREC_FP64 1   /* double blocks, FP64 gathers and FP64 GEMM (CUDA cores) */
+#define SYM_PREC_BF16X3 2 /* float blocks, split-BF16 x3 tcgen05 GEMM, FP32 accumulate */
+
+typedef struct {
+  int n;              /* number of labels */
+  const int* labels;  /* U(1) charges or SU(2) doubled spins, strictly increasing */
+  const int* degens;  /* degeneracy d of every label, >= 1 */
+  int dir;            /* +1 out, -1 in */
+} sym_leg;
+
+typedef struct sym_tensor_s* sym_tensor;
+typedef struct sym_plan_s* sym_plan;
+
+/* Last error message of the calling thread ("" if none). */
+const char* sym_last_error(void);
+
+/* Library build information, e.g. "symtensor sm_103a". */
+const char* sym_version(void);
+
+/* ---------------------------------------------------------------- tensors ---
+ * sym_tensor_create: build the sector table of a tensor (host only, no GPU).
+ *   group: SYM_U1 or SYM_SU2.  0 <= rank <= 6 (rank 0 is a scalar).
+ *   legs: rank leg descriptors (copied).
+ *   total: U(1) total charge Q; ignored for SU(2) (total spin is 0).
+ *   tree: SU(2) fusion tree as 2*(rank-1) ints, NULL = left comb; ignored for U(1).
+ * Errors: SYM_ERR_ARG for malformed legs or trees.                          */
+int sym_tensor_create(int group, int rank, const sym_leg* legs, int total,
+                      const int* tree, sym_tensor* out);
+int sym_tensor_destroy(sym_tensor t);
+
+/* group, rank, numel (elements of all blocks), nsec (number of sectors). */
+int sym_tensor_info(sym_tensor t, int* group, int* rank, int64_t* numel,
+                    int64_t* nsec);
+/* Copy leg `leg` (labels/degens may be NULL to query *n first). */
+int sym_tensor_leg(sym_tensor t, int leg, int* n, int* labels, int* degens,
+                   int* dir);
+/* Copy the tree (2*(rank-1) ints) of an SU(2) tensor. */
+int sym_tensor_tree(sym_tensor t, int* nodes);
+/* Sector table: labels receives nsec*(rank + max(rank-2,0)) ints (leg label
+ * positions, then SU(2) non-root node spins 2j); offsets receives nsec+1
+ * block offsets (exclusive prefix sum of block sizes).  Either may be NULL. */
+int sym_tensor_sectors(sym_tensor t, int* labels, int64_t* offsets);
+
+/* ------------------------------------------------------------- operations ---
+ * Each operation is planned once on the host (structure only; the result's
+ * structure handle is returned) and executed any number of times on device
+ * data.  `precision` selects the data type the plan works in.
+ *
+ * sym_permute_plan: PERMUTE of Ch. 6 -- output leg n is input leg perm[n];
+ *   SU(2) output tree tree_out (NULL = left comb), the blocks recoupled by
+ *   v' = Gamma(tau, p, tau') v with 6j recoupling and swap factors.
+ * sym_fuse_plan: FUSE of Ch. 6 -- legs first and first+1 (equal directions)
+ *   become one leg (fused labels ascending; within a fused label the pairs
+ *   (la, lb) are ordered with la slowest and (t_a, t_b) row-major).  For
+ *   SU(2) the input is first taken to the tree where the two legs share a
+ *   node (NEWTREE), the output tree is the left comb.
+ * sym_split_plan: SPLIT of Ch. 6 -- leg `leg` is split into the two legs
+ *   parts[0], parts[1], which must fuse exactly to it; SU(2) output tree is
+ *   the left comb.
+ * sym_plan_execute: run a permute/fuse/split plan: out = op(in).          */
+int sym_permute_plan(sym_tensor in, const int* perm, const int* tree_out,
+                     int precision, sym_tensor* out, sym_plan* plan);
+int sym_fuse_plan(sym_tensor in, int first, int precision, sym_tensor* out,
+                  sym_plan* plan);
+int sym_split_plan(sym_tensor in, int leg, const sym_leg* parts, int precision,
+                   sym_tensor* out, sym_plan* plan);
+int sym_plan_execute(sym_plan plan, const void* in, void* out, void* stream);
+
+/* sym_contract_plan: the five-step contraction of Ch. 5 ("Multiplication of
+ *   two tensors", Eq. multi1-multi5) and Ch. 6 ("Multiplication of two
+ *   tensors"): legs pairsA[i] of A and pairsB[i] of B are summed over; each
+ *   pair must have identical labels/degeneracies and opposite directions
+ *   (SYM_ERR_INCOMPATIBLE_LEGS otherwise).  The result C has A's free legs
+ *   (in order) then B's free legs; U(1) total charge QA + QB; SU(2) tree
+ *   tree_c, NULL = comb over A's free legs and comb over B's free legs joined
+ *   at the root.  Steps on the device: gather A and B into per-sector matrix
+ *   form (block transpose; SU(2): recoupling by precomputed 6j/swap
+ *   coefficients), one grouped per-sector GEMM (blockwise product,
+ *   Ch. 5 Eq. blockmult), scatter into C's blocks.
+ * sym_contract: C = contract(A, B) on device buffers.
+ * sym_contract_backward: dA, dB = gradient of <dC, C> with respect to A's
+ *   and B's blocks (adjoint on the same sector tables); dA or dB may be NULL
+ *   to skip it.  Buffers are overwritten, not accumulated.
+ * sym_plan_stats: useful flops of one forward (sum over sectors of 2 m n k),
+ *   and bytes of A, B and C blocks in the plan's data type.              */
+int sym_contract_plan(sym_tensor A, sym_tensor B, int npairs, const int* pairsA,
+                      const int* pairsB, const int* tree_c, int precision,
+                      sym_tensor* C, sym_plan* plan);
+int sym_contract(sym_plan plan, const void* A, const void* B, void* C,
+                 void* stream);
+int sym_contract_backward(sym_plan plan, const void* A, const void* B,
+                          const void* dC, void* dA, void* dB, void* stream);
+int sym_plan_stats(sym_plan plan, double* flops_fwd, int64_t* bytes_a,
+                   int64_t* bytes_b, int64_t* bytes_c);
+int sym_plan_destroy(sym_plan plan);
+
+/* Number of kernel launches the last execution call on this plan issued. */
+int sym_plan_launches(sym_plan plan, int* launches);
+
+/* ------------------------------------------------ SU(2) recoupling (host) ---
+ * The symmetry-only data the planner precomputes, exposed for inspection;
+ * no GPU is touched.  Spins are doubled.
+ * sym_su2_F: the recoupling coefficient F^{jd je}_{ja jb jc J} of Ch. 5,
+ *   Eq. fmove, evaluated from the Wigner 6j symbol (Eq. sixj, Racah's
+ *   formula): the overlap <(a,b)d, c; J | a, (b,c)e; J>; 0 if not allowed.
+ * sym_su2_gamma: the matrix Gamma(tau, p, tau') of Ch. 6 (Eq. permsu2) for
+ *   fixed leg spins: out[o * n_in + i] = < tau'; labelling o | p(tau; labelling i) >,
+ *   where output leg n is input leg perm[n] and labellings enumerate the
+ *   non-root node spins of each tree in sector order.  Pass G = NULL to
+ *   query n_in / n_out; labels_in / labels_out (may be NULL) receive the
+ *   labellings, max(rank-2,0) ints each.  Trees as in sym_tensor_create.   */
+int sym_su2_F(int jd, int je, int ja, int jb, int jc, int J, double* out);
+int sym_su2_gamma(int rank, const int* spins, const int* tree_in, const int* perm,
+                  const int* tree_out, int* n_in, int* n_out, double* G,
+                  int* labels_in, int* labels_out);
+
+/* Device error word: SYM_OK, or SYM_ERR_TIMEOUT if a bounded wait in a
+ * persistent kernel expired since the last call (the word is then cleared).
+ * Synchronizes the device. */
+int sym_device_status(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SYMTENSOR_H */

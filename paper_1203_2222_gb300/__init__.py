@@ -1,0 +1,11 @@
+"""GB300-native symmetric (U(1) / SU(2)) block-sparse tensor contraction.
+
+Hot path of S. Singh's tensor-network symmetry method (arXiv:1203.2222):
+integer sector tables, block gathers with SU(2) recoupling, a grouped
+per-sector GEMM on tcgen05 tensor cores, the scatter back, and the adjoint.
+The compute lives in ``_build/libsymtensor.so`` (C ABI: include/symtensor.h);
+this package is its Python front end.
+"""
+from .symtensor import (BF16X3, FP64, SU2, U1, Plan, Structure, SymError, SymTensor, contract,  # noqa: F401
+                        contract_plan, device_status, fuse, fuse_plan, permute, permute_plan, split,
+                        split_plan, su2_F, su2_gamma)

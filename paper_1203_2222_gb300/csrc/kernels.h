@@ -1,0 +1,79 @@
+// Device work descriptors shared by the host planner and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+
+namespace sym {
+
+constexpr int kMaxDim = 6;
+
+// One work unit of the block-movement kernel: a strided box of `dims`
+// (last dim fastest) whose element t is
+//   dst  <- sum over terms  coef * src[term.off + term.ld * <t, sa> + <t, sb>]
+// Destination (by kernel mode):
+//   linear: dst[dst_off + dst_ld * <t, da> + <t, db>]
+//   image : sector matrix element (row0 + <t, da>, col0 + <t, db>) of a
+//           tiled split-BF16 operand image starting at dst_off (see gemm_tc.cu)
+// Only elements [start, start + count) of the box (row-major linear index)
+// belong to this unit; the planner guarantees that every destination element
+// is written by exactly one unit.
+struct BoxItem {
+  int64_t dst_off;
+  int32_t dst_ld;   // linear: multiplier of <t, da>; image: K tiles per row tile
+  int32_t row0, col0;
+  int32_t sel;      // source slot (bits 0-3) and destination slot (bits 4-7)
+  int32_t ndim;
+  int32_t term0, nterm;
+  int32_t start, count;
+  int32_t dims[kMaxDim];
+  int32_t sa[kMaxDim], sb[kMaxDim];
+  int32_t da[kMaxDim], db[kMaxDim];
+};
+
+struct Term {
+  int64_t off;
+  int64_t ld;
+  double coef;
+};
+
+enum BoxMode { BOX_LINEAR_F32 = 0, BOX_LINEAR_F64 = 1, BOX_IMAGE_BF16X2 = 2 };
+
+// Buffers a box launch may read (src slots) and write (dst slots; image mode
+// writes the hi image to dst[i][0] and the lo image to dst[i][1]).
+struct BoxPtrs {
+  const void* src[4];
+  void* dst[4][2];
+};
+
+// FP64 grouped GEMM (row-major): C = alpha * A (m x k, lda) * B (k x n, ldb).
+struct GemmSector64 {
+  int32_t m, n, k, lda, ldb, ldc;
+  int64_t a_off, b_off, c_off;
+  double alpha;
+};
+struct GemmTile {
+  int32_t sector, mt, nt;
+};
+
+// tcgen05 split-BF16 x3 grouped GEMM.  Operand images: A tile (mt, kt) at
+// a_img + (mt * ktiles + kt) * 8192 bf16 elements (128 rows x 64 k, 128B
+// swizzled), B tile (nt, kt) likewise with n rows.  C row-major fp32.
+struct TcSector {
+  int32_t m, n, k, ktiles;
+  int64_t a_img, b_img;
+  int64_t c_off;
+  int32_t ldc;
+  float alpha;
+};
+
+// Launchers (return cudaError_t as int).
+int launch_box(int mode, bool src_f64, const BoxItem* items, int nitems, const Term* terms,
+               const BoxPtrs& ptrs, void* stream);
+int launch_gemm_f64(const GemmSector64* secs, const GemmTile* tiles, int ntiles, const double* A,
+                    const double* B, double* C, void* stream);
+int launch_gemm_tc(const TcSector* secs, const GemmTile* tiles, int ntiles, const uint16_t* a_hi,
+                   const uint16_t* a_lo, const uint16_t* b_hi, const uint16_t* b_lo, float* C,
+                   int* err_word, void* stream);
+int tc_num_sms();
+
+}  // namespace sym

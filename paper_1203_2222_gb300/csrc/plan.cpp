@@ -1,0 +1,1089 @@
+// Planner: turns tensor structures into device work lists (host, integer
+// exact apart from the FP64 recoupling coefficients).
+//
+// A contraction (Ch. 5 "Multiplication of two tensors", steps 1-5; Ch. 6 for
+// tree decompositions) is planned as
+//   A --(permute free legs first; SU(2): Gamma to the matrix tree)--> A_mat
+//   B --(permute contracted legs first; SU(2): Gamma)---------------> B_mat
+//   per sector x:  C_x = A_x B_x   (blockwise product, Ch. 5 Eq. blockmult)
+//   C_x --(split rows/cols into blocks; SU(2): Gamma to the output tree)--> C
+// A_mat (B_mat) is a tensor whose legs are [rows..., cols...] and whose SU(2)
+// tree is a comb over the row legs and a comb over the column legs joined at
+// the root, so a sector x is the spin on the two subtrees (U(1): the fused
+// charge of the contracted legs).  Inside sector x, row groups (one per
+// labelling of the row subtree) and column groups are stacked in
+// lexicographic order of their labels; the same rule on both operands makes
+// A's columns and B's rows coincide.
+//
+// SU(2) normalisation.  With cups on incoming legs (Ch. 6) and the root
+// vertex C_{x,x->0} = omega_x (Ch. 5, Eq. singletomega), contracting the
+// column subtree of A with the row subtree of B leaves, per sector,
+//   C_x = (-1)^(2x) / sqrt(2x+1) * prod_{paired legs incoming in A} (-1)^(2j)
+//         * A_x B_x
+// (the cup on a paired leg passes through a splitting vertex unchanged when
+// both sides share the subtree; a cup on A's side is the transpose,
+// cup_j^T = (-1)^(2j) cup_j).  The factor is folded into A's gather.
+#include "plan.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <functional>
+#include <map>
+#include <cstdlib>
+#include <mutex>
+
+#include "../../include/symtensor.h"
+#include "recouple.h"
+
+namespace sym {
+
+namespace {
+
+constexpr int kChunk = 4096;
+using TermList = std::vector<std::pair<int64_t, double>>;
+
+struct Box {
+  int ndim = 0;
+  int dims[kMaxDim], sa[kMaxDim], sb[kMaxDim], da[kMaxDim], db[kMaxDim];
+  void push(int d, int a, int b, int c, int e) {
+    dims[ndim] = d;
+    sa[ndim] = a;
+    sb[ndim] = b;
+    da[ndim] = c;
+    db[ndim] = e;
+    ++ndim;
+  }
+};
+
+// drop unit dims and merge dims that are contiguous in all four mappings
+Box simplify(const Box& in) {
+  Box b;
+  for (int i = 0; i < in.ndim; ++i) {
+    if (in.dims[i] == 1) continue;
+    if (b.ndim > 0) {
+      int j = b.ndim - 1;
+      int d = in.dims[i];
+      if ((int64_t)b.sa[j] == (int64_t)in.sa[i] * d && (int64_t)b.sb[j] == (int64_t)in.sb[i] * d &&
+          (int64_t)b.da[j] == (int64_t)in.da[i] * d && (int64_t)b.db[j] == (int64_t)in.db[i] * d) {
+        b.dims[j] *= d;
+        b.sa[j] = in.sa[i];
+        b.sb[j] = in.sb[i];
+        b.da[j] = in.da[i];
+        b.db[j] = in.db[i];
+        continue;
+      }
+    }
+    b.push(in.dims[i], in.sa[i], in.sb[i], in.da[i], in.db[i]);
+  }
+  if (b.ndim == 0) b.push(1, 0, 0, 0, 0);
+  return b;
+}
+
+void emit(Plan& P, const Box& box0, int64_t dst_off, int dst_ld, int row0, int col0, int src_slot, int dst_slot,
+          const std::vector<Term>& terms) {
+  Box box = simplify(box0);
+  int64_t total = 1;
+  for (int i = 0; i < box.ndim; ++i) total *= box.dims[i];
+  if (total >= (int64_t)1 << 31) fail(SYM_ERR_UNSUPPORTED, "block larger than 2^31 elements");
+  int term0 = (int)P.terms.size();
+  P.terms.insert(P.terms.end(), terms.begin(), terms.end());
+  for (int64_t st = 0; st < total; st += kChunk) {
+    BoxItem it{};
+    it.dst_off = dst_off;
+    it.dst_ld = dst_ld;
+    it.row0 = row0;
+    it.col0 = col0;
+    it.sel = src_slot | (dst_slot << 4);
+    it.ndim = box.ndim;
+    it.term0 = term0;
+    it.nterm = (int)terms.size();
+    it.start = (int)st;
+    it.count = (int)std::min<int64_t>(kChunk, total - st);
+    for (int i = 0; i < box.ndim; ++i) {
+      it.dims[i] = box.dims[i];
+      it.sa[i] = box.sa[i];
+      it.sb[i] = box.sb[i];
+      it.da[i] = box.da[i];
+      it.db[i] = box.db[i];
+    }
+    P.items.push_back(it);
+  }
+}
+
+void block_strides(const Tensor& T, int64_t s, int* st) {
+  int64_t acc = 1;
+  for (int l = T.rank - 1; l >= 0; --l) {
+    st[l] = (int)acc;
+    acc *= T.dim(s, l);
+  }
+}
+
+// terms[s_dst] = (src sector, coef) with dst leg n = src leg perm[n]
+std::vector<TermList> make_xform(const Tensor& src, const std::vector<int>& perm, const Tensor& dst) {
+  std::vector<TermList> out(dst.nsec());
+  const int k = src.rank;
+  if (src.group == SYM_U1) {
+    std::vector<int> key(k);
+    for (int64_t s = 0; s < dst.nsec(); ++s) {
+      for (int n = 0; n < k; ++n) key[perm[n]] = dst.p(s, n);
+      int64_t ss = src.find(key);
+      if (ss < 0) fail(SYM_ERR_ARG, "internal: permuted sector missing");
+      out[s].push_back({ss, 1.0});
+    }
+    return out;
+  }
+  int64_t s = 0;
+  while (s < dst.nsec()) {
+    int64_t e = s + 1;
+    while (e < dst.nsec() && std::equal(dst.pos.begin() + e * k, dst.pos.begin() + (e + 1) * k, dst.pos.begin() + s * k))
+      ++e;
+    std::vector<int> srcpos(k), spins(k);
+    for (int n = 0; n < k; ++n) srcpos[perm[n]] = dst.p(s, n);
+    for (int l = 0; l < k; ++l) spins[l] = src.legs[l].labels[srcpos[l]];
+    Gamma g = tree_transform(spins, src.tree, perm, dst.tree);
+    std::vector<int64_t> so(g.out_labels.size()), si(g.in_labels.size());
+    for (size_t o = 0; o < so.size(); ++o) {
+      std::vector<int> key(dst.pos.begin() + s * k, dst.pos.begin() + (s + 1) * k);
+      key.insert(key.end(), g.out_labels[o].begin(), g.out_labels[o].end());
+      so[o] = dst.find(key);
+    }
+    for (size_t i = 0; i < si.size(); ++i) {
+      std::vector<int> key(srcpos);
+      key.insert(key.end(), g.in_labels[i].begin(), g.in_labels[i].end());
+      si[i] = src.find(key);
+    }
+    for (size_t o = 0; o < so.size(); ++o) {
+      if (so[o] < 0) fail(SYM_ERR_ARG, "internal: recoupled sector missing");
+      for (size_t i = 0; i < si.size(); ++i) {
+        double c = g.G[o * si.size() + i];
+        if (std::fabs(c) > 1e-13 && si[i] >= 0) out[so[o]].push_back({si[i], c});
+      }
+    }
+    s = e;
+  }
+  return out;
+}
+
+std::vector<TermList> transpose_xform(const std::vector<TermList>& x, int64_t nsrc) {
+  std::vector<TermList> t(nsrc);
+  for (int64_t s = 0; s < (int64_t)x.size(); ++s)
+    for (auto& pc : x[s]) t[pc.first].push_back({s, pc.second});
+  return t;
+}
+
+// Row/column groups of a tensor in matrix form (legs [rows..., cols...],
+// SU(2) tree = comb over rows and comb over cols joined at the root).  A
+// group key is the positions of the group's legs plus the spins of its
+// subtree's nodes below the subtree top (the top is the sector key x).
+std::vector<int> row_key(const Tensor& T, int64_t s, int nr) {
+  std::vector<int> k(T.pos.begin() + s * T.rank, T.pos.begin() + s * T.rank + nr);
+  if (T.group == SYM_SU2 && nr >= 3) k.insert(k.end(), T.inner_of(s), T.inner_of(s) + (nr - 2));
+  return k;
+}
+std::vector<int> col_key(const Tensor& T, int64_t s, int nr) {
+  const int nc = T.rank - nr;
+  std::vector<int> k(T.pos.begin() + s * T.rank + nr, T.pos.begin() + (s + 1) * T.rank);
+  if (T.group == SYM_SU2 && nc >= 3) {
+    const int c0 = nr >= 1 ? nr - 1 : 0;
+    k.insert(k.end(), T.inner_of(s) + c0, T.inner_of(s) + c0 + (nc - 2));
+  }
+  return k;
+}
+
+struct MatForm {
+  int nr = 0, nc = 0;
+  std::vector<int> xs;
+  std::map<int, int> xi;
+  std::vector<int64_t> rows, cols;
+  std::vector<int> sx;
+  std::vector<int64_t> r0, c0;
+  std::map<std::pair<int, std::vector<int>>, int64_t> rowoff, coloff;
+};
+
+MatForm make_matform(const Tensor& T, int nr, const std::function<int(int64_t)>& xkey) {
+  MatForm M;
+  M.nr = nr;
+  M.nc = T.rank - nr;
+  std::map<int, std::map<std::vector<int>, int64_t>> rg, cg;
+  M.sx.resize(T.nsec());
+  std::vector<int> xv(T.nsec());
+  for (int64_t s = 0; s < T.nsec(); ++s) {
+    int x = xkey(s);
+    xv[s] = x;
+    int64_t rs = 1, cs = 1;
+    for (int l = 0; l < nr; ++l) rs *= T.dim(s, l);
+    for (int l = nr; l < T.rank; ++l) cs *= T.dim(s, l);
+    rg[x][row_key(T, s, nr)] = rs;
+    cg[x][col_key(T, s, nr)] = cs;
+  }
+  for (auto& kv : rg) {
+    M.xi[kv.first] = (int)M.xs.size();
+    M.xs.push_back(kv.first);
+    int64_t off = 0;
+    for (auto& g : kv.second) {
+      M.rowoff[{kv.first, g.first}] = off;
+      off += g.second;
+    }
+    M.rows.push_back(off);
+    int64_t coff = 0;
+    for (auto& g : cg[kv.first]) {
+      M.coloff[{kv.first, g.first}] = coff;
+      coff += g.second;
+    }
+    M.cols.push_back(coff);
+  }
+  M.r0.resize(T.nsec());
+  M.c0.resize(T.nsec());
+  for (int64_t s = 0; s < T.nsec(); ++s) {
+    M.sx[s] = M.xi[xv[s]];
+    M.r0[s] = M.rowoff[{xv[s], row_key(T, s, nr)}];
+    M.c0[s] = M.coloff[{xv[s], col_key(T, s, nr)}];
+  }
+  return M;
+}
+
+// weights of the legs inside their row group (rw) / column group (cw)
+void group_weights(const Tensor& Tm, int64_t s, int nr, int* rw, int* cw) {
+  int64_t acc = 1;
+  for (int n = nr - 1; n >= 0; --n) {
+    rw[n] = (int)acc;
+    cw[n] = 0;
+    acc *= Tm.dim(s, n);
+  }
+  acc = 1;
+  for (int n = Tm.rank - 1; n >= nr; --n) {
+    cw[n] = (int)acc;
+    rw[n] = 0;
+    acc *= Tm.dim(s, n);
+  }
+}
+
+int su2_top(const Tensor& T, int64_t s, int nr) {
+  int nc = T.rank - nr;
+  if (nr == 0 || nc == 0) return 0;
+  if (nr == 1) return T.label(s, 0);
+  return T.inner_of(s)[nr - 2];
+}
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+Tensor permuted_tensor(const Tensor& T, const std::vector<int>& perm, const Tree& tree, int total) {
+  std::vector<Leg> legs;
+  for (int p : perm) legs.push_back(T.legs[p]);
+  return make_tensor(T.group, legs, total, tree);
+}
+
+}  // namespace
+
+bool Plan::f64() const { return precision == SYM_PREC_FP64; }
+
+namespace {
+int* g_err_word = nullptr;
+std::mutex g_err_mu;
+}  // namespace
+
+int* device_error_word() {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (!g_err_word) {
+    cudaError_t e = cudaMalloc(&g_err_word, sizeof(int));
+    if (e != cudaSuccess) {
+      g_err_word = nullptr;
+      fail(SYM_ERR_CUDA, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    cudaMemset(g_err_word, 0, sizeof(int));
+  }
+  return g_err_word;
+}
+
+int take_device_error() {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (!g_err_word) return SYM_OK;
+  int h = 0;
+  if (cudaMemcpy(&h, g_err_word, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SYM_ERR_CUDA;
+  if (h != 0) cudaMemset(g_err_word, 0, sizeof(int));
+  return h != 0 ? h : SYM_OK;
+}
+
+void* DeviceArena::alloc(size_t bytes, bool zero) {
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(e == cudaErrorMemoryAllocation ? SYM_ERR_OOM : SYM_ERR_CUDA,
+         std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  ptrs.push_back(p);
+  if (zero) {
+    e = cudaMemset(p, 0, bytes);
+    if (e != cudaSuccess) fail(SYM_ERR_CUDA, std::string("cudaMemset failed: ") + cudaGetErrorString(e));
+  }
+  return p;
+}
+
+DeviceArena::~DeviceArena() {
+  for (void* p : ptrs) cudaFree(p);
+}
+
+// Largest element offset every box item can touch, checked against the size
+// of the buffer in its source / destination slot (elements).  Strides are
+// non-negative, so the extreme is at the last index of every dimension.
+void Plan::validate(const int64_t* src_elems, const int64_t* dst_elems, bool dst0_image) const {
+  for (const BoxItem& it : items) {
+    int64_t sa = 0, sb = 0, da = 0, db = 0;
+    for (int d = 0; d < it.ndim; ++d) {
+      if (it.dims[d] < 1 || it.sa[d] < 0 || it.sb[d] < 0 || it.da[d] < 0 || it.db[d] < 0)
+        fail(SYM_ERR_ARG, "internal: negative stride or empty dim in a work item");
+      sa += (int64_t)(it.dims[d] - 1) * it.sa[d];
+      sb += (int64_t)(it.dims[d] - 1) * it.sb[d];
+      da += (int64_t)(it.dims[d] - 1) * it.da[d];
+      db += (int64_t)(it.dims[d] - 1) * it.db[d];
+    }
+    const int ss = it.sel & 3, ds = (it.sel >> 4) & 3;
+    for (int i = 0; i < it.nterm; ++i) {
+      const Term& t = terms[it.term0 + i];
+      if (t.off < 0 || t.ld < 0 || t.off + t.ld * sa + sb >= src_elems[ss])
+        fail(SYM_ERR_ARG, "internal: work item reads past its source buffer");
+    }
+    int64_t last;
+    if (ds == 0 && dst0_image) {
+      const int64_t row = it.row0 + da, col = it.col0 + db;
+      if (it.row0 < 0 || it.col0 < 0 || (col >> 6) >= it.dst_ld)
+        fail(SYM_ERR_ARG, "internal: image column past its K tiles");
+      last = it.dst_off + ((row >> 7) * it.dst_ld + (col >> 6)) * 8192 + 8191;
+    } else {
+      last = it.dst_off + (int64_t)it.dst_ld * da + db;
+    }
+    if (it.dst_off < 0 || last >= dst_elems[ds]) fail(SYM_ERR_ARG, "internal: work item writes past its destination");
+  }
+}
+
+void Plan::upload() {
+  const char* dry_env = std::getenv("SYM_PLAN_DRYRUN");
+  if (dry_env && dry_env[0] == '1') {
+    dry = true;  // host-only planning and validation; the plan cannot run
+    return;
+  }
+  auto up = [&](const void* h, size_t bytes) -> void* {
+    void* d = arena.alloc(bytes, false);
+    if (bytes) {
+      cudaError_t e = cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) fail(SYM_ERR_CUDA, std::string("cudaMemcpy failed: ") + cudaGetErrorString(e));
+    }
+    return d;
+  };
+  // validate every work unit against the buffers it touches (host-side bounds check)
+  for (const BoxItem& it : items) {
+    if (it.term0 < 0 || it.nterm < 0 || (size_t)it.term0 + it.nterm > terms.size())
+      fail(SYM_ERR_ARG, "internal: term range out of bounds");
+    if (it.ndim < 1 || it.ndim > kMaxDim || it.count <= 0 || it.start < 0) fail(SYM_ERR_ARG, "internal: bad box");
+  }
+  d_items = static_cast<BoxItem*>(up(items.data(), items.size() * sizeof(BoxItem)));
+  d_terms = static_cast<Term*>(up(terms.data(), terms.size() * sizeof(Term)));
+  if (f64())
+    d_secs = up(secs64.data(), secs64.size() * sizeof(GemmSector64));
+  else
+    d_secs = up(secs_tc.data(), secs_tc.size() * sizeof(TcSector));
+  d_tiles = static_cast<GemmTile*>(up(tiles.data(), tiles.size() * sizeof(GemmTile)));
+  if (kind == CONTRACT) {
+    if (f64()) {
+      ops0 = arena.alloc(ops_elems * sizeof(double), false);
+      outm = arena.alloc(outm_elems * sizeof(double), false);
+    } else {
+      ops0 = arena.alloc(ops_elems * 2, true);  // zero padding of the images
+      ops1 = arena.alloc(ops_elems * 2, true);
+      outm = arena.alloc(outm_elems * sizeof(float), false);
+    }
+  }
+  d_err = device_error_word();
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) fail(SYM_ERR_CUDA, std::string("plan upload: ") + cudaGetErrorString(e));
+}
+
+Leg fused_leg(const Leg& a, const Leg& b, int group) {
+  if (a.dir != b.dir) fail(SYM_ERR_INCOMPATIBLE_LEGS, "fused legs must have equal directions");
+  std::map<int, int64_t> deg;
+  for (size_t i = 0; i < a.labels.size(); ++i)
+    for (size_t j = 0; j < b.labels.size(); ++j) {
+      int64_t d = (int64_t)a.degens[i] * b.degens[j];
+      if (group == SYM_U1) {
+        deg[a.labels[i] + b.labels[j]] += d;
+      } else {
+        for (int c = std::abs(a.labels[i] - b.labels[j]); c <= a.labels[i] + b.labels[j]; c += 2) deg[c] += d;
+      }
+    }
+  Leg d;
+  d.dir = a.dir;
+  for (auto& kv : deg) {
+    if (kv.second >= (int64_t)1 << 31) fail(SYM_ERR_UNSUPPORTED, "fused degeneracy too large");
+    d.labels.push_back(kv.first);
+    d.degens.push_back((int)kv.second);
+  }
+  return d;
+}
+
+// offset of the pair (ia, ib) inside fused label c (pairs: ia slowest)
+static int64_t pair_offset(const Leg& a, const Leg& b, int group, int c, int ia, int ib) {
+  int64_t off = 0;
+  for (size_t i = 0; i < a.labels.size(); ++i)
+    for (size_t j = 0; j < b.labels.size(); ++j) {
+      bool ok = group == SYM_U1 ? a.labels[i] + b.labels[j] == c : triangle(a.labels[i], b.labels[j], c);
+      if (!ok) continue;
+      if ((int)i == ia && (int)j == ib) return off;
+      off += (int64_t)a.degens[i] * b.degens[j];
+    }
+  fail(SYM_ERR_ARG, "internal: pair not in fused label");
+}
+
+Tree fuse_pair_tree(int k, int f) {
+  Tree t;
+  t.k = k;
+  t.nodes.push_back({f, f + 1});
+  std::vector<int> items;
+  for (int i = 0; i < k; ++i) {
+    if (i == f) items.push_back(k);
+    else if (i != f + 1) items.push_back(i);
+  }
+  int top = items[0];
+  for (size_t i = 1; i < items.size(); ++i) {
+    t.nodes.push_back({top, items[i]});
+    top = k + (int)t.nodes.size() - 1;
+  }
+  t.validate();
+  return t;
+}
+
+// ------------------------------------------------------------------ transforms --
+// mode 0: permute (out leg n = in leg perm[n]); 1: fuse legs (leg, leg+1);
+// 2: split leg `leg` of `in` into out legs (leg, leg+1).
+std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const std::vector<int>& perm,
+                                     int precision, int mode, int leg) {
+  auto P = std::make_unique<Plan>();
+  P->kind = Plan::TRANSFORM;
+  P->precision = precision;
+  P->numel_a = in.numel();
+  P->numel_c = out.numel();
+  const int k = in.rank;
+  int ist[kMaxDim], ost[kMaxDim];
+  if (mode == 0) {
+    std::vector<int> pinv(k);
+    for (int n = 0; n < k; ++n) pinv[perm[n]] = n;
+    auto X = make_xform(in, perm, out);
+    for (int64_t s = 0; s < out.nsec(); ++s) {
+      block_strides(out, s, ost);
+      std::vector<Term> terms;
+      for (auto& pc : X[s]) terms.push_back({in.offs[pc.first], 1, pc.second});
+      Box b;
+      int64_t src0 = X[s].empty() ? -1 : X[s][0].first;
+      for (int l = 0; l < k; ++l) {
+        int d = out.dim(s, pinv[l]);
+        int sst = 0;
+        if (src0 >= 0) {
+          block_strides(in, src0, ist);
+          sst = ist[l];
+        }
+        b.push(d, sst, 0, ost[pinv[l]], 0);
+      }
+      emit(*P, b, out.offs[s], 1, 0, 0, 0, 1, terms);
+    }
+  } else if (mode == 1) {
+    const int f = leg;
+    const Leg& la = in.legs[f];
+    const Leg& lb = in.legs[f + 1];
+    const Leg& ld = out.legs[f];
+    Tensor mid = in.group == SYM_SU2 ? make_tensor(in.group, in.legs, 0, fuse_pair_tree(k, f)) : in;
+    std::vector<TermList> X;
+    std::vector<int> idp(k);
+    for (int i = 0; i < k; ++i) idp[i] = i;
+    if (in.group == SYM_SU2) X = make_xform(in, idp, mid);
+    for (int64_t sm = 0; sm < mid.nsec(); ++sm) {
+      int c = in.group == SYM_U1 ? la.labels[mid.p(sm, f)] + lb.labels[mid.p(sm, f + 1)] : mid.inner_of(sm)[0];
+      int iq = (int)(std::lower_bound(ld.labels.begin(), ld.labels.end(), c) - ld.labels.begin());
+      std::vector<int> key;
+      for (int l = 0; l < k; ++l) {
+        if (l == f) key.push_back(iq);
+        else if (l != f + 1) key.push_back(mid.p(sm, l));
+      }
+      if (in.group == SYM_SU2) key.insert(key.end(), mid.inner_of(sm) + 1, mid.inner_of(sm) + mid.nin);
+      int64_t so = out.find(key);
+      if (so < 0) fail(SYM_ERR_ARG, "internal: fused sector missing");
+      int64_t row0 = pair_offset(la, lb, in.group, c, mid.p(sm, f), mid.p(sm, f + 1));
+      block_strides(out, so, ost);
+      std::vector<Term> terms;
+      if (in.group == SYM_U1) {
+        terms.push_back({in.offs[sm], 1, 1.0});
+      } else {
+        for (auto& pc : X[sm]) terms.push_back({in.offs[pc.first], 1, pc.second});
+      }
+      block_strides(in, in.group == SYM_U1 ? sm : (X[sm].empty() ? 0 : X[sm][0].first), ist);
+      Box b;
+      int db_ = mid.dim(sm, f + 1);
+      for (int l = 0; l < k; ++l) {
+        int d = mid.dim(sm, l);
+        int dst = l < f ? ost[l] : l == f ? db_ * ost[f] : l == f + 1 ? ost[f] : ost[l - 1];
+        b.push(d, ist[l], 0, dst, 0);
+      }
+      emit(*P, b, out.offs[so] + row0 * ost[f], 1, 0, 0, 0, 1, terms);
+    }
+  } else {
+    const int f = leg;  // out legs f, f+1 come from in leg f
+    const int ko = out.rank;
+    const Leg& la = out.legs[f];
+    const Leg& lb = out.legs[f + 1];
+    Tensor mid = in.group == SYM_SU2 ? make_tensor(in.group, out.legs, 0, fuse_pair_tree(ko, f)) : out;
+    std::vector<TermList> X;
+    std::vector<int> idp(ko);
+    for (int i = 0; i < ko; ++i) idp[i] = i;
+    if (in.group == SYM_SU2) X = make_xform(mid, idp, out);
+    // where each mid sector lives inside `in`
+    std::vector<int64_t> m_in(mid.nsec()), m_row(mid.nsec());
+    for (int64_t sm = 0; sm < mid.nsec(); ++sm) {
+      int c = in.group == SYM_U1 ? la.labels[mid.p(sm, f)] + lb.labels[mid.p(sm, f + 1)] : mid.inner_of(sm)[0];
+      const Leg& lf = in.legs[f];
+      int iq = (int)(std::lower_bound(lf.labels.begin(), lf.labels.end(), c) - lf.labels.begin());
+      std::vector<int> key;
+      for (int l = 0; l < ko; ++l) {
+        if (l == f) key.push_back(iq);
+        else if (l != f + 1) key.push_back(mid.p(sm, l));
+      }
+      if (in.group == SYM_SU2) key.insert(key.end(), mid.inner_of(sm) + 1, mid.inner_of(sm) + mid.nin);
+      m_in[sm] = in.find(key);
+      if (m_in[sm] < 0) fail(SYM_ERR_ARG, "internal: split source sector missing");
+      m_row[sm] = pair_offset(la, lb, in.group, c, mid.p(sm, f), mid.p(sm, f + 1));
+    }
+    for (int64_t s = 0; s < out.nsec(); ++s) {
+      block_strides(out, s, ost);
+      TermList tl = in.group == SYM_U1 ? TermList{{s, 1.0}} : X[s];
+      std::vector<Term> terms;
+      int sa_[kMaxDim] = {0}, sb_[kMaxDim] = {0};
+      bool first = true;
+      for (auto& pc : tl) {
+        int64_t sm = pc.first;
+        int64_t si = m_in[sm];
+        block_strides(in, si, ist);
+        int64_t dfused = in.dim(si, f);
+        int64_t stf = ist[f];
+        terms.push_back({in.offs[si] + m_row[sm] * stf, dfused, pc.second});
+        if (first) {
+          // in legs l < f: stride = dfused * (stride without the fused dim)
+          for (int l = 0; l < f; ++l) {
+            sa_[l] = (int)(ist[l] / dfused);
+            sb_[l] = 0;
+          }
+          sa_[f] = 0;
+          sb_[f] = (int)(mid.dim(sm, f + 1) * stf);
+          sa_[f + 1] = 0;
+          sb_[f + 1] = (int)stf;
+          for (int l = f + 2; l < ko; ++l) {
+            sa_[l] = 0;
+            sb_[l] = ist[l - 1];
+          }
+          first = false;
+        }
+      }
+      Box b;
+      for (int l = 0; l < ko; ++l) b.push(out.dim(s, l), sa_[l], sb_[l], ost[l], 0);
+      emit(*P, b, out.offs[s], 1, 0, 0, 0, 1, terms);
+    }
+  }
+  P->xform = {0, (int)P->items.size()};
+  {
+    const int64_t src[4] = {in.numel(), 0, 0, 0};
+    const int64_t dst[4] = {0, out.numel(), 0, 0};
+    P->validate(src, dst, false);
+  }
+  P->upload();
+  return P;
+}
+
+// ----------------------------------------------------------------- contraction --
+std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std::vector<int>& pairsA,
+                                    const std::vector<int>& pairsB, const Tensor& C, int precision) {
+  auto P = std::make_unique<Plan>();
+  P->kind = Plan::CONTRACT;
+  P->precision = precision;
+  const bool f64 = precision == SYM_PREC_FP64;
+  const int nc = (int)pairsA.size();
+  std::vector<int> freeA, freeB;
+  for (int l = 0; l < A.rank; ++l)
+    if (std::find(pairsA.begin(), pairsA.end(), l) == pairsA.end()) freeA.push_back(l);
+  for (int l = 0; l < B.rank; ++l)
+    if (std::find(pairsB.begin(), pairsB.end(), l) == pairsB.end()) freeB.push_back(l);
+  const int na = (int)freeA.size(), nb = (int)freeB.size();
+  std::vector<int> permA(freeA), permB(pairsB);
+  permA.insert(permA.end(), pairsA.begin(), pairsA.end());
+  permB.insert(permB.end(), freeB.begin(), freeB.end());
+  const bool su2 = A.group == SYM_SU2;
+  Tensor Am = permuted_tensor(A, permA, Tree::comb_pair(na, nc), A.total);
+  Tensor Bm = permuted_tensor(B, permB, Tree::comb_pair(nc, nb), B.total);
+  std::vector<Leg> clegs;
+  for (int l : freeA) clegs.push_back(A.legs[l]);
+  for (int l : freeB) clegs.push_back(B.legs[l]);
+  Tensor Cn = make_tensor(A.group, clegs, A.total + B.total, Tree::comb_pair(na, nb));
+  const bool natural = !su2 || C.tree == Cn.tree;
+
+  auto XA = make_xform(A, permA, Am);
+  auto XB = make_xform(B, permB, Bm);
+  // SU(2) normalisation folded into A's gather terms
+  if (su2) {
+    for (int64_t s = 0; s < Am.nsec(); ++s) {
+      int x = su2_top(Am, s, na);
+      double f = ((x & 1) ? -1.0 : 1.0) / std::sqrt((double)x + 1.0);
+      for (int i = 0; i < nc; ++i)
+        if (A.legs[pairsA[i]].dir == -1 && (Am.label(s, na + i) & 1)) f = -f;
+      for (auto& pc : XA[s]) pc.second *= f;
+    }
+  }
+  std::vector<TermList> XC, XCt;
+  if (!natural) {
+    std::vector<int> idp(C.rank);
+    for (int i = 0; i < C.rank; ++i) idp[i] = i;
+    XC = make_xform(Cn, idp, C);
+    XCt = transpose_xform(XC, Cn.nsec());
+  }
+  auto XAt = transpose_xform(XA, A.nsec());
+  auto XBt = transpose_xform(XB, B.nsec());
+
+  auto keyA = [&](int64_t s) {
+    if (su2) return su2_top(Am, s, na);
+    int x = 0;
+    for (int n = na; n < Am.rank; ++n) x += Am.legs[n].dir * Am.label(s, n);
+    return x;
+  };
+  auto keyB = [&](int64_t s) {
+    if (su2) return su2_top(Bm, s, nc);
+    int x = 0;
+    for (int n = 0; n < nc; ++n) x -= Bm.legs[n].dir * Bm.label(s, n);
+    return x;
+  };
+  auto keyC = [&](int64_t s) {
+    if (su2) return su2_top(Cn, s, na);
+    int x = A.total;
+    for (int n = 0; n < na; ++n) x -= Cn.legs[n].dir * Cn.label(s, n);
+    return x;
+  };
+  MatForm MA = make_matform(Am, na, keyA);
+  MatForm MB = make_matform(Bm, nc, keyB);
+  MatForm MC = make_matform(Cn, na, keyC);
+
+  // GEMM sectors: x present on both sides
+  struct G {
+    int x;
+    int64_t m, n, k;
+    int64_t a, b, c, dc1, bt, at, dc2, da, db;  // buffer offsets
+  };
+  std::vector<G> gs;
+  std::map<int, int> gofx;
+  for (size_t i = 0; i < MA.xs.size(); ++i) {
+    auto it = MB.xi.find(MA.xs[i]);
+    if (it == MB.xi.end()) continue;
+    G g{};
+    g.x = MA.xs[i];
+    g.m = MA.rows[i];
+    g.k = MA.cols[i];
+    g.n = MB.cols[it->second];
+    if (MB.rows[it->second] != g.k) fail(SYM_ERR_INCOMPATIBLE_LEGS, "contracted sector dimensions differ");
+    if (g.m <= 0 || g.n <= 0 || g.k <= 0) continue;
+    if (g.m >= ((int64_t)1 << 31) || g.n >= ((int64_t)1 << 31) || g.k >= ((int64_t)1 << 31))
+      fail(SYM_ERR_UNSUPPORTED, "sector matrix dimension too large");
+    gofx[g.x] = (int)gs.size();
+    gs.push_back(g);
+  }
+  // buffer layout
+  const int64_t T = f64 ? 64 : 128;
+  auto img = [&](int64_t rows, int64_t kk) { return cdiv(rows, 128) * cdiv(kk, 64) * 8192; };
+  int64_t ops = 0, outm = 0;
+  for (auto& g : gs) {
+    g.a = ops;
+    ops += f64 ? g.m * g.k : img(g.m, g.k);
+    g.b = ops;
+    ops += f64 ? g.k * g.n : img(g.n, g.k);
+  }
+  for (auto& g : gs) {
+    g.dc1 = ops;
+    ops += f64 ? g.m * g.n : img(g.m, g.n);
+    g.bt = ops;
+    ops += f64 ? g.n * g.k : img(g.k, g.n);
+    g.at = ops;
+    ops += f64 ? g.k * g.m : img(g.k, g.m);
+    g.dc2 = g.dc1;
+    if (!f64) {
+      g.dc2 = ops;
+      ops += img(g.n, g.m);
+    }
+  }
+  for (auto& g : gs) {
+    g.c = outm;
+    outm += g.m * g.n;
+    g.da = outm;
+    outm += g.m * g.k;
+    g.db = outm;
+    outm += g.k * g.n;
+  }
+  P->ops_elems = ops;
+  P->outm_elems = outm;
+  for (auto& g : gs) P->flops_fwd += 2.0 * (double)g.m * (double)g.n * (double)g.k;
+  P->numel_a = A.numel();
+  P->numel_b = B.numel();
+  P->numel_c = C.numel();
+
+  // GEMM sectors and tiles: [fwd][bwd dA][bwd dB]
+  auto add_sector = [&](int64_t m, int64_t n, int64_t k, int64_t aoff, int64_t lda, int64_t boff, int64_t ldb,
+                        int64_t coff) {
+    if (f64) {
+      GemmSector64 s{(int)m, (int)n, (int)k, (int)lda, (int)ldb, (int)n, aoff, boff, coff, 1.0};
+      P->secs64.push_back(s);
+      return (int)P->secs64.size() - 1;
+    }
+    TcSector s{(int)m, (int)n, (int)k, (int)cdiv(k, 64), aoff, boff, coff, (int)n, 1.0f};
+    P->secs_tc.push_back(s);
+    return (int)P->secs_tc.size() - 1;
+  };
+  auto add_tiles = [&](int sec, int64_t m, int64_t n, std::vector<std::pair<int64_t, GemmTile>>& v, int64_t k) {
+    for (int64_t mt = 0; mt < cdiv(m, T); ++mt)
+      for (int64_t nt = 0; nt < cdiv(n, T); ++nt) v.push_back({k, GemmTile{sec, (int)mt, (int)nt}});
+  };
+  auto flush_tiles = [&](std::vector<std::pair<int64_t, GemmTile>>& v) {
+    std::stable_sort(v.begin(), v.end(), [](auto& a, auto& b) { return a.first > b.first; });
+    Range r{(int)P->tiles.size(), (int)v.size()};
+    for (auto& t : v) P->tiles.push_back(t.second);
+    return r;
+  };
+  {
+    std::vector<std::pair<int64_t, GemmTile>> v;
+    for (auto& g : gs) add_tiles(add_sector(g.m, g.n, g.k, g.a, g.k, g.b, g.n, g.c), g.m, g.n, v, g.k);
+    P->fwd_tiles = flush_tiles(v);
+    v.clear();
+    for (auto& g : gs) add_tiles(add_sector(g.m, g.k, g.n, g.dc1, g.n, g.bt, g.k, g.da), g.m, g.k, v, g.n);
+    P->bwd_tiles_a = flush_tiles(v);
+    v.clear();
+    for (auto& g : gs) add_tiles(add_sector(g.k, g.n, g.m, g.at, g.m, g.dc2, g.n, g.db), g.k, g.n, v, g.m);
+    P->bwd_tiles_b = flush_tiles(v);
+  }
+
+  int rw[kMaxDim], cw[kMaxDim], st[kMaxDim];
+  std::vector<int> pinvA(A.rank), pinvB(B.rank);
+  for (int n = 0; n < A.rank; ++n) pinvA[permA[n]] = n;
+  for (int n = 0; n < B.rank; ++n) pinvB[permB[n]] = n;
+
+  // box of a source block of S gathered into a matrix of Sm (S leg l -> Sm leg pinv[l])
+  auto gather_box = [&](const Tensor& S, const std::vector<int>& pinv, const Tensor& Sm, int64_t sm, int64_t ssrc,
+                        int nrows, bool swap_rc) {
+    group_weights(Sm, sm, nrows, rw, cw);
+    block_strides(S, ssrc, st);
+    Box b;
+    for (int l = 0; l < S.rank; ++l) {
+      int n = pinv[l];
+      b.push(S.dim(ssrc, l), st[l], 0, swap_rc ? cw[n] : rw[n], swap_rc ? rw[n] : cw[n]);
+    }
+    return b;
+  };
+  auto terms_of = [&](const TermList& tl, const Tensor& S) {
+    std::vector<Term> t;
+    for (auto& pc : tl) t.push_back({S.offs[pc.first], 1, pc.second});
+    return t;
+  };
+
+  // ---- forward gather: A -> A operand, B -> B operand
+  int begin = (int)P->items.size();
+  for (int64_t s = 0; s < Am.nsec(); ++s) {
+    auto gi = gofx.find(MA.xs[MA.sx[s]]);
+    if (gi == gofx.end() || XA[s].empty()) continue;
+    const G& g = gs[gi->second];
+    Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, false);
+    if (f64)
+      emit(*P, b, g.a + MA.r0[s] * g.k + MA.c0[s], (int)g.k, 0, 0, 0, 0, terms_of(XA[s], A));
+    else
+      emit(*P, b, g.a, (int)cdiv(g.k, 64), (int)MA.r0[s], (int)MA.c0[s], 0, 0, terms_of(XA[s], A));
+  }
+  for (int64_t s = 0; s < Bm.nsec(); ++s) {
+    auto gi = gofx.find(MB.xs[MB.sx[s]]);
+    if (gi == gofx.end() || XB[s].empty()) continue;
+    const G& g = gs[gi->second];
+    if (f64) {
+      Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, false);
+      emit(*P, b, g.b + MB.r0[s] * g.n + MB.c0[s], (int)g.n, 0, 0, 1, 0, terms_of(XB[s], B));
+    } else {
+      Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, true);
+      emit(*P, b, g.b, (int)cdiv(g.k, 64), (int)MB.c0[s], (int)MB.r0[s], 1, 0, terms_of(XB[s], B));
+    }
+  }
+  P->fwd_gather = {begin, (int)P->items.size() - begin};
+
+  // ---- forward scatter: C_x -> C blocks (SU(2): Gamma to the requested tree)
+  auto cn_term = [&](int64_t sn, double coef, std::vector<Term>& t) {
+    auto gi = gofx.find(MC.xs[MC.sx[sn]]);
+    if (gi == gofx.end()) return;
+    const G& g = gs[gi->second];
+    // C_nat row group lives in A's row groups, column group in B's column groups
+    int x = MC.xs[MC.sx[sn]];
+    int64_t r0 = MA.rowoff.at({x, row_key(Cn, sn, na)});
+    int64_t c0 = MB.coloff.at({x, col_key(Cn, sn, na)});
+    t.push_back({g.c + r0 * g.n + c0, g.n, coef});
+  };
+  begin = (int)P->items.size();
+  for (int64_t s = 0; s < C.nsec(); ++s) {
+    std::vector<Term> t;
+    if (natural) {
+      cn_term(s, 1.0, t);
+    } else {
+      for (auto& pc : XC[s]) cn_term(pc.first, pc.second, t);
+    }
+    group_weights(C, s, na, rw, cw);
+    block_strides(C, s, st);
+    Box b;
+    for (int l = 0; l < C.rank; ++l) b.push(C.dim(s, l), rw[l], cw[l], st[l], 0);
+    emit(*P, b, C.offs[s], 1, 0, 0, 3, 1, t);
+  }
+  P->fwd_scatter = {begin, (int)P->items.size() - begin};
+
+  // ---- backward gathers: [dA-only: B^T][shared (fp64): dC][dB-only: A^T]
+  int b0 = (int)P->items.size();
+  for (int64_t s = 0; s < Bm.nsec(); ++s) {
+    auto gi = gofx.find(MB.xs[MB.sx[s]]);
+    if (gi == gofx.end() || XB[s].empty()) continue;
+    const G& g = gs[gi->second];
+    if (f64) {
+      Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, true);
+      emit(*P, b, g.bt + MB.c0[s] * g.k + MB.r0[s], (int)g.k, 0, 0, 1, 0, terms_of(XB[s], B));
+    } else {
+      Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, false);
+      emit(*P, b, g.bt, (int)cdiv(g.n, 64), (int)MB.r0[s], (int)MB.c0[s], 1, 0, terms_of(XB[s], B));
+    }
+  }
+  // dC into the dA-side operand (rows m, inner n)
+  std::vector<int> idC(C.rank);
+  for (int i = 0; i < C.rank; ++i) idC[i] = i;
+  auto dc_terms = [&](int64_t sn) {
+    std::vector<Term> t;
+    if (natural) {
+      t.push_back({C.offs[sn], 1, 1.0});
+    } else {
+      for (auto& pc : XCt[sn]) t.push_back({C.offs[pc.first], 1, pc.second});
+    }
+    return t;
+  };
+  int b1 = (int)P->items.size();
+  for (int64_t sn = 0; sn < Cn.nsec(); ++sn) {
+    auto gi = gofx.find(MC.xs[MC.sx[sn]]);
+    if (gi == gofx.end()) continue;
+    const G& g = gs[gi->second];
+    int x = MC.xs[MC.sx[sn]];
+    int64_t r0 = MA.rowoff.at({x, row_key(Cn, sn, na)});
+    int64_t c0 = MB.coloff.at({x, col_key(Cn, sn, na)});
+    auto t = dc_terms(sn);
+    if (t.empty()) continue;
+    Box b = gather_box(Cn, idC, Cn, sn, sn, na, false);
+    if (f64)
+      emit(*P, b, g.dc1 + r0 * g.n + c0, (int)g.n, 0, 0, 2, 0, t);
+    else
+      emit(*P, b, g.dc1, (int)cdiv(g.n, 64), (int)r0, (int)c0, 2, 0, t);
+  }
+  int b2 = (int)P->items.size();
+  for (int64_t s = 0; s < Am.nsec(); ++s) {
+    auto gi = gofx.find(MA.xs[MA.sx[s]]);
+    if (gi == gofx.end() || XA[s].empty()) continue;
+    const G& g = gs[gi->second];
+    if (f64) {
+      Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, true);
+      emit(*P, b, g.at + MA.c0[s] * g.m + MA.r0[s], (int)g.m, 0, 0, 0, 0, terms_of(XA[s], A));
+    } else {
+      Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, true);
+      emit(*P, b, g.at, (int)cdiv(g.m, 64), (int)MA.c0[s], (int)MA.r0[s], 0, 0, terms_of(XA[s], A));
+    }
+  }
+  if (!f64) {
+    for (int64_t sn = 0; sn < Cn.nsec(); ++sn) {
+      auto gi = gofx.find(MC.xs[MC.sx[sn]]);
+      if (gi == gofx.end()) continue;
+      const G& g = gs[gi->second];
+      int x = MC.xs[MC.sx[sn]];
+      int64_t r0 = MA.rowoff.at({x, row_key(Cn, sn, na)});
+      int64_t c0 = MB.coloff.at({x, col_key(Cn, sn, na)});
+      auto t = dc_terms(sn);
+      if (t.empty()) continue;
+      Box b = gather_box(Cn, idC, Cn, sn, sn, na, true);
+      emit(*P, b, g.dc2, (int)cdiv(g.m, 64), (int)c0, (int)r0, 2, 0, t);
+    }
+  }
+  int b3 = (int)P->items.size();
+  if (f64) {
+    P->bwd_gather_a = {b0, b2 - b0};  // B^T and dC
+    P->bwd_gather_b = {b1, b3 - b1};  // dC and A^T
+  } else {
+    P->bwd_gather_a = {b0, b2 - b0};  // B^T, dC (rows m)
+    P->bwd_gather_b = {b2, b3 - b2};              // A^T, dC (rows n)
+  }
+
+  // ---- backward scatters: dA_x -> dA blocks (Gamma^T), dB_x -> dB blocks
+  begin = (int)P->items.size();
+  for (int64_t s = 0; s < A.nsec(); ++s) {
+    std::vector<Term> t;
+    int64_t sm0 = -1;
+    for (auto& pc : XAt[s]) {
+      int64_t sm = pc.first;
+      auto gi = gofx.find(MA.xs[MA.sx[sm]]);
+      if (gi == gofx.end()) continue;
+      const G& g = gs[gi->second];
+      t.push_back({g.da + MA.r0[sm] * g.k + MA.c0[sm], g.k, pc.second});
+      if (sm0 < 0) sm0 = sm;
+    }
+    block_strides(A, s, st);
+    Box b;
+    if (sm0 >= 0) group_weights(Am, sm0, na, rw, cw);
+    for (int l = 0; l < A.rank; ++l) {
+      int n = pinvA[l];
+      b.push(A.dim(s, l), sm0 >= 0 ? rw[n] : 0, sm0 >= 0 ? cw[n] : 0, st[l], 0);
+    }
+    emit(*P, b, A.offs[s], 1, 0, 0, 3, 2, t);
+  }
+  P->bwd_scatter_a = {begin, (int)P->items.size() - begin};
+  begin = (int)P->items.size();
+  for (int64_t s = 0; s < B.nsec(); ++s) {
+    std::vector<Term> t;
+    int64_t sm0 = -1;
+    for (auto& pc : XBt[s]) {
+      int64_t sm = pc.first;
+      auto gi = gofx.find(MB.xs[MB.sx[sm]]);
+      if (gi == gofx.end()) continue;
+      const G& g = gs[gi->second];
+      t.push_back({g.db + MB.r0[sm] * g.n + MB.c0[sm], g.n, pc.second});
+      if (sm0 < 0) sm0 = sm;
+    }
+    block_strides(B, s, st);
+    Box b;
+    if (sm0 >= 0) group_weights(Bm, sm0, nc, rw, cw);
+    for (int l = 0; l < B.rank; ++l) {
+      int n = pinvB[l];
+      b.push(B.dim(s, l), sm0 >= 0 ? rw[n] : 0, sm0 >= 0 ? cw[n] : 0, st[l], 0);
+    }
+    emit(*P, b, B.offs[s], 1, 0, 0, 3, 3, t);
+  }
+  P->bwd_scatter_b = {begin, (int)P->items.size() - begin};
+  {
+    const int64_t src[4] = {A.numel(), B.numel(), C.numel(), P->outm_elems};
+    const int64_t dst[4] = {P->ops_elems, C.numel(), A.numel(), B.numel()};
+    P->validate(src, dst, !f64);
+  }
+  // GEMM tiles stay inside their operand images / matrices
+  for (const GemmTile& t : P->tiles) {
+    if (f64) {
+      const GemmSector64& s = P->secs64[t.sector];
+      if (s.a_off + (int64_t)(s.m - 1) * s.lda + s.k - 1 >= P->ops_elems ||
+          s.b_off + (int64_t)(s.k - 1) * s.ldb + s.n - 1 >= P->ops_elems ||
+          s.c_off + (int64_t)(s.m - 1) * s.ldc + s.n - 1 >= P->outm_elems)
+        fail(SYM_ERR_ARG, "internal: fp64 GEMM sector past its buffers");
+    } else {
+      const TcSector& s = P->secs_tc[t.sector];
+      if (s.a_img + ((int64_t)t.mt * s.ktiles + s.ktiles) * 8192 > P->ops_elems ||
+          s.b_img + ((int64_t)t.nt * s.ktiles + s.ktiles) * 8192 > P->ops_elems ||
+          s.c_off + (int64_t)(s.m - 1) * s.ldc + s.n - 1 >= P->outm_elems || s.ktiles < 1)
+        fail(SYM_ERR_ARG, "internal: tcgen05 GEMM tile past its buffers");
+    }
+  }
+  P->upload();
+  return P;
+}
+
+// ------------------------------------------------------------------- execution --
+namespace {
+
+int cuda_code(int e, const char* what) {
+  if (e == 0) return SYM_OK;
+  fail(SYM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString((cudaError_t)e));
+}
+
+int run_box(Plan& p, Range r, int mode, const BoxPtrs& ptrs, void* stream) {
+  if (r.count <= 0) return SYM_OK;
+  p.last_launches++;
+  return cuda_code(launch_box(mode, p.f64(), p.d_items + r.first, r.count, p.d_terms, ptrs, stream), "box kernel");
+}
+
+int run_gemm(Plan& p, Range r, void* stream) {
+  if (r.count <= 0) return SYM_OK;
+  p.last_launches++;
+  if (p.f64())
+    return cuda_code(launch_gemm_f64(static_cast<GemmSector64*>(p.d_secs), p.d_tiles + r.first, r.count,
+                                     static_cast<double*>(p.ops0), static_cast<double*>(p.ops0),
+                                     static_cast<double*>(p.outm), stream),
+                     "fp64 gemm");
+  return cuda_code(launch_gemm_tc(static_cast<TcSector*>(p.d_secs), p.d_tiles + r.first, r.count,
+                                  static_cast<uint16_t*>(p.ops0), static_cast<uint16_t*>(p.ops1),
+                                  static_cast<uint16_t*>(p.ops0), static_cast<uint16_t*>(p.ops1),
+                                  static_cast<float*>(p.outm), p.d_err, stream),
+                   "tcgen05 gemm");
+}
+
+}  // namespace
+
+int exec_transform(Plan& p, const void* in, void* out, void* stream) {
+  if (p.dry) fail(SYM_ERR_UNSUPPORTED, "plan was built with SYM_PLAN_DRYRUN=1 and cannot run");
+  p.last_launches = 0;
+  BoxPtrs ptrs{};
+  ptrs.src[0] = in;
+  ptrs.dst[1][0] = out;
+  int mode = p.f64() ? BOX_LINEAR_F64 : BOX_LINEAR_F32;
+  return run_box(p, p.xform, mode, ptrs, stream);
+}
+
+int exec_contract(Plan& p, const void* A, const void* B, void* C, void* stream) {
+  if (p.dry) fail(SYM_ERR_UNSUPPORTED, "plan was built with SYM_PLAN_DRYRUN=1 and cannot run");
+  p.last_launches = 0;
+  BoxPtrs g{};
+  g.src[0] = A;
+  g.src[1] = B;
+  g.dst[0][0] = p.ops0;
+  g.dst[0][1] = p.ops1;
+  int rc = run_box(p, p.fwd_gather, p.f64() ? BOX_LINEAR_F64 : BOX_IMAGE_BF16X2, g, stream);
+  if (rc) return rc;
+  rc = run_gemm(p, p.fwd_tiles, stream);
+  if (rc) return rc;
+  BoxPtrs s{};
+  s.src[3] = p.outm;
+  s.dst[1][0] = C;
+  return run_box(p, p.fwd_scatter, p.f64() ? BOX_LINEAR_F64 : BOX_LINEAR_F32, s, stream);
+}
+
+int exec_contract_backward(Plan& p, const void* A, const void* B, const void* dC, void* dA, void* dB,
+                           void* stream) {
+  if (p.dry) fail(SYM_ERR_UNSUPPORTED, "plan was built with SYM_PLAN_DRYRUN=1 and cannot run");
+  p.last_launches = 0;
+  if (!dA && !dB) return SYM_OK;
+  BoxPtrs g{};
+  g.src[0] = A;
+  g.src[1] = B;
+  g.src[2] = dC;
+  g.dst[0][0] = p.ops0;
+  g.dst[0][1] = p.ops1;
+  Range gr;
+  if (dA && dB) {
+    int first = std::min(p.bwd_gather_a.first, p.bwd_gather_b.first);
+    int last = std::max(p.bwd_gather_a.first + p.bwd_gather_a.count, p.bwd_gather_b.first + p.bwd_gather_b.count);
+    gr = {first, last - first};
+  } else {
+    gr = dA ? p.bwd_gather_a : p.bwd_gather_b;
+  }
+  int rc = run_box(p, gr, p.f64() ? BOX_LINEAR_F64 : BOX_IMAGE_BF16X2, g, stream);
+  if (rc) return rc;
+  Range tr;
+  if (dA && dB)
+    tr = {p.bwd_tiles_a.first, p.bwd_tiles_a.count + p.bwd_tiles_b.count};
+  else
+    tr = dA ? p.bwd_tiles_a : p.bwd_tiles_b;
+  rc = run_gemm(p, tr, stream);
+  if (rc) return rc;
+  BoxPtrs s{};
+  s.src[3] = p.outm;
+  s.dst[2][0] = dA;
+  s.dst[3][0] = dB;
+  Range sr;
+  if (dA && dB)
+    sr = {p.bwd_scatter_a.first, p.bwd_scatter_a.count + p.bwd_scatter_b.count};
+  else
+    sr = dA ? p.bwd_scatter_a : p.bwd_scatter_b;
+  return run_box(p, sr, p.f64() ? BOX_LINEAR_F64 : BOX_LINEAR_F32, s, stream);
+}
+
+}  // namespace sym

@@ -1,0 +1,282 @@
+"""Python front end of the GB300 symmetric block-sparse tensor library.
+
+Thin layer over the C ABI (``include/symtensor.h``): structures and plans are
+host handles; block data are 1-D torch tensors on the GPU (float32 for the
+split-BF16 tensor-core path, float64 for the plain FP64 path).  Every step of
+every operation runs in the library's kernels; PyTorch provides device memory,
+the current CUDA stream and autograd bookkeeping.
+
+    A = SymTensor.randn(Structure(U1, legs_a, total=0), seed, dtype=torch.float32)
+    C = contract(A, B, pairsA=[2, 3], pairsB=[0, 1])     # autograd-aware
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+U1, SU2 = L.SYM_U1, L.SYM_SU2
+FP64, BF16X3 = L.SYM_PREC_FP64, L.SYM_PREC_BF16X3
+SymError = L.SymError
+
+
+def _byref(x):
+    return ctypes.byref(x)
+
+
+class Structure:
+    """Sector table of a symmetric tensor (legs, total charge or tree); host only.
+
+    ``legs`` is a sequence of ``(labels, degens, dir)`` (U(1) charges or SU(2)
+    doubled spins, strictly increasing; dir +1 out, -1 in).  ``tree`` (SU(2))
+    is a list of ``(left, right)`` node children, None for the left comb.
+    """
+
+    def __init__(self, group, legs=None, total=0, tree=None, _handle=None):
+        self.group = int(group)
+        if _handle is None:
+            arr, _keep = L.leg_array(legs)
+            h = ctypes.c_void_p()
+            L.check(L.lib.sym_tensor_create(self.group, len(legs), arr, int(total),
+                                            L.tree_array(tree), _byref(h)))
+            self._h = h
+        else:
+            self._h = _handle
+        self.total = int(total) if self.group == U1 else 0
+        g, r, n, ns = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+        L.check(L.lib.sym_tensor_info(self._h, _byref(g), _byref(r), _byref(n), _byref(ns)))
+        self.rank, self.numel, self.nsec = r.value, n.value, ns.value
+        self.legs = [self._leg(i) for i in range(self.rank)]
+        self.tree = None
+        if self.group == SU2 and self.rank >= 2:
+            buf = (ctypes.c_int * (2 * (self.rank - 1)))()
+            L.check(L.lib.sym_tensor_tree(self._h, buf))
+            self.tree = [(buf[2 * i], buf[2 * i + 1]) for i in range(self.rank - 1)]
+
+    def _leg(self, i):
+        n, d = ctypes.c_int(), ctypes.c_int()
+        L.check(L.lib.sym_tensor_leg(self._h, i, _byref(n), None, None, _byref(d)))
+        la = (ctypes.c_int * n.value)()
+        de = (ctypes.c_int * n.value)()
+        L.check(L.lib.sym_tensor_leg(self._h, i, None, la, de, None))
+        return (tuple(la), tuple(de), d.value)
+
+    def sectors(self):
+        """(labels[nsec, rank + max(rank-2,0)] int32, offsets[nsec+1] int64)."""
+        w = self.rank + (max(self.rank - 2, 0) if self.group == SU2 else 0)
+        lab = np.zeros((self.nsec, w), dtype=np.int32)
+        off = np.zeros(self.nsec + 1, dtype=np.int64)
+        L.check(L.lib.sym_tensor_sectors(self._h, lab.ctypes.data_as(L._IP) if lab.size else None,
+                                         off.ctypes.data_as(L._LP)))
+        return lab, off
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and L is not None and L.lib is not None:
+            L.lib.sym_tensor_destroy(h)
+            self._h = None
+
+
+class Plan:
+    """Precomputed tables + scratch of one operation (owned handle)."""
+
+    def __init__(self, handle, out, kind):
+        self._h = handle
+        self.out = out
+        self.kind = kind
+
+    def stats(self):
+        f = ctypes.c_double()
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        L.check(L.lib.sym_plan_stats(self._h, _byref(f), _byref(a), _byref(b), _byref(c)))
+        return {"flops_fwd": f.value, "bytes_a": a.value, "bytes_b": b.value, "bytes_c": c.value}
+
+    def launches(self):
+        n = ctypes.c_int()
+        L.check(L.lib.sym_plan_launches(self._h, _byref(n)))
+        return n.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and L is not None and L.lib is not None:
+            L.lib.sym_plan_destroy(h)
+            self._h = None
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _precision(dtype):
+    if dtype == torch.float64:
+        return FP64
+    if dtype == torch.float32:
+        return BF16X3
+    raise TypeError("block data must be float32 (split-BF16 path) or float64 (FP64 path)")
+
+
+_PLANS = {}
+
+
+def contract_plan(A, B, pairsA, pairsB, precision=BF16X3, tree_c=None):
+    """Plan (cached) of contracting structure A's legs pairsA with B's pairsB."""
+    key = ("c", id(A), id(B), tuple(pairsA), tuple(pairsB), precision,
+           None if tree_c is None else tuple(map(tuple, tree_c)))
+    hit = _PLANS.get(key)
+    if hit is not None:
+        return hit[0]
+    c, p = ctypes.c_void_p(), ctypes.c_void_p()
+    L.check(L.lib.sym_contract_plan(A._h, B._h, len(pairsA), L.int_array(pairsA), L.int_array(pairsB),
+                                    L.tree_array(tree_c), int(precision), _byref(c), _byref(p)))
+    out = Structure(A.group, total=A.total + B.total, _handle=c)
+    plan = Plan(p, out, "contract")
+    _PLANS[key] = (plan, A, B)
+    return plan
+
+
+def _transform_plan(key, make):
+    hit = _PLANS.get(key)
+    if hit is not None:
+        return hit[0]
+    o, p = ctypes.c_void_p(), ctypes.c_void_p()
+    total = make(o, p)
+    plan = Plan(p, None, key[0])
+    plan.out = Structure(key[-1].group, total=total, _handle=o)
+    _PLANS[key] = (plan,)
+    return plan
+
+
+def permute_plan(S, perm, tree=None, precision=BF16X3):
+    key = ("p", id(S), tuple(perm), None if tree is None else tuple(map(tuple, tree)), precision, S)
+    return _transform_plan(key, lambda o, p: (L.check(L.lib.sym_permute_plan(
+        S._h, L.int_array(perm), L.tree_array(tree), int(precision), _byref(o), _byref(p))), S.total)[1])
+
+
+def fuse_plan(S, first, precision=BF16X3):
+    key = ("f", id(S), int(first), precision, S)
+    return _transform_plan(key, lambda o, p: (L.check(L.lib.sym_fuse_plan(
+        S._h, int(first), int(precision), _byref(o), _byref(p))), S.total)[1])
+
+
+def split_plan(S, leg, parts, precision=BF16X3):
+    key = ("s", id(S), int(leg), tuple((tuple(a), tuple(b), int(c)) for a, b, c in parts), precision, S)
+
+    def make(o, p):
+        arr, _keep = L.leg_array(parts)
+        L.check(L.lib.sym_split_plan(S._h, int(leg), arr, int(precision), _byref(o), _byref(p)))
+        return S.total
+
+    return _transform_plan(key, make)
+
+
+class _Contract(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, plan, a, b):
+        c = torch.empty(plan.out.numel, dtype=a.dtype, device=a.device)
+        L.check(L.lib.sym_contract(plan._h, _ptr(a), _ptr(b), _ptr(c), _stream()))
+        ctx.plan = plan
+        ctx.save_for_backward(a, b)
+        return c
+
+    @staticmethod
+    def backward(ctx, dc):
+        a, b = ctx.saved_tensors
+        dc = dc.contiguous()
+        da = torch.empty_like(a) if ctx.needs_input_grad[1] else None
+        db = torch.empty_like(b) if ctx.needs_input_grad[2] else None
+        L.check(L.lib.sym_contract_backward(ctx.plan._h, _ptr(a), _ptr(b), _ptr(dc), _ptr(da), _ptr(db),
+                                            _stream()))
+        return None, da, db
+
+
+class SymTensor:
+    """A symmetric tensor: structure + its block data (1-D CUDA tensor)."""
+
+    def __init__(self, structure, data):
+        if not (isinstance(data, torch.Tensor) and data.is_cuda):
+            raise TypeError("block data must be a CUDA tensor")
+        if data.dim() != 1 or data.numel() != structure.numel:
+            raise ValueError(f"data must be 1-D with {structure.numel} elements, got {tuple(data.shape)}")
+        _precision(data.dtype)
+        self.structure = structure
+        self.data = data if data.is_contiguous() else data.contiguous()
+
+    @property
+    def group(self):
+        return self.structure.group
+
+    @property
+    def legs(self):
+        return self.structure.legs
+
+    @staticmethod
+    def zeros(structure, dtype=torch.float32, device="cuda"):
+        return SymTensor(structure, torch.zeros(structure.numel, dtype=dtype, device=device))
+
+    @staticmethod
+    def from_numpy(structure, values, dtype=torch.float32, device="cuda"):
+        t = torch.as_tensor(np.asarray(values, dtype=np.float64)).to(dtype)
+        return SymTensor(structure, t.to(device))
+
+
+def contract(A, B, pairsA, pairsB, tree_c=None):
+    """C = contract(A, B) summing A's legs pairsA with B's legs pairsB (autograd-aware)."""
+    prec = _precision(A.data.dtype)
+    if B.data.dtype != A.data.dtype:
+        raise TypeError("A and B must share a dtype")
+    plan = contract_plan(A.structure, B.structure, pairsA, pairsB, prec, tree_c)
+    return SymTensor(plan.out, _Contract.apply(plan, A.data, B.data))
+
+
+def _run_transform(plan, T):
+    out = torch.empty(plan.out.numel, dtype=T.data.dtype, device=T.data.device)
+    L.check(L.lib.sym_plan_execute(plan._h, _ptr(T.data), _ptr(out), _stream()))
+    return SymTensor(plan.out, out)
+
+
+def permute(T, perm, tree=None):
+    """PERMUTE: output leg n is input leg perm[n] (SU(2): recoupled into ``tree``)."""
+    return _run_transform(permute_plan(T.structure, perm, tree, _precision(T.data.dtype)), T)
+
+
+def fuse(T, first):
+    """FUSE legs (first, first+1) into one leg."""
+    return _run_transform(fuse_plan(T.structure, first, _precision(T.data.dtype)), T)
+
+
+def split(T, leg, parts):
+    """SPLIT leg ``leg`` into the two legs ``parts`` (which must fuse to it)."""
+    return _run_transform(split_plan(T.structure, leg, parts, _precision(T.data.dtype)), T)
+
+
+def device_status():
+    """Raise SymError(SYM_ERR_TIMEOUT) if a bounded device wait expired."""
+    L.check(L.lib.sym_device_status())
+
+
+def su2_F(jd, je, ja, jb, jc, J):
+    out = ctypes.c_double()
+    L.check(L.lib.sym_su2_F(jd, je, ja, jb, jc, J, _byref(out)))
+    return out.value
+
+
+def su2_gamma(spins, tree_in, perm, tree_out):
+    """(G[n_out, n_in], labels_in, labels_out) of the host Gamma builder."""
+    k = len(spins)
+    ni, no = ctypes.c_int(), ctypes.c_int()
+    args = (k, L.int_array(spins), L.tree_array(tree_in), L.int_array(perm), L.tree_array(tree_out))
+    L.check(L.lib.sym_su2_gamma(*args, _byref(ni), _byref(no), None, None, None))
+    w = max(k - 2, 1)
+    G = np.zeros(max(ni.value * no.value, 1))
+    li = np.zeros(max(ni.value * w, 1), dtype=np.int32)
+    lo = np.zeros(max(no.value * w, 1), dtype=np.int32)
+    L.check(L.lib.sym_su2_gamma(*args, None, None, G.ctypes.data_as(L._DP), li.ctypes.data_as(L._IP),
+                                lo.ctypes.data_as(L._IP)))
+    wk = max(k - 2, 0)
+    return (G[:ni.value * no.value].reshape(no.value, ni.value),
+            li[:ni.value * wk].reshape(ni.value, wk), lo[:no.value * wk].reshape(no.value, wk))

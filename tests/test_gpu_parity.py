@@ -1,0 +1,216 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element.
+
+Tolerances (relative Frobenius error against the oracle):
+  FP64 path            1e-12
+  split-BF16 x3 path   2e-5   (inputs are the float32 values the GPU holds,
+                               cast to float64 for the oracle)
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import contract as oc  # noqa: E402
+from oracle import su2 as osu2  # noqa: E402
+from oracle import u1 as ou1  # noqa: E402
+
+TOL = {torch.float64: 1e-12, torch.float32: 2e-5}
+
+
+def _lib():
+    import paper_1203_2222_gb300 as P
+    return P
+
+
+def rel(x, y):
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    ny = np.linalg.norm(y)
+    return float(np.linalg.norm(x - y) / (ny if ny > 0 else 1.0))
+
+
+def _oleg(group, l):
+    return (ou1.Leg if group == "u1" else osu2.Leg)(*l)
+
+
+def _otree(group, S, legs_spec):
+    if group == "u1":
+        return S.total
+    return S.tree if S.tree is not None else osu2.left_comb(len(legs_spec))
+
+
+def _make(group, legs, seed, dtype, total=0, tree=None):
+    P = _lib()
+    S = P.Structure(P.U1 if group == "u1" else P.SU2, legs, total=total, tree=tree)
+    vals = np.random.default_rng(seed).standard_normal(S.numel)
+    T = P.SymTensor.from_numpy(S, vals, dtype=dtype)
+    host = T.data.double().cpu().numpy()  # exactly what the GPU holds
+    return S, T, host
+
+
+def _contract_case(group, la, lb, pa, pb, dtype, QA=0, QB=0, ta=None, tb=None, tree_c=None, grad=True, seed=0):
+    P = _lib()
+    SA, A, a = _make(group, la, seed, dtype, QA, ta)
+    SB, B, b = _make(group, lb, seed + 1, dtype, QB, tb)
+    A.data.requires_grad_(grad)
+    B.data.requires_grad_(grad)
+    C = P.contract(A, B, pa, pb, tree_c=tree_c)
+    torch.cuda.synchronize()
+    oA = ([_oleg(group, l) for l in la], _otree(group, SA, la), a)
+    oB = ([_oleg(group, l) for l in lb], _otree(group, SB, lb), b)
+    lc, tc, c_ref, resid = oc.contract(group, oA, oB, pa, pb, tree_c=C.structure.tree if group == "su2" else None)
+    assert resid < 1e-10
+    assert C.structure.numel == len(c_ref)
+    c = C.data.detach().double().cpu().numpy()
+    err = rel(c, c_ref)
+    assert err <= TOL[dtype], f"forward rel err {err:.3e}"
+    if grad:
+        g = np.random.default_rng(seed + 2).standard_normal(C.structure.numel)
+        gt = torch.as_tensor(g).to(dtype).cuda()
+        C.data.backward(gt)
+        torch.cuda.synchronize()
+        g_used = gt.double().cpu().numpy()
+        dA_ref, dB_ref, r2 = oc.contract_grad(group, oA, oB, pa, pb, g_used, tree_c=C.structure.tree if group == "su2" else None)
+        assert r2 < 1e-10
+        eA = rel(A.data.grad.double().cpu().numpy(), dA_ref)
+        eB = rel(B.data.grad.double().cpu().numpy(), dB_ref)
+        assert eA <= TOL[dtype], f"dA rel err {eA:.3e}"
+        assert eB <= TOL[dtype], f"dB rel err {eB:.3e}"
+    P.device_status()
+    return err
+
+
+DTYPES = [torch.float64, torch.float32]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_u1_pairwise_workload(dtype):
+    from paper_1203_2222_gb300 import synthetic
+    c = synthetic.u1_pairwise()
+    _contract_case("u1", c["A"], c["B"], c["pairsA"], c["pairsB"], dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_u1_ragged_multi_tile(dtype):
+    # sector matrices spanning several 128-tiles with ragged tails in m, n and k
+    qs = [-1, 0, 1]
+    la = [(qs, [70, 150, 33], -1), (qs, [5, 9, 2], 1), (qs, [90, 140, 61], 1)]
+    lb = [(qs, [90, 140, 61], -1), (qs, [100, 131, 7], 1)]
+    _contract_case("u1", la, lb, [2], [0], dtype, QA=0, QB=0)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_u1_permuted_pairs_and_charges(dtype):
+    qs = [-2, -1, 0, 1, 2]
+    la = [(qs, [1, 2, 3, 2, 1], 1), (qs, [2, 1, 2, 1, 2], -1), (qs, [3, 1, 1, 2, 1], 1), (qs, [1, 1, 2, 2, 1], -1)]
+    lb = [(qs, [1, 1, 2, 2, 1], 1), (qs, [2, 3, 1, 1, 1], 1), (qs, [3, 1, 1, 2, 1], -1)]
+    # contract A3<->B0 and A2<->B2 (pairs out of order), nonzero total charges
+    _contract_case("u1", la, lb, [3, 2], [0, 2], dtype, QA=1, QB=-2)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_u1_edge_cases(dtype):
+    qs = [0]
+    # single sector, 1x1 blocks
+    _contract_case("u1", [(qs, [1], 1), (qs, [1], -1)], [(qs, [1], 1), (qs, [1], 1)], [1], [0], dtype)
+    # full contraction to a scalar
+    la = [([-1, 0, 1], [2, 3, 1], 1), ([-1, 0, 1], [1, 2, 2], -1)]
+    lb = [([-1, 0, 1], [2, 3, 1], -1), ([-1, 0, 1], [1, 2, 2], 1)]
+    _contract_case("u1", la, lb, [0, 1], [0, 1], dtype)
+    # outer product (no pairs)
+    _contract_case("u1", la, [([-1, 0, 1], [2, 1, 3], 1)], [], [], dtype, QB=1)
+
+
+SU2_TREES = [None, [(1, 2), (0, 4), (5, 3)], [(0, 1), (2, 3), (4, 5)]]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("ti", range(len(SU2_TREES)))
+def test_su2_recoupling_contraction(dtype, ti):
+    # the recoupling workload at reduced size: 2j <= 4, degeneracies 1..3
+    from paper_1203_2222_gb300 import synthetic
+    c = synthetic.su2_recouple(dmax=3, jmax2=4)
+    _contract_case("su2", c["A"], c["B"], c["pairsA"], c["pairsB"], dtype, ta=SU2_TREES[ti])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_su2_mixed_directions_and_output_tree(dtype):
+    sp = [0, 1, 2, 3]
+    la = [(sp, [2, 1, 2, 1], -1), (sp, [1, 2, 1, 1], 1), (sp, [2, 2, 1, 1], -1), (sp, [1, 1, 2, 1], 1)]
+    lb = [(sp, [1, 2, 1, 1], -1), (sp, [2, 2, 1, 1], 1), (sp, [1, 1, 1, 2], 1)]
+    _contract_case("su2", la, lb, [1, 2], [0, 1], dtype, ta=[(1, 2), (0, 4), (5, 3)])
+    # requested output tree different from the natural one
+    _contract_case("su2", la, lb, [1, 2], [0, 1], dtype, tree_c=[(1, 2), (0, 3)])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_su2_matrix_and_edge_cases(dtype):
+    sp = [0, 1, 2, 3]
+    m = [(sp, [3, 2, 2, 1], -1), (sp, [3, 2, 2, 1], 1)]
+    n = [(sp, [3, 2, 2, 1], -1), (sp, [2, 1, 3, 2], 1)]
+    _contract_case("su2", m, n, [1], [0], dtype)
+    # full contraction to a scalar and a rank-1 result
+    a = [(sp, [2, 1, 1, 1], 1), (sp, [1, 2, 1, 1], 1)]
+    b = [(sp, [2, 1, 1, 1], -1), (sp, [1, 2, 1, 1], -1)]
+    _contract_case("su2", a, b, [0, 1], [0, 1], dtype)
+    c3 = [(sp, [2, 1, 1, 1], 1), (sp, [1, 2, 1, 1], 1), ([0, 2], [2, 1], 1)]
+    _contract_case("su2", c3, b, [0, 1], [0, 1], dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_su2_large_sectors_multi_tile(dtype):
+    # sector matrices of a few hundred rows/cols: several tiles with ragged tails
+    sp = [0, 1, 2]
+    la = [(sp, [40, 35, 9], 1), (sp, [13, 7, 5], 1), (sp, [31, 22, 17], 1)]
+    lb = [(sp, [31, 22, 17], -1), (sp, [29, 15, 11], 1)]
+    _contract_case("su2", la, lb, [2], [0], dtype, grad=True)
+
+
+# ----------------------------------------------------------- transforms ------
+
+def _transform_case(group, legs, op, args, dtype, tree=None, seed=5):
+    P = _lib()
+    S, T, t = _make(group, legs, seed, dtype, 0, tree)
+    oT = ([_oleg(group, l) for l in legs], _otree(group, S, legs), t)
+    if op == "permute":
+        out = P.permute(T, args[0], args[1])
+        lo, to, ref, resid = oc.permute(group, oT, args[0], out.structure.tree if group == "su2" else None)
+    elif op == "fuse":
+        out = P.fuse(T, args[0])
+        lo, to, ref, resid = oc.fuse(group, oT, args[0], out.structure.tree if group == "su2" else None)
+        assert [tuple(l.labels) for l in lo] == [tuple(l[0]) for l in out.structure.legs]
+        assert [tuple(l.degens) for l in lo] == [tuple(l[1]) for l in out.structure.legs]
+    torch.cuda.synchronize()
+    assert resid < 1e-10
+    err = rel(out.data.double().cpu().numpy(), ref)
+    assert err <= TOL[dtype] if dtype == torch.float64 else err <= 1e-6, err
+    return S, T, out
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_permute(dtype):
+    qs = [-1, 0, 1]
+    u = [(qs, [2, 3, 1], 1), (qs, [1, 2, 2], -1), (qs, [3, 1, 2], 1), (qs, [2, 2, 1], -1)]
+    _transform_case("u1", u, "permute", ([2, 0, 3, 1], None), dtype)
+    sp = [0, 1, 2, 3]
+    s = [(sp, [2, 1, 1, 1], 1), (sp, [1, 2, 1, 1], -1), (sp, [1, 1, 2, 1], 1), (sp, [1, 1, 1, 2], 1)]
+    _transform_case("su2", s, "permute", ([2, 0, 3, 1], None), dtype)
+    _transform_case("su2", s, "permute", ([0, 2, 1, 3], [(0, 1), (2, 3), (4, 5)]), dtype,
+                    tree=[(1, 2), (0, 4), (5, 3)])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_fuse_then_split_roundtrip(dtype):
+    P = _lib()
+    for group, legs in [
+        ("u1", [([-1, 0, 1], [2, 3, 1], 1), ([-1, 0, 1], [1, 2, 2], 1), ([-2, -1, 0, 1, 2], [1, 1, 2, 1, 1], -1)]),
+        ("su2", [([0, 1, 2], [2, 1, 1], 1), ([0, 1, 2], [1, 2, 1], 1), ([0, 1, 2, 3, 4], [1, 1, 2, 1, 1], 1)]),
+        ("su2", [([0, 1, 2], [2, 1, 1], -1), ([0, 1, 2], [1, 2, 1], -1), ([0, 1, 2, 3, 4], [1, 1, 2, 1, 1], 1)]),
+    ]:
+        S, T, F = _transform_case(group, legs, "fuse", (0,), dtype)
+        back = P.split(F, 0, [legs[0], legs[1]])
+        torch.cuda.synchronize()
+        err = rel(back.data.double().cpu().numpy(), T.data.double().cpu().numpy())
+        assert err <= (1e-13 if dtype == torch.float64 else 1e-6), (group, err)

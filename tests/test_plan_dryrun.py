@@ -1,0 +1,65 @@
+"""Plans of every GPU test case and workload, built and bounds-checked on the host.
+
+Runs the planner in a subprocess with SYM_PLAN_DRYRUN=1: every work item's
+largest source/destination offset is checked against its buffer before any
+GPU sees the plan (no GPU needed)."""
+import os
+import subprocess
+import sys
+
+from tests.conftest import ROOT
+
+SCRIPT = r'''
+import numpy as np
+import paper_1203_2222_gb300 as P
+from paper_1203_2222_gb300 import synthetic
+import tests.test_gpu_parity as T
+
+def plan(group, la, lb, pa, pb, ta=None, tb=None, tree_c=None, QA=0, QB=0):
+    g = P.U1 if group == "u1" else P.SU2
+    A = P.Structure(g, la, total=QA, tree=ta); B = P.Structure(g, lb, total=QB, tree=tb)
+    for prec in (P.FP64, P.BF16X3):
+        p = P.contract_plan(A, B, pa, pb, prec, tree_c)
+        st = p.stats()
+        assert st["flops_fwd"] >= 0
+    return st
+
+c = synthetic.u1_pairwise(); plan("u1", c["A"], c["B"], c["pairsA"], c["pairsB"])
+qs = [-1, 0, 1]
+plan("u1", [(qs, [70, 150, 33], -1), (qs, [5, 9, 2], 1), (qs, [90, 140, 61], 1)],
+     [(qs, [90, 140, 61], -1), (qs, [100, 131, 7], 1)], [2], [0])
+s = synthetic.su2_recouple(dmax=3, jmax2=4)
+for ti in T.SU2_TREES:
+    plan("su2", s["A"], s["B"], s["pairsA"], s["pairsB"], ta=ti)
+sp = [0, 1, 2, 3]
+la = [(sp, [2, 1, 2, 1], -1), (sp, [1, 2, 1, 1], 1), (sp, [2, 2, 1, 1], -1), (sp, [1, 1, 2, 1], 1)]
+lb = [(sp, [1, 2, 1, 1], -1), (sp, [2, 2, 1, 1], 1), (sp, [1, 1, 1, 2], 1)]
+plan("su2", la, lb, [1, 2], [0, 1], ta=[(1, 2), (0, 4), (5, 3)])
+plan("su2", la, lb, [1, 2], [0, 1], tree_c=[(1, 2), (0, 3)])
+a = [(sp, [2, 1, 1, 1], 1), (sp, [1, 2, 1, 1], 1)]; b = [(sp, [2, 1, 1, 1], -1), (sp, [1, 2, 1, 1], -1)]
+plan("su2", a, b, [0, 1], [0, 1])
+m = synthetic.u1_mps_heff()
+Ls = [P.Structure(P.U1, m[n]) for n in ("L", "A", "W", "R")]
+t1 = P.contract_plan(Ls[0], Ls[1], [2], [0], P.BF16X3)
+t2 = P.contract_plan(t1.out, Ls[2], [1, 2], [0, 2], P.BF16X3)
+t3 = P.contract_plan(t2.out, Ls[3], [1, 3], [2, 1], P.BF16X3)
+print("MPS flops", t1.stats()["flops_fwd"] + t2.stats()["flops_fwd"] + t3.stats()["flops_fwd"])
+# transforms
+U = P.Structure(P.U1, [(qs, [2, 3, 1], 1), (qs, [1, 2, 2], 1), (qs, [3, 1, 2], -1)])
+P.permute_plan(U, [2, 0, 1]); f = P.fuse_plan(U, 0); P.split_plan(f.out, 0, [U.legs[0], U.legs[1]])
+S = P.Structure(P.SU2, [([0, 1, 2], [2, 1, 1], 1), ([0, 1, 2], [1, 2, 1], 1), ([0, 1, 2, 3, 4], [1, 1, 2, 1, 1], 1)])
+P.permute_plan(S, [2, 0, 1]); f = P.fuse_plan(S, 0); P.split_plan(f.out, 0, [S.legs[0], S.legs[1]])
+try:
+    P.contract(None, None, [], [])
+except Exception:
+    pass
+print("DRYRUN OK")
+'''
+
+
+def test_all_plans_bounds_check_on_host():
+    env = dict(os.environ, SYM_PLAN_DRYRUN="1", PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-c", SCRIPT], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "DRYRUN OK" in r.stdout
