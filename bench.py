@@ -1,0 +1,504 @@
+#!/usr/bin/env python
+"""Benchmark: symmetric block-sparse contraction, forward + backward, on one GB300.
+
+Workload (the MPS effective-Hamiltonian apply with U(1) symmetry): bond
+D = 2048 over charges -20..20 (Gaussian degeneracies, sigma 6), physical leg
+{0:1, 1:1}, MPO leg {-1:1, 0:3, +1:1}; one step = Y = ((L.A).W).R forward and
+the gradients of <G, Y> with respect to L, A, W and R (autograd through the
+library's adjoint), all on synthetic N(0,1) blocks.
+
+Metric: useful TFLOP/s = block-sparse GEMM flops (sum over sectors of 2 m n k,
+forward + backward) / device time.  Reported for the split-BF16 x3 tcgen05
+path (the value), next to the plain FP64 GPU path and the FP64 CPU oracle.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Rank 0 prints one JSON line.  Under torchrun (N > 1) every rank runs the same
+workload on its own GPU (replicas; weak scaling) and the slowest rank's time
+is used.  L2 is flushed (a 256 MiB write) between timed steps; each step is
+bracketed by CUDA events on the compute stream.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "useful TFLOP/s of symmetric block-sparse contraction fwd+bwd vs plain FP64 GPU"
+WORKLOAD = ("u1_mps_heff: ((L.A).W).R fwd+bwd, D=2048 over q=-20..20 (gaussian sigma=6), "
+            "phys {0:1,1:1}, MPO w=5 {-1:1,0:3,+1:1}")
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--cpu-sample-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying a CUDA graph")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers ---
+
+def load_peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            p = json.load(f)
+        return p, "measured"
+    except (OSError, ValueError):
+        return dict(FALLBACK_PEAKS), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while a region runs (read-only queries)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        load = [s for s in sm if mx and s >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def mps_structures(P):
+    from paper_1203_2222_gb300 import synthetic
+    m = synthetic.u1_mps_heff()
+    S = {n: P.Structure(P.U1, m[n]) for n in ("L", "A", "W", "R")}
+    return m, S
+
+
+def make_inputs(P, m, S, dtype, device):
+    import torch
+    from paper_1203_2222_gb300 import synthetic
+    t = {}
+    for n, s in S.items():
+        v = torch.as_tensor(synthetic.normal(m["seeds"][n], s.numel)).to(dtype)
+        t[n] = v.to(device)
+    return t
+
+
+def mps_step(P, S, data, G):
+    """Y = ((L.A).W).R and d<G,Y>/d(L, A, W, R) through the public API."""
+    import torch
+    L = P.SymTensor(S["L"], data["L"])
+    A = P.SymTensor(S["A"], data["A"])
+    W = P.SymTensor(S["W"], data["W"])
+    R = P.SymTensor(S["R"], data["R"])
+    T1 = P.contract(L, A, [2], [0])
+    T2 = P.contract(T1, W, [1, 2], [0, 2])
+    Y = P.contract(T2, R, [1, 3], [2, 1])
+    grads = torch.autograd.grad(Y.data, [data["L"], data["A"], data["W"], data["R"]], grad_outputs=G)
+    return Y.data, grads
+
+
+def step_flops(P):
+    """Useful flops of one step: forward GEMMs + backward GEMMs (dA and dB)."""
+    tot = 0.0
+    for p in P.cached_plans():
+        if p.kind == "contract":
+            tot += 3.0 * p.stats()["flops_fwd"]
+    return tot
+
+
+# -------------------------------------------------------------- our path ---
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_1203_2222_gb300 as P
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    m, S = mps_structures(P)
+
+    # ---- split-BF16 x3 path (the value)
+    data = make_inputs(P, m, S, torch.float32, dev)
+    for v in data.values():
+        v.requires_grad_(True)
+    from paper_1203_2222_gb300 import synthetic
+
+    def run_once(dt, Gt):
+        return mps_step(P, S, dt, Gt)
+
+    # build plans (first call) with a provisional cotangent
+    L_ = P.SymTensor(S["L"], data["L"])
+    A_ = P.SymTensor(S["A"], data["A"])
+    W_ = P.SymTensor(S["W"], data["W"])
+    R_ = P.SymTensor(S["R"], data["R"])
+    Yt = P.contract(P.contract(P.contract(L_, A_, [2], [0]), W_, [1, 2], [0, 2]), R_, [1, 3], [2, 1])
+    G = torch.as_tensor(synthetic.normal(4242, Yt.structure.numel)).to(torch.float32).to(dev)
+    del Yt, L_, A_, W_, R_
+    flops = step_flops(P)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    use_graph = not args.no_graph
+    graph = None
+    static_out = None
+    for _ in range(max(args.warmup, 1)):
+        run_once(data, G)
+    torch.cuda.synchronize()
+    if use_graph:
+        try:
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                for _ in range(2):
+                    run_once(data, G)
+            torch.cuda.current_stream().wait_stream(s)
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                static_out = run_once(data, G)
+            torch.cuda.synchronize()
+            for _ in range(2):
+                graph.replay()
+            torch.cuda.synchronize()
+        except Exception as e:  # capture unsupported: fall back to eager launches
+            print(f"# graph capture failed ({e}); timing eager launches", file=sys.stderr)
+            graph = None
+
+    def one_step():
+        if graph is not None:
+            graph.replay()
+        else:
+            run_once(data, G)
+
+    # launches per step (eager count; a graph replays the same kernels)
+    for p in P.cached_plans():
+        p.profile(True)
+    run_once(data, G)
+    torch.cuda.synchronize()
+    launches_per_step = sum(p.profile_read(ph)["launches"] for p in P.cached_plans() for ph in range(7))
+    # live per-kernel timing: the library records events around its own launches.
+    # A graph replay cannot record host-side events, so per-kernel timing runs
+    # the same kernels eagerly on the same stream for K steps right after.
+    for p in P.cached_plans():
+        p.profile(True)
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one_step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    if graph is not None:
+        # per-kernel event timing of the same kernels, eager, same stream
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            run_once(data, G)
+        torch.cuda.synchronize()
+    prof = {}
+    for p in P.cached_plans():
+        for name, ph in P.PHASES.items():
+            r = p.profile_read(ph)
+            if r["launches"] == 0:
+                continue
+            kern = "gemm_tc" if "gemm" in name else "box"
+            d = prof.setdefault(kern, {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
+            for k in d:
+                d[k] += r[k]
+        p.profile(False)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = flops * args.steps * world / (ms * 1e-3) / 1e12
+
+    # ---- accuracy against the FP64 path, and the FP64 GPU comparator
+    y32, g32 = (static_out if graph is not None else run_once(data, G))
+    torch.cuda.synchronize()
+    data64 = {n: v.detach().double().requires_grad_(True) for n, v in data.items()}
+    G64 = G.double()
+    y64, g64 = mps_step(P, S, data64, G64)
+    torch.cuda.synchronize()
+
+    def rel(a, b):
+        return float((a.double() - b).norm() / b.norm())
+
+    err = max([rel(y32, y64)] + [rel(a, b) for a, b in zip(g32, g64)])
+    for _ in range(2):
+        mps_step(P, S, data64, G64)
+    torch.cuda.synchronize()
+    e64 = []
+    for _ in range(args.fp64_steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mps_step(P, S, data64, G64)
+        e1.record(stream)
+        e64.append((e0, e1))
+    torch.cuda.synchronize()
+    ms64 = sum(a.elapsed_time(b) for a, b in e64) / args.fp64_steps
+    value64 = flops * world / (ms64 * 1e-3) / 1e12
+
+    # ---- end to end through the public API: pinned host inputs -> result on host
+    host_in = {n: v.detach().cpu().pin_memory() for n, v in data.items()}
+    dev_in = {n: torch.empty_like(v.detach()).requires_grad_(True) for n, v in data.items()}
+    host_y = torch.empty(y32.numel(), dtype=torch.float32).pin_memory()
+    host_g = {n: torch.empty(v.numel(), dtype=torch.float32).pin_memory() for n, v in data.items()}
+    h2d = sum(v.numel() * 4 for v in host_in.values())
+    d2h = host_y.numel() * 4 + sum(v.numel() * 4 for v in host_g.values())
+
+    def e2e_step():
+        with torch.no_grad():
+            for n in dev_in:
+                dev_in[n].copy_(host_in[n], non_blocking=True)
+        yy, gg = mps_step(P, S, dev_in, G)
+        host_y.copy_(yy.detach(), non_blocking=True)
+        for n, gv in zip(("L", "A", "W", "R"), gg):
+            host_g[n].copy_(gv, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    ee = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        e1.synchronize()  # the host reads the result every step
+        ee.append((e0, e1))
+    ms_e2e = sum(a.elapsed_time(b) for a, b in ee) / args.steps
+    e2e_value = flops * world / (ms_e2e * 1e-3) / 1e12
+
+    # ---- roofline of the dominant kernel
+    peaks, peak_src = load_peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"]) if prof else None
+    roof = None
+    if dom == "gemm_tc":
+        d = prof[dom]
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        peak = peaks["bf16_tflops_sustained"] / 3.0
+        roof = {"bound": "tensor", "kernel": "gemm_tc_kernel (split-BF16 x3, useful flops)",
+                "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": f"{peak_src} bf16_tflops_sustained / 3 passes"}
+    elif dom == "box":
+        d = prof[dom]
+        achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "kernel": "box_kernel (block gathers/scatters)",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "peak_source": f"{peak_src} hbm_gbs"}
+    if roof is not None:
+        d = prof[dom]
+        roof["launches_timed"] = d["launches"]
+        roof["avg_launch_us"] = round(d["ms"] * 1e3 / max(d["launches"], 1), 2)
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                   "share": round(v["ms"] / max(sum(x["ms"] for x in prof.values()), 1e-12), 4)}
+               for k, v in prof.items()}
+
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3-f32acc", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "split-BF16 x3 on tcgen05, FP32 accumulate, fp32 blocks",
+                   "useful_gflop_per_step": round(flops / 1e9, 4),
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "launch": "cuda graph replay" if graph is not None else "eager",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof, "kernels": kernels,
+        "fp64_gpu": {"value": round(value64, 5), "unit": "TFLOP/s", "ms_per_step": round(ms64, 4)},
+        "speedup_vs_fp64_gpu": round(value / value64 / world, 3) if value64 > 0 else None,
+        "max_rel_err_vs_fp64": err,
+        "e2e": {"value": round(e2e_value, 4), "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e, 4)},
+        "clocks": clk, "gpu_launches": launches_per_step * args.steps,
+    }
+    return out, flops
+
+
+# ------------------------------------------------------------ oracle (CPU) ---
+
+class OracleMPS:
+    """The FP64 CPU oracle on the same workload (dense embedding, brute force)."""
+
+    def __init__(self):
+        from oracle import u1
+        from paper_1203_2222_gb300 import synthetic
+        m = synthetic.u1_mps_heff()
+        self.legs = {n: [u1.Leg(*l) for l in m[n]] for n in ("L", "A", "W", "R")}
+        self.data = {n: synthetic.normal(m["seeds"][n], u1.layout(self.legs[n], 0)[2]) for n in self.legs}
+        self.steps = [("L", "A", [2], [0]), (None, "W", [1, 2], [0, 2]), (None, "R", [1, 3], [2, 1])]
+
+    def contraction(self, i, a=None):
+        """Forward + gradient of contraction i of the chain (i = 0, 1, 2)."""
+        from oracle import contract as oc
+        an, bn, pa, pb = self.steps[i]
+        A = (self.legs[an], 0, self.data[an]) if an else a
+        B = (self.legs[bn], 0, self.data[bn])
+        lc, qc, c, _ = oc.contract("u1", A, B, pa, pb)
+        g = np.random.default_rng(i).standard_normal(c.size)
+        oc.contract_grad("u1", A, B, pa, pb, g)
+        return (lc, qc, c)
+
+    def full_step(self):
+        a = None
+        for i in range(3):
+            a = self.contraction(i, a)
+
+    def inputs_of(self, i):
+        """Input of contraction i (computed once, outside any timing)."""
+        from oracle import contract as oc
+        a = None
+        for j in range(i):
+            an, bn, pa, pb = self.steps[j]
+            A = (self.legs[an], 0, self.data[an]) if an else a
+            lc, qc, c, _ = oc.contract("u1", A, (self.legs[bn], 0, self.data[bn]), pa, pb)
+            a = (lc, qc, c)
+        return a
+
+
+np = None
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def cpu_baseline(flops, steps):
+    o = OracleMPS()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.full_step()
+    dt = time.perf_counter() - t0
+    return {"value": round(flops * steps / dt / 1e12, 6), "unit": "TFLOP/s", "cores": cpu_cores(),
+            "kind": "oracle",
+            "sample": f"{steps} full fwd+bwd step(s) of the same workload, dense FP64 numpy oracle, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, flops_by_contraction):
+    """The oracle as the reference arm: each step is one contraction of the chain (fwd + grad), rotating."""
+    o = OracleMPS()
+    ins = [o.inputs_of(i) for i in range(3)]
+    for w in range(args.warmup):
+        o.contraction(w % 3, ins[w % 3])
+    t0 = time.perf_counter()
+    fl = 0.0
+    for s in range(args.steps):
+        o.contraction(s % 3, ins[s % 3])
+        fl += 3.0 * flops_by_contraction[s % 3]
+    dt = time.perf_counter() - t0
+    value = fl / dt / 1e12
+    return {
+        "metric": METRIC, "value": round(value, 6), "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "sample": "step s = contraction (s mod 3) of the chain, fwd + grad"},
+        "cpu_baseline": {"value": round(value, 6), "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": "one contraction of ((L.A).W).R per step, rotating, dense FP64 numpy oracle"},
+        "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def contraction_flops_host():
+    """Useful forward flops of each contraction of the chain (host planning only)."""
+    os.environ["SYM_PLAN_DRYRUN"] = "1"
+    import paper_1203_2222_gb300 as P
+    m, S = mps_structures(P)
+    t1 = P.contract_plan(S["L"], S["A"], [2], [0], P.BF16X3)
+    t2 = P.contract_plan(t1.out, S["W"], [1, 2], [0, 2], P.BF16X3)
+    t3 = P.contract_plan(t2.out, S["R"], [1, 3], [2, 1], P.BF16X3)
+    return [t.stats()["flops_fwd"] for t in (t1, t2, t3)]
+
+
+def main():
+    global np
+    import numpy
+    np = numpy
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        out = run_reference(args, contraction_flops_host())
+        print(json.dumps(out))
+        return 0
+    import torch
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    out, flops = run_ours(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(flops, args.cpu_sample_steps)
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -163,6 +163,28 @@ int sym_plan_stats(sym_plan plan, double* flops_fwd, int64_t* bytes_a,
                    int64_t* bytes_b, int64_t* bytes_c);
 int sym_plan_destroy(sym_plan plan);
 
+/* GEMM sectors of a contraction plan (forward, dA and dB GEMMs of every
+ * sector): *nsec receives their number and mnk (may be NULL) 4*nsec ints
+ * (m, n, k, kernel) with kernel 0 = tcgen05 split-BF16, 1 = CUDA cores. */
+int sym_plan_gemm_shapes(sym_plan plan, int* nsec, int* mnk);
+
+/* Per-phase device timing of a plan's own launches.  sym_plan_profile(p, 1)
+ * clears and starts recording a CUDA event pair around every launch (on the
+ * launch stream); 0 stops.  sym_plan_profile_read synchronizes on the
+ * recorded events and returns, for one phase, the number of launches, their
+ * summed device time, and their algorithmic bytes (block data read once +
+ * destination written once) and useful flops (sum of 2 m n k).           */
+#define SYM_PHASE_FWD_GATHER 0
+#define SYM_PHASE_FWD_GEMM 1
+#define SYM_PHASE_FWD_SCATTER 2
+#define SYM_PHASE_BWD_GATHER 3
+#define SYM_PHASE_BWD_GEMM 4
+#define SYM_PHASE_BWD_SCATTER 5
+#define SYM_PHASE_TRANSFORM 6
+int sym_plan_profile(sym_plan plan, int enable);
+int sym_plan_profile_read(sym_plan plan, int phase, int* launches,
+                          double* total_ms, double* bytes, double* flops);
+
 /* Number of kernel launches the last execution call on this plan issued. */
 int sym_plan_launches(sym_plan plan, int* launches);
 

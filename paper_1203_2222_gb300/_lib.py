@@ -69,7 +69,10 @@ _SIGS = {
     "sym_contract_backward": ([_P, _P, _P, _P, _P, _P, _P], _I),
     "sym_plan_stats": ([_P, _DP, _LP, _LP, _LP], _I),
     "sym_plan_launches": ([_P, _IP], _I),
+    "sym_plan_profile": ([_P, _I], _I),
+    "sym_plan_profile_read": ([_P, _I, _IP, _DP, _DP, _DP], _I),
     "sym_plan_destroy": ([_P], _I),
+    "sym_plan_gemm_shapes": ([_P, _IP, _IP], _I),
     "sym_device_status": ([], _I),
     "sym_su2_F": ([_I, _I, _I, _I, _I, _I, _DP], _I),
     "sym_su2_gamma": ([_I, _IP, _IP, _IP, _IP, _IP, _IP, _DP, _IP, _IP], _I),

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <memory>
 #include <new>
 #include <string>
@@ -299,6 +300,52 @@ int sym_plan_launches(sym_plan plan, int* launches) {
   return guard([&] {
     need(plan && plan->p && launches, "NULL argument");
     *launches = plan->p->last_launches;
+    return SYM_OK;
+  });
+}
+
+int sym_plan_profile(sym_plan plan, int enable) {
+  return guard([&] {
+    need(plan && plan->p, "plan is NULL");
+    if (enable) plan->p->clear_profile();
+    plan->p->profiling = enable != 0;
+    return SYM_OK;
+  });
+}
+
+int sym_plan_profile_read(sym_plan plan, int phase, int* launches, double* total_ms, double* bytes, double* flops) {
+  return guard([&] {
+    need(plan && plan->p, "plan is NULL");
+    need(phase >= 0 && phase < sym::PH_COUNT, "bad phase");
+    sym::PhaseProfile& pp = plan->p->prof[phase];
+    double ms = 0.0;
+    for (auto& e : pp.events) {
+      cudaError_t err = cudaEventSynchronize(static_cast<cudaEvent_t>(e.second));
+      if (err != cudaSuccess) sym::fail(SYM_ERR_CUDA, std::string("event: ") + cudaGetErrorString(err));
+      float t = 0.f;
+      cudaEventElapsedTime(&t, static_cast<cudaEvent_t>(e.first), static_cast<cudaEvent_t>(e.second));
+      ms += t;
+    }
+    if (launches) *launches = pp.launches;
+    if (total_ms) *total_ms = ms;
+    if (bytes) *bytes = pp.bytes;
+    if (flops) *flops = pp.flops;
+    return SYM_OK;
+  });
+}
+
+int sym_plan_gemm_shapes(sym_plan plan, int* nsec, int* mnk) {
+  return guard([&] {
+    need(plan && plan->p && nsec, "NULL argument");
+    const sym::Plan& p = *plan->p;
+    // one entry per GEMM sector: tensor-core sectors, then CUDA-core sectors
+    std::vector<std::array<int, 4>> v;
+    for (const auto& s : p.secs_tc) v.push_back({s.m, s.n, s.k, 0});
+    for (const auto& s : p.secs_simt) v.push_back({s.m, s.n, s.k, 1});
+    if (mnk)
+      for (size_t i = 0; i < v.size(); ++i)
+        for (int j = 0; j < 4; ++j) mnk[4 * i + j] = v[i][j];
+    *nsec = (int)v.size();
     return SYM_OK;
   });
 }

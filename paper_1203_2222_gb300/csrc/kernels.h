@@ -7,21 +7,25 @@ namespace sym {
 
 constexpr int kMaxDim = 6;
 
+// Destination slots of a box launch.
+enum DstSlot { DST_IMAGE = 0, DST_OUT = 1, DST_DA = 2, DST_DB = 3, DST_OPS = 4, DST_OUTM = 5, DST_COUNT = 6 };
+constexpr int kSelImage = 1 << 8;  // BoxItem::sel flag: destination is a split-BF16 image
+
 // One work unit of the block-movement kernel: a strided box of `dims`
 // (last dim fastest) whose element t is
 //   dst  <- sum over terms  coef * src[term.off + term.ld * <t, sa> + <t, sb>]
-// Destination (by kernel mode):
+// Destination:
 //   linear: dst[dst_off + dst_ld * <t, da> + <t, db>]
 //   image : sector matrix element (row0 + <t, da>, col0 + <t, db>) of a
 //           tiled split-BF16 operand image starting at dst_off (see gemm_tc.cu)
 // Only elements [start, start + count) of the box (row-major linear index)
 // belong to this unit; the planner guarantees that every destination element
-// is written by exactly one unit.
+// is written by exactly one unit.  An item with no terms writes zeros.
 struct BoxItem {
   int64_t dst_off;
   int32_t dst_ld;   // linear: multiplier of <t, da>; image: K tiles per row tile
   int32_t row0, col0;
-  int32_t sel;      // source slot (bits 0-3) and destination slot (bits 4-7)
+  int32_t sel;      // source slot (bits 0-1), destination slot (bits 4-6), kSelImage
   int32_t ndim;
   int32_t term0, nterm;
   int32_t start, count;
@@ -36,23 +40,24 @@ struct Term {
   double coef;
 };
 
-enum BoxMode { BOX_LINEAR_F32 = 0, BOX_LINEAR_F64 = 1, BOX_IMAGE_BF16X2 = 2 };
-
-// Buffers a box launch may read (src slots) and write (dst slots; image mode
-// writes the hi image to dst[i][0] and the lo image to dst[i][1]).
+// Buffers a box launch may read (src slots) and write (dst slots; image
+// items write the hi image to dst[i][0] and the lo image to dst[i][1]).
 struct BoxPtrs {
   const void* src[4];
-  void* dst[4][2];
+  void* dst[DST_COUNT][2];
 };
 
-// FP64 grouped GEMM (row-major): C = alpha * A (m x k, lda) * B (k x n, ldb).
-struct GemmSector64 {
+// CUDA-core grouped GEMM (row-major): C = alpha * A (m x k, lda) * B (k x n, ldb).
+struct GemmSectorSimt {
   int32_t m, n, k, lda, ldb, ldc;
   int64_t a_off, b_off, c_off;
   double alpha;
 };
+// One output tile; [k0, k1) is its slice of the reduction (split-K tiles of
+// one sector add into a zero-filled C with atomics when `atomic` is set).
 struct GemmTile {
   int32_t sector, mt, nt;
+  int32_t k0, k1, atomic;
 };
 
 // tcgen05 split-BF16 x3 grouped GEMM.  Operand images: A tile (mt, kt) at
@@ -66,11 +71,14 @@ struct TcSector {
   float alpha;
 };
 
+// CUDA-core GEMM tile shapes
+enum SimtShape { SIMT_64x64 = 0, SIMT_256x16 = 1, SIMT_SHAPES = 2 };
+
 // Launchers (return cudaError_t as int).
-int launch_box(int mode, bool src_f64, const BoxItem* items, int nitems, const Term* terms,
+int launch_box(bool src_f64, bool dst_f64, const BoxItem* items, int nitems, const Term* terms,
                const BoxPtrs& ptrs, void* stream);
-int launch_gemm_f64(const GemmSector64* secs, const GemmTile* tiles, int ntiles, const double* A,
-                    const double* B, double* C, void* stream);
+int launch_gemm_simt(bool f64, int shape, const GemmSectorSimt* secs, const GemmTile* tiles, int ntiles,
+                     const void* ops, void* outm, void* stream);
 int launch_gemm_tc(const TcSector* secs, const GemmTile* tiles, int ntiles, const uint16_t* a_hi,
                    const uint16_t* a_lo, const uint16_t* b_hi, const uint16_t* b_lo, float* C,
                    int* err_word, void* stream);

@@ -330,9 +330,12 @@ DeviceArena::~DeviceArena() {
 // Largest element offset every box item can touch, checked against the size
 // of the buffer in its source / destination slot (elements).  Strides are
 // non-negative, so the extreme is at the last index of every dimension.
-void Plan::validate(const int64_t* src_elems, const int64_t* dst_elems, bool dst0_image) const {
+void Plan::validate(const int64_t* src_elems, const int64_t* dst_elems) const {
   for (const BoxItem& it : items) {
-    int64_t sa = 0, sb = 0, da = 0, db = 0;
+    if (it.term0 < 0 || it.nterm < 0 || (size_t)it.term0 + it.nterm > terms.size())
+      fail(SYM_ERR_ARG, "internal: term range out of bounds");
+    if (it.ndim < 1 || it.ndim > kMaxDim || it.count <= 0 || it.start < 0) fail(SYM_ERR_ARG, "internal: bad box");
+    int64_t sa = 0, sb = 0, da = 0, db = 0, total = 1;
     for (int d = 0; d < it.ndim; ++d) {
       if (it.dims[d] < 1 || it.sa[d] < 0 || it.sb[d] < 0 || it.da[d] < 0 || it.db[d] < 0)
         fail(SYM_ERR_ARG, "internal: negative stride or empty dim in a work item");
@@ -340,15 +343,19 @@ void Plan::validate(const int64_t* src_elems, const int64_t* dst_elems, bool dst
       sb += (int64_t)(it.dims[d] - 1) * it.sb[d];
       da += (int64_t)(it.dims[d] - 1) * it.da[d];
       db += (int64_t)(it.dims[d] - 1) * it.db[d];
+      total *= it.dims[d];
     }
-    const int ss = it.sel & 3, ds = (it.sel >> 4) & 3;
+    if ((int64_t)it.start + it.count > total) fail(SYM_ERR_ARG, "internal: chunk past its box");
+    const int ss = it.sel & 3, ds = (it.sel >> 4) & 7;
+    if (ds >= DST_COUNT) fail(SYM_ERR_ARG, "internal: bad destination slot");
     for (int i = 0; i < it.nterm; ++i) {
       const Term& t = terms[it.term0 + i];
       if (t.off < 0 || t.ld < 0 || t.off + t.ld * sa + sb >= src_elems[ss])
         fail(SYM_ERR_ARG, "internal: work item reads past its source buffer");
     }
     int64_t last;
-    if (ds == 0 && dst0_image) {
+    if (it.sel & kSelImage) {
+      if (ds != DST_IMAGE) fail(SYM_ERR_ARG, "internal: image item outside the image slot");
       const int64_t row = it.row0 + da, col = it.col0 + db;
       if (it.row0 < 0 || it.col0 < 0 || (col >> 6) >= it.dst_ld)
         fail(SYM_ERR_ARG, "internal: image column past its K tiles");
@@ -360,7 +367,47 @@ void Plan::validate(const int64_t* src_elems, const int64_t* dst_elems, bool dst
   }
 }
 
+void Plan::set_item_bytes(Range r, int es_src, int es_dst) {
+  if (item_bytes_prefix.size() != items.size() + 1) item_bytes_prefix.assign(items.size() + 1, 0.0);
+  for (int i = r.first; i < r.first + r.count; ++i) {
+    const BoxItem& it = items[i];
+    item_bytes_prefix[i + 1] = (double)it.count * ((it.nterm > 0 ? es_src : 0) + es_dst);
+  }
+}
+
+void Plan::clear_profile() {
+  for (auto& p : prof) {
+    for (auto& e : p.events) {
+      cudaEventDestroy(static_cast<cudaEvent_t>(e.first));
+      cudaEventDestroy(static_cast<cudaEvent_t>(e.second));
+    }
+    p = PhaseProfile{};
+  }
+}
+
+Plan::~Plan() { clear_profile(); }
+
 void Plan::upload() {
+  // finish the statistics tables (prefix sums)
+  if (item_bytes_prefix.size() != items.size() + 1) item_bytes_prefix.assign(items.size() + 1, 0.0);
+  for (size_t i = 0; i < items.size(); ++i) item_bytes_prefix[i + 1] += item_bytes_prefix[i];
+  tile_flops_prefix.assign(tiles.size() + 1, 0.0);
+  for (size_t i = 0; i < tiles.size(); ++i) {
+    const GemmTile& t = tiles[i];
+    int64_t m, n, TM, TN;
+    if (tile_kind[i] == 0) {
+      m = secs_tc[t.sector].m;
+      n = secs_tc[t.sector].n;
+      TM = TN = 128;
+    } else {
+      m = secs_simt[t.sector].m;
+      n = secs_simt[t.sector].n;
+      TM = tile_kind[i] == 1 ? 64 : 256;
+      TN = tile_kind[i] == 1 ? 64 : 16;
+    }
+    const int64_t r = std::min<int64_t>(TM, m - t.mt * TM), c = std::min<int64_t>(TN, n - t.nt * TN);
+    tile_flops_prefix[i + 1] = tile_flops_prefix[i] + 2.0 * (double)r * (double)c * (double)(t.k1 - t.k0);
+  }
   const char* dry_env = std::getenv("SYM_PLAN_DRYRUN");
   if (dry_env && dry_env[0] == '1') {
     dry = true;  // host-only planning and validation; the plan cannot run
@@ -374,28 +421,19 @@ void Plan::upload() {
     }
     return d;
   };
-  // validate every work unit against the buffers it touches (host-side bounds check)
-  for (const BoxItem& it : items) {
-    if (it.term0 < 0 || it.nterm < 0 || (size_t)it.term0 + it.nterm > terms.size())
-      fail(SYM_ERR_ARG, "internal: term range out of bounds");
-    if (it.ndim < 1 || it.ndim > kMaxDim || it.count <= 0 || it.start < 0) fail(SYM_ERR_ARG, "internal: bad box");
-  }
   d_items = static_cast<BoxItem*>(up(items.data(), items.size() * sizeof(BoxItem)));
   d_terms = static_cast<Term*>(up(terms.data(), terms.size() * sizeof(Term)));
-  if (f64())
-    d_secs = up(secs64.data(), secs64.size() * sizeof(GemmSector64));
-  else
-    d_secs = up(secs_tc.data(), secs_tc.size() * sizeof(TcSector));
+  d_secs_simt = static_cast<GemmSectorSimt*>(up(secs_simt.data(), secs_simt.size() * sizeof(GemmSectorSimt)));
+  d_secs_tc = static_cast<TcSector*>(up(secs_tc.data(), secs_tc.size() * sizeof(TcSector)));
   d_tiles = static_cast<GemmTile*>(up(tiles.data(), tiles.size() * sizeof(GemmTile)));
   if (kind == CONTRACT) {
-    if (f64()) {
-      ops0 = arena.alloc(ops_elems * sizeof(double), false);
-      outm = arena.alloc(outm_elems * sizeof(double), false);
-    } else {
-      ops0 = arena.alloc(ops_elems * 2, true);  // zero padding of the images
-      ops1 = arena.alloc(ops_elems * 2, true);
-      outm = arena.alloc(outm_elems * sizeof(float), false);
+    const size_t es = f64() ? sizeof(double) : sizeof(float);
+    if (img_elems > 0) {
+      img_hi = arena.alloc(img_elems * 2, true);  // zero padding of the images
+      img_lo = arena.alloc(img_elems * 2, true);
     }
+    lin = arena.alloc(lin_elems * es, false);
+    outm = arena.alloc(outm_elems * es, false);
   }
   d_err = device_error_word();
   cudaError_t e = cudaDeviceSynchronize();
@@ -590,15 +628,43 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
   }
   P->xform = {0, (int)P->items.size()};
   {
+    const int es = precision == SYM_PREC_FP64 ? 8 : 4;
+    P->set_item_bytes(P->xform, es, es);
+  }
+  {
     const int64_t src[4] = {in.numel(), 0, 0, 0};
-    const int64_t dst[4] = {0, out.numel(), 0, 0};
-    P->validate(src, dst, false);
+    const int64_t dst[DST_COUNT] = {0, out.numel(), 0, 0, 0, 0};
+    P->validate(src, dst);
   }
   P->upload();
   return P;
 }
 
 // ----------------------------------------------------------------- contraction --
+namespace {
+
+// Kernel choice of one GEMM (m x n result, reduction k) of a split-BF16 plan:
+// the tensor cores when the 128 x 128 x 64 tile is well filled, the exact
+// FP32 CUDA-core kernel otherwise (thin matrices are bandwidth-bound, and
+// very long reductions are split across CTAs there).  Thresholds can be
+// overridden with SYM_TC_MIN_MN / SYM_TC_MIN_K / SYM_TC_MAX_K.
+int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return v && *v ? std::atoi(v) : dflt;
+}
+
+int choose_kind(bool f64, int64_t m, int64_t n, int64_t k) {
+  const int simt = n <= 16 ? 2 : 1;
+  if (f64) return simt;
+  static const int min_mn = env_int("SYM_TC_MIN_MN", 96);
+  static const int min_k = env_int("SYM_TC_MIN_K", 48);
+  static const int max_k = env_int("SYM_TC_MAX_K", 16384);
+  if (m >= min_mn && n >= min_mn && k >= min_k && k <= max_k) return 0;
+  return simt;
+}
+
+}  // namespace
+
 std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std::vector<int>& pairsA,
                                     const std::vector<int>& pairsB, const Tensor& C, int precision) {
   auto P = std::make_unique<Plan>();
@@ -668,11 +734,16 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   MatForm MB = make_matform(Bm, nc, keyB);
   MatForm MC = make_matform(Cn, na, keyC);
 
-  // GEMM sectors: x present on both sides
+  // GEMM sectors: x present on both sides.  Per sector three GEMMs:
+  // forward C = A B (m n k), dA = dC B^T (m k n), dB = A^T dC (k n m).
   struct G {
     int x;
     int64_t m, n, k;
-    int64_t a, b, c, dc1, bt, at, dc2, da, db;  // buffer offsets
+    int kind[3];
+    // operand offsets: images (bf16 elements) or linear (elements)
+    int64_t a, b, dc1, bt, at, dc2, dcl;
+    int64_t c, da, db;  // output matrices
+    bool split[3];
   };
   std::vector<G> gs;
   std::map<int, int> gofx;
@@ -688,87 +759,103 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     if (g.m <= 0 || g.n <= 0 || g.k <= 0) continue;
     if (g.m >= ((int64_t)1 << 31) || g.n >= ((int64_t)1 << 31) || g.k >= ((int64_t)1 << 31))
       fail(SYM_ERR_UNSUPPORTED, "sector matrix dimension too large");
+    g.kind[0] = choose_kind(f64, g.m, g.n, g.k);
+    g.kind[1] = choose_kind(f64, g.m, g.k, g.n);
+    g.kind[2] = choose_kind(f64, g.k, g.n, g.m);
     gofx[g.x] = (int)gs.size();
     gs.push_back(g);
   }
-  // buffer layout
-  const int64_t T = f64 ? 64 : 128;
   auto img = [&](int64_t rows, int64_t kk) { return cdiv(rows, 128) * cdiv(kk, 64) * 8192; };
-  int64_t ops = 0, outm = 0;
+  int64_t ie = 0, le = 0, oe = 0;
   for (auto& g : gs) {
-    g.a = ops;
-    ops += f64 ? g.m * g.k : img(g.m, g.k);
-    g.b = ops;
-    ops += f64 ? g.k * g.n : img(g.n, g.k);
-  }
-  for (auto& g : gs) {
-    g.dc1 = ops;
-    ops += f64 ? g.m * g.n : img(g.m, g.n);
-    g.bt = ops;
-    ops += f64 ? g.n * g.k : img(g.k, g.n);
-    g.at = ops;
-    ops += f64 ? g.k * g.m : img(g.k, g.m);
-    g.dc2 = g.dc1;
-    if (!f64) {
-      g.dc2 = ops;
-      ops += img(g.n, g.m);
+    if (g.kind[0] == 0) {
+      g.a = ie, ie += img(g.m, g.k);
+      g.b = ie, ie += img(g.n, g.k);
+    } else {
+      g.a = le, le += g.m * g.k;
+      g.b = le, le += g.k * g.n;
     }
   }
   for (auto& g : gs) {
-    g.c = outm;
-    outm += g.m * g.n;
-    g.da = outm;
-    outm += g.m * g.k;
-    g.db = outm;
-    outm += g.k * g.n;
+    if (g.kind[1] == 0) {
+      g.dc1 = ie, ie += img(g.m, g.n);
+      g.bt = ie, ie += img(g.k, g.n);
+    } else {
+      g.bt = le, le += g.n * g.k;
+    }
+    if (g.kind[2] == 0) {
+      g.at = ie, ie += img(g.k, g.m);
+      g.dc2 = ie, ie += img(g.n, g.m);
+    } else {
+      g.at = le, le += g.k * g.m;
+    }
+    if (g.kind[1] != 0 || g.kind[2] != 0) g.dcl = le, le += g.m * g.n;
   }
-  P->ops_elems = ops;
-  P->outm_elems = outm;
+  for (auto& g : gs) {
+    g.c = oe, oe += g.m * g.n;
+    g.da = oe, oe += g.m * g.k;
+    g.db = oe, oe += g.k * g.n;
+  }
+  P->img_elems = ie;
+  P->lin_elems = le;
+  P->outm_elems = oe;
   for (auto& g : gs) P->flops_fwd += 2.0 * (double)g.m * (double)g.n * (double)g.k;
   P->numel_a = A.numel();
   P->numel_b = B.numel();
   P->numel_c = C.numel();
 
-  // GEMM sectors and tiles: [fwd][bwd dA][bwd dB]
-  auto add_sector = [&](int64_t m, int64_t n, int64_t k, int64_t aoff, int64_t lda, int64_t boff, int64_t ldb,
-                        int64_t coff) {
-    if (f64) {
-      GemmSector64 s{(int)m, (int)n, (int)k, (int)lda, (int)ldb, (int)n, aoff, boff, coff, 1.0};
-      P->secs64.push_back(s);
-      return (int)P->secs64.size() - 1;
+  // ---- GEMM sectors and tiles: lists per (kind, gemm phase)
+  std::vector<std::pair<int64_t, GemmTile>> lists[3][3];
+  const int nsm = 152;
+  auto add_gemm = [&](int kind, int ph, int64_t m, int64_t n, int64_t k, int64_t aoff, int64_t lda, int64_t boff,
+                      int64_t ldb, int64_t coff) -> bool {
+    if (kind == 0) {
+      P->secs_tc.push_back(TcSector{(int)m, (int)n, (int)k, (int)cdiv(k, 64), aoff, boff, coff, (int)n, 1.0f});
+      const int sec = (int)P->secs_tc.size() - 1;
+      for (int64_t mt = 0; mt < cdiv(m, 128); ++mt)
+        for (int64_t nt = 0; nt < cdiv(n, 128); ++nt)
+          lists[0][ph].push_back({k, GemmTile{sec, (int)mt, (int)nt, 0, (int)k, 0}});
+      return false;
     }
-    TcSector s{(int)m, (int)n, (int)k, (int)cdiv(k, 64), aoff, boff, coff, (int)n, 1.0f};
-    P->secs_tc.push_back(s);
-    return (int)P->secs_tc.size() - 1;
+    P->secs_simt.push_back(GemmSectorSimt{(int)m, (int)n, (int)k, (int)lda, (int)ldb, (int)n, aoff, boff, coff, 1.0});
+    const int sec = (int)P->secs_simt.size() - 1;
+    const int64_t TM = kind == 1 ? 64 : 256, TN = kind == 1 ? 64 : 16;
+    const int64_t ntl = cdiv(m, TM) * cdiv(n, TN);
+    int64_t nsplit = 1;
+    if (k > 4096 && ntl < 2 * nsm) nsplit = std::min<int64_t>(cdiv(k, 2048), cdiv(4 * nsm, ntl));
+    const int64_t kc = cdiv(cdiv(k, nsplit), 16) * 16;
+    nsplit = cdiv(k, kc);
+    for (int64_t mt = 0; mt < cdiv(m, TM); ++mt)
+      for (int64_t nt = 0; nt < cdiv(n, TN); ++nt)
+        for (int64_t s = 0; s < nsplit; ++s) {
+          const int64_t k0 = s * kc, k1 = std::min(k, k0 + kc);
+          lists[kind][ph].push_back({k1 - k0, GemmTile{sec, (int)mt, (int)nt, (int)k0, (int)k1, nsplit > 1 ? 1 : 0}});
+        }
+    return nsplit > 1;
   };
-  auto add_tiles = [&](int sec, int64_t m, int64_t n, std::vector<std::pair<int64_t, GemmTile>>& v, int64_t k) {
-    for (int64_t mt = 0; mt < cdiv(m, T); ++mt)
-      for (int64_t nt = 0; nt < cdiv(n, T); ++nt) v.push_back({k, GemmTile{sec, (int)mt, (int)nt}});
-  };
-  auto flush_tiles = [&](std::vector<std::pair<int64_t, GemmTile>>& v) {
-    std::stable_sort(v.begin(), v.end(), [](auto& a, auto& b) { return a.first > b.first; });
-    Range r{(int)P->tiles.size(), (int)v.size()};
-    for (auto& t : v) P->tiles.push_back(t.second);
-    return r;
-  };
-  {
-    std::vector<std::pair<int64_t, GemmTile>> v;
-    for (auto& g : gs) add_tiles(add_sector(g.m, g.n, g.k, g.a, g.k, g.b, g.n, g.c), g.m, g.n, v, g.k);
-    P->fwd_tiles = flush_tiles(v);
-    v.clear();
-    for (auto& g : gs) add_tiles(add_sector(g.m, g.k, g.n, g.dc1, g.n, g.bt, g.k, g.da), g.m, g.k, v, g.n);
-    P->bwd_tiles_a = flush_tiles(v);
-    v.clear();
-    for (auto& g : gs) add_tiles(add_sector(g.k, g.n, g.m, g.at, g.m, g.dc2, g.n, g.db), g.k, g.n, v, g.m);
-    P->bwd_tiles_b = flush_tiles(v);
+  for (auto& g : gs) {
+    g.split[0] = add_gemm(g.kind[0], 0, g.m, g.n, g.k, g.a, g.k, g.b, g.n, g.c);
+    g.split[1] = add_gemm(g.kind[1], 1, g.m, g.k, g.n, g.kind[1] == 0 ? g.dc1 : g.dcl, g.n, g.bt, g.k, g.da);
+    g.split[2] = add_gemm(g.kind[2], 2, g.k, g.n, g.m, g.at, g.m, g.kind[2] == 0 ? g.dc2 : g.dcl, g.n, g.db);
   }
+  for (int kind = 0; kind < 3; ++kind)
+    for (int ph = 0; ph < 3; ++ph) {
+      auto& v = lists[kind][ph];
+      std::stable_sort(v.begin(), v.end(), [](auto& a, auto& b) { return a.first > b.first; });
+      P->gemm_range[kind][ph] = Range{(int)P->tiles.size(), (int)v.size()};
+      for (auto& t : v) {
+        P->tiles.push_back(t.second);
+        P->tile_kind.push_back(kind);
+      }
+    }
 
   int rw[kMaxDim], cw[kMaxDim], st[kMaxDim];
   std::vector<int> pinvA(A.rank), pinvB(B.rank);
   for (int n = 0; n < A.rank; ++n) pinvA[permA[n]] = n;
   for (int n = 0; n < B.rank; ++n) pinvB[permB[n]] = n;
 
-  // box of a source block of S gathered into a matrix of Sm (S leg l -> Sm leg pinv[l])
+  // box of a source block of S gathered into the matrix form of Sm (S leg l -> Sm leg pinv[l]);
+  // swap_rc exchanges the roles of row and column weights (transposed operands)
   auto gather_box = [&](const Tensor& S, const std::vector<int>& pinv, const Tensor& Sm, int64_t sm, int64_t ssrc,
                         int nrows, bool swap_rc) {
     group_weights(Sm, sm, nrows, rw, cw);
@@ -785,31 +872,45 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     for (auto& pc : tl) t.push_back({S.offs[pc.first], 1, pc.second});
     return t;
   };
+  // operand written either as an image (rows, K-tiles) or as a linear matrix
+  auto put = [&](const Box& b, int src, bool image, int64_t off, int64_t kk, int64_t row0, int64_t col0,
+                 int64_t ld, const std::vector<Term>& t) {
+    if (image)
+      emit(*P, b, off, (int)cdiv(kk, 64), (int)row0, (int)col0, src, DST_IMAGE | (kSelImage >> 4), t);
+    else
+      emit(*P, b, off + row0 * ld + col0, (int)ld, 0, 0, src, DST_OPS, t);
+  };
+  // zero-fill of an output matrix before a split-K GEMM adds into it
+  auto zero_fill = [&](int64_t off, int64_t rows, int64_t cols) {
+    Box b;
+    b.push((int)rows, 0, 0, 1, 0);
+    b.push((int)cols, 0, 0, 0, 1);
+    emit(*P, b, off, (int)cols, 0, 0, 3, DST_OUTM, {});
+  };
 
-  // ---- forward gather: A -> A operand, B -> B operand
+  // ---- forward gather: A -> A operand, B -> B operand (+ zero fills)
   int begin = (int)P->items.size();
   for (int64_t s = 0; s < Am.nsec(); ++s) {
     auto gi = gofx.find(MA.xs[MA.sx[s]]);
     if (gi == gofx.end() || XA[s].empty()) continue;
     const G& g = gs[gi->second];
     Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, false);
-    if (f64)
-      emit(*P, b, g.a + MA.r0[s] * g.k + MA.c0[s], (int)g.k, 0, 0, 0, 0, terms_of(XA[s], A));
-    else
-      emit(*P, b, g.a, (int)cdiv(g.k, 64), (int)MA.r0[s], (int)MA.c0[s], 0, 0, terms_of(XA[s], A));
+    put(b, 0, g.kind[0] == 0, g.a, g.k, MA.r0[s], MA.c0[s], g.k, terms_of(XA[s], A));
   }
   for (int64_t s = 0; s < Bm.nsec(); ++s) {
     auto gi = gofx.find(MB.xs[MB.sx[s]]);
     if (gi == gofx.end() || XB[s].empty()) continue;
     const G& g = gs[gi->second];
-    if (f64) {
-      Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, false);
-      emit(*P, b, g.b + MB.r0[s] * g.n + MB.c0[s], (int)g.n, 0, 0, 1, 0, terms_of(XB[s], B));
-    } else {
+    if (g.kind[0] == 0) {  // image rows n (free), K = k (contracted)
       Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, true);
-      emit(*P, b, g.b, (int)cdiv(g.k, 64), (int)MB.c0[s], (int)MB.r0[s], 1, 0, terms_of(XB[s], B));
+      put(b, 1, true, g.b, g.k, MB.c0[s], MB.r0[s], 0, terms_of(XB[s], B));
+    } else {
+      Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, false);
+      put(b, 1, false, g.b, 0, MB.r0[s], MB.c0[s], g.n, terms_of(XB[s], B));
     }
   }
+  for (auto& g : gs)
+    if (g.split[0]) zero_fill(g.c, g.m, g.n);
   P->fwd_gather = {begin, (int)P->items.size() - begin};
 
   // ---- forward scatter: C_x -> C blocks (SU(2): Gamma to the requested tree)
@@ -817,7 +918,6 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     auto gi = gofx.find(MC.xs[MC.sx[sn]]);
     if (gi == gofx.end()) return;
     const G& g = gs[gi->second];
-    // C_nat row group lives in A's row groups, column group in B's column groups
     int x = MC.xs[MC.sx[sn]];
     int64_t r0 = MA.rowoff.at({x, row_key(Cn, sn, na)});
     int64_t c0 = MB.coloff.at({x, col_key(Cn, sn, na)});
@@ -835,25 +935,11 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     block_strides(C, s, st);
     Box b;
     for (int l = 0; l < C.rank; ++l) b.push(C.dim(s, l), rw[l], cw[l], st[l], 0);
-    emit(*P, b, C.offs[s], 1, 0, 0, 3, 1, t);
+    emit(*P, b, C.offs[s], 1, 0, 0, 3, DST_OUT, t);
   }
   P->fwd_scatter = {begin, (int)P->items.size() - begin};
 
-  // ---- backward gathers: [dA-only: B^T][shared (fp64): dC][dB-only: A^T]
-  int b0 = (int)P->items.size();
-  for (int64_t s = 0; s < Bm.nsec(); ++s) {
-    auto gi = gofx.find(MB.xs[MB.sx[s]]);
-    if (gi == gofx.end() || XB[s].empty()) continue;
-    const G& g = gs[gi->second];
-    if (f64) {
-      Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, true);
-      emit(*P, b, g.bt + MB.c0[s] * g.k + MB.r0[s], (int)g.k, 0, 0, 1, 0, terms_of(XB[s], B));
-    } else {
-      Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, false);
-      emit(*P, b, g.bt, (int)cdiv(g.n, 64), (int)MB.r0[s], (int)MB.c0[s], 1, 0, terms_of(XB[s], B));
-    }
-  }
-  // dC into the dA-side operand (rows m, inner n)
+  // ---- backward gathers: [dA only: B^T, dC image][shared: dC linear][dB only: A^T, dC image]
   std::vector<int> idC(C.rank);
   for (int i = 0; i < C.rank; ++i) idC[i] = i;
   auto dc_terms = [&](int64_t sn) {
@@ -865,57 +951,65 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     }
     return t;
   };
-  int b1 = (int)P->items.size();
-  for (int64_t sn = 0; sn < Cn.nsec(); ++sn) {
-    auto gi = gofx.find(MC.xs[MC.sx[sn]]);
-    if (gi == gofx.end()) continue;
-    const G& g = gs[gi->second];
-    int x = MC.xs[MC.sx[sn]];
-    int64_t r0 = MA.rowoff.at({x, row_key(Cn, sn, na)});
-    int64_t c0 = MB.coloff.at({x, col_key(Cn, sn, na)});
-    auto t = dc_terms(sn);
-    if (t.empty()) continue;
-    Box b = gather_box(Cn, idC, Cn, sn, sn, na, false);
-    if (f64)
-      emit(*P, b, g.dc1 + r0 * g.n + c0, (int)g.n, 0, 0, 2, 0, t);
-    else
-      emit(*P, b, g.dc1, (int)cdiv(g.n, 64), (int)r0, (int)c0, 2, 0, t);
-  }
-  int b2 = (int)P->items.size();
-  for (int64_t s = 0; s < Am.nsec(); ++s) {
-    auto gi = gofx.find(MA.xs[MA.sx[s]]);
-    if (gi == gofx.end() || XA[s].empty()) continue;
-    const G& g = gs[gi->second];
-    if (f64) {
-      Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, true);
-      emit(*P, b, g.at + MA.c0[s] * g.m + MA.r0[s], (int)g.m, 0, 0, 0, 0, terms_of(XA[s], A));
-    } else {
-      Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, true);
-      emit(*P, b, g.at, (int)cdiv(g.m, 64), (int)MA.c0[s], (int)MA.r0[s], 0, 0, terms_of(XA[s], A));
-    }
-  }
-  if (!f64) {
+  auto for_dc = [&](const std::function<void(const G&, int64_t, int64_t, int64_t)>& fn) {
     for (int64_t sn = 0; sn < Cn.nsec(); ++sn) {
       auto gi = gofx.find(MC.xs[MC.sx[sn]]);
       if (gi == gofx.end()) continue;
       const G& g = gs[gi->second];
       int x = MC.xs[MC.sx[sn]];
-      int64_t r0 = MA.rowoff.at({x, row_key(Cn, sn, na)});
-      int64_t c0 = MB.coloff.at({x, col_key(Cn, sn, na)});
-      auto t = dc_terms(sn);
-      if (t.empty()) continue;
-      Box b = gather_box(Cn, idC, Cn, sn, sn, na, true);
-      emit(*P, b, g.dc2, (int)cdiv(g.m, 64), (int)c0, (int)r0, 2, 0, t);
+      fn(g, sn, MA.rowoff.at({x, row_key(Cn, sn, na)}), MB.coloff.at({x, col_key(Cn, sn, na)}));
+    }
+  };
+  const int b0 = (int)P->items.size();
+  for (int64_t s = 0; s < Bm.nsec(); ++s) {
+    auto gi = gofx.find(MB.xs[MB.sx[s]]);
+    if (gi == gofx.end() || XB[s].empty()) continue;
+    const G& g = gs[gi->second];
+    if (g.kind[1] == 0) {  // image rows k (contracted), K = n (free)
+      Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, false);
+      put(b, 1, true, g.bt, g.n, MB.r0[s], MB.c0[s], 0, terms_of(XB[s], B));
+    } else {  // linear B^T (n x k)
+      Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, true);
+      put(b, 1, false, g.bt, 0, MB.c0[s], MB.r0[s], g.k, terms_of(XB[s], B));
     }
   }
-  int b3 = (int)P->items.size();
-  if (f64) {
-    P->bwd_gather_a = {b0, b2 - b0};  // B^T and dC
-    P->bwd_gather_b = {b1, b3 - b1};  // dC and A^T
-  } else {
-    P->bwd_gather_a = {b0, b2 - b0};  // B^T, dC (rows m)
-    P->bwd_gather_b = {b2, b3 - b2};              // A^T, dC (rows n)
+  for_dc([&](const G& g, int64_t sn, int64_t r0, int64_t c0) {
+    if (g.kind[1] != 0) return;
+    auto t = dc_terms(sn);
+    if (t.empty()) return;
+    put(gather_box(Cn, idC, Cn, sn, sn, na, false), 2, true, g.dc1, g.n, r0, c0, 0, t);
+  });
+  for (auto& g : gs)
+    if (g.split[1]) zero_fill(g.da, g.m, g.k);
+  const int b1 = (int)P->items.size();
+  for_dc([&](const G& g, int64_t sn, int64_t r0, int64_t c0) {
+    if (g.kind[1] == 0 && g.kind[2] == 0) return;
+    auto t = dc_terms(sn);
+    if (t.empty()) return;
+    put(gather_box(Cn, idC, Cn, sn, sn, na, false), 2, false, g.dcl, 0, r0, c0, g.n, t);
+  });
+  const int b2 = (int)P->items.size();
+  for (int64_t s = 0; s < Am.nsec(); ++s) {
+    auto gi = gofx.find(MA.xs[MA.sx[s]]);
+    if (gi == gofx.end() || XA[s].empty()) continue;
+    const G& g = gs[gi->second];
+    Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, true);
+    if (g.kind[2] == 0)  // image rows k (contracted), K = m (free)
+      put(b, 0, true, g.at, g.m, MA.c0[s], MA.r0[s], 0, terms_of(XA[s], A));
+    else  // linear A^T (k x m)
+      put(b, 0, false, g.at, 0, MA.c0[s], MA.r0[s], g.m, terms_of(XA[s], A));
   }
+  for_dc([&](const G& g, int64_t sn, int64_t r0, int64_t c0) {
+    if (g.kind[2] != 0) return;
+    auto t = dc_terms(sn);
+    if (t.empty()) return;
+    put(gather_box(Cn, idC, Cn, sn, sn, na, true), 2, true, g.dc2, g.m, c0, r0, 0, t);
+  });
+  for (auto& g : gs)
+    if (g.split[2]) zero_fill(g.db, g.k, g.n);
+  const int b3 = (int)P->items.size();
+  P->bwd_gather_a = {b0, b2 - b0};
+  P->bwd_gather_b = {b1, b3 - b1};
 
   // ---- backward scatters: dA_x -> dA blocks (Gamma^T), dB_x -> dB blocks
   begin = (int)P->items.size();
@@ -937,7 +1031,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
       int n = pinvA[l];
       b.push(A.dim(s, l), sm0 >= 0 ? rw[n] : 0, sm0 >= 0 ? cw[n] : 0, st[l], 0);
     }
-    emit(*P, b, A.offs[s], 1, 0, 0, 3, 2, t);
+    emit(*P, b, A.offs[s], 1, 0, 0, 3, DST_DA, t);
   }
   P->bwd_scatter_a = {begin, (int)P->items.size() - begin};
   begin = (int)P->items.size();
@@ -959,26 +1053,33 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
       int n = pinvB[l];
       b.push(B.dim(s, l), sm0 >= 0 ? rw[n] : 0, sm0 >= 0 ? cw[n] : 0, st[l], 0);
     }
-    emit(*P, b, B.offs[s], 1, 0, 0, 3, 3, t);
+    emit(*P, b, B.offs[s], 1, 0, 0, 3, DST_DB, t);
   }
   P->bwd_scatter_b = {begin, (int)P->items.size() - begin};
   {
-    const int64_t src[4] = {A.numel(), B.numel(), C.numel(), P->outm_elems};
-    const int64_t dst[4] = {P->ops_elems, C.numel(), A.numel(), B.numel()};
-    P->validate(src, dst, !f64);
+    const int es = f64 ? 8 : 4;
+    P->set_item_bytes({0, (int)P->items.size()}, es, es);
+    // image items write hi + lo bf16 = 4 bytes per element, as fp32
   }
-  // GEMM tiles stay inside their operand images / matrices
-  for (const GemmTile& t : P->tiles) {
-    if (f64) {
-      const GemmSector64& s = P->secs64[t.sector];
-      if (s.a_off + (int64_t)(s.m - 1) * s.lda + s.k - 1 >= P->ops_elems ||
-          s.b_off + (int64_t)(s.k - 1) * s.ldb + s.n - 1 >= P->ops_elems ||
+  {
+    const int64_t src[4] = {A.numel(), B.numel(), C.numel(), P->outm_elems};
+    const int64_t dst[DST_COUNT] = {P->img_elems, C.numel(), A.numel(), B.numel(), P->lin_elems, P->outm_elems};
+    P->validate(src, dst);
+  }
+  // GEMM tiles stay inside their operand buffers
+  for (size_t i = 0; i < P->tiles.size(); ++i) {
+    const GemmTile& t = P->tiles[i];
+    if (P->tile_kind[i] != 0) {
+      const GemmSectorSimt& s = P->secs_simt[t.sector];
+      if (t.k0 < 0 || t.k1 > s.k || t.k0 >= t.k1 ||
+          s.a_off + (int64_t)(s.m - 1) * s.lda + s.k - 1 >= P->lin_elems ||
+          s.b_off + (int64_t)(s.k - 1) * s.ldb + s.n - 1 >= P->lin_elems ||
           s.c_off + (int64_t)(s.m - 1) * s.ldc + s.n - 1 >= P->outm_elems)
-        fail(SYM_ERR_ARG, "internal: fp64 GEMM sector past its buffers");
+        fail(SYM_ERR_ARG, "internal: CUDA-core GEMM sector past its buffers");
     } else {
       const TcSector& s = P->secs_tc[t.sector];
-      if (s.a_img + ((int64_t)t.mt * s.ktiles + s.ktiles) * 8192 > P->ops_elems ||
-          s.b_img + ((int64_t)t.nt * s.ktiles + s.ktiles) * 8192 > P->ops_elems ||
+      if (s.a_img + ((int64_t)t.mt * s.ktiles + s.ktiles) * 8192 > P->img_elems ||
+          s.b_img + ((int64_t)t.nt * s.ktiles + s.ktiles) * 8192 > P->img_elems ||
           s.c_off + (int64_t)(s.m - 1) * s.ldc + s.n - 1 >= P->outm_elems || s.ktiles < 1)
         fail(SYM_ERR_ARG, "internal: tcgen05 GEMM tile past its buffers");
     }
@@ -995,25 +1096,72 @@ int cuda_code(int e, const char* what) {
   fail(SYM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString((cudaError_t)e));
 }
 
-int run_box(Plan& p, Range r, int mode, const BoxPtrs& ptrs, void* stream) {
+struct ProfScope {
+  Plan& p;
+  int phase;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaStream_t s;
+  ProfScope(Plan& p_, int ph, void* stream, double bytes, double flops) : p(p_), phase(ph) {
+    s = static_cast<cudaStream_t>(stream);
+    if (!p.profiling) return;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    p.prof[ph].launches++;
+    p.prof[ph].bytes += bytes;
+    p.prof[ph].flops += flops;
+  }
+  ~ProfScope() {
+    if (!p.profiling) return;
+    cudaEventRecord(e1, s);
+    p.prof[phase].events.push_back({e0, e1});
+  }
+};
+
+int run_box(Plan& p, Range r, const BoxPtrs& ptrs, void* stream, int phase) {
   if (r.count <= 0) return SYM_OK;
   p.last_launches++;
-  return cuda_code(launch_box(mode, p.f64(), p.d_items + r.first, r.count, p.d_terms, ptrs, stream), "box kernel");
+  ProfScope ps(p, phase, stream, p.item_bytes_prefix[r.first + r.count] - p.item_bytes_prefix[r.first], 0.0);
+  return cuda_code(launch_box(p.f64(), p.f64(), p.d_items + r.first, r.count, p.d_terms, ptrs, stream),
+                   "box kernel");
 }
 
-int run_gemm(Plan& p, Range r, void* stream) {
+int run_gemm_kind(Plan& p, int kind, Range r, void* stream, int phase) {
   if (r.count <= 0) return SYM_OK;
   p.last_launches++;
-  if (p.f64())
-    return cuda_code(launch_gemm_f64(static_cast<GemmSector64*>(p.d_secs), p.d_tiles + r.first, r.count,
-                                     static_cast<double*>(p.ops0), static_cast<double*>(p.ops0),
-                                     static_cast<double*>(p.outm), stream),
-                     "fp64 gemm");
-  return cuda_code(launch_gemm_tc(static_cast<TcSector*>(p.d_secs), p.d_tiles + r.first, r.count,
-                                  static_cast<uint16_t*>(p.ops0), static_cast<uint16_t*>(p.ops1),
-                                  static_cast<uint16_t*>(p.ops0), static_cast<uint16_t*>(p.ops1),
-                                  static_cast<float*>(p.outm), p.d_err, stream),
-                   "tcgen05 gemm");
+  ProfScope ps(p, phase, stream, 0.0, p.tile_flops_prefix[r.first + r.count] - p.tile_flops_prefix[r.first]);
+  if (kind == 0)
+    return cuda_code(launch_gemm_tc(p.d_secs_tc, p.d_tiles + r.first, r.count, static_cast<uint16_t*>(p.img_hi),
+                                    static_cast<uint16_t*>(p.img_lo), static_cast<uint16_t*>(p.img_hi),
+                                    static_cast<uint16_t*>(p.img_lo), static_cast<float*>(p.outm), p.d_err, stream),
+                     "tcgen05 gemm");
+  return cuda_code(launch_gemm_simt(p.f64(), kind == 1 ? SIMT_64x64 : SIMT_256x16, p.d_secs_simt,
+                                    p.d_tiles + r.first, r.count, p.lin, p.outm, stream),
+                   "cuda-core gemm");
+}
+
+// GEMM phases [ph0, ph1] (contiguous within each kind)
+int run_gemm(Plan& p, int ph0, int ph1, void* stream, int phase) {
+  for (int kind = 0; kind < 3; ++kind) {
+    Range r{p.gemm_range[kind][ph0].first, 0};
+    for (int ph = ph0; ph <= ph1; ++ph) r.count += p.gemm_range[kind][ph].count;
+    int rc = run_gemm_kind(p, kind, r, stream, phase);
+    if (rc) return rc;
+  }
+  return SYM_OK;
+}
+
+BoxPtrs gather_ptrs(Plan& p, const void* A, const void* B, const void* dC) {
+  BoxPtrs g{};
+  g.src[0] = A;
+  g.src[1] = B;
+  g.src[2] = dC;
+  g.src[3] = p.outm;
+  g.dst[DST_IMAGE][0] = p.img_hi;
+  g.dst[DST_IMAGE][1] = p.img_lo;
+  g.dst[DST_OPS][0] = p.lin;
+  g.dst[DST_OUTM][0] = p.outm;
+  return g;
 }
 
 }  // namespace
@@ -1023,27 +1171,22 @@ int exec_transform(Plan& p, const void* in, void* out, void* stream) {
   p.last_launches = 0;
   BoxPtrs ptrs{};
   ptrs.src[0] = in;
-  ptrs.dst[1][0] = out;
-  int mode = p.f64() ? BOX_LINEAR_F64 : BOX_LINEAR_F32;
-  return run_box(p, p.xform, mode, ptrs, stream);
+  ptrs.dst[DST_OUT][0] = out;
+  return run_box(p, p.xform, ptrs, stream, PH_XFORM);
 }
 
 int exec_contract(Plan& p, const void* A, const void* B, void* C, void* stream) {
   if (p.dry) fail(SYM_ERR_UNSUPPORTED, "plan was built with SYM_PLAN_DRYRUN=1 and cannot run");
   p.last_launches = 0;
-  BoxPtrs g{};
-  g.src[0] = A;
-  g.src[1] = B;
-  g.dst[0][0] = p.ops0;
-  g.dst[0][1] = p.ops1;
-  int rc = run_box(p, p.fwd_gather, p.f64() ? BOX_LINEAR_F64 : BOX_IMAGE_BF16X2, g, stream);
+  BoxPtrs g = gather_ptrs(p, A, B, nullptr);
+  int rc = run_box(p, p.fwd_gather, g, stream, PH_FWD_GATHER);
   if (rc) return rc;
-  rc = run_gemm(p, p.fwd_tiles, stream);
+  rc = run_gemm(p, 0, 0, stream, PH_FWD_GEMM);
   if (rc) return rc;
   BoxPtrs s{};
   s.src[3] = p.outm;
-  s.dst[1][0] = C;
-  return run_box(p, p.fwd_scatter, p.f64() ? BOX_LINEAR_F64 : BOX_LINEAR_F32, s, stream);
+  s.dst[DST_OUT][0] = C;
+  return run_box(p, p.fwd_scatter, s, stream, PH_FWD_SCATTER);
 }
 
 int exec_contract_backward(Plan& p, const void* A, const void* B, const void* dC, void* dA, void* dB,
@@ -1051,12 +1194,7 @@ int exec_contract_backward(Plan& p, const void* A, const void* B, const void* dC
   if (p.dry) fail(SYM_ERR_UNSUPPORTED, "plan was built with SYM_PLAN_DRYRUN=1 and cannot run");
   p.last_launches = 0;
   if (!dA && !dB) return SYM_OK;
-  BoxPtrs g{};
-  g.src[0] = A;
-  g.src[1] = B;
-  g.src[2] = dC;
-  g.dst[0][0] = p.ops0;
-  g.dst[0][1] = p.ops1;
+  BoxPtrs g = gather_ptrs(p, A, B, dC);
   Range gr;
   if (dA && dB) {
     int first = std::min(p.bwd_gather_a.first, p.bwd_gather_b.first);
@@ -1065,25 +1203,20 @@ int exec_contract_backward(Plan& p, const void* A, const void* B, const void* dC
   } else {
     gr = dA ? p.bwd_gather_a : p.bwd_gather_b;
   }
-  int rc = run_box(p, gr, p.f64() ? BOX_LINEAR_F64 : BOX_IMAGE_BF16X2, g, stream);
+  int rc = run_box(p, gr, g, stream, PH_BWD_GATHER);
   if (rc) return rc;
-  Range tr;
-  if (dA && dB)
-    tr = {p.bwd_tiles_a.first, p.bwd_tiles_a.count + p.bwd_tiles_b.count};
-  else
-    tr = dA ? p.bwd_tiles_a : p.bwd_tiles_b;
-  rc = run_gemm(p, tr, stream);
+  rc = run_gemm(p, dA ? 1 : 2, dB ? 2 : 1, stream, PH_BWD_GEMM);
   if (rc) return rc;
   BoxPtrs s{};
   s.src[3] = p.outm;
-  s.dst[2][0] = dA;
-  s.dst[3][0] = dB;
+  s.dst[DST_DA][0] = dA;
+  s.dst[DST_DB][0] = dB;
   Range sr;
   if (dA && dB)
     sr = {p.bwd_scatter_a.first, p.bwd_scatter_a.count + p.bwd_scatter_b.count};
   else
     sr = dA ? p.bwd_scatter_a : p.bwd_scatter_b;
-  return run_box(p, sr, p.f64() ? BOX_LINEAR_F64 : BOX_LINEAR_F32, s, stream);
+  return run_box(p, sr, s, stream, PH_BWD_SCATTER);
 }
 
 }  // namespace sym

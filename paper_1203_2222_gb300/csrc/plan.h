@@ -20,6 +20,16 @@ struct DeviceArena {
   ~DeviceArena();
 };
 
+// Phases of a plan's launches (profiling and statistics).
+enum Phase { PH_FWD_GATHER = 0, PH_FWD_GEMM, PH_FWD_SCATTER, PH_BWD_GATHER, PH_BWD_GEMM, PH_BWD_SCATTER,
+             PH_XFORM, PH_COUNT };
+
+struct PhaseProfile {
+  std::vector<std::pair<void*, void*>> events;  // cudaEvent_t pairs around each launch
+  int launches = 0;
+  double bytes = 0.0, flops = 0.0;  // algorithmic, summed over the recorded launches
+};
+
 struct Plan {
   enum Kind { TRANSFORM = 1, CONTRACT = 2 };
   int kind = 0;
@@ -34,14 +44,16 @@ struct Plan {
   Range bwd_gather_a, bwd_gather_b;   // backward gathers needed for dA / dB
   Range bwd_scatter_a, bwd_scatter_b;
 
-  // GEMM work lists (one of the two sector kinds is used)
-  std::vector<GemmSector64> secs64;
+  // GEMM work lists.  Kinds: 0 = tcgen05 split-BF16 x3, 1 = CUDA-core 64x64,
+  // 2 = CUDA-core 256x16; GEMM phases: 0 = forward, 1 = dA, 2 = dB.
+  std::vector<GemmSectorSimt> secs_simt;
   std::vector<TcSector> secs_tc;
-  std::vector<GemmTile> tiles;
-  Range fwd_tiles, bwd_tiles_a, bwd_tiles_b;
+  std::vector<GemmTile> tiles;  // grouped by kind, then by GEMM phase
+  Range gemm_range[3][3];       // [kind][gemm phase]
+  std::vector<int> tile_kind;   // kind of every tile (statistics)
 
-  // scratch sizes (elements): operands (bf16 pairs or fp64) and output matrices
-  int64_t ops_elems = 0, outm_elems = 0;
+  // scratch sizes (elements): split-BF16 images, linear operands, output matrices
+  int64_t img_elems = 0, lin_elems = 0, outm_elems = 0;
 
   // statistics
   double flops_fwd = 0.0;
@@ -49,18 +61,29 @@ struct Plan {
   int last_launches = 0;
   bool dry = false;  // built with SYM_PLAN_DRYRUN=1: validated on the host, never uploaded
 
+  // algorithmic bytes of every box item and useful flops of every tile,
+  // as prefix sums (launch statistics for any range in O(1))
+  std::vector<double> item_bytes_prefix, tile_flops_prefix;
+  void set_item_bytes(Range r, int es_src, int es_dst);
+  bool profiling = false;
+  PhaseProfile prof[PH_COUNT];
+  void clear_profile();
+  ~Plan();
+
   // device copies
   DeviceArena arena;
   BoxItem* d_items = nullptr;
   Term* d_terms = nullptr;
-  void* d_secs = nullptr;
+  GemmSectorSimt* d_secs_simt = nullptr;
+  TcSector* d_secs_tc = nullptr;
   GemmTile* d_tiles = nullptr;
-  void* ops0 = nullptr;  // fp64 operands, or bf16 hi images
-  void* ops1 = nullptr;  // bf16 lo images
-  void* outm = nullptr;  // fp32 / fp64 output matrices
+  void* img_hi = nullptr;  // bf16 hi images
+  void* img_lo = nullptr;  // bf16 lo images
+  void* lin = nullptr;     // linear operands (fp32 or fp64)
+  void* outm = nullptr;    // output matrices (fp32 or fp64)
   int* d_err = nullptr;
 
-  void validate(const int64_t* src_elems, const int64_t* dst_elems, bool dst0_image) const;
+  void validate(const int64_t* src_elems, const int64_t* dst_elems) const;
   void upload();
 };
 

@@ -97,6 +97,25 @@ class Plan:
         L.check(L.lib.sym_plan_launches(self._h, _byref(n)))
         return n.value
 
+    def gemm_shapes(self):
+        """(m, n, k, kernel) of every GEMM; kernel 0 = tcgen05, 1 = CUDA cores."""
+        n = ctypes.c_int()
+        L.check(L.lib.sym_plan_gemm_shapes(self._h, _byref(n), None))
+        buf = (ctypes.c_int * max(4 * n.value, 1))()
+        L.check(L.lib.sym_plan_gemm_shapes(self._h, _byref(n), buf))
+        return [tuple(buf[4 * i:4 * i + 4]) for i in range(n.value)]
+
+    def profile(self, enable=True):
+        """Start (clear) or stop recording device time of this plan's launches."""
+        L.check(L.lib.sym_plan_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self, phase):
+        """{launches, ms, bytes, flops} recorded for one phase (see SYM_PHASE_*)."""
+        n = ctypes.c_int()
+        ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        L.check(L.lib.sym_plan_profile_read(self._h, int(phase), _byref(n), _byref(ms), _byref(by), _byref(fl)))
+        return {"launches": n.value, "ms": ms.value, "bytes": by.value, "flops": fl.value}
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and L is not None and L.lib is not None:
@@ -121,6 +140,15 @@ def _precision(dtype):
 
 
 _PLANS = {}
+
+# phases of a plan's launches (include/symtensor.h, SYM_PHASE_*)
+PHASES = {"fwd_gather": 0, "fwd_gemm": 1, "fwd_scatter": 2, "bwd_gather": 3, "bwd_gemm": 4,
+          "bwd_scatter": 5, "transform": 6}
+
+
+def cached_plans():
+    """Every plan built so far (for profiling and statistics)."""
+    return [v[0] for v in _PLANS.values()]
 
 
 def contract_plan(A, B, pairsA, pairsB, precision=BF16X3, tree_c=None):

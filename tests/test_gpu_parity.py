@@ -83,16 +83,17 @@ def _contract_case(group, la, lb, pa, pb, dtype, QA=0, QB=0, ta=None, tb=None, t
 
 
 DTYPES = [torch.float64, torch.float32]
+DTYPE_IDS = ["float64", "float32"]
 
 
-@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
 def test_u1_pairwise_workload(dtype):
     from paper_1203_2222_gb300 import synthetic
     c = synthetic.u1_pairwise()
     _contract_case("u1", c["A"], c["B"], c["pairsA"], c["pairsB"], dtype)
 
 
-@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
 def test_u1_ragged_multi_tile(dtype):
     # sector matrices spanning several 128-tiles with ragged tails in m, n and k
     qs = [-1, 0, 1]
@@ -101,7 +102,16 @@ def test_u1_ragged_multi_tile(dtype):
     _contract_case("u1", la, lb, [2], [0], dtype, QA=0, QB=0)
 
 
-@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
+def test_u1_long_reduction_split_k(dtype):
+    # thin outputs with reductions of several thousand: split across CTAs
+    qs = [-1, 0, 1]
+    la = [(qs, [5000, 6000, 4500], -1), (qs, [1, 2, 1], 1)]
+    lb = [(qs, [5000, 6000, 4500], 1), (qs, [1, 1, 2], 1)]
+    _contract_case("u1", la, lb, [0], [0], dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
 def test_u1_permuted_pairs_and_charges(dtype):
     qs = [-2, -1, 0, 1, 2]
     la = [(qs, [1, 2, 3, 2, 1], 1), (qs, [2, 1, 2, 1, 2], -1), (qs, [3, 1, 1, 2, 1], 1), (qs, [1, 1, 2, 2, 1], -1)]
@@ -110,7 +120,7 @@ def test_u1_permuted_pairs_and_charges(dtype):
     _contract_case("u1", la, lb, [3, 2], [0, 2], dtype, QA=1, QB=-2)
 
 
-@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
 def test_u1_edge_cases(dtype):
     qs = [0]
     # single sector, 1x1 blocks
@@ -126,7 +136,7 @@ def test_u1_edge_cases(dtype):
 SU2_TREES = [None, [(1, 2), (0, 4), (5, 3)], [(0, 1), (2, 3), (4, 5)]]
 
 
-@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
 @pytest.mark.parametrize("ti", range(len(SU2_TREES)))
 def test_su2_recoupling_contraction(dtype, ti):
     # the recoupling workload at reduced size: 2j <= 4, degeneracies 1..3
@@ -135,7 +145,7 @@ def test_su2_recoupling_contraction(dtype, ti):
     _contract_case("su2", c["A"], c["B"], c["pairsA"], c["pairsB"], dtype, ta=SU2_TREES[ti])
 
 
-@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
 def test_su2_mixed_directions_and_output_tree(dtype):
     sp = [0, 1, 2, 3]
     la = [(sp, [2, 1, 2, 1], -1), (sp, [1, 2, 1, 1], 1), (sp, [2, 2, 1, 1], -1), (sp, [1, 1, 2, 1], 1)]
@@ -145,7 +155,7 @@ def test_su2_mixed_directions_and_output_tree(dtype):
     _contract_case("su2", la, lb, [1, 2], [0, 1], dtype, tree_c=[(1, 2), (0, 3)])
 
 
-@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
 def test_su2_matrix_and_edge_cases(dtype):
     sp = [0, 1, 2, 3]
     m = [(sp, [3, 2, 2, 1], -1), (sp, [3, 2, 2, 1], 1)]
@@ -159,7 +169,7 @@ def test_su2_matrix_and_edge_cases(dtype):
     _contract_case("su2", c3, b, [0, 1], [0, 1], dtype)
 
 
-@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
 def test_su2_large_sectors_multi_tile(dtype):
     # sector matrices of a few hundred rows/cols: several tiles with ragged tails
     sp = [0, 1, 2]
@@ -189,7 +199,7 @@ def _transform_case(group, legs, op, args, dtype, tree=None, seed=5):
     return S, T, out
 
 
-@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
 def test_permute(dtype):
     qs = [-1, 0, 1]
     u = [(qs, [2, 3, 1], 1), (qs, [1, 2, 2], -1), (qs, [3, 1, 2], 1), (qs, [2, 2, 1], -1)]
@@ -201,7 +211,7 @@ def test_permute(dtype):
                     tree=[(1, 2), (0, 4), (5, 3)])
 
 
-@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
 def test_fuse_then_split_roundtrip(dtype):
     P = _lib()
     for group, legs in [
