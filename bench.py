@@ -218,7 +218,7 @@ def run_ours(args, rank, world):
         p.profile(True)
     run_once(data, G)
     torch.cuda.synchronize()
-    launches_per_step = sum(p.profile_read(ph)["launches"] for p in P.cached_plans() for ph in range(7))
+    launches_per_step = sum(p.profile_read(ph)["launches"] for p in P.cached_plans() for ph in P.PHASES.values())
     # live per-kernel timing: the library records events around its own launches.
     # A graph replay cannot record host-side events, so per-kernel timing runs
     # the same kernels eagerly on the same stream for K steps right after.
@@ -255,7 +255,7 @@ def run_ours(args, rank, world):
             r = p.profile_read(ph)
             if r["launches"] == 0:
                 continue
-            kern = "gemm_tc" if "gemm" in name else "box"
+            kern = "gemm_tc" if "gemm_tc" in name else "gemm_cuda_cores" if "gemm" in name else "box"
             d = prof.setdefault(kern, {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
             for k in d:
                 d[k] += r[k]
@@ -338,6 +338,16 @@ def run_ours(args, rank, world):
                 "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "peak_source": f"{peak_src} bf16_tflops_sustained / 3 passes"}
+    elif dom == "gemm_cuda_cores":
+        d = prof[dom]
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        # FP32 CUDA cores: 152 SMs x 128 FMA/clk x 2 flops at the sampled SM clock
+        mhz = (clk.get("sm_mhz") or 2070.0)
+        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": "gemm_simt/gemm_thin (FP32 CUDA cores)",
+                "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x sampled SM clock"}
     elif dom == "box":
         d = prof[dom]
         achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9

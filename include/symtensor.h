@@ -175,12 +175,14 @@ int sym_plan_gemm_shapes(sym_plan plan, int* nsec, int* mnk);
  * summed device time, and their algorithmic bytes (block data read once +
  * destination written once) and useful flops (sum of 2 m n k).           */
 #define SYM_PHASE_FWD_GATHER 0
-#define SYM_PHASE_FWD_GEMM 1
+#define SYM_PHASE_FWD_GEMM 1 /* forward sectors on the tcgen05 GEMM */
 #define SYM_PHASE_FWD_SCATTER 2
 #define SYM_PHASE_BWD_GATHER 3
 #define SYM_PHASE_BWD_GEMM 4
 #define SYM_PHASE_BWD_SCATTER 5
 #define SYM_PHASE_TRANSFORM 6
+#define SYM_PHASE_FWD_GEMM_CUDA_CORES 7 /* forward sectors on the CUDA-core GEMMs */
+#define SYM_PHASE_BWD_GEMM_CUDA_CORES 8
 int sym_plan_profile(sym_plan plan, int enable);
 int sym_plan_profile_read(sym_plan plan, int phase, int* launches,
                           double* total_ms, double* bytes, double* flops);

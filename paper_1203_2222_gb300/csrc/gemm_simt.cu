@@ -3,14 +3,19 @@
 // Blockwise matrix multiply of Ch. 5, Eq. blockmult, T_j = M_j N_j, for
 // every sector j of a contraction in one launch.  It is the whole GEMM of the
 // plain FP64 path and, in the split-BF16 path, the kernel for sectors whose
-// matrices are too thin to fill a 128 x 128 tensor-core tile (tiny k, or
-// n <= 16) -- those are bandwidth-bound and are computed here in FP32.
+// matrices are too thin to fill a 128 x 128 tensor-core tile -- those are
+// bandwidth- or latency-bound and are computed here in FP32.
 //
-// One CTA of 256 threads per output tile (TM x TN, each thread a
-// (TM/16) x (TN/16) register tile), 16-deep k slices staged in shared
-// memory.  A tile may cover only a slice [k0, k1) of the reduction: the
-// planner splits long reductions with few output tiles across CTAs, which
-// then add into a zero-filled C with atomics.
+// Three kernels, chosen per sector by the planner:
+//   tile  TM x TN output tile per 256-thread CTA, 32-deep k slices staged in
+//         shared memory, the next slice prefetched into registers while the
+//         current one is multiplied; a tile may cover a slice [k0, k1) of the
+//         reduction (split-K: slices add into a zero-filled C with atomics).
+//   rows  k, n <= 16: one output row per thread, B held in shared memory --
+//         a streaming kernel (read a row of A, write a row of C).
+//   thin  m, n <= 8 and a long reduction: each thread streams k and keeps
+//         the whole m x n outer-product sum in registers, then the CTA
+//         reduces and adds its slice into C.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -18,13 +23,12 @@
 namespace sym {
 namespace {
 
-constexpr int KS = 16;
-
-template <typename T, int TM, int TN>
-__global__ void __launch_bounds__(256) gemm_simt_kernel(const GemmSectorSimt* __restrict__ secs,
+template <typename T, int TM, int TN, int KS = (TM == 256 && sizeof(T) == 8) ? 16 : 32>
+__global__ void __launch_bounds__(256) gemm_tile_kernel(const GemmSectorSimt* __restrict__ secs,
                                                         const GemmTile* __restrict__ tiles,
                                                         const T* __restrict__ ops, T* __restrict__ outm) {
   constexpr int RM = TM / 16, RN = TN / 16;
+  constexpr int LA = TM * KS / 256, LB = TN * KS / 256;  // slice elements per thread
   __shared__ T As[KS][TM + 1];
   __shared__ T Bs[KS][TN];
   const GemmTile tl = tiles[blockIdx.x];
@@ -36,20 +40,39 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const GemmSectorSimt* __
   for (int i = 0; i < RM; ++i)
 #pragma unroll
     for (int j = 0; j < RN; ++j) acc[i][j] = T(0);
-  const T* a = ops + s.a_off;
-  const T* b = ops + s.b_off;
-  for (int kb = tl.k0; kb < tl.k1; kb += KS) {
-    for (int i = threadIdx.x; i < TM * KS; i += 256) {
+  const T* __restrict__ a = ops + s.a_off;
+  const T* __restrict__ b = ops + s.b_off;
+  T ra[LA], rb[LB];
+  auto load = [&](int kb) {
+#pragma unroll
+    for (int u = 0; u < LA; ++u) {
+      const int i = threadIdx.x + 256 * u;
       const int r = i / KS, c = i % KS;
       const int gr = m0 + r, gc = kb + c;
-      As[c][r] = (gr < s.m && gc < tl.k1) ? a[(int64_t)gr * s.lda + gc] : T(0);
+      ra[u] = (gr < s.m && gc < tl.k1) ? __ldg(a + (int64_t)gr * s.lda + gc) : T(0);
     }
-    for (int i = threadIdx.x; i < TN * KS; i += 256) {
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int i = threadIdx.x + 256 * u;
       const int r = i / TN, c = i % TN;
       const int gr = kb + r, gc = n0 + c;
-      Bs[r][c] = (gr < tl.k1 && gc < s.n) ? b[(int64_t)gr * s.ldb + gc] : T(0);
+      rb[u] = (gr < tl.k1 && gc < s.n) ? __ldg(b + (int64_t)gr * s.ldb + gc) : T(0);
+    }
+  };
+  load(tl.k0);
+  for (int kb = tl.k0; kb < tl.k1; kb += KS) {
+#pragma unroll
+    for (int u = 0; u < LA; ++u) {
+      const int i = threadIdx.x + 256 * u;
+      As[i % KS][i / KS] = ra[u];
+    }
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int i = threadIdx.x + 256 * u;
+      Bs[i / TN][i % TN] = rb[u];
     }
     __syncthreads();
+    if (kb + KS < tl.k1) load(kb + KS);  // next slice in flight during the multiply
 #pragma unroll
     for (int kk = 0; kk < KS; ++kk) {
       T av[RM], bv[RN];
@@ -82,15 +105,111 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const GemmSectorSimt* __
   }
 }
 
+// k, n <= 16: C[r, :] = A[r, :] B, one row per thread, 256 rows per CTA.
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_rows_kernel(const GemmSectorSimt* __restrict__ secs,
+                                                        const GemmTile* __restrict__ tiles,
+                                                        const T* __restrict__ ops, T* __restrict__ outm) {
+  __shared__ T Bs[16][17];
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmSectorSimt s = secs[tl.sector];
+  const T* __restrict__ a = ops + s.a_off;
+  const T* __restrict__ b = ops + s.b_off;
+  for (int i = threadIdx.x; i < s.k * s.n; i += 256) Bs[i / s.n][i % s.n] = __ldg(b + (int64_t)(i / s.n) * s.ldb + i % s.n);
+  __syncthreads();
+  const int r = tl.mt * 256 + threadIdx.x;
+  if (r >= s.m) return;
+  T av[16];
+#pragma unroll
+  for (int kk = 0; kk < 16; ++kk) av[kk] = kk < s.k ? __ldg(a + (int64_t)r * s.lda + kk) : T(0);
+  T* c = outm + s.c_off + (int64_t)r * s.ldc;
+  const T alpha = T(s.alpha);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j >= s.n) break;
+    T acc = T(0);
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk)
+      if (kk < s.k) acc = fma(av[kk], Bs[kk][j], acc);
+    c[j] = alpha * acc;
+  }
+}
+
+// Thin GEMM: m, n <= 8 and a long reduction (e.g. the gradient of a small
+// operator).  Each thread streams k values (coalesced along A's rows and
+// B's short rows) and keeps the whole m x n outer-product sum in registers;
+// the CTA then reduces across its threads and adds its slice into C.
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_thin_kernel(const GemmSectorSimt* __restrict__ secs,
+                                                        const GemmTile* __restrict__ tiles,
+                                                        const T* __restrict__ ops, T* __restrict__ outm) {
+  constexpr int MX = 8, U = 4;
+  __shared__ T red[8][MX * MX];
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmSectorSimt s = secs[tl.sector];
+  const T* __restrict__ a = ops + s.a_off;
+  const T* __restrict__ b = ops + s.b_off;
+  T acc[MX][MX];
+#pragma unroll
+  for (int i = 0; i < MX; ++i)
+#pragma unroll
+    for (int j = 0; j < MX; ++j) acc[i][j] = T(0);
+  for (int k = tl.k0 + threadIdx.x; k < tl.k1; k += 256 * U) {
+    T av[U][MX], bv[U][MX];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int kk = k + 256 * u;
+      const bool ok = kk < tl.k1;
+#pragma unroll
+      for (int i = 0; i < MX; ++i) av[u][i] = (ok && i < s.m) ? __ldg(a + (int64_t)i * s.lda + kk) : T(0);
+#pragma unroll
+      for (int j = 0; j < MX; ++j) bv[u][j] = (ok && j < s.n) ? __ldg(b + (int64_t)kk * s.ldb + j) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int i = 0; i < MX; ++i)
+#pragma unroll
+        for (int j = 0; j < MX; ++j) acc[i][j] = fma(av[u][i], bv[u][j], acc[i][j]);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < MX; ++i)
+#pragma unroll
+    for (int j = 0; j < MX; ++j) {
+      T v = acc[i][j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][i * MX + j] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < MX * MX) {
+    const int i = threadIdx.x / MX, j = threadIdx.x % MX;
+    if (i < s.m && j < s.n) {
+      T v = T(0);
+#pragma unroll
+      for (int w = 0; w < 8; ++w) v += red[w][threadIdx.x];
+      v *= T(s.alpha);
+      T* c = outm + s.c_off + (int64_t)i * s.ldc + j;
+      if (tl.atomic)
+        atomicAdd(c, v);
+      else
+        *c = v;
+    }
+  }
+}
+
 template <typename T>
 int launch_t(int shape, const GemmSectorSimt* secs, const GemmTile* tiles, int ntiles, const void* ops, void* outm,
              cudaStream_t s) {
   const T* o = static_cast<const T*>(ops);
   T* c = static_cast<T*>(outm);
-  if (shape == SIMT_64x64)
-    gemm_simt_kernel<T, 64, 64><<<ntiles, 256, 0, s>>>(secs, tiles, o, c);
-  else
-    gemm_simt_kernel<T, 256, 16><<<ntiles, 256, 0, s>>>(secs, tiles, o, c);
+  switch (shape) {
+    case SIMT_64x64: gemm_tile_kernel<T, 64, 64><<<ntiles, 256, 0, s>>>(secs, tiles, o, c); break;
+    case SIMT_256x16: gemm_tile_kernel<T, 256, 16><<<ntiles, 256, 0, s>>>(secs, tiles, o, c); break;
+    case SIMT_THIN: gemm_thin_kernel<T><<<ntiles, 256, 0, s>>>(secs, tiles, o, c); break;
+    default: gemm_rows_kernel<T><<<ntiles, 256, 0, s>>>(secs, tiles, o, c); break;
+  }
   return (int)cudaGetLastError();
 }
 

@@ -10,6 +10,7 @@ constexpr int kMaxDim = 6;
 // Destination slots of a box launch.
 enum DstSlot { DST_IMAGE = 0, DST_OUT = 1, DST_DA = 2, DST_DB = 3, DST_OPS = 4, DST_OUTM = 5, DST_COUNT = 6 };
 constexpr int kSelImage = 1 << 8;  // BoxItem::sel flag: destination is a split-BF16 image
+constexpr int kSelTile = 1 << 9;   // BoxItem::sel flag: 32 x 32 transposing tile (see box.cu)
 
 // One work unit of the block-movement kernel: a strided box of `dims`
 // (last dim fastest) whose element t is
@@ -21,7 +22,13 @@ constexpr int kSelImage = 1 << 8;  // BoxItem::sel flag: destination is a split-
 // Only elements [start, start + count) of the box (row-major linear index)
 // belong to this unit; the planner guarantees that every destination element
 // is written by exactly one unit.  An item with no terms writes zeros.
+// Tile items (kSelTile) instead cover outer indices [start, start + count)
+// of dims[0..ndim-2) times one 32 x 32 tile (origin p0, q0) of the last two
+// dims, whose last is the source's contiguous one and whose second-to-last is
+// the destination's.
 struct BoxItem {
+  int64_t t0_off, t0_ld;  // first term, inline (no second round trip when nterm == 1)
+  double t0_coef;
   int64_t dst_off;
   int32_t dst_ld;   // linear: multiplier of <t, da>; image: K tiles per row tile
   int32_t row0, col0;
@@ -29,6 +36,7 @@ struct BoxItem {
   int32_t ndim;
   int32_t term0, nterm;
   int32_t start, count;
+  int32_t p0, q0;  // tile items: origin of the 32 x 32 tile in the last two dims
   int32_t dims[kMaxDim];
   int32_t sa[kMaxDim], sb[kMaxDim];
   int32_t da[kMaxDim], db[kMaxDim];
@@ -72,7 +80,7 @@ struct TcSector {
 };
 
 // CUDA-core GEMM tile shapes
-enum SimtShape { SIMT_64x64 = 0, SIMT_256x16 = 1, SIMT_SHAPES = 2 };
+enum SimtShape { SIMT_64x64 = 0, SIMT_256x16 = 1, SIMT_THIN = 2, SIMT_ROWS = 3, SIMT_SHAPES = 4 };
 
 // Launchers (return cudaError_t as int).
 int launch_box(bool src_f64, bool dst_f64, const BoxItem* items, int nitems, const Term* terms,

@@ -41,7 +41,7 @@ namespace sym {
 
 namespace {
 
-constexpr int kChunk = 4096;
+constexpr int kChunk = 2048;  // elements per box work unit (256 threads x 8)
 using TermList = std::vector<std::pair<int64_t, double>>;
 
 struct Box {
@@ -81,33 +81,84 @@ Box simplify(const Box& in) {
   return b;
 }
 
+BoxItem make_item(const Box& box, int64_t dst_off, int dst_ld, int row0, int col0, int sel, int term0,
+                  const std::vector<Term>& terms) {
+  BoxItem it{};
+  it.dst_off = dst_off;
+  it.dst_ld = dst_ld;
+  it.row0 = row0;
+  it.col0 = col0;
+  it.sel = sel;
+  it.ndim = box.ndim;
+  it.term0 = term0;
+  it.nterm = (int)terms.size();
+  if (!terms.empty()) {
+    it.t0_off = terms[0].off;
+    it.t0_ld = terms[0].ld;
+    it.t0_coef = terms[0].coef;
+  }
+  for (int i = 0; i < box.ndim; ++i) {
+    it.dims[i] = box.dims[i];
+    it.sa[i] = box.sa[i];
+    it.sb[i] = box.sb[i];
+    it.da[i] = box.da[i];
+    it.db[i] = box.db[i];
+  }
+  return it;
+}
+
+// Emit the work items of one box.  When the source's contiguous dimension is
+// not the destination's, the box is cut into 32 x 32 transposing tiles over
+// (destination-contiguous dim, source-contiguous dim); otherwise into linear
+// chunks of kChunk elements.
 void emit(Plan& P, const Box& box0, int64_t dst_off, int dst_ld, int row0, int col0, int src_slot, int dst_slot,
           const std::vector<Term>& terms) {
   Box box = simplify(box0);
   int64_t total = 1;
   for (int i = 0; i < box.ndim; ++i) total *= box.dims[i];
   if (total >= (int64_t)1 << 31) fail(SYM_ERR_UNSUPPORTED, "block larger than 2^31 elements");
-  int term0 = (int)P.terms.size();
+  const int term0 = (int)P.terms.size();
   P.terms.insert(P.terms.end(), terms.begin(), terms.end());
+  const int sel = src_slot | (dst_slot << 4);
+  const bool image = (sel & kSelImage) != 0;
+  // transposition check
+  const int64_t ld0 = terms.empty() ? 1 : terms[0].ld;
+  auto src_stride = [&](int d) { return ld0 * box.sa[d] + box.sb[d]; };
+  auto dst_unit = [&](int d) {
+    return image ? (box.db[d] == 1 && box.da[d] == 0) : ((int64_t)dst_ld * box.da[d] + box.db[d] == 1);
+  };
+  const int q = box.ndim - 1;
+  int pdim = -1;
+  if (!terms.empty() && box.ndim >= 2 && src_stride(q) == 1 && !dst_unit(q) && box.dims[q] >= 16) {
+    for (int d = 0; d < q; ++d)
+      if (dst_unit(d) && box.dims[d] >= 16) pdim = d;
+  }
+  if (pdim >= 0) {
+    Box t;
+    for (int d = 0; d < box.ndim; ++d)
+      if (d != pdim && d != q) t.push(box.dims[d], box.sa[d], box.sb[d], box.da[d], box.db[d]);
+    t.push(box.dims[pdim], box.sa[pdim], box.sb[pdim], box.da[pdim], box.db[pdim]);
+    t.push(box.dims[q], box.sa[q], box.sb[q], box.da[q], box.db[q]);
+    int64_t outer = 1;
+    for (int d = 0; d < t.ndim - 2; ++d) outer *= t.dims[d];
+    const int Pd = t.dims[t.ndim - 2], Qd = t.dims[t.ndim - 1];
+    const int64_t per = 4;  // outer indices per item (4 x 1024 elements)
+    for (int tp = 0; tp < Pd; tp += 32)
+      for (int tq = 0; tq < Qd; tq += 32)
+        for (int64_t o = 0; o < outer; o += per) {
+          BoxItem it = make_item(t, dst_off, dst_ld, row0, col0, sel | kSelTile, term0, terms);
+          it.start = (int)o;
+          it.count = (int)std::min<int64_t>(per, outer - o);
+          it.p0 = tp;
+          it.q0 = tq;
+          P.items.push_back(it);
+        }
+    return;
+  }
   for (int64_t st = 0; st < total; st += kChunk) {
-    BoxItem it{};
-    it.dst_off = dst_off;
-    it.dst_ld = dst_ld;
-    it.row0 = row0;
-    it.col0 = col0;
-    it.sel = src_slot | (dst_slot << 4);
-    it.ndim = box.ndim;
-    it.term0 = term0;
-    it.nterm = (int)terms.size();
+    BoxItem it = make_item(box, dst_off, dst_ld, row0, col0, sel, term0, terms);
     it.start = (int)st;
     it.count = (int)std::min<int64_t>(kChunk, total - st);
-    for (int i = 0; i < box.ndim; ++i) {
-      it.dims[i] = box.dims[i];
-      it.sa[i] = box.sa[i];
-      it.sb[i] = box.sb[i];
-      it.da[i] = box.da[i];
-      it.db[i] = box.db[i];
-    }
     P.items.push_back(it);
   }
 }
@@ -345,7 +396,15 @@ void Plan::validate(const int64_t* src_elems, const int64_t* dst_elems) const {
       db += (int64_t)(it.dims[d] - 1) * it.db[d];
       total *= it.dims[d];
     }
-    if ((int64_t)it.start + it.count > total) fail(SYM_ERR_ARG, "internal: chunk past its box");
+    if (it.sel & kSelTile) {
+      if (it.ndim < 2) fail(SYM_ERR_ARG, "internal: tile item needs two dims");
+      const int64_t outer = total / ((int64_t)it.dims[it.ndim - 2] * it.dims[it.ndim - 1]);
+      if ((int64_t)it.start + it.count > outer || it.p0 < 0 || it.q0 < 0 || it.p0 >= it.dims[it.ndim - 2] ||
+          it.q0 >= it.dims[it.ndim - 1])
+        fail(SYM_ERR_ARG, "internal: tile past its box");
+    } else if ((int64_t)it.start + it.count > total) {
+      fail(SYM_ERR_ARG, "internal: chunk past its box");
+    }
     const int ss = it.sel & 3, ds = (it.sel >> 4) & 7;
     if (ds >= DST_COUNT) fail(SYM_ERR_ARG, "internal: bad destination slot");
     for (int i = 0; i < it.nterm; ++i) {
@@ -371,7 +430,10 @@ void Plan::set_item_bytes(Range r, int es_src, int es_dst) {
   if (item_bytes_prefix.size() != items.size() + 1) item_bytes_prefix.assign(items.size() + 1, 0.0);
   for (int i = r.first; i < r.first + r.count; ++i) {
     const BoxItem& it = items[i];
-    item_bytes_prefix[i + 1] = (double)it.count * ((it.nterm > 0 ? es_src : 0) + es_dst);
+    double elems = (double)it.count;
+    if (it.sel & kSelTile)
+      elems *= (double)std::min(32, it.dims[it.ndim - 2] - it.p0) * std::min(32, it.dims[it.ndim - 1] - it.q0);
+    item_bytes_prefix[i + 1] = elems * ((it.nterm > 0 ? es_src : 0) + es_dst);
   }
 }
 
@@ -402,8 +464,9 @@ void Plan::upload() {
     } else {
       m = secs_simt[t.sector].m;
       n = secs_simt[t.sector].n;
-      TM = tile_kind[i] == 1 ? 64 : 256;
-      TN = tile_kind[i] == 1 ? 64 : 16;
+      const int kd = tile_kind[i];
+      TM = kd == 1 ? 64 : kd == 2 ? 256 : kd == 3 ? 8 : 256;
+      TN = kd == 1 ? 64 : kd == 2 ? 16 : kd == 3 ? 8 : 16;
     }
     const int64_t r = std::min<int64_t>(TM, m - t.mt * TM), c = std::min<int64_t>(TN, n - t.nt * TN);
     tile_flops_prefix[i + 1] = tile_flops_prefix[i] + 2.0 * (double)r * (double)c * (double)(t.k1 - t.k0);
@@ -654,6 +717,8 @@ int env_int(const char* name, int dflt) {
 }
 
 int choose_kind(bool f64, int64_t m, int64_t n, int64_t k) {
+  if (m <= 8 && n <= 8) return 3;
+  if (k <= 16 && n <= 16) return 4;
   const int simt = n <= 16 ? 2 : 1;
   if (f64) return simt;
   static const int min_mn = env_int("SYM_TC_MIN_MN", 96);
@@ -805,7 +870,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   P->numel_c = C.numel();
 
   // ---- GEMM sectors and tiles: lists per (kind, gemm phase)
-  std::vector<std::pair<int64_t, GemmTile>> lists[3][3];
+  std::vector<std::pair<int64_t, GemmTile>> lists[kGemmKinds][3];
   const int nsm = 152;
   auto add_gemm = [&](int kind, int ph, int64_t m, int64_t n, int64_t k, int64_t aoff, int64_t lda, int64_t boff,
                       int64_t ldb, int64_t coff) -> bool {
@@ -819,11 +884,24 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     }
     P->secs_simt.push_back(GemmSectorSimt{(int)m, (int)n, (int)k, (int)lda, (int)ldb, (int)n, aoff, boff, coff, 1.0});
     const int sec = (int)P->secs_simt.size() - 1;
+    if (kind == 4) {  // rows: 256 output rows per CTA, whole (short) reduction
+      for (int64_t mt = 0; mt < cdiv(m, 256); ++mt)
+        lists[4][ph].push_back({k, GemmTile{sec, (int)mt, 0, 0, (int)k, 0}});
+      return false;
+    }
+    if (kind == 3) {  // thin: one CTA per 4096-long slice of the reduction
+      const int64_t kc = 4096, nsplit = cdiv(k, kc);
+      for (int64_t sp = 0; sp < nsplit; ++sp) {
+        const int64_t k0 = sp * kc, k1 = std::min(k, k0 + kc);
+        lists[3][ph].push_back({k1 - k0, GemmTile{sec, 0, 0, (int)k0, (int)k1, nsplit > 1 ? 1 : 0}});
+      }
+      return nsplit > 1;
+    }
     const int64_t TM = kind == 1 ? 64 : 256, TN = kind == 1 ? 64 : 16;
     const int64_t ntl = cdiv(m, TM) * cdiv(n, TN);
     int64_t nsplit = 1;
-    if (k > 4096 && ntl < 2 * nsm) nsplit = std::min<int64_t>(cdiv(k, 2048), cdiv(4 * nsm, ntl));
-    const int64_t kc = cdiv(cdiv(k, nsplit), 16) * 16;
+    if (k >= 256 && ntl < 2 * nsm) nsplit = std::min<int64_t>(cdiv(k, 128), cdiv(2 * nsm, ntl));
+    const int64_t kc = cdiv(cdiv(k, nsplit), 32) * 32;
     nsplit = cdiv(k, kc);
     for (int64_t mt = 0; mt < cdiv(m, TM); ++mt)
       for (int64_t nt = 0; nt < cdiv(n, TN); ++nt)
@@ -838,7 +916,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     g.split[1] = add_gemm(g.kind[1], 1, g.m, g.k, g.n, g.kind[1] == 0 ? g.dc1 : g.dcl, g.n, g.bt, g.k, g.da);
     g.split[2] = add_gemm(g.kind[2], 2, g.k, g.n, g.m, g.at, g.m, g.kind[2] == 0 ? g.dc2 : g.dcl, g.n, g.db);
   }
-  for (int kind = 0; kind < 3; ++kind)
+  for (int kind = 0; kind < kGemmKinds; ++kind)
     for (int ph = 0; ph < 3; ++ph) {
       auto& v = lists[kind][ph];
       std::stable_sort(v.begin(), v.end(), [](auto& a, auto& b) { return a.first > b.first; });
@@ -1129,20 +1207,22 @@ int run_box(Plan& p, Range r, const BoxPtrs& ptrs, void* stream, int phase) {
 int run_gemm_kind(Plan& p, int kind, Range r, void* stream, int phase) {
   if (r.count <= 0) return SYM_OK;
   p.last_launches++;
+  if (kind != 0) phase = phase == PH_FWD_GEMM ? PH_FWD_GEMM_SIMT : PH_BWD_GEMM_SIMT;
   ProfScope ps(p, phase, stream, 0.0, p.tile_flops_prefix[r.first + r.count] - p.tile_flops_prefix[r.first]);
   if (kind == 0)
     return cuda_code(launch_gemm_tc(p.d_secs_tc, p.d_tiles + r.first, r.count, static_cast<uint16_t*>(p.img_hi),
                                     static_cast<uint16_t*>(p.img_lo), static_cast<uint16_t*>(p.img_hi),
                                     static_cast<uint16_t*>(p.img_lo), static_cast<float*>(p.outm), p.d_err, stream),
                      "tcgen05 gemm");
-  return cuda_code(launch_gemm_simt(p.f64(), kind == 1 ? SIMT_64x64 : SIMT_256x16, p.d_secs_simt,
+  const int shape = kind == 1 ? SIMT_64x64 : kind == 2 ? SIMT_256x16 : kind == 3 ? SIMT_THIN : SIMT_ROWS;
+  return cuda_code(launch_gemm_simt(p.f64(), shape, p.d_secs_simt,
                                     p.d_tiles + r.first, r.count, p.lin, p.outm, stream),
                    "cuda-core gemm");
 }
 
 // GEMM phases [ph0, ph1] (contiguous within each kind)
 int run_gemm(Plan& p, int ph0, int ph1, void* stream, int phase) {
-  for (int kind = 0; kind < 3; ++kind) {
+  for (int kind = 0; kind < kGemmKinds; ++kind) {
     Range r{p.gemm_range[kind][ph0].first, 0};
     for (int ph = ph0; ph <= ph1; ++ph) r.count += p.gemm_range[kind][ph].count;
     int rc = run_gemm_kind(p, kind, r, stream, phase);

@@ -22,7 +22,8 @@ struct DeviceArena {
 
 // Phases of a plan's launches (profiling and statistics).
 enum Phase { PH_FWD_GATHER = 0, PH_FWD_GEMM, PH_FWD_SCATTER, PH_BWD_GATHER, PH_BWD_GEMM, PH_BWD_SCATTER,
-             PH_XFORM, PH_COUNT };
+             PH_XFORM, PH_FWD_GEMM_SIMT, PH_BWD_GEMM_SIMT, PH_COUNT };
+constexpr int kGemmKinds = 5;  // 0 tcgen05, CUDA cores: 1 tile 64x64, 2 tile 256x16, 3 thin, 4 rows
 
 struct PhaseProfile {
   std::vector<std::pair<void*, void*>> events;  // cudaEvent_t pairs around each launch
@@ -45,11 +46,13 @@ struct Plan {
   Range bwd_scatter_a, bwd_scatter_b;
 
   // GEMM work lists.  Kinds: 0 = tcgen05 split-BF16 x3, 1 = CUDA-core 64x64,
-  // 2 = CUDA-core 256x16; GEMM phases: 0 = forward, 1 = dA, 2 = dB.
+  // 2 = CUDA-core 256x16, 3 = CUDA-core thin (m, n <= 8), 4 = CUDA-core
+  // rows (k, n <= 16); GEMM phases:
+  // 0 = forward, 1 = dA, 2 = dB.
   std::vector<GemmSectorSimt> secs_simt;
   std::vector<TcSector> secs_tc;
   std::vector<GemmTile> tiles;  // grouped by kind, then by GEMM phase
-  Range gemm_range[3][3];       // [kind][gemm phase]
+  Range gemm_range[kGemmKinds][3];  // [kind][gemm phase]
   std::vector<int> tile_kind;   // kind of every tile (statistics)
 
   // scratch sizes (elements): split-BF16 images, linear operands, output matrices
