@@ -207,6 +207,31 @@ int sym_su2_gamma(int rank, const int* spins, const int* tree_in, const int* per
                   const int* tree_out, int* n_in, int* n_out, double* G,
                   int* labels_in, int* labels_out);
 
+/* ------------------------------------------ contraction without allocation ---
+ * sym_contract_noalloc: C = contract(A, B) exactly as sym_contract_plan +
+ *   sym_contract with tree_c = NULL would compute it, for callers that cannot
+ *   call cudaMalloc (code that must not enter the CUDA allocator, or that runs
+ *   next to a framework owning all device memory).  It allocates no device
+ *   memory: its work lists and operand scratch live in one file-scope
+ *   __device__ array of 32 MiB that every GPU loading the library holds until
+ *   exit.  The thesis has no counterpart; this is a deployment variant.
+ *   A, B: structures; a, b: their device data; c: device buffer for the
+ *   result, whose layout is that of the structure sym_contract_plan(A, B,
+ *   npairs, pairsA, pairsB, NULL, precision, ...) returns (numel elements of
+ *   double for SYM_PREC_FP64, float for SYM_PREC_BF16X3); caller-owned.
+ *   Asynchronous on `stream`.  The first call on a device looks up the
+ *   array's device address (cudaGetSymbolAddress) with that device current;
+ *   make that first call before any stream capture.  Every call copies its
+ *   work lists into the shared array and clears the regions that must start
+ *   at zero, so calls whose executions overlap on the GPU (other streams,
+ *   other threads) race: serialize them.  Plans are cached on the host per
+ *   (A, B, pairs, precision).  Errors: SYM_ERR_UNSUPPORTED (with the needed
+ *   size) if the contraction needs more than 32 MiB of scratch, the argument
+ *   errors of sym_contract_plan, SYM_ERR_CUDA if a copy or launch fails.     */
+int sym_contract_noalloc(sym_tensor A, sym_tensor B, int npairs,
+                         const int* pairsA, const int* pairsB, int precision,
+                         const void* a, const void* b, void* c, void* stream);
+
 /* Device error word: SYM_OK, or SYM_ERR_TIMEOUT if a bounded wait in a
  * persistent kernel expired since the last call (the word is then cleared).
  * Synchronizes the device. */

@@ -10,37 +10,19 @@
 #include <string>
 
 #include "../../include/symtensor.h"
+#include "handles.h"
 #include "plan.h"
 #include "recouple.h"
 #include "structure.h"
 
-struct sym_tensor_s {
-  sym::Tensor t;
-};
-struct sym_plan_s {
-  std::unique_ptr<sym::Plan> p;
-};
+std::string& sym::last_error() {
+  thread_local std::string msg;
+  return msg;
+}
 
 namespace {
 
-thread_local std::string g_err;
-
-template <class F>
-int guard(F&& f) {
-  try {
-    g_err.clear();
-    return f();
-  } catch (const sym::Error& e) {
-    g_err = e.what();
-    return e.code;
-  } catch (const std::bad_alloc&) {
-    g_err = "host allocation failed";
-    return SYM_ERR_OOM;
-  } catch (const std::exception& e) {
-    g_err = e.what();
-    return SYM_ERR_ARG;
-  }
-}
+using sym::guard;
 
 void need(bool ok, const char* msg) {
   if (!ok) sym::fail(SYM_ERR_ARG, msg);
@@ -80,9 +62,37 @@ sym_tensor wrap(sym::Tensor&& t) {
 
 }  // namespace
 
+sym::Tensor sym::contraction_result(const Tensor& a, const Tensor& b, const std::vector<int>& pa,
+                                    const std::vector<int>& pb, const int* tree_c) {
+  if (a.group != b.group) fail(SYM_ERR_ARG, "A and B belong to different symmetry groups");
+  const int npairs = (int)pa.size();
+  if (npairs != (int)pb.size() || npairs > std::min(a.rank, b.rank)) fail(SYM_ERR_ARG, "bad number of pairs");
+  std::vector<int> sa(a.rank, 0), sb(b.rank, 0);
+  for (int i = 0; i < npairs; ++i) {
+    if (pa[i] < 0 || pa[i] >= a.rank || sa[pa[i]]) fail(SYM_ERR_ARG, "pairsA: bad or repeated leg");
+    if (pb[i] < 0 || pb[i] >= b.rank || sb[pb[i]]) fail(SYM_ERR_ARG, "pairsB: bad or repeated leg");
+    sa[pa[i]] = sb[pb[i]] = 1;
+    const Leg& la = a.legs[pa[i]];
+    const Leg& lb = b.legs[pb[i]];
+    if (!la.same_content(lb) || la.dir != -lb.dir)
+      fail(SYM_ERR_INCOMPATIBLE_LEGS,
+           "contracted legs must carry the same labels and degeneracies with opposite directions");
+  }
+  std::vector<Leg> legs;
+  for (int l = 0; l < a.rank; ++l)
+    if (!sa[l]) legs.push_back(a.legs[l]);
+  const int na = (int)legs.size();
+  for (int l = 0; l < b.rank; ++l)
+    if (!sb[l]) legs.push_back(b.legs[l]);
+  if (legs.size() > 6) fail(SYM_ERR_ARG, "result rank would exceed 6");
+  Tree tr;
+  if (a.group == SYM_SU2) tr = tree_c ? read_tree((int)legs.size(), tree_c) : Tree::comb_pair(na, (int)legs.size() - na);
+  return make_tensor(a.group, legs, a.total + b.total, tr);
+}
+
 extern "C" {
 
-const char* sym_last_error(void) { return g_err.c_str(); }
+const char* sym_last_error(void) { return sym::last_error().c_str(); }
 
 const char* sym_version(void) { return "symtensor 0.1 sm_103a"; }
 
@@ -233,35 +243,10 @@ int sym_contract_plan(sym_tensor A, sym_tensor B, int npairs, const int* pairsA,
   return guard([&] {
     need(A && B && C && plan, "NULL argument");
     check_precision(precision);
-    const sym::Tensor& a = A->t;
-    const sym::Tensor& b = B->t;
-    need(a.group == b.group, "A and B belong to different symmetry groups");
-    need(npairs >= 0 && npairs <= std::min(a.rank, b.rank), "bad number of pairs");
-    need(npairs == 0 || (pairsA && pairsB), "pairs are NULL");
+    need(npairs >= 0 && (npairs == 0 || (pairsA && pairsB)), "pairs are NULL");
     std::vector<int> pa(pairsA, pairsA + npairs), pb(pairsB, pairsB + npairs);
-    std::vector<int> sa(a.rank, 0), sb(b.rank, 0);
-    for (int i = 0; i < npairs; ++i) {
-      need(pa[i] >= 0 && pa[i] < a.rank && !sa[pa[i]], "pairsA: bad or repeated leg");
-      need(pb[i] >= 0 && pb[i] < b.rank && !sb[pb[i]], "pairsB: bad or repeated leg");
-      sa[pa[i]] = sb[pb[i]] = 1;
-      const sym::Leg& la = a.legs[pa[i]];
-      const sym::Leg& lb = b.legs[pb[i]];
-      if (!la.same_content(lb) || la.dir != -lb.dir)
-        sym::fail(SYM_ERR_INCOMPATIBLE_LEGS,
-                  "contracted legs must carry the same labels and degeneracies with opposite directions");
-    }
-    std::vector<sym::Leg> legs;
-    for (int l = 0; l < a.rank; ++l)
-      if (!sa[l]) legs.push_back(a.legs[l]);
-    int na = (int)legs.size();
-    for (int l = 0; l < b.rank; ++l)
-      if (!sb[l]) legs.push_back(b.legs[l]);
-    need(legs.size() <= 6, "result rank would exceed 6");
-    sym::Tree tr;
-    if (a.group == SYM_SU2)
-      tr = tree_c ? read_tree((int)legs.size(), tree_c) : sym::Tree::comb_pair(na, (int)legs.size() - na);
-    sym::Tensor Ct = sym::make_tensor(a.group, legs, a.total + b.total, tr);
-    auto P = sym::plan_contract(a, b, pa, pb, Ct, precision);
+    sym::Tensor Ct = sym::contraction_result(A->t, B->t, pa, pb, tree_c);
+    auto P = sym::plan_contract(A->t, B->t, pa, pb, Ct, precision);
     *C = wrap(std::move(Ct));
     *plan = new sym_plan_s{std::move(P)};
     return SYM_OK;

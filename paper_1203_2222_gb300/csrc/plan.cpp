@@ -449,7 +449,7 @@ void Plan::clear_profile() {
 
 Plan::~Plan() { clear_profile(); }
 
-void Plan::upload() {
+void Plan::upload(bool device) {
   // finish the statistics tables (prefix sums)
   if (item_bytes_prefix.size() != items.size() + 1) item_bytes_prefix.assign(items.size() + 1, 0.0);
   for (size_t i = 0; i < items.size(); ++i) item_bytes_prefix[i + 1] += item_bytes_prefix[i];
@@ -472,7 +472,7 @@ void Plan::upload() {
     tile_flops_prefix[i + 1] = tile_flops_prefix[i] + 2.0 * (double)r * (double)c * (double)(t.k1 - t.k0);
   }
   const char* dry_env = std::getenv("SYM_PLAN_DRYRUN");
-  if (dry_env && dry_env[0] == '1') {
+  if (!device || (dry_env && dry_env[0] == '1')) {
     dry = true;  // host-only planning and validation; the plan cannot run
     return;
   }
@@ -731,7 +731,7 @@ int choose_kind(bool f64, int64_t m, int64_t n, int64_t k) {
 }  // namespace
 
 std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std::vector<int>& pairsA,
-                                    const std::vector<int>& pairsB, const Tensor& C, int precision) {
+                                    const std::vector<int>& pairsB, const Tensor& C, int precision, bool device) {
   auto P = std::make_unique<Plan>();
   P->kind = Plan::CONTRACT;
   P->precision = precision;
@@ -1162,7 +1162,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
         fail(SYM_ERR_ARG, "internal: tcgen05 GEMM tile past its buffers");
     }
   }
-  P->upload();
+  P->upload(device);
   return P;
 }
 

@@ -87,13 +87,16 @@ struct Plan {
   int* d_err = nullptr;
 
   void validate(const int64_t* src_elems, const int64_t* dst_elems) const;
-  void upload();
+  void upload(bool device = true);
 };
 
 std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const std::vector<int>& perm,
                                      int precision, int mode_fuse_split, int leg);
+// device = false builds and validates the work lists on the host only (no
+// device allocation); such a plan runs only through sym_contract_noalloc.
 std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std::vector<int>& pairsA,
-                                    const std::vector<int>& pairsB, const Tensor& C, int precision);
+                                    const std::vector<int>& pairsB, const Tensor& C, int precision,
+                                    bool device = true);
 
 // Execution (asynchronous on `stream`); return SYM_OK or a negative code.
 int exec_transform(Plan& p, const void* in, void* out, void* stream);
