@@ -182,11 +182,15 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream()
 
     use_graph = not args.no_graph
-    graph = None
+    graph = graph_prof = None
     static_out = None
     for _ in range(max(args.warmup, 1)):
         run_once(data, G)
     torch.cuda.synchronize()
+    plans = P.cached_plans()
+    # The library records a CUDA event pair around each of its own launches
+    # (on the launch stream).  Captured into the graph, every replay re-records
+    # them with the kernels' own device times.
     if use_graph:
         try:
             s = torch.cuda.Stream()
@@ -199,31 +203,38 @@ def run_ours(args, rank, world):
             graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(graph):
                 static_out = run_once(data, G)
+            # a second graph of the same step with the library's event pairs
+            # captured around every launch, for the per-kernel timing pass
+            for p in plans:
+                p.profile(True)
+            graph_prof = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph_prof):
+                run_once(data, G)
+            for p in plans:
+                p.profile(False)  # keep the captured events, record no more
             torch.cuda.synchronize()
             for _ in range(2):
                 graph.replay()
+                graph_prof.replay()
             torch.cuda.synchronize()
         except Exception as e:  # capture unsupported: fall back to eager launches
             print(f"# graph capture failed ({e}); timing eager launches", file=sys.stderr)
             graph = None
+    if graph is None:
+        for p in plans:
+            p.profile(True)
+        run_once(data, G)
+        torch.cuda.synchronize()
+    launches_per_step = sum(p.profile_read(ph)["launches"] for p in plans for ph in P.PHASES.values())
+    if graph is None:
+        for p in plans:
+            p.profile(True)  # eager: record over the timed region itself
 
     def one_step():
         if graph is not None:
             graph.replay()
         else:
             run_once(data, G)
-
-    # launches per step (eager count; a graph replays the same kernels)
-    for p in P.cached_plans():
-        p.profile(True)
-    run_once(data, G)
-    torch.cuda.synchronize()
-    launches_per_step = sum(p.profile_read(ph)["launches"] for p in P.cached_plans() for ph in P.PHASES.values())
-    # live per-kernel timing: the library records events around its own launches.
-    # A graph replay cannot record host-side events, so per-kernel timing runs
-    # the same kernels eagerly on the same stream for K steps right after.
-    for p in P.cached_plans():
-        p.profile(True)
 
     if world > 1:
         torch.distributed.barrier()
@@ -243,23 +254,32 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in evs)
+
+    prof = {}
+
+    def accumulate():
+        for p in plans:
+            for name, ph in P.PHASES.items():
+                r = p.profile_read(ph)
+                if r["launches"] == 0:
+                    continue
+                kern = "gemm_tc" if "gemm_tc" in name else "gemm_cuda_cores" if "gemm" in name else "box"
+                d = prof.setdefault(kern, {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
+                for k in d:
+                    d[k] += r[k]
+
     if graph is not None:
-        # per-kernel event timing of the same kernels, eager, same stream
+        # per-kernel device times: K replays of the instrumented graph, each
+        # read back from the event pairs captured around every library launch
         for _ in range(args.steps):
             flush.fill_(1.0)
-            run_once(data, G)
-        torch.cuda.synchronize()
-    prof = {}
-    for p in P.cached_plans():
-        for name, ph in P.PHASES.items():
-            r = p.profile_read(ph)
-            if r["launches"] == 0:
-                continue
-            kern = "gemm_tc" if "gemm_tc" in name else "gemm_cuda_cores" if "gemm" in name else "box"
-            d = prof.setdefault(kern, {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
-            for k in d:
-                d[k] += r[k]
-        p.profile(False)
+            graph_prof.replay()
+            torch.cuda.synchronize()
+            accumulate()
+    else:
+        accumulate()
+        for p in plans:
+            p.profile(False)
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)

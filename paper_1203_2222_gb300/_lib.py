@@ -7,7 +7,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libsymtensor.so")
+# SYMTENSOR_LIB selects another build of the same library (e.g. an
+# instrumented one); the default is the in-tree build.
+LIB_PATH = os.environ.get("SYMTENSOR_LIB") or os.path.join(HERE, "_build", "libsymtensor.so")
 
 SYM_OK = 0
 SYM_ERR_ARG = -1

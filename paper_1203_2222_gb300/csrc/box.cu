@@ -3,15 +3,24 @@
 // being a short sum of coefficient x source element (one term for U(1) and
 // for pure re-indexing; the recoupling sum of Ch. 6, Eq. permsu2, for SU(2)).
 //
-// One CTA of 256 threads handles one BoxItem: a chunk of at most 2048
-// elements of one box, 8 per thread.  Every thread first computes the offsets
-// of its 8 elements (index decomposition by reciprocal multiplication) and
-// issues all their loads, then stores them, so a CTA needs a single memory
-// round trip after reading its descriptor; the first term of the sum is
-// carried in the descriptor itself.  Consecutive threads take consecutive
-// elements of the box, whose last dimension the planner makes the source's
-// fastest one (coalesced reads).  Memory-bound: bytes = source read +
-// destination written.
+// The kernel is persistent and its warps are independent: warp g of the grid
+// takes items g, g + W, g + 2W, ... (W warps in all), keeps the current
+// descriptor in its own slice of shared memory, fetches the next one into
+// registers while it works, and never waits on the rest of its CTA.
+//  - A linear item is at most 512 elements of one box, 16 per lane; lane l
+//    takes elements start + l + 32u, so consecutive lanes read consecutive
+//    source elements (the planner makes the box's last dim the source's
+//    fastest).  The multi-index of an element is split off by multiply-high
+//    division (magic numbers from the planner) in registers, with the number
+//    of dims a template parameter; all 16 loads are issued before any store.
+//  - A flat item (one term, linear destination, 32-bit spans) addresses both
+//    sides with a single dot product each; the general form (recoupling sums,
+//    split-BF16 operand images) keeps the two-part source and destination
+//    offsets.
+//  - A tile item is one 32 x 32 tile of the box's last two dims at one outer
+//    index: the warp reads it along the source-contiguous dim into its own
+//    shared-memory tile and writes it along the destination-contiguous dim.
+// Memory-bound: bytes = source read + destination written.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -20,193 +29,330 @@
 namespace sym {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kBatch = 8;
-constexpr int kMaxSmemTerms = 64;
-constexpr int kItemWords = (int)(sizeof(BoxItem) / 4);
+constexpr int kThreads = 128;
+constexpr int kWarps = kThreads / 32;
+constexpr int kBatch = kBoxChunk / 32;  // elements per lane of a linear item
+constexpr int kItemWords = (int)(sizeof(BoxItem) / 8);
 static_assert(sizeof(BoxItem) % 8 == 0, "BoxItem must be a whole number of 8-byte words");
+static_assert(kItemWords <= 32, "a warp loads a descriptor with one word per lane");
 
-// floor(a / n) for a >= 0: float reciprocal (off by at most one for
-// a < 2^22, then corrected), exact integer division beyond
-__device__ __forceinline__ int fdiv(int a, int n, float rn) {
-  if (a >= (1 << 22)) return a / n;
-  int q = __float2int_rz(__int2float_rz(a) * rn);
-  const int r = a - q * n;
-  q += (r >= n) - (r < 0);
-  return q;
+__device__ __forceinline__ int div_magic(int a, uint32_t mag, int shf) {
+  return (int)(__umulhi((uint32_t)a << 1, mag) >> shf);
 }
 
-template <typename TD>
-__device__ __forceinline__ void store_elem(const BoxItem& it, void* dst0, void* dst1, bool image, TD v, int da,
-                                           int db) {
-  if (!image) {
-    static_cast<TD*>(dst0)[it.dst_off + (int64_t)it.dst_ld * da + db] = v;
-  } else {
-    // split-BF16: hi = bf16(v), lo = bf16(v - hi); tiled, 128B-swizzled image
-    const float x = (float)v;
-    const int row = it.row0 + da;
-    const int col = it.col0 + db;
-    const int64_t off = it.dst_off + ((int64_t)(row >> 7) * it.dst_ld + (col >> 6)) * 8192 + (row & 127) * 64 +
-                        ((((col >> 3) & 7) ^ (row & 7)) << 3) + (col & 7);
-    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-    static_cast<__nv_bfloat16*>(dst0)[off] = hi;
-    static_cast<__nv_bfloat16*>(dst1)[off] = lo;
-  }
-}
-
-template <typename TS, typename TD>
-__device__ __forceinline__ TD load_elem(const BoxItem& it, const Term* __restrict__ terms, const int64_t* toff,
-                                        const int64_t* tld, const double* tcoef, const TS* __restrict__ src, int sa,
-                                        int sb) {
-  const int nterm = it.nterm;
-  if (nterm == 1) return TD(it.t0_coef) * TD(__ldg(src + it.t0_off + it.t0_ld * sa + sb));
-  TD acc = TD(0);
-  for (int i = 0; i < nterm; ++i) {
-    int64_t off;
-    double c;
-    if (i < kMaxSmemTerms) {
-      off = toff[i] + tld[i] * sa;
-      c = tcoef[i];
-    } else {
-      const Term t = terms[it.term0 + i];
-      off = t.off + t.ld * sa;
-      c = t.coef;
-    }
-    acc += TD(c) * TD(__ldg(src + off + sb));
-  }
-  return acc;
-}
-
-// Transposing tile: read 32 x 32 elements along the source-contiguous last
-// dim (q), stage them in shared memory, write them along the destination-
-// contiguous dim (p) -- both sides coalesced.
-template <typename TS, typename TD>
-__device__ __noinline__ void tile_path(const BoxItem& it, const float* rcp, const Term* __restrict__ terms,
-                                       const int64_t* toff, const int64_t* tld, const double* tcoef,
-                                       const TS* __restrict__ src, void* dst0, void* dst1, bool image) {
-  __shared__ TD tile[32][33];
-  const int nd = it.ndim;
-  const int P = it.dims[nd - 2], Q = it.dims[nd - 1];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // 8 warps
-  for (int o = it.start; o < it.start + it.count; ++o) {
-    int rem = o, sa = 0, sb = 0, da = 0, db = 0;
+// descriptor fields of an item with ND dims, in registers
+template <int ND>
+struct Shape {
+  int n[ND], shf[ND];
+  uint32_t mag[ND];
+  __device__ __forceinline__ explicit Shape(const BoxItem& it) {
 #pragma unroll
-    for (int d = kMaxDim - 3; d >= 0; --d) {
-      if (d < nd - 2) {
-        const int n = it.dims[d];
-        const int q = fdiv(rem, n, rcp[d]);
-        const int t = rem - q * n;
-        rem = q;
-        sa += t * it.sa[d];
-        sb += t * it.sb[d];
-        da += t * it.da[d];
-        db += t * it.db[d];
+    for (int d = 0; d < ND; ++d) {
+      n[d] = it.dims[d];
+      mag[d] = it.mag[d];
+      shf[d] = it.shf[d];
+    }
+  }
+  // multi-index of linear element e (last dim fastest)
+  __device__ __forceinline__ void split(int e, int (&t)[ND]) const {
+    int rem = e;
+#pragma unroll
+    for (int d = ND - 1; d > 0; --d) {
+      const int q = div_magic(rem, mag[d], shf[d]);
+      t[d] = rem - q * n[d];
+      rem = q;
+    }
+    t[0] = rem;
+  }
+};
+
+template <int ND>
+__device__ __forceinline__ int dot(const int (&t)[ND], const int (&s)[ND]) {
+  int r = 0;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) r += t[d] * s[d];
+  return r;
+}
+
+template <int ND>
+__device__ __forceinline__ void load_strides(const int32_t* src, int (&s)[ND]) {
+#pragma unroll
+  for (int d = 0; d < ND; ++d) s[d] = src[d];
+}
+
+// source side of the general form: sum over terms of coef x src[off + ld * a + b]
+template <typename TS, typename TD>
+struct Src {
+  const TS* __restrict__ p;
+  const Term* __restrict__ terms;
+  int64_t off0, ld0;
+  TD c0;
+  int nterm, term0;
+
+  __device__ __forceinline__ TD load(int a, int b) const {
+    if (nterm == 1) return c0 * TD(__ldg(p + off0 + ld0 * a + b));
+    TD acc = TD(0);
+    for (int i = 0; i < nterm; ++i) {
+      const Term* t = terms + term0 + i;
+      acc += TD(__ldg(&t->coef)) * TD(__ldg(p + __ldg(&t->off) + __ldg(&t->ld) * a + b));
+    }
+    return acc;
+  }
+};
+
+// destination side of the general form: linear, or a split-BF16 operand image
+template <typename TD>
+struct Dst {
+  void* p0;
+  void* p1;
+  int64_t off, ld;
+  int row0, col0;
+  bool image;
+
+  __device__ __forceinline__ void store(TD v, int a, int b) const {
+    if (!image) {
+      static_cast<TD*>(p0)[off + ld * a + b] = v;
+    } else {
+      // split-BF16: hi = bf16(v), lo = bf16(v - hi); tiled, 128B-swizzled image
+      const float x = (float)v;
+      const int row = row0 + a;
+      const int col = col0 + b;
+      const int64_t o = off + ((int64_t)(row >> 7) * ld + (col >> 6)) * 8192 + (row & 127) * 64 +
+                        ((((col >> 3) & 7) ^ (row & 7)) << 3) + (col & 7);
+      const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+      static_cast<__nv_bfloat16*>(p0)[o] = hi;
+      static_cast<__nv_bfloat16*>(p1)[o] = lo;
+    }
+  }
+};
+
+template <int ND, typename TS, typename TD>
+__device__ __forceinline__ void linear_flat(const BoxItem& it, const TS* __restrict__ src, TD* __restrict__ dst,
+                                            int lane) {
+  const Shape<ND> sh(it);
+  int sa[ND], da[ND];
+  load_strides(it.sa, sa);
+  load_strides(it.da, da);
+  const TS* ps = src + it.t0_off;
+  TD* pd = dst + it.dst_off;
+  const bool has_src = it.nterm > 0;
+  const TD c = TD(it.t0_coef);
+  const bool unit = it.t0_coef == 1.0;
+  const int left = it.count - lane;
+  TD v[kBatch];
+  int dof[kBatch];
+#pragma unroll
+  for (int u = 0; u < kBatch; ++u) {
+    v[u] = TD(0);
+    dof[u] = 0;
+    if (32 * u < left) {
+      int t[ND];
+      sh.split(it.start + lane + 32 * u, t);
+      dof[u] = dot(t, da);
+      if (has_src) v[u] = TD(__ldg(ps + dot(t, sa)));
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kBatch; ++u)
+    if (32 * u < left) pd[dof[u]] = unit ? v[u] : c * v[u];
+}
+
+template <int ND, typename TS, typename TD>
+__device__ __forceinline__ void linear_general(const BoxItem& it, const Src<TS, TD>& src, const Dst<TD>& dst,
+                                               int lane) {
+  const Shape<ND> sh(it);
+  const int left = it.count - lane;
+  TD v[kBatch];
+  {
+    int sa[ND], sb[ND];
+    load_strides(it.sa, sa);
+    load_strides(it.sb, sb);
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      v[u] = TD(0);
+      if (32 * u < left) {
+        int t[ND];
+        sh.split(it.start + lane + 32 * u, t);
+        v[u] = src.load(dot(t, sa), dot(t, sb));
       }
     }
-    TD v[4];
+  }
+  int da[ND], db[ND];
+  load_strides(it.da, da);
+  load_strides(it.db, db);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int p = it.p0 + w + 8 * u, q = it.q0 + lane;
-      v[u] = (p < P && q < Q) ? load_elem<TS, TD>(it, terms, toff, tld, tcoef, src,
-                                                  sa + p * it.sa[nd - 2] + q * it.sa[nd - 1],
-                                                  sb + p * it.sb[nd - 2] + q * it.sb[nd - 1])
-                              : TD(0);
+  for (int u = 0; u < kBatch; ++u) {
+    if (32 * u < left) {
+      int t[ND];
+      sh.split(it.start + lane + 32 * u, t);
+      dst.store(v[u], dot(t, da), dot(t, db));
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) tile[w + 8 * u][lane] = v[u];
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int q = it.q0 + w + 8 * u, p = it.p0 + lane;
-      if (p < P && q < Q)
-        store_elem<TD>(it, dst0, dst1, image, tile[lane][w + 8 * u], da + p * it.da[nd - 2] + q * it.da[nd - 1],
-                       db + p * it.db[nd - 2] + q * it.db[nd - 1]);
-    }
-    __syncthreads();
   }
 }
 
-// offsets of element e: rolled loop over the dims (descriptor in shared memory)
-__device__ __forceinline__ void offsets(const BoxItem& it, const float* rcp, int nd, int e, int& sa, int& sb,
-                                        int& da, int& db) {
-  int rem = e;
-  sa = sb = da = db = 0;
+// one 32 x 32 tile (origin p0, q0) of the last two dims at outer index
+// it.start (p: destination-contiguous, q: source-contiguous)
+template <typename TS, typename TD>
+__device__ __forceinline__ void tile_item(const BoxItem& it, const TS* __restrict__ fsrc, TD* __restrict__ fdst,
+                                          const Src<TS, TD>& src, const Dst<TD>& dst, TD (*tile)[33], int lane) {
+  const int nd = it.ndim;
+  const int P = it.dims[nd - 2], Q = it.dims[nd - 1];
+  int rem = it.start, sa = 0, sb = 0, da = 0, db = 0;
 #pragma unroll 1
-  for (int d = nd - 1; d >= 0; --d) {
-    const int n = it.dims[d];
-    const int q = fdiv(rem, n, rcp[d]);
-    const int t = rem - q * n;
+  for (int d = nd - 3; d >= 0; --d) {
+    const int q = d > 0 ? div_magic(rem, it.mag[d], it.shf[d]) : 0;
+    const int t = rem - q * it.dims[d];
     rem = q;
     sa += t * it.sa[d];
     sb += t * it.sb[d];
     da += t * it.da[d];
     db += t * it.db[d];
   }
+  const bool flat = (it.sel & kSelFlat) != 0;
+  const int sap = it.sa[nd - 2], saq = it.sa[nd - 1], sbp = it.sb[nd - 2], sbq = it.sb[nd - 1];
+  const int dap = it.da[nd - 2], daq = it.da[nd - 1], dbp = it.db[nd - 2], dbq = it.db[nd - 1];
+  const int q = it.q0 + lane;
+  const int rows = min(32, P - it.p0);
+  // two halves of 16 rows: 16 loads per lane in flight, half the registers
+#pragma unroll
+  for (int h = 0; h < 32; h += 16) {
+    TD v[16];
+    if (flat) {
+      const TS* ps = fsrc + it.t0_off + sa + q * saq + (it.p0 + h) * sap;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = (h + r < rows && q < Q) ? TD(__ldg(ps + r * sap)) : TD(0);
+    } else {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int p = it.p0 + h + r;
+        v[r] = (h + r < rows && q < Q) ? src.load(sa + p * sap + q * saq, sb + p * sbp + q * sbq) : TD(0);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 16; ++r) tile[h + r][lane] = v[r];
+  }
+  __syncwarp();
+  const int p = it.p0 + lane;
+  const int cols = min(32, Q - it.q0);
+  if (p < P) {
+    if (flat) {
+      const TD c = TD(it.t0_coef);
+      const bool unit = it.t0_coef == 1.0;
+      TD* pd = fdst + it.dst_off + da + p * dap + it.q0 * daq;
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k)
+        if (k < cols) pd[k * daq] = unit ? tile[lane][k] : c * tile[lane][k];
+    } else {
+#pragma unroll 4
+      for (int k = 0; k < 32; ++k) {
+        const int qq = it.q0 + k;
+        if (k < cols) dst.store(tile[lane][k], da + p * dap + qq * daq, db + p * dbp + qq * dbq);
+      }
+    }
+  }
+  __syncwarp();
 }
 
 template <typename TS, typename TD>
-__global__ void __launch_bounds__(kThreads) box_kernel(const BoxItem* __restrict__ items,
-                                                          const Term* __restrict__ terms, const BoxPtrs ptrs) {
-  __shared__ int64_t raw[kItemWords / 2];
-  __shared__ float rcp[kMaxDim];
-  __shared__ int64_t toff[kMaxSmemTerms], tld[kMaxSmemTerms];
-  __shared__ double tcoef[kMaxSmemTerms];
-  const int64_t* g = reinterpret_cast<const int64_t*>(items + blockIdx.x);
-  if (threadIdx.x < kItemWords / 2) raw[threadIdx.x] = g[threadIdx.x];
-  __syncthreads();
-  const BoxItem& it = *reinterpret_cast<const BoxItem*>(raw);
-  const int nterm = it.nterm;
-  if (threadIdx.x < it.ndim) rcp[threadIdx.x] = 1.0f / (float)it.dims[threadIdx.x];
-  if (nterm > 1) {
-    for (int i = threadIdx.x; i < nterm && i < kMaxSmemTerms; i += blockDim.x) {
-      const Term t = terms[it.term0 + i];
-      toff[i] = t.off;
-      tld[i] = t.ld;
-      tcoef[i] = t.coef;
-    }
-  }
-  __syncthreads();
+__device__ __forceinline__ void run_item(const BoxItem& it, const Term* __restrict__ terms, const BoxPtrs& ptrs,
+                                         TD (*tile)[33], int lane) {
   const int sslot = it.sel & 3, dslot = (it.sel >> 4) & 7;
-  const TS* __restrict__ src = static_cast<const TS*>(sslot == 0   ? ptrs.src[0]
-                                                      : sslot == 1 ? ptrs.src[1]
-                                                      : sslot == 2 ? ptrs.src[2]
-                                                                   : ptrs.src[3]);
-  void* dst0;
-  void* dst1 = ptrs.dst[0][1];
+  const TS* sp = static_cast<const TS*>(sslot == 0 ? ptrs.src[0]
+                                        : sslot == 1 ? ptrs.src[1]
+                                        : sslot == 2 ? ptrs.src[2]
+                                                     : ptrs.src[3]);
+  void* dp;
   switch (dslot) {
-    case 0: dst0 = ptrs.dst[0][0]; break;
-    case 1: dst0 = ptrs.dst[1][0]; break;
-    case 2: dst0 = ptrs.dst[2][0]; break;
-    case 3: dst0 = ptrs.dst[3][0]; break;
-    case 4: dst0 = ptrs.dst[4][0]; break;
-    default: dst0 = ptrs.dst[5][0]; break;
+    case 0: dp = ptrs.dst[0][0]; break;
+    case 1: dp = ptrs.dst[1][0]; break;
+    case 2: dp = ptrs.dst[2][0]; break;
+    case 3: dp = ptrs.dst[3][0]; break;
+    case 4: dp = ptrs.dst[4][0]; break;
+    default: dp = ptrs.dst[5][0]; break;
   }
-  const bool image = (it.sel & kSelImage) != 0;
-  const int nd = it.ndim;
+  const bool flat = (it.sel & kSelFlat) != 0;
+  Src<TS, TD> src;
+  src.p = sp;
+  src.terms = terms;
+  src.off0 = it.t0_off;
+  src.ld0 = it.t0_ld;
+  src.c0 = TD(it.t0_coef);
+  src.nterm = it.nterm;
+  src.term0 = it.term0;
+  Dst<TD> dst;
+  dst.p0 = dp;
+  dst.p1 = ptrs.dst[0][1];
+  dst.off = it.dst_off;
+  dst.ld = it.dst_ld;
+  dst.row0 = it.row0;
+  dst.col0 = it.col0;
+  dst.image = (it.sel & kSelImage) != 0;
   if (it.sel & kSelTile) {
-    tile_path<TS, TD>(it, rcp, terms, toff, tld, tcoef, src, dst0, dst1, image);
+    tile_item<TS, TD>(it, sp, static_cast<TD*>(dp), src, dst, tile, lane);
     return;
   }
-  const int e_end = it.start + it.count;
-  TD v[kBatch];
-  int dda[kBatch], ddb[kBatch];
-#pragma unroll
-  for (int u = 0; u < kBatch; ++u) {
-    const int e = it.start + threadIdx.x + kThreads * u;
-    v[u] = TD(0);
-    dda[u] = ddb[u] = 0;
-    if (e < e_end) {
-      int sa, sb;
-      offsets(it, rcp, nd, e, sa, sb, dda[u], ddb[u]);
-      v[u] = load_elem<TS, TD>(it, terms, toff, tld, tcoef, src, sa, sb);
+  if (flat) {
+    TD* d = static_cast<TD*>(dp);
+    switch (it.ndim) {
+      case 1: linear_flat<1, TS, TD>(it, sp, d, lane); break;
+      case 2: linear_flat<2, TS, TD>(it, sp, d, lane); break;
+      case 3: linear_flat<3, TS, TD>(it, sp, d, lane); break;
+      case 4: linear_flat<4, TS, TD>(it, sp, d, lane); break;
+      case 5: linear_flat<5, TS, TD>(it, sp, d, lane); break;
+      default: linear_flat<6, TS, TD>(it, sp, d, lane); break;
+    }
+  } else {
+    switch (it.ndim) {
+      case 1: linear_general<1, TS, TD>(it, src, dst, lane); break;
+      case 2: linear_general<2, TS, TD>(it, src, dst, lane); break;
+      case 3: linear_general<3, TS, TD>(it, src, dst, lane); break;
+      case 4: linear_general<4, TS, TD>(it, src, dst, lane); break;
+      case 5: linear_general<5, TS, TD>(it, src, dst, lane); break;
+      default: linear_general<6, TS, TD>(it, src, dst, lane); break;
     }
   }
-#pragma unroll
-  for (int u = 0; u < kBatch; ++u) {
-    const int e = it.start + threadIdx.x + kThreads * u;
-    if (e < e_end) store_elem<TD>(it, dst0, dst1, image, v[u], dda[u], ddb[u]);
+}
+
+template <typename TS, typename TD>
+__global__ void __launch_bounds__(kThreads) box_kernel(const BoxItem* __restrict__ items, int nitems,
+                                                       const Term* __restrict__ terms, const BoxPtrs ptrs) {
+  __shared__ int64_t raw[kWarps][kItemWords];
+  __shared__ TD tiles[kWarps][32][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nwarps = gridDim.x * kWarps;
+  int item = blockIdx.x * kWarps + w;
+  if (item >= nitems) return;
+  const int64_t* words = reinterpret_cast<const int64_t*>(items);
+  int64_t word = lane < kItemWords ? __ldg(words + (int64_t)item * kItemWords + lane) : 0;
+  const BoxItem& it = *reinterpret_cast<const BoxItem*>(raw[w]);
+  for (; item < nitems; item += nwarps) {
+    if (lane < kItemWords) raw[w][lane] = word;
+    __syncwarp();
+    const int next = item + nwarps;
+    if (lane < kItemWords && next < nitems) word = __ldg(words + (int64_t)next * kItemWords + lane);
+    run_item<TS, TD>(it, terms, ptrs, tiles[w], lane);
+    __syncwarp();
   }
+}
+
+template <typename TS, typename TD>
+int launch_t(const BoxItem* items, int nitems, const Term* terms, const BoxPtrs& ptrs, cudaStream_t s) {
+  static int slots = 0;  // resident warps of this instantiation on the device
+  if (slots == 0) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, box_kernel<TS, TD>, kThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    slots = per_sm * nsm * kWarps;
+  }
+  const int warps = nitems < slots ? nitems : slots;
+  const int grid = (warps + kWarps - 1) / kWarps;
+  box_kernel<TS, TD><<<grid, kThreads, 0, s>>>(items, nitems, terms, ptrs);
+  return (int)cudaGetLastError();
 }
 
 }  // namespace
@@ -215,14 +361,9 @@ int launch_box(bool src_f64, bool dst_f64, const BoxItem* items, int nitems, con
                void* stream) {
   if (nitems <= 0) return 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  dim3 grid(nitems), block(kThreads);
-  if (src_f64 && dst_f64)
-    box_kernel<double, double><<<grid, block, 0, s>>>(items, terms, ptrs);
-  else if (!src_f64 && !dst_f64)
-    box_kernel<float, float><<<grid, block, 0, s>>>(items, terms, ptrs);
-  else
-    return (int)cudaErrorInvalidValue;
-  return (int)cudaGetLastError();
+  if (src_f64 && dst_f64) return launch_t<double, double>(items, nitems, terms, ptrs, s);
+  if (!src_f64 && !dst_f64) return launch_t<float, float>(items, nitems, terms, ptrs, s);
+  return (int)cudaErrorInvalidValue;
 }
 
 }  // namespace sym

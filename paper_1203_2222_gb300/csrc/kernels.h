@@ -11,6 +11,11 @@ constexpr int kMaxDim = 6;
 enum DstSlot { DST_IMAGE = 0, DST_OUT = 1, DST_DA = 2, DST_DB = 3, DST_OPS = 4, DST_OUTM = 5, DST_COUNT = 6 };
 constexpr int kSelImage = 1 << 8;  // BoxItem::sel flag: destination is a split-BF16 image
 constexpr int kSelTile = 1 << 9;   // BoxItem::sel flag: 32 x 32 transposing tile (see box.cu)
+// BoxItem::sel flag: at most one term with t0_ld == 1, linear destination with
+// dst_ld == 1, sb == db == 0, and both <t, sa> and <t, da> below 2^31, so the
+// kernel addresses source and destination with one 32-bit dot product each
+constexpr int kSelFlat = 1 << 10;
+constexpr int kBoxChunk = 512;  // elements of a linear work item (32 lanes x 16)
 
 // One work unit of the block-movement kernel: a strided box of `dims`
 // (last dim fastest) whose element t is
@@ -40,6 +45,12 @@ struct BoxItem {
   int32_t dims[kMaxDim];
   int32_t sa[kMaxDim], sb[kMaxDim];
   int32_t da[kMaxDim], db[kMaxDim];
+  // division by dims[d] without a divide: for 0 <= a < 2^31,
+  // floor(a / dims[d]) = umulhi(2a, mag[d]) >> shf[d] (Granlund & Montgomery,
+  // PLDI 1994, Thm 4.2 with N = 31: shf = ceil(log2 dims), mag = ceil(2^(31+shf) / dims))
+  uint32_t mag[kMaxDim];
+  int8_t shf[kMaxDim];
+  int8_t pad_[2];
 };
 
 struct Term {

@@ -41,7 +41,7 @@ namespace sym {
 
 namespace {
 
-constexpr int kChunk = 2048;  // elements per box work unit (256 threads x 8)
+constexpr int kChunk = kBoxChunk;  // elements of a linear box work item
 using TermList = std::vector<std::pair<int64_t, double>>;
 
 struct Box {
@@ -81,6 +81,16 @@ Box simplify(const Box& in) {
   return b;
 }
 
+// Magic numbers for dividing 31-bit dividends by d >= 1 with one multiply-high
+// (Granlund & Montgomery, PLDI 1994, Thm 4.2 with N = 31):
+// s = ceil(log2 d), m = ceil(2^(31+s) / d) < 2^32, floor(a / d) = (2a * m) >> (32 + s).
+void div_magic(int d, uint32_t& m, int8_t& s) {
+  int l = 0;
+  while (((int64_t)1 << l) < d) ++l;
+  m = (uint32_t)((((uint64_t)1 << (31 + l)) + (uint64_t)d - 1) / (uint64_t)d);
+  s = (int8_t)l;
+}
+
 BoxItem make_item(const Box& box, int64_t dst_off, int dst_ld, int row0, int col0, int sel, int term0,
                   const std::vector<Term>& terms) {
   BoxItem it{};
@@ -103,6 +113,7 @@ BoxItem make_item(const Box& box, int64_t dst_off, int dst_ld, int row0, int col
     it.sb[i] = box.sb[i];
     it.da[i] = box.da[i];
     it.db[i] = box.db[i];
+    div_magic(box.dims[i], it.mag[i], it.shf[i]);
   }
   return it;
 }
@@ -112,15 +123,40 @@ BoxItem make_item(const Box& box, int64_t dst_off, int dst_ld, int row0, int col
 // (destination-contiguous dim, source-contiguous dim); otherwise into linear
 // chunks of kChunk elements.
 void emit(Plan& P, const Box& box0, int64_t dst_off, int dst_ld, int row0, int col0, int src_slot, int dst_slot,
-          const std::vector<Term>& terms) {
-  Box box = simplify(box0);
+          const std::vector<Term>& terms0) {
+  int sel = src_slot | (dst_slot << 4);
+  const bool image = (sel & kSelImage) != 0;
+  // Flat form: with at most one term and a linear destination, fold the
+  // two-part offsets (ld * a + b) into one stride per dim on each side when
+  // every offset of the box stays below 2^31.
+  Box box = box0;
+  std::vector<Term> terms = terms0;
+  if (!image && terms.size() <= 1) {
+    const int64_t ld0 = terms.empty() ? 0 : terms[0].ld;
+    Box f;
+    int64_t sspan = 0, dspan = 0;
+    bool ok = true;
+    for (int d = 0; d < box0.ndim; ++d) {
+      const int64_t s = terms.empty() ? 0 : ld0 * box0.sa[d] + box0.sb[d];
+      const int64_t t = (int64_t)dst_ld * box0.da[d] + box0.db[d];
+      if (s < 0 || t < 0 || s >= ((int64_t)1 << 31) || t >= ((int64_t)1 << 31)) ok = false;
+      sspan += (int64_t)(box0.dims[d] - 1) * s;
+      dspan += (int64_t)(box0.dims[d] - 1) * t;
+      f.push(box0.dims[d], (int)s, 0, (int)t, 0);
+    }
+    if (ok && sspan < ((int64_t)1 << 31) && dspan < ((int64_t)1 << 31)) {
+      box = f;
+      dst_ld = 1;
+      if (!terms.empty()) terms[0].ld = 1;
+      sel |= kSelFlat;
+    }
+  }
+  box = simplify(box);
   int64_t total = 1;
   for (int i = 0; i < box.ndim; ++i) total *= box.dims[i];
   if (total >= (int64_t)1 << 31) fail(SYM_ERR_UNSUPPORTED, "block larger than 2^31 elements");
   const int term0 = (int)P.terms.size();
   P.terms.insert(P.terms.end(), terms.begin(), terms.end());
-  const int sel = src_slot | (dst_slot << 4);
-  const bool image = (sel & kSelImage) != 0;
   // transposition check
   const int64_t ld0 = terms.empty() ? 1 : terms[0].ld;
   auto src_stride = [&](int d) { return ld0 * box.sa[d] + box.sb[d]; };
@@ -142,7 +178,7 @@ void emit(Plan& P, const Box& box0, int64_t dst_off, int dst_ld, int row0, int c
     int64_t outer = 1;
     for (int d = 0; d < t.ndim - 2; ++d) outer *= t.dims[d];
     const int Pd = t.dims[t.ndim - 2], Qd = t.dims[t.ndim - 1];
-    const int64_t per = 4;  // outer indices per item (4 x 1024 elements)
+    const int64_t per = 1;  // outer indices per item (one 32 x 32 tile)
     for (int tp = 0; tp < Pd; tp += 32)
       for (int tq = 0; tq < Qd; tq += 32)
         for (int64_t o = 0; o < outer; o += per) {
@@ -395,6 +431,19 @@ void Plan::validate(const int64_t* src_elems, const int64_t* dst_elems) const {
       da += (int64_t)(it.dims[d] - 1) * it.da[d];
       db += (int64_t)(it.dims[d] - 1) * it.db[d];
       total *= it.dims[d];
+      uint32_t m;
+      int8_t sh;
+      div_magic(it.dims[d], m, sh);
+      if (m != it.mag[d] || sh != it.shf[d]) fail(SYM_ERR_ARG, "internal: stale division constants in a work item");
+    }
+    if (sa >= ((int64_t)1 << 31) || sb >= ((int64_t)1 << 31) || da >= ((int64_t)1 << 31) ||
+        db >= ((int64_t)1 << 31) || it.row0 + da >= ((int64_t)1 << 31) || it.col0 + db >= ((int64_t)1 << 31))
+      fail(SYM_ERR_UNSUPPORTED, "internal: box offsets beyond 32 bits");
+    if (it.sel & kSelFlat) {
+      if ((it.sel & kSelImage) || it.nterm > 1 || it.dst_ld != 1 || (it.nterm == 1 && (it.t0_ld != 1 || terms[it.term0].ld != 1)))
+        fail(SYM_ERR_ARG, "internal: flat work item with a two-part offset");
+      for (int d = 0; d < it.ndim; ++d)
+        if (it.sb[d] != 0 || it.db[d] != 0) fail(SYM_ERR_ARG, "internal: flat work item with a two-part offset");
     }
     if (it.sel & kSelTile) {
       if (it.ndim < 2) fail(SYM_ERR_ARG, "internal: tile item needs two dims");
@@ -1184,14 +1233,24 @@ struct ProfScope {
     if (!p.profiling) return;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    cudaEventRecord(e0, s);
+    record(e0);
     p.prof[ph].launches++;
     p.prof[ph].bytes += bytes;
     p.prof[ph].flops += flops;
   }
+  // inside a stream capture the events become external record nodes of the
+  // graph, so every replay re-records them
+  void record(cudaEvent_t e) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &st);
+    if (st == cudaStreamCaptureStatusActive)
+      cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+      cudaEventRecord(e, s);
+  }
   ~ProfScope() {
     if (!p.profiling) return;
-    cudaEventRecord(e1, s);
+    record(e1);
     p.prof[phase].events.push_back({e0, e1});
   }
 };
