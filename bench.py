@@ -40,7 +40,7 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=10)
@@ -62,51 +62,110 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples every 200 ms while a region runs (read-only queries)."""
+    """SM clock, power and clock-event reasons sampled during a timed region.
 
+    Read-only NVML queries (through ctypes, no Python binding needed) from a
+    thread polling every 2 ms, so that even a region of a few milliseconds
+    gets samples; the device is looked up by UUID so that the index mapping
+    of CUDA_VISIBLE_DEVICES cannot pick another GPU.  Falls back to
+    ``nvidia-smi -lms 200`` when NVML cannot be loaded.
+    """
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index):
-        self.idx = device_index
+    def __init__(self, device):
+        import threading
+        self.device = device
+        self.rows = []
+        self.stop_evt = threading.Event()
+        self.thread = None
         self.proc = None
-        self.path = None
+        self.nvml = self.handle = None
+        self.source = None
+        try:
+            import ctypes
+            import torch
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit failed")
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(device).uuid)
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) != 0:
+                raise OSError("device not found by UUID")
+            self.nvml, self.handle, self.ct = lib, h, ctypes
+            self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.source = "nvml"
+        except Exception:
+            self.nvml = None
+
+    def _poll(self):
+        ct, lib, h = self.ct, self.nvml, self.handle
+        clk, mx, mw, rs = ct.c_uint(), ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        while not self.stop_evt.is_set():
+            ok = lib.nvmlDeviceGetClockInfo(h, 1, ct.byref(clk)) == 0  # NVML_CLOCK_SM
+            ok = ok and lib.nvmlDeviceGetMaxClockInfo(h, 1, ct.byref(mx)) == 0
+            ok = ok and self.reasons_fn(h, ct.byref(rs)) == 0
+            if ok:
+                pw = mw.value / 1000.0 if lib.nvmlDeviceGetPowerUsage(h, ct.byref(mw)) == 0 else None
+                self.rows.append((float(clk.value), float(mx.value), pw, int(rs.value)))
+            self.stop_evt.wait(0.002)
 
     def start(self):
+        import threading
+        if self.nvml is not None:
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                ["nvidia-smi", "-i", str(self.device.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+            self.source = "nvidia-smi"
+            time.sleep(1.0)  # let the first samples arrive before the region starts
         except OSError:
             self.proc = None
 
     def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        self.f.close()
-        rows = []
-        with open(self.path) as f:
-            for line in f:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
-        os.unlink(self.path)
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
-        load = [s for s in sm if mx and s >= 0.5 * max(mx)] or sm
+        if self.thread is not None:
+            self.stop_evt.set()
+            self.thread.join()
+            sm = [r[0] for r in self.rows]
+            mx = [r[1] for r in self.rows]
+            pw = [r[2] for r in self.rows if r[2] is not None]
+            reasons = sorted({n for r in self.rows for bit, n in self.REASONS.items() if r[3] & bit})
+        elif self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+            rows = []
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            os.unlink(self.path)
+            sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+            mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+            pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        else:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock source"], "samples": 0}
+        load = [x for x in sm if mx and x >= 0.5 * max(mx)] or sm
         return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "power_w_median": statistics.median(pw) if pw else None,
+                "reasons": reasons, "samples": len(sm), "source": self.source}
 
 
 def mps_structures(P):
@@ -239,7 +298,7 @@ def run_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(dev.index)
+    clocks = ClockSampler(dev)
     clocks.start()
     evs = []
     for _ in range(args.steps):

@@ -36,6 +36,15 @@ constexpr int kItemWords = (int)(sizeof(BoxItem) / 8);
 static_assert(sizeof(BoxItem) % 8 == 0, "BoxItem must be a whole number of 8-byte words");
 static_assert(kItemWords <= 32, "a warp loads a descriptor with one word per lane");
 
+// coefficient in the data type: FP32 kernels read the planner's FP32 copy
+// and so issue no FP64 instruction (FP64 is a low-rate pipe)
+template <typename TD>
+__device__ __forceinline__ TD coef(double c, float cf);
+template <>
+__device__ __forceinline__ double coef<double>(double c, float) { return c; }
+template <>
+__device__ __forceinline__ float coef<float>(double, float cf) { return cf; }
+
 __device__ __forceinline__ int div_magic(int a, uint32_t mag, int shf) {
   return (int)(__umulhi((uint32_t)a << 1, mag) >> shf);
 }
@@ -94,7 +103,7 @@ struct Src {
     TD acc = TD(0);
     for (int i = 0; i < nterm; ++i) {
       const Term* t = terms + term0 + i;
-      acc += TD(__ldg(&t->coef)) * TD(__ldg(p + __ldg(&t->off) + __ldg(&t->ld) * a + b));
+      acc += coef<TD>(__ldg(&t->coef), __ldg(&t->coef_f)) * TD(__ldg(p + __ldg(&t->off) + __ldg(&t->ld) * a + b));
     }
     return acc;
   }
@@ -127,6 +136,8 @@ struct Dst {
   }
 };
 
+// Lanes past the end of a partial item redo its last element: the same load
+// and the same value stored to the same place, so no lane needs a predicate.
 template <int ND, typename TS, typename TD>
 __device__ __forceinline__ void linear_flat(const BoxItem& it, const TS* __restrict__ src, TD* __restrict__ dst,
                                             int lane) {
@@ -136,33 +147,35 @@ __device__ __forceinline__ void linear_flat(const BoxItem& it, const TS* __restr
   load_strides(it.da, da);
   const TS* ps = src + it.t0_off;
   TD* pd = dst + it.dst_off;
-  const bool has_src = it.nterm > 0;
-  const TD c = TD(it.t0_coef);
-  const bool unit = it.t0_coef == 1.0;
-  const int left = it.count - lane;
+  const int last = it.start + it.count - 1;
+  if (it.nterm == 0) {  // zero fill: nothing to read
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      int t[ND];
+      sh.split(min(it.start + lane + 32 * u, last), t);
+      pd[dot(t, da)] = TD(0);
+    }
+    return;
+  }
+  const TD c = coef<TD>(it.t0_coef, it.t0_coef_f);
   TD v[kBatch];
   int dof[kBatch];
 #pragma unroll
   for (int u = 0; u < kBatch; ++u) {
-    v[u] = TD(0);
-    dof[u] = 0;
-    if (32 * u < left) {
-      int t[ND];
-      sh.split(it.start + lane + 32 * u, t);
-      dof[u] = dot(t, da);
-      if (has_src) v[u] = TD(__ldg(ps + dot(t, sa)));
-    }
+    int t[ND];
+    sh.split(min(it.start + lane + 32 * u, last), t);
+    dof[u] = dot(t, da);
+    v[u] = TD(__ldg(ps + dot(t, sa)));
   }
 #pragma unroll
-  for (int u = 0; u < kBatch; ++u)
-    if (32 * u < left) pd[dof[u]] = unit ? v[u] : c * v[u];
+  for (int u = 0; u < kBatch; ++u) pd[dof[u]] = c * v[u];
 }
 
 template <int ND, typename TS, typename TD>
 __device__ __forceinline__ void linear_general(const BoxItem& it, const Src<TS, TD>& src, const Dst<TD>& dst,
                                                int lane) {
   const Shape<ND> sh(it);
-  const int left = it.count - lane;
+  const int last = it.start + it.count - 1;
   TD v[kBatch];
   {
     int sa[ND], sb[ND];
@@ -170,12 +183,9 @@ __device__ __forceinline__ void linear_general(const BoxItem& it, const Src<TS, 
     load_strides(it.sb, sb);
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
-      v[u] = TD(0);
-      if (32 * u < left) {
-        int t[ND];
-        sh.split(it.start + lane + 32 * u, t);
-        v[u] = src.load(dot(t, sa), dot(t, sb));
-      }
+      int t[ND];
+      sh.split(min(it.start + lane + 32 * u, last), t);
+      v[u] = src.load(dot(t, sa), dot(t, sb));
     }
   }
   int da[ND], db[ND];
@@ -183,11 +193,9 @@ __device__ __forceinline__ void linear_general(const BoxItem& it, const Src<TS, 
   load_strides(it.db, db);
 #pragma unroll
   for (int u = 0; u < kBatch; ++u) {
-    if (32 * u < left) {
-      int t[ND];
-      sh.split(it.start + lane + 32 * u, t);
-      dst.store(v[u], dot(t, da), dot(t, db));
-    }
+    int t[ND];
+    sh.split(min(it.start + lane + 32 * u, last), t);
+    dst.store(v[u], dot(t, da), dot(t, db));
   }
 }
 
@@ -237,8 +245,8 @@ __device__ __forceinline__ void tile_item(const BoxItem& it, const TS* __restric
   const int cols = min(32, Q - it.q0);
   if (p < P) {
     if (flat) {
-      const TD c = TD(it.t0_coef);
-      const bool unit = it.t0_coef == 1.0;
+      const TD c = coef<TD>(it.t0_coef, it.t0_coef_f);
+      const bool unit = (it.sel & kSelUnit) != 0;
       TD* pd = fdst + it.dst_off + da + p * dap + it.q0 * daq;
 #pragma unroll 8
       for (int k = 0; k < 32; ++k)
@@ -255,29 +263,80 @@ __device__ __forceinline__ void tile_item(const BoxItem& it, const TS* __restric
 }
 
 template <typename TS, typename TD>
+__device__ __forceinline__ const TS* src_slot(const BoxItem& it, const BoxPtrs& ptrs) {
+  const int k = it.sel & 3;
+  return static_cast<const TS*>(k == 0 ? ptrs.src[0] : k == 1 ? ptrs.src[1] : k == 2 ? ptrs.src[2] : ptrs.src[3]);
+}
+
+__device__ __forceinline__ void* dst_slot(const BoxItem& it, const BoxPtrs& ptrs) {
+  switch ((it.sel >> 4) & 7) {
+    case 0: return ptrs.dst[0][0];
+    case 1: return ptrs.dst[1][0];
+    case 2: return ptrs.dst[2][0];
+    case 3: return ptrs.dst[3][0];
+    case 4: return ptrs.dst[4][0];
+    default: return ptrs.dst[5][0];
+  }
+}
+
+// flat linear item of 4 to 6 dims (rare): the index split reads the descriptor
+// from shared memory dim by dim instead of holding it in registers
+template <typename TS, typename TD>
+__device__ __forceinline__ void linear_flat_rolled(const BoxItem& it, const TS* __restrict__ src,
+                                                   TD* __restrict__ dst, int lane) {
+  const TS* ps = src + it.t0_off;
+  TD* pd = dst + it.dst_off;
+  const int last = it.start + it.count - 1;
+  const bool has_src = it.nterm > 0;
+  const TD c = coef<TD>(it.t0_coef, it.t0_coef_f);
+  TD v[kBatch];
+  int dof[kBatch];
+#pragma unroll
+  for (int u = 0; u < kBatch; ++u) {
+    int rem = min(it.start + lane + 32 * u, last), so = 0, dd = 0;
+#pragma unroll 1
+    for (int d = kMaxDim - 1; d >= 0; --d) {
+      const int q = d > 0 ? div_magic(rem, it.mag[d], it.shf[d]) : 0;
+      const int t = rem - q * it.dims[d];
+      rem = q;
+      so += t * it.sa[d];
+      dd += t * it.da[d];
+    }
+    dof[u] = dd;
+    v[u] = has_src ? c * TD(__ldg(ps + so)) : TD(0);
+  }
+#pragma unroll
+  for (int u = 0; u < kBatch; ++u) pd[dof[u]] = v[u];
+}
+
+// flat linear item
+template <typename TS, typename TD>
+__device__ __forceinline__ void run_flat(const BoxItem& it, const BoxPtrs& ptrs, int lane) {
+  const TS* sp = src_slot<TS, TD>(it, ptrs);
+  TD* d = static_cast<TD*>(dst_slot(it, ptrs));
+  switch (it.ndim) {
+    case 1: linear_flat<1, TS, TD>(it, sp, d, lane); break;
+    case 2: linear_flat<2, TS, TD>(it, sp, d, lane); break;
+    case 3: linear_flat<3, TS, TD>(it, sp, d, lane); break;
+    default: linear_flat_rolled<TS, TD>(it, sp, d, lane); break;
+  }
+}
+
+template <typename TS, typename TD>
 __device__ __forceinline__ void run_item(const BoxItem& it, const Term* __restrict__ terms, const BoxPtrs& ptrs,
                                          TD (*tile)[33], int lane) {
-  const int sslot = it.sel & 3, dslot = (it.sel >> 4) & 7;
-  const TS* sp = static_cast<const TS*>(sslot == 0 ? ptrs.src[0]
-                                        : sslot == 1 ? ptrs.src[1]
-                                        : sslot == 2 ? ptrs.src[2]
-                                                     : ptrs.src[3]);
-  void* dp;
-  switch (dslot) {
-    case 0: dp = ptrs.dst[0][0]; break;
-    case 1: dp = ptrs.dst[1][0]; break;
-    case 2: dp = ptrs.dst[2][0]; break;
-    case 3: dp = ptrs.dst[3][0]; break;
-    case 4: dp = ptrs.dst[4][0]; break;
-    default: dp = ptrs.dst[5][0]; break;
+  if ((it.sel & (kSelFlat | kSelTile)) == kSelFlat) {
+    run_flat<TS, TD>(it, ptrs, lane);
+    return;
   }
-  const bool flat = (it.sel & kSelFlat) != 0;
+  const TS* sp = src_slot<TS, TD>(it, ptrs);
+  void* dp = dst_slot(it, ptrs);
   Src<TS, TD> src;
   src.p = sp;
   src.terms = terms;
   src.off0 = it.t0_off;
   src.ld0 = it.t0_ld;
-  src.c0 = TD(it.t0_coef);
+  src.c0 = coef<TD>(it.t0_coef, it.t0_coef_f);
   src.nterm = it.nterm;
   src.term0 = it.term0;
   Dst<TD> dst;
@@ -292,33 +351,20 @@ __device__ __forceinline__ void run_item(const BoxItem& it, const Term* __restri
     tile_item<TS, TD>(it, sp, static_cast<TD*>(dp), src, dst, tile, lane);
     return;
   }
-  if (flat) {
-    TD* d = static_cast<TD*>(dp);
-    switch (it.ndim) {
-      case 1: linear_flat<1, TS, TD>(it, sp, d, lane); break;
-      case 2: linear_flat<2, TS, TD>(it, sp, d, lane); break;
-      case 3: linear_flat<3, TS, TD>(it, sp, d, lane); break;
-      case 4: linear_flat<4, TS, TD>(it, sp, d, lane); break;
-      case 5: linear_flat<5, TS, TD>(it, sp, d, lane); break;
-      default: linear_flat<6, TS, TD>(it, sp, d, lane); break;
-    }
-  } else {
-    switch (it.ndim) {
-      case 1: linear_general<1, TS, TD>(it, src, dst, lane); break;
-      case 2: linear_general<2, TS, TD>(it, src, dst, lane); break;
-      case 3: linear_general<3, TS, TD>(it, src, dst, lane); break;
-      case 4: linear_general<4, TS, TD>(it, src, dst, lane); break;
-      case 5: linear_general<5, TS, TD>(it, src, dst, lane); break;
-      default: linear_general<6, TS, TD>(it, src, dst, lane); break;
-    }
+  switch (it.ndim) {
+    case 1: linear_general<1, TS, TD>(it, src, dst, lane); break;
+    case 2: linear_general<2, TS, TD>(it, src, dst, lane); break;
+    case 3: linear_general<3, TS, TD>(it, src, dst, lane); break;
+    default: linear_general<kMaxDim, TS, TD>(it, src, dst, lane); break;
   }
 }
 
-template <typename TS, typename TD>
-__global__ void __launch_bounds__(kThreads) box_kernel(const BoxItem* __restrict__ items, int nitems,
-                                                       const Term* __restrict__ terms, const BoxPtrs ptrs) {
+// kFlat: every item of the launch is a flat linear item; this variant has
+// no tile buffer and a 64-register cap, so twice the warps stay resident.
+template <typename TS, typename TD, bool kFlat>
+__global__ void __launch_bounds__(kThreads, kFlat ? 8 : (sizeof(TD) == 4 ? 5 : 4))
+    box_kernel(const BoxItem* __restrict__ items, int nitems, const Term* __restrict__ terms, const BoxPtrs ptrs) {
   __shared__ int64_t raw[kWarps][kItemWords];
-  __shared__ TD tiles[kWarps][32][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nwarps = gridDim.x * kWarps;
   int item = blockIdx.x * kWarps + w;
@@ -331,17 +377,23 @@ __global__ void __launch_bounds__(kThreads) box_kernel(const BoxItem* __restrict
     __syncwarp();
     const int next = item + nwarps;
     if (lane < kItemWords && next < nitems) word = __ldg(words + (int64_t)next * kItemWords + lane);
-    run_item<TS, TD>(it, terms, ptrs, tiles[w], lane);
+    if constexpr (kFlat) {
+      run_flat<TS, TD>(it, ptrs, lane);
+    } else {
+      __shared__ TD tiles[kWarps][32][33];
+      run_item<TS, TD>(it, terms, ptrs, tiles[w], lane);
+    }
     __syncwarp();
   }
 }
 
-template <typename TS, typename TD>
+template <typename TS, typename TD, bool kFlat>
 int launch_t(const BoxItem* items, int nitems, const Term* terms, const BoxPtrs& ptrs, cudaStream_t s) {
   static int slots = 0;  // resident warps of this instantiation on the device
   if (slots == 0) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, box_kernel<TS, TD>, kThreads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, box_kernel<TS, TD, kFlat>, kThreads, 0) !=
+            cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
     int dev = 0, nsm = 1;
@@ -351,18 +403,22 @@ int launch_t(const BoxItem* items, int nitems, const Term* terms, const BoxPtrs&
   }
   const int warps = nitems < slots ? nitems : slots;
   const int grid = (warps + kWarps - 1) / kWarps;
-  box_kernel<TS, TD><<<grid, kThreads, 0, s>>>(items, nitems, terms, ptrs);
+  box_kernel<TS, TD, kFlat><<<grid, kThreads, 0, s>>>(items, nitems, terms, ptrs);
   return (int)cudaGetLastError();
 }
 
 }  // namespace
 
-int launch_box(bool src_f64, bool dst_f64, const BoxItem* items, int nitems, const Term* terms, const BoxPtrs& ptrs,
-               void* stream) {
+int launch_box(bool src_f64, bool dst_f64, bool flat_only, const BoxItem* items, int nitems, const Term* terms,
+               const BoxPtrs& ptrs, void* stream) {
   if (nitems <= 0) return 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (src_f64 && dst_f64) return launch_t<double, double>(items, nitems, terms, ptrs, s);
-  if (!src_f64 && !dst_f64) return launch_t<float, float>(items, nitems, terms, ptrs, s);
+  if (src_f64 && dst_f64)
+    return flat_only ? launch_t<double, double, true>(items, nitems, terms, ptrs, s)
+                     : launch_t<double, double, false>(items, nitems, terms, ptrs, s);
+  if (!src_f64 && !dst_f64)
+    return flat_only ? launch_t<float, float, true>(items, nitems, terms, ptrs, s)
+                     : launch_t<float, float, false>(items, nitems, terms, ptrs, s);
   return (int)cudaErrorInvalidValue;
 }
 

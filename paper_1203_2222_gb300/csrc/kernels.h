@@ -15,6 +15,7 @@ constexpr int kSelTile = 1 << 9;   // BoxItem::sel flag: 32 x 32 transposing til
 // dst_ld == 1, sb == db == 0, and both <t, sa> and <t, da> below 2^31, so the
 // kernel addresses source and destination with one 32-bit dot product each
 constexpr int kSelFlat = 1 << 10;
+constexpr int kSelUnit = 1 << 11;  // BoxItem::sel flag: one term whose coefficient is exactly 1
 constexpr int kBoxChunk = 512;  // elements of a linear work item (32 lanes x 16)
 
 // One work unit of the block-movement kernel: a strided box of `dims`
@@ -45,18 +46,24 @@ struct BoxItem {
   int32_t dims[kMaxDim];
   int32_t sa[kMaxDim], sb[kMaxDim];
   int32_t da[kMaxDim], db[kMaxDim];
+  // Dims d >= ndim hold size 1 with zero strides, so a kernel may treat the
+  // box as having more dims than it does.
   // division by dims[d] without a divide: for 0 <= a < 2^31,
   // floor(a / dims[d]) = umulhi(2a, mag[d]) >> shf[d] (Granlund & Montgomery,
   // PLDI 1994, Thm 4.2 with N = 31: shf = ceil(log2 dims), mag = ceil(2^(31+shf) / dims))
   uint32_t mag[kMaxDim];
   int8_t shf[kMaxDim];
   int8_t pad_[2];
+  float t0_coef_f;  // t0_coef rounded to FP32 (the FP32 kernels issue no FP64 instruction)
 };
+static_assert(sizeof(BoxItem) == 232, "BoxItem layout");
 
 struct Term {
   int64_t off;
   int64_t ld;
   double coef;
+  float coef_f;  // coef rounded to FP32 (set by the planner)
+  int32_t pad_;
 };
 
 // Buffers a box launch may read (src slots) and write (dst slots; image
@@ -94,7 +101,8 @@ struct TcSector {
 enum SimtShape { SIMT_64x64 = 0, SIMT_256x16 = 1, SIMT_THIN = 2, SIMT_ROWS = 3, SIMT_SHAPES = 4 };
 
 // Launchers (return cudaError_t as int).
-int launch_box(bool src_f64, bool dst_f64, const BoxItem* items, int nitems, const Term* terms,
+// flat_only: every item is a flat linear item (kSelFlat without kSelTile)
+int launch_box(bool src_f64, bool dst_f64, bool flat_only, const BoxItem* items, int nitems, const Term* terms,
                const BoxPtrs& ptrs, void* stream);
 int launch_gemm_simt(bool f64, int shape, const GemmSectorSimt* secs, const GemmTile* tiles, int ntiles,
                      const void* ops, void* outm, void* stream);

@@ -106,6 +106,7 @@ BoxItem make_item(const Box& box, int64_t dst_off, int dst_ld, int row0, int col
     it.t0_off = terms[0].off;
     it.t0_ld = terms[0].ld;
     it.t0_coef = terms[0].coef;
+    it.t0_coef_f = (float)terms[0].coef;
   }
   for (int i = 0; i < box.ndim; ++i) {
     it.dims[i] = box.dims[i];
@@ -115,6 +116,11 @@ BoxItem make_item(const Box& box, int64_t dst_off, int dst_ld, int row0, int col
     it.db[i] = box.db[i];
     div_magic(box.dims[i], it.mag[i], it.shf[i]);
   }
+  for (int i = box.ndim; i < kMaxDim; ++i) {
+    it.dims[i] = 1;
+    div_magic(1, it.mag[i], it.shf[i]);
+  }
+  if (terms.size() == 1 && terms[0].coef == 1.0) it.sel |= kSelUnit;
   return it;
 }
 
@@ -156,6 +162,7 @@ void emit(Plan& P, const Box& box0, int64_t dst_off, int dst_ld, int row0, int c
   for (int i = 0; i < box.ndim; ++i) total *= box.dims[i];
   if (total >= (int64_t)1 << 31) fail(SYM_ERR_UNSUPPORTED, "block larger than 2^31 elements");
   const int term0 = (int)P.terms.size();
+  for (Term& t : terms) t.coef_f = (float)t.coef;
   P.terms.insert(P.terms.end(), terms.begin(), terms.end());
   // transposition check
   const int64_t ld0 = terms.empty() ? 1 : terms[0].ld;
@@ -439,6 +446,15 @@ void Plan::validate(const int64_t* src_elems, const int64_t* dst_elems) const {
     if (sa >= ((int64_t)1 << 31) || sb >= ((int64_t)1 << 31) || da >= ((int64_t)1 << 31) ||
         db >= ((int64_t)1 << 31) || it.row0 + da >= ((int64_t)1 << 31) || it.col0 + db >= ((int64_t)1 << 31))
       fail(SYM_ERR_UNSUPPORTED, "internal: box offsets beyond 32 bits");
+    for (int d = it.ndim; d < kMaxDim; ++d) {
+      uint32_t m;
+      int8_t sh;
+      div_magic(1, m, sh);
+      if (it.dims[d] != 1 || it.sa[d] || it.sb[d] || it.da[d] || it.db[d] || it.mag[d] != m || it.shf[d] != sh)
+        fail(SYM_ERR_ARG, "internal: unused dim of a work item is not a unit dim");
+    }
+    if ((it.sel & kSelUnit) && (it.nterm != 1 || it.t0_coef != 1.0 || it.t0_coef_f != 1.0f))
+      fail(SYM_ERR_ARG, "internal: unit flag on a work item whose coefficient is not 1");
     if (it.sel & kSelFlat) {
       if ((it.sel & kSelImage) || it.nterm > 1 || it.dst_ld != 1 || (it.nterm == 1 && (it.t0_ld != 1 || terms[it.term0].ld != 1)))
         fail(SYM_ERR_ARG, "internal: flat work item with a two-part offset");
@@ -502,6 +518,9 @@ void Plan::upload(bool device) {
   // finish the statistics tables (prefix sums)
   if (item_bytes_prefix.size() != items.size() + 1) item_bytes_prefix.assign(items.size() + 1, 0.0);
   for (size_t i = 0; i < items.size(); ++i) item_bytes_prefix[i + 1] += item_bytes_prefix[i];
+  flat_prefix.assign(items.size() + 1, 0);
+  for (size_t i = 0; i < items.size(); ++i)
+    flat_prefix[i + 1] = flat_prefix[i] + ((items[i].sel & (kSelFlat | kSelTile)) == kSelFlat ? 1 : 0);
   tile_flops_prefix.assign(tiles.size() + 1, 0.0);
   for (size_t i = 0; i < tiles.size(); ++i) {
     const GemmTile& t = tiles[i];
@@ -1259,7 +1278,8 @@ int run_box(Plan& p, Range r, const BoxPtrs& ptrs, void* stream, int phase) {
   if (r.count <= 0) return SYM_OK;
   p.last_launches++;
   ProfScope ps(p, phase, stream, p.item_bytes_prefix[r.first + r.count] - p.item_bytes_prefix[r.first], 0.0);
-  return cuda_code(launch_box(p.f64(), p.f64(), p.d_items + r.first, r.count, p.d_terms, ptrs, stream),
+  const bool flat_only = p.flat_prefix[r.first + r.count] - p.flat_prefix[r.first] == r.count;
+  return cuda_code(launch_box(p.f64(), p.f64(), flat_only, p.d_items + r.first, r.count, p.d_terms, ptrs, stream),
                    "box kernel");
 }
 
