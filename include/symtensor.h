@@ -150,6 +150,12 @@ int sym_plan_execute(sym_plan plan, const void* in, void* out, void* stream);
  * sym_contract_backward: dA, dB = gradient of <dC, C> with respect to A's
  *   and B's blocks (adjoint on the same sector tables); dA or dB may be NULL
  *   to skip it.  Buffers are overwritten, not accumulated.
+ *   Both are asynchronous on `stream`.  The GEMM launches of one call run
+ *   concurrently on side streams that the plan creates on first use, forked
+ *   from `stream` and joined back into it with events (in a stream capture
+ *   they become graph dependencies).  A plan owns its scratch buffers:
+ *   executions of one plan must not overlap (serialize calls that share a
+ *   plan across streams or threads).
  * sym_plan_stats: useful flops of one forward (sum over sectors of 2 m n k),
  *   and bytes of A, B and C blocks in the plan's data type.              */
 int sym_contract_plan(sym_tensor A, sym_tensor B, int npairs, const int* pairsA,

@@ -70,6 +70,7 @@ extern "C" int sym_contract_noalloc(sym_tensor A, sym_tensor B, int npairs, cons
     if (it == g_plans.end()) {
       Tensor Ct = contraction_result(A->t, B->t, pa, pb, nullptr);
       it = g_plans.emplace(key, plan_contract(A->t, B->t, pa, pb, Ct, precision, /*device=*/false)).first;
+      it->second->concurrent = false;  // no side streams or events: launch the GEMM kinds in order
     }
     Plan& p = *it->second;
     if (!a || !b || (p.numel_c > 0 && !c)) fail(SYM_ERR_ARG, "NULL data pointer");

@@ -512,7 +512,14 @@ void Plan::clear_profile() {
   }
 }
 
-Plan::~Plan() { clear_profile(); }
+Plan::~Plan() {
+  clear_profile();
+  for (int i = 0; i < kGemmKinds - 1; ++i) {
+    if (side[i]) cudaStreamDestroy(static_cast<cudaStream_t>(side[i]));
+    if (ev_join[i]) cudaEventDestroy(static_cast<cudaEvent_t>(ev_join[i]));
+  }
+  if (ev_fork) cudaEventDestroy(static_cast<cudaEvent_t>(ev_fork));
+}
 
 void Plan::upload(bool device) {
   // finish the statistics tables (prefix sums)
@@ -1299,15 +1306,62 @@ int run_gemm_kind(Plan& p, int kind, Range r, void* stream, int phase) {
                    "cuda-core gemm");
 }
 
-// GEMM phases [ph0, ph1] (contiguous within each kind)
+// GEMM phases [ph0, ph1] (contiguous within each kind).  The kinds with
+// work run concurrently: the first on `stream`, the others on the plan's
+// side streams, forked from and joined back into `stream` with events.
 int run_gemm(Plan& p, int ph0, int ph1, void* stream, int phase) {
+  int kinds[kGemmKinds];
+  Range rs[kGemmKinds];
+  int n = 0;
   for (int kind = 0; kind < kGemmKinds; ++kind) {
     Range r{p.gemm_range[kind][ph0].first, 0};
     for (int ph = ph0; ph <= ph1; ++ph) r.count += p.gemm_range[kind][ph].count;
-    int rc = run_gemm_kind(p, kind, r, stream, phase);
-    if (rc) return rc;
+    if (r.count > 0) {
+      kinds[n] = kind;
+      rs[n++] = r;
+    }
   }
-  return SYM_OK;
+  if (n <= 1 || !p.concurrent) {
+    for (int i = 0; i < n; ++i)
+      if (int rc = run_gemm_kind(p, kinds[i], rs[i], stream, phase)) return rc;
+    return SYM_OK;
+  }
+  cudaStream_t s0 = static_cast<cudaStream_t>(stream);
+  auto check = [](cudaError_t e, const char* what) {
+    if (e != cudaSuccess) fail(SYM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  if (!p.ev_fork) {
+    cudaEvent_t e;
+    check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+    p.ev_fork = e;
+  }
+  for (int i = 0; i < n - 1; ++i) {
+    if (!p.side[i]) {
+      cudaStream_t st;
+      check(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "cudaStreamCreate");
+      p.side[i] = st;
+    }
+    if (!p.ev_join[i]) {
+      cudaEvent_t e;
+      check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+      p.ev_join[i] = e;
+    }
+  }
+  check(cudaEventRecord(static_cast<cudaEvent_t>(p.ev_fork), s0), "cudaEventRecord");
+  for (int i = 0; i < n - 1; ++i)
+    check(cudaStreamWaitEvent(static_cast<cudaStream_t>(p.side[i]), static_cast<cudaEvent_t>(p.ev_fork), 0),
+          "cudaStreamWaitEvent");
+  int rc = run_gemm_kind(p, kinds[0], rs[0], stream, phase);
+  for (int i = 1; i < n; ++i) {
+    const int r = run_gemm_kind(p, kinds[i], rs[i], p.side[i - 1], phase);
+    if (!rc) rc = r;
+  }
+  // join every side stream, also after a failed launch
+  for (int i = 0; i < n - 1; ++i) {
+    cudaEventRecord(static_cast<cudaEvent_t>(p.ev_join[i]), static_cast<cudaStream_t>(p.side[i]));
+    cudaStreamWaitEvent(s0, static_cast<cudaEvent_t>(p.ev_join[i]), 0);
+  }
+  return rc;
 }
 
 BoxPtrs gather_ptrs(Plan& p, const void* A, const void* B, const void* dC) {

@@ -87,6 +87,15 @@ struct Plan {
   void* outm = nullptr;    // output matrices (fp32 or fp64)
   int* d_err = nullptr;
 
+  // The GEMM kinds of one phase touch disjoint sectors: they are forked onto
+  // side streams and joined back (created on first use; events and streams
+  // are captured into a CUDA graph as dependencies).  Off for plans that
+  // must create nothing (sym_contract_noalloc).
+  bool concurrent = true;
+  void* side[kGemmKinds - 1] = {};     // cudaStream_t
+  void* ev_fork = nullptr;             // cudaEvent_t
+  void* ev_join[kGemmKinds - 1] = {};  // cudaEvent_t
+
   void validate(const int64_t* src_elems, const int64_t* dst_elems) const;
   void upload(bool device = true);
 };
