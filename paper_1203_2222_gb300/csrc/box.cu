@@ -13,15 +13,13 @@
 //    fastest).  The multi-index of an element is split off by multiply-high
 //    division (magic numbers from the planner) in registers, with the number
 //    of dims a template parameter; all 16 loads are issued before any store.
-//  - A flat item (one term, linear destination, 32-bit spans) addresses both
-//    sides with a single dot product each; the general form (recoupling sums,
-//    split-BF16 operand images) keeps the two-part source and destination
-//    offsets.
+//  - A flat item (at most one term, 32-bit spans) addresses both sides with
+//    a single dot product each; the general form (recoupling sums, offsets
+//    beyond 32 bits) keeps the two-part source and destination offsets.
 //  - A tile item is one 32 x 32 tile of the box's last two dims at one outer
 //    index: the warp reads it along the source-contiguous dim into its own
 //    shared-memory tile and writes it along the destination-contiguous dim.
 // Memory-bound: bytes = source read + destination written.
-#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -109,31 +107,12 @@ struct Src {
   }
 };
 
-// destination side of the general form: linear, or a split-BF16 operand image
+// destination side of the general form: dst[off + ld * a + b]
 template <typename TD>
 struct Dst {
-  void* p0;
-  void* p1;
+  TD* p;
   int64_t off, ld;
-  int row0, col0;
-  bool image;
-
-  __device__ __forceinline__ void store(TD v, int a, int b) const {
-    if (!image) {
-      static_cast<TD*>(p0)[off + ld * a + b] = v;
-    } else {
-      // split-BF16: hi = bf16(v), lo = bf16(v - hi); tiled, 128B-swizzled image
-      const float x = (float)v;
-      const int row = row0 + a;
-      const int col = col0 + b;
-      const int64_t o = off + ((int64_t)(row >> 7) * ld + (col >> 6)) * 8192 + (row & 127) * 64 +
-                        ((((col >> 3) & 7) ^ (row & 7)) << 3) + (col & 7);
-      const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-      const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-      static_cast<__nv_bfloat16*>(p0)[o] = hi;
-      static_cast<__nv_bfloat16*>(p1)[o] = lo;
-    }
-  }
+  __device__ __forceinline__ void store(TD v, int a, int b) const { p[off + ld * a + b] = v; }
 };
 
 // Lanes past the end of a partial item redo its last element: the same load
@@ -270,12 +249,11 @@ __device__ __forceinline__ const TS* src_slot(const BoxItem& it, const BoxPtrs& 
 
 __device__ __forceinline__ void* dst_slot(const BoxItem& it, const BoxPtrs& ptrs) {
   switch ((it.sel >> 4) & 7) {
-    case 0: return ptrs.dst[0][0];
-    case 1: return ptrs.dst[1][0];
-    case 2: return ptrs.dst[2][0];
-    case 3: return ptrs.dst[3][0];
-    case 4: return ptrs.dst[4][0];
-    default: return ptrs.dst[5][0];
+    case 0: return ptrs.dst[0];
+    case 1: return ptrs.dst[1];
+    case 2: return ptrs.dst[2];
+    case 3: return ptrs.dst[3];
+    default: return ptrs.dst[4];
   }
 }
 
@@ -340,13 +318,9 @@ __device__ __forceinline__ void run_item(const BoxItem& it, const Term* __restri
   src.nterm = it.nterm;
   src.term0 = it.term0;
   Dst<TD> dst;
-  dst.p0 = dp;
-  dst.p1 = ptrs.dst[0][1];
+  dst.p = static_cast<TD*>(dp);
   dst.off = it.dst_off;
   dst.ld = it.dst_ld;
-  dst.row0 = it.row0;
-  dst.col0 = it.col0;
-  dst.image = (it.sel & kSelImage) != 0;
   if (it.sel & kSelTile) {
     tile_item<TS, TD>(it, sp, static_cast<TD*>(dp), src, dst, tile, lane);
     return;

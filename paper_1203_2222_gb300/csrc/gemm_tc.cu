@@ -6,10 +6,11 @@
 // hi = bf16(a), lo = bf16(a - hi) and the product is accumulated in FP32 in
 // tensor memory as  A_hi B_hi + A_hi B_lo + A_lo B_hi  (3 passes).
 //
-// Operands arrive as tiled images written by the gather (box.cu): a tile is
-// 128 rows x 64 k of bf16 (16 KB) in the canonical K-major, 128-byte-swizzle
-// layout of the tensor-core shared-memory descriptors, so one bulk copy
-// (cp.async.bulk, the TMA engine's linear mode) stages it with no tensor map.
+// Operands arrive as tiled images made by the pack kernel below from the
+// FP32 matrices that the gather (box.cu) writes: a tile is 128 rows x 64 k of
+// bf16 (16 KB) in the canonical K-major, 128-byte-swizzle layout of the
+// tensor-core shared-memory descriptors, so one bulk copy (cp.async.bulk,
+// the TMA engine's linear mode) stages it with no tensor map.
 //
 // Roles (192 threads, one CTA per SM, persistent over the tile list):
 //   warp 0     one thread issues the bulk copies into a 3-stage ring;
@@ -340,6 +341,41 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
 }
 
+// Operand images from FP32 row-major matrices.  One CTA per image tile
+// (128 rows x 64 columns); thread t converts the 8-column chunk t % 8 of
+// rows t / 8 + 32 i, i = 0..3: eight FP32 loads, then hi = bf16(x) and
+// lo = bf16(x - hi) (round to nearest) as one 16-byte store each, at the
+// chunk's 128-byte-swizzled place.  Positions outside the matrix are zero,
+// so the tensor cores read zeros in every padded row and column.
+__global__ void __launch_bounds__(256) pack_kernel(const PackTile* __restrict__ tiles, const float* __restrict__ lin,
+                                                   __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const PackTile t = tiles[blockIdx.x];
+  const int chunk = threadIdx.x & 7;
+  const int c0 = t.kt * 64 + chunk * 8;
+  const int64_t tile = t.img + ((int64_t)t.mt * t.ktiles + t.kt) * TILE_ELEMS;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int rr = (threadIdx.x >> 3) + 32 * i;
+    const int r = t.mt * 128 + rr;
+    const float* src = lin + t.src + (int64_t)r * t.ld;
+    float x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = (r < t.rows && c0 + j < t.cols) ? __ldg(src + c0 + j) : 0.0f;
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const __nv_bfloat162 hv = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+      const __nv_bfloat162 lv =
+          __floats2bfloat162_rn(x[2 * j] - __low2float(hv), x[2 * j + 1] - __high2float(hv));
+      h[j] = *reinterpret_cast<const uint32_t*>(&hv);
+      l[j] = *reinterpret_cast<const uint32_t*>(&lv);
+    }
+    const int64_t o = tile + rr * 64 + ((chunk ^ (rr & 7)) << 3);
+    *reinterpret_cast<uint4*>(hi + o) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(lo + o) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
 int g_num_sms = 0;
 
 }  // namespace
@@ -368,6 +404,13 @@ int launch_gemm_tc(const TcSector* secs, const GemmTile* tiles, int ntiles, cons
   gemm_tc_kernel<<<grid, NUM_THREADS, SMEM_BYTES, static_cast<cudaStream_t>(stream)>>>(
       secs, tiles, ntiles, reinterpret_cast<const __nv_bfloat16*>(a_hi), reinterpret_cast<const __nv_bfloat16*>(a_lo),
       reinterpret_cast<const __nv_bfloat16*>(b_hi), reinterpret_cast<const __nv_bfloat16*>(b_lo), C, err_word);
+  return (int)cudaGetLastError();
+}
+
+int launch_pack(const PackTile* tiles, int ntiles, const float* lin, uint16_t* hi, uint16_t* lo, void* stream) {
+  if (ntiles <= 0) return 0;
+  pack_kernel<<<ntiles, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      tiles, lin, reinterpret_cast<__nv_bfloat16*>(hi), reinterpret_cast<__nv_bfloat16*>(lo));
   return (int)cudaGetLastError();
 }
 

@@ -8,8 +8,7 @@ namespace sym {
 constexpr int kMaxDim = 6;
 
 // Destination slots of a box launch.
-enum DstSlot { DST_IMAGE = 0, DST_OUT = 1, DST_DA = 2, DST_DB = 3, DST_OPS = 4, DST_OUTM = 5, DST_COUNT = 6 };
-constexpr int kSelImage = 1 << 8;  // BoxItem::sel flag: destination is a split-BF16 image
+enum DstSlot { DST_OUT = 0, DST_DA = 1, DST_DB = 2, DST_OPS = 3, DST_OUTM = 4, DST_COUNT = 5 };
 constexpr int kSelTile = 1 << 9;   // BoxItem::sel flag: 32 x 32 transposing tile (see box.cu)
 // BoxItem::sel flag: at most one term with t0_ld == 1, linear destination with
 // dst_ld == 1, sb == db == 0, and both <t, sa> and <t, da> below 2^31, so the
@@ -21,10 +20,7 @@ constexpr int kBoxChunk = 512;  // elements of a linear work item (32 lanes x 16
 // One work unit of the block-movement kernel: a strided box of `dims`
 // (last dim fastest) whose element t is
 //   dst  <- sum over terms  coef * src[term.off + term.ld * <t, sa> + <t, sb>]
-// Destination:
-//   linear: dst[dst_off + dst_ld * <t, da> + <t, db>]
-//   image : sector matrix element (row0 + <t, da>, col0 + <t, db>) of a
-//           tiled split-BF16 operand image starting at dst_off (see gemm_tc.cu)
+// written to dst[dst_off + dst_ld * <t, da> + <t, db>].
 // Only elements [start, start + count) of the box (row-major linear index)
 // belong to this unit; the planner guarantees that every destination element
 // is written by exactly one unit.  An item with no terms writes zeros.
@@ -36,9 +32,8 @@ struct BoxItem {
   int64_t t0_off, t0_ld;  // first term, inline (no second round trip when nterm == 1)
   double t0_coef;
   int64_t dst_off;
-  int32_t dst_ld;   // linear: multiplier of <t, da>; image: K tiles per row tile
-  int32_t row0, col0;
-  int32_t sel;      // source slot (bits 0-1), destination slot (bits 4-6), kSelImage
+  int32_t dst_ld;   // multiplier of <t, da>
+  int32_t sel;      // source slot (bits 0-1), destination slot (bits 4-6), kSel* flags
   int32_t ndim;
   int32_t term0, nterm;
   int32_t start, count;
@@ -56,7 +51,7 @@ struct BoxItem {
   int8_t pad_[2];
   float t0_coef_f;  // t0_coef rounded to FP32 (the FP32 kernels issue no FP64 instruction)
 };
-static_assert(sizeof(BoxItem) == 232, "BoxItem layout");
+static_assert(sizeof(BoxItem) == 224, "BoxItem layout");
 
 struct Term {
   int64_t off;
@@ -66,11 +61,10 @@ struct Term {
   int32_t pad_;
 };
 
-// Buffers a box launch may read (src slots) and write (dst slots; image
-// items write the hi image to dst[i][0] and the lo image to dst[i][1]).
+// Buffers a box launch may read (src slots) and write (dst slots).
 struct BoxPtrs {
   const void* src[4];
-  void* dst[DST_COUNT][2];
+  void* dst[DST_COUNT];
 };
 
 // CUDA-core grouped GEMM (row-major): C = alpha * A (m x k, lda) * B (k x n, ldb).
@@ -89,12 +83,21 @@ struct GemmTile {
 // tcgen05 split-BF16 x3 grouped GEMM.  Operand images: A tile (mt, kt) at
 // a_img + (mt * ktiles + kt) * 8192 bf16 elements (128 rows x 64 k, 128B
 // swizzled), B tile (nt, kt) likewise with n rows.  C row-major fp32.
+// The images are made from FP32 row-major matrices by the pack kernel, one
+// PackTile per image tile: rows [128 mt, 128 mt + 128) and columns
+// [64 kt, 64 kt + 64) of the rows x cols matrix at src (row stride ld),
+// zero outside it, written as the hi and lo images of tile (mt, kt) of the
+// operand image at img (ktiles tiles per row tile).
 struct TcSector {
   int32_t m, n, k, ktiles;
   int64_t a_img, b_img;
   int64_t c_off;
   int32_t ldc;
   float alpha;
+};
+struct PackTile {
+  int64_t src, img;
+  int32_t rows, cols, ld, ktiles, mt, kt;
 };
 
 // CUDA-core GEMM tile shapes
@@ -109,6 +112,7 @@ int launch_gemm_simt(bool f64, int shape, const GemmSectorSimt* secs, const Gemm
 int launch_gemm_tc(const TcSector* secs, const GemmTile* tiles, int ntiles, const uint16_t* a_hi,
                    const uint16_t* a_lo, const uint16_t* b_hi, const uint16_t* b_lo, float* C,
                    int* err_word, void* stream);
+int launch_pack(const PackTile* tiles, int ntiles, const float* lin, uint16_t* hi, uint16_t* lo, void* stream);
 int tc_num_sms();
 
 }  // namespace sym

@@ -87,6 +87,7 @@ extern "C" int sym_contract_noalloc(sym_tensor A, sym_tensor B, int npairs, cons
     const size_t o_simt = region(p.secs_simt.size() * sizeof(GemmSectorSimt));
     const size_t o_tc = region(p.secs_tc.size() * sizeof(TcSector));
     const size_t o_tiles = region(p.tiles.size() * sizeof(GemmTile));
+    const size_t o_packs = region(p.packs.size() * sizeof(PackTile));
     const size_t o_err = region(sizeof(int));
     const size_t o_hi = region((size_t)p.img_elems * 2);
     const size_t o_lo = region((size_t)p.img_elems * 2);
@@ -113,15 +114,16 @@ extern "C" int sym_contract_noalloc(sym_tensor A, sym_tensor B, int npairs, cons
     copy(o_simt, p.secs_simt.data(), p.secs_simt.size() * sizeof(GemmSectorSimt));
     copy(o_tc, p.secs_tc.data(), p.secs_tc.size() * sizeof(TcSector));
     copy(o_tiles, p.tiles.data(), p.tiles.size() * sizeof(GemmTile));
-    // the array keeps the previous call's contents: clear what must start at zero
+    copy(o_packs, p.packs.data(), p.packs.size() * sizeof(PackTile));
+    // the array keeps the previous call's contents: clear what must start at
+    // zero (the pack kernel writes every image element, padding included)
     zero(o_err, sizeof(int));
-    zero(o_hi, (size_t)p.img_elems * 2);  // image padding feeds the tensor cores
-    zero(o_lo, (size_t)p.img_elems * 2);
     p.d_items = reinterpret_cast<BoxItem*>(base + o_items);
     p.d_terms = reinterpret_cast<Term*>(base + o_terms);
     p.d_secs_simt = reinterpret_cast<GemmSectorSimt*>(base + o_simt);
     p.d_secs_tc = reinterpret_cast<TcSector*>(base + o_tc);
     p.d_tiles = reinterpret_cast<GemmTile*>(base + o_tiles);
+    p.d_packs = reinterpret_cast<PackTile*>(base + o_packs);
     p.d_err = reinterpret_cast<int*>(base + o_err);
     p.img_hi = base + o_hi;
     p.img_lo = base + o_lo;

@@ -91,13 +91,11 @@ void div_magic(int d, uint32_t& m, int8_t& s) {
   s = (int8_t)l;
 }
 
-BoxItem make_item(const Box& box, int64_t dst_off, int dst_ld, int row0, int col0, int sel, int term0,
+BoxItem make_item(const Box& box, int64_t dst_off, int dst_ld, int sel, int term0,
                   const std::vector<Term>& terms) {
   BoxItem it{};
   it.dst_off = dst_off;
   it.dst_ld = dst_ld;
-  it.row0 = row0;
-  it.col0 = col0;
   it.sel = sel;
   it.ndim = box.ndim;
   it.term0 = term0;
@@ -128,16 +126,15 @@ BoxItem make_item(const Box& box, int64_t dst_off, int dst_ld, int row0, int col
 // not the destination's, the box is cut into 32 x 32 transposing tiles over
 // (destination-contiguous dim, source-contiguous dim); otherwise into linear
 // chunks of kChunk elements.
-void emit(Plan& P, const Box& box0, int64_t dst_off, int dst_ld, int row0, int col0, int src_slot, int dst_slot,
+void emit(Plan& P, const Box& box0, int64_t dst_off, int dst_ld, int src_slot, int dst_slot,
           const std::vector<Term>& terms0) {
   int sel = src_slot | (dst_slot << 4);
-  const bool image = (sel & kSelImage) != 0;
   // Flat form: with at most one term and a linear destination, fold the
   // two-part offsets (ld * a + b) into one stride per dim on each side when
   // every offset of the box stays below 2^31.
   Box box = box0;
   std::vector<Term> terms = terms0;
-  if (!image && terms.size() <= 1) {
+  if (terms.size() <= 1) {
     const int64_t ld0 = terms.empty() ? 0 : terms[0].ld;
     Box f;
     int64_t sspan = 0, dspan = 0;
@@ -168,7 +165,7 @@ void emit(Plan& P, const Box& box0, int64_t dst_off, int dst_ld, int row0, int c
   const int64_t ld0 = terms.empty() ? 1 : terms[0].ld;
   auto src_stride = [&](int d) { return ld0 * box.sa[d] + box.sb[d]; };
   auto dst_unit = [&](int d) {
-    return image ? (box.db[d] == 1 && box.da[d] == 0) : ((int64_t)dst_ld * box.da[d] + box.db[d] == 1);
+    return (int64_t)dst_ld * box.da[d] + box.db[d] == 1;
   };
   const int q = box.ndim - 1;
   int pdim = -1;
@@ -189,7 +186,7 @@ void emit(Plan& P, const Box& box0, int64_t dst_off, int dst_ld, int row0, int c
     for (int tp = 0; tp < Pd; tp += 32)
       for (int tq = 0; tq < Qd; tq += 32)
         for (int64_t o = 0; o < outer; o += per) {
-          BoxItem it = make_item(t, dst_off, dst_ld, row0, col0, sel | kSelTile, term0, terms);
+          BoxItem it = make_item(t, dst_off, dst_ld, sel | kSelTile, term0, terms);
           it.start = (int)o;
           it.count = (int)std::min<int64_t>(per, outer - o);
           it.p0 = tp;
@@ -199,7 +196,7 @@ void emit(Plan& P, const Box& box0, int64_t dst_off, int dst_ld, int row0, int c
     return;
   }
   for (int64_t st = 0; st < total; st += kChunk) {
-    BoxItem it = make_item(box, dst_off, dst_ld, row0, col0, sel, term0, terms);
+    BoxItem it = make_item(box, dst_off, dst_ld, sel, term0, terms);
     it.start = (int)st;
     it.count = (int)std::min<int64_t>(kChunk, total - st);
     P.items.push_back(it);
@@ -444,7 +441,7 @@ void Plan::validate(const int64_t* src_elems, const int64_t* dst_elems) const {
       if (m != it.mag[d] || sh != it.shf[d]) fail(SYM_ERR_ARG, "internal: stale division constants in a work item");
     }
     if (sa >= ((int64_t)1 << 31) || sb >= ((int64_t)1 << 31) || da >= ((int64_t)1 << 31) ||
-        db >= ((int64_t)1 << 31) || it.row0 + da >= ((int64_t)1 << 31) || it.col0 + db >= ((int64_t)1 << 31))
+        db >= ((int64_t)1 << 31))
       fail(SYM_ERR_UNSUPPORTED, "internal: box offsets beyond 32 bits");
     for (int d = it.ndim; d < kMaxDim; ++d) {
       uint32_t m;
@@ -456,7 +453,7 @@ void Plan::validate(const int64_t* src_elems, const int64_t* dst_elems) const {
     if ((it.sel & kSelUnit) && (it.nterm != 1 || it.t0_coef != 1.0 || it.t0_coef_f != 1.0f))
       fail(SYM_ERR_ARG, "internal: unit flag on a work item whose coefficient is not 1");
     if (it.sel & kSelFlat) {
-      if ((it.sel & kSelImage) || it.nterm > 1 || it.dst_ld != 1 || (it.nterm == 1 && (it.t0_ld != 1 || terms[it.term0].ld != 1)))
+      if (it.nterm > 1 || it.dst_ld != 1 || (it.nterm == 1 && (it.t0_ld != 1 || terms[it.term0].ld != 1)))
         fail(SYM_ERR_ARG, "internal: flat work item with a two-part offset");
       for (int d = 0; d < it.ndim; ++d)
         if (it.sb[d] != 0 || it.db[d] != 0) fail(SYM_ERR_ARG, "internal: flat work item with a two-part offset");
@@ -477,16 +474,7 @@ void Plan::validate(const int64_t* src_elems, const int64_t* dst_elems) const {
       if (t.off < 0 || t.ld < 0 || t.off + t.ld * sa + sb >= src_elems[ss])
         fail(SYM_ERR_ARG, "internal: work item reads past its source buffer");
     }
-    int64_t last;
-    if (it.sel & kSelImage) {
-      if (ds != DST_IMAGE) fail(SYM_ERR_ARG, "internal: image item outside the image slot");
-      const int64_t row = it.row0 + da, col = it.col0 + db;
-      if (it.row0 < 0 || it.col0 < 0 || (col >> 6) >= it.dst_ld)
-        fail(SYM_ERR_ARG, "internal: image column past its K tiles");
-      last = it.dst_off + ((row >> 7) * it.dst_ld + (col >> 6)) * 8192 + 8191;
-    } else {
-      last = it.dst_off + (int64_t)it.dst_ld * da + db;
-    }
+    const int64_t last = it.dst_off + (int64_t)it.dst_ld * da + db;
     if (it.dst_off < 0 || last >= dst_elems[ds]) fail(SYM_ERR_ARG, "internal: work item writes past its destination");
   }
 }
@@ -525,6 +513,12 @@ void Plan::upload(bool device) {
   // finish the statistics tables (prefix sums)
   if (item_bytes_prefix.size() != items.size() + 1) item_bytes_prefix.assign(items.size() + 1, 0.0);
   for (size_t i = 0; i < items.size(); ++i) item_bytes_prefix[i + 1] += item_bytes_prefix[i];
+  pack_bytes_prefix.assign(packs.size() + 1, 0.0);
+  for (size_t i = 0; i < packs.size(); ++i) {  // FP32 read once, hi + lo tile written (padding included)
+    const PackTile& t = packs[i];
+    const double r = std::min(128, t.rows - 128 * t.mt), c = std::min(64, t.cols - 64 * t.kt);
+    pack_bytes_prefix[i + 1] = pack_bytes_prefix[i] + 4.0 * r * c + 4.0 * 128 * 64;
+  }
   flat_prefix.assign(items.size() + 1, 0);
   for (size_t i = 0; i < items.size(); ++i)
     flat_prefix[i + 1] = flat_prefix[i] + ((items[i].sel & (kSelFlat | kSelTile)) == kSelFlat ? 1 : 0);
@@ -564,11 +558,12 @@ void Plan::upload(bool device) {
   d_secs_simt = static_cast<GemmSectorSimt*>(up(secs_simt.data(), secs_simt.size() * sizeof(GemmSectorSimt)));
   d_secs_tc = static_cast<TcSector*>(up(secs_tc.data(), secs_tc.size() * sizeof(TcSector)));
   d_tiles = static_cast<GemmTile*>(up(tiles.data(), tiles.size() * sizeof(GemmTile)));
+  d_packs = static_cast<PackTile*>(up(packs.data(), packs.size() * sizeof(PackTile)));
   if (kind == CONTRACT) {
     const size_t es = f64() ? sizeof(double) : sizeof(float);
-    if (img_elems > 0) {
-      img_hi = arena.alloc(img_elems * 2, true);  // zero padding of the images
-      img_lo = arena.alloc(img_elems * 2, true);
+    if (img_elems > 0) {  // every image element, padding included, is written by the pack kernel
+      img_hi = arena.alloc(img_elems * 2, false);
+      img_lo = arena.alloc(img_elems * 2, false);
     }
     lin = arena.alloc(lin_elems * es, false);
     outm = arena.alloc(outm_elems * es, false);
@@ -662,7 +657,7 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
         }
         b.push(d, sst, 0, ost[pinv[l]], 0);
       }
-      emit(*P, b, out.offs[s], 1, 0, 0, 0, 1, terms);
+      emit(*P, b, out.offs[s], 1, 0, DST_OUT, terms);
     }
   } else if (mode == 1) {
     const int f = leg;
@@ -701,7 +696,7 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
         int dst = l < f ? ost[l] : l == f ? db_ * ost[f] : l == f + 1 ? ost[f] : ost[l - 1];
         b.push(d, ist[l], 0, dst, 0);
       }
-      emit(*P, b, out.offs[so] + row0 * ost[f], 1, 0, 0, 0, 1, terms);
+      emit(*P, b, out.offs[so] + row0 * ost[f], 1, 0, DST_OUT, terms);
     }
   } else {
     const int f = leg;  // out legs f, f+1 come from in leg f
@@ -761,7 +756,7 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
       }
       Box b;
       for (int l = 0; l < ko; ++l) b.push(out.dim(s, l), sa_[l], sb_[l], ost[l], 0);
-      emit(*P, b, out.offs[s], 1, 0, 0, 0, 1, terms);
+      emit(*P, b, out.offs[s], 1, 0, DST_OUT, terms);
     }
   }
   P->xform = {0, (int)P->items.size()};
@@ -771,7 +766,7 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
   }
   {
     const int64_t src[4] = {in.numel(), 0, 0, 0};
-    const int64_t dst[DST_COUNT] = {0, out.numel(), 0, 0, 0, 0};
+    const int64_t dst[DST_COUNT] = {out.numel(), 0, 0, 0, 0};
     P->validate(src, dst);
   }
   P->upload();
@@ -880,8 +875,12 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     int x;
     int64_t m, n, k;
     int kind[3];
-    // operand offsets: images (bf16 elements) or linear (elements)
-    int64_t a, b, dc1, bt, at, dc2, dcl;
+    // linear FP32/FP64 operands (elements of `lin`): the gather writes these
+    int64_t a, b, bt, at, dcl, dct;
+    // split-BF16 images of the tcgen05 operands (bf16 elements), packed from
+    // the linear operands: forward a (m x k) and b (n x k, = B^T); dA dcl
+    // (m x n) and bt (k x n, = B); dB at (k x m) and dct (n x m, = dC^T)
+    int64_t ia, ib, idc1, ibt, iat, idc2;
     int64_t c, da, db;  // output matrices
     bool split[3];
   };
@@ -907,34 +906,61 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   }
   auto img = [&](int64_t rows, int64_t kk) { return cdiv(rows, 128) * cdiv(kk, 64) * 8192; };
   int64_t ie = 0, le = 0, oe = 0;
+  // forward operands: A (m x k); B as k x n, or as B^T (n x k) for the tensor cores
   for (auto& g : gs) {
+    g.a = le, le += g.m * g.k;
+    g.b = le, le += g.k * g.n;
     if (g.kind[0] == 0) {
-      g.a = ie, ie += img(g.m, g.k);
-      g.b = ie, ie += img(g.n, g.k);
-    } else {
-      g.a = le, le += g.m * g.k;
-      g.b = le, le += g.k * g.n;
+      g.ia = ie, ie += img(g.m, g.k);
+      g.ib = ie, ie += img(g.n, g.k);
     }
   }
+  // backward operands: dC (m x n) always; dA takes B^T (n x k), or B (k x n)
+  // for the tensor cores; dB takes A^T (k x m) and, on the tensor cores, dC^T
   for (auto& g : gs) {
+    g.dcl = le, le += g.m * g.n;
+    g.bt = le, le += g.n * g.k;
+    g.at = le, le += g.k * g.m;
     if (g.kind[1] == 0) {
-      g.dc1 = ie, ie += img(g.m, g.n);
-      g.bt = ie, ie += img(g.k, g.n);
-    } else {
-      g.bt = le, le += g.n * g.k;
+      g.idc1 = ie, ie += img(g.m, g.n);
+      g.ibt = ie, ie += img(g.k, g.n);
     }
     if (g.kind[2] == 0) {
-      g.at = ie, ie += img(g.k, g.m);
-      g.dc2 = ie, ie += img(g.n, g.m);
-    } else {
-      g.at = le, le += g.k * g.m;
+      g.dct = le, le += g.n * g.m;
+      g.iat = ie, ie += img(g.k, g.m);
+      g.idc2 = ie, ie += img(g.n, g.m);
     }
-    if (g.kind[1] != 0 || g.kind[2] != 0) g.dcl = le, le += g.m * g.n;
   }
   for (auto& g : gs) {
     g.c = oe, oe += g.m * g.n;
     g.da = oe, oe += g.m * g.k;
     g.db = oe, oe += g.k * g.n;
+  }
+  // pack lists, one per GEMM phase: image tiles of every tcgen05 operand
+  std::vector<PackTile> packs[3];
+  auto add_pack = [&](int ph, int64_t src, int64_t rows, int64_t cols, int64_t im) {
+    const int64_t kt = cdiv(cols, 64);
+    for (int64_t mt = 0; mt < cdiv(rows, 128); ++mt)
+      for (int64_t t = 0; t < kt; ++t)
+        packs[ph].push_back(PackTile{src, im, (int)rows, (int)cols, (int)cols, (int)kt, (int)mt, (int)t});
+  };
+  for (auto& g : gs) {
+    if (g.kind[0] == 0) {
+      add_pack(0, g.a, g.m, g.k, g.ia);
+      add_pack(0, g.b, g.n, g.k, g.ib);
+    }
+    if (g.kind[1] == 0) {
+      add_pack(1, g.dcl, g.m, g.n, g.idc1);
+      add_pack(1, g.bt, g.k, g.n, g.ibt);
+    }
+    if (g.kind[2] == 0) {
+      add_pack(2, g.at, g.k, g.m, g.iat);
+      add_pack(2, g.dct, g.n, g.m, g.idc2);
+    }
+  }
+  for (int ph = 0; ph < 3; ++ph) {
+    P->pack_range[ph] = Range{(int)P->packs.size(), (int)packs[ph].size()};
+    P->packs.insert(P->packs.end(), packs[ph].begin(), packs[ph].end());
   }
   P->img_elems = ie;
   P->lin_elems = le;
@@ -987,9 +1013,10 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     return nsplit > 1;
   };
   for (auto& g : gs) {
-    g.split[0] = add_gemm(g.kind[0], 0, g.m, g.n, g.k, g.a, g.k, g.b, g.n, g.c);
-    g.split[1] = add_gemm(g.kind[1], 1, g.m, g.k, g.n, g.kind[1] == 0 ? g.dc1 : g.dcl, g.n, g.bt, g.k, g.da);
-    g.split[2] = add_gemm(g.kind[2], 2, g.k, g.n, g.m, g.at, g.m, g.kind[2] == 0 ? g.dc2 : g.dcl, g.n, g.db);
+    const bool t0 = g.kind[0] == 0, t1 = g.kind[1] == 0, t2 = g.kind[2] == 0;
+    g.split[0] = add_gemm(g.kind[0], 0, g.m, g.n, g.k, t0 ? g.ia : g.a, g.k, t0 ? g.ib : g.b, g.n, g.c);
+    g.split[1] = add_gemm(g.kind[1], 1, g.m, g.k, g.n, t1 ? g.idc1 : g.dcl, g.n, t1 ? g.ibt : g.bt, g.k, g.da);
+    g.split[2] = add_gemm(g.kind[2], 2, g.k, g.n, g.m, t2 ? g.iat : g.at, g.m, t2 ? g.idc2 : g.dcl, g.n, g.db);
   }
   for (int kind = 0; kind < kGemmKinds; ++kind)
     for (int ph = 0; ph < 3; ++ph) {
@@ -1025,20 +1052,15 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     for (auto& pc : tl) t.push_back({S.offs[pc.first], 1, pc.second});
     return t;
   };
-  // operand written either as an image (rows, K-tiles) or as a linear matrix
-  auto put = [&](const Box& b, int src, bool image, int64_t off, int64_t kk, int64_t row0, int64_t col0,
-                 int64_t ld, const std::vector<Term>& t) {
-    if (image)
-      emit(*P, b, off, (int)cdiv(kk, 64), (int)row0, (int)col0, src, DST_IMAGE | (kSelImage >> 4), t);
-    else
-      emit(*P, b, off + row0 * ld + col0, (int)ld, 0, 0, src, DST_OPS, t);
-  };
+  // operand block written into a linear matrix (row stride ld) at (row0, col0)
+  auto put = [&](const Box& b, int src, int64_t off, int64_t row0, int64_t col0, int64_t ld,
+                 const std::vector<Term>& t) { emit(*P, b, off + row0 * ld + col0, (int)ld, src, DST_OPS, t); };
   // zero-fill of an output matrix before a split-K GEMM adds into it
   auto zero_fill = [&](int64_t off, int64_t rows, int64_t cols) {
     Box b;
     b.push((int)rows, 0, 0, 1, 0);
     b.push((int)cols, 0, 0, 0, 1);
-    emit(*P, b, off, (int)cols, 0, 0, 3, DST_OUTM, {});
+    emit(*P, b, off, (int)cols, 3, DST_OUTM, {});
   };
 
   // ---- forward gather: A -> A operand, B -> B operand (+ zero fills)
@@ -1048,18 +1070,18 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     if (gi == gofx.end() || XA[s].empty()) continue;
     const G& g = gs[gi->second];
     Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, false);
-    put(b, 0, g.kind[0] == 0, g.a, g.k, MA.r0[s], MA.c0[s], g.k, terms_of(XA[s], A));
+    put(b, 0, g.a, MA.r0[s], MA.c0[s], g.k, terms_of(XA[s], A));
   }
   for (int64_t s = 0; s < Bm.nsec(); ++s) {
     auto gi = gofx.find(MB.xs[MB.sx[s]]);
     if (gi == gofx.end() || XB[s].empty()) continue;
     const G& g = gs[gi->second];
-    if (g.kind[0] == 0) {  // image rows n (free), K = k (contracted)
+    if (g.kind[0] == 0) {  // B^T (n x k): image rows n (free), K = k (contracted)
       Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, true);
-      put(b, 1, true, g.b, g.k, MB.c0[s], MB.r0[s], 0, terms_of(XB[s], B));
+      put(b, 1, g.b, MB.c0[s], MB.r0[s], g.k, terms_of(XB[s], B));
     } else {
       Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, false);
-      put(b, 1, false, g.b, 0, MB.r0[s], MB.c0[s], g.n, terms_of(XB[s], B));
+      put(b, 1, g.b, MB.r0[s], MB.c0[s], g.n, terms_of(XB[s], B));
     }
   }
   for (auto& g : gs)
@@ -1088,11 +1110,11 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     block_strides(C, s, st);
     Box b;
     for (int l = 0; l < C.rank; ++l) b.push(C.dim(s, l), rw[l], cw[l], st[l], 0);
-    emit(*P, b, C.offs[s], 1, 0, 0, 3, DST_OUT, t);
+    emit(*P, b, C.offs[s], 1, 3, DST_OUT, t);
   }
   P->fwd_scatter = {begin, (int)P->items.size() - begin};
 
-  // ---- backward gathers: [dA only: B^T, dC image][shared: dC linear][dB only: A^T, dC image]
+  // ---- backward gathers: [dA only: B or B^T][shared: dC][dB only: A^T, dC^T]
   std::vector<int> idC(C.rank);
   for (int i = 0; i < C.rank; ++i) idC[i] = i;
   auto dc_terms = [&](int64_t sn) {
@@ -1118,45 +1140,35 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     auto gi = gofx.find(MB.xs[MB.sx[s]]);
     if (gi == gofx.end() || XB[s].empty()) continue;
     const G& g = gs[gi->second];
-    if (g.kind[1] == 0) {  // image rows k (contracted), K = n (free)
+    if (g.kind[1] == 0) {  // B (k x n): image rows k (contracted), K = n (free)
       Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, false);
-      put(b, 1, true, g.bt, g.n, MB.r0[s], MB.c0[s], 0, terms_of(XB[s], B));
-    } else {  // linear B^T (n x k)
+      put(b, 1, g.bt, MB.r0[s], MB.c0[s], g.n, terms_of(XB[s], B));
+    } else {  // B^T (n x k)
       Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, true);
-      put(b, 1, false, g.bt, 0, MB.c0[s], MB.r0[s], g.k, terms_of(XB[s], B));
+      put(b, 1, g.bt, MB.c0[s], MB.r0[s], g.k, terms_of(XB[s], B));
     }
   }
-  for_dc([&](const G& g, int64_t sn, int64_t r0, int64_t c0) {
-    if (g.kind[1] != 0) return;
-    auto t = dc_terms(sn);
-    if (t.empty()) return;
-    put(gather_box(Cn, idC, Cn, sn, sn, na, false), 2, true, g.dc1, g.n, r0, c0, 0, t);
-  });
   for (auto& g : gs)
     if (g.split[1]) zero_fill(g.da, g.m, g.k);
   const int b1 = (int)P->items.size();
-  for_dc([&](const G& g, int64_t sn, int64_t r0, int64_t c0) {
-    if (g.kind[1] == 0 && g.kind[2] == 0) return;
+  for_dc([&](const G& g, int64_t sn, int64_t r0, int64_t c0) {  // dC (m x n), both gradients
     auto t = dc_terms(sn);
     if (t.empty()) return;
-    put(gather_box(Cn, idC, Cn, sn, sn, na, false), 2, false, g.dcl, 0, r0, c0, g.n, t);
+    put(gather_box(Cn, idC, Cn, sn, sn, na, false), 2, g.dcl, r0, c0, g.n, t);
   });
   const int b2 = (int)P->items.size();
-  for (int64_t s = 0; s < Am.nsec(); ++s) {
+  for (int64_t s = 0; s < Am.nsec(); ++s) {  // A^T (k x m)
     auto gi = gofx.find(MA.xs[MA.sx[s]]);
     if (gi == gofx.end() || XA[s].empty()) continue;
     const G& g = gs[gi->second];
     Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, true);
-    if (g.kind[2] == 0)  // image rows k (contracted), K = m (free)
-      put(b, 0, true, g.at, g.m, MA.c0[s], MA.r0[s], 0, terms_of(XA[s], A));
-    else  // linear A^T (k x m)
-      put(b, 0, false, g.at, 0, MA.c0[s], MA.r0[s], g.m, terms_of(XA[s], A));
+    put(b, 0, g.at, MA.c0[s], MA.r0[s], g.m, terms_of(XA[s], A));
   }
-  for_dc([&](const G& g, int64_t sn, int64_t r0, int64_t c0) {
+  for_dc([&](const G& g, int64_t sn, int64_t r0, int64_t c0) {  // dC^T (n x m) for the tensor cores
     if (g.kind[2] != 0) return;
     auto t = dc_terms(sn);
     if (t.empty()) return;
-    put(gather_box(Cn, idC, Cn, sn, sn, na, true), 2, true, g.dc2, g.m, c0, r0, 0, t);
+    put(gather_box(Cn, idC, Cn, sn, sn, na, true), 2, g.dct, c0, r0, g.m, t);
   });
   for (auto& g : gs)
     if (g.split[2]) zero_fill(g.db, g.k, g.n);
@@ -1184,7 +1196,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
       int n = pinvA[l];
       b.push(A.dim(s, l), sm0 >= 0 ? rw[n] : 0, sm0 >= 0 ? cw[n] : 0, st[l], 0);
     }
-    emit(*P, b, A.offs[s], 1, 0, 0, 3, DST_DA, t);
+    emit(*P, b, A.offs[s], 1, 3, DST_DA, t);
   }
   P->bwd_scatter_a = {begin, (int)P->items.size() - begin};
   begin = (int)P->items.size();
@@ -1206,17 +1218,16 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
       int n = pinvB[l];
       b.push(B.dim(s, l), sm0 >= 0 ? rw[n] : 0, sm0 >= 0 ? cw[n] : 0, st[l], 0);
     }
-    emit(*P, b, B.offs[s], 1, 0, 0, 3, DST_DB, t);
+    emit(*P, b, B.offs[s], 1, 3, DST_DB, t);
   }
   P->bwd_scatter_b = {begin, (int)P->items.size() - begin};
   {
     const int es = f64 ? 8 : 4;
     P->set_item_bytes({0, (int)P->items.size()}, es, es);
-    // image items write hi + lo bf16 = 4 bytes per element, as fp32
   }
   {
     const int64_t src[4] = {A.numel(), B.numel(), C.numel(), P->outm_elems};
-    const int64_t dst[DST_COUNT] = {P->img_elems, C.numel(), A.numel(), B.numel(), P->lin_elems, P->outm_elems};
+    const int64_t dst[DST_COUNT] = {C.numel(), A.numel(), B.numel(), P->lin_elems, P->outm_elems};
     P->validate(src, dst);
   }
   // GEMM tiles stay inside their operand buffers
@@ -1236,6 +1247,14 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
           s.c_off + (int64_t)(s.m - 1) * s.ldc + s.n - 1 >= P->outm_elems || s.ktiles < 1)
         fail(SYM_ERR_ARG, "internal: tcgen05 GEMM tile past its buffers");
     }
+  }
+  // pack tiles read inside the FP32 operands and write inside the images
+  for (const PackTile& t : P->packs) {
+    if (f64 || t.rows < 1 || t.cols < 1 || t.ld < t.cols || t.src < 0 || t.mt < 0 || t.kt < 0 ||
+        (int64_t)t.mt * 128 >= t.rows || t.ktiles != cdiv(t.cols, 64) || t.kt >= t.ktiles ||
+        t.src + (int64_t)(t.rows - 1) * t.ld + t.cols - 1 >= P->lin_elems || t.img < 0 ||
+        t.img + ((int64_t)t.mt * t.ktiles + t.kt + 1) * 8192 > P->img_elems)
+      fail(SYM_ERR_ARG, "internal: operand pack tile past its buffers");
   }
   P->upload(device);
   return P;
@@ -1290,8 +1309,20 @@ int run_box(Plan& p, Range r, const BoxPtrs& ptrs, void* stream, int phase) {
                    "box kernel");
 }
 
-int run_gemm_kind(Plan& p, int kind, Range r, void* stream, int phase) {
+// tcgen05 operand images of the pack range `pk`, then (same stream) the GEMM
+int run_pack(Plan& p, Range pk, void* stream) {
+  if (pk.count <= 0) return SYM_OK;
+  p.last_launches++;
+  ProfScope ps(p, PH_PACK, stream, p.pack_bytes_prefix[pk.first + pk.count] - p.pack_bytes_prefix[pk.first], 0.0);
+  return cuda_code(launch_pack(p.d_packs + pk.first, pk.count, static_cast<const float*>(p.lin),
+                               static_cast<uint16_t*>(p.img_hi), static_cast<uint16_t*>(p.img_lo), stream),
+                   "operand pack");
+}
+
+int run_gemm_kind(Plan& p, int kind, Range r, Range pk, void* stream, int phase) {
   if (r.count <= 0) return SYM_OK;
+  if (kind == 0)
+    if (int rc = run_pack(p, pk, stream)) return rc;
   p.last_launches++;
   if (kind != 0) phase = phase == PH_FWD_GEMM ? PH_FWD_GEMM_SIMT : PH_BWD_GEMM_SIMT;
   ProfScope ps(p, phase, stream, 0.0, p.tile_flops_prefix[r.first + r.count] - p.tile_flops_prefix[r.first]);
@@ -1313,6 +1344,8 @@ int run_gemm(Plan& p, int ph0, int ph1, void* stream, int phase) {
   int kinds[kGemmKinds];
   Range rs[kGemmKinds];
   int n = 0;
+  Range pk{p.pack_range[ph0].first, 0};
+  for (int ph = ph0; ph <= ph1; ++ph) pk.count += p.pack_range[ph].count;
   for (int kind = 0; kind < kGemmKinds; ++kind) {
     Range r{p.gemm_range[kind][ph0].first, 0};
     for (int ph = ph0; ph <= ph1; ++ph) r.count += p.gemm_range[kind][ph].count;
@@ -1323,7 +1356,7 @@ int run_gemm(Plan& p, int ph0, int ph1, void* stream, int phase) {
   }
   if (n <= 1 || !p.concurrent) {
     for (int i = 0; i < n; ++i)
-      if (int rc = run_gemm_kind(p, kinds[i], rs[i], stream, phase)) return rc;
+      if (int rc = run_gemm_kind(p, kinds[i], rs[i], pk, stream, phase)) return rc;
     return SYM_OK;
   }
   cudaStream_t s0 = static_cast<cudaStream_t>(stream);
@@ -1351,9 +1384,9 @@ int run_gemm(Plan& p, int ph0, int ph1, void* stream, int phase) {
   for (int i = 0; i < n - 1; ++i)
     check(cudaStreamWaitEvent(static_cast<cudaStream_t>(p.side[i]), static_cast<cudaEvent_t>(p.ev_fork), 0),
           "cudaStreamWaitEvent");
-  int rc = run_gemm_kind(p, kinds[0], rs[0], stream, phase);
+  int rc = run_gemm_kind(p, kinds[0], rs[0], pk, stream, phase);
   for (int i = 1; i < n; ++i) {
-    const int r = run_gemm_kind(p, kinds[i], rs[i], p.side[i - 1], phase);
+    const int r = run_gemm_kind(p, kinds[i], rs[i], pk, p.side[i - 1], phase);
     if (!rc) rc = r;
   }
   // join every side stream, also after a failed launch
@@ -1370,10 +1403,8 @@ BoxPtrs gather_ptrs(Plan& p, const void* A, const void* B, const void* dC) {
   g.src[1] = B;
   g.src[2] = dC;
   g.src[3] = p.outm;
-  g.dst[DST_IMAGE][0] = p.img_hi;
-  g.dst[DST_IMAGE][1] = p.img_lo;
-  g.dst[DST_OPS][0] = p.lin;
-  g.dst[DST_OUTM][0] = p.outm;
+  g.dst[DST_OPS] = p.lin;
+  g.dst[DST_OUTM] = p.outm;
   return g;
 }
 
@@ -1384,7 +1415,7 @@ int exec_transform(Plan& p, const void* in, void* out, void* stream) {
   p.last_launches = 0;
   BoxPtrs ptrs{};
   ptrs.src[0] = in;
-  ptrs.dst[DST_OUT][0] = out;
+  ptrs.dst[DST_OUT] = out;
   return run_box(p, p.xform, ptrs, stream, PH_XFORM);
 }
 
@@ -1398,7 +1429,7 @@ int exec_contract(Plan& p, const void* A, const void* B, void* C, void* stream) 
   if (rc) return rc;
   BoxPtrs s{};
   s.src[3] = p.outm;
-  s.dst[DST_OUT][0] = C;
+  s.dst[DST_OUT] = C;
   return run_box(p, p.fwd_scatter, s, stream, PH_FWD_SCATTER);
 }
 
@@ -1422,8 +1453,8 @@ int exec_contract_backward(Plan& p, const void* A, const void* B, const void* dC
   if (rc) return rc;
   BoxPtrs s{};
   s.src[3] = p.outm;
-  s.dst[DST_DA][0] = dA;
-  s.dst[DST_DB][0] = dB;
+  s.dst[DST_DA] = dA;
+  s.dst[DST_DB] = dB;
   Range sr;
   if (dA && dB)
     sr = {p.bwd_scatter_a.first, p.bwd_scatter_a.count + p.bwd_scatter_b.count};

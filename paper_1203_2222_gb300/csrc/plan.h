@@ -22,7 +22,7 @@ struct DeviceArena {
 
 // Phases of a plan's launches (profiling and statistics).
 enum Phase { PH_FWD_GATHER = 0, PH_FWD_GEMM, PH_FWD_SCATTER, PH_BWD_GATHER, PH_BWD_GEMM, PH_BWD_SCATTER,
-             PH_XFORM, PH_FWD_GEMM_SIMT, PH_BWD_GEMM_SIMT, PH_COUNT };
+             PH_XFORM, PH_FWD_GEMM_SIMT, PH_BWD_GEMM_SIMT, PH_PACK, PH_COUNT };
 constexpr int kGemmKinds = 5;  // 0 tcgen05, CUDA cores: 1 tile 64x64, 2 tile 256x16, 3 thin, 4 rows
 
 struct PhaseProfile {
@@ -54,6 +54,8 @@ struct Plan {
   std::vector<GemmTile> tiles;  // grouped by kind, then by GEMM phase
   Range gemm_range[kGemmKinds][3];  // [kind][gemm phase]
   std::vector<int> tile_kind;   // kind of every tile (statistics)
+  std::vector<PackTile> packs;  // image tiles of the tcgen05 operands
+  Range pack_range[3];          // [gemm phase]
 
   // scratch sizes (elements): split-BF16 images, linear operands, output matrices
   int64_t img_elems = 0, lin_elems = 0, outm_elems = 0;
@@ -68,6 +70,7 @@ struct Plan {
   // as prefix sums (launch statistics for any range in O(1))
   std::vector<double> item_bytes_prefix, tile_flops_prefix;
   std::vector<int> flat_prefix;  // flat linear items among the first i (launch variant choice)
+  std::vector<double> pack_bytes_prefix;
   void set_item_bytes(Range r, int es_src, int es_dst);
   bool profiling = false;
   PhaseProfile prof[PH_COUNT];
@@ -81,6 +84,7 @@ struct Plan {
   GemmSectorSimt* d_secs_simt = nullptr;
   TcSector* d_secs_tc = nullptr;
   GemmTile* d_tiles = nullptr;
+  PackTile* d_packs = nullptr;
   void* img_hi = nullptr;  // bf16 hi images
   void* img_lo = nullptr;  // bf16 lo images
   void* lin = nullptr;     // linear operands (fp32 or fp64)
