@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "pdl.h"
 
 namespace sym {
 namespace {
@@ -345,6 +346,8 @@ __global__ void __launch_bounds__(kThreads, kFlat ? 8 : (sizeof(TD) == 4 ? 5 : 4
   if (item >= nitems) return;
   const int64_t* words = reinterpret_cast<const int64_t*>(items);
   int64_t word = lane < kItemWords ? __ldg(words + (int64_t)item * kItemWords + lane) : 0;
+  pdl_wait();  // the descriptors are plan constants; the data is not
+  pdl_launch_dependents();
   const BoxItem& it = *reinterpret_cast<const BoxItem*>(raw[w]);
   for (; item < nitems; item += nwarps) {
     if (lane < kItemWords) raw[w][lane] = word;
@@ -377,8 +380,7 @@ int launch_t(const BoxItem* items, int nitems, const Term* terms, const BoxPtrs&
   }
   const int warps = nitems < slots ? nitems : slots;
   const int grid = (warps + kWarps - 1) / kWarps;
-  box_kernel<TS, TD, kFlat><<<grid, kThreads, 0, s>>>(items, nitems, terms, ptrs);
-  return (int)cudaGetLastError();
+  return (int)launch_pdl(box_kernel<TS, TD, kFlat>, dim3(grid), dim3(kThreads), 0, s, items, nitems, terms, ptrs);
 }
 
 }  // namespace

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "pdl.h"
 
 namespace sym {
 namespace {
@@ -33,6 +34,8 @@ __global__ void __launch_bounds__(256) gemm_tile_kernel(const GemmSectorSimt* __
   __shared__ T Bs[KS][TN];
   const GemmTile tl = tiles[blockIdx.x];
   const GemmSectorSimt s = secs[tl.sector];
+  pdl_wait();
+  pdl_launch_dependents();
   const int m0 = tl.mt * TM, n0 = tl.nt * TN;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   T acc[RM][RN];
@@ -113,6 +116,8 @@ __global__ void __launch_bounds__(256) gemm_rows_kernel(const GemmSectorSimt* __
   __shared__ T Bs[16][17];
   const GemmTile tl = tiles[blockIdx.x];
   const GemmSectorSimt s = secs[tl.sector];
+  pdl_wait();
+  pdl_launch_dependents();
   const T* __restrict__ a = ops + s.a_off;
   const T* __restrict__ b = ops + s.b_off;
   for (int i = threadIdx.x; i < s.k * s.n; i += 256) Bs[i / s.n][i % s.n] = __ldg(b + (int64_t)(i / s.n) * s.ldb + i % s.n);
@@ -147,6 +152,8 @@ __global__ void __launch_bounds__(256) gemm_thin_kernel(const GemmSectorSimt* __
   __shared__ T red[8][MX * MX];
   const GemmTile tl = tiles[blockIdx.x];
   const GemmSectorSimt s = secs[tl.sector];
+  pdl_wait();
+  pdl_launch_dependents();
   const T* __restrict__ a = ops + s.a_off;
   const T* __restrict__ b = ops + s.b_off;
   T acc[MX][MX];
@@ -204,13 +211,13 @@ int launch_t(int shape, const GemmSectorSimt* secs, const GemmTile* tiles, int n
              cudaStream_t s) {
   const T* o = static_cast<const T*>(ops);
   T* c = static_cast<T*>(outm);
+  const dim3 g(ntiles), b(256);
   switch (shape) {
-    case SIMT_64x64: gemm_tile_kernel<T, 64, 64><<<ntiles, 256, 0, s>>>(secs, tiles, o, c); break;
-    case SIMT_256x16: gemm_tile_kernel<T, 256, 16><<<ntiles, 256, 0, s>>>(secs, tiles, o, c); break;
-    case SIMT_THIN: gemm_thin_kernel<T><<<ntiles, 256, 0, s>>>(secs, tiles, o, c); break;
-    default: gemm_rows_kernel<T><<<ntiles, 256, 0, s>>>(secs, tiles, o, c); break;
+    case SIMT_64x64: return (int)launch_pdl(gemm_tile_kernel<T, 64, 64>, g, b, 0, s, secs, tiles, o, c);
+    case SIMT_256x16: return (int)launch_pdl(gemm_tile_kernel<T, 256, 16>, g, b, 0, s, secs, tiles, o, c);
+    case SIMT_THIN: return (int)launch_pdl(gemm_thin_kernel<T>, g, b, 0, s, secs, tiles, o, c);
+    default: return (int)launch_pdl(gemm_rows_kernel<T>, g, b, 0, s, secs, tiles, o, c);
   }
-  return (int)cudaGetLastError();
 }
 
 }  // namespace

@@ -26,6 +26,7 @@
 
 #include "../../include/symtensor.h"
 #include "kernels.h"
+#include "pdl.h"
 
 namespace sym {
 namespace {
@@ -210,6 +211,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  pdl_wait();  // barriers and tensor memory are set up; operands and C belong to earlier kernels
+  pdl_launch_dependents();
 
   if (warp == 0) {
     if (lane == 0) {
@@ -350,6 +353,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 __global__ void __launch_bounds__(256) pack_kernel(const PackTile* __restrict__ tiles, const float* __restrict__ lin,
                                                    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
   const PackTile t = tiles[blockIdx.x];
+  pdl_wait();
+  pdl_launch_dependents();
   const int chunk = threadIdx.x & 7;
   const int c0 = t.kt * 64 + chunk * 8;
   const int64_t tile = t.img + ((int64_t)t.mt * t.ktiles + t.kt) * TILE_ELEMS;
@@ -401,17 +406,16 @@ int launch_gemm_tc(const TcSector* secs, const GemmTile* tiles, int ntiles, cons
     attr_set = true;
   }
   int grid = ntiles < tc_num_sms() ? ntiles : tc_num_sms();
-  gemm_tc_kernel<<<grid, NUM_THREADS, SMEM_BYTES, static_cast<cudaStream_t>(stream)>>>(
-      secs, tiles, ntiles, reinterpret_cast<const __nv_bfloat16*>(a_hi), reinterpret_cast<const __nv_bfloat16*>(a_lo),
-      reinterpret_cast<const __nv_bfloat16*>(b_hi), reinterpret_cast<const __nv_bfloat16*>(b_lo), C, err_word);
-  return (int)cudaGetLastError();
+  return (int)launch_pdl(gemm_tc_kernel, dim3(grid), dim3(NUM_THREADS), SMEM_BYTES, static_cast<cudaStream_t>(stream),
+                         secs, tiles, ntiles, reinterpret_cast<const __nv_bfloat16*>(a_hi),
+                         reinterpret_cast<const __nv_bfloat16*>(a_lo), reinterpret_cast<const __nv_bfloat16*>(b_hi),
+                         reinterpret_cast<const __nv_bfloat16*>(b_lo), C, err_word);
 }
 
 int launch_pack(const PackTile* tiles, int ntiles, const float* lin, uint16_t* hi, uint16_t* lo, void* stream) {
   if (ntiles <= 0) return 0;
-  pack_kernel<<<ntiles, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      tiles, lin, reinterpret_cast<__nv_bfloat16*>(hi), reinterpret_cast<__nv_bfloat16*>(lo));
-  return (int)cudaGetLastError();
+  return (int)launch_pdl(pack_kernel, dim3(ntiles), dim3(256), 0, static_cast<cudaStream_t>(stream), tiles, lin,
+                         reinterpret_cast<__nv_bfloat16*>(hi), reinterpret_cast<__nv_bfloat16*>(lo));
 }
 
 }  // namespace sym
