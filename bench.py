@@ -322,8 +322,7 @@ def run_ours(args, rank, world):
                 r = p.profile_read(ph)
                 if r["launches"] == 0:
                     continue
-                kern = ("gemm_tc" if "gemm_tc" in name else "gemm_cuda_cores" if "gemm" in name
-                        else "pack" if name == "pack" else "box")
+                kern = "gemm_tc" if "gemm_tc" in name else "gemm_cuda_cores" if "gemm" in name else "box"
                 d = prof.setdefault(kern, {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
                 for k in d:
                     d[k] += r[k]
@@ -428,12 +427,11 @@ def run_ours(args, rank, world):
                 "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x sampled SM clock"}
-    elif dom in ("box", "pack"):
+    elif dom == "box":
         d = prof[dom]
         achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
         peak = peaks["hbm_gbs"]
-        roof = {"bound": "hbm", "kernel": "box_kernel (block gathers/scatters)" if dom == "box"
-                else "pack_kernel (FP32 operands -> split-BF16 images)",
+        roof = {"bound": "hbm", "kernel": "box_kernel (block gathers/scatters)",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None, "peak_source": f"{peak_src} hbm_gbs"}
     if roof is not None:

@@ -189,7 +189,6 @@ int sym_plan_gemm_shapes(sym_plan plan, int* nsec, int* mnk);
 #define SYM_PHASE_TRANSFORM 6
 #define SYM_PHASE_FWD_GEMM_CUDA_CORES 7 /* forward sectors on the CUDA-core GEMMs */
 #define SYM_PHASE_BWD_GEMM_CUDA_CORES 8
-#define SYM_PHASE_PACK 9 /* FP32 operands -> split-BF16 tcgen05 images */
 int sym_plan_profile(sym_plan plan, int enable);
 int sym_plan_profile_read(sym_plan plan, int phase, int* launches,
                           double* total_ms, double* bytes, double* flops);

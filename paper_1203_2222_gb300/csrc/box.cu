@@ -20,6 +20,7 @@
 //    index: the warp reads it along the source-contiguous dim into its own
 //    shared-memory tile and writes it along the destination-contiguous dim.
 // Memory-bound: bytes = source read + destination written.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -108,19 +109,34 @@ struct Src {
   }
 };
 
+// split-BF16 store: hi = bf16(x) at h[o], lo = bf16(x - hi) at h[o + lo_off]
+__device__ __forceinline__ void store_split(__nv_bfloat16* h, int64_t lo_off, int64_t o, float x) {
+  const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+  h[o] = hi;
+  h[o + lo_off] = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
 // destination side of the general form: dst[off + ld * a + b]
 template <typename TD>
 struct Dst {
-  TD* p;
-  int64_t off, ld;
-  __device__ __forceinline__ void store(TD v, int a, int b) const { p[off + ld * a + b] = v; }
+  void* p;
+  int64_t off, ld, lo_off;
+  bool split;
+  __device__ __forceinline__ void store(TD v, int a, int b) const {
+    const int64_t o = off + ld * a + b;
+    if (split)
+      store_split(static_cast<__nv_bfloat16*>(p), lo_off, o, (float)v);
+    else
+      static_cast<TD*>(p)[o] = v;
+  }
 };
 
 // Lanes past the end of a partial item redo its last element: the same load
 // and the same value stored to the same place, so no lane needs a predicate.
 template <int ND, typename TS, typename TD>
-__device__ __forceinline__ void linear_flat(const BoxItem& it, const TS* __restrict__ src, TD* __restrict__ dst,
-                                            int lane) {
+__device__ __forceinline__ void linear_flat(const BoxItem& it, const TS* __restrict__ src, void* __restrict__ dstv,
+                                            int64_t lo_off, int lane) {
+  TD* dst = static_cast<TD*>(dstv);
   const Shape<ND> sh(it);
   int sa[ND], da[ND];
   load_strides(it.sa, sa);
@@ -146,6 +162,12 @@ __device__ __forceinline__ void linear_flat(const BoxItem& it, const TS* __restr
     sh.split(min(it.start + lane + 32 * u, last), t);
     dof[u] = dot(t, da);
     v[u] = TD(__ldg(ps + dot(t, sa)));
+  }
+  if (((it.sel >> 4) & 7) == DST_SPLIT) {
+    __nv_bfloat16* ph = static_cast<__nv_bfloat16*>(dstv) + it.dst_off;
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) store_split(ph, lo_off, dof[u], (float)(c * v[u]));
+    return;
   }
 #pragma unroll
   for (int u = 0; u < kBatch; ++u) pd[dof[u]] = c * v[u];
@@ -226,11 +248,18 @@ __device__ __forceinline__ void tile_item(const BoxItem& it, const TS* __restric
   if (p < P) {
     if (flat) {
       const TD c = coef<TD>(it.t0_coef, it.t0_coef_f);
-      const bool unit = (it.sel & kSelUnit) != 0;
-      TD* pd = fdst + it.dst_off + da + p * dap + it.q0 * daq;
+      const int64_t o = it.dst_off + da + (int64_t)p * dap + (int64_t)it.q0 * daq;
+      if (dst.split) {
+        __nv_bfloat16* ph = static_cast<__nv_bfloat16*>(dst.p);
 #pragma unroll 8
-      for (int k = 0; k < 32; ++k)
-        if (k < cols) pd[k * daq] = unit ? tile[lane][k] : c * tile[lane][k];
+        for (int k = 0; k < 32; ++k)
+          if (k < cols) store_split(ph, dst.lo_off, o + (int64_t)k * daq, (float)(c * tile[lane][k]));
+      } else {
+        TD* pd = fdst + o;
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k)
+          if (k < cols) pd[k * daq] = c * tile[lane][k];
+      }
     } else {
 #pragma unroll 4
       for (int k = 0; k < 32; ++k) {
@@ -254,7 +283,8 @@ __device__ __forceinline__ void* dst_slot(const BoxItem& it, const BoxPtrs& ptrs
     case 1: return ptrs.dst[1];
     case 2: return ptrs.dst[2];
     case 3: return ptrs.dst[3];
-    default: return ptrs.dst[4];
+    case 4: return ptrs.dst[4];
+    default: return ptrs.dst[5];
   }
 }
 
@@ -262,7 +292,8 @@ __device__ __forceinline__ void* dst_slot(const BoxItem& it, const BoxPtrs& ptrs
 // from shared memory dim by dim instead of holding it in registers
 template <typename TS, typename TD>
 __device__ __forceinline__ void linear_flat_rolled(const BoxItem& it, const TS* __restrict__ src,
-                                                   TD* __restrict__ dst, int lane) {
+                                                   void* __restrict__ dstv, int64_t lo_off, int lane) {
+  TD* dst = static_cast<TD*>(dstv);
   const TS* ps = src + it.t0_off;
   TD* pd = dst + it.dst_off;
   const int last = it.start + it.count - 1;
@@ -284,6 +315,12 @@ __device__ __forceinline__ void linear_flat_rolled(const BoxItem& it, const TS* 
     dof[u] = dd;
     v[u] = has_src ? c * TD(__ldg(ps + so)) : TD(0);
   }
+  if (((it.sel >> 4) & 7) == DST_SPLIT) {
+    __nv_bfloat16* ph = static_cast<__nv_bfloat16*>(dstv) + it.dst_off;
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) store_split(ph, lo_off, dof[u], (float)v[u]);
+    return;
+  }
 #pragma unroll
   for (int u = 0; u < kBatch; ++u) pd[dof[u]] = v[u];
 }
@@ -292,12 +329,13 @@ __device__ __forceinline__ void linear_flat_rolled(const BoxItem& it, const TS* 
 template <typename TS, typename TD>
 __device__ __forceinline__ void run_flat(const BoxItem& it, const BoxPtrs& ptrs, int lane) {
   const TS* sp = src_slot<TS, TD>(it, ptrs);
-  TD* d = static_cast<TD*>(dst_slot(it, ptrs));
+  void* d = dst_slot(it, ptrs);
+  const int64_t lo = ptrs.split_lo;
   switch (it.ndim) {
-    case 1: linear_flat<1, TS, TD>(it, sp, d, lane); break;
-    case 2: linear_flat<2, TS, TD>(it, sp, d, lane); break;
-    case 3: linear_flat<3, TS, TD>(it, sp, d, lane); break;
-    default: linear_flat_rolled<TS, TD>(it, sp, d, lane); break;
+    case 1: linear_flat<1, TS, TD>(it, sp, d, lo, lane); break;
+    case 2: linear_flat<2, TS, TD>(it, sp, d, lo, lane); break;
+    case 3: linear_flat<3, TS, TD>(it, sp, d, lo, lane); break;
+    default: linear_flat_rolled<TS, TD>(it, sp, d, lo, lane); break;
   }
 }
 
@@ -319,9 +357,11 @@ __device__ __forceinline__ void run_item(const BoxItem& it, const Term* __restri
   src.nterm = it.nterm;
   src.term0 = it.term0;
   Dst<TD> dst;
-  dst.p = static_cast<TD*>(dp);
+  dst.p = dp;
   dst.off = it.dst_off;
   dst.ld = it.dst_ld;
+  dst.lo_off = ptrs.split_lo;
+  dst.split = ((it.sel >> 4) & 7) == DST_SPLIT;
   if (it.sel & kSelTile) {
     tile_item<TS, TD>(it, sp, static_cast<TD*>(dp), src, dst, tile, lane);
     return;

@@ -6,14 +6,14 @@
 // hi = bf16(a), lo = bf16(a - hi) and the product is accumulated in FP32 in
 // tensor memory as  A_hi B_hi + A_hi B_lo + A_lo B_hi  (3 passes).
 //
-// Operands arrive as tiled images made by the pack kernel below from the
-// FP32 matrices that the gather (box.cu) writes: a tile is 128 rows x 64 k of
-// bf16 (16 KB) in the canonical K-major, 128-byte-swizzle layout of the
-// tensor-core shared-memory descriptors, so one bulk copy (cp.async.bulk,
-// the TMA engine's linear mode) stages it with no tensor map.
+// Operands arrive as row-major bf16 matrices (hi and lo planes) written by the
+// gather (box.cu); the TMA engine loads 128-row x 64-k boxes of them through
+// 3-D tensor maps (k, row, plane) with 128-byte swizzling, which is the
+// canonical K-major layout of the tensor-core shared-memory descriptors, and
+// fills boxes past the matrix edges with zeros.
 //
 // Roles (192 threads, one CTA per SM, persistent over the tile list):
-//   warp 0     one thread issues the bulk copies into a 3-stage ring;
+//   warp 0     one thread issues the TMA tensor loads into a 3-stage ring;
 //   warp 1     allocates 256 TMEM columns (two 128x128 FP32 accumulators),
 //              one thread issues tcgen05.mma (M=128, N=128, K=16);
 //   warps 2-5  epilogue: tcgen05.ld of the accumulator, transpose through
@@ -21,6 +21,7 @@
 // Every wait on an mbarrier is bounded (2 s of %globaltimer); on expiry the
 // CTA sets the device error word and leaves its loops, waits (bounded) for
 // its outstanding copies and MMAs, and frees its TMEM.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -33,8 +34,7 @@ namespace {
 
 constexpr int BM = 128, BN = 128;
 constexpr int STAGES = 3;
-constexpr int TILE_ELEMS = 128 * 64;
-constexpr int TILE_BYTES = TILE_ELEMS * 2;
+constexpr int TILE_BYTES = 128 * 64 * 2;  // one 128-row x 64-k bf16 box
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A_hi, A_lo, B_hi, B_lo
 constexpr int EPI_PITCH = 33;
 constexpr int EPI_BYTES = 4 * 32 * EPI_PITCH * 4;
@@ -77,11 +77,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+// one 64 x 128 x 1 box of a 3-D tensor map at (x, y, z) into shared memory
+__device__ __forceinline__ void tma_load_3d(void* sdst, const TensorMap* map, int x, int y, int z, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(sdst)),
-      "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(sdst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
@@ -172,9 +173,7 @@ __device__ void drain_bar(uint64_t* bar, uint32_t parity) {
 
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     gemm_tc_kernel(const TcSector* __restrict__ secs, const GemmTile* __restrict__ tiles, int ntiles,
-                   const __nv_bfloat16* __restrict__ a_hi, const __nv_bfloat16* __restrict__ a_lo,
-                   const __nv_bfloat16* __restrict__ b_hi, const __nv_bfloat16* __restrict__ b_lo,
-                   float* __restrict__ C, int* err) {
+                   const TensorMap* __restrict__ maps, float* __restrict__ C, int* err) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -230,12 +229,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           }
           mbar_arrive_expect_tx(&full[stage], STAGE_BYTES);
           uint8_t* sp = stages + stage * STAGE_BYTES;
-          const int64_t ao = s.a_img + ((int64_t)t.mt * s.ktiles + kt) * TILE_ELEMS;
-          const int64_t bo = s.b_img + ((int64_t)t.nt * s.ktiles + kt) * TILE_ELEMS;
-          bulk_g2s(sp, a_hi + ao, TILE_BYTES, &full[stage]);
-          bulk_g2s(sp + TILE_BYTES, a_lo + ao, TILE_BYTES, &full[stage]);
-          bulk_g2s(sp + 2 * TILE_BYTES, b_hi + bo, TILE_BYTES, &full[stage]);
-          bulk_g2s(sp + 3 * TILE_BYTES, b_lo + bo, TILE_BYTES, &full[stage]);
+          const int x = kt * 64;  // 128-byte aligned k offset of the box
+          tma_load_3d(sp, maps + s.amap, x, t.mt * BM, 0, &full[stage]);
+          tma_load_3d(sp + TILE_BYTES, maps + s.amap, x, t.mt * BM, 1, &full[stage]);
+          tma_load_3d(sp + 2 * TILE_BYTES, maps + s.bmap, x, t.nt * BN, 0, &full[stage]);
+          tma_load_3d(sp + 3 * TILE_BYTES, maps + s.bmap, x, t.nt * BN, 1, &full[stage]);
           ++issued;
           if (++stage == STAGES) {
             stage = 0;
@@ -344,43 +342,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
 }
 
-// Operand images from FP32 row-major matrices.  One CTA per image tile
-// (128 rows x 64 columns); thread t converts the 8-column chunk t % 8 of
-// rows t / 8 + 32 i, i = 0..3: eight FP32 loads, then hi = bf16(x) and
-// lo = bf16(x - hi) (round to nearest) as one 16-byte store each, at the
-// chunk's 128-byte-swizzled place.  Positions outside the matrix are zero,
-// so the tensor cores read zeros in every padded row and column.
-__global__ void __launch_bounds__(256) pack_kernel(const PackTile* __restrict__ tiles, const float* __restrict__ lin,
-                                                   __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
-  const PackTile t = tiles[blockIdx.x];
-  pdl_wait();
-  pdl_launch_dependents();
-  const int chunk = threadIdx.x & 7;
-  const int c0 = t.kt * 64 + chunk * 8;
-  const int64_t tile = t.img + ((int64_t)t.mt * t.ktiles + t.kt) * TILE_ELEMS;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int rr = (threadIdx.x >> 3) + 32 * i;
-    const int r = t.mt * 128 + rr;
-    const float* src = lin + t.src + (int64_t)r * t.ld;
-    float x[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = (r < t.rows && c0 + j < t.cols) ? __ldg(src + c0 + j) : 0.0f;
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const __nv_bfloat162 hv = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
-      const __nv_bfloat162 lv =
-          __floats2bfloat162_rn(x[2 * j] - __low2float(hv), x[2 * j + 1] - __high2float(hv));
-      h[j] = *reinterpret_cast<const uint32_t*>(&hv);
-      l[j] = *reinterpret_cast<const uint32_t*>(&lv);
-    }
-    const int64_t o = tile + rr * 64 + ((chunk ^ (rr & 7)) << 3);
-    *reinterpret_cast<uint4*>(hi + o) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4*>(lo + o) = make_uint4(l[0], l[1], l[2], l[3]);
-  }
-}
-
 int g_num_sms = 0;
 
 }  // namespace
@@ -395,9 +356,8 @@ int tc_num_sms() {
   return g_num_sms;
 }
 
-int launch_gemm_tc(const TcSector* secs, const GemmTile* tiles, int ntiles, const uint16_t* a_hi,
-                   const uint16_t* a_lo, const uint16_t* b_hi, const uint16_t* b_lo, float* C, int* err_word,
-                   void* stream) {
+int launch_gemm_tc(const TcSector* secs, const GemmTile* tiles, int ntiles, const TensorMap* maps, float* C,
+                   int* err_word, void* stream) {
   if (ntiles <= 0) return 0;
   static bool attr_set = false;
   if (!attr_set) {
@@ -407,15 +367,39 @@ int launch_gemm_tc(const TcSector* secs, const GemmTile* tiles, int ntiles, cons
   }
   int grid = ntiles < tc_num_sms() ? ntiles : tc_num_sms();
   return (int)launch_pdl(gemm_tc_kernel, dim3(grid), dim3(NUM_THREADS), SMEM_BYTES, static_cast<cudaStream_t>(stream),
-                         secs, tiles, ntiles, reinterpret_cast<const __nv_bfloat16*>(a_hi),
-                         reinterpret_cast<const __nv_bfloat16*>(a_lo), reinterpret_cast<const __nv_bfloat16*>(b_hi),
-                         reinterpret_cast<const __nv_bfloat16*>(b_lo), C, err_word);
+                         secs, tiles, ntiles, maps, C, err_word);
 }
 
-int launch_pack(const PackTile* tiles, int ntiles, const float* lin, uint16_t* hi, uint16_t* lo, void* stream) {
-  if (ntiles <= 0) return 0;
-  return (int)launch_pdl(pack_kernel, dim3(ntiles), dim3(256), 0, static_cast<cudaStream_t>(stream), tiles, lin,
-                         reinterpret_cast<__nv_bfloat16*>(hi), reinterpret_cast<__nv_bfloat16*>(lo));
+namespace {
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_fn() {
+  static EncodeTiled fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
 }
+}  // namespace
+
+int encode_operand_map(TensorMap* out, const void* hi, const TcOperand& op, int64_t split_lo) {
+  static_assert(sizeof(TensorMap) == sizeof(CUtensorMap), "TensorMap must hold a CUtensorMap");
+  EncodeTiled fn = encode_fn();
+  if (!fn) return (int)CUDA_ERROR_NOT_FOUND;
+  const cuuint64_t dims[3] = {(cuuint64_t)op.cols, (cuuint64_t)op.rows, 2};
+  const cuuint64_t strides[2] = {(cuuint64_t)op.ld * 2, (cuuint64_t)split_lo * 2};  // bytes, dims 1 and 2
+  const cuuint32_t box[3] = {64, (cuuint32_t)BM, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  void* base = const_cast<uint16_t*>(static_cast<const uint16_t*>(hi) + op.off);
+  return (int)fn(reinterpret_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
+                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
 
 }  // namespace sym

@@ -8,7 +8,10 @@ namespace sym {
 constexpr int kMaxDim = 6;
 
 // Destination slots of a box launch.
-enum DstSlot { DST_OUT = 0, DST_DA = 1, DST_DB = 2, DST_OPS = 3, DST_OUTM = 4, DST_COUNT = 5 };
+// DST_SPLIT: split-BF16 operands of the tensor cores; an element v goes to
+// dst[DST_SPLIT] as hi = bf16(v) and, split_lo elements further, as
+// lo = bf16(v - hi) (both rounded to nearest).
+enum DstSlot { DST_OUT = 0, DST_DA = 1, DST_DB = 2, DST_OPS = 3, DST_OUTM = 4, DST_SPLIT = 5, DST_COUNT = 6 };
 constexpr int kSelTile = 1 << 9;   // BoxItem::sel flag: 32 x 32 transposing tile (see box.cu)
 // BoxItem::sel flag: at most one term with t0_ld == 1, linear destination with
 // dst_ld == 1, sb == db == 0, and both <t, sa> and <t, da> below 2^31, so the
@@ -65,6 +68,7 @@ struct Term {
 struct BoxPtrs {
   const void* src[4];
   void* dst[DST_COUNT];
+  int64_t split_lo;  // DST_SPLIT: element distance from the hi to the lo plane
 };
 
 // CUDA-core grouped GEMM (row-major): C = alpha * A (m x k, lda) * B (k x n, ldb).
@@ -80,24 +84,28 @@ struct GemmTile {
   int32_t k0, k1, atomic;
 };
 
-// tcgen05 split-BF16 x3 grouped GEMM.  Operand images: A tile (mt, kt) at
-// a_img + (mt * ktiles + kt) * 8192 bf16 elements (128 rows x 64 k, 128B
-// swizzled), B tile (nt, kt) likewise with n rows.  C row-major fp32.
-// The images are made from FP32 row-major matrices by the pack kernel, one
-// PackTile per image tile: rows [128 mt, 128 mt + 128) and columns
-// [64 kt, 64 kt + 64) of the rows x cols matrix at src (row stride ld),
-// zero outside it, written as the hi and lo images of tile (mt, kt) of the
-// operand image at img (ktiles tiles per row tile).
+// tcgen05 split-BF16 x3 grouped GEMM, C (m x n, row-major FP32, ldc) =
+// alpha A B.  The operands are row-major bf16 matrices with their hi and lo
+// planes split_lo elements apart: A as m x k, B as B^T (n x k).  Each is
+// described by a TensorMap (amap, bmap index the plan's map array): a 3-D
+// tiled tensor map (k, rows, plane) whose 64 x 128 x 1 boxes the TMA engine
+// writes to shared memory in the 128-byte-swizzled K-major layout of the
+// tensor-core descriptors, with zeros past the matrix edges.
 struct TcSector {
   int32_t m, n, k, ktiles;
-  int64_t a_img, b_img;
+  int32_t amap, bmap;
   int64_t c_off;
   int32_t ldc;
   float alpha;
 };
-struct PackTile {
-  int64_t src, img;
-  int32_t rows, cols, ld, ktiles, mt, kt;
+struct alignas(64) TensorMap {  // opaque CUtensorMap (128 bytes)
+  uint64_t w[16];
+};
+// Operand of a tensor-core GEMM: rows x cols bf16 at element `off` of the hi
+// plane (row stride ld, a multiple of 8; off a multiple of 8).
+struct TcOperand {
+  int64_t off;
+  int32_t rows, cols, ld;
 };
 
 // CUDA-core GEMM tile shapes
@@ -109,10 +117,11 @@ int launch_box(bool src_f64, bool dst_f64, bool flat_only, const BoxItem* items,
                const BoxPtrs& ptrs, void* stream);
 int launch_gemm_simt(bool f64, int shape, const GemmSectorSimt* secs, const GemmTile* tiles, int ntiles,
                      const void* ops, void* outm, void* stream);
-int launch_gemm_tc(const TcSector* secs, const GemmTile* tiles, int ntiles, const uint16_t* a_hi,
-                   const uint16_t* a_lo, const uint16_t* b_hi, const uint16_t* b_lo, float* C,
+int launch_gemm_tc(const TcSector* secs, const GemmTile* tiles, int ntiles, const TensorMap* maps, float* C,
                    int* err_word, void* stream);
-int launch_pack(const PackTile* tiles, int ntiles, const float* lin, uint16_t* hi, uint16_t* lo, void* stream);
+// Tensor map of one operand whose hi plane starts at `hi` (bf16) and whose lo
+// plane is split_lo elements further; 0 or a CUDA driver error code.
+int encode_operand_map(TensorMap* out, const void* hi, const TcOperand& op, int64_t split_lo);
 int tc_num_sms();
 
 }  // namespace sym

@@ -87,10 +87,9 @@ extern "C" int sym_contract_noalloc(sym_tensor A, sym_tensor B, int npairs, cons
     const size_t o_simt = region(p.secs_simt.size() * sizeof(GemmSectorSimt));
     const size_t o_tc = region(p.secs_tc.size() * sizeof(TcSector));
     const size_t o_tiles = region(p.tiles.size() * sizeof(GemmTile));
-    const size_t o_packs = region(p.packs.size() * sizeof(PackTile));
+    const size_t o_maps = region(p.tc_ops.size() * sizeof(TensorMap));
     const size_t o_err = region(sizeof(int));
-    const size_t o_hi = region((size_t)p.img_elems * 2);
-    const size_t o_lo = region((size_t)p.img_elems * 2);
+    const size_t o_img = region((size_t)p.img_elems * 2 * 2);  // hi and lo planes
     const size_t o_lin = region((size_t)p.lin_elems * es);
     const size_t o_outm = region((size_t)p.outm_elems * es);
     if (off > kNoallocBytes)
@@ -114,19 +113,21 @@ extern "C" int sym_contract_noalloc(sym_tensor A, sym_tensor B, int npairs, cons
     copy(o_simt, p.secs_simt.data(), p.secs_simt.size() * sizeof(GemmSectorSimt));
     copy(o_tc, p.secs_tc.data(), p.secs_tc.size() * sizeof(TcSector));
     copy(o_tiles, p.tiles.data(), p.tiles.size() * sizeof(GemmTile));
-    copy(o_packs, p.packs.data(), p.packs.size() * sizeof(PackTile));
+    if (!p.tc_ops.empty()) {  // tensor maps point into this array: encode them for its address
+      p.encode_maps(base + o_img);
+      copy(o_maps, p.maps.data(), p.maps.size() * sizeof(TensorMap));
+    }
     // the array keeps the previous call's contents: clear what must start at
-    // zero (the pack kernel writes every image element, padding included)
+    // zero (the TMA loads of the tensor cores read zeros past the operand edges)
     zero(o_err, sizeof(int));
     p.d_items = reinterpret_cast<BoxItem*>(base + o_items);
     p.d_terms = reinterpret_cast<Term*>(base + o_terms);
     p.d_secs_simt = reinterpret_cast<GemmSectorSimt*>(base + o_simt);
     p.d_secs_tc = reinterpret_cast<TcSector*>(base + o_tc);
     p.d_tiles = reinterpret_cast<GemmTile*>(base + o_tiles);
-    p.d_packs = reinterpret_cast<PackTile*>(base + o_packs);
+    p.d_maps = reinterpret_cast<TensorMap*>(base + o_maps);
     p.d_err = reinterpret_cast<int*>(base + o_err);
-    p.img_hi = base + o_hi;
-    p.img_lo = base + o_lo;
+    p.img = base + o_img;
     p.lin = base + o_lin;
     p.outm = base + o_outm;
     p.dry = false;

@@ -509,16 +509,19 @@ Plan::~Plan() {
   if (ev_fork) cudaEventDestroy(static_cast<cudaEvent_t>(ev_fork));
 }
 
+void Plan::encode_maps(const void* img_base) {
+  if (maps_base == img_base && maps.size() == tc_ops.size()) return;
+  maps.assign(tc_ops.size(), TensorMap{});
+  for (size_t i = 0; i < tc_ops.size(); ++i)
+    if (int e = encode_operand_map(&maps[i], img_base, tc_ops[i], img_elems))
+      fail(SYM_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(e) + ") for a tensor-core operand");
+  maps_base = img_base;
+}
+
 void Plan::upload(bool device) {
   // finish the statistics tables (prefix sums)
   if (item_bytes_prefix.size() != items.size() + 1) item_bytes_prefix.assign(items.size() + 1, 0.0);
   for (size_t i = 0; i < items.size(); ++i) item_bytes_prefix[i + 1] += item_bytes_prefix[i];
-  pack_bytes_prefix.assign(packs.size() + 1, 0.0);
-  for (size_t i = 0; i < packs.size(); ++i) {  // FP32 read once, hi + lo tile written (padding included)
-    const PackTile& t = packs[i];
-    const double r = std::min(128, t.rows - 128 * t.mt), c = std::min(64, t.cols - 64 * t.kt);
-    pack_bytes_prefix[i + 1] = pack_bytes_prefix[i] + 4.0 * r * c + 4.0 * 128 * 64;
-  }
   flat_prefix.assign(items.size() + 1, 0);
   for (size_t i = 0; i < items.size(); ++i)
     flat_prefix[i + 1] = flat_prefix[i] + ((items[i].sel & (kSelFlat | kSelTile)) == kSelFlat ? 1 : 0);
@@ -558,12 +561,12 @@ void Plan::upload(bool device) {
   d_secs_simt = static_cast<GemmSectorSimt*>(up(secs_simt.data(), secs_simt.size() * sizeof(GemmSectorSimt)));
   d_secs_tc = static_cast<TcSector*>(up(secs_tc.data(), secs_tc.size() * sizeof(TcSector)));
   d_tiles = static_cast<GemmTile*>(up(tiles.data(), tiles.size() * sizeof(GemmTile)));
-  d_packs = static_cast<PackTile*>(up(packs.data(), packs.size() * sizeof(PackTile)));
   if (kind == CONTRACT) {
     const size_t es = f64() ? sizeof(double) : sizeof(float);
-    if (img_elems > 0) {  // every image element, padding included, is written by the pack kernel
-      img_hi = arena.alloc(img_elems * 2, false);
-      img_lo = arena.alloc(img_elems * 2, false);
+    if (img_elems > 0) {  // hi and lo planes; the TMA loads fill past-the-edge boxes with zeros
+      img = arena.alloc(img_elems * 2 * 2, false);
+      encode_maps(img);
+      d_maps = static_cast<TensorMap*>(up(maps.data(), maps.size() * sizeof(TensorMap)));
     }
     lin = arena.alloc(lin_elems * es, false);
     outm = arena.alloc(outm_elems * es, false);
@@ -766,7 +769,7 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
   }
   {
     const int64_t src[4] = {in.numel(), 0, 0, 0};
-    const int64_t dst[DST_COUNT] = {out.numel(), 0, 0, 0, 0};
+    const int64_t dst[DST_COUNT] = {out.numel(), 0, 0, 0, 0, 0};
     P->validate(src, dst);
   }
   P->upload();
@@ -791,7 +794,7 @@ int choose_kind(bool f64, int64_t m, int64_t n, int64_t k) {
   if (k <= 16 && n <= 16) return 4;
   const int simt = n <= 16 ? 2 : 1;
   if (f64) return simt;
-  static const int min_mn = env_int("SYM_TC_MIN_MN", 96);
+  static const int min_mn = env_int("SYM_TC_MIN_MN", 64);
   static const int min_k = env_int("SYM_TC_MIN_K", 48);
   static const int max_k = env_int("SYM_TC_MAX_K", 16384);
   if (m >= min_mn && n >= min_mn && k >= min_k && k <= max_k) return 0;
@@ -875,12 +878,12 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     int x;
     int64_t m, n, k;
     int kind[3];
-    // linear FP32/FP64 operands (elements of `lin`): the gather writes these
-    int64_t a, b, bt, at, dcl, dct;
-    // split-BF16 images of the tcgen05 operands (bf16 elements), packed from
-    // the linear operands: forward a (m x k) and b (n x k, = B^T); dA dcl
-    // (m x n) and bt (k x n, = B); dB at (k x m) and dct (n x m, = dC^T)
-    int64_t ia, ib, idc1, ibt, iat, idc2;
+    // linear FP32/FP64 operands of the CUDA-core GEMMs (elements of `lin`):
+    // forward A (m x k), B (k x n); dA B^T (n x k); dB A^T (k x m); dC (m x n)
+    int64_t a = -1, b = -1, bt = -1, at = -1, dcl = -1;
+    // split-BF16 operands of the tcgen05 GEMMs (indices into P->tc_ops):
+    // forward A (m x k), B^T (n x k); dA dC (m x n), B (k x n); dB A^T (k x m), dC^T (n x m)
+    int oa = -1, ob = -1, odc1 = -1, obt = -1, oat = -1, odc2 = -1;
     int64_t c, da, db;  // output matrices
     bool split[3];
   };
@@ -904,65 +907,43 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     gofx[g.x] = (int)gs.size();
     gs.push_back(g);
   }
-  auto img = [&](int64_t rows, int64_t kk) { return cdiv(rows, 128) * cdiv(kk, 64) * 8192; };
   int64_t ie = 0, le = 0, oe = 0;
-  // forward operands: A (m x k); B as k x n, or as B^T (n x k) for the tensor cores
+  // tcgen05 operand: rows x cols bf16 in the hi plane; rows start on 128-byte
+  // boundaries, so every 128-byte row of a TMA box is one cache line
+  auto add_op = [&](int64_t rows, int64_t cols) {
+    const int64_t ld = cdiv(cols, 64) * 64;
+    P->tc_ops.push_back(TcOperand{ie, (int)rows, (int)cols, (int)ld});
+    ie += rows * ld;
+    return (int)P->tc_ops.size() - 1;
+  };
   for (auto& g : gs) {
-    g.a = le, le += g.m * g.k;
-    g.b = le, le += g.k * g.n;
     if (g.kind[0] == 0) {
-      g.ia = ie, ie += img(g.m, g.k);
-      g.ib = ie, ie += img(g.n, g.k);
+      g.oa = add_op(g.m, g.k);
+      g.ob = add_op(g.n, g.k);
+    } else {
+      g.a = le, le += g.m * g.k;
+      g.b = le, le += g.k * g.n;
     }
-  }
-  // backward operands: dC (m x n) always; dA takes B^T (n x k), or B (k x n)
-  // for the tensor cores; dB takes A^T (k x m) and, on the tensor cores, dC^T
-  for (auto& g : gs) {
-    g.dcl = le, le += g.m * g.n;
-    g.bt = le, le += g.n * g.k;
-    g.at = le, le += g.k * g.m;
     if (g.kind[1] == 0) {
-      g.idc1 = ie, ie += img(g.m, g.n);
-      g.ibt = ie, ie += img(g.k, g.n);
+      g.odc1 = add_op(g.m, g.n);
+      g.obt = add_op(g.k, g.n);
+    } else {
+      g.bt = le, le += g.n * g.k;
     }
     if (g.kind[2] == 0) {
-      g.dct = le, le += g.n * g.m;
-      g.iat = ie, ie += img(g.k, g.m);
-      g.idc2 = ie, ie += img(g.n, g.m);
+      g.oat = add_op(g.k, g.m);
+      g.odc2 = add_op(g.n, g.m);
+    } else {
+      g.at = le, le += g.k * g.m;
     }
+    if (g.kind[1] != 0 || g.kind[2] != 0) g.dcl = le, le += g.m * g.n;
   }
   for (auto& g : gs) {
     g.c = oe, oe += g.m * g.n;
     g.da = oe, oe += g.m * g.k;
     g.db = oe, oe += g.k * g.n;
   }
-  // pack lists, one per GEMM phase: image tiles of every tcgen05 operand
-  std::vector<PackTile> packs[3];
-  auto add_pack = [&](int ph, int64_t src, int64_t rows, int64_t cols, int64_t im) {
-    const int64_t kt = cdiv(cols, 64);
-    for (int64_t mt = 0; mt < cdiv(rows, 128); ++mt)
-      for (int64_t t = 0; t < kt; ++t)
-        packs[ph].push_back(PackTile{src, im, (int)rows, (int)cols, (int)cols, (int)kt, (int)mt, (int)t});
-  };
-  for (auto& g : gs) {
-    if (g.kind[0] == 0) {
-      add_pack(0, g.a, g.m, g.k, g.ia);
-      add_pack(0, g.b, g.n, g.k, g.ib);
-    }
-    if (g.kind[1] == 0) {
-      add_pack(1, g.dcl, g.m, g.n, g.idc1);
-      add_pack(1, g.bt, g.k, g.n, g.ibt);
-    }
-    if (g.kind[2] == 0) {
-      add_pack(2, g.at, g.k, g.m, g.iat);
-      add_pack(2, g.dct, g.n, g.m, g.idc2);
-    }
-  }
-  for (int ph = 0; ph < 3; ++ph) {
-    P->pack_range[ph] = Range{(int)P->packs.size(), (int)packs[ph].size()};
-    P->packs.insert(P->packs.end(), packs[ph].begin(), packs[ph].end());
-  }
-  P->img_elems = ie;
+  P->img_elems = cdiv(ie, 64) * 64;  // the lo plane starts 128-byte aligned
   P->lin_elems = le;
   P->outm_elems = oe;
   for (auto& g : gs) P->flops_fwd += 2.0 * (double)g.m * (double)g.n * (double)g.k;
@@ -973,10 +954,11 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   // ---- GEMM sectors and tiles: lists per (kind, gemm phase)
   std::vector<std::pair<int64_t, GemmTile>> lists[kGemmKinds][3];
   const int nsm = 152;
+  // kind 0: aoff, boff are tcgen05 operand indices; otherwise linear offsets
   auto add_gemm = [&](int kind, int ph, int64_t m, int64_t n, int64_t k, int64_t aoff, int64_t lda, int64_t boff,
                       int64_t ldb, int64_t coff) -> bool {
     if (kind == 0) {
-      P->secs_tc.push_back(TcSector{(int)m, (int)n, (int)k, (int)cdiv(k, 64), aoff, boff, coff, (int)n, 1.0f});
+      P->secs_tc.push_back(TcSector{(int)m, (int)n, (int)k, (int)cdiv(k, 64), (int)aoff, (int)boff, coff, (int)n, 1.0f});
       const int sec = (int)P->secs_tc.size() - 1;
       for (int64_t mt = 0; mt < cdiv(m, 128); ++mt)
         for (int64_t nt = 0; nt < cdiv(n, 128); ++nt)
@@ -1014,9 +996,9 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   };
   for (auto& g : gs) {
     const bool t0 = g.kind[0] == 0, t1 = g.kind[1] == 0, t2 = g.kind[2] == 0;
-    g.split[0] = add_gemm(g.kind[0], 0, g.m, g.n, g.k, t0 ? g.ia : g.a, g.k, t0 ? g.ib : g.b, g.n, g.c);
-    g.split[1] = add_gemm(g.kind[1], 1, g.m, g.k, g.n, t1 ? g.idc1 : g.dcl, g.n, t1 ? g.ibt : g.bt, g.k, g.da);
-    g.split[2] = add_gemm(g.kind[2], 2, g.k, g.n, g.m, t2 ? g.iat : g.at, g.m, t2 ? g.idc2 : g.dcl, g.n, g.db);
+    g.split[0] = add_gemm(g.kind[0], 0, g.m, g.n, g.k, t0 ? g.oa : g.a, g.k, t0 ? g.ob : g.b, g.n, g.c);
+    g.split[1] = add_gemm(g.kind[1], 1, g.m, g.k, g.n, t1 ? g.odc1 : g.dcl, g.n, t1 ? g.obt : g.bt, g.k, g.da);
+    g.split[2] = add_gemm(g.kind[2], 2, g.k, g.n, g.m, t2 ? g.oat : g.at, g.m, t2 ? g.odc2 : g.dcl, g.n, g.db);
   }
   for (int kind = 0; kind < kGemmKinds; ++kind)
     for (int ph = 0; ph < 3; ++ph) {
@@ -1055,6 +1037,11 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   // operand block written into a linear matrix (row stride ld) at (row0, col0)
   auto put = [&](const Box& b, int src, int64_t off, int64_t row0, int64_t col0, int64_t ld,
                  const std::vector<Term>& t) { emit(*P, b, off + row0 * ld + col0, (int)ld, src, DST_OPS, t); };
+  // operand block written into tcgen05 operand `op` (split-BF16) at (row0, col0)
+  auto put_tc = [&](const Box& b, int src, int op, int64_t row0, int64_t col0, const std::vector<Term>& t) {
+    const TcOperand& o = P->tc_ops[op];
+    emit(*P, b, o.off + row0 * o.ld + col0, o.ld, src, DST_SPLIT, t);
+  };
   // zero-fill of an output matrix before a split-K GEMM adds into it
   auto zero_fill = [&](int64_t off, int64_t rows, int64_t cols) {
     Box b;
@@ -1070,15 +1057,18 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     if (gi == gofx.end() || XA[s].empty()) continue;
     const G& g = gs[gi->second];
     Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, false);
-    put(b, 0, g.a, MA.r0[s], MA.c0[s], g.k, terms_of(XA[s], A));
+    if (g.kind[0] == 0)
+      put_tc(b, 0, g.oa, MA.r0[s], MA.c0[s], terms_of(XA[s], A));
+    else
+      put(b, 0, g.a, MA.r0[s], MA.c0[s], g.k, terms_of(XA[s], A));
   }
   for (int64_t s = 0; s < Bm.nsec(); ++s) {
     auto gi = gofx.find(MB.xs[MB.sx[s]]);
     if (gi == gofx.end() || XB[s].empty()) continue;
     const G& g = gs[gi->second];
-    if (g.kind[0] == 0) {  // B^T (n x k): image rows n (free), K = k (contracted)
+    if (g.kind[0] == 0) {  // B^T (n x k): rows n (free), K = k (contracted)
       Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, true);
-      put(b, 1, g.b, MB.c0[s], MB.r0[s], g.k, terms_of(XB[s], B));
+      put_tc(b, 1, g.ob, MB.c0[s], MB.r0[s], terms_of(XB[s], B));
     } else {
       Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, false);
       put(b, 1, g.b, MB.r0[s], MB.c0[s], g.n, terms_of(XB[s], B));
@@ -1114,7 +1104,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   }
   P->fwd_scatter = {begin, (int)P->items.size() - begin};
 
-  // ---- backward gathers: [dA only: B or B^T][shared: dC][dB only: A^T, dC^T]
+  // ---- backward gathers: [dA only: B or B^T, dC split][shared: dC linear][dB only: A^T, dC^T split]
   std::vector<int> idC(C.rank);
   for (int i = 0; i < C.rank; ++i) idC[i] = i;
   auto dc_terms = [&](int64_t sn) {
@@ -1140,18 +1130,25 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     auto gi = gofx.find(MB.xs[MB.sx[s]]);
     if (gi == gofx.end() || XB[s].empty()) continue;
     const G& g = gs[gi->second];
-    if (g.kind[1] == 0) {  // B (k x n): image rows k (contracted), K = n (free)
+    if (g.kind[1] == 0) {  // B (k x n): rows k (contracted), K = n (free)
       Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, false);
-      put(b, 1, g.bt, MB.r0[s], MB.c0[s], g.n, terms_of(XB[s], B));
+      put_tc(b, 1, g.obt, MB.r0[s], MB.c0[s], terms_of(XB[s], B));
     } else {  // B^T (n x k)
       Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, true);
       put(b, 1, g.bt, MB.c0[s], MB.r0[s], g.k, terms_of(XB[s], B));
     }
   }
+  for_dc([&](const G& g, int64_t sn, int64_t r0, int64_t c0) {  // dC (m x n) for dA on the tensor cores
+    if (g.kind[1] != 0) return;
+    auto t = dc_terms(sn);
+    if (t.empty()) return;
+    put_tc(gather_box(Cn, idC, Cn, sn, sn, na, false), 2, g.odc1, r0, c0, t);
+  });
   for (auto& g : gs)
     if (g.split[1]) zero_fill(g.da, g.m, g.k);
   const int b1 = (int)P->items.size();
-  for_dc([&](const G& g, int64_t sn, int64_t r0, int64_t c0) {  // dC (m x n), both gradients
+  for_dc([&](const G& g, int64_t sn, int64_t r0, int64_t c0) {  // dC (m x n) for the CUDA-core GEMMs
+    if (g.dcl < 0) return;
     auto t = dc_terms(sn);
     if (t.empty()) return;
     put(gather_box(Cn, idC, Cn, sn, sn, na, false), 2, g.dcl, r0, c0, g.n, t);
@@ -1162,13 +1159,16 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     if (gi == gofx.end() || XA[s].empty()) continue;
     const G& g = gs[gi->second];
     Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, true);
-    put(b, 0, g.at, MA.c0[s], MA.r0[s], g.m, terms_of(XA[s], A));
+    if (g.kind[2] == 0)
+      put_tc(b, 0, g.oat, MA.c0[s], MA.r0[s], terms_of(XA[s], A));
+    else
+      put(b, 0, g.at, MA.c0[s], MA.r0[s], g.m, terms_of(XA[s], A));
   }
-  for_dc([&](const G& g, int64_t sn, int64_t r0, int64_t c0) {  // dC^T (n x m) for the tensor cores
+  for_dc([&](const G& g, int64_t sn, int64_t r0, int64_t c0) {  // dC^T (n x m) for dB on the tensor cores
     if (g.kind[2] != 0) return;
     auto t = dc_terms(sn);
     if (t.empty()) return;
-    put(gather_box(Cn, idC, Cn, sn, sn, na, true), 2, g.dct, c0, r0, g.m, t);
+    put_tc(gather_box(Cn, idC, Cn, sn, sn, na, true), 2, g.odc2, c0, r0, t);
   });
   for (auto& g : gs)
     if (g.split[2]) zero_fill(g.db, g.k, g.n);
@@ -1227,7 +1227,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   }
   {
     const int64_t src[4] = {A.numel(), B.numel(), C.numel(), P->outm_elems};
-    const int64_t dst[DST_COUNT] = {C.numel(), A.numel(), B.numel(), P->lin_elems, P->outm_elems};
+    const int64_t dst[DST_COUNT] = {C.numel(), A.numel(), B.numel(), P->lin_elems, P->outm_elems, P->img_elems};
     P->validate(src, dst);
   }
   // GEMM tiles stay inside their operand buffers
@@ -1242,20 +1242,19 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
         fail(SYM_ERR_ARG, "internal: CUDA-core GEMM sector past its buffers");
     } else {
       const TcSector& s = P->secs_tc[t.sector];
-      if (s.a_img + ((int64_t)t.mt * s.ktiles + s.ktiles) * 8192 > P->img_elems ||
-          s.b_img + ((int64_t)t.nt * s.ktiles + s.ktiles) * 8192 > P->img_elems ||
+      const int nops = (int)P->tc_ops.size();
+      if (s.amap < 0 || s.amap >= nops || s.bmap < 0 || s.bmap >= nops || s.ktiles != cdiv(s.k, 64) ||
+          P->tc_ops[s.amap].rows != s.m || P->tc_ops[s.amap].cols != s.k || P->tc_ops[s.bmap].rows != s.n ||
+          P->tc_ops[s.bmap].cols != s.k || t.mt * 128 >= s.m || t.nt * 128 >= s.n ||
           s.c_off + (int64_t)(s.m - 1) * s.ldc + s.n - 1 >= P->outm_elems || s.ktiles < 1)
         fail(SYM_ERR_ARG, "internal: tcgen05 GEMM tile past its buffers");
     }
   }
-  // pack tiles read inside the FP32 operands and write inside the images
-  for (const PackTile& t : P->packs) {
-    if (f64 || t.rows < 1 || t.cols < 1 || t.ld < t.cols || t.src < 0 || t.mt < 0 || t.kt < 0 ||
-        (int64_t)t.mt * 128 >= t.rows || t.ktiles != cdiv(t.cols, 64) || t.kt >= t.ktiles ||
-        t.src + (int64_t)(t.rows - 1) * t.ld + t.cols - 1 >= P->lin_elems || t.img < 0 ||
-        t.img + ((int64_t)t.mt * t.ktiles + t.kt + 1) * 8192 > P->img_elems)
-      fail(SYM_ERR_ARG, "internal: operand pack tile past its buffers");
-  }
+  // tcgen05 operands: 16-byte aligned rows inside the hi plane (TMA rules)
+  for (const TcOperand& o : P->tc_ops)
+    if (f64 || o.off < 0 || o.off % 8 || o.ld % 8 || o.ld < o.cols || o.rows < 1 || o.cols < 1 ||
+        o.off + (int64_t)o.rows * o.ld > P->img_elems)
+      fail(SYM_ERR_ARG, "internal: tensor-core operand past its buffer");
   P->upload(device);
   return P;
 }
@@ -1309,27 +1308,14 @@ int run_box(Plan& p, Range r, const BoxPtrs& ptrs, void* stream, int phase) {
                    "box kernel");
 }
 
-// tcgen05 operand images of the pack range `pk`, then (same stream) the GEMM
-int run_pack(Plan& p, Range pk, void* stream) {
-  if (pk.count <= 0) return SYM_OK;
-  p.last_launches++;
-  ProfScope ps(p, PH_PACK, stream, p.pack_bytes_prefix[pk.first + pk.count] - p.pack_bytes_prefix[pk.first], 0.0);
-  return cuda_code(launch_pack(p.d_packs + pk.first, pk.count, static_cast<const float*>(p.lin),
-                               static_cast<uint16_t*>(p.img_hi), static_cast<uint16_t*>(p.img_lo), stream),
-                   "operand pack");
-}
-
-int run_gemm_kind(Plan& p, int kind, Range r, Range pk, void* stream, int phase) {
+int run_gemm_kind(Plan& p, int kind, Range r, void* stream, int phase) {
   if (r.count <= 0) return SYM_OK;
-  if (kind == 0)
-    if (int rc = run_pack(p, pk, stream)) return rc;
   p.last_launches++;
   if (kind != 0) phase = phase == PH_FWD_GEMM ? PH_FWD_GEMM_SIMT : PH_BWD_GEMM_SIMT;
   ProfScope ps(p, phase, stream, 0.0, p.tile_flops_prefix[r.first + r.count] - p.tile_flops_prefix[r.first]);
   if (kind == 0)
-    return cuda_code(launch_gemm_tc(p.d_secs_tc, p.d_tiles + r.first, r.count, static_cast<uint16_t*>(p.img_hi),
-                                    static_cast<uint16_t*>(p.img_lo), static_cast<uint16_t*>(p.img_hi),
-                                    static_cast<uint16_t*>(p.img_lo), static_cast<float*>(p.outm), p.d_err, stream),
+    return cuda_code(launch_gemm_tc(p.d_secs_tc, p.d_tiles + r.first, r.count, p.d_maps,
+                                    static_cast<float*>(p.outm), p.d_err, stream),
                      "tcgen05 gemm");
   const int shape = kind == 1 ? SIMT_64x64 : kind == 2 ? SIMT_256x16 : kind == 3 ? SIMT_THIN : SIMT_ROWS;
   return cuda_code(launch_gemm_simt(p.f64(), shape, p.d_secs_simt,
@@ -1344,8 +1330,6 @@ int run_gemm(Plan& p, int ph0, int ph1, void* stream, int phase) {
   int kinds[kGemmKinds];
   Range rs[kGemmKinds];
   int n = 0;
-  Range pk{p.pack_range[ph0].first, 0};
-  for (int ph = ph0; ph <= ph1; ++ph) pk.count += p.pack_range[ph].count;
   for (int kind = 0; kind < kGemmKinds; ++kind) {
     Range r{p.gemm_range[kind][ph0].first, 0};
     for (int ph = ph0; ph <= ph1; ++ph) r.count += p.gemm_range[kind][ph].count;
@@ -1356,7 +1340,7 @@ int run_gemm(Plan& p, int ph0, int ph1, void* stream, int phase) {
   }
   if (n <= 1 || !p.concurrent) {
     for (int i = 0; i < n; ++i)
-      if (int rc = run_gemm_kind(p, kinds[i], rs[i], pk, stream, phase)) return rc;
+      if (int rc = run_gemm_kind(p, kinds[i], rs[i], stream, phase)) return rc;
     return SYM_OK;
   }
   cudaStream_t s0 = static_cast<cudaStream_t>(stream);
@@ -1384,9 +1368,9 @@ int run_gemm(Plan& p, int ph0, int ph1, void* stream, int phase) {
   for (int i = 0; i < n - 1; ++i)
     check(cudaStreamWaitEvent(static_cast<cudaStream_t>(p.side[i]), static_cast<cudaEvent_t>(p.ev_fork), 0),
           "cudaStreamWaitEvent");
-  int rc = run_gemm_kind(p, kinds[0], rs[0], pk, stream, phase);
+  int rc = run_gemm_kind(p, kinds[0], rs[0], stream, phase);
   for (int i = 1; i < n; ++i) {
-    const int r = run_gemm_kind(p, kinds[i], rs[i], pk, p.side[i - 1], phase);
+    const int r = run_gemm_kind(p, kinds[i], rs[i], p.side[i - 1], phase);
     if (!rc) rc = r;
   }
   // join every side stream, also after a failed launch
@@ -1405,6 +1389,8 @@ BoxPtrs gather_ptrs(Plan& p, const void* A, const void* B, const void* dC) {
   g.src[3] = p.outm;
   g.dst[DST_OPS] = p.lin;
   g.dst[DST_OUTM] = p.outm;
+  g.dst[DST_SPLIT] = p.img;
+  g.split_lo = p.img_elems;
   return g;
 }
 

@@ -22,7 +22,7 @@ struct DeviceArena {
 
 // Phases of a plan's launches (profiling and statistics).
 enum Phase { PH_FWD_GATHER = 0, PH_FWD_GEMM, PH_FWD_SCATTER, PH_BWD_GATHER, PH_BWD_GEMM, PH_BWD_SCATTER,
-             PH_XFORM, PH_FWD_GEMM_SIMT, PH_BWD_GEMM_SIMT, PH_PACK, PH_COUNT };
+             PH_XFORM, PH_FWD_GEMM_SIMT, PH_BWD_GEMM_SIMT, PH_COUNT };
 constexpr int kGemmKinds = 5;  // 0 tcgen05, CUDA cores: 1 tile 64x64, 2 tile 256x16, 3 thin, 4 rows
 
 struct PhaseProfile {
@@ -54,8 +54,10 @@ struct Plan {
   std::vector<GemmTile> tiles;  // grouped by kind, then by GEMM phase
   Range gemm_range[kGemmKinds][3];  // [kind][gemm phase]
   std::vector<int> tile_kind;   // kind of every tile (statistics)
-  std::vector<PackTile> packs;  // image tiles of the tcgen05 operands
-  Range pack_range[3];          // [gemm phase]
+  std::vector<TcOperand> tc_ops;  // split-BF16 operands of the tcgen05 GEMMs
+  std::vector<TensorMap> maps;    // their tensor maps (encoded for the image buffer at maps_base)
+  const void* maps_base = nullptr;
+  void encode_maps(const void* img_base);
 
   // scratch sizes (elements): split-BF16 images, linear operands, output matrices
   int64_t img_elems = 0, lin_elems = 0, outm_elems = 0;
@@ -70,7 +72,6 @@ struct Plan {
   // as prefix sums (launch statistics for any range in O(1))
   std::vector<double> item_bytes_prefix, tile_flops_prefix;
   std::vector<int> flat_prefix;  // flat linear items among the first i (launch variant choice)
-  std::vector<double> pack_bytes_prefix;
   void set_item_bytes(Range r, int es_src, int es_dst);
   bool profiling = false;
   PhaseProfile prof[PH_COUNT];
@@ -84,9 +85,8 @@ struct Plan {
   GemmSectorSimt* d_secs_simt = nullptr;
   TcSector* d_secs_tc = nullptr;
   GemmTile* d_tiles = nullptr;
-  PackTile* d_packs = nullptr;
-  void* img_hi = nullptr;  // bf16 hi images
-  void* img_lo = nullptr;  // bf16 lo images
+  TensorMap* d_maps = nullptr;
+  void* img = nullptr;     // split-BF16 operands: hi plane, then lo plane img_elems further
   void* lin = nullptr;     // linear operands (fp32 or fp64)
   void* outm = nullptr;    // output matrices (fp32 or fp64)
   int* d_err = nullptr;

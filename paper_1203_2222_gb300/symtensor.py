@@ -143,7 +143,7 @@ _PLANS = {}
 
 # phases of a plan's launches (include/symtensor.h, SYM_PHASE_*)
 PHASES = {"fwd_gather": 0, "fwd_gemm_tc": 1, "fwd_scatter": 2, "bwd_gather": 3, "bwd_gemm_tc": 4,
-          "bwd_scatter": 5, "transform": 6, "fwd_gemm_cuda_cores": 7, "bwd_gemm_cuda_cores": 8, "pack": 9}
+          "bwd_scatter": 5, "transform": 6, "fwd_gemm_cuda_cores": 7, "bwd_gemm_cuda_cores": 8}
 
 
 def cached_plans():
