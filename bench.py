@@ -208,6 +208,75 @@ def step_flops(P):
     return tot
 
 
+# ---------------------------------------------------------------- roofline ---
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
+# each kernel over one step of this workload, from one ncu pass on the bench
+# command (profiles/traffic_u1_mps_heff.md), with the SHA-256 of the kernel's
+# sources at that time: once a source changes, the figure no longer applies
+# and the bench reports null.
+TRAFFIC = {
+    "box_flat": {"bytes_per_launch": 9246112, "sha": "7caa23204aa92eac"},
+    "box": {"bytes_per_launch": 12494144, "sha": "7caa23204aa92eac"},
+    "gemm_tc": {"bytes_per_launch": 14657152, "sha": "b64755ea88806cf8"},
+    "gemm_tile": {"bytes_per_launch": 807616, "sha": "e9cb7580d709691c"},
+    "gemm_rows": {"bytes_per_launch": 3204045, "sha": "e9cb7580d709691c"},
+    "gemm_thin": {"bytes_per_launch": 3170355, "sha": "e9cb7580d709691c"},
+    "gemm_wide": {"bytes_per_launch": 71083, "sha": "e9cb7580d709691c"},
+}
+KERNEL_SOURCES = {
+    "box": ["box.cu", "kernels.h", "pdl.h"], "box_flat": ["box.cu", "kernels.h", "pdl.h"],
+    "gemm_tc": ["gemm_tc.cu", "kernels.h", "pdl.h"],
+    "gemm_tile": ["gemm_simt.cu", "kernels.h", "pdl.h"], "gemm_wide": ["gemm_simt.cu", "kernels.h", "pdl.h"],
+    "gemm_thin": ["gemm_simt.cu", "kernels.h", "pdl.h"], "gemm_rows": ["gemm_simt.cu", "kernels.h", "pdl.h"],
+}
+
+
+def kernel_source_sha(kern):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kern]:
+        with open(os.path.join(ROOT, "paper_1203_2222_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def roofline(prof, clk):
+    """Roofline of the kernel with the largest summed device time.
+
+    box kernels: HBM-bound, algorithmic bytes (block data read once + written
+    once) per launch / mean launch time vs the measured copy bandwidth;
+    tcgen05: useful flops vs the measured bf16 peak / 3 (three BF16 passes);
+    CUDA-core GEMMs: FP32 FMA peak from the unit count and the sampled clock.
+    """
+    if not prof:
+        return None
+    peaks, peak_src = load_peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    n = max(d["launches"], 1)
+    sec = d["ms"] * 1e-3 / n  # mean launch duration
+    if dom.startswith("box"):
+        bound, unit, per = "hbm", "GB/s", d["bytes"] / n
+        achieved, peak = per / sec / 1e9, peaks["hbm_gbs"]
+        src = f"{peak_src} hbm_gbs"
+    elif dom == "gemm_tc":
+        bound, unit, per = "tensor", "TFLOP/s", d["flops"] / n
+        achieved, peak = per / sec / 1e12, peaks["bf16_tflops"] / 3.0
+        src = f"{peak_src} bf16_tflops (burst, kernels of a short step) / 3 passes"
+    else:
+        mhz = clk.get("sm_mhz") or 2070.0
+        bound, unit, per = "alu", "TFLOP/s", d["flops"] / n
+        achieved, peak = per / sec / 1e12, 152 * 128 * 2 * mhz * 1e6 / 1e12
+        src = "152 SMs x 128 FP32 FMA/clk x 2 flops x sampled SM clock"
+    t = TRAFFIC.get(dom)
+    traffic = t["bytes_per_launch"] if t and t["sha"] == kernel_source_sha(dom) else None
+    return {"bound": bound, "kernel": dom, "symbol": __import__("paper_1203_2222_gb300").KERNEL_SYMBOLS[dom],
+            "achieved": round(achieved, 4), "peak": round(peak, 1), "unit": unit, "frac": round(achieved / peak, 4),
+            "traffic": traffic, "algorithmic_per_launch": per, "launches_timed": d["launches"],
+            "avg_launch_us": round(sec * 1e6, 2), "peak_source": src}
+
+
 # -------------------------------------------------------------- our path ---
 
 def run_ours(args, rank, world):
@@ -318,11 +387,10 @@ def run_ours(args, rank, world):
 
     def accumulate():
         for p in plans:
-            for name, ph in P.PHASES.items():
-                r = p.profile_read(ph)
+            for kern, kid in P.KERNELS.items():
+                r = p.profile_kernel(kid)
                 if r["launches"] == 0:
                     continue
-                kern = "gemm_tc" if "gemm_tc" in name else "gemm_cuda_cores" if "gemm" in name else "box"
                 d = prof.setdefault(kern, {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
                 for k in d:
                     d[k] += r[k]
@@ -405,42 +473,11 @@ def run_ours(args, rank, world):
     ms_e2e = sum(a.elapsed_time(b) for a, b in ee) / args.steps
     e2e_value = flops * world / (ms_e2e * 1e-3) / 1e12
 
-    # ---- roofline of the dominant kernel
-    peaks, peak_src = load_peaks()
-    dom = max(prof, key=lambda k: prof[k]["ms"]) if prof else None
-    roof = None
-    if dom == "gemm_tc":
-        d = prof[dom]
-        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
-        peak = peaks["bf16_tflops_sustained"] / 3.0
-        roof = {"bound": "tensor", "kernel": "gemm_tc_kernel (split-BF16 x3, useful flops)",
-                "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": f"{peak_src} bf16_tflops_sustained / 3 passes"}
-    elif dom == "gemm_cuda_cores":
-        d = prof[dom]
-        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
-        # FP32 CUDA cores: 152 SMs x 128 FMA/clk x 2 flops at the sampled SM clock
-        mhz = (clk.get("sm_mhz") or 2070.0)
-        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "kernel": "gemm_simt/gemm_thin (FP32 CUDA cores)",
-                "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x sampled SM clock"}
-    elif dom == "box":
-        d = prof[dom]
-        achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
-        peak = peaks["hbm_gbs"]
-        roof = {"bound": "hbm", "kernel": "box_kernel (block gathers/scatters)",
-                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "peak_source": f"{peak_src} hbm_gbs"}
-    if roof is not None:
-        d = prof[dom]
-        roof["launches_timed"] = d["launches"]
-        roof["avg_launch_us"] = round(d["ms"] * 1e3 / max(d["launches"], 1), 2)
-    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+    # ---- roofline of the dominant kernel (largest summed device time)
+    roof = roofline(prof, clk)
+    kernels = {k: {"symbol": P.KERNEL_SYMBOLS[k], "launches": v["launches"], "ms": round(v["ms"], 4),
                    "share": round(v["ms"] / max(sum(x["ms"] for x in prof.values()), 1e-12), 4)}
-               for k, v in prof.items()}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
 
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": world,

@@ -193,6 +193,20 @@ int sym_plan_profile(sym_plan plan, int enable);
 int sym_plan_profile_read(sym_plan plan, int phase, int* launches,
                           double* total_ms, double* bytes, double* flops);
 
+/* The same records by kernel: sym_plan_profile_kernel returns launches,
+ * summed device time, algorithmic bytes and useful flops of the recorded
+ * launches of one kernel (SYM_KERNEL_*), over all phases.                */
+#define SYM_KERNEL_BOX 0       /* block movement, general form (tiles, recoupling sums) */
+#define SYM_KERNEL_BOX_FLAT 1  /* block movement, launches of flat linear items only */
+#define SYM_KERNEL_GEMM_TC 2   /* tcgen05 split-BF16 x3 grouped GEMM */
+#define SYM_KERNEL_GEMM_TILE 3 /* CUDA cores, 64 x 64 tiles */
+#define SYM_KERNEL_GEMM_WIDE 4 /* CUDA cores, 256 x 16 tiles */
+#define SYM_KERNEL_GEMM_THIN 5 /* CUDA cores, m, n <= 8, split reduction */
+#define SYM_KERNEL_GEMM_ROWS 6 /* CUDA cores, k, n <= 16 */
+#define SYM_KERNEL_COUNT 7
+int sym_plan_profile_kernel(sym_plan plan, int kernel, int* launches,
+                            double* total_ms, double* bytes, double* flops);
+
 /* Number of kernel launches the last execution call on this plan issued. */
 int sym_plan_launches(sym_plan plan, int* launches);
 

@@ -8,4 +8,5 @@ this package is its Python front end.
 """
 from .symtensor import (BF16X3, FP64, SU2, U1, Plan, Structure, SymError, SymTensor, contract,  # noqa: F401
                         contract_plan, device_status, fuse, fuse_plan, permute, permute_plan, split,
-                        split_plan, su2_F, su2_gamma, PHASES, cached_plans)
+                        split_plan, su2_F, su2_gamma, PHASES, KERNELS, KERNEL_SYMBOLS,
+                        cached_plans)

@@ -73,6 +73,7 @@ _SIGS = {
     "sym_plan_launches": ([_P, _IP], _I),
     "sym_plan_profile": ([_P, _I], _I),
     "sym_plan_profile_read": ([_P, _I, _IP, _DP, _DP, _DP], _I),
+    "sym_plan_profile_kernel": ([_P, _I, _IP, _DP, _DP, _DP], _I),
     "sym_plan_destroy": ([_P], _I),
     "sym_plan_gemm_shapes": ([_P, _IP, _IP], _I),
     "sym_device_status": ([], _I),

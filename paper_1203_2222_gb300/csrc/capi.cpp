@@ -298,23 +298,51 @@ int sym_plan_profile(sym_plan plan, int enable) {
   });
 }
 
+namespace {
+// device time of one recorded launch (waits for its end event)
+double launch_ms(const sym::LaunchRecord& e) {
+  cudaError_t err = cudaEventSynchronize(static_cast<cudaEvent_t>(e.e1));
+  if (err != cudaSuccess) sym::fail(SYM_ERR_CUDA, std::string("event: ") + cudaGetErrorString(err));
+  float t = 0.f;
+  cudaEventElapsedTime(&t, static_cast<cudaEvent_t>(e.e0), static_cast<cudaEvent_t>(e.e1));
+  return t;
+}
+}  // namespace
+
 int sym_plan_profile_read(sym_plan plan, int phase, int* launches, double* total_ms, double* bytes, double* flops) {
   return guard([&] {
     need(plan && plan->p, "plan is NULL");
     need(phase >= 0 && phase < sym::PH_COUNT, "bad phase");
     sym::PhaseProfile& pp = plan->p->prof[phase];
     double ms = 0.0;
-    for (auto& e : pp.events) {
-      cudaError_t err = cudaEventSynchronize(static_cast<cudaEvent_t>(e.second));
-      if (err != cudaSuccess) sym::fail(SYM_ERR_CUDA, std::string("event: ") + cudaGetErrorString(err));
-      float t = 0.f;
-      cudaEventElapsedTime(&t, static_cast<cudaEvent_t>(e.first), static_cast<cudaEvent_t>(e.second));
-      ms += t;
-    }
+    for (auto& e : pp.events) ms += launch_ms(e);
     if (launches) *launches = pp.launches;
     if (total_ms) *total_ms = ms;
     if (bytes) *bytes = pp.bytes;
     if (flops) *flops = pp.flops;
+    return SYM_OK;
+  });
+}
+
+int sym_plan_profile_kernel(sym_plan plan, int kernel, int* launches, double* total_ms, double* bytes,
+                            double* flops) {
+  return guard([&] {
+    need(plan && plan->p, "plan is NULL");
+    need(kernel >= 0 && kernel < SYM_KERNEL_COUNT, "bad kernel");
+    int n = 0;
+    double ms = 0.0, by = 0.0, fl = 0.0;
+    for (const sym::PhaseProfile& pp : plan->p->prof)
+      for (const auto& e : pp.events)
+        if (e.kernel == kernel) {
+          ++n;
+          ms += launch_ms(e);
+          by += e.bytes;
+          fl += e.flops;
+        }
+    if (launches) *launches = n;
+    if (total_ms) *total_ms = ms;
+    if (bytes) *bytes = by;
+    if (flops) *flops = fl;
     return SYM_OK;
   });
 }

@@ -493,8 +493,8 @@ void Plan::set_item_bytes(Range r, int es_src, int es_dst) {
 void Plan::clear_profile() {
   for (auto& p : prof) {
     for (auto& e : p.events) {
-      cudaEventDestroy(static_cast<cudaEvent_t>(e.first));
-      cudaEventDestroy(static_cast<cudaEvent_t>(e.second));
+      cudaEventDestroy(static_cast<cudaEvent_t>(e.e0));
+      cudaEventDestroy(static_cast<cudaEvent_t>(e.e1));
     }
     p = PhaseProfile{};
   }
@@ -1269,10 +1269,12 @@ int cuda_code(int e, const char* what) {
 
 struct ProfScope {
   Plan& p;
-  int phase;
+  int phase, kernel;
+  double bytes, flops;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaStream_t s;
-  ProfScope(Plan& p_, int ph, void* stream, double bytes, double flops) : p(p_), phase(ph) {
+  ProfScope(Plan& p_, int ph, int kern, void* stream, double by, double fl)
+      : p(p_), phase(ph), kernel(kern), bytes(by), flops(fl) {
     s = static_cast<cudaStream_t>(stream);
     if (!p.profiling) return;
     cudaEventCreate(&e0);
@@ -1295,15 +1297,16 @@ struct ProfScope {
   ~ProfScope() {
     if (!p.profiling) return;
     record(e1);
-    p.prof[phase].events.push_back({e0, e1});
+    p.prof[phase].events.push_back(LaunchRecord{e0, e1, kernel, bytes, flops});
   }
 };
 
 int run_box(Plan& p, Range r, const BoxPtrs& ptrs, void* stream, int phase) {
   if (r.count <= 0) return SYM_OK;
   p.last_launches++;
-  ProfScope ps(p, phase, stream, p.item_bytes_prefix[r.first + r.count] - p.item_bytes_prefix[r.first], 0.0);
   const bool flat_only = p.flat_prefix[r.first + r.count] - p.flat_prefix[r.first] == r.count;
+  ProfScope ps(p, phase, flat_only ? SYM_KERNEL_BOX_FLAT : SYM_KERNEL_BOX, stream,
+               p.item_bytes_prefix[r.first + r.count] - p.item_bytes_prefix[r.first], 0.0);
   return cuda_code(launch_box(p.f64(), p.f64(), flat_only, p.d_items + r.first, r.count, p.d_terms, ptrs, stream),
                    "box kernel");
 }
@@ -1312,7 +1315,10 @@ int run_gemm_kind(Plan& p, int kind, Range r, void* stream, int phase) {
   if (r.count <= 0) return SYM_OK;
   p.last_launches++;
   if (kind != 0) phase = phase == PH_FWD_GEMM ? PH_FWD_GEMM_SIMT : PH_BWD_GEMM_SIMT;
-  ProfScope ps(p, phase, stream, 0.0, p.tile_flops_prefix[r.first + r.count] - p.tile_flops_prefix[r.first]);
+  static const int kernel_of_kind[kGemmKinds] = {SYM_KERNEL_GEMM_TC, SYM_KERNEL_GEMM_TILE, SYM_KERNEL_GEMM_WIDE,
+                                                 SYM_KERNEL_GEMM_THIN, SYM_KERNEL_GEMM_ROWS};
+  ProfScope ps(p, phase, kernel_of_kind[kind], stream, 0.0,
+               p.tile_flops_prefix[r.first + r.count] - p.tile_flops_prefix[r.first]);
   if (kind == 0)
     return cuda_code(launch_gemm_tc(p.d_secs_tc, p.d_tiles + r.first, r.count, p.d_maps,
                                     static_cast<float*>(p.outm), p.d_err, stream),

@@ -25,8 +25,16 @@ enum Phase { PH_FWD_GATHER = 0, PH_FWD_GEMM, PH_FWD_SCATTER, PH_BWD_GATHER, PH_B
              PH_XFORM, PH_FWD_GEMM_SIMT, PH_BWD_GEMM_SIMT, PH_COUNT };
 constexpr int kGemmKinds = 5;  // 0 tcgen05, CUDA cores: 1 tile 64x64, 2 tile 256x16, 3 thin, 4 rows
 
+// One recorded launch: cudaEvent_t pair around it, kernel (SYM_KERNEL_*),
+// algorithmic bytes and useful flops.
+struct LaunchRecord {
+  void* e0;
+  void* e1;
+  int kernel;
+  double bytes, flops;
+};
 struct PhaseProfile {
-  std::vector<std::pair<void*, void*>> events;  // cudaEvent_t pairs around each launch
+  std::vector<LaunchRecord> events;
   int launches = 0;
   double bytes = 0.0, flops = 0.0;  // algorithmic, summed over the recorded launches
 };
