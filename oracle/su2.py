@@ -203,6 +203,47 @@ def embed(legs, nodes, data):
     return dense
 
 
+def embed_slice(legs, nodes, data, fixed):
+    """Sub-tensor of embed(legs, nodes, data) with some legs held at one index.
+
+    ``fixed`` maps leg -> dense index on that leg; the result runs over the
+    other legs in order (a scalar when every leg is fixed).  Only the sectors
+    whose spins on the fixed legs match contribute, so one slice of a large
+    tensor costs a fraction of the full embedding.  ``data`` may be any flat
+    array indexable by the layout's block offsets (read in FP64).
+    """
+    secs, offs, _ = layout(legs, nodes)
+    loffs = [l.offsets() for l in legs]
+    k = len(legs)
+    dec = {}
+    for l, i in fixed.items():
+        leg = legs[l]
+        for p, (o, j2, d) in enumerate(zip(loffs[l], leg.labels, leg.degens)):
+            if o <= i < o + (j2 + 1) * d:
+                r = i - o
+                dec[l] = (p, r // (j2 + 1), r % (j2 + 1))  # spin position, t, m
+                break
+        else:
+            raise IndexError(f"index {i} outside leg {l}")
+    free = [l for l in range(k) if l not in fixed]
+    out = np.zeros([legs[l].dim for l in free])
+    for s, o in zip(secs, offs):
+        if any(s[0][l] != dec[l][0] for l in fixed):
+            continue
+        shp = block_shape(legs, s)
+        P = np.asarray(data[o:o + int(np.prod(shp, dtype=np.int64))], dtype=np.float64).reshape(shp)
+        Q = structure_tensor(legs, nodes, s)
+        ip = tuple(dec[l][1] if l in fixed else slice(None) for l in range(k))
+        iq = tuple(dec[l][2] if l in fixed else slice(None) for l in range(k))
+        sl = []
+        for l in free:
+            p = s[0][l]
+            n = (legs[l].labels[p] + 1) * legs[l].degens[p]
+            sl.append(slice(loffs[l][p], loffs[l][p] + n))
+        out[tuple(sl)] += _interleave(np.asarray(P[ip]), np.asarray(Q[iq]))
+    return out
+
+
 def extract(legs, nodes, dense):
     """(blocks, residual): P = <Q,T>/<Q,Q> per sector; residual = |T - embed(P)|."""
     secs, offs, n = layout(legs, nodes)

@@ -47,6 +47,11 @@ constexpr uint32_t TMEM_COLS = 256;
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 constexpr uint64_t WAIT_NS = 2000000000ull;
+// The tensor pipe accumulates at most KCHUNK k-tiles (512 of the reduction)
+// in one TMEM accumulator; the epilogue adds the chunks in FP32 registers with
+// round-to-nearest.  Long in-pipe accumulations measured an error growing
+// with k (1.5e-5 relative at k = 4096); per-chunk folding keeps it flat.
+constexpr int KCHUNK = 8;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -264,36 +269,43 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
         const GemmTile t = tiles[ti];
         const TcSector s = secs[t.sector];
-        if (!wait_bar(&tempty[acc], aphase ^ 1u, ctl, err)) break;
-        tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
-        for (int kt = 0; kt < s.ktiles; ++kt) {
-          if (!wait_bar(&full[stage], phase, ctl, err)) {
+        // one TMEM accumulator per chunk of KCHUNK k-tiles, alternating buffers
+        for (int k0 = 0; k0 < s.ktiles && ok; k0 += KCHUNK) {
+          if (!wait_bar(&tempty[acc], aphase ^ 1u, ctl, err)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t base = smem_u32(stages + stage * STAGE_BYTES);
+          const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+          const int k1 = min(s.ktiles, k0 + KCHUNK);
+          for (int kt = k0; kt < k1; ++kt) {
+            if (!wait_bar(&full[stage], phase, ctl, err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t base = smem_u32(stages + stage * STAGE_BYTES);
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t ah = sw128_desc(base + kk * 32);
-            const uint64_t al = sw128_desc(base + TILE_BYTES + kk * 32);
-            const uint64_t bh = sw128_desc(base + 2 * TILE_BYTES + kk * 32);
-            const uint64_t bl = sw128_desc(base + 3 * TILE_BYTES + kk * 32);
-            mma_bf16(d_tmem, ah, bh, (kt | kk) != 0);
-            mma_bf16(d_tmem, ah, bl, 1u);
-            mma_bf16(d_tmem, al, bh, 1u);
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t ah = sw128_desc(base + kk * 32);
+              const uint64_t al = sw128_desc(base + TILE_BYTES + kk * 32);
+              const uint64_t bh = sw128_desc(base + 2 * TILE_BYTES + kk * 32);
+              const uint64_t bl = sw128_desc(base + 3 * TILE_BYTES + kk * 32);
+              mma_bf16(d_tmem, ah, bh, (kt != k0 || kk != 0) ? 1u : 0u);
+              mma_bf16(d_tmem, ah, bl, 1u);
+              mma_bf16(d_tmem, al, bh, 1u);
+            }
+            mma_commit(&empty[stage]);
+            if (++stage == STAGES) {
+              stage = 0;
+              phase ^= 1u;
+            }
           }
-          mma_commit(&empty[stage]);
-          if (++stage == STAGES) {
-            stage = 0;
-            phase ^= 1u;
-          }
+          if (!ok) break;
+          mma_commit(&tfull[acc]);
+          acc ^= 1;
+          if (acc == 0) aphase ^= 1u;
         }
-        if (!ok) break;
-        mma_commit(&tfull[acc]);
-        acc ^= 1;
-        if (acc == 0) aphase ^= 1u;
       }
       // all MMAs issued by this thread complete before TMEM is released
       mma_commit(mma_done);
@@ -304,34 +316,51 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     float* buf = epi + (warp - 2) * 32 * EPI_PITCH;
     int acc = 0;
     uint32_t aphase = 0;
-    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    bool ok = true;
+    for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
       const GemmTile t = tiles[ti];
       const TcSector s = secs[t.sector];
-      if (!wait_bar(&tfull[acc], aphase, ctl, err)) break;
-      tc_fence_after();
+      // this thread's row of the 128 x 128 tile, summed over the k chunks
+      float racc[BN];
+#pragma unroll
+      for (int i = 0; i < BN; ++i) racc[i] = 0.0f;
+      for (int k0 = 0; k0 < s.ktiles; k0 += KCHUNK) {
+        if (!wait_bar(&tfull[acc], aphase, ctl, err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int c = 0; c < BN; c += 32) {
+          uint32_t r[32];
+          tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
+          tmem_ld_wait();
+#pragma unroll
+          for (int i = 0; i < 32; ++i) racc[c + i] += __uint_as_float(r[i]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[acc]);
+        acc ^= 1;
+        if (acc == 0) aphase ^= 1u;
+      }
+      if (!ok) break;
+      // transpose through shared memory: coalesced row segments of C
       const int row_base = t.mt * BM + q * 32;
+#pragma unroll
       for (int c = 0; c < BN; c += 32) {
         const int col0 = t.nt * BN + c;
-        if (col0 >= s.n) break;
-        uint32_t r[32];
-        tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
-        tmem_ld_wait();
 #pragma unroll
-        for (int i = 0; i < 32; ++i) buf[lane * EPI_PITCH + i] = __uint_as_float(r[i]);
+        for (int i = 0; i < 32; ++i) buf[lane * EPI_PITCH + i] = racc[c + i];
         __syncwarp();
         const int col = col0 + lane;
-        for (int rr = 0; rr < 32; ++rr) {
-          const int row = row_base + rr;
-          if (row < s.m && col < s.n)
-            C[s.c_off + (int64_t)row * s.ldc + col] = s.alpha * buf[rr * EPI_PITCH + lane];
-        }
+        if (col < s.n)
+          for (int rr = 0; rr < 32; ++rr) {
+            const int row = row_base + rr;
+            if (row < s.m) C[s.c_off + (int64_t)row * s.ldc + col] = s.alpha * buf[rr * EPI_PITCH + lane];
+          }
         __syncwarp();
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[acc]);
-      acc ^= 1;
-      if (acc == 0) aphase ^= 1u;
     }
   }
   tc_fence_before();

@@ -312,3 +312,39 @@ def test_contract_grad_matches_finite_differences(group):
         va, vb = rng.standard_normal(a.size), rng.standard_normal(b.size)
         fd = (f(a + h * va, b + h * vb) - f(a - h * va, b - h * vb)) / (2 * h)
         assert fd == pytest.approx(float(dA @ va + dB @ vb), rel=1e-7, abs=1e-8)
+
+
+# ------------------------------------------------------- sampled dense elements ---
+
+@pytest.mark.parametrize("tree", [None, [(1, 2), (0, 4), (5, 3)], [(0, 1), (2, 3), (4, 5)]])
+def test_su2_embed_slice_is_the_slice_of_the_embedding(tree):
+    # embed_slice only visits the sectors whose spins match the fixed legs: every
+    # pattern of fixed legs must reproduce the same slice of the full embedding
+    rng = _rng(11)
+    legs = [su2.Leg([0, 1, 2], [2, 1, 2], 1), su2.Leg([1, 3], [1, 2], -1),
+            su2.Leg([0, 2], [2, 1], 1), su2.Leg([1, 2, 3], [1, 1, 2], 1)]
+    nodes = tree or su2.left_comb(4)
+    n = su2.layout(legs, nodes)[2]
+    x = rng.standard_normal(n)
+    dense = su2.embed(legs, nodes, x)
+    for fixed in ({0: 3}, {1: 2, 3: 5}, {0: 1, 1: 0, 2: 3, 3: 4}, {2: 0}, {}):
+        idx = tuple(fixed.get(l, slice(None)) for l in range(4))
+        assert np.array_equal(su2.embed_slice(legs, nodes, x, fixed), dense[idx])
+
+
+def test_su2_sampled_contraction_element_matches_dense_contraction():
+    # one element of C = contract(A, B) from two embedded slices equals the
+    # element of the dense brute-force contraction
+    rng = _rng(12)
+    la = [su2.Leg([0, 1, 2], [1, 2, 1], 1) for _ in range(4)]
+    lb = [la[1].dual(), la[3].dual(), su2.Leg([0, 2], [2, 1], 1), su2.Leg([1, 3], [1, 1], 1)]
+    na, nb = su2.layout(la, su2.left_comb(4))[2], su2.layout(lb, su2.left_comb(4))[2]
+    xa, xb = rng.standard_normal(na), rng.standard_normal(nb)
+    Ad, Bd = su2.embed(la, su2.left_comb(4), xa), su2.embed(lb, su2.left_comb(4), xb)
+    Cd = oc.contract_dense(Ad, Bd, [1, 3], [0, 1])
+    for _ in range(12):
+        i0, i2 = (int(rng.integers(l.dim)) for l in (la[0], la[2]))
+        i4, i5 = (int(rng.integers(l.dim)) for l in (lb[2], lb[3]))
+        sa = su2.embed_slice(la, su2.left_comb(4), xa, {0: i0, 2: i2})
+        sb = su2.embed_slice(lb, su2.left_comb(4), xb, {2: i4, 3: i5})
+        assert abs(float(np.sum(sa * sb)) - Cd[i0, i2, i4, i5]) <= 1e-12 * max(1.0, abs(Cd[i0, i2, i4, i5]))
