@@ -271,6 +271,78 @@ __device__ __forceinline__ void tile_item(const BoxItem& it, const TS* __restric
   __syncwarp();
 }
 
+// Fused recoupling item (kSelRecouple): for every position of the box, the
+// n_s source values are loaded once and the n_d destinations receive their
+// coefficient-weighted sums (Ch. 6, Eq. permsu2, all output labels of one
+// set of leg spins at once).  Coefficients and offsets are staged in the
+// warp's shared-memory tile; two positions per lane are in flight (FP32).
+template <int ND, typename TS, typename TD>
+__device__ __forceinline__ void recouple_item(const BoxItem& it, const Term* __restrict__ terms,
+                                              const TS* __restrict__ src, void* dstv, int64_t lo_off, bool split,
+                                              TD (*tile)[33], int lane) {
+  const int ns = it.nterm, nd = it.p0;
+  const Term* T = terms + it.term0;
+  TD* cf = &tile[0][0];                                               // [nd][ns]
+  int64_t* soff = reinterpret_cast<int64_t*>(cf + kMaxRecouple * kMaxRecouple);
+  int64_t* sld = soff + kMaxRecouple;
+  int64_t* doff = sld + kMaxRecouple;
+  int64_t* dld = doff + kMaxRecouple;
+  for (int i = lane; i < nd * ns; i += 32) {
+    const Term& c = T[ns + nd + i];
+    cf[i] = coef<TD>(c.coef, c.coef_f);
+  }
+  if (lane < ns) {
+    soff[lane] = T[lane].off;
+    sld[lane] = T[lane].ld;
+  }
+  if (lane < nd) {
+    doff[lane] = T[ns + lane].off;
+    dld[lane] = T[ns + lane].ld;
+  }
+  __syncwarp();
+  const Shape<ND> sh(it);
+  int sa[ND], sb[ND], da[ND], db[ND];
+  load_strides(it.sa, sa);
+  load_strides(it.sb, sb);
+  load_strides(it.da, da);
+  load_strides(it.db, db);
+  const int last = it.start + it.count - 1;
+  constexpr int H = sizeof(TD) == 4 ? 2 : 1;  // positions in flight per lane
+#pragma unroll 1
+  for (int u = 0; u < kBatch; u += H) {
+    int a[H], b[H], c[H], e[H];
+    TD v[H][kMaxRecouple];
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      int t[ND];
+      sh.split(min(it.start + lane + 32 * (u + h), last), t);
+      a[h] = dot(t, sa);
+      b[h] = dot(t, sb);
+      c[h] = dot(t, da);
+      e[h] = dot(t, db);
+#pragma unroll
+      for (int q = 0; q < kMaxRecouple; ++q)
+        v[h][q] = q < ns ? TD(__ldg(src + soff[q] + sld[q] * a[h] + b[h])) : TD(0);
+    }
+#pragma unroll 1
+    for (int d = 0; d < nd; ++d) {
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        TD acc = TD(0);
+#pragma unroll
+        for (int q = 0; q < kMaxRecouple; ++q)
+          if (q < ns) acc += cf[d * ns + q] * v[h][q];
+        const int64_t o = doff[d] + dld[d] * c[h] + e[h];
+        if (split)
+          store_split(static_cast<__nv_bfloat16*>(dstv), lo_off, o, (float)acc);
+        else
+          static_cast<TD*>(dstv)[o] = acc;
+      }
+    }
+  }
+  __syncwarp();
+}
+
 template <typename TS, typename TD>
 __device__ __forceinline__ const TS* src_slot(const BoxItem& it, const BoxPtrs& ptrs) {
   const int k = it.sel & 3;
@@ -348,6 +420,16 @@ __device__ __forceinline__ void run_item(const BoxItem& it, const Term* __restri
   }
   const TS* sp = src_slot<TS, TD>(it, ptrs);
   void* dp = dst_slot(it, ptrs);
+  if (it.sel & kSelRecouple) {
+    const bool split = ((it.sel >> 4) & 7) == DST_SPLIT;
+    switch (it.ndim) {
+      case 1: recouple_item<1, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
+      case 2: recouple_item<2, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
+      case 3: recouple_item<3, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
+      default: recouple_item<kMaxDim, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
+    }
+    return;
+  }
   Src<TS, TD> src;
   src.p = sp;
   src.terms = terms;

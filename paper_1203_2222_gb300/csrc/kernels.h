@@ -18,6 +18,14 @@ constexpr int kSelTile = 1 << 9;   // BoxItem::sel flag: 32 x 32 transposing til
 // kernel addresses source and destination with one 32-bit dot product each
 constexpr int kSelFlat = 1 << 10;
 constexpr int kSelUnit = 1 << 11;  // BoxItem::sel flag: one term whose coefficient is exactly 1
+// BoxItem::sel flag: fused recoupling item.  nterm = n_s sources and p0 = n_d
+// destinations share the box; terms[term0 .. term0 + n_s) are the sources
+// (src[off + ld <t, sa> + <t, sb>]), the next n_d the destinations
+// (dst[off + ld <t, da> + <t, db>]), then the n_d x n_s coefficients
+// (row-major, in coef / coef_f): destination d receives
+// sum_s coef[d][s] source_s.  Each source element is read once for all d.
+constexpr int kSelRecouple = 1 << 12;
+constexpr int kMaxRecouple = 16;  // largest n_s and n_d of a fused recoupling item
 constexpr int kBoxChunk = 512;  // elements of a linear work item (32 lanes x 16)
 
 // One work unit of the block-movement kernel: a strided box of `dims`

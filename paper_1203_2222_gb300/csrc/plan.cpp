@@ -203,6 +203,42 @@ void emit(Plan& P, const Box& box0, int64_t dst_off, int dst_ld, int src_slot, i
   }
 }
 
+// Fused recoupling (kSelRecouple): destinations d = 0..n_d-1 that share the
+// source blocks s = 0..n_s-1 and the box, destination d receiving
+// sum_s coef[d][s] source_s.  srcs/dsts hold (offset, ld) of each side (the
+// element at box index t is at off + ld <t, a> + <t, b>).  Returns false
+// (nothing emitted) when the box's last dim is not contiguous on both sides
+// or the group is too large; the caller then emits per-destination items.
+bool emit_recouple(Plan& P, const Box& box0, const std::vector<std::pair<int64_t, int64_t>>& srcs,
+                   const std::vector<std::pair<int64_t, int64_t>>& dsts, const std::vector<double>& coef,
+                   int src_slot, int dst_slot) {
+  const int ns = (int)srcs.size(), nd = (int)dsts.size();
+  if (ns < 1 || nd < 1 || ns > kMaxRecouple || nd > kMaxRecouple) return false;
+  const Box box = simplify(box0);
+  const int q = box.ndim - 1;
+  for (auto& x : srcs)
+    if (x.second * box.sa[q] + box.sb[q] != 1) return false;
+  for (auto& x : dsts)
+    if (x.second * box.da[q] + box.db[q] != 1) return false;
+  int64_t total = 1;
+  for (int i = 0; i < box.ndim; ++i) total *= box.dims[i];
+  if (total >= (int64_t)1 << 31) fail(SYM_ERR_UNSUPPORTED, "block larger than 2^31 elements");
+  const int term0 = (int)P.terms.size();
+  for (auto& x : srcs) P.terms.push_back(Term{x.first, x.second, 0.0, 0.0f, 0});
+  for (auto& x : dsts) P.terms.push_back(Term{x.first, x.second, 0.0, 0.0f, 0});
+  for (double c : coef) P.terms.push_back(Term{0, 0, c, (float)c, 0});
+  const std::vector<Term> none;
+  for (int64_t st = 0; st < total; st += kChunk) {
+    BoxItem it = make_item(box, 0, 0, src_slot | (dst_slot << 4) | kSelRecouple, term0, none);
+    it.nterm = ns;
+    it.p0 = nd;
+    it.start = (int)st;
+    it.count = (int)std::min<int64_t>(kChunk, total - st);
+    P.items.push_back(it);
+  }
+  return true;
+}
+
 void block_strides(const Tensor& T, int64_t s, int* st) {
   int64_t acc = 1;
   for (int l = T.rank - 1; l >= 0; --l) {
@@ -474,6 +510,18 @@ void Plan::validate(const int64_t* src_elems, const int64_t* dst_elems) const {
       if (t.off < 0 || t.ld < 0 || t.off + t.ld * sa + sb >= src_elems[ss])
         fail(SYM_ERR_ARG, "internal: work item reads past its source buffer");
     }
+    if (it.sel & kSelRecouple) {
+      const int ns = it.nterm, nd = it.p0;
+      if (ns < 1 || nd < 1 || ns > kMaxRecouple || nd > kMaxRecouple || (it.sel & (kSelTile | kSelFlat)) ||
+          (size_t)it.term0 + ns + nd + (size_t)ns * nd > terms.size())
+        fail(SYM_ERR_ARG, "internal: bad recoupling item");
+      for (int i = 0; i < nd; ++i) {
+        const Term& t = terms[it.term0 + ns + i];
+        if (t.off < 0 || t.ld < 0 || t.off + t.ld * da + db >= dst_elems[ds])
+          fail(SYM_ERR_ARG, "internal: recoupling item writes past its destination");
+      }
+      continue;
+    }
     const int64_t last = it.dst_off + (int64_t)it.dst_ld * da + db;
     if (it.dst_off < 0 || last >= dst_elems[ds]) fail(SYM_ERR_ARG, "internal: work item writes past its destination");
   }
@@ -486,7 +534,10 @@ void Plan::set_item_bytes(Range r, int es_src, int es_dst) {
     double elems = (double)it.count;
     if (it.sel & kSelTile)
       elems *= (double)std::min(32, it.dims[it.ndim - 2] - it.p0) * std::min(32, it.dims[it.ndim - 1] - it.q0);
-    item_bytes_prefix[i + 1] = elems * ((it.nterm > 0 ? es_src : 0) + es_dst);
+    if (it.sel & kSelRecouple)  // every source read once, every destination written once
+      item_bytes_prefix[i + 1] = elems * ((double)it.nterm * es_src + (double)it.p0 * es_dst);
+    else
+      item_bytes_prefix[i + 1] = elems * ((it.nterm > 0 ? es_src : 0) + es_dst);
   }
 }
 
@@ -1050,11 +1101,72 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     emit(*P, b, off, (int)cols, 3, DST_OUTM, {});
   };
 
+  // Fused recoupling of one gather or scatter (SU(2)): destinations whose
+  // recoupling sums run over the same source sectors (the same leg spins)
+  // and that write the same buffer form one group, emitted as fused items;
+  // `done` marks the destinations emitted that way.  dst_of(d) gives the
+  // destination's (offset, ld) and slot, src_of(s) a source's (offset, ld),
+  // box_of(d, s) the shared box.
+  using OffLd = std::pair<int64_t, int64_t>;
+  auto fuse_recoupling = [&](int64_t ndst, const std::vector<TermList>& X, int src_slot,
+                             const std::function<bool(int64_t, OffLd&, int&)>& dst_of,
+                             const std::function<OffLd(int64_t)>& src_of,
+                             const std::function<Box(int64_t, int64_t)>& box_of, std::vector<char>& done) {
+    done.assign(ndst, 0);
+    if (!su2) return;
+    std::map<std::pair<std::vector<int64_t>, int>, std::vector<int64_t>> groups;
+    for (int64_t d = 0; d < ndst; ++d) {
+      OffLd o;
+      int slot;
+      if (X[d].size() < 2 || !dst_of(d, o, slot)) continue;
+      std::vector<int64_t> key;
+      for (auto& pc : X[d]) key.push_back(pc.first);
+      std::sort(key.begin(), key.end());
+      groups[{key, slot}].push_back(d);
+    }
+    for (auto& gr : groups) {
+      const std::vector<int64_t>& srcs = gr.first.first;
+      const std::vector<int64_t>& ds = gr.second;
+      std::vector<OffLd> so, dof;
+      for (int64_t sidx : srcs) so.push_back(src_of(sidx));
+      std::vector<double> coef(ds.size() * srcs.size(), 0.0);
+      for (size_t i = 0; i < ds.size(); ++i) {
+        OffLd o;
+        int slot;
+        dst_of(ds[i], o, slot);
+        dof.push_back(o);
+        for (auto& pc : X[ds[i]])
+          coef[i * srcs.size() + (std::lower_bound(srcs.begin(), srcs.end(), pc.first) - srcs.begin())] += pc.second;
+      }
+      if (emit_recouple(*P, box_of(ds[0], srcs[0]), so, dof, coef, src_slot, gr.first.second))
+        for (int64_t d : ds) done[d] = 1;
+    }
+  };
+
   // ---- forward gather: A -> A operand, B -> B operand (+ zero fills)
   int begin = (int)P->items.size();
+  std::vector<char> doneA;
+  fuse_recoupling(
+      Am.nsec(), XA, 0,
+      [&](int64_t s, OffLd& o, int& slot) {
+        auto gi = gofx.find(MA.xs[MA.sx[s]]);
+        if (gi == gofx.end()) return false;
+        const G& g = gs[gi->second];
+        if (g.kind[0] == 0) {
+          const TcOperand& op = P->tc_ops[g.oa];
+          o = {op.off + MA.r0[s] * op.ld + MA.c0[s], op.ld};
+          slot = DST_SPLIT;
+        } else {
+          o = {g.a + MA.r0[s] * g.k + MA.c0[s], g.k};
+          slot = DST_OPS;
+        }
+        return true;
+      },
+      [&](int64_t sa) { return OffLd{A.offs[sa], 1}; },
+      [&](int64_t s, int64_t sa) { return gather_box(A, pinvA, Am, s, sa, na, false); }, doneA);
   for (int64_t s = 0; s < Am.nsec(); ++s) {
     auto gi = gofx.find(MA.xs[MA.sx[s]]);
-    if (gi == gofx.end() || XA[s].empty()) continue;
+    if (gi == gofx.end() || XA[s].empty() || doneA[s]) continue;
     const G& g = gs[gi->second];
     Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, false);
     if (g.kind[0] == 0)
@@ -1178,7 +1290,30 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
 
   // ---- backward scatters: dA_x -> dA blocks (Gamma^T), dB_x -> dB blocks
   begin = (int)P->items.size();
+  std::vector<char> doneDA;
+  fuse_recoupling(
+      A.nsec(), XAt, 3,
+      [&](int64_t s, OffLd& o, int& slot) {
+        for (auto& pc : XAt[s])
+          if (gofx.find(MA.xs[MA.sx[pc.first]]) == gofx.end()) return false;
+        o = {A.offs[s], 1};
+        slot = DST_DA;
+        return true;
+      },
+      [&](int64_t sm) {
+        const G& g = gs[gofx.at(MA.xs[MA.sx[sm]])];
+        return OffLd{g.da + MA.r0[sm] * g.k + MA.c0[sm], g.k};
+      },
+      [&](int64_t s, int64_t sm) {
+        group_weights(Am, sm, na, rw, cw);
+        block_strides(A, s, st);
+        Box b;
+        for (int l = 0; l < A.rank; ++l) b.push(A.dim(s, l), rw[pinvA[l]], cw[pinvA[l]], st[l], 0);
+        return b;
+      },
+      doneDA);
   for (int64_t s = 0; s < A.nsec(); ++s) {
+    if (doneDA[s]) continue;
     std::vector<Term> t;
     int64_t sm0 = -1;
     for (auto& pc : XAt[s]) {

@@ -81,10 +81,11 @@ class Structure:
 class Plan:
     """Precomputed tables + scratch of one operation (owned handle)."""
 
-    def __init__(self, handle, out, kind):
+    def __init__(self, handle, out, kind, precision=None):
         self._h = handle
         self.out = out
         self.kind = kind
+        self.precision = precision
 
     def stats(self):
         f = ctypes.c_double()
@@ -176,7 +177,7 @@ def contract_plan(A, B, pairsA, pairsB, precision=BF16X3, tree_c=None):
     L.check(L.lib.sym_contract_plan(A._h, B._h, len(pairsA), L.int_array(pairsA), L.int_array(pairsB),
                                     L.tree_array(tree_c), int(precision), _byref(c), _byref(p)))
     out = Structure(A.group, total=A.total + B.total, _handle=c)
-    plan = Plan(p, out, "contract")
+    plan = Plan(p, out, "contract", int(precision))
     _PLANS[key] = (plan, A, B)
     return plan
 
