@@ -82,7 +82,7 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// one 64 x 128 x 1 box of a 3-D tensor map at (x, y, z) into shared memory
+// one box of a 3-D tensor map at (x, y, z) into shared memory
 __device__ __forceinline__ void tma_load_3d(void* sdst, const TensorMap* map, int x, int y, int z, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
@@ -107,12 +107,13 @@ __device__ __forceinline__ void tmem_relinquish() {
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accum)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
       : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -145,6 +146,33 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= (uint64_t)1 << 46;
   d |= (uint64_t)2 << 61;
   return d;
+}
+// MN-major, 128-byte swizzle: rows of 64 MN elements (128 bytes) along K,
+// 8-row K groups 1024 bytes apart (SBO), the two 64-wide MN halves of the
+// 128-wide tile 8192 bytes apart (LBO).  Every address an MMA of K = 16
+// touches stays inside the 16 KB tile.
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(8192 >> 4) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// one operand tile (128 rows of the M or N dim x 64 of K) of k-tile kt: a
+// K-major map yields it in one 64 x 128 box, an MN-major map in two 64 x 64
+// boxes (the MN halves, 8 KB apart)
+__device__ __forceinline__ void load_operand(uint8_t* sp, const TensorMap* map, bool mn, int row0, int kt, int plane,
+                                             uint64_t* bar);
+
+__device__ __forceinline__ void load_operand(uint8_t* sp, const TensorMap* map, bool mn, int row0, int kt, int plane,
+                                             uint64_t* bar) {
+  if (mn) {  // x = MN offset (128-byte aligned), y = k
+    tma_load_3d(sp, map, row0, kt * 64, plane, bar);
+    tma_load_3d(sp + TILE_BYTES / 2, map, row0 + 64, kt * 64, plane, bar);
+  } else {   // x = k offset (128-byte aligned), y = row
+    tma_load_3d(sp, map, kt * 64, row0, plane, bar);
+  }
 }
 
 struct Ctl {
@@ -234,11 +262,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           }
           mbar_arrive_expect_tx(&full[stage], STAGE_BYTES);
           uint8_t* sp = stages + stage * STAGE_BYTES;
-          const int x = kt * 64;  // 128-byte aligned k offset of the box
-          tma_load_3d(sp, maps + s.amap, x, t.mt * BM, 0, &full[stage]);
-          tma_load_3d(sp + TILE_BYTES, maps + s.amap, x, t.mt * BM, 1, &full[stage]);
-          tma_load_3d(sp + 2 * TILE_BYTES, maps + s.bmap, x, t.nt * BN, 0, &full[stage]);
-          tma_load_3d(sp + 3 * TILE_BYTES, maps + s.bmap, x, t.nt * BN, 1, &full[stage]);
+          load_operand(sp, maps + s.amap, s.a_mn, t.mt * BM, kt, 0, &full[stage]);
+          load_operand(sp + TILE_BYTES, maps + s.amap, s.a_mn, t.mt * BM, kt, 1, &full[stage]);
+          load_operand(sp + 2 * TILE_BYTES, maps + s.bmap, s.b_mn, t.nt * BN, kt, 0, &full[stage]);
+          load_operand(sp + 3 * TILE_BYTES, maps + s.bmap, s.b_mn, t.nt * BN, kt, 1, &full[stage]);
           ++issued;
           if (++stage == STAGES) {
             stage = 0;
@@ -278,6 +305,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           tc_fence_after();
           const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
           const int k1 = min(s.ktiles, k0 + KCHUNK);
+          // transpose bits: A MN-major (bit 15), B MN-major (bit 16)
+          const uint32_t idesc = IDESC | ((uint32_t)(s.a_mn != 0) << 15) | ((uint32_t)(s.b_mn != 0) << 16);
           for (int kt = k0; kt < k1; ++kt) {
             if (!wait_bar(&full[stage], phase, ctl, err)) {
               ok = false;
@@ -287,13 +316,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const uint32_t base = smem_u32(stages + stage * STAGE_BYTES);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t ah = sw128_desc(base + kk * 32);
-              const uint64_t al = sw128_desc(base + TILE_BYTES + kk * 32);
-              const uint64_t bh = sw128_desc(base + 2 * TILE_BYTES + kk * 32);
-              const uint64_t bl = sw128_desc(base + 3 * TILE_BYTES + kk * 32);
-              mma_bf16(d_tmem, ah, bh, (kt != k0 || kk != 0) ? 1u : 0u);
-              mma_bf16(d_tmem, ah, bl, 1u);
-              mma_bf16(d_tmem, al, bh, 1u);
+              // k advances 16: 32 bytes along a K-major row, two 8-row groups MN-major
+              const uint64_t ah = s.a_mn ? sw128_mn_desc(base + kk * 2048) : sw128_desc(base + kk * 32);
+              const uint64_t al = s.a_mn ? sw128_mn_desc(base + TILE_BYTES + kk * 2048)
+                                         : sw128_desc(base + TILE_BYTES + kk * 32);
+              const uint64_t bh = s.b_mn ? sw128_mn_desc(base + 2 * TILE_BYTES + kk * 2048)
+                                         : sw128_desc(base + 2 * TILE_BYTES + kk * 32);
+              const uint64_t bl = s.b_mn ? sw128_mn_desc(base + 3 * TILE_BYTES + kk * 2048)
+                                         : sw128_desc(base + 3 * TILE_BYTES + kk * 32);
+              mma_bf16(d_tmem, ah, bh, idesc, (kt != k0 || kk != 0) ? 1u : 0u);
+              mma_bf16(d_tmem, ah, bl, idesc, 1u);
+              mma_bf16(d_tmem, al, bh, idesc, 1u);
             }
             mma_commit(&empty[stage]);
             if (++stage == STAGES) {
@@ -422,7 +455,8 @@ int encode_operand_map(TensorMap* out, const void* hi, const TcOperand& op, int6
   if (!fn) return (int)CUDA_ERROR_NOT_FOUND;
   const cuuint64_t dims[3] = {(cuuint64_t)op.cols, (cuuint64_t)op.rows, 2};
   const cuuint64_t strides[2] = {(cuuint64_t)op.ld * 2, (cuuint64_t)split_lo * 2};  // bytes, dims 1 and 2
-  const cuuint32_t box[3] = {64, (cuuint32_t)BM, 1};
+  // K-major: 64 k x 128 rows; MN-major: 64 of the M/N dim x 64 k (two per tile)
+  const cuuint32_t box[3] = {64, op.mn ? 64u : (cuuint32_t)BM, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   void* base = const_cast<uint16_t*>(static_cast<const uint16_t*>(hi) + op.off);
   return (int)fn(reinterpret_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,

@@ -94,14 +94,17 @@ struct GemmTile {
 
 // tcgen05 split-BF16 x3 grouped GEMM, C (m x n, row-major FP32, ldc) =
 // alpha A B.  The operands are row-major bf16 matrices with their hi and lo
-// planes split_lo elements apart: A as m x k, B as B^T (n x k).  Each is
-// described by a TensorMap (amap, bmap index the plan's map array): a 3-D
-// tiled tensor map (k, rows, plane) whose 64 x 128 x 1 boxes the TMA engine
-// writes to shared memory in the 128-byte-swizzled K-major layout of the
-// tensor-core descriptors, with zeros past the matrix edges.
+// planes split_lo elements apart, each described by a TensorMap (amap, bmap
+// index the plan's map array: 3-D tiled maps (inner, outer, plane) whose
+// boxes the TMA engine writes to shared memory in the 128-byte-swizzled
+// layouts of the tensor-core descriptors, with zeros past the edges).
+// a_mn = 0: A stored m x k (K-major, 64 x 128 boxes of (k, row));
+// a_mn = 1: A stored k x m (MN-major, 64 x 64 boxes of (m, k), two per tile).
+// b_mn = 0: B stored as B^T, n x k (K-major); b_mn = 1: B stored k x n.
 struct TcSector {
   int32_t m, n, k, ktiles;
   int32_t amap, bmap;
+  int32_t a_mn, b_mn;
   int64_t c_off;
   int32_t ldc;
   float alpha;
@@ -109,11 +112,13 @@ struct TcSector {
 struct alignas(64) TensorMap {  // opaque CUtensorMap (128 bytes)
   uint64_t w[16];
 };
-// Operand of a tensor-core GEMM: rows x cols bf16 at element `off` of the hi
-// plane (row stride ld, a multiple of 8; off a multiple of 8).
+// Operand of a tensor-core GEMM: a rows x cols bf16 matrix at element `off`
+// of the hi plane (row stride ld and off multiples of 64).  mn = 0: K-major
+// (rows = the M or N dim, cols = K); mn = 1: MN-major (rows = K, cols = the
+// M or N dim).  One buffer may carry one map of each kind.
 struct TcOperand {
   int64_t off;
-  int32_t rows, cols, ld;
+  int32_t rows, cols, ld, mn;
 };
 
 // CUDA-core GEMM tile shapes

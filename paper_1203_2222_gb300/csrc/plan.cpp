@@ -932,9 +932,12 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     // linear FP32/FP64 operands of the CUDA-core GEMMs (elements of `lin`):
     // forward A (m x k), B (k x n); dA B^T (n x k); dB A^T (k x m); dC (m x n)
     int64_t a = -1, b = -1, bt = -1, at = -1, dcl = -1;
-    // split-BF16 operands of the tcgen05 GEMMs (indices into P->tc_ops):
-    // forward A (m x k), B^T (n x k); dA dC (m x n), B (k x n); dB A^T (k x m), dC^T (n x m)
-    int oa = -1, ob = -1, odc1 = -1, obt = -1, oat = -1, odc2 = -1;
+    // split-BF16 buffers of the tcgen05 GEMMs (elements of the hi plane),
+    // stored A (m x k), B (k x n), dC (m x n) and read K-major or MN-major:
+    // forward A (K), B (MN); dA dC (K), B (K); dB A (MN), dC (MN).  The
+    // forward's A and B serve the backward unchanged.
+    int64_t ta = -1, tb = -1, tdc = -1;
+    int fa = -1, fb = -1, dAa = -1, dAb = -1, dBa = -1, dBb = -1;  // map indices (P->tc_ops)
     int64_t c, da, db;  // output matrices
     bool split[3];
   };
@@ -959,35 +962,44 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     gs.push_back(g);
   }
   int64_t ie = 0, le = 0, oe = 0;
-  // tcgen05 operand: rows x cols bf16 in the hi plane; rows start on 128-byte
-  // boundaries, so every 128-byte row of a TMA box is one cache line
-  auto add_op = [&](int64_t rows, int64_t cols) {
-    const int64_t ld = cdiv(cols, 64) * 64;
-    P->tc_ops.push_back(TcOperand{ie, (int)rows, (int)cols, (int)ld});
-    ie += rows * ld;
+  auto ld64 = [](int64_t cols) { return cdiv(cols, 64) * 64; };  // rows on 128-byte lines
+  // split-BF16 buffer of rows x cols bf16 in the hi plane
+  auto add_buf = [&](int64_t rows, int64_t cols) {
+    const int64_t off = ie;
+    ie += rows * ld64(cols);
+    return off;
+  };
+  // tensor map of a buffer (rows x cols stored): K-major or MN-major view
+  auto add_op = [&](int64_t off, int64_t rows, int64_t cols, int mn) {
+    P->tc_ops.push_back(TcOperand{off, (int)rows, (int)cols, (int)ld64(cols), mn});
     return (int)P->tc_ops.size() - 1;
   };
   for (auto& g : gs) {
-    if (g.kind[0] == 0) {
-      g.oa = add_op(g.m, g.k);
-      g.ob = add_op(g.n, g.k);
+    const bool t0 = g.kind[0] == 0, t1 = g.kind[1] == 0, t2 = g.kind[2] == 0;
+    if (t0 || t2) g.ta = add_buf(g.m, g.k);
+    if (t0 || t1) g.tb = add_buf(g.k, g.n);
+    if (t1 || t2) g.tdc = add_buf(g.m, g.n);
+    if (t0) {
+      g.fa = add_op(g.ta, g.m, g.k, 0);
+      g.fb = add_op(g.tb, g.k, g.n, 1);
     } else {
       g.a = le, le += g.m * g.k;
       g.b = le, le += g.k * g.n;
     }
-    if (g.kind[1] == 0) {
-      g.odc1 = add_op(g.m, g.n);
-      g.obt = add_op(g.k, g.n);
+    if (t1) {
+      g.dAa = add_op(g.tdc, g.m, g.n, 0);
+      g.dAb = add_op(g.tb, g.k, g.n, 0);
     } else {
       g.bt = le, le += g.n * g.k;
     }
-    if (g.kind[2] == 0) {
-      g.oat = add_op(g.k, g.m);
-      g.odc2 = add_op(g.n, g.m);
+    if (t2) {
+      g.dBa = add_op(g.ta, g.m, g.k, 1);
+      g.dBb = add_op(g.tdc, g.m, g.n, 1);
     } else {
       g.at = le, le += g.k * g.m;
     }
-    if (g.kind[1] != 0 || g.kind[2] != 0) g.dcl = le, le += g.m * g.n;
+    if (!t1 || !t2) g.dcl = le, le += g.m * g.n;
+    if (t0 && (t1 || t2)) P->bwd_reads_fwd_operands = true;
   }
   for (auto& g : gs) {
     g.c = oe, oe += g.m * g.n;
@@ -1009,7 +1021,9 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   auto add_gemm = [&](int kind, int ph, int64_t m, int64_t n, int64_t k, int64_t aoff, int64_t lda, int64_t boff,
                       int64_t ldb, int64_t coff) -> bool {
     if (kind == 0) {
-      P->secs_tc.push_back(TcSector{(int)m, (int)n, (int)k, (int)cdiv(k, 64), (int)aoff, (int)boff, coff, (int)n, 1.0f});
+      const int amn = P->tc_ops[aoff].mn, bmn = P->tc_ops[boff].mn;
+      P->secs_tc.push_back(
+          TcSector{(int)m, (int)n, (int)k, (int)cdiv(k, 64), (int)aoff, (int)boff, amn, bmn, coff, (int)n, 1.0f});
       const int sec = (int)P->secs_tc.size() - 1;
       for (int64_t mt = 0; mt < cdiv(m, 128); ++mt)
         for (int64_t nt = 0; nt < cdiv(n, 128); ++nt)
@@ -1047,9 +1061,9 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   };
   for (auto& g : gs) {
     const bool t0 = g.kind[0] == 0, t1 = g.kind[1] == 0, t2 = g.kind[2] == 0;
-    g.split[0] = add_gemm(g.kind[0], 0, g.m, g.n, g.k, t0 ? g.oa : g.a, g.k, t0 ? g.ob : g.b, g.n, g.c);
-    g.split[1] = add_gemm(g.kind[1], 1, g.m, g.k, g.n, t1 ? g.odc1 : g.dcl, g.n, t1 ? g.obt : g.bt, g.k, g.da);
-    g.split[2] = add_gemm(g.kind[2], 2, g.k, g.n, g.m, t2 ? g.oat : g.at, g.m, t2 ? g.odc2 : g.dcl, g.n, g.db);
+    g.split[0] = add_gemm(g.kind[0], 0, g.m, g.n, g.k, t0 ? g.fa : g.a, g.k, t0 ? g.fb : g.b, g.n, g.c);
+    g.split[1] = add_gemm(g.kind[1], 1, g.m, g.k, g.n, t1 ? g.dAa : g.dcl, g.n, t1 ? g.dAb : g.bt, g.k, g.da);
+    g.split[2] = add_gemm(g.kind[2], 2, g.k, g.n, g.m, t2 ? g.dBa : g.at, g.m, t2 ? g.dBb : g.dcl, g.n, g.db);
   }
   for (int kind = 0; kind < kGemmKinds; ++kind)
     for (int ph = 0; ph < 3; ++ph) {
@@ -1088,10 +1102,10 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   // operand block written into a linear matrix (row stride ld) at (row0, col0)
   auto put = [&](const Box& b, int src, int64_t off, int64_t row0, int64_t col0, int64_t ld,
                  const std::vector<Term>& t) { emit(*P, b, off + row0 * ld + col0, (int)ld, src, DST_OPS, t); };
-  // operand block written into tcgen05 operand `op` (split-BF16) at (row0, col0)
-  auto put_tc = [&](const Box& b, int src, int op, int64_t row0, int64_t col0, const std::vector<Term>& t) {
-    const TcOperand& o = P->tc_ops[op];
-    emit(*P, b, o.off + row0 * o.ld + col0, o.ld, src, DST_SPLIT, t);
+  // operand block written into a split-BF16 buffer (rows of `cols`) at (row0, col0)
+  auto put_tc = [&](const Box& b, int src, int64_t off, int64_t cols, int64_t row0, int64_t col0,
+                    const std::vector<Term>& t) {
+    emit(*P, b, off + row0 * ld64(cols) + col0, (int)ld64(cols), src, DST_SPLIT, t);
   };
   // zero-fill of an output matrix before a split-K GEMM adds into it
   auto zero_fill = [&](int64_t off, int64_t rows, int64_t cols) {
@@ -1153,8 +1167,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
         if (gi == gofx.end()) return false;
         const G& g = gs[gi->second];
         if (g.kind[0] == 0) {
-          const TcOperand& op = P->tc_ops[g.oa];
-          o = {op.off + MA.r0[s] * op.ld + MA.c0[s], op.ld};
+          o = {g.ta + MA.r0[s] * ld64(g.k) + MA.c0[s], ld64(g.k)};
           slot = DST_SPLIT;
         } else {
           o = {g.a + MA.r0[s] * g.k + MA.c0[s], g.k};
@@ -1170,7 +1183,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     const G& g = gs[gi->second];
     Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, false);
     if (g.kind[0] == 0)
-      put_tc(b, 0, g.oa, MA.r0[s], MA.c0[s], terms_of(XA[s], A));
+      put_tc(b, 0, g.ta, g.k, MA.r0[s], MA.c0[s], terms_of(XA[s], A));
     else
       put(b, 0, g.a, MA.r0[s], MA.c0[s], g.k, terms_of(XA[s], A));
   }
@@ -1178,13 +1191,11 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     auto gi = gofx.find(MB.xs[MB.sx[s]]);
     if (gi == gofx.end() || XB[s].empty()) continue;
     const G& g = gs[gi->second];
-    if (g.kind[0] == 0) {  // B^T (n x k): rows n (free), K = k (contracted)
-      Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, true);
-      put_tc(b, 1, g.ob, MB.c0[s], MB.r0[s], terms_of(XB[s], B));
-    } else {
-      Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, false);
+    Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, false);  // B (k x n)
+    if (g.kind[0] == 0)
+      put_tc(b, 1, g.tb, g.n, MB.r0[s], MB.c0[s], terms_of(XB[s], B));
+    else
       put(b, 1, g.b, MB.r0[s], MB.c0[s], g.n, terms_of(XB[s], B));
-    }
   }
   for (auto& g : gs)
     if (g.split[0]) zero_fill(g.c, g.m, g.n);
@@ -1216,7 +1227,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   }
   P->fwd_scatter = {begin, (int)P->items.size() - begin};
 
-  // ---- backward gathers: [dA only: B or B^T, dC split][shared: dC linear][dB only: A^T, dC^T split]
+  // ---- backward gathers: [dA only: B or B^T][shared: dC][dB only: A or A^T]
   std::vector<int> idC(C.rank);
   for (int i = 0; i < C.rank; ++i) idC[i] = i;
   auto dc_terms = [&](int64_t sn) {
@@ -1242,46 +1253,39 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     auto gi = gofx.find(MB.xs[MB.sx[s]]);
     if (gi == gofx.end() || XB[s].empty()) continue;
     const G& g = gs[gi->second];
-    if (g.kind[1] == 0) {  // B (k x n): rows k (contracted), K = n (free)
+    if (g.kind[1] == 0) {  // B (k x n) for the tensor cores, unless the forward wrote it
+      if (g.kind[0] == 0) continue;
       Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, false);
-      put_tc(b, 1, g.obt, MB.r0[s], MB.c0[s], terms_of(XB[s], B));
+      put_tc(b, 1, g.tb, g.n, MB.r0[s], MB.c0[s], terms_of(XB[s], B));
     } else {  // B^T (n x k)
       Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, true);
       put(b, 1, g.bt, MB.c0[s], MB.r0[s], g.k, terms_of(XB[s], B));
     }
   }
-  for_dc([&](const G& g, int64_t sn, int64_t r0, int64_t c0) {  // dC (m x n) for dA on the tensor cores
-    if (g.kind[1] != 0) return;
-    auto t = dc_terms(sn);
-    if (t.empty()) return;
-    put_tc(gather_box(Cn, idC, Cn, sn, sn, na, false), 2, g.odc1, r0, c0, t);
-  });
   for (auto& g : gs)
     if (g.split[1]) zero_fill(g.da, g.m, g.k);
   const int b1 = (int)P->items.size();
-  for_dc([&](const G& g, int64_t sn, int64_t r0, int64_t c0) {  // dC (m x n) for the CUDA-core GEMMs
-    if (g.dcl < 0) return;
+  for_dc([&](const G& g, int64_t sn, int64_t r0, int64_t c0) {  // dC (m x n), both gradients
     auto t = dc_terms(sn);
     if (t.empty()) return;
-    put(gather_box(Cn, idC, Cn, sn, sn, na, false), 2, g.dcl, r0, c0, g.n, t);
+    Box b = gather_box(Cn, idC, Cn, sn, sn, na, false);
+    if (g.tdc >= 0) put_tc(b, 2, g.tdc, g.n, r0, c0, t);
+    if (g.dcl >= 0) put(b, 2, g.dcl, r0, c0, g.n, t);
   });
   const int b2 = (int)P->items.size();
-  for (int64_t s = 0; s < Am.nsec(); ++s) {  // A^T (k x m)
+  for (int64_t s = 0; s < Am.nsec(); ++s) {
     auto gi = gofx.find(MA.xs[MA.sx[s]]);
     if (gi == gofx.end() || XA[s].empty()) continue;
     const G& g = gs[gi->second];
-    Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, true);
-    if (g.kind[2] == 0)
-      put_tc(b, 0, g.oat, MA.c0[s], MA.r0[s], terms_of(XA[s], A));
-    else
+    if (g.kind[2] == 0) {  // A (m x k) for the tensor cores, unless the forward wrote it
+      if (g.kind[0] == 0) continue;
+      Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, false);
+      put_tc(b, 0, g.ta, g.k, MA.r0[s], MA.c0[s], terms_of(XA[s], A));
+    } else {  // A^T (k x m)
+      Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, true);
       put(b, 0, g.at, MA.c0[s], MA.r0[s], g.m, terms_of(XA[s], A));
+    }
   }
-  for_dc([&](const G& g, int64_t sn, int64_t r0, int64_t c0) {  // dC^T (n x m) for dB on the tensor cores
-    if (g.kind[2] != 0) return;
-    auto t = dc_terms(sn);
-    if (t.empty()) return;
-    put_tc(gather_box(Cn, idC, Cn, sn, sn, na, true), 2, g.odc2, c0, r0, t);
-  });
   for (auto& g : gs)
     if (g.split[2]) zero_fill(g.db, g.k, g.n);
   const int b3 = (int)P->items.size();
@@ -1378,17 +1382,21 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     } else {
       const TcSector& s = P->secs_tc[t.sector];
       const int nops = (int)P->tc_ops.size();
-      if (s.amap < 0 || s.amap >= nops || s.bmap < 0 || s.bmap >= nops || s.ktiles != cdiv(s.k, 64) ||
-          P->tc_ops[s.amap].rows != s.m || P->tc_ops[s.amap].cols != s.k || P->tc_ops[s.bmap].rows != s.n ||
-          P->tc_ops[s.bmap].cols != s.k || t.mt * 128 >= s.m || t.nt * 128 >= s.n ||
-          s.c_off + (int64_t)(s.m - 1) * s.ldc + s.n - 1 >= P->outm_elems || s.ktiles < 1)
+      auto fits = [&](int op, int mn, int64_t mnd, int64_t kd) {  // operand of the M (or N) dim mnd
+        if (op < 0 || op >= nops) return false;
+        const TcOperand& o = P->tc_ops[op];
+        return o.mn == mn && (mn ? (o.cols == mnd && o.rows == kd) : (o.rows == mnd && o.cols == kd));
+      };
+      if (!fits(s.amap, s.a_mn, s.m, s.k) || !fits(s.bmap, s.b_mn, s.n, s.k) || s.ktiles != cdiv(s.k, 64) ||
+          t.mt * 128 >= s.m || t.nt * 128 >= s.n || s.c_off + (int64_t)(s.m - 1) * s.ldc + s.n - 1 >= P->outm_elems ||
+          s.ktiles < 1)
         fail(SYM_ERR_ARG, "internal: tcgen05 GEMM tile past its buffers");
     }
   }
   // tcgen05 operands: 16-byte aligned rows inside the hi plane (TMA rules)
   for (const TcOperand& o : P->tc_ops)
-    if (f64 || o.off < 0 || o.off % 8 || o.ld % 8 || o.ld < o.cols || o.rows < 1 || o.cols < 1 ||
-        o.off + (int64_t)o.rows * o.ld > P->img_elems)
+    if (f64 || o.off < 0 || o.off % 64 || o.ld % 64 || o.ld < o.cols || o.rows < 1 || o.cols < 1 ||
+        (o.mn != 0 && o.mn != 1) || o.off + (int64_t)o.rows * o.ld > P->img_elems)
       fail(SYM_ERR_ARG, "internal: tensor-core operand past its buffer");
   P->upload(device);
   return P;
@@ -1554,6 +1562,8 @@ int exec_contract(Plan& p, const void* A, const void* B, void* C, void* stream) 
   if (rc) return rc;
   rc = run_gemm(p, 0, 0, stream, PH_FWD_GEMM);
   if (rc) return rc;
+  p.fwd_a = A;
+  p.fwd_b = B;
   BoxPtrs s{};
   s.src[3] = p.outm;
   s.dst[DST_OUT] = C;
@@ -1566,6 +1576,12 @@ int exec_contract_backward(Plan& p, const void* A, const void* B, const void* dC
   p.last_launches = 0;
   if (!dA && !dB) return SYM_OK;
   BoxPtrs g = gather_ptrs(p, A, B, dC);
+  if (p.bwd_reads_fwd_operands && (p.fwd_a != A || p.fwd_b != B)) {
+    // the operand buffers hold another forward's inputs: gather A and B again
+    if (int rc = run_box(p, p.fwd_gather, g, stream, PH_BWD_GATHER)) return rc;
+    p.fwd_a = A;
+    p.fwd_b = B;
+  }
   Range gr;
   if (dA && dB) {
     int first = std::min(p.bwd_gather_a.first, p.bwd_gather_b.first);

@@ -104,6 +104,12 @@ struct Plan {
   // are captured into a CUDA graph as dependencies).  Off for plans that
   // must create nothing (sym_contract_noalloc).
   bool concurrent = true;
+  // The backward reads the tensor-core operands the forward gathered when
+  // bwd_reads_fwd_operands; they are reused if the plan's last forward ran
+  // on the same A and B buffers, and gathered again otherwise.
+  bool bwd_reads_fwd_operands = false;
+  const void* fwd_a = nullptr;
+  const void* fwd_b = nullptr;
   void* side[kGemmKinds - 1] = {};     // cudaStream_t
   void* ev_fork = nullptr;             // cudaEvent_t
   void* ev_join[kGemmKinds - 1] = {};  // cudaEvent_t

@@ -224,3 +224,32 @@ def test_fuse_then_split_roundtrip(dtype):
         torch.cuda.synchronize()
         err = rel(back.data.double().cpu().numpy(), T.data.double().cpu().numpy())
         assert err <= (1e-13 if dtype == torch.float64 else 1e-6), (group, err)
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
+def test_backward_after_another_forward_on_the_same_plan(dtype):
+    # The backward reads the tensor-core operand forms its forward gathered
+    # unless the plan has run a forward on other inputs since; then it
+    # gathers them again.  Interleave two forwards and check both gradients.
+    P = _lib()
+    qs = [-1, 0, 1]
+    la = [(qs, [70, 150, 33], -1), (qs, [5, 9, 2], 1), (qs, [90, 140, 61], 1)]
+    lb = [(qs, [90, 140, 61], -1), (qs, [100, 131, 7], 1)]
+    runs = []
+    for seed in (0, 10):
+        SA, A, a = _make("u1", la, seed, dtype)
+        SB, B, b = _make("u1", lb, seed + 1, dtype)
+        A.data.requires_grad_(True)
+        B.data.requires_grad_(True)
+        runs.append((A, B, a, b, P.contract(A, B, [2], [0])))
+    for i, (A, B, a, b, C) in enumerate(runs):
+        g = np.random.default_rng(20 + i).standard_normal(C.structure.numel)
+        gt = torch.as_tensor(g).to(dtype).cuda()
+        C.data.backward(gt)
+        torch.cuda.synchronize()
+        oA = ([_oleg("u1", l) for l in la], 0, a)
+        oB = ([_oleg("u1", l) for l in lb], 0, b)
+        dA_ref, dB_ref, _ = oc.contract_grad("u1", oA, oB, [2], [0], gt.double().cpu().numpy())
+        assert rel(A.data.grad.double().cpu().numpy(), dA_ref) <= TOL[dtype]
+        assert rel(B.data.grad.double().cpu().numpy(), dB_ref) <= TOL[dtype]
+    P.device_status()
