@@ -40,8 +40,10 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--workload", choices=["u1_mps_heff", "su2_recouple"], default="u1_mps_heff",
-                    help="u1_mps_heff (default, the metric's configuration) or the large-sector su2_recouple")
+    ap.add_argument("--workload", choices=["u1_mps_heff", "su2_recouple", "u1_two_site_batch"],
+                    default="u1_mps_heff",
+                    help="u1_mps_heff (default, the metric's configuration), the large-sector su2_recouple, "
+                         "or the 512-problem u1_two_site_batch")
     ap.add_argument("--steps", type=int, default=None, help="timed steps (default 100; su2_recouple 5)")
     ap.add_argument("--warmup", type=int, default=None, help="warm-up steps (default 5; su2_recouple 3)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -279,7 +281,55 @@ class SU2Workload:
         return C.data, grads
 
 
-WORKLOADS = {"u1_mps_heff": MPSWorkload, "su2_recouple": SU2Workload}
+BATCH_STREAMS = {"L": 1, "theta": 2, "W": 3, "R": 4}  # random sub-stream of each tensor role
+
+
+class BatchWorkload:
+    """512 independent two-site effective-Hamiltonian applies, fwd + bwd, as
+    one batch plan per contraction of the chain (one launch per kernel and
+    phase for all problems)."""
+    name = "u1_two_site_batch"
+    describe = ("u1_two_site_batch: 512 independent U(1) two-site H_eff applies (((L.theta).W1).W2).R fwd+bwd, "
+                "D_i log-uniform in 64..1024 over q=-12..12 (Gaussian profile, sigma_i U(2,6)), seeded per problem; "
+                "one batch plan per contraction")
+    default_steps, default_warmup, default_fp64_steps = 50, 5, 3
+    names = ("L", "theta", "W", "R")
+
+    def build(self, P, dev):
+        import torch
+        from paper_1203_2222_gb300 import synthetic
+        self.spec = synthetic.u1_two_site_batch()
+        pr = self.spec["problems"]
+        self.S = {n: [P.Structure(P.U1, p[n]) for p in pr] for n in self.names}
+        plans = self.plans(P, P.BF16X3)
+        self.offs = {"L": plans[0].off_a, "theta": plans[0].off_b, "W": plans[1].off_b, "R": plans[3].off_b}
+        self.data = {}
+        for n in self.names:
+            parts = [synthetic.normal(p["seed"], self.offs[n][i + 1] - self.offs[n][i], stream=BATCH_STREAMS[n])
+                     for i, p in enumerate(pr)]
+            self.data[n] = torch.as_tensor(np.concatenate(parts)).to(torch.float32).to(dev).requires_grad_(True)
+        self.G = torch.as_tensor(synthetic.normal(4243, plans[3].off_c[-1])).to(torch.float32).to(dev)
+
+    def plans(self, P, prec):
+        out, cur = [], self.S["L"]
+        for an, bn, pa, pb in self.spec["steps"]:
+            bp = P.contract_batch_plan(cur if an is None else self.S[an], self.S[bn], pa, pb, prec)
+            out.append(bp)
+            cur = bp.outs
+        return out
+
+    def step(self, P, data, G):
+        import torch
+        pl = self.plans(P, P.FP64 if data["L"].dtype == torch.float64 else P.BF16X3)
+        t1 = P.contract_batch(pl[0], data["L"], data["theta"])
+        t2 = P.contract_batch(pl[1], t1, data["W"])
+        t3 = P.contract_batch(pl[2], t2, data["W"])
+        y = P.contract_batch(pl[3], t3, data["R"])
+        grads = torch.autograd.grad(y, [data[n] for n in self.names], grad_outputs=G)
+        return y, grads
+
+
+WORKLOADS = {"u1_mps_heff": MPSWorkload, "su2_recouple": SU2Workload, "u1_two_site_batch": BatchWorkload}
 
 
 # ---------------------------------------------------------------- roofline ---
@@ -694,7 +744,68 @@ def su2_flops_per_entry():
 SU2_SAMPLE = 4  # dense elements per oracle step (about 2-3 s of host work)
 
 
+class OracleBatch:
+    """The FP64 CPU oracle on the batch workload: the whole chain of one
+    problem, forward and the gradients of <G, Y> (dense embedding, brute
+    force), with the problem's own seeded inputs."""
+
+    def __init__(self):
+        from paper_1203_2222_gb300 import synthetic
+        self.spec = synthetic.u1_two_site_batch()
+        self.order = sorted(range(len(self.spec["problems"])), key=lambda i: self.spec["problems"][i]["D"])
+
+    def problem_flops(self, i):
+        """Useful flops of problem i's fwd + bwd (host planning only)."""
+        os.environ["SYM_PLAN_DRYRUN"] = "1"
+        try:
+            import paper_1203_2222_gb300 as P
+            p = self.spec["problems"][i]
+            S = {n: P.Structure(P.U1, p[n]) for n in ("L", "theta", "W", "R")}
+            tot, cur = 0.0, S["L"]
+            for an, bn, pa, pb in self.spec["steps"]:
+                pl = P.contract_plan(cur if an is None else S[an], S[bn], pa, pb, P.BF16X3)
+                tot += 3.0 * pl.stats()["flops_fwd"]
+                cur = pl.out
+            return tot
+        finally:
+            del os.environ["SYM_PLAN_DRYRUN"]
+
+    def step(self, i):
+        from oracle import contract as oc
+        from oracle import u1
+        from paper_1203_2222_gb300 import synthetic
+        p = self.spec["problems"][i]
+        legs = {n: [u1.Leg(*l) for l in p[n]] for n in ("L", "theta", "W", "R")}
+        data = {n: synthetic.normal(p["seed"], u1.layout(legs[n], 0)[2], stream=BATCH_STREAMS[n]) for n in legs}
+        ins, cur = [], (legs["L"], 0, data["L"])
+        for an, bn, pa, pb in self.spec["steps"]:
+            a = cur if an is None else (legs[an], 0, data[an])
+            b = (legs[bn], 0, data[bn])
+            lc, qc, c, _ = oc.contract("u1", a, b, pa, pb)
+            ins.append((a, b, pa, pb))
+            cur = (lc, qc, c)
+        dc = np.random.default_rng(i).standard_normal(cur[2].size)
+        for a, b, pa, pb in reversed(ins):
+            dc, _, _ = oc.contract_grad("u1", a, b, pa, pb, dc)
+
+
+BATCH_SAMPLE = 4  # problems per oracle step (the smallest ones, about a second of host work)
+BATCH_BASELINE = 24  # problems of the cpu_baseline sample (about 10 s of host work)
+
+
 def cpu_baseline(args, flops, steps):
+    if args.workload == "u1_two_site_batch":
+        o = OracleBatch()
+        probs = o.order[:BATCH_BASELINE * max(steps, 1)]
+        fl = sum(o.problem_flops(i) for i in probs)
+        t0 = time.perf_counter()
+        for i in probs:
+            o.step(i)
+        dt = time.perf_counter() - t0
+        return {"value": round(fl / dt / 1e12, 9), "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+                "sample": f"the {len(probs)} smallest problems of the batch (D = "
+                          f"{', '.join(str(o.spec['problems'][i]['D']) for i in probs)}), whole chain fwd + grad, "
+                          f"dense FP64 numpy oracle, credited their own useful flops; {dt:.1f} s"}
     if args.workload == "su2_recouple":
         o = OracleSU2()
         per = flops / 3.0 / su2_flops_per_entry_cached()
@@ -725,6 +836,35 @@ def su2_flops_per_entry_cached():
     if not _PER_ENTRY:
         _PER_ENTRY.append(su2_flops_per_entry())
     return _PER_ENTRY[0]
+
+
+def run_reference_batch(args):
+    """Oracle reference arm for u1_two_site_batch: each step is BATCH_SAMPLE problems (smallest first, rotating)."""
+    o = OracleBatch()
+    pool = o.order[:16]
+    fl_of = {i: o.problem_flops(i) for i in pool}
+    for w in range(args.warmup):
+        o.step(pool[w % len(pool)])
+    t0 = time.perf_counter()
+    fl = 0.0
+    for s_ in range(args.steps):
+        for q in range(BATCH_SAMPLE):
+            i = pool[(s_ * BATCH_SAMPLE + q) % len(pool)]
+            o.step(i)
+            fl += fl_of[i]
+    dt = time.perf_counter() - t0
+    value = fl / dt / 1e12
+    sample = (f"step = {BATCH_SAMPLE} of the 16 smallest problems of the batch, rotating, whole chain fwd + grad, "
+              f"dense FP64 numpy oracle, credited their own useful flops")
+    return {
+        "metric": METRIC, "value": round(value, 9), "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": BatchWorkload.describe, "sample": sample},
+        "cpu_baseline": {"value": round(value, 9), "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 9), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
 
 
 def run_reference_su2(args):
@@ -798,8 +938,12 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        out = run_reference_su2(args) if args.workload == "su2_recouple" else \
-            run_reference(args, contraction_flops_host())
+        if args.workload == "su2_recouple":
+            out = run_reference_su2(args)
+        elif args.workload == "u1_two_site_batch":
+            out = run_reference_batch(args)
+        else:
+            out = run_reference(args, contraction_flops_host())
         print(json.dumps(out))
         return 0
     import torch

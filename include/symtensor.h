@@ -150,6 +150,11 @@ int sym_plan_execute(sym_plan plan, const void* in, void* out, void* stream);
  * sym_contract_backward: dA, dB = gradient of <dC, C> with respect to A's
  *   and B's blocks (adjoint on the same sector tables); dA or dB may be NULL
  *   to skip it.  Buffers are overwritten, not accumulated.
+ *   sym_contract_backward reads the tensor-core operand forms of A and B
+ *   that the plan's last sym_contract gathered when that call received the
+ *   same A and B pointers (A and B must then not have been modified in
+ *   between, as for any saved autograd input); otherwise it gathers them
+ *   again from A and B.
  *   Both are asynchronous on `stream`.  The GEMM launches of one call run
  *   concurrently on side streams that the plan creates on first use, forked
  *   from `stream` and joined back into it with events (in a stream capture
@@ -165,6 +170,24 @@ int sym_contract(sym_plan plan, const void* A, const void* B, void* C,
                  void* stream);
 int sym_contract_backward(sym_plan plan, const void* A, const void* B,
                           const void* dC, void* dA, void* dB, void* stream);
+/* sym_contract_batch_plan: nprob independent contractions of the same kind
+ *   (the contraction of Ch. 5, "Multiplication of two tensors", for every
+ *   pair A[i], B[i] over the same leg pairs) as ONE plan: their blocks live in
+ *   packed buffers, problem i's A at element offsets[i] of the packed A, its
+ *   B at offsets[nprob + 1 + i] of the packed B and its C at
+ *   offsets[2 (nprob + 1) + i] of the packed C (offsets: 3 (nprob + 1)
+ *   int64, written; each list ends with the packed size).  C[i] (nprob
+ *   handles, written, owned by the caller) are the result structures, as
+ *   sym_contract_plan makes them.  sym_contract / sym_contract_backward on
+ *   the packed buffers then run every phase of all problems in one launch per
+ *   kernel (GEMM tiles of all problems scheduled longest reduction first).
+ *   The thesis runs its contractions one at a time; grouping is this
+ *   library's.  Problems are planned in parallel on the host.  Errors as
+ *   sym_contract_plan (the first failing problem's).                     */
+int sym_contract_batch_plan(int nprob, const sym_tensor* A, const sym_tensor* B,
+                            int npairs, const int* pairsA, const int* pairsB,
+                            int precision, sym_tensor* C, int64_t* offsets,
+                            sym_plan* plan);
 int sym_plan_stats(sym_plan plan, double* flops_fwd, int64_t* bytes_a,
                    int64_t* bytes_b, int64_t* bytes_c);
 int sym_plan_destroy(sym_plan plan);

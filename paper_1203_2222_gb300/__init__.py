@@ -6,7 +6,7 @@ per-sector GEMM on tcgen05 tensor cores, the scatter back, and the adjoint.
 The compute lives in ``_build/libsymtensor.so`` (C ABI: include/symtensor.h);
 this package is its Python front end.
 """
-from .symtensor import (BF16X3, FP64, SU2, U1, Plan, Structure, SymError, SymTensor, contract,  # noqa: F401
-                        contract_plan, device_status, fuse, fuse_plan, permute, permute_plan, split,
-                        split_plan, su2_F, su2_gamma, PHASES, KERNELS, KERNEL_SYMBOLS,
-                        cached_plans)
+from .symtensor import (BF16X3, FP64, KERNEL_SYMBOLS, KERNELS, PHASES, SU2, U1, BatchPlan,  # noqa: F401
+                        Plan, Structure, SymError, SymTensor, cached_plans, contract, contract_batch,
+                        contract_batch_plan, contract_plan, device_status, fuse, fuse_plan, permute,
+                        permute_plan, split, split_plan, su2_F, su2_gamma)

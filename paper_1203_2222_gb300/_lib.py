@@ -67,6 +67,8 @@ _SIGS = {
     "sym_split_plan": ([_P, _I, ctypes.POINTER(sym_leg), _I, ctypes.POINTER(_P), ctypes.POINTER(_P)], _I),
     "sym_plan_execute": ([_P, _P, _P, _P], _I),
     "sym_contract_plan": ([_P, _P, _I, _IP, _IP, _IP, _I, ctypes.POINTER(_P), ctypes.POINTER(_P)], _I),
+    "sym_contract_batch_plan": ([_I, ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _IP, _IP, _I,
+                                 ctypes.POINTER(_P), _LP, ctypes.POINTER(_P)], _I),
     "sym_contract": ([_P, _P, _P, _P, _P], _I),
     "sym_contract_backward": ([_P, _P, _P, _P, _P, _P, _P], _I),
     "sym_plan_stats": ([_P, _DP, _LP, _LP, _LP], _I),

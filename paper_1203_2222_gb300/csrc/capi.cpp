@@ -5,9 +5,13 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
+#include <exception>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 
 #include "../../include/symtensor.h"
 #include "handles.h"
@@ -249,6 +253,55 @@ int sym_contract_plan(sym_tensor A, sym_tensor B, int npairs, const int* pairsA,
     auto P = sym::plan_contract(A->t, B->t, pa, pb, Ct, precision);
     *C = wrap(std::move(Ct));
     *plan = new sym_plan_s{std::move(P)};
+    return SYM_OK;
+  });
+}
+
+int sym_contract_batch_plan(int nprob, const sym_tensor* A, const sym_tensor* B, int npairs, const int* pairsA,
+                            const int* pairsB, int precision, sym_tensor* C, int64_t* offsets, sym_plan* plan) {
+  return guard([&] {
+    need(nprob >= 1 && A && B && C && offsets && plan, "NULL argument");
+    check_precision(precision);
+    need(npairs >= 0 && (npairs == 0 || (pairsA && pairsB)), "pairs are NULL");
+    for (int i = 0; i < nprob; ++i) need(A[i] && B[i], "NULL tensor in the batch");
+    const std::vector<int> pa(pairsA, pairsA + npairs), pb(pairsB, pairsB + npairs);
+    std::vector<sym::Tensor> Ct(nprob);
+    std::vector<std::unique_ptr<sym::Plan>> ps(nprob);
+    // the problems are planned independently, on up to 16 host threads
+    std::atomic<int> next{0};
+    std::exception_ptr err;
+    std::mutex emu;
+    auto work = [&] {
+      for (int i = next++; i < nprob; i = next++) {
+        try {
+          Ct[i] = sym::contraction_result(A[i]->t, B[i]->t, pa, pb, nullptr);
+          ps[i] = sym::plan_contract(A[i]->t, B[i]->t, pa, pb, Ct[i], precision, /*device=*/false);
+        } catch (...) {
+          std::lock_guard<std::mutex> lk(emu);
+          if (!err) err = std::current_exception();
+        }
+      }
+    };
+    const int nth = std::max(1, std::min({nprob, 16, (int)std::thread::hardware_concurrency()}));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nth; ++t) pool.emplace_back(work);
+    work();
+    for (auto& t : pool) t.join();
+    if (err) std::rethrow_exception(err);
+    std::vector<int64_t> oa(nprob + 1, 0), ob(nprob + 1, 0), oc(nprob + 1, 0);
+    for (int i = 0; i < nprob; ++i) {
+      oa[i + 1] = oa[i] + A[i]->t.numel();
+      ob[i + 1] = ob[i] + B[i]->t.numel();
+      oc[i + 1] = oc[i] + Ct[i].numel();
+    }
+    auto M = sym::merge_contract_plans(ps, oa, ob, oc);
+    for (int i = 0; i <= nprob; ++i) {
+      offsets[i] = oa[i];
+      offsets[nprob + 1 + i] = ob[i];
+      offsets[2 * (nprob + 1) + i] = oc[i];
+    }
+    for (int i = 0; i < nprob; ++i) C[i] = wrap(std::move(Ct[i]));
+    *plan = new sym_plan_s{std::move(M)};
     return SYM_OK;
   });
 }

@@ -854,6 +854,40 @@ int choose_kind(bool f64, int64_t m, int64_t n, int64_t k) {
 
 }  // namespace
 
+// GEMM tiles and tensor-core operands stay inside their buffers (host check)
+void validate_gemms(const Plan& P, bool f64) {
+  for (size_t i = 0; i < P.tiles.size(); ++i) {
+    const GemmTile& t = P.tiles[i];
+    if (P.tile_kind[i] != 0) {
+      if (t.sector < 0 || t.sector >= (int)P.secs_simt.size()) fail(SYM_ERR_ARG, "internal: bad GEMM sector index");
+      const GemmSectorSimt& s = P.secs_simt[t.sector];
+      if (t.k0 < 0 || t.k1 > s.k || t.k0 >= t.k1 || s.a_off < 0 || s.b_off < 0 || s.c_off < 0 ||
+          s.a_off + (int64_t)(s.m - 1) * s.lda + s.k - 1 >= P.lin_elems ||
+          s.b_off + (int64_t)(s.k - 1) * s.ldb + s.n - 1 >= P.lin_elems ||
+          s.c_off + (int64_t)(s.m - 1) * s.ldc + s.n - 1 >= P.outm_elems)
+        fail(SYM_ERR_ARG, "internal: CUDA-core GEMM sector past its buffers");
+    } else {
+      if (t.sector < 0 || t.sector >= (int)P.secs_tc.size()) fail(SYM_ERR_ARG, "internal: bad GEMM sector index");
+      const TcSector& s = P.secs_tc[t.sector];
+      const int nops = (int)P.tc_ops.size();
+      auto fits = [&](int op, int mn, int64_t mnd, int64_t kd) {  // operand of the M (or N) dim mnd
+        if (op < 0 || op >= nops) return false;
+        const TcOperand& o = P.tc_ops[op];
+        return o.mn == mn && (mn ? (o.cols == mnd && o.rows == kd) : (o.rows == mnd && o.cols == kd));
+      };
+      if (!fits(s.amap, s.a_mn, s.m, s.k) || !fits(s.bmap, s.b_mn, s.n, s.k) || s.ktiles != cdiv(s.k, 64) ||
+          t.mt * 128 >= s.m || t.nt * 128 >= s.n || s.c_off < 0 ||
+          s.c_off + (int64_t)(s.m - 1) * s.ldc + s.n - 1 >= P.outm_elems || s.ktiles < 1)
+        fail(SYM_ERR_ARG, "internal: tcgen05 GEMM tile past its buffers");
+    }
+  }
+  // tcgen05 operands: rows on 128-byte lines inside the hi plane (TMA rules)
+  for (const TcOperand& o : P.tc_ops)
+    if (f64 || o.off < 0 || o.off % 64 || o.ld % 64 || o.ld < o.cols || o.rows < 1 || o.cols < 1 ||
+        (o.mn != 0 && o.mn != 1) || o.off + (int64_t)o.rows * o.ld > P.img_elems)
+      fail(SYM_ERR_ARG, "internal: tensor-core operand past its buffer");
+}
+
 std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std::vector<int>& pairsA,
                                     const std::vector<int>& pairsB, const Tensor& C, int precision, bool device) {
   auto P = std::make_unique<Plan>();
@@ -1369,37 +1403,154 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     const int64_t dst[DST_COUNT] = {C.numel(), A.numel(), B.numel(), P->lin_elems, P->outm_elems, P->img_elems};
     P->validate(src, dst);
   }
-  // GEMM tiles stay inside their operand buffers
-  for (size_t i = 0; i < P->tiles.size(); ++i) {
-    const GemmTile& t = P->tiles[i];
-    if (P->tile_kind[i] != 0) {
-      const GemmSectorSimt& s = P->secs_simt[t.sector];
-      if (t.k0 < 0 || t.k1 > s.k || t.k0 >= t.k1 ||
-          s.a_off + (int64_t)(s.m - 1) * s.lda + s.k - 1 >= P->lin_elems ||
-          s.b_off + (int64_t)(s.k - 1) * s.ldb + s.n - 1 >= P->lin_elems ||
-          s.c_off + (int64_t)(s.m - 1) * s.ldc + s.n - 1 >= P->outm_elems)
-        fail(SYM_ERR_ARG, "internal: CUDA-core GEMM sector past its buffers");
-    } else {
-      const TcSector& s = P->secs_tc[t.sector];
-      const int nops = (int)P->tc_ops.size();
-      auto fits = [&](int op, int mn, int64_t mnd, int64_t kd) {  // operand of the M (or N) dim mnd
-        if (op < 0 || op >= nops) return false;
-        const TcOperand& o = P->tc_ops[op];
-        return o.mn == mn && (mn ? (o.cols == mnd && o.rows == kd) : (o.rows == mnd && o.cols == kd));
-      };
-      if (!fits(s.amap, s.a_mn, s.m, s.k) || !fits(s.bmap, s.b_mn, s.n, s.k) || s.ktiles != cdiv(s.k, 64) ||
-          t.mt * 128 >= s.m || t.nt * 128 >= s.n || s.c_off + (int64_t)(s.m - 1) * s.ldc + s.n - 1 >= P->outm_elems ||
-          s.ktiles < 1)
-        fail(SYM_ERR_ARG, "internal: tcgen05 GEMM tile past its buffers");
-    }
-  }
-  // tcgen05 operands: 16-byte aligned rows inside the hi plane (TMA rules)
-  for (const TcOperand& o : P->tc_ops)
-    if (f64 || o.off < 0 || o.off % 64 || o.ld % 64 || o.ld < o.cols || o.rows < 1 || o.cols < 1 ||
-        (o.mn != 0 && o.mn != 1) || o.off + (int64_t)o.rows * o.ld > P->img_elems)
-      fail(SYM_ERR_ARG, "internal: tensor-core operand past its buffer");
+  validate_gemms(*P, f64);
   P->upload(device);
   return P;
+}
+
+// One plan running many independent contractions: the host plans (device =
+// false) of problems i = 0..n-1 merged with their offsets shifted into packed
+// buffers (problem i's A at offA[i] of the packed A, likewise B and C) and into
+// shared scratch.  Every phase stays one launch per kernel over all problems:
+// items are concatenated phase by phase (the backward gathers keep their
+// dA-only / shared dC / dB-only order) and the GEMM tiles of each kind and
+// phase are concatenated and re-sorted by reduction length (longest first).
+std::unique_ptr<Plan> merge_contract_plans(std::vector<std::unique_ptr<Plan>>& ps, const std::vector<int64_t>& offA,
+                                           const std::vector<int64_t>& offB, const std::vector<int64_t>& offC,
+                                           bool device) {
+  const int n = (int)ps.size();
+  if (n < 1) fail(SYM_ERR_ARG, "empty batch");
+  auto M = std::make_unique<Plan>();
+  M->kind = Plan::CONTRACT;
+  M->precision = ps[0]->precision;
+  const bool f64 = M->precision == SYM_PREC_FP64;
+  std::vector<int64_t> lin0(n), outm0(n), img0(n);
+  std::vector<int> ops0(n), simt0(n), tc0(n);
+  for (int i = 0; i < n; ++i) {
+    const Plan& p = *ps[i];
+    if (p.kind != Plan::CONTRACT || p.precision != M->precision) fail(SYM_ERR_ARG, "batch plans must match");
+    lin0[i] = M->lin_elems;
+    M->lin_elems += p.lin_elems;
+    outm0[i] = M->outm_elems;
+    M->outm_elems += p.outm_elems;
+    img0[i] = M->img_elems;
+    M->img_elems += cdiv(p.img_elems, 64) * 64;
+    ops0[i] = (int)M->tc_ops.size();
+    for (TcOperand o : p.tc_ops) {
+      o.off += img0[i];
+      M->tc_ops.push_back(o);
+    }
+    simt0[i] = (int)M->secs_simt.size();
+    for (GemmSectorSimt g : p.secs_simt) {
+      g.a_off += lin0[i];
+      g.b_off += lin0[i];
+      g.c_off += outm0[i];
+      M->secs_simt.push_back(g);
+    }
+    tc0[i] = (int)M->secs_tc.size();
+    for (TcSector g : p.secs_tc) {
+      g.amap += ops0[i];
+      g.bmap += ops0[i];
+      g.c_off += outm0[i];
+      M->secs_tc.push_back(g);
+    }
+    M->flops_fwd += p.flops_fwd;
+    M->numel_a = offA[i] + p.numel_a;
+    M->numel_b = offB[i] + p.numel_b;
+    M->numel_c = offC[i] + p.numel_c;
+    M->bwd_reads_fwd_operands |= p.bwd_reads_fwd_operands;
+  }
+  // items, with their term blocks copied once per problem
+  std::vector<std::vector<int>> remap(n);
+  for (int i = 0; i < n; ++i) remap[i].assign(ps[i]->terms.size(), -1);
+  auto copy_range = [&](int i, int first, int count) {
+    const Plan& p = *ps[i];
+    const int64_t src_shift[4] = {offA[i], offB[i], offC[i], outm0[i]};
+    const int64_t dst_shift[DST_COUNT] = {offC[i], offA[i], offB[i], lin0[i], outm0[i], img0[i]};
+    for (int k = first; k < first + count; ++k) {
+      BoxItem it = p.items[k];
+      const int ss = it.sel & 3, ds = (it.sel >> 4) & 7;
+      const bool rec = (it.sel & kSelRecouple) != 0;
+      const int nt = rec ? it.nterm + it.p0 + it.nterm * it.p0 : it.nterm;
+      if (nt > 0) {
+        if (remap[i][it.term0] < 0) {
+          remap[i][it.term0] = (int)M->terms.size();
+          for (int q = 0; q < nt; ++q) {
+            Term t = p.terms[it.term0 + q];
+            if (!rec || q < it.nterm)
+              t.off += src_shift[ss];
+            else if (q < it.nterm + it.p0)
+              t.off += dst_shift[ds];
+            M->terms.push_back(t);
+          }
+        }
+        it.term0 = remap[i][it.term0];
+      } else {
+        it.term0 = (int)M->terms.size();
+      }
+      if (!rec) {
+        if (it.nterm > 0) it.t0_off += src_shift[ss];
+        it.dst_off += dst_shift[ds];
+      }
+      M->items.push_back(it);
+    }
+  };
+  auto concat = [&](const std::function<Range(const Plan&)>& sub) {
+    const int first = (int)M->items.size();
+    for (int i = 0; i < n; ++i) {
+      const Range r = sub(*ps[i]);
+      copy_range(i, r.first, r.count);
+    }
+    return Range{first, (int)M->items.size() - first};
+  };
+  M->fwd_gather = concat([](const Plan& p) { return p.fwd_gather; });
+  M->fwd_scatter = concat([](const Plan& p) { return p.fwd_scatter; });
+  // backward gathers: [a-only) [shared) [b-only)
+  auto a_only = [](const Plan& p) { return Range{p.bwd_gather_a.first, p.bwd_gather_b.first - p.bwd_gather_a.first}; };
+  auto shared = [](const Plan& p) {
+    return Range{p.bwd_gather_b.first, p.bwd_gather_a.first + p.bwd_gather_a.count - p.bwd_gather_b.first};
+  };
+  auto b_only = [](const Plan& p) {
+    const int e = p.bwd_gather_a.first + p.bwd_gather_a.count;
+    return Range{e, p.bwd_gather_b.first + p.bwd_gather_b.count - e};
+  };
+  for (auto& pp : ps)
+    if (a_only(*pp).count < 0 || shared(*pp).count < 0 || b_only(*pp).count < 0)
+      fail(SYM_ERR_ARG, "internal: backward gather ranges out of order");
+  const Range ra = concat(a_only), rs = concat(shared), rb = concat(b_only);
+  M->bwd_gather_a = {ra.first, ra.count + rs.count};
+  M->bwd_gather_b = {rs.first, rs.count + rb.count};
+  M->bwd_scatter_a = concat([](const Plan& p) { return p.bwd_scatter_a; });
+  M->bwd_scatter_b = concat([](const Plan& p) { return p.bwd_scatter_b; });
+  // GEMM tiles per (kind, phase), longest reductions first across problems
+  for (int kind = 0; kind < kGemmKinds; ++kind)
+    for (int ph = 0; ph < 3; ++ph) {
+      std::vector<GemmTile> v;
+      for (int i = 0; i < n; ++i) {
+        const Range r = ps[i]->gemm_range[kind][ph];
+        for (int t = r.first; t < r.first + r.count; ++t) {
+          GemmTile g = ps[i]->tiles[t];
+          g.sector += kind == 0 ? tc0[i] : simt0[i];
+          v.push_back(g);
+        }
+      }
+      std::stable_sort(v.begin(), v.end(), [](const GemmTile& a, const GemmTile& b) { return a.k1 - a.k0 > b.k1 - b.k0; });
+      M->gemm_range[kind][ph] = Range{(int)M->tiles.size(), (int)v.size()};
+      for (auto& g : v) {
+        M->tiles.push_back(g);
+        M->tile_kind.push_back(kind);
+      }
+    }
+  {
+    const int es = f64 ? 8 : 4;
+    M->set_item_bytes({0, (int)M->items.size()}, es, es);
+    const int64_t src[4] = {M->numel_a, M->numel_b, M->numel_c, M->outm_elems};
+    const int64_t dst[DST_COUNT] = {M->numel_c, M->numel_a, M->numel_b, M->lin_elems, M->outm_elems, M->img_elems};
+    M->validate(src, dst);
+  }
+  validate_gemms(*M, f64);
+  M->upload(device);
+  return M;
 }
 
 // ------------------------------------------------------------------- execution --

@@ -125,6 +125,10 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
 std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std::vector<int>& pairsA,
                                     const std::vector<int>& pairsB, const Tensor& C, int precision,
                                     bool device = true);
+// many independent contractions as one plan over packed buffers (see plan.cpp)
+std::unique_ptr<Plan> merge_contract_plans(std::vector<std::unique_ptr<Plan>>& ps, const std::vector<int64_t>& offA,
+                                           const std::vector<int64_t>& offB, const std::vector<int64_t>& offC,
+                                           bool device = true);
 
 // Execution (asynchronous on `stream`); return SYM_OK or a negative code.
 int exec_transform(Plan& p, const void* in, void* out, void* stream);

@@ -87,6 +87,11 @@ class Plan:
         self.kind = kind
         self.precision = precision
 
+    @property
+    def c_numel(self):
+        """Elements of the result (of all problems, for a batch plan)."""
+        return self.out.numel
+
     def stats(self):
         f = ctypes.c_double()
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
@@ -182,6 +187,59 @@ def contract_plan(A, B, pairsA, pairsB, precision=BF16X3, tree_c=None):
     return plan
 
 
+class BatchPlan(Plan):
+    """One plan over many independent contractions on packed buffers.
+
+    ``outs[i]`` is problem i's result structure; ``off_a``, ``off_b``,
+    ``off_c`` (length n + 1) are the element offsets of each problem in the
+    packed A, B and C (the last entry is the packed size).
+    """
+
+    def __init__(self, handle, outs, offsets, precision):
+        super().__init__(handle, None, "contract", precision)
+        n = len(outs)
+        self.outs = outs
+        self.off_a = [int(x) for x in offsets[:n + 1]]
+        self.off_b = [int(x) for x in offsets[n + 1:2 * (n + 1)]]
+        self.off_c = [int(x) for x in offsets[2 * (n + 1):]]
+
+    @property
+    def c_numel(self):
+        return self.off_c[-1]
+
+
+def contract_batch_plan(As, Bs, pairsA, pairsB, precision=BF16X3):
+    """Plan (cached) of contracting As[i] with Bs[i] over the same leg pairs, all i at once."""
+    key = ("b", tuple(id(a) for a in As), tuple(id(b) for b in Bs), tuple(pairsA), tuple(pairsB), precision)
+    hit = _PLANS.get(key)
+    if hit is not None:
+        return hit[0]
+    n = len(As)
+    if n != len(Bs) or n < 1:
+        raise ValueError("As and Bs must be non-empty lists of equal length")
+    Ah = (ctypes.c_void_p * n)(*[a._h for a in As])
+    Bh = (ctypes.c_void_p * n)(*[b._h for b in Bs])
+    Ch = (ctypes.c_void_p * n)()
+    offs = np.zeros(3 * (n + 1), dtype=np.int64)
+    p = ctypes.c_void_p()
+    L.check(L.lib.sym_contract_batch_plan(n, Ah, Bh, len(pairsA), L.int_array(pairsA), L.int_array(pairsB),
+                                          int(precision), Ch, offs.ctypes.data_as(L._LP), _byref(p)))
+    outs = [Structure(As[i].group, total=As[i].total + Bs[i].total, _handle=ctypes.c_void_p(Ch[i]))
+            for i in range(n)]
+    plan = BatchPlan(p, outs, offs, int(precision))
+    _PLANS[key] = (plan, tuple(As), tuple(Bs))
+    return plan
+
+
+def contract_batch(plan, a, b):
+    """Packed results of a batch plan: c[off_c[i]:off_c[i+1]] = contract(problem i) (autograd-aware)."""
+    if a.numel() != plan.off_a[-1] or b.numel() != plan.off_b[-1]:
+        raise ValueError("packed inputs do not match the batch plan")
+    if _precision(a.dtype) != plan.precision or b.dtype != a.dtype:
+        raise TypeError("packed inputs must have the plan's precision")
+    return _Contract.apply(plan, a.contiguous(), b.contiguous())
+
+
 def _transform_plan(key, make):
     hit = _PLANS.get(key)
     if hit is not None:
@@ -220,7 +278,7 @@ def split_plan(S, leg, parts, precision=BF16X3):
 class _Contract(torch.autograd.Function):
     @staticmethod
     def forward(ctx, plan, a, b):
-        c = torch.empty(plan.out.numel, dtype=a.dtype, device=a.device)
+        c = torch.empty(plan.c_numel, dtype=a.dtype, device=a.device)
         L.check(L.lib.sym_contract(plan._h, _ptr(a), _ptr(b), _ptr(c), _stream()))
         ctx.plan = plan
         ctx.save_for_backward(a, b)

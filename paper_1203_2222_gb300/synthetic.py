@@ -16,6 +16,11 @@ Workload shapes (all seeds are ``1234 + index``):
 * ``u1_mps_heff``   MPS effective-Hamiltonian apply (L.A).W.R with bond
   D = 2048 over charges -20..20 (Gaussian degeneracy profile, sigma 6),
   physical leg {0:1, 1:1}, MPO leg {-1:1, 0:3, +1:1}.
+* ``u1_two_site_batch``  n independent two-site effective-Hamiltonian
+  applies Y = (((L.theta).W1).W2).R, problem i seeded by seed * 1000 + i:
+  bond D_i = round(exp(U(ln 64, ln 1024))) over charges -12..12 with the
+  Gaussian profile above (sigma_i ~ U(2, 6)), physical legs {0:1, 1:1},
+  MPO legs {-1:1, 0:3, +1:1}.
 * ``su2_recouple``  rank-4 SU(2) tensors, every leg with 2j = 0..8 and
   degeneracies uniform in 1..dmax (32 at full size); A has all legs out in
   the comb tree, is permuted (0,2,1,3) into the matrix tree and its legs 1,3
@@ -101,3 +106,35 @@ def su2_recouple(dmax=32, jmax2=8, seed=1236):
     B = [(spins, dl[1], -1), (spins, dl[3], -1), (spins, dl[4], 1), (spins, dl[5], 1)]
     return {"group": "su2", "A": A, "B": B, "perm": [0, 2, 1, 3],
             "pairsA": [1, 3], "pairsB": [0, 1], "seedA": seed, "seedB": seed + 1}
+
+
+def u1_two_site_batch(n=512, seed=1238, dmin=64, dmax=1024, qmax=12):
+    """Legs of n two-site problems L[a,w,a'] theta[a',s1',s2',b'] W1 W2 R[b,w'',b'].
+
+    Directions: L (in, in, out), theta (in, in, in, out), W (out, in, out, in),
+    R (out, out, in).  Contraction chain per problem:
+      T1 = L.theta   over L2 <-> theta0          -> [a, w, s1', s2', b']
+      T2 = T1.W1     over T1(1,2) <-> W1(0,2)    -> [a, s2', b', s1, w']
+      T3 = T2.W2     over T2(1,4) <-> W2(2,0)    -> [a, b', s1, s2, w'']
+      Y  = T3.R      over T3(1,4) <-> R(2,1)     -> [a, s1, s2, b]
+    """
+    wq, wd = [-1, 0, 1], [1, 3, 1]
+    phys_in, phys_out = ([0, 1], [1, 1], -1), ([0, 1], [1, 1], 1)
+    probs = []
+    for i in range(n):
+        rng = np.random.default_rng(seed * 1000 + i)
+        D = int(round(math.exp(rng.uniform(math.log(dmin), math.log(dmax)))))
+        sigma = float(rng.uniform(2.0, 6.0))
+        qs, d = gaussian_degeneracies(D, -qmax, qmax, sigma)
+        bond_in, bond_out = (qs, d, -1), (qs, d, 1)
+        probs.append({
+            "D": D, "sigma": sigma,
+            "L": [bond_in, (wq, wd, -1), bond_out],
+            "theta": [bond_in, phys_in, phys_in, bond_out],
+            "W": [(wq, wd, 1), phys_in, phys_out, (wq, wd, -1)],
+            "R": [bond_out, (wq, wd, 1), bond_in],
+            "seed": seed * 1000 + i,
+        })
+    steps = [("L", "theta", [2], [0]), (None, "W", [1, 2], [0, 2]), (None, "W", [1, 4], [2, 0]),
+             (None, "R", [1, 4], [2, 1])]
+    return {"group": "u1", "problems": probs, "steps": steps}
