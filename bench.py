@@ -40,10 +40,10 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--workload", choices=["u1_mps_heff", "su2_recouple", "u1_two_site_batch"],
+    ap.add_argument("--workload", choices=["u1_mps_heff", "su2_recouple", "u1_two_site_batch", "u1_mera_grad"],
                     default="u1_mps_heff",
                     help="u1_mps_heff (default, the metric's configuration), the large-sector su2_recouple, "
-                         "or the 512-problem u1_two_site_batch")
+                         "the 512-problem u1_two_site_batch or the MERA gradient u1_mera_grad")
     ap.add_argument("--steps", type=int, default=None, help="timed steps (default 100; su2_recouple 5)")
     ap.add_argument("--warmup", type=int, default=None, help="warm-up steps (default 5; su2_recouple 3)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -329,7 +329,78 @@ class BatchWorkload:
         return y, grads
 
 
-WORKLOADS = {"u1_mps_heff": MPSWorkload, "su2_recouple": SU2Workload, "u1_two_site_batch": BatchWorkload}
+class MeraWorkload:
+    """Energy E = <psi|h|psi>/<psi|psi> of a ternary-MERA patch (U(1), chi = 48)
+    and its gradient with respect to the disentangler u and the isometry w,
+    the environment checkpointed (recomputed in the backward pass)."""
+    name = "u1_mera_grad"
+    describe = ("u1_mera_grad: E of psi=(1x1xux1x1)(wxw)t, chi=48 over q=-4..4 (deg 5, +1 on q=-1,0,1), "
+                "XXZ-like h on the bond under u, gradient w.r.t. u and w (environment checkpointed)")
+    default_steps, default_warmup, default_fp64_steps = 50, 5, 5
+
+    def build(self, P, dev):
+        import torch
+        from paper_1203_2222_gb300 import networks, synthetic
+        self.spec = synthetic.u1_mera()
+        self.S = networks.mera_structures(self.spec)
+        h, one = networks.mera_h_and_identity(self.S, self.spec)
+        scale = 1.0 / np.sqrt(self.spec["chi"])
+        self.const = {}
+        for n in ("t",):
+            self.const[n] = torch.as_tensor(synthetic.normal(self.spec["seeds"][n], self.S[n].numel) * scale)
+        self.const["h"], self.const["1"] = torch.as_tensor(h), torch.as_tensor(one)
+        self.dev = dev
+        self.data = {n: torch.as_tensor(synthetic.normal(self.spec["seeds"][n], self.S[n].numel) * scale)
+                     .to(torch.float32).to(dev).requires_grad_(True) for n in ("w", "u")}
+        self.G = torch.ones((), device=dev)
+        self.step(P, self.data, self.G)  # plans
+
+    def _const(self, dtype):
+        cache = self.__dict__.setdefault("_by_dtype", {})
+        if dtype not in cache:
+            cache[dtype] = {n: v.to(dtype).to(self.dev) for n, v in self.const.items()}
+        return cache[dtype]
+
+    def step(self, P, data, G):
+        import torch
+        from paper_1203_2222_gb300 import networks
+        c = self._const(data["w"].dtype)
+        E = networks.mera_energy(self.S, c["t"], data["w"], data["u"], c["h"], c["1"], checkpoint=True)
+        grads = torch.autograd.grad(E, [data["w"], data["u"]], grad_outputs=G.to(E.dtype))
+        return E.reshape(1), grads
+
+    def contractions(self, P, prec):
+        """(plan, gradient w.r.t. A computed, w.r.t. B computed) of every contraction of the step."""
+        S = self.S
+        cp = lambda a, b, pa, pb: P.contract_plan(a, b, pa, pb, prec)
+        top = cp(S["t"], S["t*"], [], [])
+        w1 = cp(S["w"], S["w*"], [1, 2], [1, 2])
+        w2 = cp(S["w"], S["w*"], [2, 3], [2, 3])
+        x = cp(top.out, w1.out, [0, 2], [0, 2])
+        rho = cp(x.out, w2.out, [0, 1], [0, 2])
+        y = cp(S["u"], rho.out, [2, 3], [0, 2])
+        rp = cp(y.out, S["u*"], [2, 3], [2, 3])
+        num = cp(rp.out, S["h*"], [0, 1, 2, 3], [0, 1, 2, 3])
+        den = cp(rp.out, S["1*"], [0, 1, 2, 3], [0, 1, 2, 3])
+        # the environment is checkpointed: its forward contractions run twice
+        env = [(top, False, False), (w1, True, True), (w2, True, True), (x, False, True), (rho, True, True)]
+        rest = [(y, True, True), (rp, True, True), (num, True, False), (den, True, False)]
+        return env + [(p, False, False) for p, _, _ in env] + rest
+
+    def flops_and_bytes(self, P, prec):
+        """Useful flops and algorithmic bytes of one step: each contraction's
+        forward, plus one GEMM and its operands per gradient it computes."""
+        fl = by = 0.0
+        for p, ga, gb in self.contractions(P, prec):
+            st = p.stats()
+            a, b, c = st["bytes_a"], st["bytes_b"], st["bytes_c"]
+            fl += st["flops_fwd"] * (1 + ga + gb)
+            by += a + b + c + (c + b + a if ga else 0) + (c + a + b if gb else 0)
+        return fl, by
+
+
+WORKLOADS = {"u1_mps_heff": MPSWorkload, "su2_recouple": SU2Workload, "u1_two_site_batch": BatchWorkload,
+             "u1_mera_grad": MeraWorkload}
 
 
 # ---------------------------------------------------------------- roofline ---
@@ -419,8 +490,11 @@ def run_ours(args, rank, world):
     def run_once(dt, Gt):
         return wl.step(P, dt, Gt)
 
-    flops = step_flops(P, P.BF16X3)
-    alg_bytes = step_alg_bytes(P, P.BF16X3)
+    if hasattr(wl, "flops_and_bytes"):
+        flops, alg_bytes = wl.flops_and_bytes(P, P.BF16X3)
+    else:
+        flops = step_flops(P, P.BF16X3)
+        alg_bytes = step_alg_bytes(P, P.BF16X3)
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -789,11 +863,57 @@ class OracleBatch:
             dc, _, _ = oc.contract_grad("u1", a, b, pa, pb, dc)
 
 
+class OracleMera:
+    """The FP64 CPU oracle on the MERA workload: the dense energy of the patch
+    (oracle.mera.energy, reduced density matrices, numpy BLAS einsums)."""
+
+    def __init__(self):
+        from oracle import mera, u1
+        from paper_1203_2222_gb300 import synthetic
+        spec = synthetic.u1_mera()
+        legs = {n: [u1.Leg(*l) for l in spec[n]] for n in ("t", "w", "u", "h")}
+        scale = 1.0 / np.sqrt(spec["chi"])
+        self.dense = {n: u1.embed(legs[n], 0, synthetic.normal(spec["seeds"][n], u1.layout(legs[n], 0)[2]) * scale)
+                      for n in ("t", "w", "u")}
+        self.H = mera.h_dense(legs["h"], lambda *a: synthetic.mera_h_entry(spec["delta"], *a))
+        self.mera = mera
+
+    def energy(self):
+        d = self.dense
+        return self.mera.energy(d["t"], d["w"], d["u"], self.H)
+
+
+def mera_forward_flops():
+    """Useful forward flops of the MERA energy (host planning only)."""
+    os.environ["SYM_PLAN_DRYRUN"] = "1"
+    try:
+        import paper_1203_2222_gb300 as P
+        wl = MeraWorkload()
+        from paper_1203_2222_gb300 import networks, synthetic
+        wl.spec = synthetic.u1_mera()
+        wl.S = networks.mera_structures(wl.spec)
+        uniq = {id(p): p for p, _, _ in wl.contractions(P, P.BF16X3)}
+        return sum(p.stats()["flops_fwd"] for p in uniq.values())
+    finally:
+        del os.environ["SYM_PLAN_DRYRUN"]
+
+
 BATCH_SAMPLE = 4  # problems per oracle step (the smallest ones, about a second of host work)
 BATCH_BASELINE = 24  # problems of the cpu_baseline sample (about 10 s of host work)
 
 
 def cpu_baseline(args, flops, steps):
+    if args.workload == "u1_mera_grad":
+        o = OracleMera()
+        fwd = mera_forward_flops()
+        n = max(steps, 1) * 3
+        t0 = time.perf_counter()
+        for _ in range(n):
+            o.energy()
+        dt = time.perf_counter() - t0
+        return {"value": round(fwd * n / dt / 1e12, 9), "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+                "sample": f"{n} dense evaluations of the energy (no gradient: the oracle has none but finite "
+                          f"differences), credited the forward useful flops of the block-sparse path; {dt:.1f} s"}
     if args.workload == "u1_two_site_batch":
         o = OracleBatch()
         probs = o.order[:BATCH_BASELINE * max(steps, 1)]
@@ -836,6 +956,30 @@ def su2_flops_per_entry_cached():
     if not _PER_ENTRY:
         _PER_ENTRY.append(su2_flops_per_entry())
     return _PER_ENTRY[0]
+
+
+def run_reference_mera(args):
+    """Oracle reference arm for u1_mera_grad: each step is one dense energy evaluation."""
+    fwd = mera_forward_flops()
+    o = OracleMera()
+    for _ in range(args.warmup):
+        o.energy()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.energy()
+    dt = time.perf_counter() - t0
+    value = fwd * args.steps / dt / 1e12
+    sample = ("step = one dense FP64 evaluation of the energy (numpy oracle, no gradient), credited the forward "
+              "useful flops of the block-sparse path")
+    return {
+        "metric": METRIC, "value": round(value, 9), "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": MeraWorkload.describe, "sample": sample},
+        "cpu_baseline": {"value": round(value, 9), "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 9), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
 
 
 def run_reference_batch(args):
@@ -942,6 +1086,8 @@ def main():
             out = run_reference_su2(args)
         elif args.workload == "u1_two_site_batch":
             out = run_reference_batch(args)
+        elif args.workload == "u1_mera_grad":
+            out = run_reference_mera(args)
         else:
             out = run_reference(args, contraction_flops_host())
         print(json.dumps(out))

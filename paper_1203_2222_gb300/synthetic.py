@@ -21,6 +21,11 @@ Workload shapes (all seeds are ``1234 + index``):
   bond D_i = round(exp(U(ln 64, ln 1024))) over charges -12..12 with the
   Gaussian profile above (sigma_i ~ U(2, 6)), physical legs {0:1, 1:1},
   MPO legs {-1:1, 0:3, +1:1}.
+* ``u1_mera``  a patch of a ternary U(1) MERA: bond chi = 48 over charges
+  -4..4 (degeneracy 5, plus 1 on q = -1, 0, 1), a charge-0 top t (out, out),
+  two copies of the isometry w (upper leg in, three lower legs out) and a
+  disentangler u (two lower legs in, two upper legs out) on the middle bond;
+  h is the XXZ-like two-site term given entry by entry (``mera_h_entry``).
 * ``su2_recouple``  rank-4 SU(2) tensors, every leg with 2j = 0..8 and
   degeneracies uniform in 1..dmax (32 at full size); A has all legs out in
   the comb tree, is permuted (0,2,1,3) into the matrix tree and its legs 1,3
@@ -138,3 +143,36 @@ def u1_two_site_batch(n=512, seed=1238, dmin=64, dmax=1024, qmax=12):
     steps = [("L", "theta", [2], [0]), (None, "W", [1, 2], [0, 2]), (None, "W", [1, 4], [2, 0]),
              (None, "R", [1, 4], [2, 1])]
     return {"group": "u1", "problems": probs, "steps": steps}
+
+
+def u1_mera(chi_extra=1, qmax=4, deg=5, delta=0.8, seed=1237):
+    """Legs of the MERA patch: t[T, S], w[T, a1, a2, a3], u[c, d, a, b], h[c, d, c', d'].
+
+    chi = deg * (2 qmax + 1) + chi_extra * 3 (48 by default): degeneracy
+    ``deg`` on every charge plus ``chi_extra`` on q = -1, 0, 1.  h acts on the
+    two middle sites (w1's a3 and w2's a1 after u): upper legs c, d (out),
+    lower legs c', d' (in).
+    """
+    qs = list(range(-qmax, qmax + 1))
+    d = [deg + (chi_extra if abs(q) <= 1 else 0) for q in qs]
+    out_, in_ = (qs, d, 1), (qs, d, -1)
+    return {"group": "u1", "chi": sum(d), "delta": delta,
+            "t": [out_, out_], "w": [in_, out_, out_, out_], "u": [out_, out_, in_, in_],
+            "h": [out_, out_, in_, in_],
+            "seeds": {"t": seed, "w": seed + 1, "u": seed + 2}}
+
+
+def mera_h_entry(delta, qc, tc, qd, td, qc2, tc2, qd2, td2):
+    """<c d| h |c' d'> for h = (S+ S- + S- S+) / 2 + delta Sz Sz on two sites.
+
+    Sz = diag(q); S+ raises the charge by one and keeps the degeneracy index
+    (zero where the target charge has fewer states, which the caller's index
+    range already excludes).  Charges and indices of the upper legs c, d and
+    of the lower legs c', d'.
+    """
+    v = 0.0
+    if qc == qc2 and qd == qd2 and tc == tc2 and td == td2:
+        v += delta * qc2 * qd2
+    if tc == tc2 and td == td2 and ((qc == qc2 + 1 and qd == qd2 - 1) or (qc == qc2 - 1 and qd == qd2 + 1)):
+        v += 0.5
+    return v
