@@ -44,6 +44,9 @@ def parse():
                     default="u1_mps_heff",
                     help="u1_mps_heff (default, the metric's configuration), the large-sector su2_recouple, "
                          "the 512-problem u1_two_site_batch or the MERA gradient u1_mera_grad")
+    ap.add_argument("--su2-dmax", type=int, default=32,
+                    help="su2_recouple: largest degeneracy (32 = the full configuration; smaller sizes serve "
+                         "profiler captures of the same kernels)")
     ap.add_argument("--steps", type=int, default=None, help="timed steps (default 100; su2_recouple 5)")
     ap.add_argument("--warmup", type=int, default=None, help="warm-up steps (default 5; su2_recouple 3)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -260,10 +263,12 @@ class SU2Workload:
                 "A comb tree recoupled (6j) to the matrix tree, contract A(1,3) with B(0,1); fwd+bwd")
     default_steps, default_warmup, default_fp64_steps = 5, 3, 1
 
+    dmax = 32
+
     def build(self, P, dev):
         import torch
         from paper_1203_2222_gb300 import synthetic
-        self.c = synthetic.su2_recouple(dmax=32, jmax2=8)
+        self.c = synthetic.su2_recouple(dmax=self.dmax, jmax2=8)
         self.S = {"A": P.Structure(P.SU2, self.c["A"]), "B": P.Structure(P.SU2, self.c["B"])}
         gen = torch.Generator(device=dev)
         gen.manual_seed(1236)
@@ -411,13 +416,13 @@ WORKLOADS = {"u1_mps_heff": MPSWorkload, "su2_recouple": SU2Workload, "u1_two_si
 # sources at that time: once a source changes, the figure no longer applies
 # and the bench reports null.
 TRAFFIC = {
-    "box_flat": {"bytes_per_launch": 9246112, "sha": "7caa23204aa92eac"},
-    "box": {"bytes_per_launch": 12494144, "sha": "7caa23204aa92eac"},
-    "gemm_tc": {"bytes_per_launch": 14657152, "sha": "b64755ea88806cf8"},
-    "gemm_tile": {"bytes_per_launch": 807616, "sha": "e9cb7580d709691c"},
-    "gemm_rows": {"bytes_per_launch": 3204045, "sha": "e9cb7580d709691c"},
-    "gemm_thin": {"bytes_per_launch": 3170355, "sha": "e9cb7580d709691c"},
-    "gemm_wide": {"bytes_per_launch": 71083, "sha": "e9cb7580d709691c"},
+    "box_flat": {"bytes_per_launch": 8914432, "sha": "2051b6c5a77d9fe4"},
+    "box": {"bytes_per_launch": 8430848, "sha": "2051b6c5a77d9fe4"},
+    "gemm_tc": {"bytes_per_launch": 12505728, "sha": "4bfc4e6cd1d23db5"},
+    "gemm_tile": {"bytes_per_launch": 807360, "sha": "8ee88fc5d4527c52"},
+    "gemm_rows": {"bytes_per_launch": 3203789, "sha": "8ee88fc5d4527c52"},
+    "gemm_thin": {"bytes_per_launch": 3170406, "sha": "8ee88fc5d4527c52"},
+    "gemm_wide": {"bytes_per_launch": 71168, "sha": "8ee88fc5d4527c52"},
 }
 KERNEL_SOURCES = {
     "box": ["box.cu", "kernels.h", "pdl.h"], "box_flat": ["box.cu", "kernels.h", "pdl.h"],
@@ -482,6 +487,8 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     wl = WORKLOADS[args.workload]()
+    if args.workload == "su2_recouple":
+        wl.dmax = args.su2_dmax
 
     # ---- split-BF16 x3 path (the value); the first contraction builds the plans
     wl.build(P, dev)
@@ -695,7 +702,8 @@ def run_ours(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16x3-f32acc", "data": "synthetic",
-        "config": {"workload": wl.describe, "precision": "split-BF16 x3 on tcgen05, FP32 accumulate, fp32 blocks",
+        "config": {"workload": wl.describe + (f" [dmax {args.su2_dmax}]" if args.workload == "su2_recouple" and
+                                               args.su2_dmax != 32 else ""), "precision": "split-BF16 x3 on tcgen05, FP32 accumulate, fp32 blocks",
                    "useful_gflop_per_step": round(flops / 1e9, 4),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "launch": launch_mode,
