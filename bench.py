@@ -429,6 +429,7 @@ KERNEL_SOURCES = {
     "gemm_tc": ["gemm_tc.cu", "kernels.h", "pdl.h"],
     "gemm_tile": ["gemm_simt.cu", "kernels.h", "pdl.h"], "gemm_wide": ["gemm_simt.cu", "kernels.h", "pdl.h"],
     "gemm_thin": ["gemm_simt.cu", "kernels.h", "pdl.h"], "gemm_rows": ["gemm_simt.cu", "kernels.h", "pdl.h"],
+    "direct": ["direct.cu", "kernels.h", "pdl.h"],
 }
 
 
@@ -444,8 +445,9 @@ def kernel_source_sha(kern):
 def roofline(prof, clk, sustained=False):
     """Roofline of the kernel with the largest summed device time.
 
-    box kernels: HBM-bound, algorithmic bytes (block data read once + written
-    once) per launch / mean launch time vs the measured copy bandwidth;
+    box kernels, the direct kernel and the rows / thin GEMMs: HBM-bound,
+    algorithmic bytes (block data read once + written once) per launch / mean
+    launch time vs the measured copy bandwidth;
     tcgen05: useful flops vs the measured bf16 peak / 3 (three BF16 passes);
     CUDA-core GEMMs: FP32 FMA peak from the unit count and the sampled clock.
     """
@@ -456,7 +458,9 @@ def roofline(prof, clk, sustained=False):
     d = prof[dom]
     n = max(d["launches"], 1)
     sec = d["ms"] * 1e-3 / n  # mean launch duration
-    if dom.startswith("box"):
+    if dom.startswith("box") or dom in ("direct", "gemm_rows", "gemm_thin"):
+        # streaming kernels: block movement, the direct contraction of tiny
+        # sectors, and the GEMMs with a side of at most 16 (A, B, C once)
         bound, unit, per = "hbm", "GB/s", d["bytes"] / n
         achieved, peak = per / sec / 1e9, peaks["hbm_gbs"]
         src = f"{peak_src} hbm_gbs"

@@ -145,7 +145,11 @@ int sym_plan_execute(sym_plan plan, const void* in, void* out, void* stream);
  *   at the root.  Steps on the device: gather A and B into per-sector matrix
  *   form (block transpose; SU(2): recoupling by precomputed 6j/swap
  *   coefficients), one grouped per-sector GEMM (blockwise product,
- *   Ch. 5 Eq. blockmult), scatter into C's blocks.
+ *   Ch. 5 Eq. blockmult), scatter into C's blocks.  U(1) sectors whose
+ *   matrix of B is at most 4 x 4 (an MPO or physical leg on the contracted
+ *   side) skip the matrix form: their product is taken directly on A's and
+ *   C's blocks with B's sector matrix as coefficients (one streaming pass;
+ *   the gradient of B is an atomic reduction into dB).
  * sym_contract: C = contract(A, B) on device buffers.
  * sym_contract_backward: dA, dB = gradient of <dC, C> with respect to A's
  *   and B's blocks (adjoint on the same sector tables); dA or dB may be NULL
@@ -212,6 +216,8 @@ int sym_plan_gemm_shapes(sym_plan plan, int* nsec, int* mnk);
 #define SYM_PHASE_TRANSFORM 6
 #define SYM_PHASE_FWD_GEMM_CUDA_CORES 7 /* forward sectors on the CUDA-core GEMMs */
 #define SYM_PHASE_BWD_GEMM_CUDA_CORES 8
+#define SYM_PHASE_FWD_DIRECT 9  /* forward sectors contracted directly on the blocks */
+#define SYM_PHASE_BWD_DIRECT 10 /* their dA and dB */
 int sym_plan_profile(sym_plan plan, int enable);
 int sym_plan_profile_read(sym_plan plan, int phase, int* launches,
                           double* total_ms, double* bytes, double* flops);
@@ -226,7 +232,8 @@ int sym_plan_profile_read(sym_plan plan, int phase, int* launches,
 #define SYM_KERNEL_GEMM_WIDE 4 /* CUDA cores, 256 x 16 tiles */
 #define SYM_KERNEL_GEMM_THIN 5 /* CUDA cores, m, n <= 8, split reduction */
 #define SYM_KERNEL_GEMM_ROWS 6 /* CUDA cores, k, n <= 16 */
-#define SYM_KERNEL_COUNT 7
+#define SYM_KERNEL_DIRECT 7    /* sectors with a tiny matrix, contracted on the blocks */
+#define SYM_KERNEL_COUNT 8
 int sym_plan_profile_kernel(sym_plan plan, int kernel, int* launches,
                             double* total_ms, double* bytes, double* flops);
 

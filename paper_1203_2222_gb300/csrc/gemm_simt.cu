@@ -11,12 +11,14 @@
 //         shared memory, the next slice prefetched into registers while the
 //         current one is multiplied; a tile may cover a slice [k0, k1) of the
 //         reduction (split-K: slices add into a zero-filled C with atomics).
-//   rows  k, n <= 16: one output row per thread, B held in shared memory --
-//         a streaming kernel (read a row of A, write a row of C).
+//   rows  k, n <= 16: a persistent streaming kernel -- each warp stages runs
+//         of whole rows of A in shared memory and writes whole rows of C.
 //   thin  m, n <= 8 and a long reduction: each thread streams k and keeps
 //         the whole m x n outer-product sum in registers, then the CTA
 //         reduces and adds its slice into C.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "kernels.h"
 #include "pdl.h"
@@ -108,42 +110,75 @@ __global__ void __launch_bounds__(256) gemm_tile_kernel(const GemmSectorSimt* __
   }
 }
 
-// k, n <= 16: C[r, :] = A[r, :] B, one row per thread, 256 rows per CTA.
+// k, n <= 16: C = A B streamed.  Persistent: each warp walks its own tiles
+// (row ranges of one sector).  Per step it reads rows_span(k) whole rows of
+// A -- one contiguous run of <= 512 elements -- with coalesced loads into its
+// shared-memory span (the next run is in flight in registers meanwhile);
+// then lane (rl, j) = (lane >> lg, lane & (2^lg - 1)), 2^lg >= n, computes
+// C[r, j] for rows r = rl, rl + 32 >> lg, ... of the run, with its column of
+// B in registers, so each store instruction writes whole consecutive rows of
+// C.  A and C are dense (lda == k, ldc == n); B may be stored transposed.
 template <typename T>
 __global__ void __launch_bounds__(256) gemm_rows_kernel(const GemmSectorSimt* __restrict__ secs,
-                                                        const GemmTile* __restrict__ tiles,
+                                                        const GemmTile* __restrict__ tiles, int ntiles,
                                                         const T* __restrict__ ops, T* __restrict__ outm) {
-  __shared__ T Bs[16][17];
-  const GemmTile tl = tiles[blockIdx.x];
-  const GemmSectorSimt s = secs[tl.sector];
+  constexpr int V = kRowsSpan / 32;  // elements of a run per lane
+  __shared__ T span[8][kRowsSpan];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* __restrict__ sp = span[warp];
   pdl_wait();
   pdl_launch_dependents();
-  const T* __restrict__ a = ops + s.a_off;
-  const T* __restrict__ b = ops + s.b_off;
-  for (int i = threadIdx.x; i < s.k * s.n; i += 256) Bs[i / s.n][i % s.n] = __ldg(b + (int64_t)(i / s.n) * s.ldb + i % s.n);
-  __syncthreads();
-  const int r = tl.mt * 256 + threadIdx.x;
-  if (r >= s.m) return;
-  T av[16];
+  for (int t = blockIdx.x * 8 + warp; t < ntiles; t += gridDim.x * 8) {
+    const GemmTile tl = tiles[t];
+    const GemmSectorSimt s = secs[tl.sector];
+    const int k = s.k, n = s.n;
+    const int lg = n <= 1 ? 0 : n <= 2 ? 1 : n <= 4 ? 2 : n <= 8 ? 3 : 4;
+    const int j = lane & ((1 << lg) - 1), rl = lane >> lg, rstep = 32 >> lg;
+    const int rw = rows_span(k);
+    const T* __restrict__ a = ops + s.a_off;
+    const T* __restrict__ b = ops + s.b_off;
+    T* __restrict__ c = outm + s.c_off;
+    const int64_t bj = (s.trans & kTransB) ? (int64_t)j * s.ldb : j, bk = (s.trans & kTransB) ? 1 : s.ldb;
+    T bv[16];
 #pragma unroll
-  for (int kk = 0; kk < 16; ++kk) av[kk] = kk < s.k ? __ldg(a + (int64_t)r * s.lda + kk) : T(0);
-  T* c = outm + s.c_off + (int64_t)r * s.ldc;
-  const T alpha = T(s.alpha);
+    for (int kk = 0; kk < 16; ++kk) bv[kk] = (kk < k && j < n) ? __ldg(b + bj + kk * bk) : T(0);
+    const T alpha = T(s.alpha);
+    T v[V];
+    auto load = [&](int r0) {
+      const int lim = min(rw, tl.k1 - r0) * k;  // elements of this run
+      const T* __restrict__ src = a + (int64_t)r0 * k;
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    if (j >= s.n) break;
-    T acc = T(0);
+      for (int u = 0; u < V; ++u) {
+        const int e = lane + 32 * u;
+        v[u] = e < lim ? __ldg(src + e) : T(0);
+      }
+    };
+    load(tl.k0);
+    for (int r0 = tl.k0; r0 < tl.k1; r0 += rw) {
+      __syncwarp();  // the previous run's readers are done with the span
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk)
-      if (kk < s.k) acc = fma(av[kk], Bs[kk][j], acc);
-    c[j] = alpha * acc;
+      for (int u = 0; u < V; ++u) sp[lane + 32 * u] = v[u];
+      __syncwarp();
+      if (r0 + rw < tl.k1) load(r0 + rw);
+      const int nr = min(rw, tl.k1 - r0);
+      T* __restrict__ cr = c + (int64_t)r0 * n + j;
+      for (int rr = rl; rr < nr; rr += rstep) {
+        const T* __restrict__ row = sp + rr * k;
+        T acc = T(0);
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk)
+          if (kk < k) acc = fma(row[kk], bv[kk], acc);
+        if (j < n) cr[(int64_t)rr * n] = alpha * acc;
+      }
+    }
   }
 }
 
 // Thin GEMM: m, n <= 8 and a long reduction (e.g. the gradient of a small
 // operator).  Each thread streams k values (coalesced along A's rows and
-// B's short rows) and keeps the whole m x n outer-product sum in registers;
-// the CTA then reduces across its threads and adds its slice into C.
+// B's short rows, or through L1 along the short rows of a transposed A) and
+// keeps the whole m x n outer-product sum in registers; the CTA then reduces
+// across its threads and adds its slice into C.
 template <typename T>
 __global__ void __launch_bounds__(256) gemm_thin_kernel(const GemmSectorSimt* __restrict__ secs,
                                                         const GemmTile* __restrict__ tiles,
@@ -156,6 +191,9 @@ __global__ void __launch_bounds__(256) gemm_thin_kernel(const GemmSectorSimt* __
   pdl_launch_dependents();
   const T* __restrict__ a = ops + s.a_off;
   const T* __restrict__ b = ops + s.b_off;
+  // element strides of A (i, kk) and B (kk, j), plain or transposed storage
+  const int64_t ai = (s.trans & kTransA) ? 1 : s.lda, ak = (s.trans & kTransA) ? s.lda : 1;
+  const int64_t bk = (s.trans & kTransB) ? 1 : s.ldb, bj = (s.trans & kTransB) ? s.ldb : 1;
   T acc[MX][MX];
 #pragma unroll
   for (int i = 0; i < MX; ++i)
@@ -168,9 +206,9 @@ __global__ void __launch_bounds__(256) gemm_thin_kernel(const GemmSectorSimt* __
       const int kk = k + 256 * u;
       const bool ok = kk < tl.k1;
 #pragma unroll
-      for (int i = 0; i < MX; ++i) av[u][i] = (ok && i < s.m) ? __ldg(a + (int64_t)i * s.lda + kk) : T(0);
+      for (int i = 0; i < MX; ++i) av[u][i] = (ok && i < s.m) ? __ldg(a + i * ai + kk * ak) : T(0);
 #pragma unroll
-      for (int j = 0; j < MX; ++j) bv[u][j] = (ok && j < s.n) ? __ldg(b + (int64_t)kk * s.ldb + j) : T(0);
+      for (int j = 0; j < MX; ++j) bv[u][j] = (ok && j < s.n) ? __ldg(b + kk * bk + j * bj) : T(0);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u)
@@ -206,6 +244,17 @@ __global__ void __launch_bounds__(256) gemm_thin_kernel(const GemmSectorSimt* __
   }
 }
 
+// resident CTAs of the rows kernel per SM (queried once per type)
+template <typename T>
+int rows_ctas_per_sm() {
+  static const int n = [] {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, gemm_rows_kernel<T>, 256, 0) != cudaSuccess || v < 1) v = 1;
+    return v;
+  }();
+  return n;
+}
+
 template <typename T>
 int launch_t(int shape, const GemmSectorSimt* secs, const GemmTile* tiles, int ntiles, const void* ops, void* outm,
              cudaStream_t s) {
@@ -216,7 +265,10 @@ int launch_t(int shape, const GemmSectorSimt* secs, const GemmTile* tiles, int n
     case SIMT_64x64: return (int)launch_pdl(gemm_tile_kernel<T, 64, 64>, g, b, 0, s, secs, tiles, o, c);
     case SIMT_256x16: return (int)launch_pdl(gemm_tile_kernel<T, 256, 16>, g, b, 0, s, secs, tiles, o, c);
     case SIMT_THIN: return (int)launch_pdl(gemm_thin_kernel<T>, g, b, 0, s, secs, tiles, o, c);
-    default: return (int)launch_pdl(gemm_rows_kernel<T>, g, b, 0, s, secs, tiles, o, c);
+    default: {
+      const int ctas = std::min((ntiles + 7) / 8, tc_num_sms() * rows_ctas_per_sm<T>());
+      return (int)launch_pdl(gemm_rows_kernel<T>, dim3(ctas), b, 0, s, secs, tiles, ntiles, o, c);
+    }
   }
 }
 

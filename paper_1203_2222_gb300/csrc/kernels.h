@@ -3,6 +3,12 @@
 
 #include <cstdint>
 
+#ifdef __CUDACC__
+#define SYM_HD __host__ __device__
+#else
+#define SYM_HD
+#endif
+
 namespace sym {
 
 constexpr int kMaxDim = 6;
@@ -80,17 +86,31 @@ struct BoxPtrs {
 };
 
 // CUDA-core grouped GEMM (row-major): C = alpha * A (m x k, lda) * B (k x n, ldb).
+// trans bit 0: A is stored transposed, element (i, kk) at a[kk * lda + i];
+// bit 1: B is stored transposed, element (kk, j) at b[j * ldb + kk] (the
+// backward reads the forward's operands this way instead of gathering
+// transposed copies).  The rows kernel takes bit 1 only and needs lda == k,
+// ldc == n; the thin kernel takes both; the tile kernels neither.
 struct GemmSectorSimt {
   int32_t m, n, k, lda, ldb, ldc;
   int64_t a_off, b_off, c_off;
   double alpha;
+  int32_t trans, pad_;
 };
+constexpr int kTransA = 1, kTransB = 2;
 // One output tile; [k0, k1) is its slice of the reduction (split-K tiles of
 // one sector add into a zero-filled C with atomics when `atomic` is set).
+// Rows kernel: [k0, k1) are the tile's rows of C instead (the reduction is
+// always whole there), and a tile is the work of one warp.
 struct GemmTile {
   int32_t sector, mt, nt;
   int32_t k0, k1, atomic;
 };
+// Rows kernel: a warp stages kRowsSpan consecutive elements of A (whole rows,
+// rows_span(k) of them) in shared memory per step; a tile is kRowsSpansPerTile steps.
+constexpr int kRowsSpan = 512;
+constexpr int kRowsSpansPerTile = 8;
+SYM_HD inline int rows_span(int k) { return (kRowsSpan / k) & ~31; }  // k <= 16: >= 32 rows
 
 // tcgen05 split-BF16 x3 grouped GEMM, C (m x n, row-major FP32, ldc) =
 // alpha A B.  The operands are row-major bf16 matrices with their hi and lo
@@ -121,6 +141,35 @@ struct TcOperand {
   int32_t rows, cols, ld, mn;
 };
 
+// Direct contraction of a sector whose matrix on one side is tiny (k, n <=
+// kMaxDirect): the GEMM runs on the tensors' blocks themselves, with no
+// matrix form.  A position t of the box (the free legs of the large operand)
+// holds, for source column s, the element at src + off_s + ld_s <t, sa> +
+// <t, sb>, and for destination column d the element at dst + off_d + ld_d
+// <t, da> + <t, db> (off, ld: terms ts + s, td + d).  Coefficient (d, s) is
+// coef * slot2[off] of term tk + d kd + s ks.
+//   apply: dst_d[t] = sum_s coefficient(d, s) src_s[t]           (C = A B, dA = dC B^T)
+//   outer: out(s, d) += sum_t src_s[t] * src2_d[t], the destination columns
+//          read from slot 2 and the sums added (atomically) into the
+//          destination slot at the coefficient terms' offsets      (dB = A^T dC)
+constexpr int kMaxDirect = 4;
+constexpr int kDirectDims = 3;
+constexpr int kDirectApplyChunk = 1024;  // positions per apply item
+constexpr int kDirectOuterChunk = 8192;  // positions per outer item (one set of atomics each)
+enum DirectOp { kDirectApply = 0, kDirectOuter = 1 };
+struct DirectItem {
+  int32_t op, ns, nd, ndim;
+  int32_t start, count;
+  int32_t ts, td, tk;  // first term of the sources, destinations, coefficients
+  int32_t kd, ks;      // coefficient (d, s) is term tk + d * kd + s * ks
+  int32_t slots;       // bits 0-1 source slot, 2-3 second source slot, 4-6 destination slot
+  int32_t dims[kDirectDims], sa[kDirectDims], sb[kDirectDims], da[kDirectDims], db[kDirectDims];
+  uint32_t mag[kDirectDims];  // Granlund-Montgomery division by dims[d] (as in BoxItem)
+  int32_t shf;                // the three shifts, one byte each
+  int32_t pad_;
+};
+static_assert(sizeof(DirectItem) == 128, "DirectItem layout");
+
 // CUDA-core GEMM tile shapes
 enum SimtShape { SIMT_64x64 = 0, SIMT_256x16 = 1, SIMT_THIN = 2, SIMT_ROWS = 3, SIMT_SHAPES = 4 };
 
@@ -130,6 +179,8 @@ int launch_box(bool src_f64, bool dst_f64, bool flat_only, const BoxItem* items,
                const BoxPtrs& ptrs, void* stream);
 int launch_gemm_simt(bool f64, int shape, const GemmSectorSimt* secs, const GemmTile* tiles, int ntiles,
                      const void* ops, void* outm, void* stream);
+int launch_direct(bool f64, const DirectItem* items, int nitems, const Term* terms, const BoxPtrs& ptrs,
+                  void* stream);
 int launch_gemm_tc(const TcSector* secs, const GemmTile* tiles, int ntiles, const TensorMap* maps, float* C,
                    int* err_word, void* stream);
 // Tensor map of one operand whose hi plane starts at `hi` (bf16) and whose lo

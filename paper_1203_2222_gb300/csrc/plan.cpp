@@ -33,6 +33,7 @@
 #include <map>
 #include <cstdlib>
 #include <mutex>
+#include <set>
 
 #include "../../include/symtensor.h"
 #include "recouple.h"
@@ -577,6 +578,7 @@ void Plan::upload(bool device) {
   for (size_t i = 0; i < items.size(); ++i)
     flat_prefix[i + 1] = flat_prefix[i] + ((items[i].sel & (kSelFlat | kSelTile)) == kSelFlat ? 1 : 0);
   tile_flops_prefix.assign(tiles.size() + 1, 0.0);
+  tile_bytes_prefix.assign(tiles.size() + 1, 0.0);
   for (size_t i = 0; i < tiles.size(); ++i) {
     const GemmTile& t = tiles[i];
     int64_t m, n, TM, TN;
@@ -591,8 +593,31 @@ void Plan::upload(bool device) {
       TM = kd == 1 ? 64 : kd == 2 ? 256 : kd == 3 ? 8 : 256;
       TN = kd == 1 ? 64 : kd == 2 ? 16 : kd == 3 ? 8 : 16;
     }
-    const int64_t r = std::min<int64_t>(TM, m - t.mt * TM), c = std::min<int64_t>(TN, n - t.nt * TN);
-    tile_flops_prefix[i + 1] = tile_flops_prefix[i] + 2.0 * (double)r * (double)c * (double)(t.k1 - t.k0);
+    double fl;
+    const int64_t k = tile_kind[i] == 0 ? secs_tc[t.sector].k : secs_simt[t.sector].k;
+    if (tile_kind[i] == 4) {  // rows: [k0, k1) are rows, the reduction is whole
+      fl = 2.0 * (double)(t.k1 - t.k0) * (double)n * (double)k;
+    } else {
+      const int64_t r = std::min<int64_t>(TM, m - t.mt * TM), c = std::min<int64_t>(TN, n - t.nt * TN);
+      fl = 2.0 * (double)r * (double)c * (double)(t.k1 - t.k0);
+    }
+    tile_flops_prefix[i + 1] = tile_flops_prefix[i] + fl;
+    // algorithmic bytes: the sector's A, B and C once, shared out by flops
+    const double es = f64() ? 8.0 : 4.0;
+    const double sector_bytes = es * ((double)m * k + (double)k * n + (double)m * n);
+    tile_bytes_prefix[i + 1] = tile_bytes_prefix[i] + sector_bytes * fl / (2.0 * (double)m * n * k);
+  }
+  // direct items: algorithmic bytes (every column read or written once per
+  // position) and useful flops (2 ns nd per position)
+  ditem_bytes_prefix.assign(ditems.size() + 1, 0.0);
+  ditem_flops_prefix.assign(ditems.size() + 1, 0.0);
+  {
+    const double es = f64() ? 8.0 : 4.0;
+    for (size_t i = 0; i < ditems.size(); ++i) {
+      const DirectItem& it = ditems[i];
+      ditem_bytes_prefix[i + 1] = ditem_bytes_prefix[i] + (double)it.count * (it.ns + it.nd) * es;
+      ditem_flops_prefix[i + 1] = ditem_flops_prefix[i] + 2.0 * (double)it.count * it.ns * it.nd;
+    }
   }
   const char* dry_env = std::getenv("SYM_PLAN_DRYRUN");
   if (!device || (dry_env && dry_env[0] == '1')) {
@@ -612,6 +637,8 @@ void Plan::upload(bool device) {
   d_secs_simt = static_cast<GemmSectorSimt*>(up(secs_simt.data(), secs_simt.size() * sizeof(GemmSectorSimt)));
   d_secs_tc = static_cast<TcSector*>(up(secs_tc.data(), secs_tc.size() * sizeof(TcSector)));
   d_tiles = static_cast<GemmTile*>(up(tiles.data(), tiles.size() * sizeof(GemmTile)));
+  d_ditems = static_cast<DirectItem*>(up(ditems.data(), ditems.size() * sizeof(DirectItem)));
+  d_dterms = static_cast<Term*>(up(dterms.data(), dterms.size() * sizeof(Term)));
   if (kind == CONTRACT) {
     const size_t es = f64() ? sizeof(double) : sizeof(float);
     if (img_elems > 0) {  // hi and lo planes; the TMA loads fill past-the-edge boxes with zeros
@@ -861,11 +888,21 @@ void validate_gemms(const Plan& P, bool f64) {
     if (P.tile_kind[i] != 0) {
       if (t.sector < 0 || t.sector >= (int)P.secs_simt.size()) fail(SYM_ERR_ARG, "internal: bad GEMM sector index");
       const GemmSectorSimt& s = P.secs_simt[t.sector];
-      if (t.k0 < 0 || t.k1 > s.k || t.k0 >= t.k1 || s.a_off < 0 || s.b_off < 0 || s.c_off < 0 ||
-          s.a_off + (int64_t)(s.m - 1) * s.lda + s.k - 1 >= P.lin_elems ||
-          s.b_off + (int64_t)(s.k - 1) * s.ldb + s.n - 1 >= P.lin_elems ||
+      const bool ta = (s.trans & kTransA) != 0, tb = (s.trans & kTransB) != 0;
+      const int64_t a_last = ta ? (int64_t)(s.k - 1) * s.lda + s.m - 1 : (int64_t)(s.m - 1) * s.lda + s.k - 1;
+      const int64_t b_last = tb ? (int64_t)(s.n - 1) * s.ldb + s.k - 1 : (int64_t)(s.k - 1) * s.ldb + s.n - 1;
+      if (s.m < 1 || s.n < 1 || s.k < 1 || (s.trans & ~(kTransA | kTransB)) != 0 || s.a_off < 0 ||
+          s.b_off < 0 || s.c_off < 0 || s.a_off + a_last >= P.lin_elems || s.b_off + b_last >= P.lin_elems ||
           s.c_off + (int64_t)(s.m - 1) * s.ldc + s.n - 1 >= P.outm_elems)
         fail(SYM_ERR_ARG, "internal: CUDA-core GEMM sector past its buffers");
+      if (P.tile_kind[i] == 4) {  // rows: [k0, k1) rows of dense A and C, B maybe transposed
+        if (t.k0 < 0 || t.k1 > s.m || t.k0 >= t.k1 || s.k > 16 || s.n > 16 || s.lda != s.k || s.ldc != s.n || ta)
+          fail(SYM_ERR_ARG, "internal: rows GEMM tile out of range");
+      } else {
+        if (t.k0 < 0 || t.k1 > s.k || t.k0 >= t.k1) fail(SYM_ERR_ARG, "internal: GEMM tile reduction out of range");
+        if (P.tile_kind[i] != 3 && s.trans != 0) fail(SYM_ERR_ARG, "internal: transposed operand on a tile kernel");
+        if (P.tile_kind[i] == 3 && (s.m > 8 || s.n > 8)) fail(SYM_ERR_ARG, "internal: thin GEMM too wide");
+      }
     } else {
       if (t.sector < 0 || t.sector >= (int)P.secs_tc.size()) fail(SYM_ERR_ARG, "internal: bad GEMM sector index");
       const TcSector& s = P.secs_tc[t.sector];
@@ -886,6 +923,65 @@ void validate_gemms(const Plan& P, bool f64) {
     if (f64 || o.off < 0 || o.off % 64 || o.ld % 64 || o.ld < o.cols || o.rows < 1 || o.cols < 1 ||
         (o.mn != 0 && o.mn != 1) || o.off + (int64_t)o.rows * o.ld > P.img_elems)
       fail(SYM_ERR_ARG, "internal: tensor-core operand past its buffer");
+}
+
+// Direct items stay inside the tensors they address: numel_a (A, dA),
+// numel_b (B, dB), numel_c (C, dC); strides non-negative, so the extreme of
+// every column is at the last index of every dim.
+void validate_direct(const Plan& P) {
+  const int64_t ne[3] = {P.numel_a, P.numel_b, P.numel_c};
+  if (P.dterm_space.size() != P.dterms.size()) fail(SYM_ERR_ARG, "internal: direct term spaces missing");
+  // tensor of a source slot (0 A, 1 B, 2 dC) and of a destination slot
+  auto src_space = [](int slot) { return slot == 0 ? 0 : slot == 1 ? 1 : slot == 2 ? 2 : -1; };
+  auto dst_space = [](int slot) { return slot == DST_OUT ? 2 : slot == DST_DA ? 0 : slot == DST_DB ? 1 : -1; };
+  const Range rs[3] = {P.fwd_direct, P.bwd_direct_a, P.bwd_direct_b};
+  int expect = 0;
+  for (const Range& r : rs) {
+    if (r.first != expect || r.count < 0) fail(SYM_ERR_ARG, "internal: direct ranges out of order");
+    expect += r.count;
+  }
+  if (expect != (int)P.ditems.size()) fail(SYM_ERR_ARG, "internal: direct ranges do not cover the items");
+  for (const DirectItem& it : P.ditems) {
+    if ((it.op != kDirectApply && it.op != kDirectOuter) || it.ns < 1 || it.nd < 1 || it.ns > kMaxDirect ||
+        it.nd > kMaxDirect || it.ndim < 1 || it.ndim > kDirectDims || it.start < 0 || it.count < 1)
+      fail(SYM_ERR_ARG, "internal: bad direct item");
+    int64_t sa = 0, sb = 0, da = 0, db = 0, total = 1;
+    for (int d = 0; d < kDirectDims; ++d) {
+      if (it.dims[d] < 1 || it.sa[d] < 0 || it.sb[d] < 0 || it.da[d] < 0 || it.db[d] < 0)
+        fail(SYM_ERR_ARG, "internal: negative stride or empty dim in a direct item");
+      if (d >= it.ndim && (it.dims[d] != 1 || it.sa[d] || it.sb[d] || it.da[d] || it.db[d]))
+        fail(SYM_ERR_ARG, "internal: unused dim of a direct item is not a unit dim");
+      uint32_t m;
+      int8_t sh;
+      div_magic(it.dims[d], m, sh);
+      if (m != it.mag[d] || sh != (int8_t)((it.shf >> (8 * d)) & 0xff))
+        fail(SYM_ERR_ARG, "internal: stale division constants in a direct item");
+      sa += (int64_t)(it.dims[d] - 1) * it.sa[d];
+      sb += (int64_t)(it.dims[d] - 1) * it.sb[d];
+      da += (int64_t)(it.dims[d] - 1) * it.da[d];
+      db += (int64_t)(it.dims[d] - 1) * it.db[d];
+      total *= it.dims[d];
+    }
+    if (sa >= ((int64_t)1 << 31) || sb >= ((int64_t)1 << 31) || da >= ((int64_t)1 << 31) ||
+        db >= ((int64_t)1 << 31) || (int64_t)it.start + it.count > total)
+      fail(SYM_ERR_ARG, "internal: direct item past its box");
+    const int s1 = it.slots & 3, s2 = (it.slots >> 2) & 3, ds = (it.slots >> 4) & 7;
+    const int sp = src_space(s1);
+    const int qp = it.op == kDirectApply ? dst_space(ds) : src_space(s2);  // space of the d columns
+    const int kp = it.op == kDirectApply ? src_space(s2) : dst_space(ds);  // space of the coefficient terms
+    if (sp < 0 || qp < 0 || kp < 0) fail(SYM_ERR_ARG, "internal: bad slot in a direct item");
+    auto check = [&](int t, int space, int64_t ma, int64_t mb) {
+      if (t < 0 || t >= (int)P.dterms.size() || P.dterm_space[t] != space)
+        fail(SYM_ERR_ARG, "internal: direct term out of range");
+      const Term& x = P.dterms[t];
+      if (x.off < 0 || x.ld < 0 || x.ld >= ((int64_t)1 << 31) || x.off + x.ld * ma + mb >= ne[space])
+        fail(SYM_ERR_ARG, "internal: direct item addresses past its tensor");
+    };
+    for (int s = 0; s < it.ns; ++s) check(it.ts + s, sp, sa, sb);
+    for (int d = 0; d < it.nd; ++d) check(it.td + d, qp, da, db);
+    for (int d = 0; d < it.nd; ++d)
+      for (int s = 0; s < it.ns; ++s) check(it.tk + d * it.kd + s * it.ks, kp, 0, 0);
+  }
 }
 
 std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std::vector<int>& pairsA,
@@ -995,6 +1091,268 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     gofx[g.x] = (int)gs.size();
     gs.push_back(g);
   }
+
+  // ---- direct sectors (U(1), B_x at most kMaxDirect x kMaxDirect): the
+  // product runs on A's and C's blocks (kernels.h, DirectItem).  Such sectors
+  // leave gs: no matrix form, GEMM, gather or scatter of their own (the dB
+  // scatter below still zero-fills their dB blocks for the atomic reduction).
+  std::set<int> dset;
+  std::vector<DirectItem> dfw, dba, dbb;
+  int rw[kMaxDim], cw[kMaxDim], st[kMaxDim];
+  if (!su2 && C.nsec() == Cn.nsec()) {
+    static const int dmax = std::min(env_int("SYM_DIRECT_MAX", kMaxDirect), kMaxDirect);
+    std::map<int, std::map<std::vector<int>, std::vector<int64_t>>> arow, crow;  // x -> row key -> sectors
+    std::map<int, std::vector<int64_t>> bsec;                                   // x -> Bm sectors
+    for (int64_t s = 0; s < Am.nsec(); ++s) arow[MA.xs[MA.sx[s]]][row_key(Am, s, na)].push_back(s);
+    for (int64_t s = 0; s < Cn.nsec(); ++s) crow[MC.xs[MC.sx[s]]][row_key(Cn, s, na)].push_back(s);
+    for (int64_t s = 0; s < Bm.nsec(); ++s) bsec[MB.xs[MB.sx[s]]].push_back(s);
+    // one column of a row group: matrix column, offset of the free origin,
+    // strides of the free legs in its block
+    struct Col {
+      int64_t idx, off;
+      std::vector<int64_t> fs;
+    };
+    // enumerate the index tuples of dims[lo..hi) (last fastest)
+    auto each = [](const std::vector<int>& dims, int lo, int hi, const std::function<void(const int*)>& fn) {
+      std::vector<int> t(dims.size(), 0);
+      int64_t tot = 1;
+      for (int n = lo; n < hi; ++n) tot *= dims[n];
+      for (int64_t e = 0; e < tot; ++e) {
+        int64_t r = e;
+        for (int n = hi - 1; n >= lo; --n) {
+          t[n] = (int)(r % dims[n]);
+          r /= dims[n];
+        }
+        fn(t.data());
+      }
+    };
+    // ld[c], sa[n], sb[n] with fs[c][n] = ld[c] sa[n] + sb[n]: one multiplier
+    // per column, the stride of the last (innermost) free leg whose stride
+    // varies between columns, covers every varying leg
+    auto fit = [](const std::vector<Col>& cols, int nf, std::vector<int64_t>& ld, std::vector<int64_t>& sa,
+                  std::vector<int64_t>& sb) {
+      ld.assign(cols.size(), 1);
+      sa.assign(nf, 0);
+      sb.assign(nf, 0);
+      int n0 = -1;
+      for (int n = 0; n < nf; ++n)
+        for (auto& c : cols)
+          if (c.fs[n] != cols[0].fs[n]) n0 = n;
+      if (n0 >= 0)
+        for (size_t c = 0; c < cols.size(); ++c) ld[c] = cols[c].fs[n0];
+      for (int n = 0; n < nf; ++n) {
+        bool same = true;
+        for (auto& c : cols) same = same && c.fs[n] == cols[0].fs[n];
+        if (same) {
+          sb[n] = cols[0].fs[n];
+          continue;
+        }
+        if (ld[0] <= 0 || cols[0].fs[n] % ld[0]) return false;
+        sa[n] = cols[0].fs[n] / ld[0];
+        for (size_t c = 0; c < cols.size(); ++c)
+          if (cols[c].fs[n] != ld[c] * sa[n]) return false;
+      }
+      for (int n = 0; n < nf; ++n)
+        if (sa[n] >= ((int64_t)1 << 31) || sb[n] >= ((int64_t)1 << 31)) return false;
+      return true;
+    };
+    auto plan_direct = [&](const G& g) -> bool {
+      const int x = g.x;
+      std::vector<int64_t> koff(g.k * g.n, 0);
+      std::vector<double> kcoef(g.k * g.n, 0.0);
+      for (int64_t sb : bsec[x]) {  // B_x[c][j] -> B offset and coefficient
+        if (XB[sb].empty()) continue;
+        if (XB[sb].size() != 1) return false;
+        const int64_t src = XB[sb][0].first;
+        group_weights(Bm, sb, nc, rw, cw);
+        block_strides(B, src, st);
+        std::vector<int> dims(Bm.rank);
+        for (int n = 0; n < Bm.rank; ++n) dims[n] = Bm.dim(sb, n);
+        each(dims, 0, Bm.rank, [&](const int* t) {
+          int64_t r = MB.r0[sb], c = MB.c0[sb], off = B.offs[src];
+          for (int n = 0; n < Bm.rank; ++n) {
+            r += (int64_t)t[n] * rw[n];
+            c += (int64_t)t[n] * cw[n];
+            off += (int64_t)t[n] * st[permB[n]];
+          }
+          koff[r * g.n + c] = off;
+          kcoef[r * g.n + c] = XB[sb][0].second;
+        });
+      }
+      std::vector<DirectItem> f, ba, bb;
+      std::vector<Term> terms;
+      std::vector<int8_t> space;
+      const int tbase = (int)P->dterms.size();
+      for (auto& rk : arow[x]) {
+        std::vector<Col> ac, cc;
+        std::vector<int> fd(na, 1);
+        for (int64_t s : rk.second) {  // A columns: contracted positions of each block
+          if (XA[s].empty()) continue;
+          if (XA[s].size() != 1 || XA[s][0].second != 1.0) return false;
+          const int64_t src = XA[s][0].first;
+          group_weights(Am, s, na, rw, cw);
+          block_strides(A, src, st);
+          std::vector<int> dims(Am.rank);
+          std::vector<int64_t> fs(na);
+          for (int n = 0; n < Am.rank; ++n) dims[n] = Am.dim(s, n);
+          for (int n = 0; n < na; ++n) {
+            fd[n] = dims[n];
+            fs[n] = st[permA[n]];
+          }
+          each(dims, na, Am.rank, [&](const int* t) {
+            int64_t c = MA.c0[s], off = A.offs[src];
+            for (int n = na; n < Am.rank; ++n) {
+              c += (int64_t)t[n] * cw[n];
+              off += (int64_t)t[n] * st[permA[n]];
+            }
+            ac.push_back(Col{c, off, fs});
+          });
+        }
+        auto ci = crow[x].find(rk.first);
+        if (ci != crow[x].end())
+          for (int64_t sn : ci->second) {  // C columns: B-free positions of each block
+            group_weights(Cn, sn, na, rw, cw);
+            block_strides(C, sn, st);
+            std::vector<int> dims(Cn.rank);
+            std::vector<int64_t> fs(na);
+            for (int n = 0; n < Cn.rank; ++n) dims[n] = Cn.dim(sn, n);
+            for (int n = 0; n < na; ++n) {
+              if (dims[n] != fd[n]) return false;
+              fs[n] = st[n];
+            }
+            const int64_t c0 = MB.coloff.at({x, col_key(Cn, sn, na)});
+            each(dims, na, Cn.rank, [&](const int* t) {
+              int64_t c = c0, off = C.offs[sn];
+              for (int n = na; n < Cn.rank; ++n) {
+                c += (int64_t)t[n] * cw[n];
+                off += (int64_t)t[n] * st[n];
+              }
+              cc.push_back(Col{c, off, fs});
+            });
+          }
+        if (ac.empty() && cc.empty()) continue;
+        if (ac.empty() || cc.empty()) return false;  // a side without columns: leave x to the general path
+        if ((int)ac.size() > kMaxDirect || (int)cc.size() > kMaxDirect) return false;
+        std::vector<int64_t> ald, asa, asb, cld, csa, csb;
+        if (!fit(ac, na, ald, asa, asb) || !fit(cc, na, cld, csa, csb)) return false;
+        Box box;
+        for (int n = 0; n < na; ++n) box.push(fd[n], (int)asa[n], (int)asb[n], (int)csa[n], (int)csb[n]);
+        box = simplify(box);
+        // peel leading dims beyond kDirectDims into offset shifts
+        std::vector<std::pair<std::vector<int64_t>, std::vector<int64_t>>> origins;
+        {
+          std::vector<int64_t> so, dof;
+          for (auto& c : ac) so.push_back(c.off);
+          for (auto& c : cc) dof.push_back(c.off);
+          origins.push_back({so, dof});
+        }
+        while (box.ndim > kDirectDims) {
+          std::vector<std::pair<std::vector<int64_t>, std::vector<int64_t>>> next;
+          for (auto& o : origins)
+            for (int i = 0; i < box.dims[0]; ++i) {
+              auto so = o.first, dof = o.second;
+              for (size_t c = 0; c < so.size(); ++c) so[c] += (int64_t)i * (ald[c] * box.sa[0] + box.sb[0]);
+              for (size_t c = 0; c < dof.size(); ++c) dof[c] += (int64_t)i * (cld[c] * box.da[0] + box.db[0]);
+              next.push_back({so, dof});
+            }
+          origins.swap(next);
+          Box b2;
+          for (int d = 1; d < box.ndim; ++d) b2.push(box.dims[d], box.sa[d], box.sb[d], box.da[d], box.db[d]);
+          box = b2;
+        }
+        int64_t total = 1, span = 0;
+        for (int d = 0; d < box.ndim; ++d) total *= box.dims[d];
+        for (int d = 0; d < box.ndim; ++d)
+          span = std::max({span, (int64_t)(box.dims[d] - 1) * box.sa[d], (int64_t)(box.dims[d] - 1) * box.sb[d],
+                           (int64_t)(box.dims[d] - 1) * box.da[d], (int64_t)(box.dims[d] - 1) * box.db[d]});
+        if (total >= ((int64_t)1 << 31) || span * kDirectDims >= ((int64_t)1 << 31)) return false;
+        const int ns = (int)ac.size(), nd = (int)cc.size();
+        for (auto& o : origins) {
+          const int ta = tbase + (int)terms.size();
+          for (int c = 0; c < ns; ++c) {
+            terms.push_back(Term{o.first[c], ald[c], 1.0, 1.0f, 0});
+            space.push_back(0);
+          }
+          const int tc = tbase + (int)terms.size();
+          for (int j = 0; j < nd; ++j) {
+            terms.push_back(Term{o.second[j], cld[j], 1.0, 1.0f, 0});
+            space.push_back(2);
+          }
+          const int tk = tbase + (int)terms.size();
+          for (int c = 0; c < ns; ++c)
+            for (int j = 0; j < nd; ++j) {
+              const int64_t e = ac[c].idx * g.n + cc[j].idx;
+              terms.push_back(Term{koff[e], 0, kcoef[e], (float)kcoef[e], 0});
+              space.push_back(1);
+            }
+          auto item = [&](int op, int ins, int ind, int ts, int td, int kd, int ks, int slots, bool swap,
+                          int64_t st0, int64_t cnt) {
+            DirectItem it{};
+            it.op = op;
+            it.ns = ins;
+            it.nd = ind;
+            it.ndim = box.ndim;
+            it.start = (int)st0;
+            it.count = (int)cnt;
+            it.ts = ts;
+            it.td = td;
+            it.tk = tk;
+            it.kd = kd;
+            it.ks = ks;
+            it.slots = slots;
+            for (int d = 0; d < kDirectDims; ++d) {
+              const bool on = d < box.ndim;
+              it.dims[d] = on ? box.dims[d] : 1;
+              it.sa[d] = on ? (swap ? box.da[d] : box.sa[d]) : 0;
+              it.sb[d] = on ? (swap ? box.db[d] : box.sb[d]) : 0;
+              it.da[d] = on ? (swap ? box.sa[d] : box.da[d]) : 0;
+              it.db[d] = on ? (swap ? box.sb[d] : box.db[d]) : 0;
+              int8_t sh;
+              div_magic(it.dims[d], it.mag[d], sh);
+              it.shf |= (int)(uint8_t)sh << (8 * d);
+            }
+            return it;
+          };
+          for (int64_t p0 = 0; p0 < total; p0 += kDirectApplyChunk) {
+            const int64_t cnt = std::min<int64_t>(kDirectApplyChunk, total - p0);
+            // C = A B: sources A (slot 0), coefficients B (slot 1), destination C
+            f.push_back(item(kDirectApply, ns, nd, ta, tc, 1, nd, 0 | (1 << 2) | (DST_OUT << 4), false, p0, cnt));
+            // dA = dC B^T: sources dC (slot 2), coefficients B, destination dA
+            ba.push_back(item(kDirectApply, nd, ns, tc, ta, nd, 1, 2 | (1 << 2) | (DST_DA << 4), true, p0, cnt));
+          }
+          for (int64_t p0 = 0; p0 < total; p0 += kDirectOuterChunk) {
+            const int64_t cnt = std::min<int64_t>(kDirectOuterChunk, total - p0);
+            // dB += A^T dC: sources A (slot 0) and dC (slot 2), sums into dB
+            bb.push_back(item(kDirectOuter, ns, nd, ta, tc, 1, nd, 0 | (2 << 2) | (DST_DB << 4), false, p0, cnt));
+          }
+        }
+      }
+      P->dterms.insert(P->dterms.end(), terms.begin(), terms.end());
+      P->dterm_space.insert(P->dterm_space.end(), space.begin(), space.end());
+      dfw.insert(dfw.end(), f.begin(), f.end());
+      dba.insert(dba.end(), ba.begin(), ba.end());
+      dbb.insert(dbb.end(), bb.begin(), bb.end());
+      return true;
+    };
+    std::vector<G> keep;
+    for (auto& g : gs) {
+      if (g.k <= dmax && g.n <= dmax && plan_direct(g)) {
+        dset.insert(g.x);
+        P->flops_fwd += 2.0 * (double)g.m * (double)g.n * (double)g.k;
+      } else {
+        keep.push_back(g);
+      }
+    }
+    gs.swap(keep);
+    gofx.clear();
+    for (size_t i = 0; i < gs.size(); ++i) gofx[gs[i].x] = (int)i;
+  }
+  P->fwd_direct = {0, (int)dfw.size()};
+  P->bwd_direct_a = {(int)dfw.size(), (int)dba.size()};
+  P->bwd_direct_b = {(int)(dfw.size() + dba.size()), (int)dbb.size()};
+  P->ditems = dfw;
+  P->ditems.insert(P->ditems.end(), dba.begin(), dba.end());
+  P->ditems.insert(P->ditems.end(), dbb.begin(), dbb.end());
   int64_t ie = 0, le = 0, oe = 0;
   auto ld64 = [](int64_t cols) { return cdiv(cols, 64) * 64; };  // rows on 128-byte lines
   // split-BF16 buffer of rows x cols bf16 in the hi plane
@@ -1020,20 +1378,25 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
       g.a = le, le += g.m * g.k;
       g.b = le, le += g.k * g.n;
     }
+    // the rows and thin kernels read the forward's linear B (dA = dC B^T) and
+    // the thin kernel its linear A (dB = A^T dC) transposed, in place of
+    // gathered transposed copies
+    const bool reuse_b = !t0 && (g.kind[1] == 3 || g.kind[1] == 4);
+    const bool reuse_a = !t0 && g.kind[2] == 3;
     if (t1) {
       g.dAa = add_op(g.tdc, g.m, g.n, 0);
       g.dAb = add_op(g.tb, g.k, g.n, 0);
-    } else {
+    } else if (!reuse_b) {
       g.bt = le, le += g.n * g.k;
     }
     if (t2) {
       g.dBa = add_op(g.ta, g.m, g.k, 1);
       g.dBb = add_op(g.tdc, g.m, g.n, 1);
-    } else {
+    } else if (!reuse_a) {
       g.at = le, le += g.k * g.m;
     }
     if (!t1 || !t2) g.dcl = le, le += g.m * g.n;
-    if (t0 && (t1 || t2)) P->bwd_reads_fwd_operands = true;
+    if ((t0 && (t1 || t2)) || reuse_a || reuse_b) P->bwd_reads_fwd_operands = true;
   }
   for (auto& g : gs) {
     g.c = oe, oe += g.m * g.n;
@@ -1053,7 +1416,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   const int nsm = 152;
   // kind 0: aoff, boff are tcgen05 operand indices; otherwise linear offsets
   auto add_gemm = [&](int kind, int ph, int64_t m, int64_t n, int64_t k, int64_t aoff, int64_t lda, int64_t boff,
-                      int64_t ldb, int64_t coff) -> bool {
+                      int64_t ldb, int64_t coff, int trans) -> bool {
     if (kind == 0) {
       const int amn = P->tc_ops[aoff].mn, bmn = P->tc_ops[boff].mn;
       P->secs_tc.push_back(
@@ -1064,11 +1427,15 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
           lists[0][ph].push_back({k, GemmTile{sec, (int)mt, (int)nt, 0, (int)k, 0}});
       return false;
     }
-    P->secs_simt.push_back(GemmSectorSimt{(int)m, (int)n, (int)k, (int)lda, (int)ldb, (int)n, aoff, boff, coff, 1.0});
+    P->secs_simt.push_back(
+        GemmSectorSimt{(int)m, (int)n, (int)k, (int)lda, (int)ldb, (int)n, aoff, boff, coff, 1.0, trans, 0});
     const int sec = (int)P->secs_simt.size() - 1;
-    if (kind == 4) {  // rows: 256 output rows per CTA, whole (short) reduction
-      for (int64_t mt = 0; mt < cdiv(m, 256); ++mt)
-        lists[4][ph].push_back({k, GemmTile{sec, (int)mt, 0, 0, (int)k, 0}});
+    if (kind == 4) {  // rows: per-warp tiles of whole rows, whole (short) reduction
+      const int64_t tr = (int64_t)kRowsSpansPerTile * rows_span((int)k);
+      for (int64_t r0 = 0; r0 < m; r0 += tr) {
+        const int64_t r1 = std::min(m, r0 + tr);
+        lists[4][ph].push_back({(r1 - r0) * (k + n), GemmTile{sec, 0, 0, (int)r0, (int)r1, 0}});
+      }
       return false;
     }
     if (kind == 3) {  // thin: one CTA per 4096-long slice of the reduction
@@ -1095,9 +1462,15 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   };
   for (auto& g : gs) {
     const bool t0 = g.kind[0] == 0, t1 = g.kind[1] == 0, t2 = g.kind[2] == 0;
-    g.split[0] = add_gemm(g.kind[0], 0, g.m, g.n, g.k, t0 ? g.fa : g.a, g.k, t0 ? g.fb : g.b, g.n, g.c);
-    g.split[1] = add_gemm(g.kind[1], 1, g.m, g.k, g.n, t1 ? g.dAa : g.dcl, g.n, t1 ? g.dAb : g.bt, g.k, g.da);
-    g.split[2] = add_gemm(g.kind[2], 2, g.k, g.n, g.m, t2 ? g.dBa : g.at, g.m, t2 ? g.dBb : g.dcl, g.n, g.db);
+    g.split[0] = add_gemm(g.kind[0], 0, g.m, g.n, g.k, t0 ? g.fa : g.a, g.k, t0 ? g.fb : g.b, g.n, g.c, 0);
+    if (t1 || g.bt >= 0)
+      g.split[1] = add_gemm(g.kind[1], 1, g.m, g.k, g.n, t1 ? g.dAa : g.dcl, g.n, t1 ? g.dAb : g.bt, g.k, g.da, 0);
+    else  // B^T read from the forward's B (k x n)
+      g.split[1] = add_gemm(g.kind[1], 1, g.m, g.k, g.n, g.dcl, g.n, g.b, g.n, g.da, kTransB);
+    if (t2 || g.at >= 0)
+      g.split[2] = add_gemm(g.kind[2], 2, g.k, g.n, g.m, t2 ? g.dBa : g.at, g.m, t2 ? g.dBb : g.dcl, g.n, g.db, 0);
+    else  // A^T read from the forward's A (m x k)
+      g.split[2] = add_gemm(g.kind[2], 2, g.k, g.n, g.m, g.a, g.k, g.dcl, g.n, g.db, kTransA);
   }
   for (int kind = 0; kind < kGemmKinds; ++kind)
     for (int ph = 0; ph < 3; ++ph) {
@@ -1110,7 +1483,6 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
       }
     }
 
-  int rw[kMaxDim], cw[kMaxDim], st[kMaxDim];
   std::vector<int> pinvA(A.rank), pinvB(B.rank);
   for (int n = 0; n < A.rank; ++n) pinvA[permA[n]] = n;
   for (int n = 0; n < B.rank; ++n) pinvB[permB[n]] = n;
@@ -1247,6 +1619,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   };
   begin = (int)P->items.size();
   for (int64_t s = 0; s < C.nsec(); ++s) {
+    if (natural && dset.count(MC.xs[MC.sx[s]])) continue;  // written by the direct kernel
     std::vector<Term> t;
     if (natural) {
       cn_term(s, 1.0, t);
@@ -1291,7 +1664,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
       if (g.kind[0] == 0) continue;
       Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, false);
       put_tc(b, 1, g.tb, g.n, MB.r0[s], MB.c0[s], terms_of(XB[s], B));
-    } else {  // B^T (n x k)
+    } else if (g.bt >= 0) {  // B^T (n x k), unless the GEMM reads the forward's B
       Box b = gather_box(B, pinvB, Bm, s, XB[s][0].first, nc, true);
       put(b, 1, g.bt, MB.c0[s], MB.r0[s], g.k, terms_of(XB[s], B));
     }
@@ -1315,7 +1688,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
       if (g.kind[0] == 0) continue;
       Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, false);
       put_tc(b, 0, g.ta, g.k, MA.r0[s], MA.c0[s], terms_of(XA[s], A));
-    } else {  // A^T (k x m)
+    } else if (g.at >= 0) {  // A^T (k x m), unless the GEMM reads the forward's A
       Box b = gather_box(A, pinvA, Am, s, XA[s][0].first, na, true);
       put(b, 0, g.at, MA.c0[s], MA.r0[s], g.m, terms_of(XA[s], A));
     }
@@ -1352,6 +1725,9 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
       doneDA);
   for (int64_t s = 0; s < A.nsec(); ++s) {
     if (doneDA[s]) continue;
+    bool direct = false;  // dA written by the direct kernel
+    for (auto& pc : XAt[s]) direct = direct || dset.count(MA.xs[MA.sx[pc.first]]) > 0;
+    if (direct) continue;
     std::vector<Term> t;
     int64_t sm0 = -1;
     for (auto& pc : XAt[s]) {
@@ -1404,6 +1780,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     P->validate(src, dst);
   }
   validate_gemms(*P, f64);
+  validate_direct(*P);
   P->upload(device);
   return P;
 }
@@ -1522,6 +1899,37 @@ std::unique_ptr<Plan> merge_contract_plans(std::vector<std::unique_ptr<Plan>>& p
   M->bwd_gather_b = {rs.first, rs.count + rb.count};
   M->bwd_scatter_a = concat([](const Plan& p) { return p.bwd_scatter_a; });
   M->bwd_scatter_b = concat([](const Plan& p) { return p.bwd_scatter_b; });
+  // direct items: each problem's terms shifted into the packed tensors
+  {
+    std::vector<int> dt0(n);
+    for (int i = 0; i < n; ++i) {
+      const Plan& p = *ps[i];
+      dt0[i] = (int)M->dterms.size();
+      const int64_t shift[3] = {offA[i], offB[i], offC[i]};
+      for (size_t t = 0; t < p.dterms.size(); ++t) {
+        Term x = p.dterms[t];
+        x.off += shift[p.dterm_space[t]];
+        M->dterms.push_back(x);
+        M->dterm_space.push_back(p.dterm_space[t]);
+      }
+    }
+    Range* dst[3] = {&M->fwd_direct, &M->bwd_direct_a, &M->bwd_direct_b};
+    for (int r = 0; r < 3; ++r) {
+      const int first = (int)M->ditems.size();
+      for (int i = 0; i < n; ++i) {
+        const Plan& p = *ps[i];
+        const Range src = r == 0 ? p.fwd_direct : r == 1 ? p.bwd_direct_a : p.bwd_direct_b;
+        for (int k = src.first; k < src.first + src.count; ++k) {
+          DirectItem it = p.ditems[k];
+          it.ts += dt0[i];
+          it.td += dt0[i];
+          it.tk += dt0[i];
+          M->ditems.push_back(it);
+        }
+      }
+      *dst[r] = Range{first, (int)M->ditems.size() - first};
+    }
+  }
   // GEMM tiles per (kind, phase), longest reductions first across problems
   for (int kind = 0; kind < kGemmKinds; ++kind)
     for (int ph = 0; ph < 3; ++ph) {
@@ -1549,6 +1957,7 @@ std::unique_ptr<Plan> merge_contract_plans(std::vector<std::unique_ptr<Plan>>& p
     M->validate(src, dst);
   }
   validate_gemms(*M, f64);
+  validate_direct(*M);
   M->upload(device);
   return M;
 }
@@ -1605,13 +2014,23 @@ int run_box(Plan& p, Range r, const BoxPtrs& ptrs, void* stream, int phase) {
                    "box kernel");
 }
 
+int run_direct(Plan& p, Range r, const BoxPtrs& ptrs, void* stream, int phase) {
+  if (r.count <= 0) return SYM_OK;
+  p.last_launches++;
+  ProfScope ps(p, phase, SYM_KERNEL_DIRECT, stream,
+               p.ditem_bytes_prefix[r.first + r.count] - p.ditem_bytes_prefix[r.first],
+               p.ditem_flops_prefix[r.first + r.count] - p.ditem_flops_prefix[r.first]);
+  return cuda_code(launch_direct(p.f64(), p.d_ditems + r.first, r.count, p.d_dterms, ptrs, stream), "direct kernel");
+}
+
 int run_gemm_kind(Plan& p, int kind, Range r, void* stream, int phase) {
   if (r.count <= 0) return SYM_OK;
   p.last_launches++;
   if (kind != 0) phase = phase == PH_FWD_GEMM ? PH_FWD_GEMM_SIMT : PH_BWD_GEMM_SIMT;
   static const int kernel_of_kind[kGemmKinds] = {SYM_KERNEL_GEMM_TC, SYM_KERNEL_GEMM_TILE, SYM_KERNEL_GEMM_WIDE,
                                                  SYM_KERNEL_GEMM_THIN, SYM_KERNEL_GEMM_ROWS};
-  ProfScope ps(p, phase, kernel_of_kind[kind], stream, 0.0,
+  ProfScope ps(p, phase, kernel_of_kind[kind], stream,
+               p.tile_bytes_prefix[r.first + r.count] - p.tile_bytes_prefix[r.first],
                p.tile_flops_prefix[r.first + r.count] - p.tile_flops_prefix[r.first]);
   if (kind == 0)
     return cuda_code(launch_gemm_tc(p.d_secs_tc, p.d_tiles + r.first, r.count, p.d_maps,
@@ -1718,7 +2137,13 @@ int exec_contract(Plan& p, const void* A, const void* B, void* C, void* stream) 
   BoxPtrs s{};
   s.src[3] = p.outm;
   s.dst[DST_OUT] = C;
-  return run_box(p, p.fwd_scatter, s, stream, PH_FWD_SCATTER);
+  rc = run_box(p, p.fwd_scatter, s, stream, PH_FWD_SCATTER);
+  if (rc) return rc;
+  BoxPtrs d{};
+  d.src[0] = A;
+  d.src[1] = B;
+  d.dst[DST_OUT] = C;
+  return run_direct(p, p.fwd_direct, d, stream, PH_FWD_DIRECT);
 }
 
 int exec_contract_backward(Plan& p, const void* A, const void* B, const void* dC, void* dA, void* dB,
@@ -1754,7 +2179,21 @@ int exec_contract_backward(Plan& p, const void* A, const void* B, const void* dC
     sr = {p.bwd_scatter_a.first, p.bwd_scatter_a.count + p.bwd_scatter_b.count};
   else
     sr = dA ? p.bwd_scatter_a : p.bwd_scatter_b;
-  return run_box(p, sr, s, stream, PH_BWD_SCATTER);
+  rc = run_box(p, sr, s, stream, PH_BWD_SCATTER);
+  if (rc) return rc;
+  // after the scatter, which zero-filled the dB blocks the direct sums add into
+  BoxPtrs d{};
+  d.src[0] = A;
+  d.src[1] = B;
+  d.src[2] = dC;
+  d.dst[DST_DA] = dA;
+  d.dst[DST_DB] = dB;
+  Range dr;
+  if (dA && dB)
+    dr = {p.bwd_direct_a.first, p.bwd_direct_a.count + p.bwd_direct_b.count};
+  else
+    dr = dA ? p.bwd_direct_a : p.bwd_direct_b;
+  return run_direct(p, dr, d, stream, PH_BWD_DIRECT);
 }
 
 }  // namespace sym

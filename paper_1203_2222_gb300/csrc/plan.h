@@ -22,7 +22,7 @@ struct DeviceArena {
 
 // Phases of a plan's launches (profiling and statistics).
 enum Phase { PH_FWD_GATHER = 0, PH_FWD_GEMM, PH_FWD_SCATTER, PH_BWD_GATHER, PH_BWD_GEMM, PH_BWD_SCATTER,
-             PH_XFORM, PH_FWD_GEMM_SIMT, PH_BWD_GEMM_SIMT, PH_COUNT };
+             PH_XFORM, PH_FWD_GEMM_SIMT, PH_BWD_GEMM_SIMT, PH_FWD_DIRECT, PH_BWD_DIRECT, PH_COUNT };
 constexpr int kGemmKinds = 5;  // 0 tcgen05, CUDA cores: 1 tile 64x64, 2 tile 256x16, 3 thin, 4 rows
 
 // One recorded launch: cudaEvent_t pair around it, kernel (SYM_KERNEL_*),
@@ -53,6 +53,15 @@ struct Plan {
   Range bwd_gather_a, bwd_gather_b;   // backward gathers needed for dA / dB
   Range bwd_scatter_a, bwd_scatter_b;
 
+  // direct-contraction work lists (sectors with a tiny matrix on one side,
+  // see kernels.h); dterm_space[i] says which tensor term i's offset points
+  // into: 0 = A (or dA), 1 = B (or dB), 2 = C (or dC)
+  std::vector<DirectItem> ditems;
+  std::vector<Term> dterms;
+  std::vector<int8_t> dterm_space;
+  Range fwd_direct, bwd_direct_a, bwd_direct_b;  // C = A B; dA = dC B^T; dB += A^T dC
+  std::vector<double> ditem_bytes_prefix, ditem_flops_prefix;  // launch statistics
+
   // GEMM work lists.  Kinds: 0 = tcgen05 split-BF16 x3, 1 = CUDA-core 64x64,
   // 2 = CUDA-core 256x16, 3 = CUDA-core thin (m, n <= 8), 4 = CUDA-core
   // rows (k, n <= 16); GEMM phases:
@@ -78,7 +87,7 @@ struct Plan {
 
   // algorithmic bytes of every box item and useful flops of every tile,
   // as prefix sums (launch statistics for any range in O(1))
-  std::vector<double> item_bytes_prefix, tile_flops_prefix;
+  std::vector<double> item_bytes_prefix, tile_flops_prefix, tile_bytes_prefix;
   std::vector<int> flat_prefix;  // flat linear items among the first i (launch variant choice)
   void set_item_bytes(Range r, int es_src, int es_dst);
   bool profiling = false;
@@ -90,6 +99,8 @@ struct Plan {
   DeviceArena arena;
   BoxItem* d_items = nullptr;
   Term* d_terms = nullptr;
+  DirectItem* d_ditems = nullptr;
+  Term* d_dterms = nullptr;
   GemmSectorSimt* d_secs_simt = nullptr;
   TcSector* d_secs_tc = nullptr;
   GemmTile* d_tiles = nullptr;

@@ -3,7 +3,9 @@
 The split-BF16 path picks, per sector, the tcgen05 tensor-core GEMM or the
 exact-FP32 CUDA-core GEMM (SYM_TC_MIN_MN / SYM_TC_MIN_K / SYM_TC_MAX_K
 thresholds).  Running the parity tests with all sectors on the tensor cores,
-and with all on the CUDA cores, covers both kernels on every case."""
+and with all on the CUDA cores, covers both kernels on every case; with
+SYM_DIRECT_MAX=0 the sectors the direct kernel takes (B's matrix at most
+4 x 4) go through the matrix form and the GEMM kernels instead."""
 import os
 import subprocess
 import sys
@@ -17,6 +19,7 @@ pytestmark = pytest.mark.gpu
 FORCED = {
     "all_tensor_cores": {"SYM_TC_MIN_MN": "1", "SYM_TC_MIN_K": "1", "SYM_TC_MAX_K": "100000000"},
     "all_cuda_cores": {"SYM_TC_MIN_MN": "1000000000"},
+    "no_direct_sectors": {"SYM_DIRECT_MAX": "0"},
 }
 
 

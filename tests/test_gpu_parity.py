@@ -133,6 +133,42 @@ def test_u1_edge_cases(dtype):
     _contract_case("u1", la, [([-1, 0, 1], [2, 1, 3], 1)], [], [], dtype, QB=1)
 
 
+# Sectors whose matrix of B is at most 4 x 4 are contracted directly on the
+# blocks (no matrix form); the cases below put every sector there.
+MPO = ([-1, 0, 1], [1, 3, 1])
+PHYS = ([0, 1], [1, 1])
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
+def test_u1_mpo_step_direct(dtype):
+    # T[a, w, s, b] . W[w, s, s', w'] over (w, s): contracted legs in the middle
+    # of T, free-leg strides that vary with the MPO charge on both sides
+    qs = [-2, -1, 0, 1, 2]
+    bond_in, bond_out = (qs, [7, 19, 33, 21, 5], -1), (qs, [6, 17, 40, 23, 9], 1)
+    la = [bond_in, (*MPO, -1), (*PHYS, -1), bond_out]
+    lb = [(*MPO, 1), (*PHYS, -1), (*PHYS, 1), (*MPO, -1)]
+    _contract_case("u1", la, lb, [1, 2], [0, 2], dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
+def test_u1_mpo_split_contracted_legs_direct(dtype):
+    # T[a, s2, b, s1, w] . W[w, s, s', w'] over T(1, 4) <-> W(2, 0): the
+    # contracted legs sit on both sides of free legs
+    qs = [-2, -1, 0, 1, 2]
+    la = [(qs, [4, 11, 20, 9, 3], -1), (*PHYS, -1), (qs, [5, 13, 17, 12, 6], 1), (*PHYS, 1), (*MPO, 1)]
+    lb = [(*MPO, -1), (*PHYS, 1), (*PHYS, 1), (*MPO, 1)]
+    _contract_case("u1", la, lb, [1, 4], [2, 0], dtype, QA=1)
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
+def test_u1_tiny_b_with_missing_blocks_direct(dtype):
+    # B's sector matrices have structurally absent blocks (total charge 1 and a
+    # leg without every charge), m large with a ragged box, k = n = 1 sectors
+    la = [([-1, 0, 1, 2], [37, 64, 129, 3], 1), ([-1, 0, 1], [1, 2, 1], -1)]
+    lb = [([-1, 0, 1], [1, 2, 1], 1), ([0, 2], [1, 2], 1)]
+    _contract_case("u1", la, lb, [1], [0], dtype, QB=1)
+
+
 SU2_TREES = [None, [(1, 2), (0, 4), (5, 3)], [(0, 1), (2, 3), (4, 5)]]
 
 

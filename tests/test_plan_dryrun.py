@@ -44,6 +44,27 @@ t1 = P.contract_plan(Ls[0], Ls[1], [2], [0], P.BF16X3)
 t2 = P.contract_plan(t1.out, Ls[2], [1, 2], [0, 2], P.BF16X3)
 t3 = P.contract_plan(t2.out, Ls[3], [1, 3], [2, 1], P.BF16X3)
 print("MPS flops", t1.stats()["flops_fwd"] + t2.stats()["flops_fwd"] + t3.stats()["flops_fwd"])
+# the MPO step: every sector has B's matrix at most 4 x 4 and is contracted
+# directly on the blocks, unless SYM_DIRECT_MAX=0 sends it through the GEMMs
+import os
+direct = os.environ.get("SYM_DIRECT_MAX") != "0"
+assert (len(t2.gemm_shapes()) == 0) == direct, len(t2.gemm_shapes())
+assert len(t1.gemm_shapes()) > 0 and len(t3.gemm_shapes()) > 0
+bond_in, bond_out = (T.MPO[0], T.MPO[1], -1), (T.MPO[0], T.MPO[1], 1)
+qs5 = [-2, -1, 0, 1, 2]
+plan("u1", [(qs5, [7, 19, 33, 21, 5], -1), (*T.MPO, -1), (*T.PHYS, -1), (qs5, [6, 17, 40, 23, 9], 1)],
+     [(*T.MPO, 1), (*T.PHYS, -1), (*T.PHYS, 1), (*T.MPO, -1)], [1, 2], [0, 2])
+plan("u1", [(qs5, [4, 11, 20, 9, 3], -1), (*T.PHYS, -1), (qs5, [5, 13, 17, 12, 6], 1), (*T.PHYS, 1), (*T.MPO, 1)],
+     [(*T.MPO, -1), (*T.PHYS, 1), (*T.PHYS, 1), (*T.MPO, 1)], [1, 4], [2, 0], QA=1)
+plan("u1", [([-1, 0, 1, 2], [37, 64, 129, 3], 1), ([-1, 0, 1], [1, 2, 1], -1)],
+     [([-1, 0, 1], [1, 2, 1], 1), ([0, 2], [1, 2], 1)], [1], [0], QB=1)
+b5 = synthetic.u1_two_site_batch(n=6, seed=7, dmin=40, dmax=90, qmax=4)
+pr = b5["problems"]
+S5 = {n: [P.Structure(P.U1, q[n]) for q in pr] for n in ("L", "theta", "W", "R")}
+cur = S5["L"]
+for an, bn, pa, pb in b5["steps"]:
+    bp = P.contract_batch_plan(cur if an is None else S5[an], S5[bn], pa, pb, P.BF16X3)
+    cur = bp.outs
 # transforms
 U = P.Structure(P.U1, [(qs, [2, 3, 1], 1), (qs, [1, 2, 2], 1), (qs, [3, 1, 2], -1)])
 P.permute_plan(U, [2, 0, 1]); f = P.fuse_plan(U, 0); P.split_plan(f.out, 0, [U.legs[0], U.legs[1]])
@@ -57,8 +78,15 @@ print("DRYRUN OK")
 '''
 
 
-def test_all_plans_bounds_check_on_host():
+import pytest  # noqa: E402
+
+
+@pytest.mark.parametrize("direct", ["default", "off"])
+def test_all_plans_bounds_check_on_host(direct):
     env = dict(os.environ, SYM_PLAN_DRYRUN="1", PYTHONPATH=ROOT)
+    env.pop("SYM_DIRECT_MAX", None)
+    if direct == "off":
+        env["SYM_DIRECT_MAX"] = "0"
     r = subprocess.run([sys.executable, "-c", SCRIPT], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
