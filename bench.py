@@ -54,6 +54,13 @@ def parse():
     ap.add_argument("--cpu-sample-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying a CUDA graph")
+    ap.add_argument("--tune", choices=["table", "search", "off"], default="table",
+                    help="planning parameters: the autotuned table entry for this device and workload (default; "
+                         "the library defaults when there is none), a new autotuner search (stored in "
+                         "--tune-table), or the library defaults")
+    ap.add_argument("--tune-table", default=None, help="autotuner table (default paper_1203_2222_gb300/tuned.json)")
+    ap.add_argument("--tune-space", default=None,
+                    help="comma-separated planning parameters the search varies (default: all of autotune.SPACE)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     args.steps = wl.default_steps if args.steps is None else args.steps
@@ -494,12 +501,33 @@ def run_ours(args, rank, world):
     if args.workload == "su2_recouple":
         wl.dmax = args.su2_dmax
 
+    # ---- planning parameters (autotuned table entry, search, or defaults)
+    from paper_1203_2222_gb300 import autotune
+    table = args.tune_table or autotune.TABLE
+    tuning = {"source": "library defaults", "params": P.tune_get()}
+    if args.tune == "table":
+        params = autotune.load(args.workload, table)
+        if params:
+            tuning = {"source": "autotuned table", "params": P.tune_set(**params)}
+
     # ---- split-BF16 x3 path (the value); the first contraction builds the plans
     wl.build(P, dev)
     data, G = wl.data, wl.G
 
     def run_once(dt, Gt):
         return wl.step(P, dt, Gt)
+
+    if args.tune == "search":
+        t0 = time.time()
+        space = autotune.SPACE if not args.tune_space else {k: autotune.SPACE[k] for k in args.tune_space.split(",")}
+        params, ms_t, hist = autotune.tune(lambda: run_once(data, G), space=space, graph=not args.no_graph,
+                                           log=lambda m: print("# " + m, file=sys.stderr, flush=True))
+        autotune.save(args.workload, params, ms_t, hist[0]["ms"], len(hist), path=table)
+        tuning = {"source": "autotuner search", "params": params, "evaluations": len(hist),
+                  "ms_per_step_defaults": hist[0]["ms"], "ms_per_step_tuned": round(ms_t, 5),
+                  "search_s": round(time.time() - t0, 1), "table": os.path.relpath(table, ROOT)}
+        run_once(data, G)  # plans under the installed parameters (the search's last change dropped the old ones)
+        torch.cuda.synchronize()
 
     if hasattr(wl, "flops_and_bytes"):
         flops, alg_bytes = wl.flops_and_bytes(P, P.BF16X3)
@@ -720,6 +748,7 @@ def run_ours(args, rank, world):
         "e2e": {"value": round(e2e_value, 4), "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e, 4)},
         "clocks": clk, "gpu_launches": launches_per_step * args.steps,
+        "tuning": tuning,
     }
     return out, flops
 

@@ -237,6 +237,33 @@ int sym_plan_profile_read(sym_plan plan, int phase, int* launches,
 int sym_plan_profile_kernel(sym_plan plan, int kernel, int* launches,
                             double* total_ms, double* bytes, double* flops);
 
+/* Planning parameters: the kernel choice per GEMM shape and the schedule of
+ * the grouped launches.  Every plan built after sym_tune_set uses them (plans
+ * already built keep theirs); sym_tune_epoch counts the sym_tune_set calls,
+ * so a caller that caches plans can tell when to rebuild them.  Defaults
+ * (SYM_TC_MIN_MN, SYM_TC_MIN_K, SYM_TC_MAX_K and SYM_DIRECT_MAX in the
+ * environment override the first four at load):
+ *   tc_min_mn 64, tc_min_k 48, tc_max_k 16384: a GEMM (m x n, reduction k)
+ *     runs on the tensor cores when m, n >= tc_min_mn and tc_min_k <= k <=
+ *     tc_max_k (and m, n > 8, not k, n <= 16), else on the CUDA cores;
+ *   direct_max 4 (0..4): U(1) sectors whose B matrix is at most direct_max
+ *     square are contracted directly on the blocks;
+ *   direct_chunk 1024 (multiple of 32): positions per direct work item;
+ *   rows_spans 8 (1..64): rows kernel, row runs per warp tile;
+ *   splitk_ctas 2 (0..64): CUDA-core tile GEMMs split their reductions until
+ *     a launch has splitk_ctas CTAs per SM (0: never split);
+ *   thin_slice 4096 (multiple of 256): thin GEMMs, reduction per CTA;
+ *   tc_order 0: tcgen05 tiles longest reduction first; 1: in sector order.
+ * sym_tune_set rejects a value out of range with SYM_ERR_ARG.             */
+typedef struct {
+  int tc_min_mn, tc_min_k, tc_max_k;
+  int direct_max, direct_chunk;
+  int rows_spans, splitk_ctas, thin_slice, tc_order;
+} sym_tune;
+int sym_tune_get(sym_tune* out);
+int sym_tune_set(const sym_tune* in);
+int sym_tune_epoch(int* epoch);
+
 /* Number of kernel launches the last execution call on this plan issued. */
 int sym_plan_launches(sym_plan plan, int* launches);
 

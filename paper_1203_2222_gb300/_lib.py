@@ -41,6 +41,14 @@ class sym_leg(ctypes.Structure):
                 ("degens", ctypes.POINTER(ctypes.c_int)), ("dir", ctypes.c_int)]
 
 
+TUNE_FIELDS = ("tc_min_mn", "tc_min_k", "tc_max_k", "direct_max", "direct_chunk", "rows_spans", "splitk_ctas",
+               "thin_slice", "tc_order")
+
+
+class sym_tune(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int) for f in TUNE_FIELDS]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_1203_2222_gb300/build.py` "
                       "(or __graft_entry__.build())")
@@ -82,6 +90,9 @@ _SIGS = {
     "sym_su2_F": ([_I, _I, _I, _I, _I, _I, _DP], _I),
     "sym_contract_noalloc": ([_P, _P, _I, _IP, _IP, _I, _P, _P, _P, _P], _I),
     "sym_su2_gamma": ([_I, _IP, _IP, _IP, _IP, _IP, _IP, _DP, _IP, _IP], _I),
+    "sym_tune_get": ([ctypes.POINTER(sym_tune)], _I),
+    "sym_tune_set": ([ctypes.POINTER(sym_tune)], _I),
+    "sym_tune_epoch": ([_IP], _I),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(lib, _name)

@@ -400,6 +400,30 @@ int sym_plan_profile_kernel(sym_plan plan, int kernel, int* launches, double* to
   });
 }
 
+int sym_tune_get(sym_tune* out) {
+  return guard([&] {
+    need(out != nullptr, "NULL argument");
+    *out = sym::current_tune();
+    return SYM_OK;
+  });
+}
+
+int sym_tune_set(const sym_tune* in) {
+  return guard([&] {
+    need(in != nullptr, "NULL argument");
+    sym::set_tune(*in);
+    return SYM_OK;
+  });
+}
+
+int sym_tune_epoch(int* epoch) {
+  return guard([&] {
+    need(epoch != nullptr, "NULL argument");
+    *epoch = sym::tune_epoch();
+    return SYM_OK;
+  });
+}
+
 int sym_plan_gemm_shapes(sym_plan plan, int* nsec, int* mnk) {
   return guard([&] {
     need(plan && plan->p && nsec, "NULL argument");

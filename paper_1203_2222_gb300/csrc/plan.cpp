@@ -34,6 +34,7 @@
 #include <cstdlib>
 #include <mutex>
 #include <set>
+#include <string>
 
 #include "../../include/symtensor.h"
 #include "recouple.h"
@@ -857,25 +858,93 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
 // ----------------------------------------------------------------- contraction --
 namespace {
 
-// Kernel choice of one GEMM (m x n result, reduction k) of a split-BF16 plan:
-// the tensor cores when the 128 x 128 x 64 tile is well filled, the exact
-// FP32 CUDA-core kernel otherwise (thin matrices are bandwidth-bound, and
-// very long reductions are split across CTAs there).  Thresholds can be
-// overridden with SYM_TC_MIN_MN / SYM_TC_MIN_K / SYM_TC_MAX_K.
 int env_int(const char* name, int dflt) {
   const char* v = std::getenv(name);
   return v && *v ? std::atoi(v) : dflt;
 }
 
-int choose_kind(bool f64, int64_t m, int64_t n, int64_t k) {
+}  // namespace
+
+// ------------------------------------------------------ planning parameters --
+// Read by every plan built afterwards (plans already built keep theirs).
+// Defaults, then SYM_* environment variables, then sym_tune_set.
+namespace {
+std::mutex tune_mu;
+int tune_ver = 0;
+sym_tune& tune_state() {
+  static sym_tune t = [] {
+    sym_tune d;
+    d.tc_min_mn = env_int("SYM_TC_MIN_MN", 64);
+    d.tc_min_k = env_int("SYM_TC_MIN_K", 48);
+    d.tc_max_k = env_int("SYM_TC_MAX_K", 16384);
+    d.direct_max = std::max(0, std::min(env_int("SYM_DIRECT_MAX", kMaxDirect), kMaxDirect));
+    d.direct_chunk = kDirectApplyChunk;
+    d.rows_spans = kRowsSpansPerTile;
+    d.splitk_ctas = 2;
+    d.thin_slice = 4096;
+    d.tc_order = 0;
+    // SYM_TUNE="name=value,...": any parameter (names as in sym_tune)
+    if (const char* e = std::getenv("SYM_TUNE")) {
+      std::string all(e);
+      size_t p = 0;
+      while (p < all.size()) {
+        size_t q = all.find(',', p);
+        if (q == std::string::npos) q = all.size();
+        const std::string kv = all.substr(p, q - p);
+        const size_t eq = kv.find('=');
+        if (eq != std::string::npos) {
+          const std::string k = kv.substr(0, eq);
+          const int v = std::atoi(kv.c_str() + eq + 1);
+          int* f = k == "tc_min_mn" ? &d.tc_min_mn : k == "tc_min_k" ? &d.tc_min_k : k == "tc_max_k" ? &d.tc_max_k
+                 : k == "direct_max" ? &d.direct_max : k == "direct_chunk" ? &d.direct_chunk
+                 : k == "rows_spans" ? &d.rows_spans : k == "splitk_ctas" ? &d.splitk_ctas
+                 : k == "thin_slice" ? &d.thin_slice : k == "tc_order" ? &d.tc_order : nullptr;
+          if (f) *f = v;
+        }
+        p = q + 1;
+      }
+    }
+    return d;
+  }();
+  return t;
+}
+}  // namespace
+
+sym_tune current_tune() {
+  std::lock_guard<std::mutex> g(tune_mu);
+  return tune_state();
+}
+
+void set_tune(const sym_tune& t) {
+  auto in = [](int v, int lo, int hi) { return v >= lo && v <= hi; };
+  if (!in(t.tc_min_mn, 1, 1 << 30) || !in(t.tc_min_k, 1, 1 << 30) || !in(t.tc_max_k, t.tc_min_k, 1 << 30) ||
+      !in(t.direct_max, 0, kMaxDirect) || !in(t.direct_chunk, 32, 1 << 16) || t.direct_chunk % 32 ||
+      !in(t.rows_spans, 1, 64) || !in(t.splitk_ctas, 0, 64) || !in(t.thin_slice, 256, 1 << 20) ||
+      t.thin_slice % 256 || !in(t.tc_order, 0, 1))
+    fail(SYM_ERR_ARG, "planning parameter out of range");
+  std::lock_guard<std::mutex> g(tune_mu);
+  tune_state() = t;
+  ++tune_ver;
+}
+
+int tune_epoch() {
+  std::lock_guard<std::mutex> g(tune_mu);
+  return tune_ver;
+}
+
+namespace {
+
+// Kernel choice of one GEMM (m x n result, reduction k) of a split-BF16 plan:
+// the tensor cores when the 128 x 128 x 64 tile is well filled, the exact
+// FP32 CUDA-core kernel otherwise (thin matrices are bandwidth-bound, and
+// very long reductions are split across CTAs there).  The thresholds and
+// the schedule parameters are the planning parameters below.
+int choose_kind(bool f64, int64_t m, int64_t n, int64_t k, const sym_tune& t) {
   if (m <= 8 && n <= 8) return 3;
   if (k <= 16 && n <= 16) return 4;
   const int simt = n <= 16 ? 2 : 1;
   if (f64) return simt;
-  static const int min_mn = env_int("SYM_TC_MIN_MN", 64);
-  static const int min_k = env_int("SYM_TC_MIN_K", 48);
-  static const int max_k = env_int("SYM_TC_MAX_K", 16384);
-  if (m >= min_mn && n >= min_mn && k >= min_k && k <= max_k) return 0;
+  if (m >= t.tc_min_mn && n >= t.tc_min_mn && k >= t.tc_min_k && k <= t.tc_max_k) return 0;
   return simt;
 }
 
@@ -990,6 +1059,8 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   P->kind = Plan::CONTRACT;
   P->precision = precision;
   const bool f64 = precision == SYM_PREC_FP64;
+  const sym_tune tp = current_tune();
+  P->tc_order = tp.tc_order;
   const int nc = (int)pairsA.size();
   std::vector<int> freeA, freeB;
   for (int l = 0; l < A.rank; ++l)
@@ -1085,9 +1156,9 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     if (g.m <= 0 || g.n <= 0 || g.k <= 0) continue;
     if (g.m >= ((int64_t)1 << 31) || g.n >= ((int64_t)1 << 31) || g.k >= ((int64_t)1 << 31))
       fail(SYM_ERR_UNSUPPORTED, "sector matrix dimension too large");
-    g.kind[0] = choose_kind(f64, g.m, g.n, g.k);
-    g.kind[1] = choose_kind(f64, g.m, g.k, g.n);
-    g.kind[2] = choose_kind(f64, g.k, g.n, g.m);
+    g.kind[0] = choose_kind(f64, g.m, g.n, g.k, tp);
+    g.kind[1] = choose_kind(f64, g.m, g.k, g.n, tp);
+    g.kind[2] = choose_kind(f64, g.k, g.n, g.m, tp);
     gofx[g.x] = (int)gs.size();
     gs.push_back(g);
   }
@@ -1100,7 +1171,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   std::vector<DirectItem> dfw, dba, dbb;
   int rw[kMaxDim], cw[kMaxDim], st[kMaxDim];
   if (!su2 && C.nsec() == Cn.nsec()) {
-    static const int dmax = std::min(env_int("SYM_DIRECT_MAX", kMaxDirect), kMaxDirect);
+    const int dmax = tp.direct_max;
     std::map<int, std::map<std::vector<int>, std::vector<int64_t>>> arow, crow;  // x -> row key -> sectors
     std::map<int, std::vector<int64_t>> bsec;                                   // x -> Bm sectors
     for (int64_t s = 0; s < Am.nsec(); ++s) arow[MA.xs[MA.sx[s]]][row_key(Am, s, na)].push_back(s);
@@ -1313,8 +1384,8 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
             }
             return it;
           };
-          for (int64_t p0 = 0; p0 < total; p0 += kDirectApplyChunk) {
-            const int64_t cnt = std::min<int64_t>(kDirectApplyChunk, total - p0);
+          for (int64_t p0 = 0; p0 < total; p0 += tp.direct_chunk) {
+            const int64_t cnt = std::min<int64_t>(tp.direct_chunk, total - p0);
             // C = A B: sources A (slot 0), coefficients B (slot 1), destination C
             f.push_back(item(kDirectApply, ns, nd, ta, tc, 1, nd, 0 | (1 << 2) | (DST_OUT << 4), false, p0, cnt));
             // dA = dC B^T: sources dC (slot 2), coefficients B, destination dA
@@ -1431,7 +1502,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
         GemmSectorSimt{(int)m, (int)n, (int)k, (int)lda, (int)ldb, (int)n, aoff, boff, coff, 1.0, trans, 0});
     const int sec = (int)P->secs_simt.size() - 1;
     if (kind == 4) {  // rows: per-warp tiles of whole rows, whole (short) reduction
-      const int64_t tr = (int64_t)kRowsSpansPerTile * rows_span((int)k);
+      const int64_t tr = (int64_t)tp.rows_spans * rows_span((int)k);
       for (int64_t r0 = 0; r0 < m; r0 += tr) {
         const int64_t r1 = std::min(m, r0 + tr);
         lists[4][ph].push_back({(r1 - r0) * (k + n), GemmTile{sec, 0, 0, (int)r0, (int)r1, 0}});
@@ -1439,7 +1510,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
       return false;
     }
     if (kind == 3) {  // thin: one CTA per 4096-long slice of the reduction
-      const int64_t kc = 4096, nsplit = cdiv(k, kc);
+      const int64_t kc = tp.thin_slice, nsplit = cdiv(k, kc);
       for (int64_t sp = 0; sp < nsplit; ++sp) {
         const int64_t k0 = sp * kc, k1 = std::min(k, k0 + kc);
         lists[3][ph].push_back({k1 - k0, GemmTile{sec, 0, 0, (int)k0, (int)k1, nsplit > 1 ? 1 : 0}});
@@ -1449,7 +1520,8 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     const int64_t TM = kind == 1 ? 64 : 256, TN = kind == 1 ? 64 : 16;
     const int64_t ntl = cdiv(m, TM) * cdiv(n, TN);
     int64_t nsplit = 1;
-    if (k >= 256 && ntl < 2 * nsm) nsplit = std::min<int64_t>(cdiv(k, 128), cdiv(2 * nsm, ntl));
+    const int64_t want = (int64_t)tp.splitk_ctas * nsm;  // CTAs a launch should reach by splitting k
+    if (k >= 256 && ntl < want) nsplit = std::min<int64_t>(cdiv(k, 128), cdiv(want, ntl));
     const int64_t kc = cdiv(cdiv(k, nsplit), 32) * 32;
     nsplit = cdiv(k, kc);
     for (int64_t mt = 0; mt < cdiv(m, TM); ++mt)
@@ -1475,7 +1547,8 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   for (int kind = 0; kind < kGemmKinds; ++kind)
     for (int ph = 0; ph < 3; ++ph) {
       auto& v = lists[kind][ph];
-      std::stable_sort(v.begin(), v.end(), [](auto& a, auto& b) { return a.first > b.first; });
+      if (kind != 0 || tp.tc_order == 0)  // longest reductions first
+        std::stable_sort(v.begin(), v.end(), [](auto& a, auto& b) { return a.first > b.first; });
       P->gemm_range[kind][ph] = Range{(int)P->tiles.size(), (int)v.size()};
       for (auto& t : v) {
         P->tiles.push_back(t.second);
@@ -1801,6 +1874,7 @@ std::unique_ptr<Plan> merge_contract_plans(std::vector<std::unique_ptr<Plan>>& p
   M->kind = Plan::CONTRACT;
   M->precision = ps[0]->precision;
   const bool f64 = M->precision == SYM_PREC_FP64;
+  M->tc_order = ps[0]->tc_order;
   std::vector<int64_t> lin0(n), outm0(n), img0(n);
   std::vector<int> ops0(n), simt0(n), tc0(n);
   for (int i = 0; i < n; ++i) {
@@ -1942,7 +2016,8 @@ std::unique_ptr<Plan> merge_contract_plans(std::vector<std::unique_ptr<Plan>>& p
           v.push_back(g);
         }
       }
-      std::stable_sort(v.begin(), v.end(), [](const GemmTile& a, const GemmTile& b) { return a.k1 - a.k0 > b.k1 - b.k0; });
+      if (kind != 0 || M->tc_order == 0)
+        std::stable_sort(v.begin(), v.end(), [](const GemmTile& a, const GemmTile& b) { return a.k1 - a.k0 > b.k1 - b.k0; });
       M->gemm_range[kind][ph] = Range{(int)M->tiles.size(), (int)v.size()};
       for (auto& g : v) {
         M->tiles.push_back(g);

@@ -6,6 +6,7 @@
 
 #include "kernels.h"
 #include "structure.h"
+#include "../../include/symtensor.h"
 
 namespace sym {
 
@@ -115,6 +116,7 @@ struct Plan {
   // are captured into a CUDA graph as dependencies).  Off for plans that
   // must create nothing (sym_contract_noalloc).
   bool concurrent = true;
+  int tc_order = 0;  // tcgen05 tiles: 0 longest reduction first, 1 in sector order
   // The backward reads the tensor-core operands the forward gathered when
   // bwd_reads_fwd_operands; they are reused if the plan's last forward ran
   // on the same A and B buffers, and gathered again otherwise.
@@ -128,6 +130,11 @@ struct Plan {
   void validate(const int64_t* src_elems, const int64_t* dst_elems) const;
   void upload(bool device = true);
 };
+
+// planning parameters (sym_tune of the C ABI): read at plan time
+sym_tune current_tune();
+void set_tune(const sym_tune& t);  // validated; bumps the epoch
+int tune_epoch();
 
 std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const std::vector<int>& perm,
                                      int precision, int mode_fuse_split, int leg);

@@ -168,6 +168,36 @@ KERNEL_SYMBOLS = {"box": "box_kernel<T, T, false>", "box_flat": "box_kernel<T, T
                   "gemm_rows": "gemm_rows_kernel<T>", "direct": "direct_kernel<T>"}
 
 
+def tune_get():
+    """Current planning parameters (include/symtensor.h, sym_tune) as a dict."""
+    t = L.sym_tune()
+    L.check(L.lib.sym_tune_get(_byref(t)))
+    return {f: int(getattr(t, f)) for f in L.TUNE_FIELDS}
+
+
+def tune_set(**params):
+    """Change planning parameters; plans built afterwards use them (the plan
+    caches below are keyed by the tuning epoch, so later calls re-plan)."""
+    cur = tune_get()
+    unknown = set(params) - set(cur)
+    if unknown:
+        raise KeyError(f"unknown planning parameters: {sorted(unknown)}")
+    cur.update({k: int(v) for k, v in params.items()})
+    L.check(L.lib.sym_tune_set(_byref(L.sym_tune(**cur))))
+    # plans of older epochs are never looked up again: release them (their
+    # device scratch) unless a caller still holds them
+    e = tune_epoch()
+    for key in [k for k in _PLANS if k[0] in ("c", "b") and k[-1] != e]:
+        del _PLANS[key]
+    return cur
+
+
+def tune_epoch():
+    e = ctypes.c_int()
+    L.check(L.lib.sym_tune_epoch(_byref(e)))
+    return e.value
+
+
 def cached_plans():
     """Every plan built so far (for profiling and statistics)."""
     return [v[0] for v in _PLANS.values()]
@@ -176,7 +206,7 @@ def cached_plans():
 def contract_plan(A, B, pairsA, pairsB, precision=BF16X3, tree_c=None):
     """Plan (cached) of contracting structure A's legs pairsA with B's pairsB."""
     key = ("c", id(A), id(B), tuple(pairsA), tuple(pairsB), precision,
-           None if tree_c is None else tuple(map(tuple, tree_c)))
+           None if tree_c is None else tuple(map(tuple, tree_c)), tune_epoch())
     hit = _PLANS.get(key)
     if hit is not None:
         return hit[0]
@@ -212,7 +242,8 @@ class BatchPlan(Plan):
 
 def contract_batch_plan(As, Bs, pairsA, pairsB, precision=BF16X3):
     """Plan (cached) of contracting As[i] with Bs[i] over the same leg pairs, all i at once."""
-    key = ("b", tuple(id(a) for a in As), tuple(id(b) for b in Bs), tuple(pairsA), tuple(pairsB), precision)
+    key = ("b", tuple(id(a) for a in As), tuple(id(b) for b in Bs), tuple(pairsA), tuple(pairsB), precision,
+           tune_epoch())
     hit = _PLANS.get(key)
     if hit is not None:
         return hit[0]

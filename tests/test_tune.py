@@ -1,0 +1,77 @@
+"""Planning parameters (include/symtensor.h, sym_tune): the C-ABI round trip,
+range checks, the epoch, and that plans built afterwards follow them (host
+planning with SYM_PLAN_DRYRUN=1, no GPU)."""
+import os
+import subprocess
+import sys
+
+from tests.conftest import ROOT
+
+SCRIPT = r'''
+import paper_1203_2222_gb300 as P
+from paper_1203_2222_gb300 import synthetic
+d = P.tune_get()
+assert d == {"tc_min_mn": 64, "tc_min_k": 48, "tc_max_k": 16384, "direct_max": 4, "direct_chunk": 1024,
+             "rows_spans": 8, "splitk_ctas": 2, "thin_slice": 4096, "tc_order": 0}, d
+e0 = P.tune_epoch()
+for bad in ({"direct_max": 5}, {"direct_chunk": 100}, {"tc_max_k": 10}, {"thin_slice": 100}, {"tc_order": 2},
+            {"rows_spans": 0}):
+    try:
+        P.tune_set(**bad)
+        raise SystemExit(f"accepted {bad}")
+    except P.SymError:
+        pass
+assert P.tune_get() == d and P.tune_epoch() == e0
+try:
+    P.tune_set(no_such_parameter=1)
+    raise SystemExit("accepted an unknown name")
+except KeyError:
+    pass
+m = synthetic.u1_mps_heff()
+S = {n: P.Structure(P.U1, m[n]) for n in ("L", "A", "W", "R")}
+def kinds():
+    t1 = P.contract_plan(S["L"], S["A"], [2], [0], P.BF16X3)
+    t2 = P.contract_plan(t1.out, S["W"], [1, 2], [0, 2], P.BF16X3)
+    k1 = [x[3] for x in t1.gemm_shapes()]
+    return k1.count(0), len(k1), len(t2.gemm_shapes())
+tc0, n0, w0 = kinds()
+assert w0 == 0  # the MPO step is direct
+P.tune_set(tc_min_mn=16, tc_min_k=16)
+assert P.tune_epoch() == e0 + 1
+tc1, n1, w1 = kinds()
+assert n1 == n0 and tc1 > tc0, (tc0, tc1)  # narrower sectors moved onto the tensor cores
+P.tune_set(direct_max=0)
+assert kinds()[2] > 0  # the MPO step back on the GEMMs
+P.tune_set(**d)
+assert kinds() == (tc0, n0, w0)
+print("TUNE OK")
+'''
+
+
+def test_tune_parameters_round_trip_and_drive_planning():
+    env = dict(os.environ, SYM_PLAN_DRYRUN="1", PYTHONPATH=ROOT)
+    for k in ("SYM_TUNE", "SYM_DIRECT_MAX", "SYM_TC_MIN_MN", "SYM_TC_MIN_K", "SYM_TC_MAX_K"):
+        env.pop(k, None)
+    r = subprocess.run([sys.executable, "-c", SCRIPT], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "TUNE OK" in r.stdout
+
+
+def test_tune_environment_seeds_the_parameters():
+    env = dict(os.environ, SYM_PLAN_DRYRUN="1", PYTHONPATH=ROOT, SYM_TUNE="direct_chunk=256,tc_order=1",
+               SYM_TC_MIN_MN="32")
+    code = "import paper_1203_2222_gb300 as P; t = P.tune_get(); print(t['direct_chunk'], t['tc_order'], t['tc_min_mn'])"
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.split() == ["256", "1", "32"]
+
+
+def test_autotune_table_round_trip(tmp_path):
+    from paper_1203_2222_gb300 import autotune
+    path = str(tmp_path / "tuned.json")
+    assert autotune.load("w", path, device="dev") is None
+    p = {"tc_min_mn": 32, "tc_order": 1}
+    autotune.save("w", p, 1.5, 2.0, 7, path=path, device="dev")
+    autotune.save("other", {"tc_min_mn": 64}, 1.0, 1.0, 1, path=path, device="dev")
+    assert autotune.load("w", path, device="dev") == p
+    assert autotune.load("w", path, device="another device") is None
