@@ -59,6 +59,8 @@ def parse():
                          "the library defaults when there is none), a new autotuner search (stored in "
                          "--tune-table), or the library defaults")
     ap.add_argument("--tune-table", default=None, help="autotuner table (default paper_1203_2222_gb300/tuned.json)")
+    ap.add_argument("--batch-n", type=int, default=512,
+                    help="u1_two_site_batch: number of problems (512 at full size; fewer for a small profiling case)")
     ap.add_argument("--tune-space", default=None,
                     help="comma-separated planning parameters the search varies (default: all of autotune.SPACE)")
     args = ap.parse_args()
@@ -306,11 +308,12 @@ class BatchWorkload:
                 "one batch plan per contraction")
     default_steps, default_warmup, default_fp64_steps = 50, 5, 3
     names = ("L", "theta", "W", "R")
+    n = 512
 
     def build(self, P, dev):
         import torch
         from paper_1203_2222_gb300 import synthetic
-        self.spec = synthetic.u1_two_site_batch()
+        self.spec = synthetic.u1_two_site_batch(n=self.n)
         pr = self.spec["problems"]
         self.S = {n: [P.Structure(P.U1, p[n]) for p in pr] for n in self.names}
         plans = self.plans(P, P.BF16X3)
@@ -500,6 +503,8 @@ def run_ours(args, rank, world):
     wl = WORKLOADS[args.workload]()
     if args.workload == "su2_recouple":
         wl.dmax = args.su2_dmax
+    if args.workload == "u1_two_site_batch":
+        wl.n = args.batch_n
 
     # ---- planning parameters (autotuned table entry, search, or defaults)
     from paper_1203_2222_gb300 import autotune
@@ -735,7 +740,9 @@ def run_ours(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16x3-f32acc", "data": "synthetic",
         "config": {"workload": wl.describe + (f" [dmax {args.su2_dmax}]" if args.workload == "su2_recouple" and
-                                               args.su2_dmax != 32 else ""), "precision": "split-BF16 x3 on tcgen05, FP32 accumulate, fp32 blocks",
+                                               args.su2_dmax != 32 else "")
+                   + (f" [{args.batch_n} problems]" if args.workload == "u1_two_site_batch" and args.batch_n != 512
+                      else ""), "precision": "split-BF16 x3 on tcgen05, FP32 accumulate, fp32 blocks",
                    "useful_gflop_per_step": round(flops / 1e9, 4),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "launch": launch_mode,

@@ -253,12 +253,16 @@ int sym_plan_profile_kernel(sym_plan plan, int kernel, int* launches,
  *   splitk_ctas 2 (0..64): CUDA-core tile GEMMs split their reductions until
  *     a launch has splitk_ctas CTAs per SM (0: never split);
  *   thin_slice 4096 (multiple of 256): thin GEMMs, reduction per CTA;
- *   tc_order 0: tcgen05 tiles longest reduction first; 1: in sector order.
+ *   tc_order 0: tcgen05 tiles longest reduction first; 1: in sector order;
+ *   tc_group 8 (0..256): inside a sector the tcgen05 tiles run in groups of
+ *     tc_group row tiles, all column tiles of a group before the next
+ *     group, so that a wave of CTAs shares its operand panels in L2 (0: row
+ *     by row).
  * sym_tune_set rejects a value out of range with SYM_ERR_ARG.             */
 typedef struct {
   int tc_min_mn, tc_min_k, tc_max_k;
   int direct_max, direct_chunk;
-  int rows_spans, splitk_ctas, thin_slice, tc_order;
+  int rows_spans, splitk_ctas, thin_slice, tc_order, tc_group;
 } sym_tune;
 int sym_tune_get(sym_tune* out);
 int sym_tune_set(const sym_tune* in);

@@ -31,6 +31,7 @@ SPACE = {
     "splitk_ctas": [0, 1, 2, 4],              # CUDA-core tiles: split k up to this many CTAs per SM
     "thin_slice": [1024, 4096, 16384],        # thin GEMMs: reduction per CTA
     "tc_order": [0, 1],                       # tcgen05 tiles: longest reduction first / sector order
+    "tc_group": [0, 4, 8, 16, 32],            # tcgen05 tiles: row tiles per group (L2 panel reuse)
 }
 
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")

@@ -18,6 +18,8 @@
 // Persistent and warp-independent: a warp copies one 128-byte descriptor into
 // its shared-memory slot, stages the item's coefficients and column pointers
 // in registers, and streams the box with coalesced loads along its last dim.
+// Apply and outer items run as separate launches of their own kernels (every
+// item of a launch has the same kind).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,8 +32,28 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
-constexpr int kH = 4;   // positions in flight per lane (apply)
-constexpr int kHo = 2;  // (outer: twice the columns per position)
+// Loads are staged by cp.async into a per-lane slice of shared memory, two
+// stages deep, so that a lane keeps 2 * kH(T) positions x kMaxDirect columns
+// in flight (2 * 8 KB per warp) without holding them in registers; each lane
+// reads back only what it copied itself, so no barrier is needed.
+template <typename T>
+constexpr int kH = 32 / (int)sizeof(T);  // apply: positions per lane per stage (8 fp32, 4 fp64)
+template <typename T>
+constexpr int kHo = kH<T> / 2;           // outer: (twice the columns per position)
+constexpr int kStageBytes = 32 * 32 * kMaxDirect;  // one stage of one warp: 32 lanes x 8 fp32 x 4 columns
+
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 template <typename T>
 __device__ __forceinline__ T coef_of(const Term& t);
@@ -50,189 +72,241 @@ __device__ __forceinline__ T* dst_ptr(const BoxPtrs& p, int slot) {
   return static_cast<T*>(slot == DST_OUT ? p.dst[DST_OUT] : slot == DST_DA ? p.dst[DST_DA] : p.dst[DST_DB]);
 }
 
-// box index of position e (last dim fastest); floor(r / n) = umulhi(2r, mag) >> shf
+// Box index of position p (last dim fastest): floor(r / n) = umulhi(2r, mag) >> shf.
+// ND = the item's number of dims (1..3); one dim needs no division.
+template <int ND>
 struct DirectShape {
-  int n[kDirectDims], shf[kDirectDims];
-  uint32_t mag[kDirectDims];
-  int sa[kDirectDims], sb[kDirectDims], da[kDirectDims], db[kDirectDims];
+  int n[ND], shf[ND];
+  uint32_t mag[ND];
   __device__ __forceinline__ explicit DirectShape(const DirectItem& it) {
 #pragma unroll
-    for (int d = 0; d < kDirectDims; ++d) {
+    for (int d = 0; d < ND; ++d) {
       n[d] = it.dims[d];
       mag[d] = it.mag[d];
       shf[d] = (it.shf >> (8 * d)) & 0xff;
-      sa[d] = it.sa[d];
-      sb[d] = it.sb[d];
-      da[d] = it.da[d];
-      db[d] = it.db[d];
     }
   }
-  // source (ld multiplier a, offset b) and destination (c, e) parts of position p
-  __device__ __forceinline__ void at(int p, int& a, int& b, int& c, int& e) const {
-    int t[kDirectDims];
+  __device__ __forceinline__ void index(int p, int (&t)[ND]) const {
     int rem = p;
 #pragma unroll
-    for (int d = kDirectDims - 1; d > 0; --d) {
+    for (int d = ND - 1; d > 0; --d) {
       const int q = (int)(__umulhi((uint32_t)rem << 1, mag[d]) >> shf[d]);
       t[d] = rem - q * n[d];
       rem = q;
     }
     t[0] = rem;
-    a = b = c = e = 0;
-#pragma unroll
-    for (int d = 0; d < kDirectDims; ++d) {
-      a += t[d] * sa[d];
-      b += t[d] * sb[d];
-      c += t[d] * da[d];
-      e += t[d] * db[d];
-    }
   }
 };
 
-template <typename T>
+// Columns of one side of an item: column c at box index t is base[c][<t, str[c]>],
+// with str[c][d] = ld_c * a[d] + b[d] folded once per item (the relative
+// offset stays below 2^31 -- host check -- so it is formed in 32 bits).
+template <typename P, int NC, int ND>
+struct Cols {
+  P base[NC];
+  int str[NC][ND];
+  __device__ __forceinline__ void load(P slot, const Term* __restrict__ terms, int t0, int n, const int* a,
+                                       const int* b) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const bool on = c < n;
+      const Term t = terms[t0 + (on ? c : 0)];
+      base[c] = slot + t.off;
+      const int ld = on ? (int)t.ld : 0;
+#pragma unroll
+      for (int d = 0; d < ND; ++d) str[c][d] = on ? ld * a[d] + b[d] : 0;
+    }
+  }
+  __device__ __forceinline__ int off(int c, const int (&t)[ND]) const {
+    int o = 0;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) o += t[d] * str[c][d];
+    return o;
+  }
+};
+
+// apply: NS source and NQ destination columns (exact counts when the item has
+// them, else upper bounds with the actual counts ns <= NS, nq <= NQ)
+template <typename T, int ND, int NS, int NQ>
 __device__ __forceinline__ void apply_item(const DirectItem& it, const Term* __restrict__ terms, const BoxPtrs& ptrs,
-                                           int lane) {
-  const int ns = it.ns, nd = it.nd;
-  const T* __restrict__ src = src_ptr<T>(ptrs, it.slots & 3);
+                                           int lane, T* __restrict__ stage) {
+  const int ns = it.ns, nq = it.nd;
   const T* __restrict__ ksrc = src_ptr<T>(ptrs, (it.slots >> 2) & 3);
-  T* __restrict__ dst = dst_ptr<T>(ptrs, (it.slots >> 4) & 7);
-  const T* sp[kMaxDirect];
-  T* dp[kMaxDirect];
-  int sl[kMaxDirect], dl[kMaxDirect];
-  T cf[kMaxDirect][kMaxDirect];
+  Cols<const T*, NS, ND> S;
+  Cols<T*, NQ, ND> Q;
+  S.load(src_ptr<T>(ptrs, it.slots & 3), terms, it.ts, ns, it.sa, it.sb);
+  Q.load(dst_ptr<T>(ptrs, (it.slots >> 4) & 7), terms, it.td, nq, it.da, it.db);
+  T cf[NQ][NS];
 #pragma unroll
-  for (int s = 0; s < kMaxDirect; ++s) {
-    const bool on = s < ns;
-    const Term t = terms[it.ts + (on ? s : 0)];
-    sp[s] = src + t.off;
-    sl[s] = on ? (int)t.ld : 0;
-  }
+  for (int d = 0; d < NQ; ++d)
 #pragma unroll
-  for (int d = 0; d < kMaxDirect; ++d) {
-    const bool on = d < nd;
-    const Term t = terms[it.td + (on ? d : 0)];
-    dp[d] = dst + t.off;
-    dl[d] = on ? (int)t.ld : 0;
-  }
-#pragma unroll
-  for (int d = 0; d < kMaxDirect; ++d)
-#pragma unroll
-    for (int s = 0; s < kMaxDirect; ++s) {
-      cf[d][s] = T(0);
-      if (d < nd && s < ns) {
-        const Term t = terms[it.tk + d * it.kd + s * it.ks];
-        const T c = coef_of<T>(t);
-        if (c != T(0)) cf[d][s] = c * __ldg(ksrc + t.off);
+    for (int c = 0; c < NS; ++c) {
+      cf[d][c] = T(0);
+      if (d < nq && c < ns) {
+        const Term t = terms[it.tk + d * it.kd + c * it.ks];
+        const T k = coef_of<T>(t);
+        if (k != T(0)) cf[d][c] = k * __ldg(ksrc + t.off);
       }
     }
-  const DirectShape sh(it);
+  const DirectShape<ND> sh(it);
   const int last = it.start + it.count - 1;
-#pragma unroll 1
-  for (int u = it.start + lane; u <= last; u += 32 * kH) {
-    int c[kH], e[kH];
-    T v[kH][kMaxDirect];
+  constexpr int H = kH<T>;
+  constexpr int SLOT = H * NS * 32;  // one stage: [H][NS][32], this lane's values at [..][..][lane]
+  auto issue = [&](int u, T* buf) {
 #pragma unroll
-    for (int h = 0; h < kH; ++h) {
-      int a, b;
-      sh.at(min(u + 32 * h, last), a, b, c[h], e[h]);
+    for (int h = 0; h < H; ++h) {
+      int t[ND];
+      sh.index(min(u + 32 * h, last), t);
 #pragma unroll
-      for (int s = 0; s < kMaxDirect; ++s) v[h][s] = s < ns ? __ldg(sp[s] + (int64_t)sl[s] * a + b) : T(0);
+      for (int c = 0; c < NS; ++c)
+        if (c < ns) cp_async(buf + (h * NS + c) * 32 + lane, S.base[c] + S.off(c, t), sizeof(T));
+    }
+    cp_commit();
+  };
+  const int step = 32 * H;
+  int u = it.start + lane;
+  if (u <= last) issue(u, stage);
+  for (int k = 0; u <= last; u += step, ++k) {
+    T* cur = stage + (k & 1) * SLOT;
+    if (u + step <= last) {
+      issue(u + step, stage + ((k + 1) & 1) * SLOT);
+      cp_wait<1>();
+    } else {
+      cp_wait<0>();
     }
 #pragma unroll
-    for (int h = 0; h < kH; ++h) {
+    for (int h = 0; h < H; ++h) {
       if (u + 32 * h > last) break;
+      int t[ND];
+      sh.index(u + 32 * h, t);
+      T v[NS];
 #pragma unroll
-      for (int d = 0; d < kMaxDirect; ++d) {
-        if (d >= nd) break;
+      for (int c = 0; c < NS; ++c) v[c] = c < ns ? cur[(h * NS + c) * 32 + lane] : T(0);
+#pragma unroll
+      for (int d = 0; d < NQ; ++d) {
+        if (d >= nq) break;
         T acc = T(0);
 #pragma unroll
-        for (int s = 0; s < kMaxDirect; ++s) acc = fma(cf[d][s], v[h][s], acc);
-        dp[d][(int64_t)dl[d] * c[h] + e[h]] = acc;
+        for (int c = 0; c < NS; ++c) acc = fma(cf[d][c], v[c], acc);
+        Q.base[d][Q.off(d, t)] = acc;
       }
     }
   }
 }
 
-template <typename T>
+// outer: out(s, d) += sum_t A_s[t] dC_d[t] over the item's positions
+template <typename T, int ND, int NS, int NQ>
 __device__ __forceinline__ void outer_item(const DirectItem& it, const Term* __restrict__ terms, const BoxPtrs& ptrs,
-                                           int lane) {
-  const int ns = it.ns, nd = it.nd;
-  const T* __restrict__ src = src_ptr<T>(ptrs, it.slots & 3);
-  const T* __restrict__ src2 = src_ptr<T>(ptrs, (it.slots >> 2) & 3);
+                                           int lane, T* __restrict__ stage) {
+  const int ns = it.ns, nq = it.nd;
   T* __restrict__ dst = dst_ptr<T>(ptrs, (it.slots >> 4) & 7);
-  const T* sp[kMaxDirect];
-  const T* qp[kMaxDirect];
-  int sl[kMaxDirect], ql[kMaxDirect];
+  Cols<const T*, NS, ND> S;
+  Cols<const T*, NQ, ND> Q;
+  S.load(src_ptr<T>(ptrs, it.slots & 3), terms, it.ts, ns, it.sa, it.sb);
+  Q.load(src_ptr<T>(ptrs, (it.slots >> 2) & 3), terms, it.td, nq, it.da, it.db);
+  T acc[NS][NQ];
 #pragma unroll
-  for (int s = 0; s < kMaxDirect; ++s) {
-    const bool on = s < ns;
-    const Term t = terms[it.ts + (on ? s : 0)];
-    sp[s] = src + t.off;
-    sl[s] = on ? (int)t.ld : 0;
-  }
+  for (int c = 0; c < NS; ++c)
 #pragma unroll
-  for (int d = 0; d < kMaxDirect; ++d) {
-    const bool on = d < nd;
-    const Term t = terms[it.td + (on ? d : 0)];
-    qp[d] = src2 + t.off;
-    ql[d] = on ? (int)t.ld : 0;
-  }
-  T acc[kMaxDirect][kMaxDirect];
-#pragma unroll
-  for (int s = 0; s < kMaxDirect; ++s)
-#pragma unroll
-    for (int d = 0; d < kMaxDirect; ++d) acc[s][d] = T(0);
-  const DirectShape sh(it);
+    for (int d = 0; d < NQ; ++d) acc[c][d] = T(0);
+  const DirectShape<ND> sh(it);
   const int last = it.start + it.count - 1;
-#pragma unroll 1
-  for (int u = it.start + lane; u <= last; u += 32 * kHo) {
-    T va[kHo][kMaxDirect], vq[kHo][kMaxDirect];
+  constexpr int H = kHo<T>;
+  constexpr int W = NS + NQ;          // values per position
+  constexpr int SLOT = H * W * 32;    // one stage: [H][W][32]
+  auto issue = [&](int u, T* buf) {
 #pragma unroll
-    for (int h = 0; h < kHo; ++h) {
-      const bool ok = u + 32 * h <= last;
-      int a, b, c, e;
-      sh.at(min(u + 32 * h, last), a, b, c, e);
+    for (int h = 0; h < H; ++h) {
+      int t[ND];
+      sh.index(min(u + 32 * h, last), t);
 #pragma unroll
-      for (int s = 0; s < kMaxDirect; ++s) va[h][s] = (ok && s < ns) ? __ldg(sp[s] + (int64_t)sl[s] * a + b) : T(0);
+      for (int c = 0; c < NS; ++c)
+        if (c < ns) cp_async(buf + (h * W + c) * 32 + lane, S.base[c] + S.off(c, t), sizeof(T));
 #pragma unroll
-      for (int d = 0; d < kMaxDirect; ++d) vq[h][d] = (ok && d < nd) ? __ldg(qp[d] + (int64_t)ql[d] * c + e) : T(0);
+      for (int d = 0; d < NQ; ++d)
+        if (d < nq) cp_async(buf + (h * W + NS + d) * 32 + lane, Q.base[d] + Q.off(d, t), sizeof(T));
+    }
+    cp_commit();
+  };
+  const int step = 32 * H;
+  int u = it.start + lane;
+  if (u <= last) issue(u, stage);
+  for (int k = 0; u <= last; u += step, ++k) {
+    T* cur = stage + (k & 1) * SLOT;
+    if (u + step <= last) {
+      issue(u + step, stage + ((k + 1) & 1) * SLOT);
+      cp_wait<1>();
+    } else {
+      cp_wait<0>();
     }
 #pragma unroll
-    for (int h = 0; h < kHo; ++h)
+    for (int h = 0; h < H; ++h) {
+      if (u + 32 * h > last) break;
+      T va[NS], vq[NQ];
 #pragma unroll
-      for (int s = 0; s < kMaxDirect; ++s)
+      for (int c = 0; c < NS; ++c) va[c] = c < ns ? cur[(h * W + c) * 32 + lane] : T(0);
 #pragma unroll
-        for (int d = 0; d < kMaxDirect; ++d) acc[s][d] = fma(va[h][s], vq[h][d], acc[s][d]);
+      for (int d = 0; d < NQ; ++d) vq[d] = d < nq ? cur[(h * W + NS + d) * 32 + lane] : T(0);
+#pragma unroll
+      for (int c = 0; c < NS; ++c)
+#pragma unroll
+        for (int d = 0; d < NQ; ++d) acc[c][d] = fma(va[c], vq[d], acc[c][d]);
+    }
   }
   // butterfly: every lane ends with the warp's sums
 #pragma unroll
-  for (int s = 0; s < kMaxDirect; ++s)
+  for (int c = 0; c < NS; ++c)
 #pragma unroll
-    for (int d = 0; d < kMaxDirect; ++d)
+    for (int d = 0; d < NQ; ++d)
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[s][d] += __shfl_xor_sync(0xffffffffu, acc[s][d], o);
-  // lane s * kMaxDirect + d adds out(s, d)
-  const int s0 = lane / kMaxDirect, d0 = lane % kMaxDirect;
-  if (lane < kMaxDirect * kMaxDirect && s0 < ns && d0 < nd) {
+      for (int o = 16; o > 0; o >>= 1) acc[c][d] += __shfl_xor_sync(0xffffffffu, acc[c][d], o);
+  // lane c * NQ + d adds out(c, d)
+  const int c0 = lane / NQ, d0 = lane % NQ;
+  if (lane < NS * NQ && c0 < ns && d0 < nq) {
     T v = T(0);
 #pragma unroll
-    for (int s = 0; s < kMaxDirect; ++s)
+    for (int c = 0; c < NS; ++c)
 #pragma unroll
-      for (int d = 0; d < kMaxDirect; ++d)
-        if (s == s0 && d == d0) v = acc[s][d];
-    const Term t = terms[it.tk + d0 * it.kd + s0 * it.ks];
-    const T c = coef_of<T>(t);
-    if (c != T(0)) atomicAdd(dst + t.off, c * v);
+      for (int d = 0; d < NQ; ++d)
+        if (c == c0 && d == d0) v = acc[c][d];
+    const Term t = terms[it.tk + d0 * it.kd + c0 * it.ks];
+    const T k = coef_of<T>(t);
+    if (k != T(0)) atomicAdd(dst + t.off, k * v);
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) direct_kernel(const DirectItem* __restrict__ items, int nitems,
+// the item's column counts pick an exact variant (the MPO and physical legs
+// of a tensor network give 1 or 4 columns per side), else the bounded one
+template <typename T, int kOp, int ND>
+__device__ __forceinline__ void run_item(const DirectItem& it, const Term* __restrict__ terms, const BoxPtrs& ptrs,
+                                         int lane, T* __restrict__ stage) {
+  const int key = ND == 3 ? 0 : it.ns * 8 + it.nd;  // three-dim boxes take the bounded variant only
+  if (kOp == kDirectApply) {
+    if (key == 4 * 8 + 4) apply_item<T, ND, 4, 4>(it, terms, ptrs, lane, stage);
+    else if (key == 1 * 8 + 1) apply_item<T, ND, 1, 1>(it, terms, ptrs, lane, stage);
+    else if (key == 1 * 8 + 4) apply_item<T, ND, 1, 4>(it, terms, ptrs, lane, stage);
+    else if (key == 4 * 8 + 1) apply_item<T, ND, 4, 1>(it, terms, ptrs, lane, stage);
+    else apply_item<T, ND, kMaxDirect, kMaxDirect>(it, terms, ptrs, lane, stage);
+  } else {
+    if (key == 4 * 8 + 4) outer_item<T, ND, 4, 4>(it, terms, ptrs, lane, stage);
+    else if (key == 1 * 8 + 1) outer_item<T, ND, 1, 1>(it, terms, ptrs, lane, stage);
+    else if (key == 1 * 8 + 4) outer_item<T, ND, 1, 4>(it, terms, ptrs, lane, stage);
+    else if (key == 4 * 8 + 1) outer_item<T, ND, 4, 1>(it, terms, ptrs, lane, stage);
+    else outer_item<T, ND, kMaxDirect, kMaxDirect>(it, terms, ptrs, lane, stage);
+  }
+}
+
+// One kernel per item kind, so that each gets the registers of its own loop
+// (the apply loop keeps 8 positions x 4 columns of loads in flight per lane).
+template <typename T, int kOp>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) direct_kernel(const DirectItem* __restrict__ items, int nitems,
                                                           const Term* __restrict__ terms, BoxPtrs ptrs) {
   constexpr int kWords = sizeof(DirectItem) / 4;
   static_assert(kWords <= 32, "one descriptor word per lane");
   __shared__ uint32_t desc[kWarps][kWords];
+  extern __shared__ __align__(16) unsigned char dyn[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* stage = reinterpret_cast<T*>(dyn + (size_t)warp * 2 * kStageBytes);
   pdl_wait();
   pdl_launch_dependents();
   for (int w = blockIdx.x * kWarps + warp; w < nitems; w += gridDim.x * kWarps) {
@@ -240,37 +314,47 @@ __global__ void __launch_bounds__(kThreads) direct_kernel(const DirectItem* __re
     if (lane < kWords) desc[warp][lane] = reinterpret_cast<const uint32_t*>(items + w)[lane];
     __syncwarp();
     const DirectItem& it = *reinterpret_cast<const DirectItem*>(desc[warp]);
-    if (it.op == kDirectApply)
-      apply_item<T>(it, terms, ptrs, lane);
+    if (it.ndim == 1)
+      run_item<T, kOp, 1>(it, terms, ptrs, lane, stage);
+    else if (it.ndim == 2)
+      run_item<T, kOp, 2>(it, terms, ptrs, lane, stage);
     else
-      outer_item<T>(it, terms, ptrs, lane);
+      run_item<T, kOp, 3>(it, terms, ptrs, lane, stage);
   }
 }
 
-template <typename T>
+constexpr int kDynSmem = kWarps * 2 * kStageBytes;  // 64 KB: two stages per warp
+
+template <typename T, int kOp>
 int ctas_per_sm() {
   static const int n = [] {
     int v = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, direct_kernel<T>, kThreads, 0) != cudaSuccess || v < 1)
+    cudaFuncSetAttribute(direct_kernel<T, kOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, direct_kernel<T, kOp>, kThreads, kDynSmem) != cudaSuccess ||
+        v < 1)
       v = 1;
     return v;
   }();
   return n;
 }
 
-template <typename T>
-int launch_t(const DirectItem* items, int nitems, const Term* terms, const BoxPtrs& ptrs, cudaStream_t s) {
-  const int ctas = std::min((nitems + kWarps - 1) / kWarps, tc_num_sms() * ctas_per_sm<T>());
-  return (int)launch_pdl(direct_kernel<T>, dim3(ctas), dim3(kThreads), 0, s, items, nitems, terms, ptrs);
+template <typename T, int kOp>
+int launch_op(const DirectItem* items, int nitems, const Term* terms, const BoxPtrs& ptrs, cudaStream_t s) {
+  if (nitems <= 0) return 0;
+  const int ctas = std::min((nitems + kWarps - 1) / kWarps, tc_num_sms() * ctas_per_sm<T, kOp>());
+  return (int)launch_pdl(direct_kernel<T, kOp>, dim3(ctas), dim3(kThreads), kDynSmem, s, items, nitems, terms, ptrs);
 }
 
 }  // namespace
 
-int launch_direct(bool f64, const DirectItem* items, int nitems, const Term* terms, const BoxPtrs& ptrs,
+int launch_direct(bool f64, int op, const DirectItem* items, int nitems, const Term* terms, const BoxPtrs& ptrs,
                   void* stream) {
-  if (nitems <= 0) return 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return f64 ? launch_t<double>(items, nitems, terms, ptrs, s) : launch_t<float>(items, nitems, terms, ptrs, s);
+  if (op == kDirectApply)
+    return f64 ? launch_op<double, kDirectApply>(items, nitems, terms, ptrs, s)
+               : launch_op<float, kDirectApply>(items, nitems, terms, ptrs, s);
+  return f64 ? launch_op<double, kDirectOuter>(items, nitems, terms, ptrs, s)
+             : launch_op<float, kDirectOuter>(items, nitems, terms, ptrs, s);
 }
 
 }  // namespace sym

@@ -179,7 +179,8 @@ int launch_box(bool src_f64, bool dst_f64, bool flat_only, const BoxItem* items,
                const BoxPtrs& ptrs, void* stream);
 int launch_gemm_simt(bool f64, int shape, const GemmSectorSimt* secs, const GemmTile* tiles, int ntiles,
                      const void* ops, void* outm, void* stream);
-int launch_direct(bool f64, const DirectItem* items, int nitems, const Term* terms, const BoxPtrs& ptrs,
+// every item of [items, items + nitems) must have op == `op`
+int launch_direct(bool f64, int op, const DirectItem* items, int nitems, const Term* terms, const BoxPtrs& ptrs,
                   void* stream);
 int launch_gemm_tc(const TcSector* secs, const GemmTile* tiles, int ntiles, const TensorMap* maps, float* C,
                    int* err_word, void* stream);

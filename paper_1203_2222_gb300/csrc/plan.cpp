@@ -883,6 +883,7 @@ sym_tune& tune_state() {
     d.splitk_ctas = 2;
     d.thin_slice = 4096;
     d.tc_order = 0;
+    d.tc_group = 8;
     // SYM_TUNE="name=value,...": any parameter (names as in sym_tune)
     if (const char* e = std::getenv("SYM_TUNE")) {
       std::string all(e);
@@ -898,7 +899,8 @@ sym_tune& tune_state() {
           int* f = k == "tc_min_mn" ? &d.tc_min_mn : k == "tc_min_k" ? &d.tc_min_k : k == "tc_max_k" ? &d.tc_max_k
                  : k == "direct_max" ? &d.direct_max : k == "direct_chunk" ? &d.direct_chunk
                  : k == "rows_spans" ? &d.rows_spans : k == "splitk_ctas" ? &d.splitk_ctas
-                 : k == "thin_slice" ? &d.thin_slice : k == "tc_order" ? &d.tc_order : nullptr;
+                 : k == "thin_slice" ? &d.thin_slice : k == "tc_order" ? &d.tc_order
+                 : k == "tc_group" ? &d.tc_group : nullptr;
           if (f) *f = v;
         }
         p = q + 1;
@@ -920,7 +922,7 @@ void set_tune(const sym_tune& t) {
   if (!in(t.tc_min_mn, 1, 1 << 30) || !in(t.tc_min_k, 1, 1 << 30) || !in(t.tc_max_k, t.tc_min_k, 1 << 30) ||
       !in(t.direct_max, 0, kMaxDirect) || !in(t.direct_chunk, 32, 1 << 16) || t.direct_chunk % 32 ||
       !in(t.rows_spans, 1, 64) || !in(t.splitk_ctas, 0, 64) || !in(t.thin_slice, 256, 1 << 20) ||
-      t.thin_slice % 256 || !in(t.tc_order, 0, 1))
+      t.thin_slice % 256 || !in(t.tc_order, 0, 1) || !in(t.tc_group, 0, 256))
     fail(SYM_ERR_ARG, "planning parameter out of range");
   std::lock_guard<std::mutex> g(tune_mu);
   tune_state() = t;
@@ -1010,6 +1012,9 @@ void validate_direct(const Plan& P) {
     expect += r.count;
   }
   if (expect != (int)P.ditems.size()) fail(SYM_ERR_ARG, "internal: direct ranges do not cover the items");
+  for (int r = 0; r < 3; ++r)  // every launch runs one item kind
+    for (int i = rs[r].first; i < rs[r].first + rs[r].count; ++i)
+      if (P.ditems[i].op != (r == 2 ? kDirectOuter : kDirectApply)) fail(SYM_ERR_ARG, "internal: direct item kind");
   for (const DirectItem& it : P.ditems) {
     if ((it.op != kDirectApply && it.op != kDirectOuter) || it.ns < 1 || it.nd < 1 || it.ns > kMaxDirect ||
         it.nd > kMaxDirect || it.ndim < 1 || it.ndim > kDirectDims || it.start < 0 || it.count < 1)
@@ -1043,7 +1048,8 @@ void validate_direct(const Plan& P) {
       if (t < 0 || t >= (int)P.dterms.size() || P.dterm_space[t] != space)
         fail(SYM_ERR_ARG, "internal: direct term out of range");
       const Term& x = P.dterms[t];
-      if (x.off < 0 || x.ld < 0 || x.ld >= ((int64_t)1 << 31) || x.off + x.ld * ma + mb >= ne[space])
+      if (x.off < 0 || x.ld < 0 || x.ld >= ((int64_t)1 << 31) || x.off + x.ld * ma + mb >= ne[space] ||
+          x.ld * ma + mb >= ((int64_t)1 << 31))  // relative offsets are formed in 32 bits
         fail(SYM_ERR_ARG, "internal: direct item addresses past its tensor");
     };
     for (int s = 0; s < it.ns; ++s) check(it.ts + s, sp, sa, sb);
@@ -1493,9 +1499,13 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
       P->secs_tc.push_back(
           TcSector{(int)m, (int)n, (int)k, (int)cdiv(k, 64), (int)aoff, (int)boff, amn, bmn, coff, (int)n, 1.0f});
       const int sec = (int)P->secs_tc.size() - 1;
-      for (int64_t mt = 0; mt < cdiv(m, 128); ++mt)
-        for (int64_t nt = 0; nt < cdiv(n, 128); ++nt)
-          lists[0][ph].push_back({k, GemmTile{sec, (int)mt, (int)nt, 0, (int)k, 0}});
+      // grouped order: tc_group row tiles at a time, all column tiles of the
+      // group before the next (a wave of consecutive tiles shares panels)
+      const int64_t MT = cdiv(m, 128), NT = cdiv(n, 128), G = tp.tc_group > 0 ? tp.tc_group : 1;
+      for (int64_t g0 = 0; g0 < MT; g0 += G)
+        for (int64_t nt = 0; nt < NT; ++nt)
+          for (int64_t mt = g0; mt < std::min(MT, g0 + G); ++mt)
+            lists[0][ph].push_back({k, GemmTile{sec, (int)mt, (int)nt, 0, (int)k, 0}});
       return false;
     }
     P->secs_simt.push_back(
@@ -2089,13 +2099,15 @@ int run_box(Plan& p, Range r, const BoxPtrs& ptrs, void* stream, int phase) {
                    "box kernel");
 }
 
-int run_direct(Plan& p, Range r, const BoxPtrs& ptrs, void* stream, int phase) {
+// one launch per item kind (`op`): the apply and the outer items have kernels of their own
+int run_direct(Plan& p, int op, Range r, const BoxPtrs& ptrs, void* stream, int phase) {
   if (r.count <= 0) return SYM_OK;
   p.last_launches++;
   ProfScope ps(p, phase, SYM_KERNEL_DIRECT, stream,
                p.ditem_bytes_prefix[r.first + r.count] - p.ditem_bytes_prefix[r.first],
                p.ditem_flops_prefix[r.first + r.count] - p.ditem_flops_prefix[r.first]);
-  return cuda_code(launch_direct(p.f64(), p.d_ditems + r.first, r.count, p.d_dterms, ptrs, stream), "direct kernel");
+  return cuda_code(launch_direct(p.f64(), op, p.d_ditems + r.first, r.count, p.d_dterms, ptrs, stream),
+                   "direct kernel");
 }
 
 int run_gemm_kind(Plan& p, int kind, Range r, void* stream, int phase) {
@@ -2218,7 +2230,7 @@ int exec_contract(Plan& p, const void* A, const void* B, void* C, void* stream) 
   d.src[0] = A;
   d.src[1] = B;
   d.dst[DST_OUT] = C;
-  return run_direct(p, p.fwd_direct, d, stream, PH_FWD_DIRECT);
+  return run_direct(p, kDirectApply, p.fwd_direct, d, stream, PH_FWD_DIRECT);
 }
 
 int exec_contract_backward(Plan& p, const void* A, const void* B, const void* dC, void* dA, void* dB,
@@ -2263,12 +2275,9 @@ int exec_contract_backward(Plan& p, const void* A, const void* B, const void* dC
   d.src[2] = dC;
   d.dst[DST_DA] = dA;
   d.dst[DST_DB] = dB;
-  Range dr;
-  if (dA && dB)
-    dr = {p.bwd_direct_a.first, p.bwd_direct_a.count + p.bwd_direct_b.count};
-  else
-    dr = dA ? p.bwd_direct_a : p.bwd_direct_b;
-  return run_direct(p, dr, d, stream, PH_BWD_DIRECT);
+  if (dA)
+    if (int r = run_direct(p, kDirectApply, p.bwd_direct_a, d, stream, PH_BWD_DIRECT)) return r;
+  return dB ? run_direct(p, kDirectOuter, p.bwd_direct_b, d, stream, PH_BWD_DIRECT) : SYM_OK;
 }
 
 }  // namespace sym

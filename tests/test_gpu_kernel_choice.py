@@ -24,7 +24,7 @@ FORCED = {
     # the schedule parameters at their extremes: one-run rows tiles, 32-position
     # direct items, maximal split-K, 256-long thin slices, tiles in sector order
     "schedule_extremes": {"SYM_TUNE": "direct_chunk=32,rows_spans=1,splitk_ctas=64,thin_slice=256,tc_order=1,"
-                                      "tc_min_mn=16,tc_min_k=16"},
+                                      "tc_min_mn=16,tc_min_k=16,tc_group=3"},
 }
 
 

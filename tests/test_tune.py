@@ -12,10 +12,10 @@ import paper_1203_2222_gb300 as P
 from paper_1203_2222_gb300 import synthetic
 d = P.tune_get()
 assert d == {"tc_min_mn": 64, "tc_min_k": 48, "tc_max_k": 16384, "direct_max": 4, "direct_chunk": 1024,
-             "rows_spans": 8, "splitk_ctas": 2, "thin_slice": 4096, "tc_order": 0}, d
+             "rows_spans": 8, "splitk_ctas": 2, "thin_slice": 4096, "tc_order": 0, "tc_group": 8}, d
 e0 = P.tune_epoch()
 for bad in ({"direct_max": 5}, {"direct_chunk": 100}, {"tc_max_k": 10}, {"thin_slice": 100}, {"tc_order": 2},
-            {"rows_spans": 0}):
+            {"rows_spans": 0}, {"tc_group": -1}):
     try:
         P.tune_set(**bad)
         raise SystemExit(f"accepted {bad}")
