@@ -274,22 +274,25 @@ __device__ __forceinline__ void tile_item(const BoxItem& it, const TS* __restric
 // Fused recoupling item (kSelRecouple): for every position of the box, the
 // n_s source values are loaded once and the n_d destinations receive their
 // coefficient-weighted sums (Ch. 6, Eq. permsu2, all output labels of one
-// set of leg spins at once).  Coefficients and offsets are staged in the
-// warp's shared-memory tile; two positions per lane are in flight (FP32).
-template <int ND, typename TS, typename TD>
+// set of leg spins at once).  The coefficient matrix is staged in the warp's
+// shared-memory tile with rows padded to NS (a bound on n_s, 8 or 16) and
+// read back as 16-byte vectors, once per batch of H positions per lane; the
+// source and destination offsets are staged there too and read once per
+// column per batch.  ND is a bound on the box's dims (unused dims are unit).
+template <int ND, int NS, typename TS, typename TD>
 __device__ __forceinline__ void recouple_item(const BoxItem& it, const Term* __restrict__ terms,
                                               const TS* __restrict__ src, void* dstv, int64_t lo_off, bool split,
                                               TD (*tile)[33], int lane) {
   const int ns = it.nterm, nd = it.p0;
   const Term* T = terms + it.term0;
-  TD* cf = &tile[0][0];                                               // [nd][ns]
-  int64_t* soff = reinterpret_cast<int64_t*>(cf + kMaxRecouple * kMaxRecouple);
+  TD* cf = &tile[0][0];  // [nd][NS], zero past n_s
+  int64_t* soff = reinterpret_cast<int64_t*>(cf + kMaxRecouple * 16);
   int64_t* sld = soff + kMaxRecouple;
   int64_t* doff = sld + kMaxRecouple;
   int64_t* dld = doff + kMaxRecouple;
-  for (int i = lane; i < nd * ns; i += 32) {
-    const Term& c = T[ns + nd + i];
-    cf[i] = coef<TD>(c.coef, c.coef_f);
+  for (int i = lane; i < nd * NS; i += 32) {
+    const int d = i / NS, q = i - d * NS;
+    cf[i] = q < ns ? coef<TD>(T[ns + nd + d * ns + q].coef, T[ns + nd + d * ns + q].coef_f) : TD(0);
   }
   if (lane < ns) {
     soff[lane] = T[lane].off;
@@ -307,11 +310,11 @@ __device__ __forceinline__ void recouple_item(const BoxItem& it, const Term* __r
   load_strides(it.da, da);
   load_strides(it.db, db);
   const int last = it.start + it.count - 1;
-  constexpr int H = sizeof(TD) == 4 ? 2 : 1;  // positions in flight per lane
+  constexpr int H = (sizeof(TD) == 4 && NS <= 8) ? 4 : ND > 4 ? 1 : 2;  // positions in flight per lane
+  constexpr int V = 16 / sizeof(TD);                       // coefficients per 16-byte read
 #pragma unroll 1
   for (int u = 0; u < kBatch; u += H) {
     int a[H], b[H], c[H], e[H];
-    TD v[H][kMaxRecouple];
 #pragma unroll
     for (int h = 0; h < H; ++h) {
       int t[ND];
@@ -320,19 +323,44 @@ __device__ __forceinline__ void recouple_item(const BoxItem& it, const Term* __r
       b[h] = dot(t, sb);
       c[h] = dot(t, da);
       e[h] = dot(t, db);
+    }
+    TD v[H][NS];
 #pragma unroll
-      for (int q = 0; q < kMaxRecouple; ++q)
-        v[h][q] = q < ns ? TD(__ldg(src + soff[q] + sld[q] * a[h] + b[h])) : TD(0);
+    for (int q = 0; q < NS; ++q) {
+      if (q < ns) {
+        const TS* p = src + soff[q];
+        const int64_t l = sld[q];
+#pragma unroll
+        for (int h = 0; h < H; ++h) v[h][q] = TD(__ldg(p + l * a[h] + b[h]));
+      } else {
+#pragma unroll
+        for (int h = 0; h < H; ++h) v[h][q] = TD(0);
+      }
     }
 #pragma unroll 1
     for (int d = 0; d < nd; ++d) {
+      TD w[NS];
+#pragma unroll
+      for (int q = 0; q < NS; q += V) {  // one 16-byte shared-memory read per V coefficients
+        if constexpr (V == 4) {
+          const float4 r = *reinterpret_cast<const float4*>(cf + d * NS + q);
+          w[q] = r.x;
+          w[q + 1] = r.y;
+          w[q + 2] = r.z;
+          w[q + 3] = r.w;
+        } else {
+          const double2 r = *reinterpret_cast<const double2*>(cf + d * NS + q);
+          w[q] = r.x;
+          w[q + 1] = r.y;
+        }
+      }
+      const int64_t o0 = doff[d], l = dld[d];
 #pragma unroll
       for (int h = 0; h < H; ++h) {
         TD acc = TD(0);
 #pragma unroll
-        for (int q = 0; q < kMaxRecouple; ++q)
-          if (q < ns) acc += cf[d * ns + q] * v[h][q];
-        const int64_t o = doff[d] + dld[d] * c[h] + e[h];
+        for (int q = 0; q < NS; ++q) acc = fma(w[q], v[h][q], acc);
+        const int64_t o = o0 + l * c[h] + e[h];
         if (split)
           store_split(static_cast<__nv_bfloat16*>(dstv), lo_off, o, (float)acc);
         else
@@ -422,11 +450,14 @@ __device__ __forceinline__ void run_item(const BoxItem& it, const Term* __restri
   void* dp = dst_slot(it, ptrs);
   if (it.sel & kSelRecouple) {
     const bool split = ((it.sel >> 4) & 7) == DST_SPLIT;
-    switch (it.ndim) {
-      case 1: recouple_item<1, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
-      case 2: recouple_item<2, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
-      case 3: recouple_item<3, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
-      default: recouple_item<kMaxDim, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
+    const int k = (it.ndim <= 2 ? 0 : it.ndim <= 4 ? 1 : 2) * 2 + (it.nterm <= 8 ? 0 : 1);
+    switch (k) {
+      case 0: recouple_item<2, 8, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
+      case 1: recouple_item<2, 16, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
+      case 2: recouple_item<4, 8, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
+      case 3: recouple_item<4, 16, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
+      case 4: recouple_item<kMaxDim, 8, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
+      default: recouple_item<kMaxDim, 16, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
     }
     return;
   }
@@ -479,7 +510,7 @@ __global__ void __launch_bounds__(kThreads, kFlat ? 8 : (sizeof(TD) == 4 ? 5 : 4
     if constexpr (kFlat) {
       run_flat<TS, TD>(it, ptrs, lane);
     } else {
-      __shared__ TD tiles[kWarps][32][33];
+      __shared__ __align__(16) TD tiles[kWarps][32][33];
       run_item<TS, TD>(it, terms, ptrs, tiles[w], lane);
     }
     __syncwarp();
