@@ -86,13 +86,16 @@ def time_step(step, reps=5, warmup=2, trials=3, graph=True, flush_mb=256):
     return sorted(ts)[len(ts) // 2]
 
 
-def tune(step, space=None, start=None, reps=5, warmup=2, trials=3, rounds=2, tol=0.02, log=None, graph=True):
+def tune(step, space=None, start=None, reps=5, warmup=2, trials=3, rounds=2, tol=0.02, log=None, graph=True,
+         starts=()):
     """Coordinate descent over `space` from `start` (default: the current parameters).
 
     step() runs one step of the workload (it must plan through the cached
     plan functions, so that it re-plans after every parameter change, and
-    be capturable in a CUDA graph when `graph`).  Returns (parameters, ms
-    per step, history); the parameters are installed.
+    be capturable in a CUDA graph when `graph`).  `starts` are further
+    starting points (e.g. an earlier table entry): the descent begins at the
+    fastest of them, so a search never ends worse than a known point.
+    Returns (parameters, ms per step, history); the parameters are installed.
     """
     space = SPACE if space is None else space
     base = dict(st.tune_get() if start is None else start)
@@ -113,6 +116,11 @@ def tune(step, space=None, start=None, reps=5, warmup=2, trials=3, rounds=2, tol
     best = measure(base)
     if best is None:
         raise ValueError("starting parameters are out of range")
+    for other in starts:
+        cand = dict(base, **other)
+        ms = measure(cand)
+        if ms is not None and ms < best:
+            base, best = cand, ms
     for _ in range(rounds):
         improved = False
         for name, values in space.items():
