@@ -421,18 +421,27 @@ WORKLOADS = {"u1_mps_heff": MPSWorkload, "su2_recouple": SU2Workload, "u1_two_si
 # ---------------------------------------------------------------- roofline ---
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
-# each kernel over one step of this workload, from one ncu pass on the bench
-# command (profiles/traffic_u1_mps_heff.md), with the SHA-256 of the kernel's
-# sources at that time: once a source changes, the figure no longer applies
-# and the bench reports null.
+# the dominant kernels of each workload, from one ncu pass (profiles/), with
+# the SHA-256 of the kernel's sources at that time: once a source changes, the
+# figure no longer applies and the bench reports null.  "ratio" entries come
+# from a smaller case of the same workload: DRAM bytes / algorithmic bytes of
+# the captured launches, applied to the full launch's algorithmic bytes.
 TRAFFIC = {
-    "box_flat": {"bytes_per_launch": 8914432, "sha": "2051b6c5a77d9fe4"},
-    "box": {"bytes_per_launch": 8430848, "sha": "2051b6c5a77d9fe4"},
-    "gemm_tc": {"bytes_per_launch": 12505728, "sha": "4bfc4e6cd1d23db5"},
-    "gemm_tile": {"bytes_per_launch": 807360, "sha": "8ee88fc5d4527c52"},
-    "gemm_rows": {"bytes_per_launch": 3203789, "sha": "8ee88fc5d4527c52"},
-    "gemm_thin": {"bytes_per_launch": 3170406, "sha": "8ee88fc5d4527c52"},
-    "gemm_wide": {"bytes_per_launch": 71168, "sha": "8ee88fc5d4527c52"},
+    "u1_mps_heff": {  # profiles/traffic_u1_mps_heff.md
+        "box_flat": {"bytes_per_launch": 8020045, "sha": "74ba81806ea8ef80"},
+        "box": {"bytes_per_launch": 7493888, "sha": "74ba81806ea8ef80"},
+        "gemm_tc": {"bytes_per_launch": 13579712, "sha": "9b1e09588d5fca4d"},
+        "gemm_rows": {"bytes_per_launch": 3177216, "sha": "7dca7cc9913fd694"},
+        "gemm_thin": {"bytes_per_launch": 3174963, "sha": "7dca7cc9913fd694"},
+        "gemm_wide": {"bytes_per_launch": 70997, "sha": "7dca7cc9913fd694"},
+        "gemm_tile": {"bytes_per_launch": 44971, "sha": "7dca7cc9913fd694"},
+    },
+    "su2_recouple": {  # profiles/gemm_tc_su2_recouple.md (full size, forward and backward launches)
+        "gemm_tc": {"bytes_per_launch": 61084875776, "sha": "9b1e09588d5fca4d"},
+    },
+    "u1_two_site_batch": {  # profiles/direct_u1_two_site_batch.md (128 of the 512 problems)
+        "direct": {"ratio": 0.95, "sha": "10db12e88424ae88"},
+    },
 }
 KERNEL_SOURCES = {
     "box": ["box.cu", "kernels.h", "pdl.h"], "box_flat": ["box.cu", "kernels.h", "pdl.h"],
@@ -452,7 +461,7 @@ def kernel_source_sha(kern):
     return h.hexdigest()[:16]
 
 
-def roofline(prof, clk, sustained=False):
+def roofline(prof, clk, sustained=False, workload="u1_mps_heff"):
     """Roofline of the kernel with the largest summed device time.
 
     box kernels, the direct kernel and the rows / thin GEMMs: HBM-bound,
@@ -484,8 +493,10 @@ def roofline(prof, clk, sustained=False):
         bound, unit, per = "alu", "TFLOP/s", d["flops"] / n
         achieved, peak = per / sec / 1e12, 152 * 128 * 2 * mhz * 1e6 / 1e12
         src = "152 SMs x 128 FP32 FMA/clk x 2 flops x sampled SM clock"
-    t = TRAFFIC.get(dom)
-    traffic = t["bytes_per_launch"] if t and t["sha"] == kernel_source_sha(dom) else None
+    t = TRAFFIC.get(workload, {}).get(dom)
+    traffic = None
+    if t and t["sha"] == kernel_source_sha(dom):
+        traffic = t["bytes_per_launch"] if "bytes_per_launch" in t else round(t["ratio"] * d["bytes"] / n)
     return {"bound": bound, "kernel": dom, "symbol": __import__("paper_1203_2222_gb300").KERNEL_SYMBOLS[dom],
             "achieved": round(achieved, 4), "peak": round(peak, 1), "unit": unit, "frac": round(achieved / peak, 4),
             "traffic": traffic, "algorithmic_per_launch": per, "launches_timed": d["launches"],
@@ -720,7 +731,7 @@ def run_ours(args, rank, world):
     # the whole step: T_roof = max(useful flops / tensor peak, algorithmic
     # bytes / HBM bandwidth) against the measured step time
     long_step = ms_per_step > 20.0  # seconds-long timed region: the power cap applies
-    roof = roofline(prof, clk, sustained=long_step)
+    roof = roofline(prof, clk, sustained=long_step, workload=args.workload)
     peaks, peak_src = load_peaks()
     p_tensor = (peaks["bf16_tflops_sustained"] if long_step else peaks["bf16_tflops"]) / 3.0
     t_flop = flops / (p_tensor * 1e12)
