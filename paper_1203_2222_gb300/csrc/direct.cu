@@ -15,9 +15,10 @@
 //          warp with butterfly shuffles and added into the zero-filled
 //          gradient blocks with atomics
 //
-// Persistent and warp-independent: a warp copies one 128-byte descriptor into
-// its shared-memory slot, stages the item's coefficients and column pointers
-// in registers, and streams the box with coalesced loads along its last dim.
+// Persistent and warp-independent: a warp copies one 512-byte descriptor
+// (columns inline) into its shared-memory slot while the previous item runs,
+// stages the item's coefficients and column pointers in registers, and
+// streams the box with coalesced loads along its last dim.
 // Apply and outer items run as separate launches of their own kernels (every
 // item of a launch has the same kind).
 #include <cuda_runtime.h>
@@ -56,13 +57,6 @@ __device__ __forceinline__ void cp_wait() {
 }
 
 template <typename T>
-__device__ __forceinline__ T coef_of(const Term& t);
-template <>
-__device__ __forceinline__ float coef_of<float>(const Term& t) { return t.coef_f; }
-template <>
-__device__ __forceinline__ double coef_of<double>(const Term& t) { return t.coef; }
-
-template <typename T>
 __device__ __forceinline__ const T* src_ptr(const BoxPtrs& p, int slot) {
   return static_cast<const T*>(slot == 0 ? p.src[0] : slot == 1 ? p.src[1] : slot == 2 ? p.src[2] : p.src[3]);
 }
@@ -98,23 +92,19 @@ struct DirectShape {
   }
 };
 
-// Columns of one side of an item: column c at box index t is base[c][<t, str[c]>],
-// with str[c][d] = ld_c * a[d] + b[d] folded once per item (the relative
-// offset stays below 2^31 -- host check -- so it is formed in 32 bits).
+// Columns of one side of an item: column c at box index t is base[c][<t, str[c]>]
+// (the relative offset stays below 2^31 -- host check -- so it is formed in 32 bits).
 template <typename P, int NC, int ND>
 struct Cols {
   P base[NC];
   int str[NC][ND];
-  __device__ __forceinline__ void load(P slot, const Term* __restrict__ terms, int t0, int n, const int* a,
-                                       const int* b) {
+  __device__ __forceinline__ void load(P slot, const DirectCol* cols, int n) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const bool on = c < n;
-      const Term t = terms[t0 + (on ? c : 0)];
-      base[c] = slot + t.off;
-      const int ld = on ? (int)t.ld : 0;
+      base[c] = slot + cols[on ? c : 0].off;
 #pragma unroll
-      for (int d = 0; d < ND; ++d) str[c][d] = on ? ld * a[d] + b[d] : 0;
+      for (int d = 0; d < ND; ++d) str[c][d] = on ? cols[c].str[d] : 0;
     }
   }
   __device__ __forceinline__ int off(int c, const int (&t)[ND]) const {
@@ -126,28 +116,21 @@ struct Cols {
 };
 
 // apply: NS source and NQ destination columns (exact counts when the item has
-// them, else upper bounds with the actual counts ns <= NS, nq <= NQ)
+// them, else upper bounds with the actual counts ns <= NS, nq <= NQ); the
+// coefficient values are in this warp's cf[d * kMaxDirect + s]
 template <typename T, int ND, int NS, int NQ>
-__device__ __forceinline__ void apply_item(const DirectItem& it, const Term* __restrict__ terms, const BoxPtrs& ptrs,
+__device__ __forceinline__ void apply_item(const DirectItem& it, const T* __restrict__ cfv, const BoxPtrs& ptrs,
                                            int lane, T* __restrict__ stage) {
   const int ns = it.ns, nq = it.nd;
-  const T* __restrict__ ksrc = src_ptr<T>(ptrs, (it.slots >> 2) & 3);
   Cols<const T*, NS, ND> S;
   Cols<T*, NQ, ND> Q;
-  S.load(src_ptr<T>(ptrs, it.slots & 3), terms, it.ts, ns, it.sa, it.sb);
-  Q.load(dst_ptr<T>(ptrs, (it.slots >> 4) & 7), terms, it.td, nq, it.da, it.db);
+  S.load(src_ptr<T>(ptrs, it.slots & 3), it.src, ns);
+  Q.load(dst_ptr<T>(ptrs, (it.slots >> 4) & 7), it.dst, nq);
   T cf[NQ][NS];
 #pragma unroll
   for (int d = 0; d < NQ; ++d)
 #pragma unroll
-    for (int c = 0; c < NS; ++c) {
-      cf[d][c] = T(0);
-      if (d < nq && c < ns) {
-        const Term t = terms[it.tk + d * it.kd + c * it.ks];
-        const T k = coef_of<T>(t);
-        if (k != T(0)) cf[d][c] = k * __ldg(ksrc + t.off);
-      }
-    }
+    for (int c = 0; c < NS; ++c) cf[d][c] = (d < nq && c < ns) ? cfv[d * kMaxDirect + c] : T(0);
   const DirectShape<ND> sh(it);
   const int last = it.start + it.count - 1;
   constexpr int H = kH<T>;
@@ -194,16 +177,17 @@ __device__ __forceinline__ void apply_item(const DirectItem& it, const Term* __r
   }
 }
 
-// outer: out(s, d) += sum_t A_s[t] dC_d[t] over the item's positions
+// outer: out(s, d) = sum_t A_s[t] dC_d[t] over the item's positions, scaled
+// by kc and added into the destination at koff
 template <typename T, int ND, int NS, int NQ>
-__device__ __forceinline__ void outer_item(const DirectItem& it, const Term* __restrict__ terms, const BoxPtrs& ptrs,
-                                           int lane, T* __restrict__ stage) {
+__device__ __forceinline__ void outer_item(const DirectItem& it, const BoxPtrs& ptrs, int lane,
+                                           T* __restrict__ stage) {
   const int ns = it.ns, nq = it.nd;
   T* __restrict__ dst = dst_ptr<T>(ptrs, (it.slots >> 4) & 7);
   Cols<const T*, NS, ND> S;
   Cols<const T*, NQ, ND> Q;
-  S.load(src_ptr<T>(ptrs, it.slots & 3), terms, it.ts, ns, it.sa, it.sb);
-  Q.load(src_ptr<T>(ptrs, (it.slots >> 2) & 3), terms, it.td, nq, it.da, it.db);
+  S.load(src_ptr<T>(ptrs, it.slots & 3), it.src, ns);
+  Q.load(src_ptr<T>(ptrs, (it.slots >> 2) & 3), it.dst, nq);
   T acc[NS][NQ];
 #pragma unroll
   for (int c = 0; c < NS; ++c)
@@ -269,57 +253,72 @@ __device__ __forceinline__ void outer_item(const DirectItem& it, const Term* __r
 #pragma unroll
       for (int d = 0; d < NQ; ++d)
         if (c == c0 && d == d0) v = acc[c][d];
-    const Term t = terms[it.tk + d0 * it.kd + c0 * it.ks];
-    const T k = coef_of<T>(t);
-    if (k != T(0)) atomicAdd(dst + t.off, k * v);
+    const int e = d0 * kMaxDirect + c0;
+    const double k = it.kc[e];
+    if (k != 0.0) atomicAdd(dst + it.koff[e], T(k) * v);
   }
 }
 
 // the item's column counts pick an exact variant (the MPO and physical legs
 // of a tensor network give 1 or 4 columns per side), else the bounded one
 template <typename T, int kOp, int ND>
-__device__ __forceinline__ void run_item(const DirectItem& it, const Term* __restrict__ terms, const BoxPtrs& ptrs,
+__device__ __forceinline__ void run_item(const DirectItem& it, const T* __restrict__ cfv, const BoxPtrs& ptrs,
                                          int lane, T* __restrict__ stage) {
   const int key = ND == 3 ? 0 : it.ns * 8 + it.nd;  // three-dim boxes take the bounded variant only
   if (kOp == kDirectApply) {
-    if (key == 4 * 8 + 4) apply_item<T, ND, 4, 4>(it, terms, ptrs, lane, stage);
-    else if (key == 1 * 8 + 1) apply_item<T, ND, 1, 1>(it, terms, ptrs, lane, stage);
-    else if (key == 1 * 8 + 4) apply_item<T, ND, 1, 4>(it, terms, ptrs, lane, stage);
-    else if (key == 4 * 8 + 1) apply_item<T, ND, 4, 1>(it, terms, ptrs, lane, stage);
-    else apply_item<T, ND, kMaxDirect, kMaxDirect>(it, terms, ptrs, lane, stage);
+    if (key == 4 * 8 + 4) apply_item<T, ND, 4, 4>(it, cfv, ptrs, lane, stage);
+    else if (key == 1 * 8 + 1) apply_item<T, ND, 1, 1>(it, cfv, ptrs, lane, stage);
+    else if (key == 1 * 8 + 4) apply_item<T, ND, 1, 4>(it, cfv, ptrs, lane, stage);
+    else if (key == 4 * 8 + 1) apply_item<T, ND, 4, 1>(it, cfv, ptrs, lane, stage);
+    else apply_item<T, ND, kMaxDirect, kMaxDirect>(it, cfv, ptrs, lane, stage);
   } else {
-    if (key == 4 * 8 + 4) outer_item<T, ND, 4, 4>(it, terms, ptrs, lane, stage);
-    else if (key == 1 * 8 + 1) outer_item<T, ND, 1, 1>(it, terms, ptrs, lane, stage);
-    else if (key == 1 * 8 + 4) outer_item<T, ND, 1, 4>(it, terms, ptrs, lane, stage);
-    else if (key == 4 * 8 + 1) outer_item<T, ND, 4, 1>(it, terms, ptrs, lane, stage);
-    else outer_item<T, ND, kMaxDirect, kMaxDirect>(it, terms, ptrs, lane, stage);
+    if (key == 4 * 8 + 4) outer_item<T, ND, 4, 4>(it, ptrs, lane, stage);
+    else if (key == 1 * 8 + 1) outer_item<T, ND, 1, 1>(it, ptrs, lane, stage);
+    else if (key == 1 * 8 + 4) outer_item<T, ND, 1, 4>(it, ptrs, lane, stage);
+    else if (key == 4 * 8 + 1) outer_item<T, ND, 4, 1>(it, ptrs, lane, stage);
+    else outer_item<T, ND, kMaxDirect, kMaxDirect>(it, ptrs, lane, stage);
   }
 }
 
-// One kernel per item kind, so that each gets the registers of its own loop
-// (the apply loop keeps 8 positions x 4 columns of loads in flight per lane).
+// One kernel per item kind, so that each gets the registers of its own loop.
+// A warp keeps the next item's descriptor in flight (one 16-byte load per
+// lane) while it runs the current one, so an item's set-up costs one round
+// trip: the apply coefficients, loaded by one lane each.
 template <typename T, int kOp>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) direct_kernel(const DirectItem* __restrict__ items, int nitems,
-                                                          const Term* __restrict__ terms, BoxPtrs ptrs) {
-  constexpr int kWords = sizeof(DirectItem) / 4;
-  static_assert(kWords <= 32, "one descriptor word per lane");
-  __shared__ uint32_t desc[kWarps][kWords];
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
+    direct_kernel(const DirectItem* __restrict__ items, int nitems, BoxPtrs ptrs) {
+  static_assert(sizeof(DirectItem) == 32 * sizeof(int4), "one 16-byte descriptor word per lane");
+  __shared__ __align__(16) DirectItem desc[kWarps];
+  __shared__ T cfs[kWarps][kMaxDirect * kMaxDirect];
   extern __shared__ __align__(16) unsigned char dyn[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T* stage = reinterpret_cast<T*>(dyn + (size_t)warp * 2 * kStageBytes);
+  const int stride = gridDim.x * kWarps;
+  int w = blockIdx.x * kWarps + warp;
+  int4 next = make_int4(0, 0, 0, 0);
+  if (w < nitems) next = __ldg(reinterpret_cast<const int4*>(items + w) + lane);
   pdl_wait();
   pdl_launch_dependents();
-  for (int w = blockIdx.x * kWarps + warp; w < nitems; w += gridDim.x * kWarps) {
+  for (; w < nitems; w += stride) {
     __syncwarp();
-    if (lane < kWords) desc[warp][lane] = reinterpret_cast<const uint32_t*>(items + w)[lane];
+    reinterpret_cast<int4*>(desc + warp)[lane] = next;
     __syncwarp();
-    const DirectItem& it = *reinterpret_cast<const DirectItem*>(desc[warp]);
+    if (w + stride < nitems) next = __ldg(reinterpret_cast<const int4*>(items + w + stride) + lane);
+    const DirectItem& it = desc[warp];
+    if (kOp == kDirectApply) {  // coefficient values, one lane each
+      const T* __restrict__ ksrc = src_ptr<T>(ptrs, (it.slots >> 2) & 3);
+      if (lane < kMaxDirect * kMaxDirect) {
+        const double k = it.kc[lane];
+        cfs[warp][lane] = k != 0.0 ? T(k) * __ldg(ksrc + it.koff[lane]) : T(0);
+      }
+      __syncwarp();
+    }
     if (it.ndim == 1)
-      run_item<T, kOp, 1>(it, terms, ptrs, lane, stage);
+      run_item<T, kOp, 1>(it, cfs[warp], ptrs, lane, stage);
     else if (it.ndim == 2)
-      run_item<T, kOp, 2>(it, terms, ptrs, lane, stage);
+      run_item<T, kOp, 2>(it, cfs[warp], ptrs, lane, stage);
     else
-      run_item<T, kOp, 3>(it, terms, ptrs, lane, stage);
+      run_item<T, kOp, 3>(it, cfs[warp], ptrs, lane, stage);
   }
 }
 
@@ -339,22 +338,21 @@ int ctas_per_sm() {
 }
 
 template <typename T, int kOp>
-int launch_op(const DirectItem* items, int nitems, const Term* terms, const BoxPtrs& ptrs, cudaStream_t s) {
+int launch_op(const DirectItem* items, int nitems, const BoxPtrs& ptrs, cudaStream_t s) {
   if (nitems <= 0) return 0;
   const int ctas = std::min((nitems + kWarps - 1) / kWarps, tc_num_sms() * ctas_per_sm<T, kOp>());
-  return (int)launch_pdl(direct_kernel<T, kOp>, dim3(ctas), dim3(kThreads), kDynSmem, s, items, nitems, terms, ptrs);
+  return (int)launch_pdl(direct_kernel<T, kOp>, dim3(ctas), dim3(kThreads), kDynSmem, s, items, nitems, ptrs);
 }
 
 }  // namespace
 
-int launch_direct(bool f64, int op, const DirectItem* items, int nitems, const Term* terms, const BoxPtrs& ptrs,
-                  void* stream) {
+int launch_direct(bool f64, int op, const DirectItem* items, int nitems, const BoxPtrs& ptrs, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (op == kDirectApply)
-    return f64 ? launch_op<double, kDirectApply>(items, nitems, terms, ptrs, s)
-               : launch_op<float, kDirectApply>(items, nitems, terms, ptrs, s);
-  return f64 ? launch_op<double, kDirectOuter>(items, nitems, terms, ptrs, s)
-             : launch_op<float, kDirectOuter>(items, nitems, terms, ptrs, s);
+    return f64 ? launch_op<double, kDirectApply>(items, nitems, ptrs, s)
+               : launch_op<float, kDirectApply>(items, nitems, ptrs, s);
+  return f64 ? launch_op<double, kDirectOuter>(items, nitems, ptrs, s)
+             : launch_op<float, kDirectOuter>(items, nitems, ptrs, s);
 }
 
 }  // namespace sym

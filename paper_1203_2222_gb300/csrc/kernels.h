@@ -143,32 +143,40 @@ struct TcOperand {
 
 // Direct contraction of a sector whose matrix on one side is tiny (k, n <=
 // kMaxDirect): the GEMM runs on the tensors' blocks themselves, with no
-// matrix form.  A position t of the box (the free legs of the large operand)
-// holds, for source column s, the element at src + off_s + ld_s <t, sa> +
-// <t, sb>, and for destination column d the element at dst + off_d + ld_d
-// <t, da> + <t, db> (off, ld: terms ts + s, td + d).  Coefficient (d, s) is
-// coef * slot2[off] of term tk + d kd + s ks.
-//   apply: dst_d[t] = sum_s coefficient(d, s) src_s[t]           (C = A B, dA = dC B^T)
-//   outer: out(s, d) += sum_t src_s[t] * src2_d[t], the destination columns
-//          read from slot 2 and the sums added (atomically) into the
-//          destination slot at the coefficient terms' offsets      (dB = A^T dC)
+// matrix form.  An item is a chunk [start, start + count) of the positions t
+// of a row group's box (the free legs of the large operand, ndim <= 3 dims,
+// last fastest).  Its columns are inline: source column s holds, at
+// position t, the element at src_slot + src[s].off + <t, src[s].str>, and
+// destination column d the element at dst + dst[d].off + <t, dst[d].str>.
+//   apply: dst_d[t] = sum_s kc[d][s] * slot2[koff[d][s]] * src_s[t]       (C = A B, dA = dC B^T)
+//   outer: out(s, d) = sum_t src_s[t] * slot2_d[t], the d columns read from
+//          slot 2; kc[d][s] * out(s, d) is added (atomically) to the
+//          destination slot at koff[d][s]                                (dB = A^T dC)
+// kc == 0 marks a structurally absent coefficient.  An item is 512 bytes,
+// one 16-byte load per lane.
 constexpr int kMaxDirect = 4;
 constexpr int kDirectDims = 3;
-constexpr int kDirectApplyChunk = 1024;  // positions per apply item
-constexpr int kDirectOuterChunk = 8192;  // positions per outer item (one set of atomics each)
+constexpr int kDirectApplyChunk = 1024;  // default positions per apply item
 enum DirectOp { kDirectApply = 0, kDirectOuter = 1 };
+struct DirectCol {
+  int64_t off;
+  int32_t str[kDirectDims];
+  int32_t pad_;
+};
 struct DirectItem {
   int32_t op, ns, nd, ndim;
   int32_t start, count;
-  int32_t ts, td, tk;  // first term of the sources, destinations, coefficients
-  int32_t kd, ks;      // coefficient (d, s) is term tk + d * kd + s * ks
-  int32_t slots;       // bits 0-1 source slot, 2-3 second source slot, 4-6 destination slot
-  int32_t dims[kDirectDims], sa[kDirectDims], sb[kDirectDims], da[kDirectDims], db[kDirectDims];
+  int32_t slots;  // bits 0-1 source slot, 2-3 second source slot, 4-6 destination slot
+  int32_t shf;    // the three division shifts, one byte each
+  int32_t dims[kDirectDims];
   uint32_t mag[kDirectDims];  // Granlund-Montgomery division by dims[d] (as in BoxItem)
-  int32_t shf;                // the three shifts, one byte each
-  int32_t pad_;
+  int32_t pad_[2];
+  DirectCol src[kMaxDirect], dst[kMaxDirect];
+  int64_t koff[kMaxDirect * kMaxDirect];  // [d * kMaxDirect + s]
+  double kc[kMaxDirect * kMaxDirect];
 };
-static_assert(sizeof(DirectItem) == 128, "DirectItem layout");
+static_assert(sizeof(DirectCol) == 24, "DirectCol layout");
+static_assert(sizeof(DirectItem) == 512, "DirectItem layout");
 
 // CUDA-core GEMM tile shapes
 enum SimtShape { SIMT_64x64 = 0, SIMT_256x16 = 1, SIMT_THIN = 2, SIMT_ROWS = 3, SIMT_SHAPES = 4 };
@@ -180,8 +188,7 @@ int launch_box(bool src_f64, bool dst_f64, bool flat_only, const BoxItem* items,
 int launch_gemm_simt(bool f64, int shape, const GemmSectorSimt* secs, const GemmTile* tiles, int ntiles,
                      const void* ops, void* outm, void* stream);
 // every item of [items, items + nitems) must have op == `op`
-int launch_direct(bool f64, int op, const DirectItem* items, int nitems, const Term* terms, const BoxPtrs& ptrs,
-                  void* stream);
+int launch_direct(bool f64, int op, const DirectItem* items, int nitems, const BoxPtrs& ptrs, void* stream);
 int launch_gemm_tc(const TcSector* secs, const GemmTile* tiles, int ntiles, const TensorMap* maps, float* C,
                    int* err_word, void* stream);
 // Tensor map of one operand whose hi plane starts at `hi` (bf16) and whose lo

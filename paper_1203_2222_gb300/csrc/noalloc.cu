@@ -85,7 +85,6 @@ extern "C" int sym_contract_noalloc(sym_tensor A, sym_tensor B, int npairs, cons
     const size_t o_items = region(p.items.size() * sizeof(BoxItem));
     const size_t o_terms = region(p.terms.size() * sizeof(Term));
     const size_t o_ditems = region(p.ditems.size() * sizeof(DirectItem));
-    const size_t o_dterms = region(p.dterms.size() * sizeof(Term));
     const size_t o_simt = region(p.secs_simt.size() * sizeof(GemmSectorSimt));
     const size_t o_tc = region(p.secs_tc.size() * sizeof(TcSector));
     const size_t o_tiles = region(p.tiles.size() * sizeof(GemmTile));
@@ -113,7 +112,6 @@ extern "C" int sym_contract_noalloc(sym_tensor A, sym_tensor B, int npairs, cons
     copy(o_items, p.items.data(), p.items.size() * sizeof(BoxItem));
     copy(o_terms, p.terms.data(), p.terms.size() * sizeof(Term));
     copy(o_ditems, p.ditems.data(), p.ditems.size() * sizeof(DirectItem));
-    copy(o_dterms, p.dterms.data(), p.dterms.size() * sizeof(Term));
     copy(o_simt, p.secs_simt.data(), p.secs_simt.size() * sizeof(GemmSectorSimt));
     copy(o_tc, p.secs_tc.data(), p.secs_tc.size() * sizeof(TcSector));
     copy(o_tiles, p.tiles.data(), p.tiles.size() * sizeof(GemmTile));
@@ -127,7 +125,6 @@ extern "C" int sym_contract_noalloc(sym_tensor A, sym_tensor B, int npairs, cons
     p.d_items = reinterpret_cast<BoxItem*>(base + o_items);
     p.d_terms = reinterpret_cast<Term*>(base + o_terms);
     p.d_ditems = reinterpret_cast<DirectItem*>(base + o_ditems);
-    p.d_dterms = reinterpret_cast<Term*>(base + o_dterms);
     p.d_secs_simt = reinterpret_cast<GemmSectorSimt*>(base + o_simt);
     p.d_secs_tc = reinterpret_cast<TcSector*>(base + o_tc);
     p.d_tiles = reinterpret_cast<GemmTile*>(base + o_tiles);

@@ -639,7 +639,6 @@ void Plan::upload(bool device) {
   d_secs_tc = static_cast<TcSector*>(up(secs_tc.data(), secs_tc.size() * sizeof(TcSector)));
   d_tiles = static_cast<GemmTile*>(up(tiles.data(), tiles.size() * sizeof(GemmTile)));
   d_ditems = static_cast<DirectItem*>(up(ditems.data(), ditems.size() * sizeof(DirectItem)));
-  d_dterms = static_cast<Term*>(up(dterms.data(), dterms.size() * sizeof(Term)));
   if (kind == CONTRACT) {
     const size_t es = f64() ? sizeof(double) : sizeof(float);
     if (img_elems > 0) {  // hi and lo planes; the TMA loads fill past-the-edge boxes with zeros
@@ -998,10 +997,10 @@ void validate_gemms(const Plan& P, bool f64) {
 
 // Direct items stay inside the tensors they address: numel_a (A, dA),
 // numel_b (B, dB), numel_c (C, dC); strides non-negative, so the extreme of
-// every column is at the last index of every dim.
+// every column is at the last index of every dim, and each column's span
+// stays below 2^31 (the kernel forms it in 32 bits).
 void validate_direct(const Plan& P) {
   const int64_t ne[3] = {P.numel_a, P.numel_b, P.numel_c};
-  if (P.dterm_space.size() != P.dterms.size()) fail(SYM_ERR_ARG, "internal: direct term spaces missing");
   // tensor of a source slot (0 A, 1 B, 2 dC) and of a destination slot
   auto src_space = [](int slot) { return slot == 0 ? 0 : slot == 1 ? 1 : slot == 2 ? 2 : -1; };
   auto dst_space = [](int slot) { return slot == DST_OUT ? 2 : slot == DST_DA ? 0 : slot == DST_DB ? 1 : -1; };
@@ -1019,43 +1018,40 @@ void validate_direct(const Plan& P) {
     if ((it.op != kDirectApply && it.op != kDirectOuter) || it.ns < 1 || it.nd < 1 || it.ns > kMaxDirect ||
         it.nd > kMaxDirect || it.ndim < 1 || it.ndim > kDirectDims || it.start < 0 || it.count < 1)
       fail(SYM_ERR_ARG, "internal: bad direct item");
-    int64_t sa = 0, sb = 0, da = 0, db = 0, total = 1;
+    int64_t total = 1;
     for (int d = 0; d < kDirectDims; ++d) {
-      if (it.dims[d] < 1 || it.sa[d] < 0 || it.sb[d] < 0 || it.da[d] < 0 || it.db[d] < 0)
-        fail(SYM_ERR_ARG, "internal: negative stride or empty dim in a direct item");
-      if (d >= it.ndim && (it.dims[d] != 1 || it.sa[d] || it.sb[d] || it.da[d] || it.db[d]))
-        fail(SYM_ERR_ARG, "internal: unused dim of a direct item is not a unit dim");
+      if (it.dims[d] < 1 || (d >= it.ndim && it.dims[d] != 1))
+        fail(SYM_ERR_ARG, "internal: bad dim in a direct item");
       uint32_t m;
       int8_t sh;
       div_magic(it.dims[d], m, sh);
       if (m != it.mag[d] || sh != (int8_t)((it.shf >> (8 * d)) & 0xff))
         fail(SYM_ERR_ARG, "internal: stale division constants in a direct item");
-      sa += (int64_t)(it.dims[d] - 1) * it.sa[d];
-      sb += (int64_t)(it.dims[d] - 1) * it.sb[d];
-      da += (int64_t)(it.dims[d] - 1) * it.da[d];
-      db += (int64_t)(it.dims[d] - 1) * it.db[d];
       total *= it.dims[d];
     }
-    if (sa >= ((int64_t)1 << 31) || sb >= ((int64_t)1 << 31) || da >= ((int64_t)1 << 31) ||
-        db >= ((int64_t)1 << 31) || (int64_t)it.start + it.count > total)
-      fail(SYM_ERR_ARG, "internal: direct item past its box");
+    if ((int64_t)it.start + it.count > total) fail(SYM_ERR_ARG, "internal: direct item past its box");
     const int s1 = it.slots & 3, s2 = (it.slots >> 2) & 3, ds = (it.slots >> 4) & 7;
     const int sp = src_space(s1);
     const int qp = it.op == kDirectApply ? dst_space(ds) : src_space(s2);  // space of the d columns
-    const int kp = it.op == kDirectApply ? src_space(s2) : dst_space(ds);  // space of the coefficient terms
-    if (sp < 0 || qp < 0 || kp < 0) fail(SYM_ERR_ARG, "internal: bad slot in a direct item");
-    auto check = [&](int t, int space, int64_t ma, int64_t mb) {
-      if (t < 0 || t >= (int)P.dterms.size() || P.dterm_space[t] != space)
-        fail(SYM_ERR_ARG, "internal: direct term out of range");
-      const Term& x = P.dterms[t];
-      if (x.off < 0 || x.ld < 0 || x.ld >= ((int64_t)1 << 31) || x.off + x.ld * ma + mb >= ne[space] ||
-          x.ld * ma + mb >= ((int64_t)1 << 31))  // relative offsets are formed in 32 bits
+    const int kp = it.op == kDirectApply ? src_space(s2) : dst_space(ds);  // space of the coefficient offsets
+    if (sp < 0 || qp < 0 || kp != 1) fail(SYM_ERR_ARG, "internal: bad slot in a direct item");
+    auto check = [&](const DirectCol& c, int space) {
+      int64_t span = 0;
+      for (int d = 0; d < kDirectDims; ++d) {
+        if (c.str[d] < 0 || (d >= it.ndim && c.str[d] != 0)) fail(SYM_ERR_ARG, "internal: bad direct column stride");
+        span += (int64_t)(it.dims[d] - 1) * c.str[d];
+      }
+      if (c.off < 0 || span >= ((int64_t)1 << 31) || c.off + span >= ne[space])
         fail(SYM_ERR_ARG, "internal: direct item addresses past its tensor");
     };
-    for (int s = 0; s < it.ns; ++s) check(it.ts + s, sp, sa, sb);
-    for (int d = 0; d < it.nd; ++d) check(it.td + d, qp, da, db);
-    for (int d = 0; d < it.nd; ++d)
-      for (int s = 0; s < it.ns; ++s) check(it.tk + d * it.kd + s * it.ks, kp, 0, 0);
+    for (int c = 0; c < it.ns; ++c) check(it.src[c], sp);
+    for (int c = 0; c < it.nd; ++c) check(it.dst[c], qp);
+    for (int e = 0; e < kMaxDirect * kMaxDirect; ++e) {
+      const int d = e / kMaxDirect, c = e % kMaxDirect;
+      if (it.kc[e] == 0.0) continue;
+      if (d >= it.nd || c >= it.ns || it.koff[e] < 0 || it.koff[e] >= ne[kp])
+        fail(SYM_ERR_ARG, "internal: direct coefficient past its tensor");
+    }
   }
 }
 
@@ -1257,9 +1253,6 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
         });
       }
       std::vector<DirectItem> f, ba, bb;
-      std::vector<Term> terms;
-      std::vector<int8_t> space;
-      const int tbase = (int)P->dterms.size();
       for (auto& rk : arow[x]) {
         std::vector<Col> ac, cc;
         std::vector<int> fd(na, 1);
@@ -1345,67 +1338,62 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
         if (total >= ((int64_t)1 << 31) || span * kDirectDims >= ((int64_t)1 << 31)) return false;
         const int ns = (int)ac.size(), nd = (int)cc.size();
         for (auto& o : origins) {
-          const int ta = tbase + (int)terms.size();
+          // inline column records: A side (source of the forward and of dB,
+          // destination of dA), C side (destination of the forward, source
+          // of dA, second source of dB); coefficient (c, j) = B_x[c][j]
+          DirectCol acol[kMaxDirect] = {}, ccol[kMaxDirect] = {};
           for (int c = 0; c < ns; ++c) {
-            terms.push_back(Term{o.first[c], ald[c], 1.0, 1.0f, 0});
-            space.push_back(0);
+            acol[c].off = o.first[c];
+            for (int d = 0; d < box.ndim; ++d) acol[c].str[d] = (int32_t)(ald[c] * box.sa[d] + box.sb[d]);
           }
-          const int tc = tbase + (int)terms.size();
           for (int j = 0; j < nd; ++j) {
-            terms.push_back(Term{o.second[j], cld[j], 1.0, 1.0f, 0});
-            space.push_back(2);
+            ccol[j].off = o.second[j];
+            for (int d = 0; d < box.ndim; ++d) ccol[j].str[d] = (int32_t)(cld[j] * box.da[d] + box.db[d]);
           }
-          const int tk = tbase + (int)terms.size();
-          for (int c = 0; c < ns; ++c)
-            for (int j = 0; j < nd; ++j) {
-              const int64_t e = ac[c].idx * g.n + cc[j].idx;
-              terms.push_back(Term{koff[e], 0, kcoef[e], (float)kcoef[e], 0});
-              space.push_back(1);
-            }
-          auto item = [&](int op, int ins, int ind, int ts, int td, int kd, int ks, int slots, bool swap,
-                          int64_t st0, int64_t cnt) {
+          auto item = [&](int op, bool a_src, int slots, int64_t st0, int64_t cnt) {
             DirectItem it{};
             it.op = op;
-            it.ns = ins;
-            it.nd = ind;
+            it.ns = a_src ? ns : nd;
+            it.nd = a_src ? nd : ns;
             it.ndim = box.ndim;
             it.start = (int)st0;
             it.count = (int)cnt;
-            it.ts = ts;
-            it.td = td;
-            it.tk = tk;
-            it.kd = kd;
-            it.ks = ks;
             it.slots = slots;
             for (int d = 0; d < kDirectDims; ++d) {
-              const bool on = d < box.ndim;
-              it.dims[d] = on ? box.dims[d] : 1;
-              it.sa[d] = on ? (swap ? box.da[d] : box.sa[d]) : 0;
-              it.sb[d] = on ? (swap ? box.db[d] : box.sb[d]) : 0;
-              it.da[d] = on ? (swap ? box.sa[d] : box.da[d]) : 0;
-              it.db[d] = on ? (swap ? box.sb[d] : box.db[d]) : 0;
+              it.dims[d] = d < box.ndim ? box.dims[d] : 1;
               int8_t sh;
               div_magic(it.dims[d], it.mag[d], sh);
               it.shf |= (int)(uint8_t)sh << (8 * d);
             }
+            for (int c = 0; c < kMaxDirect; ++c) {
+              it.src[c] = a_src ? acol[c] : ccol[c];
+              it.dst[c] = a_src ? ccol[c] : acol[c];
+            }
+            // coefficient (d, s): the item's d-th destination and s-th source
+            for (int d = 0; d < it.nd; ++d)
+              for (int s2 = 0; s2 < it.ns; ++s2) {
+                const int c = a_src ? s2 : d, j = a_src ? d : s2;
+                const int64_t e = ac[c].idx * g.n + cc[j].idx;
+                it.koff[d * kMaxDirect + s2] = koff[e];
+                it.kc[d * kMaxDirect + s2] = kcoef[e];
+              }
             return it;
           };
           for (int64_t p0 = 0; p0 < total; p0 += tp.direct_chunk) {
             const int64_t cnt = std::min<int64_t>(tp.direct_chunk, total - p0);
             // C = A B: sources A (slot 0), coefficients B (slot 1), destination C
-            f.push_back(item(kDirectApply, ns, nd, ta, tc, 1, nd, 0 | (1 << 2) | (DST_OUT << 4), false, p0, cnt));
+            f.push_back(item(kDirectApply, true, 0 | (1 << 2) | (DST_OUT << 4), p0, cnt));
             // dA = dC B^T: sources dC (slot 2), coefficients B, destination dA
-            ba.push_back(item(kDirectApply, nd, ns, tc, ta, nd, 1, 2 | (1 << 2) | (DST_DA << 4), true, p0, cnt));
+            ba.push_back(item(kDirectApply, false, 2 | (1 << 2) | (DST_DA << 4), p0, cnt));
           }
-          for (int64_t p0 = 0; p0 < total; p0 += kDirectOuterChunk) {
-            const int64_t cnt = std::min<int64_t>(kDirectOuterChunk, total - p0);
+          const int64_t oc = 2 * (int64_t)tp.direct_chunk;  // outer items: one set of atomics each
+          for (int64_t p0 = 0; p0 < total; p0 += oc) {
+            const int64_t cnt = std::min<int64_t>(oc, total - p0);
             // dB += A^T dC: sources A (slot 0) and dC (slot 2), sums into dB
-            bb.push_back(item(kDirectOuter, ns, nd, ta, tc, 1, nd, 0 | (2 << 2) | (DST_DB << 4), false, p0, cnt));
+            bb.push_back(item(kDirectOuter, true, 0 | (2 << 2) | (DST_DB << 4), p0, cnt));
           }
         }
       }
-      P->dterms.insert(P->dterms.end(), terms.begin(), terms.end());
-      P->dterm_space.insert(P->dterm_space.end(), space.begin(), space.end());
       dfw.insert(dfw.end(), f.begin(), f.end());
       dba.insert(dba.end(), ba.begin(), ba.end());
       dbb.insert(dbb.end(), bb.begin(), bb.end());
@@ -1983,31 +1971,28 @@ std::unique_ptr<Plan> merge_contract_plans(std::vector<std::unique_ptr<Plan>>& p
   M->bwd_gather_b = {rs.first, rs.count + rb.count};
   M->bwd_scatter_a = concat([](const Plan& p) { return p.bwd_scatter_a; });
   M->bwd_scatter_b = concat([](const Plan& p) { return p.bwd_scatter_b; });
-  // direct items: each problem's terms shifted into the packed tensors
+  // direct items: column and coefficient offsets shifted into the packed tensors
   {
-    std::vector<int> dt0(n);
-    for (int i = 0; i < n; ++i) {
-      const Plan& p = *ps[i];
-      dt0[i] = (int)M->dterms.size();
-      const int64_t shift[3] = {offA[i], offB[i], offC[i]};
-      for (size_t t = 0; t < p.dterms.size(); ++t) {
-        Term x = p.dterms[t];
-        x.off += shift[p.dterm_space[t]];
-        M->dterms.push_back(x);
-        M->dterm_space.push_back(p.dterm_space[t]);
-      }
-    }
+    // tensor of a source slot (0 A, 1 B, 2 dC) and of a destination slot
+    auto src_space = [](int slot) { return slot == 0 ? 0 : slot == 1 ? 1 : 2; };
+    auto dst_space = [](int slot) { return slot == DST_OUT ? 2 : slot == DST_DA ? 0 : 1; };
     Range* dst[3] = {&M->fwd_direct, &M->bwd_direct_a, &M->bwd_direct_b};
     for (int r = 0; r < 3; ++r) {
       const int first = (int)M->ditems.size();
       for (int i = 0; i < n; ++i) {
         const Plan& p = *ps[i];
+        const int64_t shift[3] = {offA[i], offB[i], offC[i]};
         const Range src = r == 0 ? p.fwd_direct : r == 1 ? p.bwd_direct_a : p.bwd_direct_b;
         for (int k = src.first; k < src.first + src.count; ++k) {
           DirectItem it = p.ditems[k];
-          it.ts += dt0[i];
-          it.td += dt0[i];
-          it.tk += dt0[i];
+          const int s1 = it.slots & 3, s2 = (it.slots >> 2) & 3, ds = (it.slots >> 4) & 7;
+          const int64_t sh_src = shift[src_space(s1)];
+          const int64_t sh_dst = shift[it.op == kDirectApply ? dst_space(ds) : src_space(s2)];
+          const int64_t sh_k = shift[1];  // coefficients (apply) and outputs (outer) live in B / dB
+          for (int c = 0; c < it.ns; ++c) it.src[c].off += sh_src;
+          for (int c = 0; c < it.nd; ++c) it.dst[c].off += sh_dst;
+          for (int e = 0; e < kMaxDirect * kMaxDirect; ++e)
+            if (it.kc[e] != 0.0) it.koff[e] += sh_k;
           M->ditems.push_back(it);
         }
       }
@@ -2106,7 +2091,7 @@ int run_direct(Plan& p, int op, Range r, const BoxPtrs& ptrs, void* stream, int 
   ProfScope ps(p, phase, SYM_KERNEL_DIRECT, stream,
                p.ditem_bytes_prefix[r.first + r.count] - p.ditem_bytes_prefix[r.first],
                p.ditem_flops_prefix[r.first + r.count] - p.ditem_flops_prefix[r.first]);
-  return cuda_code(launch_direct(p.f64(), op, p.d_ditems + r.first, r.count, p.d_dterms, ptrs, stream),
+  return cuda_code(launch_direct(p.f64(), op, p.d_ditems + r.first, r.count, ptrs, stream),
                    "direct kernel");
 }
 

@@ -55,11 +55,8 @@ struct Plan {
   Range bwd_scatter_a, bwd_scatter_b;
 
   // direct-contraction work lists (sectors with a tiny matrix on one side,
-  // see kernels.h); dterm_space[i] says which tensor term i's offset points
-  // into: 0 = A (or dA), 1 = B (or dB), 2 = C (or dC)
+  // see kernels.h), their columns inline
   std::vector<DirectItem> ditems;
-  std::vector<Term> dterms;
-  std::vector<int8_t> dterm_space;
   Range fwd_direct, bwd_direct_a, bwd_direct_b;  // C = A B; dA = dC B^T; dB += A^T dC
   std::vector<double> ditem_bytes_prefix, ditem_flops_prefix;  // launch statistics
 
@@ -101,7 +98,6 @@ struct Plan {
   BoxItem* d_items = nullptr;
   Term* d_terms = nullptr;
   DirectItem* d_ditems = nullptr;
-  Term* d_dterms = nullptr;
   GemmSectorSimt* d_secs_simt = nullptr;
   TcSector* d_secs_tc = nullptr;
   GemmTile* d_tiles = nullptr;
