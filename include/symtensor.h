@@ -257,12 +257,16 @@ int sym_plan_profile_kernel(sym_plan plan, int kernel, int* launches,
  *   tc_group 8 (0..256): inside a sector the tcgen05 tiles run in groups of
  *     tc_group row tiles, all column tiles of a group before the next
  *     group, so that a wave of CTAs shares its operand panels in L2 (0: row
- *     by row).
+ *     by row);
+ *   direct_mixed 1: a contraction may mix direct sectors with GEMM sectors;
+ *     0: its sectors go direct only when all of them qualify (no extra
+ *     launches for a few tiny sectors of a large contraction).
  * sym_tune_set rejects a value out of range with SYM_ERR_ARG.             */
 typedef struct {
   int tc_min_mn, tc_min_k, tc_max_k;
   int direct_max, direct_chunk;
   int rows_spans, splitk_ctas, thin_slice, tc_order, tc_group;
+  int direct_mixed;
 } sym_tune;
 int sym_tune_get(sym_tune* out);
 int sym_tune_set(const sym_tune* in);

@@ -26,6 +26,7 @@ SPACE = {
     "tc_min_mn": [16, 32, 48, 64, 96, 128],  # tensor cores vs CUDA cores (sector width)
     "tc_min_k": [16, 32, 48, 64, 96],         # ... (reduction depth)
     "direct_max": [0, 2, 4],                  # direct contraction of tiny-matrix sectors
+    "direct_mixed": [0, 1],                   # ... also in contractions that have GEMM sectors
     "direct_chunk": [256, 512, 1024, 2048],   # positions per direct work item
     "rows_spans": [2, 4, 8, 16],              # rows kernel: runs per warp tile
     "splitk_ctas": [0, 1, 2, 4],              # CUDA-core tiles: split k up to this many CTAs per SM

@@ -883,6 +883,7 @@ sym_tune& tune_state() {
     d.thin_slice = 4096;
     d.tc_order = 0;
     d.tc_group = 8;
+    d.direct_mixed = 1;
     // SYM_TUNE="name=value,...": any parameter (names as in sym_tune)
     if (const char* e = std::getenv("SYM_TUNE")) {
       std::string all(e);
@@ -899,7 +900,7 @@ sym_tune& tune_state() {
                  : k == "direct_max" ? &d.direct_max : k == "direct_chunk" ? &d.direct_chunk
                  : k == "rows_spans" ? &d.rows_spans : k == "splitk_ctas" ? &d.splitk_ctas
                  : k == "thin_slice" ? &d.thin_slice : k == "tc_order" ? &d.tc_order
-                 : k == "tc_group" ? &d.tc_group : nullptr;
+                 : k == "tc_group" ? &d.tc_group : k == "direct_mixed" ? &d.direct_mixed : nullptr;
           if (f) *f = v;
         }
         p = q + 1;
@@ -921,7 +922,7 @@ void set_tune(const sym_tune& t) {
   if (!in(t.tc_min_mn, 1, 1 << 30) || !in(t.tc_min_k, 1, 1 << 30) || !in(t.tc_max_k, t.tc_min_k, 1 << 30) ||
       !in(t.direct_max, 0, kMaxDirect) || !in(t.direct_chunk, 32, 1 << 16) || t.direct_chunk % 32 ||
       !in(t.rows_spans, 1, 64) || !in(t.splitk_ctas, 0, 64) || !in(t.thin_slice, 256, 1 << 20) ||
-      t.thin_slice % 256 || !in(t.tc_order, 0, 1) || !in(t.tc_group, 0, 256))
+      t.thin_slice % 256 || !in(t.tc_order, 0, 1) || !in(t.tc_group, 0, 256) || !in(t.direct_mixed, 0, 1))
     fail(SYM_ERR_ARG, "planning parameter out of range");
   std::lock_guard<std::mutex> g(tune_mu);
   tune_state() = t;
@@ -1399,9 +1400,12 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
       dbb.insert(dbb.end(), bb.begin(), bb.end());
       return true;
     };
+    bool all = true;  // every sector qualifies for the direct path
+    for (auto& g : gs) all = all && g.k <= dmax && g.n <= dmax;
+    const bool use = all || tp.direct_mixed;
     std::vector<G> keep;
     for (auto& g : gs) {
-      if (g.k <= dmax && g.n <= dmax && plan_direct(g)) {
+      if (use && g.k <= dmax && g.n <= dmax && plan_direct(g)) {
         dset.insert(g.x);
         P->flops_fwd += 2.0 * (double)g.m * (double)g.n * (double)g.k;
       } else {
