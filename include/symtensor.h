@@ -65,6 +65,7 @@ extern "C" {
 
 #define SYM_U1 1
 #define SYM_SU2 2
+#define SYM_Z2F 3 /* fermion parity: labels 0/1, fusion mod 2, swap of two odd charges -1 */
 
 /* Precision of a plan (the storage dtype follows from it). */
 #define SYM_PREC_FP64 1   /* double blocks, FP64 gathers and FP64 GEMM (CUDA cores) */
@@ -88,7 +89,11 @@ const char* sym_version(void);
 
 /* ---------------------------------------------------------------- tensors ---
  * sym_tensor_create: build the sector table of a tensor (host only, no GPU).
- *   group: SYM_U1 or SYM_SU2.  0 <= rank <= 6 (rank 0 is a scalar).
+ *   group: SYM_U1, SYM_SU2 or SYM_Z2F (fermion parity of the thesis's
+ *   conclusion: labels p = 0, 1 fuse by addition mod 2, the recoupling
+ *   coefficients are 1, and exchanging two legs of odd parity multiplies a
+ *   block by -1; total = 0 or 1; every permutation, fuse and contraction
+ *   applies these swap signs, and nothing else differs from U(1)).  0 <= rank <= 6 (rank 0 is a scalar).
  *   legs: rank leg descriptors (copied).
  *   total: U(1) total charge Q; ignored for SU(2) (total spin is 0).
  *   tree: SU(2) fusion tree as 2*(rank-1) ints, NULL = left comb; ignored for U(1).

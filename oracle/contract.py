@@ -23,6 +23,7 @@ import numpy as np
 
 from . import su2 as su2m
 from . import u1 as u1m
+from . import z2f as z2fm
 
 
 def _mod(group):
@@ -65,7 +66,10 @@ def result_legs(legsA, legsB, pairsA, pairsB):
 
 
 def contract(group, A, B, pairsA, pairsB, tree_c=None):
-    """A, B = (legs, total_or_tree, data).  Returns (legsC, total_or_tree, data, resid)."""
+    """A, B = (legs, total_or_tree, data).  Returns (legsC, total_or_tree, data, resid).
+    Fermion parity ("z2f"): oracle/z2f.py, the contraction with its swap signs."""
+    if group == "z2f":
+        return z2fm.contract(A, B, pairsA, pairsB)
     m = _mod(group)
     legsA, tA, a = A
     legsB, tB, b = B
@@ -82,6 +86,8 @@ def contract(group, A, B, pairsA, pairsB, tree_c=None):
 
 def contract_grad(group, A, B, pairsA, pairsB, dC, tree_c=None):
     """(dA, dB) blocks of the gradient of <dC, contract(A, B)>."""
+    if group == "z2f":
+        return z2fm.contract_grad(A, B, pairsA, pairsB, dC)
     m = _mod(group)
     legsA, tA, a = A
     legsB, tB, b = B
@@ -120,6 +126,8 @@ def contract_grad(group, A, B, pairsA, pairsB, dC, tree_c=None):
 
 def permute(group, T, perm, tree_out=None):
     """Output leg n is input leg perm[n]; SU(2) result in tree_out (default comb)."""
+    if group == "z2f":
+        return z2fm.permute(T, perm)
     m = _mod(group)
     legs, t, data = T
     legs2 = [legs[p] for p in perm]
@@ -134,6 +142,8 @@ def permute(group, T, perm, tree_out=None):
 
 def fuse(group, T, first, tree_out=None):
     """Fuse adjacent legs (first, first+1) of equal direction into one leg."""
+    if group == "z2f":
+        return z2fm.fuse(T, first)
     m = _mod(group)
     legs, t, data = T
     la, lb = legs[first], legs[first + 1]

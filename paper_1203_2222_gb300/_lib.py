@@ -20,6 +20,7 @@ SYM_ERR_OOM = -6
 SYM_ERR_UNSUPPORTED = -7
 SYM_U1 = 1
 SYM_SU2 = 2
+SYM_Z2F = 3
 SYM_PREC_FP64 = 1
 SYM_PREC_BF16X3 = 2
 

@@ -91,7 +91,7 @@ sym::Tensor sym::contraction_result(const Tensor& a, const Tensor& b, const std:
   if (legs.size() > 6) fail(SYM_ERR_ARG, "result rank would exceed 6");
   Tree tr;
   if (a.group == SYM_SU2) tr = tree_c ? read_tree((int)legs.size(), tree_c) : Tree::comb_pair(na, (int)legs.size() - na);
-  return make_tensor(a.group, legs, a.total + b.total, tr);
+  return make_tensor(a.group, legs, a.group == SYM_Z2F ? (a.total ^ b.total) : a.total + b.total, tr);
 }
 
 extern "C" {

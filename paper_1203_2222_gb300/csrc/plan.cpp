@@ -249,17 +249,31 @@ void block_strides(const Tensor& T, int64_t s, int* st) {
   }
 }
 
+// Swap sign of a fermion-parity block moved by perm (destination leg n = source
+// leg perm[n]): the swap tensor is -1 for two odd charges and 1 otherwise, so
+// the block gains (-1)^(number of pairs of odd legs whose order perm exchanges).
+double z2f_swap_sign(const Tensor& src, const std::vector<int>& perm, const std::vector<int>& srcpos) {
+  int odd_pairs = 0;
+  const int k = (int)perm.size();
+  for (int a = 0; a < k; ++a)
+    for (int b = a + 1; b < k; ++b)
+      if (perm[a] > perm[b] && src.legs[perm[a]].labels[srcpos[perm[a]]] == 1 &&
+          src.legs[perm[b]].labels[srcpos[perm[b]]] == 1)
+        ++odd_pairs;
+  return (odd_pairs & 1) ? -1.0 : 1.0;
+}
+
 // terms[s_dst] = (src sector, coef) with dst leg n = src leg perm[n]
 std::vector<TermList> make_xform(const Tensor& src, const std::vector<int>& perm, const Tensor& dst) {
   std::vector<TermList> out(dst.nsec());
   const int k = src.rank;
-  if (src.group == SYM_U1) {
+  if (src.group != SYM_SU2) {  // U(1), fermion parity: one source block, coefficient 1 or the swap sign
     std::vector<int> key(k);
     for (int64_t s = 0; s < dst.nsec(); ++s) {
       for (int n = 0; n < k; ++n) key[perm[n]] = dst.p(s, n);
       int64_t ss = src.find(key);
       if (ss < 0) fail(SYM_ERR_ARG, "internal: permuted sector missing");
-      out[s].push_back({ss, 1.0});
+      out[s].push_back({ss, src.group == SYM_Z2F ? z2f_swap_sign(src, perm, key) : 1.0});
     }
     return out;
   }
@@ -654,6 +668,10 @@ void Plan::upload(bool device) {
   if (e != cudaSuccess) fail(SYM_ERR_CUDA, std::string("plan upload: ") + cudaGetErrorString(e));
 }
 
+// fused charge of two abelian labels (U(1): sum; fermion parity: sum mod 2)
+int abelian_fuse(int group, int a, int b) { return group == SYM_Z2F ? (a ^ b) : a + b; }
+bool z2f_group(int group) { return group == SYM_Z2F; }
+
 Leg fused_leg(const Leg& a, const Leg& b, int group) {
   if (a.dir != b.dir) fail(SYM_ERR_INCOMPATIBLE_LEGS, "fused legs must have equal directions");
   std::map<int, int64_t> deg;
@@ -662,6 +680,8 @@ Leg fused_leg(const Leg& a, const Leg& b, int group) {
       int64_t d = (int64_t)a.degens[i] * b.degens[j];
       if (group == SYM_U1) {
         deg[a.labels[i] + b.labels[j]] += d;
+      } else if (group == SYM_Z2F) {
+        deg[a.labels[i] ^ b.labels[j]] += d;
       } else {
         for (int c = std::abs(a.labels[i] - b.labels[j]); c <= a.labels[i] + b.labels[j]; c += 2) deg[c] += d;
       }
@@ -681,7 +701,9 @@ static int64_t pair_offset(const Leg& a, const Leg& b, int group, int c, int ia,
   int64_t off = 0;
   for (size_t i = 0; i < a.labels.size(); ++i)
     for (size_t j = 0; j < b.labels.size(); ++j) {
-      bool ok = group == SYM_U1 ? a.labels[i] + b.labels[j] == c : triangle(a.labels[i], b.labels[j], c);
+      bool ok = group == SYM_U1    ? a.labels[i] + b.labels[j] == c
+                : group == SYM_Z2F ? (a.labels[i] ^ b.labels[j]) == c
+                                   : triangle(a.labels[i], b.labels[j], c);
       if (!ok) continue;
       if ((int)i == ia && (int)j == ib) return off;
       off += (int64_t)a.degens[i] * b.degens[j];
@@ -751,7 +773,8 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
     for (int i = 0; i < k; ++i) idp[i] = i;
     if (in.group == SYM_SU2) X = make_xform(in, idp, mid);
     for (int64_t sm = 0; sm < mid.nsec(); ++sm) {
-      int c = in.group == SYM_U1 ? la.labels[mid.p(sm, f)] + lb.labels[mid.p(sm, f + 1)] : mid.inner_of(sm)[0];
+      int c = in.group != SYM_SU2 ? abelian_fuse(in.group, la.labels[mid.p(sm, f)], lb.labels[mid.p(sm, f + 1)])
+                                  : mid.inner_of(sm)[0];
       int iq = (int)(std::lower_bound(ld.labels.begin(), ld.labels.end(), c) - ld.labels.begin());
       std::vector<int> key;
       for (int l = 0; l < k; ++l) {
@@ -764,12 +787,12 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
       int64_t row0 = pair_offset(la, lb, in.group, c, mid.p(sm, f), mid.p(sm, f + 1));
       block_strides(out, so, ost);
       std::vector<Term> terms;
-      if (in.group == SYM_U1) {
+      if (in.group != SYM_SU2) {
         terms.push_back({in.offs[sm], 1, 1.0});
       } else {
         for (auto& pc : X[sm]) terms.push_back({in.offs[pc.first], 1, pc.second});
       }
-      block_strides(in, in.group == SYM_U1 ? sm : (X[sm].empty() ? 0 : X[sm][0].first), ist);
+      block_strides(in, in.group != SYM_SU2 ? sm : (X[sm].empty() ? 0 : X[sm][0].first), ist);
       Box b;
       int db_ = mid.dim(sm, f + 1);
       for (int l = 0; l < k; ++l) {
@@ -792,7 +815,8 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
     // where each mid sector lives inside `in`
     std::vector<int64_t> m_in(mid.nsec()), m_row(mid.nsec());
     for (int64_t sm = 0; sm < mid.nsec(); ++sm) {
-      int c = in.group == SYM_U1 ? la.labels[mid.p(sm, f)] + lb.labels[mid.p(sm, f + 1)] : mid.inner_of(sm)[0];
+      int c = in.group != SYM_SU2 ? abelian_fuse(in.group, la.labels[mid.p(sm, f)], lb.labels[mid.p(sm, f + 1)])
+                                  : mid.inner_of(sm)[0];
       const Leg& lf = in.legs[f];
       int iq = (int)(std::lower_bound(lf.labels.begin(), lf.labels.end(), c) - lf.labels.begin());
       std::vector<int> key;
@@ -807,7 +831,7 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
     }
     for (int64_t s = 0; s < out.nsec(); ++s) {
       block_strides(out, s, ost);
-      TermList tl = in.group == SYM_U1 ? TermList{{s, 1.0}} : X[s];
+      TermList tl = in.group != SYM_SU2 ? TermList{{s, 1.0}} : X[s];
       std::vector<Term> terms;
       int sa_[kMaxDim] = {0}, sb_[kMaxDim] = {0};
       bool first = true;
@@ -1080,7 +1104,8 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   std::vector<Leg> clegs;
   for (int l : freeA) clegs.push_back(A.legs[l]);
   for (int l : freeB) clegs.push_back(B.legs[l]);
-  Tensor Cn = make_tensor(A.group, clegs, A.total + B.total, Tree::comb_pair(na, nb));
+  Tensor Cn = make_tensor(A.group, clegs, z2f_group(A.group) ? (A.total ^ B.total) : A.total + B.total,
+                          Tree::comb_pair(na, nb));
   const bool natural = !su2 || C.tree == Cn.tree;
 
   auto XA = make_xform(A, permA, Am);
@@ -1105,22 +1130,25 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   auto XAt = transpose_xform(XA, A.nsec());
   auto XBt = transpose_xform(XB, B.nsec());
 
+  // sector key x of the matrix form: SU(2) coupled spin; U(1) charge of the
+  // contracted legs as A sees them; fermion parity of the contracted legs
+  const bool z2f = A.group == SYM_Z2F;
   auto keyA = [&](int64_t s) {
     if (su2) return su2_top(Am, s, na);
     int x = 0;
-    for (int n = na; n < Am.rank; ++n) x += Am.legs[n].dir * Am.label(s, n);
+    for (int n = na; n < Am.rank; ++n) x = z2f ? x ^ Am.label(s, n) : x + Am.legs[n].dir * Am.label(s, n);
     return x;
   };
   auto keyB = [&](int64_t s) {
     if (su2) return su2_top(Bm, s, nc);
     int x = 0;
-    for (int n = 0; n < nc; ++n) x -= Bm.legs[n].dir * Bm.label(s, n);
+    for (int n = 0; n < nc; ++n) x = z2f ? x ^ Bm.label(s, n) : x - Bm.legs[n].dir * Bm.label(s, n);
     return x;
   };
   auto keyC = [&](int64_t s) {
     if (su2) return su2_top(Cn, s, na);
     int x = A.total;
-    for (int n = 0; n < na; ++n) x -= Cn.legs[n].dir * Cn.label(s, n);
+    for (int n = 0; n < na; ++n) x = z2f ? x ^ Cn.label(s, n) : x - Cn.legs[n].dir * Cn.label(s, n);
     return x;
   };
   MatForm MA = make_matform(Am, na, keyA);

@@ -93,13 +93,14 @@ std::vector<std::vector<int>> tree_labelings(const Tree& tree, const std::vector
 }
 
 Tensor make_tensor(int group, const std::vector<Leg>& legs, int total, const Tree& tree_in) {
-  if (group != SYM_U1 && group != SYM_SU2) fail(SYM_ERR_ARG, "unknown symmetry group");
+  if (group != SYM_U1 && group != SYM_SU2 && group != SYM_Z2F) fail(SYM_ERR_ARG, "unknown symmetry group");
+  if (group == SYM_Z2F && total != 0 && total != 1) fail(SYM_ERR_ARG, "Z2F total parity must be 0 or 1");
   Tensor t;
   t.group = group;
   t.rank = (int)legs.size();
   if (t.rank > 6) fail(SYM_ERR_UNSUPPORTED, "rank > 6 is not supported");
   t.legs = legs;
-  t.total = group == SYM_U1 ? total : 0;
+  t.total = group == SYM_SU2 ? 0 : total;
   for (const Leg& l : legs) {
     if (l.labels.empty() || l.labels.size() != l.degens.size()) fail(SYM_ERR_ARG, "leg: empty or size mismatch");
     if (l.dir != 1 && l.dir != -1) fail(SYM_ERR_ARG, "leg: direction must be +1 or -1");
@@ -107,6 +108,7 @@ Tensor make_tensor(int group, const std::vector<Leg>& legs, int total, const Tre
       if (l.degens[i] < 1) fail(SYM_ERR_ARG, "leg: degeneracy must be >= 1");
       if (i && l.labels[i] <= l.labels[i - 1]) fail(SYM_ERR_ARG, "leg: labels must increase strictly");
       if (group == SYM_SU2 && l.labels[i] < 0) fail(SYM_ERR_ARG, "leg: negative spin");
+      if (group == SYM_Z2F && l.labels[i] != 0 && l.labels[i] != 1) fail(SYM_ERR_ARG, "leg: parity must be 0 or 1");
     }
   }
   if (group == SYM_SU2) {
@@ -131,6 +133,10 @@ Tensor make_tensor(int group, const std::vector<Leg>& legs, int total, const Tre
     if (group == SYM_U1) {
       int64_t s = 0;
       for (int l = 0; l < t.rank; ++l) s += (int64_t)legs[l].dir * legs[l].labels[idx[l]];
+      if (s == total) add({});
+    } else if (group == SYM_Z2F) {  // parities add mod 2 (a direction does not change a parity)
+      int s = 0;
+      for (int l = 0; l < t.rank; ++l) s ^= legs[l].labels[idx[l]];
       if (s == total) add({});
     } else {
       std::vector<int> spins(t.rank);

@@ -16,7 +16,7 @@ import torch
 
 from . import _lib as L
 
-U1, SU2 = L.SYM_U1, L.SYM_SU2
+U1, SU2, Z2F = L.SYM_U1, L.SYM_SU2, L.SYM_Z2F
 FP64, BF16X3 = L.SYM_PREC_FP64, L.SYM_PREC_BF16X3
 SymError = L.SymError
 
@@ -28,8 +28,9 @@ def _byref(x):
 class Structure:
     """Sector table of a symmetric tensor (legs, total charge or tree); host only.
 
-    ``legs`` is a sequence of ``(labels, degens, dir)`` (U(1) charges or SU(2)
-    doubled spins, strictly increasing; dir +1 out, -1 in).  ``tree`` (SU(2))
+    ``legs`` is a sequence of ``(labels, degens, dir)`` (U(1) charges, SU(2)
+    doubled spins or fermion parities 0/1, strictly increasing; dir +1 out,
+    -1 in).  ``tree`` (SU(2))
     is a list of ``(left, right)`` node children, None for the left comb.
     """
 
@@ -43,7 +44,7 @@ class Structure:
             self._h = h
         else:
             self._h = _handle
-        self.total = int(total) if self.group == U1 else 0
+        self.total = 0 if self.group == SU2 else int(total)
         g, r, n, ns = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
         L.check(L.lib.sym_tensor_info(self._h, _byref(g), _byref(r), _byref(n), _byref(ns)))
         self.rank, self.numel, self.nsec = r.value, n.value, ns.value
@@ -168,6 +169,11 @@ KERNEL_SYMBOLS = {"box": "box_kernel<T, T, false>", "box_flat": "box_kernel<T, T
                   "gemm_rows": "gemm_rows_kernel<T>", "direct": "direct_kernel<T>"}
 
 
+def _fuse_total(group, a, b):
+    """Total charge of a contraction's result: U(1) sum, fermion parity sum mod 2."""
+    return (a ^ b) if group == Z2F else a + b
+
+
 def tune_get():
     """Current planning parameters (include/symtensor.h, sym_tune) as a dict."""
     t = L.sym_tune()
@@ -213,7 +219,7 @@ def contract_plan(A, B, pairsA, pairsB, precision=BF16X3, tree_c=None):
     c, p = ctypes.c_void_p(), ctypes.c_void_p()
     L.check(L.lib.sym_contract_plan(A._h, B._h, len(pairsA), L.int_array(pairsA), L.int_array(pairsB),
                                     L.tree_array(tree_c), int(precision), _byref(c), _byref(p)))
-    out = Structure(A.group, total=A.total + B.total, _handle=c)
+    out = Structure(A.group, total=_fuse_total(A.group, A.total, B.total), _handle=c)
     plan = Plan(p, out, "contract", int(precision))
     _PLANS[key] = (plan, A, B)
     return plan
@@ -257,7 +263,8 @@ def contract_batch_plan(As, Bs, pairsA, pairsB, precision=BF16X3):
     p = ctypes.c_void_p()
     L.check(L.lib.sym_contract_batch_plan(n, Ah, Bh, len(pairsA), L.int_array(pairsA), L.int_array(pairsB),
                                           int(precision), Ch, offs.ctypes.data_as(L._LP), _byref(p)))
-    outs = [Structure(As[i].group, total=As[i].total + Bs[i].total, _handle=ctypes.c_void_p(Ch[i]))
+    outs = [Structure(As[i].group, total=_fuse_total(As[i].group, As[i].total, Bs[i].total),
+                      _handle=ctypes.c_void_p(Ch[i]))
             for i in range(n)]
     plan = BatchPlan(p, outs, offs, int(precision))
     _PLANS[key] = (plan, tuple(As), tuple(Bs))

@@ -15,6 +15,7 @@ pytestmark = pytest.mark.gpu
 from oracle import contract as oc  # noqa: E402
 from oracle import su2 as osu2  # noqa: E402
 from oracle import u1 as ou1  # noqa: E402
+from oracle import z2f as oz2f  # noqa: E402
 
 TOL = {torch.float64: 1e-12, torch.float32: 2e-5}
 
@@ -32,18 +33,18 @@ def rel(x, y):
 
 
 def _oleg(group, l):
-    return (ou1.Leg if group == "u1" else osu2.Leg)(*l)
+    return {"u1": ou1.Leg, "su2": osu2.Leg, "z2f": oz2f.Leg}[group](*l)
 
 
 def _otree(group, S, legs_spec):
-    if group == "u1":
+    if group in ("u1", "z2f"):
         return S.total
     return S.tree if S.tree is not None else osu2.left_comb(len(legs_spec))
 
 
 def _make(group, legs, seed, dtype, total=0, tree=None):
     P = _lib()
-    S = P.Structure(P.U1 if group == "u1" else P.SU2, legs, total=total, tree=tree)
+    S = P.Structure({"u1": P.U1, "su2": P.SU2, "z2f": P.Z2F}[group], legs, total=total, tree=tree)
     vals = np.random.default_rng(seed).standard_normal(S.numel)
     T = P.SymTensor.from_numpy(S, vals, dtype=dtype)
     host = T.data.double().cpu().numpy()  # exactly what the GPU holds
@@ -167,6 +168,46 @@ def test_u1_tiny_b_with_missing_blocks_direct(dtype):
     la = [([-1, 0, 1, 2], [37, 64, 129, 3], 1), ([-1, 0, 1], [1, 2, 1], -1)]
     lb = [([-1, 0, 1], [1, 2, 1], 1), ([0, 2], [1, 2], 1)]
     _contract_case("u1", la, lb, [1], [0], dtype, QB=1)
+
+
+# Fermion parity (the thesis's outlook): permutations carry the swap signs;
+# a contraction is A's contracted legs permuted last, B's first, then the
+# blockwise product.
+PAR = [0, 1]
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
+def test_z2f_contraction_with_swap_signs(dtype):
+    # contracted legs out of order on both sides: odd legs are exchanged
+    la = [(PAR, [23, 17], 1), (PAR, [9, 14], -1), (PAR, [30, 11], 1), (PAR, [12, 19], 1)]
+    lb = [(PAR, [12, 19], -1), (PAR, [40, 25], 1), (PAR, [9, 14], 1)]
+    _contract_case("z2f", la, lb, [3, 1], [0, 2], dtype, QA=1, QB=0)
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
+def test_z2f_multi_tile_and_edge_cases(dtype):
+    # sector matrices spanning several 128-tiles (tensor-core and CUDA-core kernels)
+    la = [(PAR, [150, 70], 1), (PAR, [5, 3], -1), (PAR, [90, 140], 1)]
+    lb = [(PAR, [90, 140], -1), (PAR, [100, 37], 1)]
+    _contract_case("z2f", la, lb, [2], [0], dtype, QA=0, QB=1)
+    # three contracted pairs in reversed order, total parity odd on both sides
+    la = [(PAR, [3, 2], 1), (PAR, [2, 3], 1), (PAR, [4, 1], -1), (PAR, [1, 2], 1)]
+    lb = [(PAR, [1, 2], -1), (PAR, [4, 1], 1), (PAR, [2, 3], -1), (PAR, [2, 2], 1)]
+    _contract_case("z2f", la, lb, [3, 2, 1], [0, 1, 2], dtype, QA=1, QB=1)
+    # full contraction to a scalar and an outer product
+    la = [(PAR, [2, 3], 1), (PAR, [3, 1], -1)]
+    lb = [(PAR, [2, 3], -1), (PAR, [3, 1], 1)]
+    _contract_case("z2f", la, lb, [0, 1], [0, 1], dtype, QA=1, QB=1)
+    _contract_case("z2f", la, [(PAR, [2, 2], 1)], [], [], dtype, QA=1, QB=1)
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
+def test_z2f_permute_and_fuse(dtype):
+    legs = [(PAR, [2, 3], 1), (PAR, [3, 1], -1), (PAR, [1, 2], 1), (PAR, [2, 2], -1)]
+    _transform_case("z2f", legs, "permute", ([2, 0, 3, 1], None), dtype)
+    _transform_case("z2f", legs, "permute", ([3, 2, 1, 0], None), dtype)
+    legs = [(PAR, [2, 3], 1), (PAR, [3, 1], 1), (PAR, [1, 2], -1)]
+    _transform_case("z2f", legs, "fuse", (0,), dtype)
 
 
 SU2_TREES = [None, [(1, 2), (0, 4), (5, 3)], [(0, 1), (2, 3), (4, 5)]]

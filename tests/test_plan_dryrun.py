@@ -58,6 +58,20 @@ plan("u1", [(qs5, [4, 11, 20, 9, 3], -1), (*T.PHYS, -1), (qs5, [5, 13, 17, 12, 6
      [(*T.MPO, -1), (*T.PHYS, 1), (*T.PHYS, 1), (*T.MPO, 1)], [1, 4], [2, 0], QA=1)
 plan("u1", [([-1, 0, 1, 2], [37, 64, 129, 3], 1), ([-1, 0, 1], [1, 2, 1], -1)],
      [([-1, 0, 1], [1, 2, 1], 1), ([0, 2], [1, 2], 1)], [1], [0], QB=1)
+# fermion parity: permutation swap signs on the gathers
+def zplan(la, lb, pa, pb, QA=0, QB=0):
+    A = P.Structure(P.Z2F, la, total=QA); B = P.Structure(P.Z2F, lb, total=QB)
+    for prec in (P.FP64, P.BF16X3):
+        P.contract_plan(A, B, pa, pb, prec)
+zplan([([0, 1], [23, 17], 1), ([0, 1], [9, 14], -1), ([0, 1], [30, 11], 1), ([0, 1], [12, 19], 1)],
+      [([0, 1], [12, 19], -1), ([0, 1], [40, 25], 1), ([0, 1], [9, 14], 1)], [3, 1], [0, 2], QA=1)
+Z = P.Structure(P.Z2F, [([0, 1], [2, 3], 1), ([0, 1], [3, 1], 1), ([0, 1], [1, 2], -1)], total=1)
+P.permute_plan(Z, [2, 0, 1]); P.fuse_plan(Z, 0)
+try:
+    P.Structure(P.Z2F, [([0, 2], [1, 1], 1)])
+    raise SystemExit("accepted a parity label 2")
+except P.SymError:
+    pass
 b5 = synthetic.u1_two_site_batch(n=6, seed=7, dmin=40, dmax=90, qmax=4)
 pr = b5["problems"]
 S5 = {n: [P.Structure(P.U1, q[n]) for q in pr] for n in ("L", "theta", "W", "R")}
