@@ -40,7 +40,8 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--workload", choices=["u1_mps_heff", "su2_recouple", "u1_two_site_batch", "u1_mera_grad"],
+    ap.add_argument("--workload", choices=["u1_mps_heff", "su2_recouple", "u1_two_site_batch", "u1_mera_grad",
+                                           "z2f_mps_heff"],
                     default="u1_mps_heff",
                     help="u1_mps_heff (default, the metric's configuration), the large-sector su2_recouple, "
                          "the 512-problem u1_two_site_batch or the MERA gradient u1_mera_grad")
@@ -189,10 +190,10 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(sm), "source": self.source}
 
 
-def mps_structures(P):
+def mps_structures(P, group="u1"):
     from paper_1203_2222_gb300 import synthetic
-    m = synthetic.u1_mps_heff()
-    S = {n: P.Structure(P.U1, m[n]) for n in ("L", "A", "W", "R")}
+    m = synthetic.u1_mps_heff() if group == "u1" else synthetic.z2f_mps_heff()
+    S = {n: P.Structure(P.U1 if group == "u1" else P.Z2F, m[n]) for n in ("L", "A", "W", "R")}
     return m, S
 
 
@@ -245,11 +246,12 @@ class MPSWorkload:
     name = "u1_mps_heff"
     describe = WORKLOAD
     default_steps, default_warmup, default_fp64_steps = 100, 5, 10
+    group = "u1"
 
     def build(self, P, dev):
         import torch
         from paper_1203_2222_gb300 import synthetic
-        self.m, self.S = mps_structures(P)
+        self.m, self.S = mps_structures(P, self.group)
         self.data = make_inputs(P, self.m, self.S, torch.float32, dev)
         for v in self.data.values():
             v.requires_grad_(True)
@@ -261,6 +263,16 @@ class MPSWorkload:
 
     def step(self, P, data, G):
         return mps_step(P, self.S, data, G)
+
+
+class Z2FMPSWorkload(MPSWorkload):
+    """The MPS chain with fermion-parity legs (swap signs on every gather):
+    two large sectors per leg, so the GEMMs run at tensor-core size."""
+    name = "z2f_mps_heff"
+    describe = ("z2f_mps_heff: fermionic ((L.A).W).R fwd+bwd, fermion-parity legs: D=2048 as {0:1024, 1:1024}, "
+                "phys {0:1, 1:1}, MPO {0:3, 1:2}; swap signs on every permutation")
+    default_steps, default_warmup, default_fp64_steps = 50, 5, 2
+    group = "z2f"
 
 
 class SU2Workload:
@@ -415,7 +427,7 @@ class MeraWorkload:
 
 
 WORKLOADS = {"u1_mps_heff": MPSWorkload, "su2_recouple": SU2Workload, "u1_two_site_batch": BatchWorkload,
-             "u1_mera_grad": MeraWorkload}
+             "u1_mera_grad": MeraWorkload, "z2f_mps_heff": Z2FMPSWorkload}
 
 
 # ---------------------------------------------------------------- roofline ---
@@ -778,12 +790,14 @@ def run_ours(args, rank, world):
 class OracleMPS:
     """The FP64 CPU oracle on the same workload (dense embedding, brute force)."""
 
-    def __init__(self):
-        from oracle import u1
+    def __init__(self, group="u1"):
+        from oracle import u1, z2f
         from paper_1203_2222_gb300 import synthetic
-        m = synthetic.u1_mps_heff()
-        self.legs = {n: [u1.Leg(*l) for l in m[n]] for n in ("L", "A", "W", "R")}
-        self.data = {n: synthetic.normal(m["seeds"][n], u1.layout(self.legs[n], 0)[2]) for n in self.legs}
+        mod = u1 if group == "u1" else z2f
+        m = synthetic.u1_mps_heff() if group == "u1" else synthetic.z2f_mps_heff()
+        self.group = group
+        self.legs = {n: [mod.Leg(*l) for l in m[n]] for n in ("L", "A", "W", "R")}
+        self.data = {n: synthetic.normal(m["seeds"][n], mod.layout(self.legs[n], 0)[2]) for n in self.legs}
         self.steps = [("L", "A", [2], [0]), (None, "W", [1, 2], [0, 2]), (None, "R", [1, 3], [2, 1])]
 
     def contraction(self, i, a=None):
@@ -792,9 +806,9 @@ class OracleMPS:
         an, bn, pa, pb = self.steps[i]
         A = (self.legs[an], 0, self.data[an]) if an else a
         B = (self.legs[bn], 0, self.data[bn])
-        lc, qc, c, _ = oc.contract("u1", A, B, pa, pb)
+        lc, qc, c, _ = oc.contract(self.group, A, B, pa, pb)
         g = np.random.default_rng(i).standard_normal(c.size)
-        oc.contract_grad("u1", A, B, pa, pb, g)
+        oc.contract_grad(self.group, A, B, pa, pb, g)
         return (lc, qc, c)
 
     def full_step(self):
@@ -809,7 +823,7 @@ class OracleMPS:
         for j in range(i):
             an, bn, pa, pb = self.steps[j]
             A = (self.legs[an], 0, self.data[an]) if an else a
-            lc, qc, c, _ = oc.contract("u1", A, (self.legs[bn], 0, self.data[bn]), pa, pb)
+            lc, qc, c, _ = oc.contract(self.group, A, (self.legs[bn], 0, self.data[bn]), pa, pb)
             a = (lc, qc, c)
         return a
 
@@ -999,7 +1013,7 @@ def cpu_baseline(args, flops, steps):
         return {"value": round(n * per / dt / 1e12, 9), "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
                 "sample": f"{n} dense elements of C from embedded slices of A and B (FP64 numpy oracle), each "
                           f"credited the forward useful flops per block entry of C; {dt:.1f} s"}
-    o = OracleMPS()
+    o = OracleMPS("z2f" if args.workload == "z2f_mps_heff" else "u1")
     t0 = time.perf_counter()
     for _ in range(steps):
         o.full_step()
@@ -1098,9 +1112,9 @@ def run_reference_su2(args):
     }
 
 
-def run_reference(args, flops_by_contraction):
+def run_reference(args, flops_by_contraction, group="u1"):
     """The oracle as the reference arm: each step is one contraction of the chain (fwd + grad), rotating."""
-    o = OracleMPS()
+    o = OracleMPS(group)
     ins = [o.inputs_of(i) for i in range(3)]
     for w in range(args.warmup):
         o.contraction(w % 3, ins[w % 3])
@@ -1115,18 +1129,19 @@ def run_reference(args, flops_by_contraction):
         "metric": METRIC, "value": round(value, 6), "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD, "sample": "step s = contraction (s mod 3) of the chain, fwd + grad"},
+        "config": {"workload": WORKLOAD if group == "u1" else Z2FMPSWorkload.describe,
+                   "sample": "step s = contraction (s mod 3) of the chain, fwd + grad"},
         "cpu_baseline": {"value": round(value, 6), "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
                          "sample": "one contraction of ((L.A).W).R per step, rotating, dense FP64 numpy oracle"},
         "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
 
-def contraction_flops_host():
+def contraction_flops_host(group="u1"):
     """Useful forward flops of each contraction of the chain (host planning only)."""
     os.environ["SYM_PLAN_DRYRUN"] = "1"
     import paper_1203_2222_gb300 as P
-    m, S = mps_structures(P)
+    m, S = mps_structures(P, group)
     t1 = P.contract_plan(S["L"], S["A"], [2], [0], P.BF16X3)
     t2 = P.contract_plan(t1.out, S["W"], [1, 2], [0, 2], P.BF16X3)
     t3 = P.contract_plan(t2.out, S["R"], [1, 3], [2, 1], P.BF16X3)
@@ -1150,7 +1165,8 @@ def main():
         elif args.workload == "u1_mera_grad":
             out = run_reference_mera(args)
         else:
-            out = run_reference(args, contraction_flops_host())
+            g = "z2f" if args.workload == "z2f_mps_heff" else "u1"
+            out = run_reference(args, contraction_flops_host(g), g)
         print(json.dumps(out))
         return 0
     import torch

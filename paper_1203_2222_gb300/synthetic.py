@@ -26,6 +26,8 @@ Workload shapes (all seeds are ``1234 + index``):
   two copies of the isometry w (upper leg in, three lower legs out) and a
   disentangler u (two lower legs in, two upper legs out) on the middle bond;
   h is the XXZ-like two-site term given entry by entry (``mera_h_entry``).
+* ``z2f_mps_heff``  the MPS chain above with fermion-parity legs: bond
+  D = 2048 as {0: 1024, 1: 1024}, physical {0:1, 1:1}, MPO {0:3, 1:2}.
 * ``su2_recouple``  rank-4 SU(2) tensors, every leg with 2j = 0..8 and
   degeneracies uniform in 1..dmax (32 at full size); A has all legs out in
   the comb tree, is permuted (0,2,1,3) into the matrix tree and its legs 1,3
@@ -98,6 +100,29 @@ def u1_mps_heff(D=2048, qmax=20, sigma=6.0, seed=1235):
     W = [(wq, wd, 1), phys_in, phys_out, (wq, wd, -1)]
     R = [bond_out, (wq, wd, 1), bond_in]
     return {"group": "u1", "L": L, "A": A, "W": W, "R": R,
+            "steps": [((1, 2), (0, 2)), ((1, 3), (2, 1))],
+            "seeds": {"L": seed, "A": seed + 100, "W": seed + 200, "R": seed + 300},
+            "D": D}
+
+
+def z2f_mps_heff(D=2048, seed=1239):
+    """Legs of the fermionic MPS effective-Hamiltonian apply ((L.A).W).R.
+
+    Fermion-parity legs (labels 0 even, 1 odd): bond D split evenly between
+    the two parities, physical leg {0:1, 1:1} (an empty or occupied fermion
+    site), MPO leg {0:3, 1:2} (three even channels -- identity, number,
+    identity -- and two odd ones carrying a creation or annihilation
+    operator, as in a hopping MPO).  Directions and contraction order as
+    ``u1_mps_heff``; every tensor has total parity 0.
+    """
+    bond_in, bond_out = ([0, 1], [D // 2, D - D // 2], -1), ([0, 1], [D // 2, D - D // 2], 1)
+    wq, wd = [0, 1], [3, 2]
+    phys_in, phys_out = ([0, 1], [1, 1], -1), ([0, 1], [1, 1], 1)
+    L = [bond_in, (wq, wd, -1), bond_out]
+    A = [bond_in, phys_in, bond_out]
+    W = [(wq, wd, 1), phys_in, phys_out, (wq, wd, -1)]
+    R = [bond_out, (wq, wd, 1), bond_in]
+    return {"group": "z2f", "L": L, "A": A, "W": W, "R": R,
             "steps": [((1, 2), (0, 2)), ((1, 3), (2, 1))],
             "seeds": {"L": seed, "A": seed + 100, "W": seed + 200, "R": seed + 300},
             "D": D}
