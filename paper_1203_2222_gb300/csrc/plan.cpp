@@ -1213,6 +1213,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     struct Col {
       int64_t idx, off;
       std::vector<int64_t> fs;
+      double sgn = 1.0;  // coefficient of the source block (a fermion-parity swap sign, else 1)
     };
     // enumerate the index tuples of dims[lo..hi) (last fastest)
     auto each = [](const std::vector<int>& dims, int lo, int hi, const std::function<void(const int*)>& fn) {
@@ -1287,8 +1288,9 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
         std::vector<int> fd(na, 1);
         for (int64_t s : rk.second) {  // A columns: contracted positions of each block
           if (XA[s].empty()) continue;
-          if (XA[s].size() != 1 || XA[s][0].second != 1.0) return false;
+          if (XA[s].size() != 1 || std::fabs(XA[s][0].second) != 1.0) return false;
           const int64_t src = XA[s][0].first;
+          const double sgn = XA[s][0].second;
           group_weights(Am, s, na, rw, cw);
           block_strides(A, src, st);
           std::vector<int> dims(Am.rank);
@@ -1304,7 +1306,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
               c += (int64_t)t[n] * cw[n];
               off += (int64_t)t[n] * st[permA[n]];
             }
-            ac.push_back(Col{c, off, fs});
+            ac.push_back(Col{c, off, fs, sgn});
           });
         }
         auto ci = crow[x].find(rk.first);
@@ -1404,7 +1406,8 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
                 const int c = a_src ? s2 : d, j = a_src ? d : s2;
                 const int64_t e = ac[c].idx * g.n + cc[j].idx;
                 it.koff[d * kMaxDirect + s2] = koff[e];
-                it.kc[d * kMaxDirect + s2] = kcoef[e];
+                // the A column's sign enters every product it is in: C, dA and dB
+                it.kc[d * kMaxDirect + s2] = kcoef[e] * ac[c].sgn;
               }
             return it;
           };
