@@ -43,7 +43,7 @@ class sym_leg(ctypes.Structure):
 
 
 TUNE_FIELDS = ("tc_min_mn", "tc_min_k", "tc_max_k", "direct_max", "direct_chunk", "rows_spans", "splitk_ctas",
-               "thin_slice", "tc_order", "tc_group", "direct_mixed")
+               "thin_slice", "tc_order", "tc_group", "direct_mixed", "tc_all")
 
 
 class sym_tune(ctypes.Structure):

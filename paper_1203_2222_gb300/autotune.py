@@ -23,6 +23,7 @@ from . import symtensor as st
 from .symtensor import SymError
 
 SPACE = {
+    "tc_all": [0, 1],                         # every GEMM on the tensor cores (one launch per phase)
     "tc_min_mn": [16, 32, 48, 64, 96, 128],  # tensor cores vs CUDA cores (sector width)
     "tc_min_k": [16, 32, 48, 64, 96],         # ... (reduction depth)
     "direct_max": [0, 2, 4],                  # direct contraction of tiny-matrix sectors

@@ -908,6 +908,7 @@ sym_tune& tune_state() {
     d.tc_order = 0;
     d.tc_group = 8;
     d.direct_mixed = 1;
+    d.tc_all = 0;
     // SYM_TUNE="name=value,...": any parameter (names as in sym_tune)
     if (const char* e = std::getenv("SYM_TUNE")) {
       std::string all(e);
@@ -924,7 +925,8 @@ sym_tune& tune_state() {
                  : k == "direct_max" ? &d.direct_max : k == "direct_chunk" ? &d.direct_chunk
                  : k == "rows_spans" ? &d.rows_spans : k == "splitk_ctas" ? &d.splitk_ctas
                  : k == "thin_slice" ? &d.thin_slice : k == "tc_order" ? &d.tc_order
-                 : k == "tc_group" ? &d.tc_group : k == "direct_mixed" ? &d.direct_mixed : nullptr;
+                 : k == "tc_group" ? &d.tc_group : k == "direct_mixed" ? &d.direct_mixed
+                 : k == "tc_all" ? &d.tc_all : nullptr;
           if (f) *f = v;
         }
         p = q + 1;
@@ -946,7 +948,8 @@ void set_tune(const sym_tune& t) {
   if (!in(t.tc_min_mn, 1, 1 << 30) || !in(t.tc_min_k, 1, 1 << 30) || !in(t.tc_max_k, t.tc_min_k, 1 << 30) ||
       !in(t.direct_max, 0, kMaxDirect) || !in(t.direct_chunk, 32, 1 << 16) || t.direct_chunk % 32 ||
       !in(t.rows_spans, 1, 64) || !in(t.splitk_ctas, 0, 64) || !in(t.thin_slice, 256, 1 << 20) ||
-      t.thin_slice % 256 || !in(t.tc_order, 0, 1) || !in(t.tc_group, 0, 256) || !in(t.direct_mixed, 0, 1))
+      t.thin_slice % 256 || !in(t.tc_order, 0, 1) || !in(t.tc_group, 0, 256) || !in(t.direct_mixed, 0, 1) ||
+      !in(t.tc_all, 0, 1))
     fail(SYM_ERR_ARG, "planning parameter out of range");
   std::lock_guard<std::mutex> g(tune_mu);
   tune_state() = t;
@@ -966,6 +969,7 @@ namespace {
 // very long reductions are split across CTAs there).  The thresholds and
 // the schedule parameters are the planning parameters below.
 int choose_kind(bool f64, int64_t m, int64_t n, int64_t k, const sym_tune& t) {
+  if (!f64 && t.tc_all) return 0;
   if (m <= 8 && n <= 8) return 3;
   if (k <= 16 && n <= 16) return 4;
   const int simt = n <= 16 ? 2 : 1;

@@ -18,7 +18,7 @@ from tests.conftest import ROOT
 pytestmark = pytest.mark.gpu
 
 FORCED = {
-    "all_tensor_cores": {"SYM_TC_MIN_MN": "1", "SYM_TC_MIN_K": "1", "SYM_TC_MAX_K": "100000000"},
+    "all_tensor_cores": {"SYM_TUNE": "tc_all=1,direct_max=0", "SYM_TC_MAX_K": "100000000"},
     "all_cuda_cores": {"SYM_TC_MIN_MN": "1000000000"},
     "no_direct_sectors": {"SYM_DIRECT_MAX": "0"},
     # the schedule parameters at their extremes: one-run rows tiles, 32-position

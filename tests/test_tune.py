@@ -13,10 +13,10 @@ from paper_1203_2222_gb300 import synthetic
 d = P.tune_get()
 assert d == {"tc_min_mn": 64, "tc_min_k": 48, "tc_max_k": 16384, "direct_max": 4, "direct_chunk": 1024,
              "rows_spans": 8, "splitk_ctas": 2, "thin_slice": 4096, "tc_order": 0, "tc_group": 8,
-             "direct_mixed": 1}, d
+             "direct_mixed": 1, "tc_all": 0}, d
 e0 = P.tune_epoch()
 for bad in ({"direct_max": 5}, {"direct_chunk": 100}, {"tc_max_k": 10}, {"thin_slice": 100}, {"tc_order": 2},
-            {"rows_spans": 0}, {"tc_group": -1}, {"direct_mixed": 2}):
+            {"rows_spans": 0}, {"tc_group": -1}, {"direct_mixed": 2}, {"tc_all": 3}):
     try:
         P.tune_set(**bad)
         raise SystemExit(f"accepted {bad}")
@@ -46,6 +46,9 @@ assert kinds()[2] > 0  # the MPO step back on the GEMMs
 P.tune_set(direct_max=4, direct_mixed=0)
 k2 = kinds()
 assert k2[2] == 0 and k2[1] >= n0  # the all-direct MPO step stays direct; mixed plans keep every sector on GEMMs
+P.tune_set(direct_max=0, tc_all=1)
+k3 = kinds()
+assert k3[0] == k3[1] > 0  # every GEMM of L.A on the tensor cores
 P.tune_set(**d)
 assert kinds() == (tc0, n0, w0)
 print("TUNE OK")
