@@ -615,7 +615,7 @@ def run_ours(args, rank, world):
     launches_per_step = sum(p.profile_read(ph)["launches"] for p in plans for ph in P.PHASES.values())
     if graph is None:
         for p in plans:
-            p.profile(True)  # eager: record over the timed region itself
+            p.profile(False)  # eager: the timed region runs without event records
 
     def one_step():
         if graph is not None:
@@ -663,6 +663,13 @@ def run_ours(args, rank, world):
             torch.cuda.synchronize()
             accumulate()
     else:
+        # per-kernel device times: K more eager steps with the event pairs on
+        for p in plans:
+            p.profile(True)
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            run_once(data, G)
+        torch.cuda.synchronize()
         accumulate()
         for p in plans:
             p.profile(False)

@@ -75,8 +75,10 @@ def mera_energy(S, t, w, u, h, one, checkpoint=False):
     """E = <psi|h|psi> / <psi|psi> (autograd-aware in t, w and u)."""
     if checkpoint:
         Srho = mera_environment_structure(S, t.dtype)
+        # the environment draws no random numbers: no RNG state to save, which
+        # also keeps the step capturable in a CUDA graph
         rho = torch.utils.checkpoint.checkpoint(lambda tt, ww: mera_environment(S, tt, ww)[0], t, w,
-                                                use_reentrant=False)
+                                                use_reentrant=False, preserve_rng_state=False)
     else:
         rho, Srho = mera_environment(S, t, w)
     Y, Sy = _contract(S["u"], u, Srho, rho, [2, 3], [0, 2])       # (c, d, a3', b1')
