@@ -550,7 +550,7 @@ def run_ours(args, rank, world):
         space = autotune.SPACE if not args.tune_space else {k: autotune.SPACE[k] for k in args.tune_space.split(",")}
         known = autotune.load(args.workload, table)  # the search starts from the better of defaults and this
         params, ms_t, hist = autotune.tune(lambda: run_once(data, G), space=space, graph=not args.no_graph,
-                                           starts=[known] if known else [],
+                                           starts=list(autotune.PRESETS) + ([known] if known else []),
                                            log=lambda m: print("# " + m, file=sys.stderr, flush=True))
         autotune.save(args.workload, params, ms_t, hist[0]["ms"], len(hist), path=table)
         tuning = {"source": "autotuner search", "params": params, "evaluations": len(hist),

@@ -266,9 +266,10 @@ int sym_plan_profile_kernel(sym_plan plan, int kernel, int* launches,
  *   direct_mixed 1: a contraction may mix direct sectors with GEMM sectors;
  *     0: its sectors go direct only when all of them qualify (no extra
  *     launches for a few tiny sectors of a large contraction);
- *   tc_all 0: 1 sends every GEMM of a split-BF16 plan to the tensor cores
- *     (small sectors padded into 128 x 128 tiles), so a GEMM phase is one
- *     launch instead of one per CUDA-core kind.
+ *   tc_all 0: 1 sends every GEMM of a split-BF16 plan with k <= tc_max_k to
+ *     the tensor cores (small sectors padded into 128 x 128 tiles), so a
+ *     GEMM phase is one launch instead of one per CUDA-core kind; longer
+ *     reductions keep the CUDA-core kernels, which split them across CTAs.
  * sym_tune_set rejects a value out of range with SYM_ERR_ARG.             */
 typedef struct {
   int tc_min_mn, tc_min_k, tc_max_k;

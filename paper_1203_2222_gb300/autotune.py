@@ -36,6 +36,15 @@ SPACE = {
     "tc_group": [0, 4, 8, 16, 32],            # tcgen05 tiles: row tiles per group (L2 panel reuse)
 }
 
+# Whole configurations a single-parameter step cannot reach from each other
+# (they change several parameters at once); the descent starts from the
+# fastest of these, the defaults and any stored entry.
+PRESETS = (
+    {"tc_all": 1, "direct_max": 4, "direct_mixed": 0},  # one tensor-core launch per GEMM phase, MPO steps direct
+    {"tc_all": 1, "direct_max": 4, "direct_mixed": 1},
+    {"tc_all": 0, "direct_max": 0, "tc_min_mn": 16, "tc_min_k": 16},  # no direct path, narrow sectors on tensor cores
+)
+
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
 
@@ -89,14 +98,15 @@ def time_step(step, reps=5, warmup=2, trials=3, graph=True, flush_mb=256):
 
 
 def tune(step, space=None, start=None, reps=5, warmup=2, trials=3, rounds=2, tol=0.02, log=None, graph=True,
-         starts=()):
+         starts=PRESETS):
     """Coordinate descent over `space` from `start` (default: the current parameters).
 
     step() runs one step of the workload (it must plan through the cached
     plan functions, so that it re-plans after every parameter change, and
     be capturable in a CUDA graph when `graph`).  `starts` are further
-    starting points (e.g. an earlier table entry): the descent begins at the
-    fastest of them, so a search never ends worse than a known point.
+    starting points, each applied over the first one (by default the presets
+    above; a caller adds e.g. an earlier table entry): the descent begins at
+    the fastest of them, so a search never ends worse than a known point.
     Returns (parameters, ms per step, history); the parameters are installed.
     """
     space = SPACE if space is None else space

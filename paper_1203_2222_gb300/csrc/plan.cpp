@@ -969,7 +969,7 @@ namespace {
 // very long reductions are split across CTAs there).  The thresholds and
 // the schedule parameters are the planning parameters below.
 int choose_kind(bool f64, int64_t m, int64_t n, int64_t k, const sym_tune& t) {
-  if (!f64 && t.tc_all) return 0;
+  if (!f64 && t.tc_all && k <= t.tc_max_k) return 0;  // long reductions keep the split CUDA-core kernels
   if (m <= 8 && n <= 8) return 3;
   if (k <= 16 && n <= 16) return 4;
   const int simt = n <= 16 ? 2 : 1;

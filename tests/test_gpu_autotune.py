@@ -31,7 +31,7 @@ def test_autotune_installs_its_choice_and_keeps_parity():
     start = P.tune_get()
     try:
         params, ms, hist = autotune.tune(step, space={"direct_chunk": [64, 256], "direct_max": [0, 4]},
-                                         reps=2, warmup=1, trials=1, rounds=1)
+                                         reps=2, warmup=1, trials=1, rounds=1, starts=())
         assert P.tune_get() == params and ms > 0
         assert len(hist) >= 3 and all(h["ms"] > 0 for h in hist)
         assert params["direct_chunk"] in (64, 256, start["direct_chunk"])
