@@ -440,19 +440,16 @@ WORKLOADS = {"u1_mps_heff": MPSWorkload, "su2_recouple": SU2Workload, "u1_two_si
 # the captured launches, applied to the full launch's algorithmic bytes.
 TRAFFIC = {
     "u1_mps_heff": {  # profiles/traffic_u1_mps_heff.md
-        "box_flat": {"bytes_per_launch": 8020045, "sha": "74ba81806ea8ef80"},
-        "box": {"bytes_per_launch": 7493888, "sha": "74ba81806ea8ef80"},
-        "gemm_tc": {"bytes_per_launch": 13579712, "sha": "9b1e09588d5fca4d"},
-        "gemm_rows": {"bytes_per_launch": 3177216, "sha": "7dca7cc9913fd694"},
-        "gemm_thin": {"bytes_per_launch": 3174963, "sha": "7dca7cc9913fd694"},
-        "gemm_wide": {"bytes_per_launch": 70997, "sha": "7dca7cc9913fd694"},
-        "gemm_tile": {"bytes_per_launch": 44971, "sha": "7dca7cc9913fd694"},
+        "gemm_tc": {"bytes_per_launch": 13773824, "sha": "1a9aa9bdfa7cce0f"},
+        "box_flat": {"bytes_per_launch": 5857248, "sha": "b7242e8ca118cb38"},
+        "box": {"bytes_per_launch": 13079040, "sha": "b7242e8ca118cb38"},
+        "direct": {"bytes_per_launch": 11909291, "sha": "32a083d9660812bd"},
     },
     "su2_recouple": {  # profiles/gemm_tc_su2_recouple.md (full size, forward and backward launches)
-        "gemm_tc": {"bytes_per_launch": 61084875776, "sha": "9b1e09588d5fca4d"},
+        "gemm_tc": {"bytes_per_launch": 61084875776, "sha": "1a9aa9bdfa7cce0f"},
     },
     "u1_two_site_batch": {  # profiles/direct_u1_two_site_batch.md (128 of the 512 problems)
-        "direct": {"ratio": 0.95, "sha": "10db12e88424ae88"},
+        "direct": {"ratio": 0.97, "sha": "32a083d9660812bd"},
     },
 }
 KERNEL_SOURCES = {
