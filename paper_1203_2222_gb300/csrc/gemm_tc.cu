@@ -353,6 +353,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
       const GemmTile t = tiles[ti];
       const TcSector s = secs[t.sector];
+      // a small sector fills part of the tile: rows past m and 32-column
+      // chunks past n are neither read from TMEM nor stored
+      const int row_base = t.mt * BM + q * 32;
+      const bool rows_live = row_base < s.m;
+      const int ncols = min(BN, s.n - t.nt * BN);
       // this thread's row of the 128 x 128 tile, summed over the k chunks
       float racc[BN];
 #pragma unroll
@@ -363,13 +368,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           break;
         }
         tc_fence_after();
+        if (rows_live) {
 #pragma unroll
-        for (int c = 0; c < BN; c += 32) {
-          uint32_t r[32];
-          tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
-          tmem_ld_wait();
+          for (int c = 0; c < BN; c += 32) {
+            if (c >= ncols) break;
+            uint32_t r[32];
+            tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
+            tmem_ld_wait();
 #pragma unroll
-          for (int i = 0; i < 32; ++i) racc[c + i] += __uint_as_float(r[i]);
+            for (int i = 0; i < 32; ++i) racc[c + i] += __uint_as_float(r[i]);
+          }
         }
         tc_fence_before();
         __syncwarp();
@@ -378,20 +386,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (acc == 0) aphase ^= 1u;
       }
       if (!ok) break;
+      if (!rows_live) continue;
       // transpose through shared memory: coalesced row segments of C
-      const int row_base = t.mt * BM + q * 32;
+      const int nrows = min(32, s.m - row_base);
 #pragma unroll
       for (int c = 0; c < BN; c += 32) {
+        if (c >= ncols) break;
         const int col0 = t.nt * BN + c;
 #pragma unroll
         for (int i = 0; i < 32; ++i) buf[lane * EPI_PITCH + i] = racc[c + i];
         __syncwarp();
         const int col = col0 + lane;
         if (col < s.n)
-          for (int rr = 0; rr < 32; ++rr) {
-            const int row = row_base + rr;
-            if (row < s.m) C[s.c_off + (int64_t)row * s.ldc + col] = s.alpha * buf[rr * EPI_PITCH + lane];
-          }
+          for (int rr = 0; rr < nrows; ++rr)
+            C[s.c_off + (int64_t)(row_base + rr) * s.ldc + col] = s.alpha * buf[rr * EPI_PITCH + lane];
         __syncwarp();
       }
     }
