@@ -22,6 +22,11 @@ non-Abelian Symmetries" (arXiv:1203.2222):
                 generator-based invariance residual (Ch. 5, Eq. Tinv).
 * ``contract``  Dense brute-force contraction (Ch. 5, Eq. tensormult) and the
                 dense gradient, extracted back to blocks.
+* ``z2f``       Fermion-parity tensors (the thesis's conclusion): parity
+                labels, swap signs of permutations and contractions.
+* ``svd``       Blockwise singular value decomposition (Ch. 5, Eq. svd0 and
+                svd1): block-diagonal form, SVD of every block, truncation,
+                factors recast as tensors.
 
 Every function works in float64 with no blocking, fusion or reordering beyond
 what the definition states.
@@ -30,5 +35,6 @@ Pins (tests/test_oracle_*.py, ``-m "not gpu"``) tie each part to values the
 paper prints or to mathematics: printed CG values and omega matrices, CG
 orthogonality, ladder-operator relations, 6j closed forms / orthogonality /
 tetrahedral symmetry, generator invariance of embedded tensors, charge
-conservation of dense products, printed storage counts and bond dimensions.
+conservation of dense products, printed storage counts and bond dimensions,
+the dense SVD's spectrum and the Eckart-Young optimum of a truncation.
 """
