@@ -41,7 +41,7 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--workload", choices=["u1_mps_heff", "su2_recouple", "u1_two_site_batch", "u1_mera_grad",
-                                           "z2f_mps_heff"],
+                                           "z2f_mps_heff", "u1_two_site_svd"],
                     default="u1_mps_heff",
                     help="u1_mps_heff (default, the metric's configuration), the large-sector su2_recouple, "
                          "the 512-problem u1_two_site_batch or the MERA gradient u1_mera_grad")
@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--tune-space", default=None,
                     help="comma-separated planning parameters the search varies (default: all of autotune.SPACE)")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = SVDWorkload if args.workload == "u1_two_site_svd" else WORKLOADS[args.workload]
     args.steps = wl.default_steps if args.steps is None else args.steps
     args.warmup = wl.default_warmup if args.warmup is None else args.warmup
     args.fp64_steps = wl.default_fp64_steps if args.fp64_steps is None else args.fp64_steps
@@ -427,7 +427,7 @@ class MeraWorkload:
 
 
 WORKLOADS = {"u1_mps_heff": MPSWorkload, "su2_recouple": SU2Workload, "u1_two_site_batch": BatchWorkload,
-             "u1_mera_grad": MeraWorkload, "z2f_mps_heff": Z2FMPSWorkload}
+             "u1_mera_grad": MeraWorkload, "z2f_mps_heff": Z2FMPSWorkload}  # u1_two_site_svd: SVDWorkload below
 
 
 # ---------------------------------------------------------------- roofline ---
@@ -451,6 +451,9 @@ TRAFFIC = {
     "u1_two_site_batch": {  # profiles/direct_u1_two_site_batch.md (128 of the 512 problems)
         "direct": {"ratio": 0.97, "sha": "32a083d9660812bd"},
     },
+    "u1_two_site_svd": {  # profiles/svd_u1_two_site_svd.md (full size, mean of 10 launches)
+        "svd_jacobi": {"bytes_per_launch": 8711347, "sha": "2435570dca9e7f53"},
+    },
 }
 KERNEL_SOURCES = {
     "box": ["box.cu", "kernels.h", "pdl.h"], "box_flat": ["box.cu", "kernels.h", "pdl.h"],
@@ -458,6 +461,7 @@ KERNEL_SOURCES = {
     "gemm_tile": ["gemm_simt.cu", "kernels.h", "pdl.h"], "gemm_wide": ["gemm_simt.cu", "kernels.h", "pdl.h"],
     "gemm_thin": ["gemm_simt.cu", "kernels.h", "pdl.h"], "gemm_rows": ["gemm_simt.cu", "kernels.h", "pdl.h"],
     "direct": ["direct.cu", "kernels.h", "pdl.h"],
+    "svd_jacobi": ["svd.cu"],
 }
 
 
@@ -787,6 +791,217 @@ def run_ours(args, rank, world):
         "tuning": tuning,
     }
     return out, flops
+
+
+# ------------------------------------------------------------- blockwise SVD ---
+
+SVD_METRIC = "blockwise FP64 SVD + truncation of the two-site tensor, per second"
+# FP64 peak: 1.25 TFLOP/s nominal over 152 SMs at the 2070 MHz maximum clock
+# is 4 flops (2 FMAs) per SM per clock, scaled to the sampled clock
+FP64_FLOPS_PER_SM_CLK = 4.0
+FP32_FLOPS_PER_SM_CLK = 256.0  # 128 FP32 FMAs per SM per clock
+
+
+class SVDWorkload:
+    describe = ("u1_two_site_svd: theta[a, s1, s2, b] of the MPS chain (D = 2048 over q = -20..20, Gaussian profile "
+                "sigma 6; phys {0:1, 1:1}; total charge 0) as the matrix (a, s1) x (s2, b): 41 diagonal blocks up "
+                "to 272 x 272, FP64 blockwise SVD, truncated to chi = 2048 singular values, factors U and S V")
+    default_steps = 20
+    default_warmup = 3
+    default_fp64_steps = 0
+
+
+def _svd_inputs(P):
+    from paper_1203_2222_gb300 import synthetic
+    w = synthetic.u1_two_site_svd()
+    S = P.Structure(P.U1, w["theta"])
+    return w, S, synthetic.normal(w["seed"], S.numel)
+
+
+def run_svd(args, rank, world):
+    """Blockwise FP64 SVD workload: one step = P.svd(theta, 2, chi) -- the
+    Jacobi launch, the singular values to the host for the truncation, and
+    the factor launch writing U and S V."""
+    import torch
+    import paper_1203_2222_gb300 as P
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w, S, vals = _svd_inputs(P)
+    T = P.SymTensor(S, torch.as_tensor(vals).to(dev))
+    chi, nrow = w["chi"], w["nrow"]
+    plan = P.svd_plan(S, nrow)
+
+    def step(t):
+        return P.svd(t, nrow, chi=chi, absorb=2)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 1)):
+        step(T)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(T)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = args.steps * world / (ms * 1e-3)
+
+    # per-kernel device times (the same launches, timed one by one)
+    kms = {"svd_jacobi": 0.0, "svd_factor": 0.0}
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        plan.execute(T.data)
+        e1.record(stream)
+        plan.factors(2)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        kms["svd_jacobi"] += e0.elapsed_time(e1)
+        kms["svd_factor"] += e1.elapsed_time(e2)
+    f64, f32 = plan.flops()
+    sweeps64, _ = plan.stats()
+    sweeps32, _ = plan.stats(fp32=True)
+    kernels = {k: {"symbol": k + "_kernel", "launches": args.steps, "ms": round(v, 4),
+                   "share": round(v / max(sum(kms.values()), 1e-12), 4)} for k, v in kms.items()}
+    jac_s = kms["svd_jacobi"] * 1e-3 / args.steps
+    mhz = clk.get("sm_mhz") or 2070.0
+    peak64 = 152 * FP64_FLOPS_PER_SM_CLK * mhz * 1e6 / 1e12
+    peak32 = 152 * FP32_FLOPS_PER_SM_CLK * mhz * 1e6 / 1e12
+    roof = {"bound": "alu", "kernel": "svd_jacobi", "symbol": "svd_jacobi_kernel",
+            "achieved": round(f64 / jac_s / 1e12, 5), "peak": round(peak64, 4), "unit": "TFLOP/s",
+            "frac": round(f64 / jac_s / 1e12 / peak64, 4), "traffic": svd_traffic(),
+            "algorithmic_per_launch": f64, "fp32_flops_per_launch": f32,
+            "avg_launch_us": round(jac_s * 1e6, 2), "launches_timed": args.steps,
+            "peak_source": "FP64 ALU: 152 SMs x 4 flops/clk (1.25 TFLOP/s nominal at 2070 MHz) x sampled SM clock",
+            "sweeps_fp64_max": max(sweeps64), "sweeps_fp32_max": max(sweeps32)}
+    # the step's floor: FP64 flops at the FP64 peak plus FP32 flops at the FP32 peak
+    t_roof = f64 / (peak64 * 1e12) + f32 / (peak32 * 1e12)
+    step_roof = {"t_roof_ms": round(t_roof * 1e3, 4), "t_meas_ms": round(ms_per_step, 4),
+                 "frac": round(t_roof / (ms_per_step * 1e-3), 4), "bound": "alu",
+                 "fp64_flops": f64, "fp32_flops": f32}
+
+    # end to end: pinned host theta -> device, SVD, U, S and S V back to the host
+    host_in = torch.as_tensor(vals).pin_memory()
+    dev_in = torch.empty_like(T.data)
+    Us, Vs = plan.bond(plan.truncation(plan.execute(T.data).cpu().numpy(), chi))
+    host_u = torch.empty(Us.numel, dtype=torch.float64).pin_memory()
+    host_v = torch.empty(Vs.numel, dtype=torch.float64).pin_memory()
+    host_s = torch.empty(chi, dtype=torch.float64).pin_memory()
+    h2d, d2h = host_in.numel() * 8, (host_u.numel() + host_v.numel() + host_s.numel()) * 8
+
+    def e2e_step():
+        dev_in.copy_(host_in, non_blocking=True)
+        U, Sk, V = step(P.SymTensor(S, dev_in))
+        host_u.copy_(U.data, non_blocking=True)
+        host_v.copy_(V.data, non_blocking=True)
+        host_s[:Sk.numel()].copy_(Sk, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    ee = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+        ee.append((e0, e1))
+    ms_e2e = sum(a.elapsed_time(b) for a, b in ee) / args.steps
+    P.device_status()
+
+    out = {
+        "metric": SVD_METRIC, "value": round(value, 4), "unit": "SVD/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": SVDWorkload.describe,
+                   "precision": "FP64 result: FP32 Jacobi sweeps seed FP64 Newton-Schulz + FP64 Jacobi sweeps",
+                   "blocks": plan.nblocks, "singular_values": plan.nsv, "chi": chi,
+                   "l2": "flushed between timed steps (256 MiB write)", "launch": "eager (host truncation)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
+        "e2e": {"value": round(1e3 / ms_e2e * world, 4), "unit": "SVD/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e, 4)},
+        "clocks": clk, "gpu_launches": 2 * args.steps,
+    }
+    return out
+
+
+def svd_traffic():
+    t = TRAFFIC["u1_two_site_svd"]["svd_jacobi"]
+    return t["bytes_per_launch"] if t["sha"] == kernel_source_sha("svd_jacobi") else None
+
+
+def _oracle_svd_step(w, To):
+    from oracle import svd as osvd
+    fac, _ = osvd.svd("u1", To, w["nrow"])
+    keep = osvd.truncation({x: f[1] for x, f in fac.items()}, w["chi"])
+    osvd.factors("u1", To, w["nrow"], keep, absorb=2, fac=fac)
+    return fac
+
+
+def _oracle_svd_inputs():
+    from oracle import u1
+    from paper_1203_2222_gb300 import synthetic
+    w = synthetic.u1_two_site_svd()
+    legs = [u1.Leg(*l) for l in w["theta"]]
+    n = u1.layout(legs, 0)[2]
+    return w, (legs, 0, synthetic.normal(w["seed"], n))
+
+
+def cpu_baseline_svd(steps):
+    w, To = _oracle_svd_inputs()
+    n = max(steps, 1) * 3
+    t0 = time.perf_counter()
+    for _ in range(n):
+        fac = _oracle_svd_step(w, To)
+    dt = time.perf_counter() - t0
+    return {"value": round(n / dt, 4), "unit": "SVD/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{n} full steps of the same workload (numpy SVD of every block, truncation, factors), "
+                      f"{dt:.1f} s"}
+
+
+def run_reference_svd(args):
+    """Oracle reference arm for u1_two_site_svd: each step is the oracle's blockwise SVD,
+    truncation and factors of the same tensor."""
+    w, To = _oracle_svd_inputs()
+    for _ in range(args.warmup):
+        _oracle_svd_step(w, To)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_svd_step(w, To)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    sample = "step = the oracle's blockwise SVD (numpy, FP64) + truncation + factors of the same tensor"
+    return {
+        "metric": SVD_METRIC, "value": round(value, 4), "unit": "SVD/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": SVDWorkload.describe, "sample": sample},
+        "cpu_baseline": {"value": round(value, 4), "unit": "SVD/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "SVD/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
 
 
 # ------------------------------------------------------------ oracle (CPU) ---
@@ -1162,7 +1377,9 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        if args.workload == "su2_recouple":
+        if args.workload == "u1_two_site_svd":
+            out = run_reference_svd(args)
+        elif args.workload == "su2_recouple":
             out = run_reference_su2(args)
         elif args.workload == "u1_two_site_batch":
             out = run_reference_batch(args)
@@ -1178,10 +1395,15 @@ def main():
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
-    out, flops = run_ours(args, rank, world)
-    if rank == 0:
-        if not args.no_cpu_baseline:
+    if args.workload == "u1_two_site_svd":
+        out = run_svd(args, rank, world)
+        if rank == 0 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_svd(args.cpu_sample_steps)
+    else:
+        out, flops = run_ours(args, rank, world)
+        if rank == 0 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args, flops, args.cpu_sample_steps)
+    if rank == 0:
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -43,7 +43,8 @@
  * Execution calls are asynchronous on the given CUDA stream (a cudaStream_t
  * passed as void*, NULL = legacy default stream); they return SYM_ERR_CUDA if
  * a launch fails.  Device-side bounded waits that expire set a device error
- * word that sym_device_status() reports as SYM_ERR_TIMEOUT.
+ * word that sym_device_status() reports as SYM_ERR_TIMEOUT (SYM_ERR_NUMERIC
+ * for an SVD block that did not converge).
  */
 #ifndef SYMTENSOR_H
 #define SYMTENSOR_H
@@ -62,6 +63,7 @@ extern "C" {
 #define SYM_ERR_TIMEOUT (-5)           /* a device-side bounded wait expired */
 #define SYM_ERR_OOM (-6)               /* host or device allocation failed */
 #define SYM_ERR_UNSUPPORTED (-7)       /* valid request outside what is built */
+#define SYM_ERR_NUMERIC (-8)           /* an iterative method did not converge */
 
 #define SYM_U1 1
 #define SYM_SU2 2
@@ -326,10 +328,77 @@ int sym_contract_noalloc(sym_tensor A, sym_tensor B, int npairs,
                          const int* pairsA, const int* pairsB, int precision,
                          const void* a, const void* b, void* c, void* stream);
 
-/* Device error word: SYM_OK, or SYM_ERR_TIMEOUT if a bounded wait in a
- * persistent kernel expired since the last call (the word is then cleared).
- * Synchronizes the device. */
+/* Device error word: SYM_OK, SYM_ERR_TIMEOUT if a bounded wait in a
+ * persistent kernel expired, or SYM_ERR_NUMERIC if an SVD block did not
+ * converge, since the last call (the word is then cleared).  Synchronizes the
+ * device. */
 int sym_device_status(void);
+
+/* ------------------------------------------ blockwise factorization (SVD) ---
+ * Singular value decomposition of a symmetric tensor seen as a matrix
+ * (Ch. 5, "Factorization of a matrix", Eq. svd0 and svd1; Ch. 6, "Matrix
+ * multiplication and factorizations"): rows = legs 0..nrow-1, columns = the
+ * other legs.  The matrix is block diagonal in the fused label x of its row
+ * legs (U(1): sum of dir*q over the row legs; fermion parity: their parity
+ * sum mod 2); block M_x is m_x x n_x, its rows the row-label tuples in
+ * lexicographic order (leg 0 slowest, prod d rows each), its columns the
+ * column-label tuples likewise, and every tensor block is the row-major
+ * sub-matrix at its tuples' first row and column.  Every M_x is decomposed
+ * independently, M_x = U_x diag(S_x) V_x, in FP64 (one-sided Jacobi, one
+ * cluster of 8 CTAs per block).  U(1) and fermion-parity tensors, rank >= 2,
+ * 1 <= nrow < rank (SYM_ERR_UNSUPPORTED for SU(2), SYM_ERR_ARG otherwise).
+ *
+ * sym_svd_plan: plan the decomposition of tensors with T's structure:
+ *   nblocks = number of diagonal blocks (labels x with rows and columns),
+ *   nsv = sum over blocks of min(m_x, n_x) (the length of S).  The plan owns
+ *   a workspace of about 2.5 (max(m,n) + min(m,n)) min(m,n) doubles per
+ *   block.
+ * sym_svd_blocks: per block, ascending x: x, m_x, n_x (arrays of nblocks
+ *   ints; any may be NULL).
+ * sym_svd_execute: decompose the FP64 blocks `T` (device, T's layout).
+ *   Jacobi sweeps in FP32 choose the starting point, which is made
+ *   orthogonal in FP64 (Newton-Schulz); FP64 sweeps then converge to FP64
+ *   accuracy, so the result is an FP64 SVD.
+ *   S (device, nsv doubles, caller-owned) receives every block's singular
+ *   values in descending order, blocks in ascending x; the singular vectors
+ *   stay in the plan's workspace until the next execute.  Asynchronous; a
+ *   block that has not converged after 64 FP64 sweeps sets the device error word
+ *   (SYM_ERR_NUMERIC, see sym_device_status).
+ * sym_svd_stats: per block of the last execute (ascending x; either array
+ *   may be NULL): the sweeps it took (the last one found nothing to rotate)
+ *   and the rotations it applied, of the FP64 sweeps (fp32 = 0) or of the
+ *   FP32 sweeps (fp32 = 1).  Synchronizes the device.
+ * sym_svd_truncation: keep[b] from a host copy of execute's S (reading of
+ *   the truncation the thesis leaves open): every singular value sorted in
+ *   descending order (ties: smaller x first, then the block's own order);
+ *   the leading ones are kept while their number stays <= chi (chi < 0: no
+ *   limit) and, if cutoff > 0, while they exceed cutoff times the largest.
+ *   SYM_ERR_NUMERIC if a value is negative or not finite.  Host only.
+ * sym_svd_bond: keep[b] (0 <= keep[b] <= min(m_x, n_x), blocks in ascending
+ *   x, at least one > 0) singular vectors per block.  Returns the structures
+ *   of U (legs: the row legs, then the bond leg, incoming; total 0) and V
+ *   (legs: the bond leg, outgoing, then the column legs; T's total); the
+ *   bond leg lists the labels x with keep > 0, degeneracy keep.  The caller
+ *   destroys both.  Host work and one upload; later factors calls use it.
+ * sym_svd_factors: write U's and V's blocks (device, FP64, the layouts of
+ *   sym_svd_bond's structures) from the last execute: U's block (rows of row
+ *   tuple, x) = those rows of U_x's first keep columns, V's block (x, column
+ *   tuple) = those columns of V_x's first keep rows.  absorb 0: plain
+ *   factors; 1: U's columns multiplied by S; 2: V's rows multiplied by S.
+ *   Sk (device, sum of keep doubles, may be NULL) receives the kept
+ *   singular values in the bond leg's order.
+ *   Where a singular value is zero, the vector obtained by dividing by it
+ *   (U's column if m_x >= n_x, else V's row) is written as zeros; the
+ *   product U_x diag(S_x) V_x is unchanged.  Asynchronous.                  */
+typedef struct sym_svd_s* sym_svd;
+int sym_svd_plan(sym_tensor T, int nrow, sym_svd* out, int* nblocks, int64_t* nsv);
+int sym_svd_blocks(sym_svd plan, int* x, int* m, int* n);
+int sym_svd_execute(sym_svd plan, const double* T, double* S, void* stream);
+int sym_svd_stats(sym_svd plan, int fp32, int* sweeps, int64_t* rotations);
+int sym_svd_truncation(sym_svd plan, const double* S, int64_t chi, double cutoff, int* keep);
+int sym_svd_bond(sym_svd plan, const int* keep, sym_tensor* U, sym_tensor* V);
+int sym_svd_factors(sym_svd plan, int absorb, double* U, double* V, double* Sk, void* stream);
+int sym_svd_destroy(sym_svd plan);
 
 #ifdef __cplusplus
 }

@@ -9,4 +9,5 @@ this package is its Python front end.
 from .symtensor import (BF16X3, FP64, KERNEL_SYMBOLS, KERNELS, PHASES, SU2, U1, BatchPlan,  # noqa: F401
                         Plan, Structure, SymError, SymTensor, cached_plans, contract, contract_batch,
                         contract_batch_plan, contract_plan, device_status, fuse, fuse_plan, permute,
-                        permute_plan, split, split_plan, su2_F, su2_gamma, tune_epoch, tune_get, tune_set, Z2F)
+                        permute_plan, split, split_plan, su2_F, su2_gamma, svd, svd_plan, SVDPlan, tune_epoch,
+                        tune_get, tune_set, Z2F)

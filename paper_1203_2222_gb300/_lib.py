@@ -18,6 +18,7 @@ SYM_ERR_CUDA = -4
 SYM_ERR_TIMEOUT = -5
 SYM_ERR_OOM = -6
 SYM_ERR_UNSUPPORTED = -7
+SYM_ERR_NUMERIC = -8
 SYM_U1 = 1
 SYM_SU2 = 2
 SYM_Z2F = 3
@@ -27,7 +28,7 @@ SYM_PREC_BF16X3 = 2
 ERR_NAMES = {
     SYM_ERR_ARG: "SYM_ERR_ARG", SYM_ERR_INCOMPATIBLE_LEGS: "SYM_ERR_INCOMPATIBLE_LEGS",
     SYM_ERR_CUDA: "SYM_ERR_CUDA", SYM_ERR_TIMEOUT: "SYM_ERR_TIMEOUT", SYM_ERR_OOM: "SYM_ERR_OOM",
-    SYM_ERR_UNSUPPORTED: "SYM_ERR_UNSUPPORTED",
+    SYM_ERR_UNSUPPORTED: "SYM_ERR_UNSUPPORTED", SYM_ERR_NUMERIC: "SYM_ERR_NUMERIC",
 }
 
 
@@ -94,6 +95,14 @@ _SIGS = {
     "sym_tune_get": ([ctypes.POINTER(sym_tune)], _I),
     "sym_tune_set": ([ctypes.POINTER(sym_tune)], _I),
     "sym_tune_epoch": ([_IP], _I),
+    "sym_svd_plan": ([_P, _I, ctypes.POINTER(_P), _IP, _LP], _I),
+    "sym_svd_blocks": ([_P, _IP, _IP, _IP], _I),
+    "sym_svd_execute": ([_P, _P, _P, _P], _I),
+    "sym_svd_stats": ([_P, _I, _IP, _LP], _I),
+    "sym_svd_truncation": ([_P, _DP, ctypes.c_int64, ctypes.c_double, _IP], _I),
+    "sym_svd_bond": ([_P, _IP, ctypes.POINTER(_P), ctypes.POINTER(_P)], _I),
+    "sym_svd_factors": ([_P, _I, _P, _P, _P, _P], _I),
+    "sym_svd_destroy": ([_P], _I),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(lib, _name)

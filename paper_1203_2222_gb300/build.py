@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsymtensor.so")
-SOURCES = ["structure.cpp", "recouple.cpp", "plan.cpp", "capi.cpp", "box.cu", "gemm_simt.cu", "gemm_tc.cu", "direct.cu", "noalloc.cu"]
+SOURCES = ["structure.cpp", "recouple.cpp", "plan.cpp", "capi.cpp", "box.cu", "gemm_simt.cu", "gemm_tc.cu", "direct.cu", "noalloc.cu", "svd.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include")]
 

@@ -484,7 +484,8 @@ int sym_device_status(void) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) sym::fail(SYM_ERR_CUDA, std::string("device: ") + cudaGetErrorString(e));
     int code = sym::take_device_error();
-    if (code != SYM_OK) sym::fail(code, "a bounded device-side wait expired");
+    if (code != SYM_OK)
+      sym::fail(code, code == SYM_ERR_NUMERIC ? "an SVD block did not converge" : "a bounded device-side wait expired");
     return SYM_OK;
   });
 }

@@ -421,3 +421,122 @@ def su2_gamma(spins, tree_in, perm, tree_out):
     wk = max(k - 2, 0)
     return (G[:ni.value * no.value].reshape(no.value, ni.value),
             li[:ni.value * wk].reshape(ni.value, wk), lo[:no.value * wk].reshape(no.value, wk))
+
+
+class SVDPlan:
+    """Blockwise SVD of tensors with structure ``S``, rows = legs 0..nrow-1
+    (include/symtensor.h, sym_svd_*; Ch. 5, Eq. svd0 and svd1)."""
+
+    def __init__(self, S, nrow):
+        h, nb, ns = ctypes.c_void_p(), ctypes.c_int(), ctypes.c_int64()
+        L.check(L.lib.sym_svd_plan(S._h, int(nrow), _byref(h), _byref(nb), _byref(ns)))
+        self._h = h
+        self.structure, self.nrow = S, int(nrow)
+        self.nblocks, self.nsv = nb.value, ns.value
+        x, m, n = [(ctypes.c_int * self.nblocks)() for _ in range(3)]
+        L.check(L.lib.sym_svd_blocks(self._h, x, m, n))
+        self.labels, self.m, self.n = list(x), list(m), list(n)
+        self.full = [min(a, b) for a, b in zip(self.m, self.n)]
+        self._bond = None
+
+    def execute(self, data):
+        """S (device, float64, nsv): every block's singular values, descending."""
+        if data.dtype != torch.float64 or not data.is_cuda or data.numel() != self.structure.numel:
+            raise TypeError("SVD input must be the tensor's float64 CUDA blocks")
+        S = torch.empty(self.nsv, dtype=torch.float64, device=data.device)
+        L.check(L.lib.sym_svd_execute(self._h, _ptr(data.contiguous()), _ptr(S), _stream()))
+        return S
+
+    def stats(self, fp32=False):
+        """(sweeps, rotations) per block of the last execute, of its FP64
+        sweeps or (fp32) of its FP32 sweeps (synchronizes)."""
+        sw = (ctypes.c_int * self.nblocks)()
+        rot = (ctypes.c_int64 * self.nblocks)()
+        L.check(L.lib.sym_svd_stats(self._h, 1 if fp32 else 0, sw, rot))
+        return list(sw), list(rot)
+
+    def flops(self):
+        """(FP64 flops, FP32 flops) of the last execute (synchronizes).
+
+        Per sweep 3 FMAs per row of every pair visited, per rotation 4
+        multiply-adds per row of W and V; in FP64 also the two Newton-Schulz
+        steps (2 C^3 FMAs each), W = A V (R C^2) and the column norms.  An
+        FMA counts 2."""
+        out = []
+        for fp32 in (False, True):
+            sweeps, rotations = self.stats(fp32)
+            f = 0.0
+            for m, n, sw, rot in zip(self.m, self.n, sweeps, rotations):
+                R, C = max(m, n), min(m, n)
+                f += sw * (C * (C - 1) // 2) * 6.0 * R + rot * 6.0 * (R + C)
+                if not fp32:
+                    f += 2.0 * (4.0 * C ** 3 + R * C * C + R * C)
+            out.append(f)
+        return tuple(out)
+
+    def truncation(self, S_host, chi=None, cutoff=0.0):
+        """keep per block (ascending x) for a host copy of execute's S."""
+        S_host = np.ascontiguousarray(S_host, dtype=np.float64)
+        keep = (ctypes.c_int * self.nblocks)()
+        L.check(L.lib.sym_svd_truncation(self._h, S_host.ctypes.data_as(L._DP), -1 if chi is None else int(chi),
+                                         float(cutoff), keep))
+        return list(keep)
+
+    def bond(self, keep):
+        """(U structure, V structure) for ``keep`` vectors per block (cached for the last keep)."""
+        keep = tuple(int(k) for k in keep)
+        if self._bond is None or self._bond[0] != keep:
+            u, v = ctypes.c_void_p(), ctypes.c_void_p()
+            L.check(L.lib.sym_svd_bond(self._h, L.int_array(keep), _byref(u), _byref(v)))
+            self._bond = (keep, Structure(self.structure.group, total=0, _handle=u),
+                          Structure(self.structure.group, total=self.structure.total, _handle=v))
+        return self._bond[1], self._bond[2]
+
+    def factors(self, absorb=0):
+        """(U data, V data, kept S) of the last execute for the last bond."""
+        keep, Us, Vs = self._bond
+        U = torch.empty(Us.numel, dtype=torch.float64, device="cuda")
+        V = torch.empty(Vs.numel, dtype=torch.float64, device="cuda")
+        Sk = torch.empty(sum(keep), dtype=torch.float64, device="cuda")
+        L.check(L.lib.sym_svd_factors(self._h, int(absorb), _ptr(U), _ptr(V), _ptr(Sk), _stream()))
+        return U, V, Sk
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and L is not None and L.lib is not None:
+            L.lib.sym_svd_destroy(h)
+            self._h = None
+
+
+_SVD_PLANS = {}
+
+
+def svd_plan(S, nrow):
+    """SVD plan (cached) of structure S with rows = legs 0..nrow-1."""
+    key = (id(S), int(nrow))
+    hit = _SVD_PLANS.get(key)
+    if hit is None or hit[1] is not S:
+        hit = (SVDPlan(S, nrow), S)
+        _SVD_PLANS[key] = hit
+    return hit[0]
+
+
+def svd(T, nrow, chi=None, cutoff=0.0, absorb=0):
+    """Blockwise SVD T = U diag(S) V of a float64 U(1) or fermion-parity tensor
+    (rows = legs 0..nrow-1), truncated to the ``chi`` largest singular values
+    above ``cutoff`` times the largest (include/symtensor.h, sym_svd_truncation).
+
+    Returns (U, S, V): U has the row legs and an incoming bond leg, V an
+    outgoing bond leg and the column legs, S the kept values in bond order;
+    absorb = 1 / 2 multiplies S into U / V.  Without chi or cutoff nothing is
+    truncated and no host synchronisation happens.
+    """
+    plan = svd_plan(T.structure, nrow)
+    S = plan.execute(T.data)
+    if chi is None and not cutoff:
+        keep = plan.full
+    else:
+        keep = plan.truncation(S.cpu().numpy(), chi, cutoff)
+    Us, Vs = plan.bond(keep)
+    U, V, Sk = plan.factors(absorb)
+    return SymTensor(Us, U), Sk, SymTensor(Vs, V)

@@ -26,6 +26,9 @@ Workload shapes (all seeds are ``1234 + index``):
   two copies of the isometry w (upper leg in, three lower legs out) and a
   disentangler u (two lower legs in, two upper legs out) on the middle bond;
   h is the XXZ-like two-site term given entry by entry (``mera_h_entry``).
+* ``u1_two_site_svd``  the two-site tensor theta[a, s1, s2, b] of that chain
+  (D = 2048, total charge 0) as the matrix (a, s1) x (s2, b), truncated to
+  chi = 2048 singular values.
 * ``z2f_mps_heff``  the MPS chain above with fermion-parity legs: bond
   D = 2048 as {0: 1024, 1: 1024}, physical {0:1, 1:1}, MPO {0:3, 1:2}.
 * ``su2_recouple``  rank-4 SU(2) tensors, every leg with 2j = 0..8 and
@@ -103,6 +106,18 @@ def u1_mps_heff(D=2048, qmax=20, sigma=6.0, seed=1235):
             "steps": [((1, 2), (0, 2)), ((1, 3), (2, 1))],
             "seeds": {"L": seed, "A": seed + 100, "W": seed + 200, "R": seed + 300},
             "D": D}
+
+
+def u1_two_site_svd(D=2048, qmax=20, sigma=6.0, seed=1240):
+    """Legs of the two-site tensor theta[a, s1, s2, b] of the MPS chain above
+    (bond D over charges -qmax..qmax, Gaussian profile; directions in, in,
+    in, out; total charge 0), split as a matrix (a, s1) x (s2, b) and
+    truncated back to chi = D singular values: the truncation step that
+    follows an effective-Hamiltonian apply."""
+    qs, d = gaussian_degeneracies(D, -qmax, qmax, sigma)
+    phys_in = ([0, 1], [1, 1], -1)
+    theta = [(qs, d, -1), phys_in, phys_in, (qs, d, 1)]
+    return {"group": "u1", "theta": theta, "nrow": 2, "chi": D, "seed": seed, "D": D}
 
 
 def z2f_mps_heff(D=2048, seed=1239):

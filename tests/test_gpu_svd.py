@@ -1,0 +1,150 @@
+"""GPU parity of the blockwise SVD (include/symtensor.h, sym_svd_*) against the
+FP64 oracle (oracle/svd.py).
+
+What is unique is compared element by element: the singular values, the
+truncation counts (integer decisions taken on each side's own FP64 values),
+and the truncated product U diag(S) V.  The singular vectors are unique up
+to signs (and rotations inside degenerate values), so for them the test
+checks what makes them valid: orthonormal columns of U and rows of V.
+Tolerance: 1e-12 relative to the largest singular value (FP64 on both sides).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import svd as osvd  # noqa: E402
+from oracle import u1 as ou1  # noqa: E402
+from oracle import z2f as oz2f  # noqa: E402
+
+TOL = 1e-12
+
+
+def _P():
+    import paper_1203_2222_gb300 as P
+    return P
+
+
+def _mods(group):
+    P = _P()
+    return {"u1": (P.U1, ou1), "z2f": (P.Z2F, oz2f)}[group]
+
+
+def _tensor(group, legs, total, values):
+    P = _P()
+    g, m = _mods(group)
+    S = P.Structure(g, legs, total=total)
+    T = P.SymTensor(S, torch.as_tensor(values, dtype=torch.float64).cuda())
+    return S, T, ([m.Leg(*l) for l in legs], total, np.asarray(values, dtype=np.float64))
+
+
+def _dense_bond(group, X, first_is_bond):
+    """Dense matrix of a factor: (rows, bond) for U, (bond, cols) for V."""
+    _, m = _mods(group)
+    legs = [m.Leg(*l) for l in X.structure.legs]
+    d = m.embed(legs, X.structure.total, X.data.cpu().numpy())
+    return d.reshape(d.shape[0], -1) if first_is_bond else d.reshape(-1, d.shape[-1])
+
+
+def _check(group, legs, total, nrow, values, chi=None, cutoff=0.0):
+    P = _P()
+    S, T, To = _tensor(group, legs, total, values)
+    plan = P.svd_plan(S, nrow)
+    Sg = plan.execute(T.data).cpu().numpy()
+    fac, bd = osvd.svd(group, To, nrow)
+    Smax = max(float(np.max(fac[x][1])) for x in fac)
+    So = np.concatenate([fac[x][1] for x in sorted(fac)])
+    assert np.max(np.abs(Sg - So)) <= TOL * Smax
+    sweeps, _ = plan.stats()
+    sweeps32, _ = plan.stats(fp32=True)
+    assert max(sweeps) < 64 and max(sweeps32) <= 40
+    keep = plan.truncation(Sg, chi, cutoff)
+    ko = osvd.truncation({x: fac[x][1] for x in fac}, chi, cutoff)
+    assert keep == [ko[x] for x in plan.labels]
+    M = osvd.matrix(group, To, nrow)
+    Uo, kept, Vo = osvd.factors(group, To, nrow, ko, absorb=1, fac=fac)
+    _, m = _mods(group)
+    ref = m.embed(Uo[0], 0, Uo[2]).reshape(-1, sum(keep)) @ m.embed(Vo[0], Vo[1], Vo[2]).reshape(sum(keep), -1)
+    for absorb in (0, 1, 2):
+        U, Sk, V = P.svd(T, nrow, chi=chi, cutoff=cutoff, absorb=absorb)
+        Sk = Sk.cpu().numpy()
+        assert np.max(np.abs(Sk - np.concatenate([kept[x] for x in sorted(kept)]))) <= TOL * Smax
+        Um, Vm = _dense_bond(group, U, False), _dense_bond(group, V, True)
+        prod = Um @ (np.diag(Sk) if absorb == 0 else np.eye(len(Sk))) @ Vm
+        assert np.max(np.abs(prod - ref)) <= TOL * Smax
+        # orthonormal vectors (a vector of a numerically zero singular value
+        # is only defined up to the rest, and is written as zeros when exactly 0)
+        live = np.where(Sk > 1e-10 * Smax)[0]
+        if absorb != 1:
+            Ul = Um[:, live]
+            assert np.max(np.abs(Ul.T @ Ul - np.eye(len(live)))) <= TOL
+        if absorb != 2:
+            Vl = Vm[live, :]
+            assert np.max(np.abs(Vl @ Vl.T - np.eye(len(live)))) <= TOL
+        # U and V carry nothing outside their blocks (their layouts are the library's own)
+        for X in (U, V):
+            legsX = [m.Leg(*l) for l in X.structure.legs]
+            assert X.structure.numel == m.layout(legsX, X.structure.total)[2]
+    if chi is None and not cutoff:
+        assert np.max(np.abs(ref - M)) <= TOL * Smax
+    P.device_status()
+    return plan
+
+
+def _rand(group, legs, total, seed):
+    _, m = _mods(group)
+    n = m.layout([m.Leg(*l) for l in legs], total)[2]
+    return np.random.default_rng(seed).standard_normal(n)
+
+
+U1_SMALL = [([-1, 0, 1], [2, 3, 1], 1), ([0, 1], [2, 2], 1), ([-1, 0, 2], [1, 2, 2], -1), ([0, 1], [1, 3], -1)]
+Z2F_SMALL = [([0, 1], [3, 2], 1), ([0, 1], [1, 2], -1), ([0, 1], [2, 3], 1)]
+
+
+@pytest.mark.parametrize("group,legs,total,nrow", [
+    ("u1", U1_SMALL, 0, 2), ("u1", U1_SMALL, 1, 1), ("u1", U1_SMALL, -1, 3),
+    ("z2f", Z2F_SMALL, 0, 1), ("z2f", Z2F_SMALL, 1, 2)])
+def test_small_tensors(group, legs, total, nrow):
+    _check(group, legs, total, nrow, _rand(group, legs, total, 21))
+
+
+def test_ragged_blocks_tall_wide_odd():
+    # blocks from 1 x 1 to ~120 x 60 and ~60 x 120: odd and even column
+    # counts (the round-robin's bye), tall and wide (A = M^T), several warps
+    legs = [([-2, -1, 0, 1, 2], [3, 17, 40, 9, 1], -1), ([0, 1], [1, 1], -1), ([-3, -2, -1, 0, 1, 2, 3],
+                                                                               [2, 5, 33, 61, 20, 7, 1], 1)]
+    vals = _rand("u1", legs, 0, 22)
+    _check("u1", legs, 0, 2, vals)
+    _check("u1", legs, 0, 1, vals)
+    _check("u1", legs, 0, 2, vals, chi=40)
+    _check("u1", legs, 0, 1, vals, cutoff=0.2)
+
+
+def test_rank_deficient_block():
+    # every block has rank 1 (outer products): most singular values are 0,
+    # the product is still exact and nothing fails to converge
+    legs = [([-1, 0, 1], [4, 6, 3], 1), ([-1, 0, 1], [5, 2, 7], -1)]
+    P = _P()
+    S = P.Structure(P.U1, legs)
+    rng = np.random.default_rng(23)
+    vals = []
+    for d1, d2 in ((4, 5), (6, 2), (3, 7)):
+        vals.append(np.outer(rng.standard_normal(d1), rng.standard_normal(d2)).reshape(-1))
+    vals = np.concatenate(vals)
+    assert vals.size == S.numel
+    _check("u1", legs, 0, 1, vals, chi=3)
+    _check("u1", legs, 0, 1, vals)
+
+
+def test_two_site_theta_full_size():
+    # the two-site tensor theta[a, s1, s2, b] of the MPS workload (bond 2048
+    # over charges -20..20), truncated back to chi = 2048
+    P = _P()
+    from paper_1203_2222_gb300 import synthetic
+    w = synthetic.u1_two_site_svd()
+    legs, total = w["theta"], 0
+    S = P.Structure(P.U1, legs)
+    vals = synthetic.normal(w["seed"], S.numel)
+    _check("u1", legs, total, w["nrow"], vals, chi=w["chi"])
