@@ -13,12 +13,20 @@ tensors with the same block structure.  The steps, in that order:
    row label tuples are listed lexicographically (leg 0 slowest), each
    taking prod d rows, and likewise the column tuples; the tensor block,
    row-major with the row legs leading, is the (prod d_rows) x (prod d_cols)
-   sub-matrix at its tuples' first row and column;
-2. M_x = U_x diag(S_x) V_x (numpy's SVD of the block, thin, descending);
+   sub-matrix at its tuples' first row and column.  SU(2): rank-2 tensors
+   (the block-diagonal form of Eq. svd0), x = the spin 2j both legs carry;
+2. M_x = U_x diag(S_x) V_x (numpy's SVD of the block, thin, descending).
+   SU(2): the stored block is not the thesis's canonical T_j.  With the
+   normalisation of reading 5 the dense matrix is the direct sum of
+   M_x / sqrt(2j+1) times a (2j+1)-dimensional orthogonal map, so its
+   singular values are S_x / sqrt(2j+1), each 2j+1 times (pinned against the
+   dense SVD), and the factors whose contraction rebuilds T are
+   sqrt(2j+1) U_x and sqrt(2j+1) V_x with those values between them;
 3. truncation (reading 17): all singular values sorted in descending order
    (ties: smaller x first, then the block's own order); keep the leading
-   ones while their number stays <= chi, and only those above cutoff times
-   the largest; keep[x] = how many of block x were kept;
+   ones while their dense count (SU(2): 2j+1 each, else 1) stays <= chi,
+   and only those above cutoff times the largest; keep[x] = how many of
+   block x were kept;
 4. recast: U with legs (row legs..., bond) and V with legs (bond, column
    legs...).  The bond leg lists the labels x with keep[x] > 0, degeneracy
    keep[x]; it is incoming on U (U carries total label 0) and outgoing on V
@@ -28,29 +36,47 @@ tensors with the same block structure.  The steps, in that order:
    columns by S, absorb = 2 V's rows.
 """
 import itertools
+from math import sqrt
 
 import numpy as np
 
+from . import su2 as su2m
 from . import u1 as u1m
 from . import z2f as z2fm
 
 
 def _mod(group):
-    if group not in ("u1", "z2f"):
-        raise ValueError("blockwise SVD of U(1) and fermion-parity tensors")
-    return u1m if group == "u1" else z2fm
+    return {"u1": u1m, "z2f": z2fm, "su2": su2m}[group]
 
 
 def _key(group, legs, idx):
     """Fused label of `legs` at label positions `idx` (step 1)."""
     if group == "u1":
         return sum(l.dir * l.labels[i] for l, i in zip(legs, idx))
+    if group == "su2":
+        (l,), (i,) = legs, idx  # rank 2: the spin of the one row leg
+        return l.labels[i]
     return sum(l.labels[i] for l, i in zip(legs, idx)) % 2
 
 
 def _col_partner(group, total, y):
     """Row label x of the diagonal block that column label y belongs to."""
+    if group == "su2":
+        return y
     return total - y if group == "u1" else (total + y) % 2
+
+
+def _weight(group, x):
+    """Dense singular values one value of block x stands for."""
+    return x + 1 if group == "su2" else 1
+
+
+def _scale(group, x):
+    return sqrt(x + 1) if group == "su2" else 1.0
+
+
+def _positions(group, s):
+    return tuple(s[0]) if group == "su2" else tuple(s)
 
 
 def _enumerate(group, legs, partner):
@@ -69,6 +95,8 @@ def block_diagonal(group, T, nrow):
     """{x: (M_x, rows, cols)} for the x that have rows and columns (step 1)."""
     legs, total, data = T
     m = _mod(group)
+    if group == "su2" and (len(legs) != 2 or nrow != 1):
+        raise ValueError("SU(2): rank-2 tensors (the block-diagonal form)")
     data = np.asarray(data, dtype=np.float64)
     rl, cl = legs[:nrow], legs[nrow:]
     rows = _enumerate(group, rl, lambda k: k)
@@ -80,6 +108,7 @@ def block_diagonal(group, T, nrow):
         out[x] = (np.zeros((mx, nx)), rows[x], cols[x])
     secs, offs, _ = m.layout(legs, total)
     for s, o in zip(secs, offs):
+        s = _positions(group, s)
         rt, ct = tuple(s[:nrow]), tuple(s[nrow:])
         x = _key(group, rl, rt)
         M, rws, cls = out[x]
@@ -90,16 +119,18 @@ def block_diagonal(group, T, nrow):
 
 
 def svd(group, T, nrow):
-    """{x: (U_x, S_x, V_x)} (step 2) and the block-diagonal form."""
+    """{x: (U_x, S_x, V_x)} (step 2; SU(2): the tensor-level factors and the
+    dense singular values) and the block-diagonal form."""
     bd = block_diagonal(group, T, nrow)
     fac = {}
     for x, (M, _, _) in bd.items():
         U, S, V = np.linalg.svd(M, full_matrices=False)
-        fac[x] = (U, S, V)
+        c = _scale(group, x)
+        fac[x] = (U * c, S / c, V * c)
     return fac, bd
 
 
-def truncation(S_by_x, chi=None, cutoff=0.0):
+def truncation(S_by_x, chi=None, cutoff=0.0, group="u1"):
     """keep[x] (step 3)."""
     vals = [(-s, x, i) for x in sorted(S_by_x) for i, s in enumerate(S_by_x[x])]
     vals.sort()
@@ -107,12 +138,13 @@ def truncation(S_by_x, chi=None, cutoff=0.0):
     keep = {x: 0 for x in S_by_x}
     n = 0
     for neg, x, i in vals:
-        if chi is not None and n >= chi:
+        w = _weight(group, x)
+        if chi is not None and n + w > chi:
             break
         if cutoff > 0.0 and -neg <= cutoff * smax:
             break
         keep[x] += 1
-        n += 1
+        n += w
     return keep
 
 
@@ -133,10 +165,13 @@ def factors(group, T, nrow, keep, absorb=0, fac=None):
     rl, cl = legs[:nrow], legs[nrow:]
     bu, bv = bond_leg(group, keep, -1), bond_leg(group, keep, 1)
     legsU, legsV = list(rl) + [bu], [bv] + list(cl)
-    secsU, offsU, nU = m.layout(legsU, 0)
-    secsV, offsV, nV = m.layout(legsV, total)
+    totU = su2m.left_comb(2) if group == "su2" else 0
+    totV = su2m.left_comb(2) if group == "su2" else total
+    secsU, offsU, nU = m.layout(legsU, totU)
+    secsV, offsV, nV = m.layout(legsV, totV)
     Ud, Vd = np.zeros(nU), np.zeros(nV)
     for s, o in zip(secsU, offsU):
+        s = _positions(group, s)
         x = bu.labels[s[-1]]
         k = keep[x]
         U, S, _ = fac[x]
@@ -144,6 +179,7 @@ def factors(group, T, nrow, keep, absorb=0, fac=None):
         blk = U[r0:r0 + h, :k] * (S[:k] if absorb == 1 else 1.0)
         Ud[o:o + h * k] = blk.reshape(-1)
     for s, o in zip(secsV, offsV):
+        s = _positions(group, s)
         x = bv.labels[s[0]]
         k = keep[x]
         _, S, V = fac[x]
@@ -151,7 +187,7 @@ def factors(group, T, nrow, keep, absorb=0, fac=None):
         blk = V[:k, c0:c0 + w] * (S[:k, None] if absorb == 2 else 1.0)
         Vd[o:o + k * w] = blk.reshape(-1)
     kept = {x: fac[x][1][:keep[x]] for x in sorted(keep) if keep[x] > 0}
-    return (legsU, 0, Ud), kept, (legsV, total, Vd)
+    return (legsU, totU, Ud), kept, (legsV, totV, Vd)
 
 
 def matrix(group, T, nrow):
@@ -160,3 +196,9 @@ def matrix(group, T, nrow):
     d = _mod(group).embed(legs, total, data)
     r = int(np.prod([l.dim for l in legs[:nrow]], dtype=np.int64))
     return d.reshape(r, -1)
+
+
+def dense_values(group, kept):
+    """The kept singular values as the dense matrix has them, in the bond
+    leg's dense order (SU(2): each value 2j+1 times, the m index fastest)."""
+    return np.concatenate([np.repeat(kept[x], _weight(group, x)) for x in sorted(kept)])

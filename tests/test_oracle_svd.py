@@ -28,7 +28,7 @@ CASES = [("u1", _u1_rank4, 0, 2), ("u1", _u1_rank4, 1, 1), ("u1", _u1_rank4, -1,
 
 def _dense(group, T):
     legs, total, data = T
-    return (u1 if group == "u1" else z2f).embed(legs, total, data)
+    return svd._mod(group).embed(legs, total, data)
 
 
 def _bond_matrix(group, U, V):
@@ -144,3 +144,66 @@ def test_block_labels_follow_the_row_legs():
         assert any(t == rt for t, _, _ in bd[x][1])
         cq = -legs[2].labels[s[2]] - legs[3].labels[s[3]]
         assert x + cq == 1
+
+
+# ---- SU(2): rank-2 tensors, the block-diagonal form of Eq. svd0
+
+SU2_DIRS = [(1, -1), (1, 1), (-1, -1), (-1, 1)]
+
+
+def _su2_tensor(dirs, seed):
+    from oracle import su2
+    legs = [su2.Leg([0, 1, 2, 3], [3, 2, 4, 2], dirs[0]), su2.Leg([0, 1, 2, 3], [2, 3, 3, 1], dirs[1])]
+    tree = su2.left_comb(2)
+    n = su2.layout(legs, tree)[2]
+    return (legs, tree, np.random.default_rng(seed).standard_normal(n))
+
+
+@pytest.mark.parametrize("dirs", SU2_DIRS)
+def test_su2_values_are_the_dense_spectrum_with_multiplicity(dirs):
+    # the dense matrix is the direct sum over spins of the stored block over
+    # sqrt(2j+1) times an orthogonal (2j+1)-dimensional map
+    T = _su2_tensor(dirs, 31)
+    fac, _ = svd.svd("su2", T, 1)
+    keep = svd.truncation({x: f[1] for x, f in fac.items()}, group="su2")
+    ours = np.sort(svd.dense_values("su2", {x: fac[x][1][:keep[x]] for x in fac}))[::-1]
+    dense = np.linalg.svd(svd.matrix("su2", T, 1), compute_uv=False)
+    assert np.allclose(ours, dense[:len(ours)], rtol=1e-12, atol=1e-12)
+    assert np.all(dense[len(ours):] < 1e-12)
+
+
+@pytest.mark.parametrize("dirs", SU2_DIRS)
+def test_su2_factors_rebuild_the_tensor_and_are_isometries(dirs):
+    T = _su2_tensor(dirs, 33)
+    fac, _ = svd.svd("su2", T, 1)
+    keep = svd.truncation({x: f[1] for x, f in fac.items()}, group="su2")
+    U, kept, V = svd.factors("su2", T, 1, keep)
+    Um, Vm = _bond_matrix("su2", U, V)
+    S = svd.dense_values("su2", kept)
+    assert np.allclose(Um @ np.diag(S) @ Vm, svd.matrix("su2", T, 1), atol=1e-12)
+    assert np.allclose(Um.T @ Um, np.eye(len(S)), atol=1e-12)
+    assert np.allclose(Vm @ Vm.T, np.eye(len(S)), atol=1e-12)
+    from oracle import su2
+    for legsX, tree, d in (U, V):
+        assert su2.extract(legsX, tree, su2.embed(legsX, tree, d))[1] < 1e-12
+    for absorb in (1, 2):
+        A, _, B = svd.factors("su2", T, 1, keep, absorb=absorb)
+        Am, Bm = _bond_matrix("su2", A, B)
+        assert np.allclose(Am @ Bm, svd.matrix("su2", T, 1), atol=1e-12)
+
+
+def test_su2_truncation_counts_multiplets():
+    # chi counts dense singular values: a spin-j value costs 2j+1 of it, and
+    # when a whole multiplet fits the error is the dense optimum
+    T = _su2_tensor((1, -1), 35)
+    M = svd.matrix("su2", T, 1)
+    dense = np.linalg.svd(M, compute_uv=False)
+    fac, _ = svd.svd("su2", T, 1)
+    for chi in (1, 4, 9, 20):
+        keep = svd.truncation({x: f[1] for x, f in fac.items()}, chi=chi, group="su2")
+        n = sum(k * (x + 1) for x, k in keep.items())
+        assert n <= chi
+        U, kept, V = svd.factors("su2", T, 1, keep, absorb=1)
+        Um, Vm = _bond_matrix("su2", U, V)
+        err = np.linalg.norm(M - Um @ Vm)
+        assert err == pytest.approx(np.sqrt(np.sum(dense[n:] ** 2)), rel=1e-10, abs=1e-12)
