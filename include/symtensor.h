@@ -345,8 +345,14 @@ int sym_device_status(void);
  * column-label tuples likewise, and every tensor block is the row-major
  * sub-matrix at its tuples' first row and column.  Every M_x is decomposed
  * independently, M_x = U_x diag(S_x) V_x, in FP64 (one-sided Jacobi, one
- * cluster of 8 CTAs per block).  U(1) and fermion-parity tensors, rank >= 2,
- * 1 <= nrow < rank (SYM_ERR_UNSUPPORTED for SU(2), SYM_ERR_ARG otherwise).
+ * cluster of 8 CTAs per block).  U(1) and fermion-parity tensors of rank
+ * >= 2 with 1 <= nrow < rank; SU(2) tensors of rank 2 (nrow = 1; the block
+ * of spin x = 2j is M_x; SYM_ERR_UNSUPPORTED for higher ranks).  SU(2)
+ * values and factors follow the block normalisation of the contraction
+ * (1/sqrt(2j+1) per block): S holds the dense matrix's singular values
+ * sigma/sqrt(2j+1) (each standing for 2j+1 of them), and U and V are
+ * sqrt(2j+1) times the orthonormal block factors, so that contracting
+ * U's bond with S and V rebuilds T, and U, V are isometries densely.
  *
  * sym_svd_plan: plan the decomposition of tensors with T's structure:
  *   nblocks = number of diagonal blocks (labels x with rows and columns),
@@ -371,8 +377,9 @@ int sym_device_status(void);
  * sym_svd_truncation: keep[b] from a host copy of execute's S (reading of
  *   the truncation the thesis leaves open): every singular value sorted in
  *   descending order (ties: smaller x first, then the block's own order);
- *   the leading ones are kept while their number stays <= chi (chi < 0: no
- *   limit) and, if cutoff > 0, while they exceed cutoff times the largest.
+ *   the leading ones are kept while their dense count (SU(2): 2j+1 each,
+ *   else 1) stays <= chi (chi < 0: no limit) and, if cutoff > 0, while
+ *   they exceed cutoff times the largest.
  *   SYM_ERR_NUMERIC if a value is negative or not finite.  Host only.
  * sym_svd_bond: keep[b] (0 <= keep[b] <= min(m_x, n_x), blocks in ascending
  *   x, at least one > 0) singular vectors per block.  Returns the structures
@@ -384,7 +391,8 @@ int sym_device_status(void);
  *   sym_svd_bond's structures) from the last execute: U's block (rows of row
  *   tuple, x) = those rows of U_x's first keep columns, V's block (x, column
  *   tuple) = those columns of V_x's first keep rows.  absorb 0: plain
- *   factors; 1: U's columns multiplied by S; 2: V's rows multiplied by S.
+ *   factors; 1: U's columns multiplied by S; 2: V's rows multiplied by S
+ *   (SU(2): the orthonormal block factor times sigma).
  *   Sk (device, sum of keep doubles, may be NULL) receives the kept
  *   singular values in the bond leg's order.
  *   Where a singular value is zero, the vector obtained by dividing by it

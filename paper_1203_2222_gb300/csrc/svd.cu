@@ -64,6 +64,7 @@ struct SvdBlock {
   int v0, nv;  // pieces of V
   int slot;    // position of the block in ascending x
   int ks;      // first kept singular value of the block in the bond order
+  double vscale;  // SU(2): sqrt(2j+1) (the factors carry it, S is divided by it), else 1
   int64_t w;   // workspace offset: W (R x C, column-major), V (C x C), norms (C), sorted S (C), then
                // the Jacobi kernel's A (R x C), Newton-Schulz factor (C x C), FP32 W and V
   int64_t s;   // first singular value of the block in S and in the permutation
@@ -463,7 +464,7 @@ __global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThread
       const double u = __ldcg(nrm + i);
       rank += (u > v) || (u == v && i < j);
     }
-    S[b.s + rank] = v;
+    S[b.s + rank] = v / b.vscale;
     Ss[rank] = v;
     perm[b.s + rank] = j;
   }
@@ -483,8 +484,11 @@ __global__ void __launch_bounds__(kSvdThreads)
   const double* Ss = V + (int64_t)C * C + C;
   const int* pm = perm + b.s;
   const int tid = threadIdx.x;
+  // SU(2): the factors are vscale times the orthonormal ones and the values
+  // are divided by it; absorbing S gives the orthonormal factor times sigma
+  const double vs = b.vscale;
   if (Sk)
-    for (int j = tid; j < k; j += kSvdThreads) Sk[b.ks + j] = Ss[j];
+    for (int j = tid; j < k; j += kSvdThreads) Sk[b.ks + j] = Ss[j] / vs;
   for (int q = 0; q < b.nu; ++q) {
     const SvdPiece pc = pieces[b.u0 + q];
     const int64_t n = (int64_t)pc.rows * k;
@@ -495,10 +499,10 @@ __global__ void __launch_bounds__(kSvdThreads)
       double v;
       if (!b.trans) {
         const double w = W[r + pj * R];
-        v = absorb == 1 ? w : (s > 0.0 ? w / s : 0.0);
+        v = absorb == 1 ? w : (s > 0.0 ? vs * w / s : 0.0);
       } else {
         v = V[r + pj * C];
-        if (absorb == 1) v *= s;
+        v *= absorb == 1 ? s : vs;
       }
       U[pc.off + e] = v;
     }
@@ -513,10 +517,10 @@ __global__ void __launch_bounds__(kSvdThreads)
       double v;
       if (!b.trans) {
         v = V[c + pj * C];
-        if (absorb == 2) v *= s;
+        v *= absorb == 2 ? s : vs;
       } else {
         const double w = W[c + pj * R];
-        v = absorb == 2 ? w : (s > 0.0 ? w / s : 0.0);
+        v = absorb == 2 ? w : (s > 0.0 ? vs * w / s : 0.0);
       }
       Vt[pc.off + e] = v;
     }
@@ -530,6 +534,7 @@ struct TupleEntry {
 using TupleMap = std::unordered_map<std::vector<int>, TupleEntry, VecHash>;
 
 int fused_label(int group, const std::vector<Leg>& legs, int l0, const std::vector<int>& pos) {
+  if (group == SYM_SU2) return legs[l0].labels[pos[0]];  // rank 2: the spin of the one leg
   int k = 0;
   for (size_t i = 0; i < pos.size(); ++i) {
     const Leg& L = legs[l0 + i];
@@ -548,7 +553,7 @@ TupleMap enumerate_tuples(int group, const std::vector<Leg>& legs, int l0, int l
   std::vector<int> pos(k, 0);
   while (true) {
     const int f = fused_label(group, legs, l0, pos);
-    const int x = !columns ? f : group == SYM_Z2F ? (total ^ f) : total - f;
+    const int x = !columns || group == SYM_SU2 ? f : group == SYM_Z2F ? (total ^ f) : total - f;
     int64_t e = 1;
     for (int i = 0; i < k; ++i) e *= legs[l0 + i].degens[pos[i]];
     int64_t& acc = extent[x];
@@ -617,8 +622,8 @@ struct SvdPlan {
 };
 
 std::unique_ptr<SvdPlan> plan_svd(const Tensor& T, int nrow) {
-  if (T.group == SYM_SU2)
-    fail(SYM_ERR_UNSUPPORTED, "blockwise SVD is built for U(1) and fermion-parity tensors");
+  if (T.group == SYM_SU2 && T.rank != 2)
+    fail(SYM_ERR_UNSUPPORTED, "blockwise SVD of SU(2) tensors is built for rank 2 (the block-diagonal form)");
   if (T.rank < 2 || nrow < 1 || nrow >= T.rank) fail(SYM_ERR_ARG, "SVD needs rank >= 2 and 1 <= nrow < rank");
   auto P = std::make_unique<SvdPlan>();
   P->T = T;
@@ -641,6 +646,7 @@ std::unique_ptr<SvdPlan> plan_svd(const Tensor& T, int nrow) {
     b.R = (int)std::max(m, n);
     b.C = (int)std::min(m, n);
     b.slot = (int)P->blocks.size();
+    b.vscale = T.group == SYM_SU2 ? std::sqrt((double)x + 1.0) : 1.0;
     b.w = P->work_elems;
     b.s = P->nsv;
     // W, V, norms, sorted S, A, the Newton-Schulz factor (doubles), W and V in FP32
@@ -788,8 +794,9 @@ int sym_svd_bond(sym_svd plan, const int* keep, sym_tensor* U, sym_tensor* V) {
     std::vector<sym::Leg> lu(T.legs.begin(), T.legs.begin() + P.nrow), lv{bv};
     lu.push_back(bu);
     lv.insert(lv.end(), T.legs.begin() + P.nrow, T.legs.end());
-    sym::Tensor tu = sym::make_tensor(T.group, lu, 0, sym::Tree{});
-    sym::Tensor tv = sym::make_tensor(T.group, lv, T.total, sym::Tree{});
+    const sym::Tree tr = T.group == SYM_SU2 ? sym::Tree::comb(2) : sym::Tree{};
+    sym::Tensor tu = sym::make_tensor(T.group, lu, 0, tr);
+    sym::Tensor tv = sym::make_tensor(T.group, lv, T.total, tr);
     std::unordered_map<int, int> slot_of;
     for (size_t i = 0; i < P.xs.size(); ++i) slot_of[P.xs[i]] = (int)i;
     std::vector<std::vector<sym::SvdPiece>> pu(P.blocks.size()), pv(P.blocks.size());
@@ -874,10 +881,11 @@ int sym_svd_truncation(sym_svd plan, const double* S, int64_t chi, double cutoff
     for (size_t b = 0; b < P.blocks.size(); ++b) keep[b] = 0;
     int64_t n = 0;
     for (const Val& x : vals) {
-      if (chi >= 0 && n >= chi) break;
+      const int w = P.T.group == SYM_SU2 ? P.xs[x.b] + 1 : 1;  // dense values one value stands for
+      if (chi >= 0 && n + w > chi) break;
       if (cutoff > 0.0 && x.v <= cutoff * vmax) break;
       ++keep[x.b];
-      ++n;
+      n += w;
     }
     return SYM_OK;
   });

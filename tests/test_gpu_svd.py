@@ -15,6 +15,7 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
+from oracle import su2 as osu2  # noqa: E402
 from oracle import svd as osvd  # noqa: E402
 from oracle import u1 as ou1  # noqa: E402
 from oracle import z2f as oz2f  # noqa: E402
@@ -29,7 +30,11 @@ def _P():
 
 def _mods(group):
     P = _P()
-    return {"u1": (P.U1, ou1), "z2f": (P.Z2F, oz2f)}[group]
+    return {"u1": (P.U1, ou1), "z2f": (P.Z2F, oz2f), "su2": (P.SU2, osu2)}[group]
+
+
+def _otot(group, total):
+    return osu2.left_comb(2) if group == "su2" else total
 
 
 def _tensor(group, legs, total, values):
@@ -37,14 +42,14 @@ def _tensor(group, legs, total, values):
     g, m = _mods(group)
     S = P.Structure(g, legs, total=total)
     T = P.SymTensor(S, torch.as_tensor(values, dtype=torch.float64).cuda())
-    return S, T, ([m.Leg(*l) for l in legs], total, np.asarray(values, dtype=np.float64))
+    return S, T, ([m.Leg(*l) for l in legs], _otot(group, total), np.asarray(values, dtype=np.float64))
 
 
 def _dense_bond(group, X, first_is_bond):
     """Dense matrix of a factor: (rows, bond) for U, (bond, cols) for V."""
     _, m = _mods(group)
     legs = [m.Leg(*l) for l in X.structure.legs]
-    d = m.embed(legs, X.structure.total, X.data.cpu().numpy())
+    d = m.embed(legs, _otot(group, X.structure.total), X.data.cpu().numpy())
     return d.reshape(d.shape[0], -1) if first_is_bond else d.reshape(-1, d.shape[-1])
 
 
@@ -61,32 +66,36 @@ def _check(group, legs, total, nrow, values, chi=None, cutoff=0.0):
     sweeps32, _ = plan.stats(fp32=True)
     assert max(sweeps) < 64 and max(sweeps32) <= 40
     keep = plan.truncation(Sg, chi, cutoff)
-    ko = osvd.truncation({x: fac[x][1] for x in fac}, chi, cutoff)
+    ko = osvd.truncation({x: fac[x][1] for x in fac}, chi, cutoff, group=group)
     assert keep == [ko[x] for x in plan.labels]
     M = osvd.matrix(group, To, nrow)
     Uo, kept, Vo = osvd.factors(group, To, nrow, ko, absorb=1, fac=fac)
     _, m = _mods(group)
-    ref = m.embed(Uo[0], 0, Uo[2]).reshape(-1, sum(keep)) @ m.embed(Vo[0], Vo[1], Vo[2]).reshape(sum(keep), -1)
+    Ud, Vd = m.embed(*Uo), m.embed(*Vo)
+    ref = Ud.reshape(-1, Ud.shape[-1]) @ Vd.reshape(Vd.shape[0], -1)
     for absorb in (0, 1, 2):
         U, Sk, V = P.svd(T, nrow, chi=chi, cutoff=cutoff, absorb=absorb)
         Sk = Sk.cpu().numpy()
         assert np.max(np.abs(Sk - np.concatenate([kept[x] for x in sorted(kept)]))) <= TOL * Smax
         Um, Vm = _dense_bond(group, U, False), _dense_bond(group, V, True)
-        prod = Um @ (np.diag(Sk) if absorb == 0 else np.eye(len(Sk))) @ Vm
+        Sd = osvd.dense_values(group, {x: Sk[o:o + k] for x, k, o in zip(
+            [x for x, k in zip(plan.labels, keep) if k], [k for k in keep if k],
+            np.cumsum([0] + [k for k in keep if k])[:-1])})
+        prod = Um @ (np.diag(Sd) if absorb == 0 else np.eye(len(Sd))) @ Vm
         assert np.max(np.abs(prod - ref)) <= TOL * Smax
         # orthonormal vectors (a vector of a numerically zero singular value
         # is only defined up to the rest, and is written as zeros when exactly 0)
-        live = np.where(Sk > 1e-10 * Smax)[0]
+        live = np.where(Sd > 1e-10 * Smax)[0]
         if absorb != 1:
             Ul = Um[:, live]
-            assert np.max(np.abs(Ul.T @ Ul - np.eye(len(live)))) <= TOL
+            assert np.max(np.abs(Ul.T @ Ul - np.eye(len(live)))) <= 4 * TOL
         if absorb != 2:
             Vl = Vm[live, :]
-            assert np.max(np.abs(Vl @ Vl.T - np.eye(len(live)))) <= TOL
+            assert np.max(np.abs(Vl @ Vl.T - np.eye(len(live)))) <= 4 * TOL
         # U and V carry nothing outside their blocks (their layouts are the library's own)
         for X in (U, V):
             legsX = [m.Leg(*l) for l in X.structure.legs]
-            assert X.structure.numel == m.layout(legsX, X.structure.total)[2]
+            assert X.structure.numel == m.layout(legsX, _otot(group, X.structure.total))[2]
     if chi is None and not cutoff:
         assert np.max(np.abs(ref - M)) <= TOL * Smax
     P.device_status()
@@ -95,7 +104,7 @@ def _check(group, legs, total, nrow, values, chi=None, cutoff=0.0):
 
 def _rand(group, legs, total, seed):
     _, m = _mods(group)
-    n = m.layout([m.Leg(*l) for l in legs], total)[2]
+    n = m.layout([m.Leg(*l) for l in legs], _otot(group, total))[2]
     return np.random.default_rng(seed).standard_normal(n)
 
 
@@ -148,3 +157,13 @@ def test_two_site_theta_full_size():
     S = P.Structure(P.U1, legs)
     vals = synthetic.normal(w["seed"], S.numel)
     _check("u1", legs, total, w["nrow"], vals, chi=w["chi"])
+
+
+@pytest.mark.parametrize("dirs", [(1, -1), (1, 1), (-1, -1), (-1, 1)])
+def test_su2_rank2(dirs):
+    # the block-diagonal form of Eq. svd0: integer and half-integer spins,
+    # blocks 1 x 1 to 40 x 33 (tall and wide), every direction pattern
+    legs = [([0, 1, 2, 3, 4], [3, 40, 7, 1, 12], dirs[0]), ([0, 1, 2, 3, 4], [5, 33, 7, 2, 1], dirs[1])]
+    vals = _rand("su2", legs, 0, 41)
+    _check("su2", legs, 0, 1, vals)
+    _check("su2", legs, 0, 1, vals, chi=30)

@@ -71,7 +71,25 @@ def rejects(code, f):
     raise SystemExit("accepted")
 
 from paper_1203_2222_gb300 import _lib as L
-rejects(L.SYM_ERR_UNSUPPORTED, lambda: P.SVDPlan(P.Structure(P.SU2, [([0, 2], [1, 1], 1)] * 2), 1))
+rejects(L.SYM_ERR_UNSUPPORTED, lambda: P.SVDPlan(P.Structure(P.SU2, [([0, 2], [1, 1], 1)] * 3), 1))
+
+# SU(2) rank 2: blocks per spin, truncation by dense count (2j+1 per value)
+from oracle import su2
+legs2 = [([0, 1, 2, 3], [3, 2, 4, 2], 1), ([0, 1, 2, 3], [2, 3, 3, 1], -1)]
+S2 = P.Structure(P.SU2, legs2)
+plan2 = P.SVDPlan(S2, 1)
+L2 = [su2.Leg(*l) for l in legs2]
+T2 = (L2, su2.left_comb(2), np.random.default_rng(3).standard_normal(su2.layout(L2, su2.left_comb(2))[2]))
+fac2, bd2 = osvd.svd("su2", T2, 1)
+assert plan2.labels == sorted(bd2) and plan2.m == [3, 2, 4, 2] and plan2.n == [2, 3, 3, 1]
+Sx2 = {x: fac2[x][1] for x in plan2.labels}
+flat2 = np.concatenate([Sx2[x] for x in plan2.labels])
+for chi in (None, 1, 2, 5, 9, 13, 20):
+    keep = plan2.truncation(flat2, chi)
+    ko = osvd.truncation(Sx2, chi, group="su2")
+    assert keep == [ko[x] for x in plan2.labels], (chi, keep, ko)
+Us2, Vs2 = plan2.bond(plan2.truncation(flat2, 9))
+assert [l[2] for l in Us2.legs] == [1, -1] and [l[2] for l in Vs2.legs] == [1, -1]
 rejects(L.SYM_ERR_ARG, lambda: P.SVDPlan(S, 0))
 rejects(L.SYM_ERR_ARG, lambda: P.SVDPlan(S, 2))
 rejects(L.SYM_ERR_ARG, lambda: plan.bond([0, 0, 0]))
