@@ -41,7 +41,7 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--workload", choices=["u1_mps_heff", "su2_recouple", "u1_two_site_batch", "u1_mera_grad",
-                                           "z2f_mps_heff", "u1_two_site_svd"],
+                                           "z2f_mps_heff", "u1_two_site_svd", "su2_micro"],
                     default="u1_mps_heff",
                     help="u1_mps_heff (default, the metric's configuration), the large-sector su2_recouple, "
                          "the 512-problem u1_two_site_batch or the MERA gradient u1_mera_grad")
@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--tune-space", default=None,
                     help="comma-separated planning parameters the search varies (default: all of autotune.SPACE)")
     args = ap.parse_args()
-    wl = SVDWorkload if args.workload == "u1_two_site_svd" else WORKLOADS[args.workload]
+    wl = {"u1_two_site_svd": SVDWorkload, "su2_micro": MicroWorkload}.get(args.workload) or WORKLOADS[args.workload]
     args.steps = wl.default_steps if args.steps is None else args.steps
     args.warmup = wl.default_warmup if args.warmup is None else args.warmup
     args.fp64_steps = wl.default_fp64_steps if args.fp64_steps is None else args.fp64_steps
@@ -1004,6 +1004,143 @@ def run_reference_svd(args):
     }
 
 
+# ------------------------------------------- SU(2) vs regular micro-benchmarks ---
+
+MICRO_METRIC = "SU(2)-invariant vs regular time ratio (regular / SU(2)), matrix multiply at the largest d"
+
+
+class MicroWorkload:
+    describe = ("su2_micro: the thesis's comparisons of SU(2)-invariant and regular tensors (Ch. 5, Figs. "
+                "permutereshapecompare and multsvdcompare): permute two indices and fuse two indices of a rank-4 "
+                "tensor whose legs have spins 0, 1, 2 with degeneracy d each (dense size 9d per leg), multiply and "
+                "SVD 9d x 9d matrices (three d x d blocks); 'regular' = the same dense tensor as a one-charge "
+                "tensor through the same kernels; plus the recoupling coefficients a permutation evaluates (Fig. sn1)")
+    default_steps = 5
+    default_warmup = 2
+    default_fp64_steps = 0
+
+
+def _time_ms(fn, steps, warmup, flush, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return sorted(ts)[len(ts) // 2]
+
+
+def run_su2_micro(args, rank, world):
+    """Every comparison of SU(2)-invariant and regular tensors the thesis plots,
+    on the library's kernels; one JSON line with every series."""
+    import torch
+    import paper_1203_2222_gb300 as P
+    from paper_1203_2222_gb300 import _lib as L
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    K, W = args.steps, args.warmup
+    spins = [0, 2, 4]  # 2j: j = 0, 1, 2
+
+    def su2_leg(d, dr):
+        return (spins, [d] * 3, dr)
+
+    def reg_leg(d, dr):
+        return ([0], [9 * d], dr)
+
+    def transform_ms(S, make_plan, dtype=torch.float64):
+        plan = make_plan(S)
+        x = torch.randn(S.numel, dtype=dtype, device=dev)
+        y = torch.empty(plan.out.numel, dtype=dtype, device=dev)
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+        fn = lambda: L.check(L.lib.sym_plan_execute(plan._h, ptr(x), ptr(y), ctypes.c_void_p(stream.cuda_stream)))
+        return _time_ms(fn, K, W, flush, stream), S.numel
+
+    import ctypes
+    series = {"permute": [], "fuse": [], "matmul": [], "svd": []}
+    for d in (2, 4, 8, 12, 16, 20):
+        row = {"d": d}
+        for kind, leg, grp in (("su2", su2_leg, P.SU2), ("regular", reg_leg, P.U1)):
+            S = P.Structure(grp, [leg(d, 1)] * 4)
+            ms, n = transform_ms(S, lambda S: P.permute_plan(S, [0, 2, 1, 3], None, P.FP64))
+            row[kind + "_ms"], row[kind + "_coefficients"] = round(ms, 4), n
+        row["ratio"] = round(row["regular_ms"] / row["su2_ms"], 3)
+        series["permute"].append(row)
+        row = {"d": d}
+        for kind, leg, grp in (("su2", su2_leg, P.SU2), ("regular", reg_leg, P.U1)):
+            S = P.Structure(grp, [leg(d, 1)] * 4)
+            ms, n = transform_ms(S, lambda S: P.fuse_plan(S, 0, P.FP64))
+            row[kind + "_ms"] = round(ms, 4)
+        row["ratio"] = round(row["regular_ms"] / row["su2_ms"], 3)
+        series["fuse"].append(row)
+        torch.cuda.empty_cache()
+
+    # (d <= 1024: a regular 9d x 9d product with 9d > 16384 would exceed the
+    # planner's longest tensor-core reduction and run on the CUDA cores)
+    for d in (64, 128, 256, 512, 1024):
+        row = {"d": d}
+        for kind, leg, grp in (("su2", su2_leg, P.SU2), ("regular", reg_leg, P.U1)):
+            SA = P.Structure(grp, [leg(d, 1), leg(d, -1)])
+            SB = P.Structure(grp, [leg(d, 1), leg(d, -1)])
+            A = P.SymTensor(SA, torch.randn(SA.numel, device=dev))
+            B = P.SymTensor(SB, torch.randn(SB.numel, device=dev))
+            with torch.no_grad():
+                row[kind + "_ms"] = round(_time_ms(lambda: P.contract(A, B, [1], [0]), K, W, flush, stream), 4)
+        row["ratio"] = round(row["regular_ms"] / row["su2_ms"], 3)
+        row["dtype"] = "split-BF16 x3 (fp32 blocks)"
+        series["matmul"].append(row)
+        torch.cuda.empty_cache()
+
+    for d in (8, 16, 32, 64):
+        row = {"d": d}
+        for kind, leg, grp in (("su2", su2_leg, P.SU2), ("regular", reg_leg, P.U1)):
+            S = P.Structure(grp, [leg(d, 1), leg(d, -1)])
+            T = P.SymTensor(S, torch.randn(S.numel, dtype=torch.float64, device=dev))
+            row[kind + "_ms"] = round(_time_ms(lambda: P.svd(T, 1), K, W, flush, stream), 4)
+        Md = torch.randn(9 * d, 9 * d, dtype=torch.float64, device=dev)
+        row["regular_library_ms"] = round(_time_ms(lambda: torch.linalg.svd(Md), K, W, flush, stream), 4)
+        row["ratio"] = round(row["regular_ms"] / row["su2_ms"], 3)
+        row["dtype"] = "f64"
+        series["svd"].append(row)
+    P.device_status()
+
+    # Fig. sn1: recoupling coefficients (spin networks) a permutation of two
+    # neighbouring legs evaluates, against the rank and the spins per leg
+    sn = []
+    for k in (3, 4, 5, 6):
+        for nsp in (1, 2, 3, 4):
+            sp = [2 * i for i in range(nsp)]
+            S = P.Structure(P.SU2, [(sp, [1] * nsp, 1)] * k)
+            t0 = time.perf_counter()
+            plan = P.permute_plan(S, [0, 2, 1] + list(range(3, k)), None, P.FP64)
+            dt = time.perf_counter() - t0
+            n = 0
+            import itertools
+            for tup in itertools.product(sp, repeat=k):
+                G, _, _ = P.su2_gamma(list(tup), None, [0, 2, 1] + list(range(3, k)), None)
+                n += int(np.count_nonzero(np.abs(G) > 1e-12))  # exact zeros may round to ~1e-17
+            sn.append({"rank": k, "spins_per_leg": nsp, "coefficients": n, "plan_ms": round(dt * 1e3, 3)})
+    last = series["matmul"][-1]
+    out = {
+        "metric": MICRO_METRIC, "value": last["ratio"], "unit": "x", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": last["su2_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 (permute, fuse, svd), bf16x3-f32acc (matmul)", "data": "synthetic",
+        "config": {"workload": MicroWorkload.describe, "l2": "flushed before every timed call (256 MiB write)",
+                   "timing": f"median of {K} calls after {W} warm-up calls, CUDA events"},
+        "series": series, "spin_networks": sn, "gpu_launches": None,
+    }
+    return out
+
+
 # ------------------------------------------------------------ oracle (CPU) ---
 
 class OracleMPS:
@@ -1377,7 +1514,10 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        if args.workload == "u1_two_site_svd":
+        if args.workload == "su2_micro":
+            out = {"impl": "reference", "unavailable": "su2_micro compares SU(2)-invariant and regular tensors on the "
+                                                      "library's own kernels; the thesis's MATLAB timings have no values"}
+        elif args.workload == "u1_two_site_svd":
             out = run_reference_svd(args)
         elif args.workload == "su2_recouple":
             out = run_reference_su2(args)
@@ -1395,7 +1535,9 @@ def main():
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
-    if args.workload == "u1_two_site_svd":
+    if args.workload == "su2_micro":
+        out = run_su2_micro(args, rank, world)
+    elif args.workload == "u1_two_site_svd":
         out = run_svd(args, rank, world)
         if rank == 0 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_svd(args.cpu_sample_steps)
