@@ -440,13 +440,13 @@ WORKLOADS = {"u1_mps_heff": MPSWorkload, "su2_recouple": SU2Workload, "u1_two_si
 # the captured launches, applied to the full launch's algorithmic bytes.
 TRAFFIC = {
     "u1_mps_heff": {  # profiles/traffic_u1_mps_heff.md
-        "gemm_tc": {"bytes_per_launch": 13773824, "sha": "1a9aa9bdfa7cce0f"},
+        "gemm_tc": {"bytes_per_launch": 13768512, "sha": "17524e1d9ff325bc"},
         "box_flat": {"bytes_per_launch": 5857248, "sha": "b7242e8ca118cb38"},
         "box": {"bytes_per_launch": 13079040, "sha": "b7242e8ca118cb38"},
         "direct": {"bytes_per_launch": 11909291, "sha": "32a083d9660812bd"},
     },
     "su2_recouple": {  # profiles/gemm_tc_su2_recouple.md (full size, forward and backward launches)
-        "gemm_tc": {"bytes_per_launch": 61084875776, "sha": "1a9aa9bdfa7cce0f"},
+        "gemm_tc": {"bytes_per_launch": 60924806400, "sha": "17524e1d9ff325bc"},
     },
     "u1_two_site_batch": {  # profiles/direct_u1_two_site_batch.md (128 of the 512 problems)
         "direct": {"ratio": 0.97, "sha": "32a083d9660812bd"},
