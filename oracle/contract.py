@@ -18,16 +18,28 @@ block layout.  No symmetry is used in the arithmetic.
 * ``fuse``: Ch. 5, Eq. fuse with the fusing tensor of Eq. basischange1 (U(1):
   the 0/1 map alone); incoming legs lose their cups first and the fused leg
   gets one (Ch. 6, reshape of indices carrying cups).
+* SU(2) x U(1) ("su2u1", oracle/su2u1.py) runs the SU(2) branches with
+  composite legs; a tensor's second member is (tree, total charge).
 """
 import numpy as np
 
 from . import su2 as su2m
+from . import su2u1 as su2u1m
 from . import u1 as u1m
 from . import z2f as z2fm
 
 
 def _mod(group):
-    return {"u1": u1m, "su2": su2m}[group]
+    return {"u1": u1m, "su2": su2m, "su2u1": su2u1m}[group]
+
+
+def _with_total(group, tree, total):
+    """The second member of a tensor: U(1) total, SU(2) tree, SU(2) x U(1) (tree, Q)."""
+    return (tree, total) if group == "su2u1" else tree
+
+
+def _charge(group, t):
+    return t[1] if group == "su2u1" else 0
 
 
 def comb_pair_tree(na, nb):
@@ -79,7 +91,8 @@ def contract(group, A, B, pairsA, pairsB, tree_c=None):
         tC = tA + tB
     else:
         na = len(legsA) - len(pairsA)
-        tC = tree_c if tree_c is not None else comb_pair_tree(na, len(legsC) - na)
+        tC = _with_total(group, tree_c if tree_c is not None else comb_pair_tree(na, len(legsC) - na),
+                         _charge(group, tA) + _charge(group, tB))
     c, resid = m.extract(legsC, tC, Cd)
     return legsC, tC, c, resid
 
@@ -97,7 +110,8 @@ def contract_grad(group, A, B, pairsA, pairsB, dC, tree_c=None):
     if group == "u1":
         tC = tA + tB
     else:
-        tC = tree_c if tree_c is not None else comb_pair_tree(na, nb)
+        tC = _with_total(group, tree_c if tree_c is not None else comb_pair_tree(na, nb),
+                         _charge(group, tA) + _charge(group, tB))
     Ad, Bd, dCd = m.embed(legsA, tA, a), m.embed(legsB, tB, b), m.embed(legsC, tC, dC)
     freeA, freeB = _free(len(legsA), pairsA), _free(len(legsB), pairsB)
     # dA[freeA, c] = sum_{freeB} dC[freeA, freeB] B[c, freeB]
@@ -135,7 +149,7 @@ def permute(group, T, perm, tree_out=None):
     if group == "u1":
         t2 = t
     else:
-        t2 = tree_out if tree_out is not None else su2m.left_comb(len(legs2))
+        t2 = _with_total(group, tree_out if tree_out is not None else su2m.left_comb(len(legs2)), _charge(group, t))
     out, resid = m.extract(legs2, t2, d)
     return legs2, t2, out, resid
 
@@ -158,16 +172,16 @@ def fuse(group, T, first, tree_out=None):
         return legs2, t, res, resid
     if la.dir == -1:
         # detach the cups (cap inverts cup), fuse as outgoing, re-attach
-        d = np.moveaxis(np.tensordot(su2m.leg_cap(la), d, axes=([1], [first])), 0, first)
-        d = np.moveaxis(np.tensordot(su2m.leg_cap(lb), d, axes=([1], [first + 1])), 0, first + 1)
-    ld, U = su2m.fusing_tensor(la.dual() if la.dir == -1 else la,
-                               lb.dual() if lb.dir == -1 else lb)
+        d = np.moveaxis(np.tensordot(m.leg_cap(la), d, axes=([1], [first])), 0, first)
+        d = np.moveaxis(np.tensordot(m.leg_cap(lb), d, axes=([1], [first + 1])), 0, first + 1)
+    ld, U = m.fusing_tensor(la.dual() if la.dir == -1 else la,
+                            lb.dual() if lb.dir == -1 else lb)
     out_d = np.tensordot(d, U, axes=([first, first + 1], [0, 1]))
     out_d = np.moveaxis(out_d, -1, first)
     if la.dir == -1:
         ld = ld.dual()
-        out_d = np.moveaxis(np.tensordot(su2m.leg_cup(ld), out_d, axes=([1], [first])), 0, first)
+        out_d = np.moveaxis(np.tensordot(m.leg_cup(ld), out_d, axes=([1], [first])), 0, first)
     legs2 = legs[:first] + [ld] + legs[first + 2:]
-    t2 = tree_out if tree_out is not None else su2m.left_comb(len(legs2))
-    res, resid = su2m.extract(legs2, t2, out_d)
+    t2 = _with_total(group, tree_out if tree_out is not None else su2m.left_comb(len(legs2)), _charge(group, t))
+    res, resid = m.extract(legs2, t2, out_d)
     return legs2, t2, res, resid
