@@ -68,6 +68,7 @@ extern "C" {
 #define SYM_U1 1
 #define SYM_SU2 2
 #define SYM_Z2F 3 /* fermion parity: labels 0/1, fusion mod 2, swap of two odd charges -1 */
+#define SYM_SU2U1 4 /* SU(2) x U(1): label = 64 q + 2j (0 <= 2j < 64), see sym_tensor_create */
 
 /* Precision of a plan (the storage dtype follows from it). */
 #define SYM_PREC_FP64 1   /* double blocks, FP64 gathers and FP64 GEMM (CUDA cores) */
@@ -95,10 +96,17 @@ const char* sym_version(void);
  *   conclusion: labels p = 0, 1 fuse by addition mod 2, the recoupling
  *   coefficients are 1, and exchanging two legs of odd parity multiplies a
  *   block by -1; total = 0 or 1; every permutation, fuse and contraction
- *   applies these swap signs, and nothing else differs from U(1)).  0 <= rank <= 6 (rank 0 is a scalar).
+ *   applies these swap signs, and nothing else differs from U(1)), or
+ *   SYM_SU2U1 (the composite symmetry of the thesis's conclusion, the two
+ *   groups acting component by component: a label is the pair (q, 2j)
+ *   stored as 64 q + 2j with 0 <= 2j < 64, so that increasing labels sort by
+ *   charge, then spin; a sector is a tree decomposition as for SU(2) on the
+ *   spins whose charges obey the U(1) rule sum_out q - sum_in q = total; the
+ *   recoupling coefficients and cups are the spins' alone; a fused label
+ *   adds the charges and couples the spins).  0 <= rank <= 6 (rank 0 is a scalar).
+ *   total: U(1) total charge Q (also for SYM_SU2U1); ignored for SU(2) (total spin is 0).
+ *   tree: SU(2) and SU(2) x U(1) fusion tree as 2*(rank-1) ints, NULL = left comb; ignored otherwise.
  *   legs: rank leg descriptors (copied).
- *   total: U(1) total charge Q; ignored for SU(2) (total spin is 0).
- *   tree: SU(2) fusion tree as 2*(rank-1) ints, NULL = left comb; ignored for U(1).
  * Errors: SYM_ERR_ARG for malformed legs or trees.                          */
 int sym_tensor_create(int group, int rank, const sym_leg* legs, int total,
                       const int* tree, sym_tensor* out);

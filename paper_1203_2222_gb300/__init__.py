@@ -10,4 +10,4 @@ from .symtensor import (BF16X3, FP64, KERNEL_SYMBOLS, KERNELS, PHASES, SU2, U1, 
                         Plan, Structure, SymError, SymTensor, cached_plans, contract, contract_batch,
                         contract_batch_plan, contract_plan, device_status, fuse, fuse_plan, permute,
                         permute_plan, split, split_plan, su2_F, su2_gamma, svd, svd_plan, SVDPlan, tune_epoch,
-                        tune_get, tune_set, Z2F)
+                        tune_get, tune_set, Z2F, SU2U1, su2u1_label)

@@ -22,6 +22,7 @@ SYM_ERR_NUMERIC = -8
 SYM_U1 = 1
 SYM_SU2 = 2
 SYM_Z2F = 3
+SYM_SU2U1 = 4
 SYM_PREC_FP64 = 1
 SYM_PREC_BF16X3 = 2
 

@@ -90,7 +90,7 @@ sym::Tensor sym::contraction_result(const Tensor& a, const Tensor& b, const std:
     if (!sb[l]) legs.push_back(b.legs[l]);
   if (legs.size() > 6) fail(SYM_ERR_ARG, "result rank would exceed 6");
   Tree tr;
-  if (a.group == SYM_SU2) tr = tree_c ? read_tree((int)legs.size(), tree_c) : Tree::comb_pair(na, (int)legs.size() - na);
+  if (sym::su2_like(a.group)) tr = tree_c ? read_tree((int)legs.size(), tree_c) : Tree::comb_pair(na, (int)legs.size() - na);
   return make_tensor(a.group, legs, a.group == SYM_Z2F ? (a.total ^ b.total) : a.total + b.total, tr);
 }
 
@@ -104,7 +104,7 @@ int sym_tensor_create(int group, int rank, const sym_leg* legs, int total, const
   return guard([&] {
     need(out != nullptr, "out is NULL");
     auto L = read_legs(rank, legs);
-    sym::Tree tr = group == SYM_SU2 ? read_tree(rank, tree) : sym::Tree{};
+    sym::Tree tr = sym::su2_like(group) ? read_tree(rank, tree) : sym::Tree{};
     *out = wrap(sym::make_tensor(group, L, total, tr));
     return SYM_OK;
   });
@@ -141,7 +141,7 @@ int sym_tensor_leg(sym_tensor t, int leg, int* n, int* labels, int* degens, int*
 int sym_tensor_tree(sym_tensor t, int* nodes) {
   return guard([&] {
     need(t != nullptr && nodes != nullptr, "NULL argument");
-    need(t->t.group == SYM_SU2, "only SU(2) tensors have a tree");
+    need(sym::su2_like(t->t.group), "only SU(2) and SU(2) x U(1) tensors have a tree");
     for (size_t n = 0; n < t->t.tree.nodes.size(); ++n) {
       nodes[2 * n] = t->t.tree.nodes[n][0];
       nodes[2 * n + 1] = t->t.tree.nodes[n][1];
@@ -181,7 +181,7 @@ int sym_permute_plan(sym_tensor in, const int* perm, const int* tree_out, int pr
     }
     std::vector<sym::Leg> legs;
     for (int x : p) legs.push_back(T.legs[x]);
-    sym::Tree tr = T.group == SYM_SU2 ? read_tree(T.rank, tree_out) : sym::Tree{};
+    sym::Tree tr = sym::su2_like(T.group) ? read_tree(T.rank, tree_out) : sym::Tree{};
     sym::Tensor O = sym::make_tensor(T.group, legs, T.total, tr);
     auto P = sym::plan_transform(T, O, p, precision, 0, 0);
     *out = wrap(std::move(O));
@@ -220,7 +220,7 @@ int sym_split_plan(sym_tensor in, int leg, const sym_leg* parts, int precision, 
     const sym::Leg& f = T.legs[leg];
     if (!(d.same_content(f) && d.dir == f.dir))
       sym::fail(SYM_ERR_INCOMPATIBLE_LEGS, "split: the two parts do not fuse to the leg");
-    if (T.group == SYM_SU2 && !(T.tree == sym::Tree::comb(T.rank)))
+    if (sym::su2_like(T.group) && !(T.tree == sym::Tree::comb(T.rank)))
       sym::fail(SYM_ERR_UNSUPPORTED, "split: SU(2) input must be in the comb tree (permute it first)");
     std::vector<sym::Leg> legs(T.legs.begin(), T.legs.begin() + leg);
     legs.push_back(ab[0]);

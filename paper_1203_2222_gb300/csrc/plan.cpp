@@ -267,7 +267,7 @@ double z2f_swap_sign(const Tensor& src, const std::vector<int>& perm, const std:
 std::vector<TermList> make_xform(const Tensor& src, const std::vector<int>& perm, const Tensor& dst) {
   std::vector<TermList> out(dst.nsec());
   const int k = src.rank;
-  if (src.group != SYM_SU2) {  // U(1), fermion parity: one source block, coefficient 1 or the swap sign
+  if (!su2_like(src.group)) {  // U(1), fermion parity: one source block, coefficient 1 or the swap sign
     std::vector<int> key(k);
     for (int64_t s = 0; s < dst.nsec(); ++s) {
       for (int n = 0; n < k; ++n) key[perm[n]] = dst.p(s, n);
@@ -284,8 +284,8 @@ std::vector<TermList> make_xform(const Tensor& src, const std::vector<int>& perm
       ++e;
     std::vector<int> srcpos(k), spins(k);
     for (int n = 0; n < k; ++n) srcpos[perm[n]] = dst.p(s, n);
-    for (int l = 0; l < k; ++l) spins[l] = src.legs[l].labels[srcpos[l]];
-    Gamma g = tree_transform(spins, src.tree, perm, dst.tree);
+    for (int l = 0; l < k; ++l) spins[l] = spin_of(src.group, src.legs[l].labels[srcpos[l]]);
+    Gamma g = tree_transform(spins, src.tree, perm, dst.tree);  // the spins' recoupling; charges move along
     std::vector<int64_t> so(g.out_labels.size()), si(g.in_labels.size());
     for (size_t o = 0; o < so.size(); ++o) {
       std::vector<int> key(dst.pos.begin() + s * k, dst.pos.begin() + (s + 1) * k);
@@ -322,13 +322,13 @@ std::vector<TermList> transpose_xform(const std::vector<TermList>& x, int64_t ns
 // subtree's nodes below the subtree top (the top is the sector key x).
 std::vector<int> row_key(const Tensor& T, int64_t s, int nr) {
   std::vector<int> k(T.pos.begin() + s * T.rank, T.pos.begin() + s * T.rank + nr);
-  if (T.group == SYM_SU2 && nr >= 3) k.insert(k.end(), T.inner_of(s), T.inner_of(s) + (nr - 2));
+  if (su2_like(T.group) && nr >= 3) k.insert(k.end(), T.inner_of(s), T.inner_of(s) + (nr - 2));
   return k;
 }
 std::vector<int> col_key(const Tensor& T, int64_t s, int nr) {
   const int nc = T.rank - nr;
   std::vector<int> k(T.pos.begin() + s * T.rank + nr, T.pos.begin() + (s + 1) * T.rank);
-  if (T.group == SYM_SU2 && nc >= 3) {
+  if (su2_like(T.group) && nc >= 3) {
     const int c0 = nr >= 1 ? nr - 1 : 0;
     k.insert(k.end(), T.inner_of(s) + c0, T.inner_of(s) + c0 + (nc - 2));
   }
@@ -406,7 +406,7 @@ void group_weights(const Tensor& Tm, int64_t s, int nr, int* rw, int* cw) {
 int su2_top(const Tensor& T, int64_t s, int nr) {
   int nc = T.rank - nr;
   if (nr == 0 || nc == 0) return 0;
-  if (nr == 1) return T.label(s, 0);
+  if (nr == 1) return spin_of(T.group, T.label(s, 0));
   return T.inner_of(s)[nr - 2];
 }
 
@@ -670,6 +670,14 @@ void Plan::upload(bool device) {
 
 // fused charge of two abelian labels (U(1): sum; fermion parity: sum mod 2)
 int abelian_fuse(int group, int a, int b) { return group == SYM_Z2F ? (a ^ b) : a + b; }
+
+// Label of the leg fused from labels a and b: U(1), fermion parity as above;
+// SU(2): the node spin s of the pair; SU(2) x U(1): the charges' sum with s.
+int fused_pair_label(int group, int a, int b, int s) {
+  if (group == SYM_SU2) return s;
+  if (group == SYM_SU2U1) return su2u1_label(charge_of(group, a) + charge_of(group, b), s);
+  return abelian_fuse(group, a, b);
+}
 bool z2f_group(int group) { return group == SYM_Z2F; }
 
 Leg fused_leg(const Leg& a, const Leg& b, int group) {
@@ -682,6 +690,10 @@ Leg fused_leg(const Leg& a, const Leg& b, int group) {
         deg[a.labels[i] + b.labels[j]] += d;
       } else if (group == SYM_Z2F) {
         deg[a.labels[i] ^ b.labels[j]] += d;
+      } else if (group == SYM_SU2U1) {  // charges add, spins couple
+        const int ja = spin_of(group, a.labels[i]), jb = spin_of(group, b.labels[j]);
+        const int q = charge_of(group, a.labels[i]) + charge_of(group, b.labels[j]);
+        for (int c = std::abs(ja - jb); c <= ja + jb; c += 2) deg[su2u1_label(q, c)] += d;
       } else {
         for (int c = std::abs(a.labels[i] - b.labels[j]); c <= a.labels[i] + b.labels[j]; c += 2) deg[c] += d;
       }
@@ -703,7 +715,10 @@ static int64_t pair_offset(const Leg& a, const Leg& b, int group, int c, int ia,
     for (size_t j = 0; j < b.labels.size(); ++j) {
       bool ok = group == SYM_U1    ? a.labels[i] + b.labels[j] == c
                 : group == SYM_Z2F ? (a.labels[i] ^ b.labels[j]) == c
-                                   : triangle(a.labels[i], b.labels[j], c);
+                : group == SYM_SU2U1
+                    ? charge_of(group, a.labels[i]) + charge_of(group, b.labels[j]) == charge_of(group, c) &&
+                          triangle(spin_of(group, a.labels[i]), spin_of(group, b.labels[j]), spin_of(group, c))
+                    : triangle(a.labels[i], b.labels[j], c);
       if (!ok) continue;
       if ((int)i == ia && (int)j == ib) return off;
       off += (int64_t)a.degens[i] * b.degens[j];
@@ -767,32 +782,33 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
     const Leg& la = in.legs[f];
     const Leg& lb = in.legs[f + 1];
     const Leg& ld = out.legs[f];
-    Tensor mid = in.group == SYM_SU2 ? make_tensor(in.group, in.legs, 0, fuse_pair_tree(k, f)) : in;
+    const bool tree = su2_like(in.group);
+    Tensor mid = tree ? make_tensor(in.group, in.legs, in.total, fuse_pair_tree(k, f)) : in;
     std::vector<TermList> X;
     std::vector<int> idp(k);
     for (int i = 0; i < k; ++i) idp[i] = i;
-    if (in.group == SYM_SU2) X = make_xform(in, idp, mid);
+    if (tree) X = make_xform(in, idp, mid);
     for (int64_t sm = 0; sm < mid.nsec(); ++sm) {
-      int c = in.group != SYM_SU2 ? abelian_fuse(in.group, la.labels[mid.p(sm, f)], lb.labels[mid.p(sm, f + 1)])
-                                  : mid.inner_of(sm)[0];
+      int c = fused_pair_label(in.group, la.labels[mid.p(sm, f)], lb.labels[mid.p(sm, f + 1)],
+                               tree ? mid.inner_of(sm)[0] : 0);
       int iq = (int)(std::lower_bound(ld.labels.begin(), ld.labels.end(), c) - ld.labels.begin());
       std::vector<int> key;
       for (int l = 0; l < k; ++l) {
         if (l == f) key.push_back(iq);
         else if (l != f + 1) key.push_back(mid.p(sm, l));
       }
-      if (in.group == SYM_SU2) key.insert(key.end(), mid.inner_of(sm) + 1, mid.inner_of(sm) + mid.nin);
+      if (tree) key.insert(key.end(), mid.inner_of(sm) + 1, mid.inner_of(sm) + mid.nin);
       int64_t so = out.find(key);
       if (so < 0) fail(SYM_ERR_ARG, "internal: fused sector missing");
       int64_t row0 = pair_offset(la, lb, in.group, c, mid.p(sm, f), mid.p(sm, f + 1));
       block_strides(out, so, ost);
       std::vector<Term> terms;
-      if (in.group != SYM_SU2) {
+      if (!tree) {
         terms.push_back({in.offs[sm], 1, 1.0});
       } else {
         for (auto& pc : X[sm]) terms.push_back({in.offs[pc.first], 1, pc.second});
       }
-      block_strides(in, in.group != SYM_SU2 ? sm : (X[sm].empty() ? 0 : X[sm][0].first), ist);
+      block_strides(in, !tree ? sm : (X[sm].empty() ? 0 : X[sm][0].first), ist);
       Box b;
       int db_ = mid.dim(sm, f + 1);
       for (int l = 0; l < k; ++l) {
@@ -807,16 +823,17 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
     const int ko = out.rank;
     const Leg& la = out.legs[f];
     const Leg& lb = out.legs[f + 1];
-    Tensor mid = in.group == SYM_SU2 ? make_tensor(in.group, out.legs, 0, fuse_pair_tree(ko, f)) : out;
+    const bool tree = su2_like(in.group);
+    Tensor mid = tree ? make_tensor(in.group, out.legs, in.total, fuse_pair_tree(ko, f)) : out;
     std::vector<TermList> X;
     std::vector<int> idp(ko);
     for (int i = 0; i < ko; ++i) idp[i] = i;
-    if (in.group == SYM_SU2) X = make_xform(mid, idp, out);
+    if (tree) X = make_xform(mid, idp, out);
     // where each mid sector lives inside `in`
     std::vector<int64_t> m_in(mid.nsec()), m_row(mid.nsec());
     for (int64_t sm = 0; sm < mid.nsec(); ++sm) {
-      int c = in.group != SYM_SU2 ? abelian_fuse(in.group, la.labels[mid.p(sm, f)], lb.labels[mid.p(sm, f + 1)])
-                                  : mid.inner_of(sm)[0];
+      int c = fused_pair_label(in.group, la.labels[mid.p(sm, f)], lb.labels[mid.p(sm, f + 1)],
+                               tree ? mid.inner_of(sm)[0] : 0);
       const Leg& lf = in.legs[f];
       int iq = (int)(std::lower_bound(lf.labels.begin(), lf.labels.end(), c) - lf.labels.begin());
       std::vector<int> key;
@@ -824,14 +841,14 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
         if (l == f) key.push_back(iq);
         else if (l != f + 1) key.push_back(mid.p(sm, l));
       }
-      if (in.group == SYM_SU2) key.insert(key.end(), mid.inner_of(sm) + 1, mid.inner_of(sm) + mid.nin);
+      if (tree) key.insert(key.end(), mid.inner_of(sm) + 1, mid.inner_of(sm) + mid.nin);
       m_in[sm] = in.find(key);
       if (m_in[sm] < 0) fail(SYM_ERR_ARG, "internal: split source sector missing");
       m_row[sm] = pair_offset(la, lb, in.group, c, mid.p(sm, f), mid.p(sm, f + 1));
     }
     for (int64_t s = 0; s < out.nsec(); ++s) {
       block_strides(out, s, ost);
-      TermList tl = in.group != SYM_SU2 ? TermList{{s, 1.0}} : X[s];
+      TermList tl = !tree ? TermList{{s, 1.0}} : X[s];
       std::vector<Term> terms;
       int sa_[kMaxDim] = {0}, sb_[kMaxDim] = {0};
       bool first = true;
@@ -1102,7 +1119,8 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   std::vector<int> permA(freeA), permB(pairsB);
   permA.insert(permA.end(), pairsA.begin(), pairsA.end());
   permB.insert(permB.end(), freeB.begin(), freeB.end());
-  const bool su2 = A.group == SYM_SU2;
+  const bool su2 = su2_like(A.group);  // tree decompositions: SU(2), SU(2) x U(1)
+  const bool composite = A.group == SYM_SU2U1;
   Tensor Am = permuted_tensor(A, permA, Tree::comb_pair(na, nc), A.total);
   Tensor Bm = permuted_tensor(B, permB, Tree::comb_pair(nc, nb), B.total);
   std::vector<Leg> clegs;
@@ -1120,7 +1138,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
       int x = su2_top(Am, s, na);
       double f = ((x & 1) ? -1.0 : 1.0) / std::sqrt((double)x + 1.0);
       for (int i = 0; i < nc; ++i)
-        if (A.legs[pairsA[i]].dir == -1 && (Am.label(s, na + i) & 1)) f = -f;
+        if (A.legs[pairsA[i]].dir == -1 && (spin_of(A.group, Am.label(s, na + i)) & 1)) f = -f;
       for (auto& pc : XA[s]) pc.second *= f;
     }
   }
@@ -1135,25 +1153,31 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   auto XBt = transpose_xform(XB, B.nsec());
 
   // sector key x of the matrix form: SU(2) coupled spin; U(1) charge of the
-  // contracted legs as A sees them; fermion parity of the contracted legs
+  // contracted legs as A sees them; fermion parity of the contracted legs;
+  // SU(2) x U(1) both, as 4096 q + 2j (a coupled spin of at most six legs
+  // below 64 each stays below 4096)
   const bool z2f = A.group == SYM_Z2F;
+  auto q_of = [&](const Tensor& T, int64_t s, int n) {
+    return composite ? charge_of(T.group, T.label(s, n)) : T.label(s, n);
+  };
+  auto both = [&](int q, int spin) { return composite ? 4096 * q + spin : spin; };
   auto keyA = [&](int64_t s) {
-    if (su2) return su2_top(Am, s, na);
     int x = 0;
-    for (int n = na; n < Am.rank; ++n) x = z2f ? x ^ Am.label(s, n) : x + Am.legs[n].dir * Am.label(s, n);
-    return x;
+    if (!su2 || composite)
+      for (int n = na; n < Am.rank; ++n) x = z2f ? x ^ Am.label(s, n) : x + Am.legs[n].dir * q_of(Am, s, n);
+    return su2 ? both(x, su2_top(Am, s, na)) : x;
   };
   auto keyB = [&](int64_t s) {
-    if (su2) return su2_top(Bm, s, nc);
     int x = 0;
-    for (int n = 0; n < nc; ++n) x = z2f ? x ^ Bm.label(s, n) : x - Bm.legs[n].dir * Bm.label(s, n);
-    return x;
+    if (!su2 || composite)
+      for (int n = 0; n < nc; ++n) x = z2f ? x ^ Bm.label(s, n) : x - Bm.legs[n].dir * q_of(Bm, s, n);
+    return su2 ? both(x, su2_top(Bm, s, nc)) : x;
   };
   auto keyC = [&](int64_t s) {
-    if (su2) return su2_top(Cn, s, na);
-    int x = A.total;
-    for (int n = 0; n < na; ++n) x = z2f ? x ^ Cn.label(s, n) : x - Cn.legs[n].dir * Cn.label(s, n);
-    return x;
+    int x = su2 && !composite ? 0 : A.total;
+    if (!su2 || composite)
+      for (int n = 0; n < na; ++n) x = z2f ? x ^ Cn.label(s, n) : x - Cn.legs[n].dir * q_of(Cn, s, n);
+    return su2 ? both(x, su2_top(Cn, s, na)) : x;
   };
   MatForm MA = make_matform(Am, na, keyA);
   MatForm MB = make_matform(Bm, nc, keyB);

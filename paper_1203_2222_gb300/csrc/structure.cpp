@@ -1,7 +1,8 @@
-// Sector tables of U(1) and SU(2) tensors (integer-exact, host).
+// Sector tables of U(1), SU(2), fermion-parity and SU(2) x U(1) tensors (integer-exact, host).
 #include "structure.h"
 
 #include <algorithm>
+#include <cstdlib>
 #include <functional>
 
 #include "../../include/symtensor.h"
@@ -93,7 +94,8 @@ std::vector<std::vector<int>> tree_labelings(const Tree& tree, const std::vector
 }
 
 Tensor make_tensor(int group, const std::vector<Leg>& legs, int total, const Tree& tree_in) {
-  if (group != SYM_U1 && group != SYM_SU2 && group != SYM_Z2F) fail(SYM_ERR_ARG, "unknown symmetry group");
+  if (group != SYM_U1 && group != SYM_SU2 && group != SYM_Z2F && group != SYM_SU2U1)
+    fail(SYM_ERR_ARG, "unknown symmetry group");
   if (group == SYM_Z2F && total != 0 && total != 1) fail(SYM_ERR_ARG, "Z2F total parity must be 0 or 1");
   Tensor t;
   t.group = group;
@@ -108,10 +110,12 @@ Tensor make_tensor(int group, const std::vector<Leg>& legs, int total, const Tre
       if (l.degens[i] < 1) fail(SYM_ERR_ARG, "leg: degeneracy must be >= 1");
       if (i && l.labels[i] <= l.labels[i - 1]) fail(SYM_ERR_ARG, "leg: labels must increase strictly");
       if (group == SYM_SU2 && l.labels[i] < 0) fail(SYM_ERR_ARG, "leg: negative spin");
+      if (group == SYM_SU2U1 && std::abs(charge_of(group, l.labels[i])) > (1 << 20))
+        fail(SYM_ERR_ARG, "leg: charge out of range");
       if (group == SYM_Z2F && l.labels[i] != 0 && l.labels[i] != 1) fail(SYM_ERR_ARG, "leg: parity must be 0 or 1");
     }
   }
-  if (group == SYM_SU2) {
+  if (su2_like(group)) {
     t.tree = tree_in.k == t.rank ? tree_in : Tree::comb(t.rank);
     t.tree.validate();
     t.nin = std::max(t.rank - 2, 0);
@@ -139,9 +143,15 @@ Tensor make_tensor(int group, const std::vector<Leg>& legs, int total, const Tre
       for (int l = 0; l < t.rank; ++l) s ^= legs[l].labels[idx[l]];
       if (s == total) add({});
     } else {
+      // SU(2); SU(2) x U(1): the spins' tree labelings, where the charges obey the U(1) rule
+      int64_t q = 0;
       std::vector<int> spins(t.rank);
-      for (int l = 0; l < t.rank; ++l) spins[l] = legs[l].labels[idx[l]];
-      for (auto& lab : tree_labelings(t.tree, spins)) add(lab);
+      for (int l = 0; l < t.rank; ++l) {
+        spins[l] = spin_of(group, legs[l].labels[idx[l]]);
+        q += (int64_t)legs[l].dir * charge_of(group, legs[l].labels[idx[l]]);
+      }
+      if (q == t.total)
+        for (auto& lab : tree_labelings(t.tree, spins)) add(lab);
     }
     int l = t.rank - 1;
     while (l >= 0) {

@@ -17,6 +17,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include "../../include/symtensor.h"
+
 namespace sym {
 
 struct Error : std::runtime_error {
@@ -25,6 +27,13 @@ struct Error : std::runtime_error {
 };
 
 [[noreturn]] void fail(int code, const std::string& msg);
+
+// Groups whose tensors are tree decompositions (SU(2), and SU(2) x U(1)
+// whose label 64 q + 2j carries a charge next to the spin).
+inline bool su2_like(int group) { return group == SYM_SU2 || group == SYM_SU2U1; }
+inline int spin_of(int group, int label) { return group == SYM_SU2U1 ? ((label % 64) + 64) % 64 : label; }
+inline int charge_of(int group, int label) { return group == SYM_SU2U1 ? (label - spin_of(group, label)) / 64 : 0; }
+inline int su2u1_label(int charge, int spin2) { return 64 * charge + spin2; }
 
 struct Leg {
   std::vector<int> labels;  // U(1) charges or SU(2) doubled spins, increasing
@@ -64,11 +73,11 @@ struct VecHash {
 };
 
 struct Tensor {
-  int group = 0;  // SYM_U1 or SYM_SU2
+  int group = 0;  // SYM_U1, SYM_SU2, SYM_Z2F or SYM_SU2U1
   int rank = 0;
   std::vector<Leg> legs;
-  int total = 0;  // U(1) total charge
-  Tree tree;      // SU(2) only
+  int total = 0;  // U(1) total charge (SYM_SU2U1: the charge part)
+  Tree tree;      // SU(2) and SU(2) x U(1)
   int nin = 0;    // SU(2) non-root node labels per sector (rank-2 for rank>=2)
   std::vector<int> pos;        // nsec * rank label positions
   std::vector<int> inner;      // nsec * nin node spins

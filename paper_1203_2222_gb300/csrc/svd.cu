@@ -622,6 +622,7 @@ struct SvdPlan {
 };
 
 std::unique_ptr<SvdPlan> plan_svd(const Tensor& T, int nrow) {
+  if (T.group == SYM_SU2U1) fail(SYM_ERR_UNSUPPORTED, "blockwise SVD of SU(2) x U(1) tensors is not built");
   if (T.group == SYM_SU2 && T.rank != 2)
     fail(SYM_ERR_UNSUPPORTED, "blockwise SVD of SU(2) tensors is built for rank 2 (the block-diagonal form)");
   if (T.rank < 2 || nrow < 1 || nrow >= T.rank) fail(SYM_ERR_ARG, "SVD needs rank >= 2 and 1 <= nrow < rank");

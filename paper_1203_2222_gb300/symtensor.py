@@ -16,7 +16,18 @@ import torch
 
 from . import _lib as L
 
-U1, SU2, Z2F = L.SYM_U1, L.SYM_SU2, L.SYM_Z2F
+U1, SU2, Z2F, SU2U1 = L.SYM_U1, L.SYM_SU2, L.SYM_Z2F, L.SYM_SU2U1
+
+
+def su2u1_label(q, spin2):
+    """The C ABI's SU(2) x U(1) label of charge q and doubled spin 2j (include/symtensor.h)."""
+    if not 0 <= spin2 < 64:
+        raise ValueError("2j must be in 0..63")
+    return 64 * int(q) + int(spin2)
+
+
+def su2u1_pair(label):
+    return ((label - label % 64) // 64, label % 64)
 FP64, BF16X3 = L.SYM_PREC_FP64, L.SYM_PREC_BF16X3
 SymError = L.SymError
 
@@ -29,14 +40,17 @@ class Structure:
     """Sector table of a symmetric tensor (legs, total charge or tree); host only.
 
     ``legs`` is a sequence of ``(labels, degens, dir)`` (U(1) charges, SU(2)
-    doubled spins or fermion parities 0/1, strictly increasing; dir +1 out,
-    -1 in).  ``tree`` (SU(2))
+    doubled spins, fermion parities 0/1, or SU(2) x U(1) pairs (q, 2j);
+    strictly increasing; dir +1 out, -1 in).  ``tree`` (SU(2), SU(2) x U(1))
     is a list of ``(left, right)`` node children, None for the left comb.
+    ``legs`` of an SU(2) x U(1) structure read back as (q, 2j) pairs.
     """
 
     def __init__(self, group, legs=None, total=0, tree=None, _handle=None):
         self.group = int(group)
         if _handle is None:
+            if self.group == SU2U1:
+                legs = [([su2u1_label(q, j) for q, j in lab], deg, d) for lab, deg, d in legs]
             arr, _keep = L.leg_array(legs)
             h = ctypes.c_void_p()
             L.check(L.lib.sym_tensor_create(self.group, len(legs), arr, int(total),
@@ -50,7 +64,7 @@ class Structure:
         self.rank, self.numel, self.nsec = r.value, n.value, ns.value
         self.legs = [self._leg(i) for i in range(self.rank)]
         self.tree = None
-        if self.group == SU2 and self.rank >= 2:
+        if self.group in (SU2, SU2U1) and self.rank >= 2:
             buf = (ctypes.c_int * (2 * (self.rank - 1)))()
             L.check(L.lib.sym_tensor_tree(self._h, buf))
             self.tree = [(buf[2 * i], buf[2 * i + 1]) for i in range(self.rank - 1)]
@@ -61,11 +75,12 @@ class Structure:
         la = (ctypes.c_int * n.value)()
         de = (ctypes.c_int * n.value)()
         L.check(L.lib.sym_tensor_leg(self._h, i, None, la, de, None))
-        return (tuple(la), tuple(de), d.value)
+        labels = tuple(su2u1_pair(x) for x in la) if self.group == SU2U1 else tuple(la)
+        return (labels, tuple(de), d.value)
 
     def sectors(self):
         """(labels[nsec, rank + max(rank-2,0)] int32, offsets[nsec+1] int64)."""
-        w = self.rank + (max(self.rank - 2, 0) if self.group == SU2 else 0)
+        w = self.rank + (max(self.rank - 2, 0) if self.group in (SU2, SU2U1) else 0)
         lab = np.zeros((self.nsec, w), dtype=np.int32)
         off = np.zeros(self.nsec + 1, dtype=np.int64)
         L.check(L.lib.sym_tensor_sectors(self._h, lab.ctypes.data_as(L._IP) if lab.size else None,
@@ -308,7 +323,10 @@ def split_plan(S, leg, parts, precision=BF16X3):
     key = ("s", id(S), int(leg), tuple((tuple(a), tuple(b), int(c)) for a, b, c in parts), precision, S)
 
     def make(o, p):
-        arr, _keep = L.leg_array(parts)
+        ps = parts
+        if S.group == SU2U1:
+            ps = [([su2u1_label(q, j) for q, j in lab], deg, d) for lab, deg, d in parts]
+        arr, _keep = L.leg_array(ps)
         L.check(L.lib.sym_split_plan(S._h, int(leg), arr, int(precision), _byref(o), _byref(p)))
         return S.total
 

@@ -14,6 +14,7 @@ pytestmark = pytest.mark.gpu
 
 from oracle import contract as oc  # noqa: E402
 from oracle import su2 as osu2  # noqa: E402
+from oracle import su2u1 as osu2u1  # noqa: E402
 from oracle import u1 as ou1  # noqa: E402
 from oracle import z2f as oz2f  # noqa: E402
 
@@ -33,18 +34,19 @@ def rel(x, y):
 
 
 def _oleg(group, l):
-    return {"u1": ou1.Leg, "su2": osu2.Leg, "z2f": oz2f.Leg}[group](*l)
+    return {"u1": ou1.Leg, "su2": osu2.Leg, "z2f": oz2f.Leg, "su2u1": osu2u1.Leg}[group](*l)
 
 
 def _otree(group, S, legs_spec):
     if group in ("u1", "z2f"):
         return S.total
-    return S.tree if S.tree is not None else osu2.left_comb(len(legs_spec))
+    tree = S.tree if S.tree is not None else osu2.left_comb(len(legs_spec))
+    return (tree, S.total) if group == "su2u1" else tree
 
 
 def _make(group, legs, seed, dtype, total=0, tree=None):
     P = _lib()
-    S = P.Structure({"u1": P.U1, "su2": P.SU2, "z2f": P.Z2F}[group], legs, total=total, tree=tree)
+    S = P.Structure({"u1": P.U1, "su2": P.SU2, "z2f": P.Z2F, "su2u1": P.SU2U1}[group], legs, total=total, tree=tree)
     vals = np.random.default_rng(seed).standard_normal(S.numel)
     T = P.SymTensor.from_numpy(S, vals, dtype=dtype)
     host = T.data.double().cpu().numpy()  # exactly what the GPU holds
@@ -61,7 +63,8 @@ def _contract_case(group, la, lb, pa, pb, dtype, QA=0, QB=0, ta=None, tb=None, t
     torch.cuda.synchronize()
     oA = ([_oleg(group, l) for l in la], _otree(group, SA, la), a)
     oB = ([_oleg(group, l) for l in lb], _otree(group, SB, lb), b)
-    lc, tc, c_ref, resid = oc.contract(group, oA, oB, pa, pb, tree_c=C.structure.tree if group == "su2" else None)
+    tree_of_c = C.structure.tree if group in ("su2", "su2u1") else None
+    lc, tc, c_ref, resid = oc.contract(group, oA, oB, pa, pb, tree_c=tree_of_c)
     assert resid < 1e-10
     assert C.structure.numel == len(c_ref)
     c = C.data.detach().double().cpu().numpy()
@@ -73,7 +76,7 @@ def _contract_case(group, la, lb, pa, pb, dtype, QA=0, QB=0, ta=None, tb=None, t
         C.data.backward(gt)
         torch.cuda.synchronize()
         g_used = gt.double().cpu().numpy()
-        dA_ref, dB_ref, r2 = oc.contract_grad(group, oA, oB, pa, pb, g_used, tree_c=C.structure.tree if group == "su2" else None)
+        dA_ref, dB_ref, r2 = oc.contract_grad(group, oA, oB, pa, pb, g_used, tree_c=tree_of_c)
         assert r2 < 1e-10
         eA = rel(A.data.grad.double().cpu().numpy(), dA_ref)
         eB = rel(B.data.grad.double().cpu().numpy(), dB_ref)
@@ -257,16 +260,16 @@ def test_su2_large_sectors_multi_tile(dtype):
 
 # ----------------------------------------------------------- transforms ------
 
-def _transform_case(group, legs, op, args, dtype, tree=None, seed=5):
+def _transform_case(group, legs, op, args, dtype, tree=None, seed=5, total=0):
     P = _lib()
-    S, T, t = _make(group, legs, seed, dtype, 0, tree)
+    S, T, t = _make(group, legs, seed, dtype, total, tree)
     oT = ([_oleg(group, l) for l in legs], _otree(group, S, legs), t)
     if op == "permute":
         out = P.permute(T, args[0], args[1])
-        lo, to, ref, resid = oc.permute(group, oT, args[0], out.structure.tree if group == "su2" else None)
+        lo, to, ref, resid = oc.permute(group, oT, args[0], out.structure.tree if group in ("su2", "su2u1") else None)
     elif op == "fuse":
         out = P.fuse(T, args[0])
-        lo, to, ref, resid = oc.fuse(group, oT, args[0], out.structure.tree if group == "su2" else None)
+        lo, to, ref, resid = oc.fuse(group, oT, args[0], out.structure.tree if group in ("su2", "su2u1") else None)
         assert [tuple(l.labels) for l in lo] == [tuple(l[0]) for l in out.structure.legs]
         assert [tuple(l.degens) for l in lo] == [tuple(l[1]) for l in out.structure.legs]
     torch.cuda.synchronize()
@@ -330,3 +333,43 @@ def test_backward_after_another_forward_on_the_same_plan(dtype):
         assert rel(A.data.grad.double().cpu().numpy(), dA_ref) <= TOL[dtype]
         assert rel(B.data.grad.double().cpu().numpy(), dB_ref) <= TOL[dtype]
     P.device_status()
+
+
+# ------------------------------------------------- SU(2) x U(1) (composite) --
+
+# labels (q, 2j); odd charges carry half-integer spins, like a spinful
+# particle number; directions mixed; nonzero total charges
+CQ = [(-1, 1), (0, 0), (0, 2), (1, 1), (2, 0)]
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
+def test_su2u1_contraction(dtype):
+    la = [(CQ, [2, 1, 2, 1, 1], 1), (CQ, [1, 2, 1, 2, 1], -1), (CQ, [2, 2, 1, 1, 2], 1), (CQ, [1, 1, 2, 1, 1], -1)]
+    lb = [(CQ, [2, 2, 1, 1, 2], -1), (CQ, [1, 1, 2, 1, 1], 1), (CQ, [2, 1, 1, 2, 1], 1)]
+    _contract_case("su2u1", la, lb, [2, 3], [0, 1], dtype, QA=2, QB=-2)
+    _contract_case("su2u1", la, lb, [2, 3], [0, 1], dtype, QA=0, QB=0, ta=[(1, 2), (0, 4), (5, 3)])
+    _contract_case("su2u1", la, lb, [2, 3], [0, 1], dtype, QA=2, QB=0, tree_c=[(1, 2), (0, 3)])
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
+def test_su2u1_large_sectors_multi_tile(dtype):
+    # sector matrices of a few hundred rows and columns: tensor-core tiles with ragged tails
+    la = [(CQ, [30, 41, 12, 25, 9], 1), (CQ, [7, 5, 3, 6, 2], 1), (CQ, [60, 52, 49, 55, 48], 1)]
+    lb = [(CQ, [60, 52, 49, 55, 48], -1), (CQ, [70, 64, 30, 66, 20], 1)]
+    _contract_case("su2u1", la, lb, [2], [0], dtype, QA=2, QB=-2)
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
+def test_su2u1_permute_fuse_split(dtype):
+    P = _lib()
+    s = [(CQ, [2, 1, 1, 1, 1], 1), (CQ, [1, 2, 1, 1, 2], -1), (CQ, [1, 1, 2, 1, 1], 1), (CQ, [1, 1, 1, 2, 1], 1)]
+    _transform_case("su2u1", s, "permute", ([2, 0, 3, 1], None), dtype, total=2)
+    _transform_case("su2u1", s, "permute", ([0, 2, 1, 3], [(0, 1), (2, 3), (4, 5)]), dtype, tree=[(1, 2), (0, 4), (5, 3)])
+    for legs in ([(CQ, [2, 1, 1, 1, 1], 1), (CQ, [1, 2, 1, 1, 2], 1), (CQ, [1, 1, 2, 1, 1], -1)],
+                 [(CQ, [2, 1, 1, 1, 1], -1), (CQ, [1, 2, 1, 1, 2], -1), (CQ, [1, 1, 2, 1, 1], 1)]):
+        for total in (0, 2):
+            S, T, F = _transform_case("su2u1", legs, "fuse", (0,), dtype, total=total)
+            back = P.split(F, 0, [legs[0], legs[1]])
+            torch.cuda.synchronize()
+            err = rel(back.data.double().cpu().numpy(), T.data.double().cpu().numpy())
+            assert err <= (1e-13 if dtype == torch.float64 else 1e-6), err
