@@ -41,7 +41,7 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--workload", choices=["u1_mps_heff", "su2_recouple", "u1_two_site_batch", "u1_mera_grad",
-                                           "z2f_mps_heff", "u1_two_site_svd", "su2_micro"],
+                                           "z2f_mps_heff", "su2u1_mps_heff", "u1_two_site_svd", "su2_micro"],
                     default="u1_mps_heff",
                     help="u1_mps_heff (default, the metric's configuration), the large-sector su2_recouple, "
                          "the 512-problem u1_two_site_batch or the MERA gradient u1_mera_grad")
@@ -192,8 +192,9 @@ class ClockSampler:
 
 def mps_structures(P, group="u1"):
     from paper_1203_2222_gb300 import synthetic
-    m = synthetic.u1_mps_heff() if group == "u1" else synthetic.z2f_mps_heff()
-    S = {n: P.Structure(P.U1 if group == "u1" else P.Z2F, m[n]) for n in ("L", "A", "W", "R")}
+    m = {"u1": synthetic.u1_mps_heff, "z2f": synthetic.z2f_mps_heff, "su2u1": synthetic.su2u1_mps_heff}[group]()
+    g = {"u1": P.U1, "z2f": P.Z2F, "su2u1": P.SU2U1}[group]
+    S = {n: P.Structure(g, m[n]) for n in ("L", "A", "W", "R")}
     return m, S
 
 
@@ -273,6 +274,17 @@ class Z2FMPSWorkload(MPSWorkload):
                 "phys {0:1, 1:1}, MPO {0:3, 1:2}; swap signs on every permutation")
     default_steps, default_warmup, default_fp64_steps = 50, 5, 2
     group = "z2f"
+
+
+class SU2U1MPSWorkload(MPSWorkload):
+    """The MPS chain with SU(2) x U(1) legs: every gather recouples the spins
+    (6j coefficients) while the charges select the blocks."""
+    name = "su2u1_mps_heff"
+    describe = ("su2u1_mps_heff: ((L.A).W).R fwd+bwd with SU(2) x U(1) legs (labels (q, 2j)): Hubbard-like site "
+                "{(0,0), (1,1), (2,0)}, MPO {(-1,1):2, (0,0):3, (1,1):2}, 1023 bond multiplets (dense 2459) over "
+                "q = -8..8, 2j = 0..4")
+    default_steps, default_warmup, default_fp64_steps = 50, 5, 2
+    group = "su2u1"
 
 
 class SU2Workload:
@@ -427,7 +439,7 @@ class MeraWorkload:
 
 
 WORKLOADS = {"u1_mps_heff": MPSWorkload, "su2_recouple": SU2Workload, "u1_two_site_batch": BatchWorkload,
-             "u1_mera_grad": MeraWorkload, "z2f_mps_heff": Z2FMPSWorkload}  # u1_two_site_svd: SVDWorkload below
+             "u1_mera_grad": MeraWorkload, "z2f_mps_heff": Z2FMPSWorkload, "su2u1_mps_heff": SU2U1MPSWorkload}  # u1_two_site_svd: SVDWorkload below
 
 
 # ---------------------------------------------------------------- roofline ---
@@ -1147,25 +1159,33 @@ class OracleMPS:
     """The FP64 CPU oracle on the same workload (dense embedding, brute force)."""
 
     def __init__(self, group="u1"):
-        from oracle import u1, z2f
+        from oracle import su2, su2u1, u1, z2f
         from paper_1203_2222_gb300 import synthetic
-        mod = u1 if group == "u1" else z2f
-        m = synthetic.u1_mps_heff() if group == "u1" else synthetic.z2f_mps_heff()
+        mod = {"u1": u1, "z2f": z2f, "su2u1": su2u1}[group]
+        m = {"u1": synthetic.u1_mps_heff, "z2f": synthetic.z2f_mps_heff, "su2u1": synthetic.su2u1_mps_heff}[group]()
         self.group = group
         self.legs = {n: [mod.Leg(*l) for l in m[n]] for n in ("L", "A", "W", "R")}
-        self.data = {n: synthetic.normal(m["seeds"][n], mod.layout(self.legs[n], 0)[2]) for n in self.legs}
+        # second member of a tensor: total charge, or (tree, total) for SU(2) x U(1)
+        self.tot = {n: (su2.left_comb(len(self.legs[n])), 0) if group == "su2u1" else 0 for n in self.legs}
+        self.data = {n: synthetic.normal(m["seeds"][n], mod.layout(self.legs[n], self.tot[n])[2]) for n in self.legs}
         self.steps = [("L", "A", [2], [0]), (None, "W", [1, 2], [0, 2]), (None, "R", [1, 3], [2, 1])]
 
     def contraction(self, i, a=None):
         """Forward + gradient of contraction i of the chain (i = 0, 1, 2)."""
         from oracle import contract as oc
         an, bn, pa, pb = self.steps[i]
-        A = (self.legs[an], 0, self.data[an]) if an else a
-        B = (self.legs[bn], 0, self.data[bn])
+        A = (self.legs[an], self.tot[an], self.data[an]) if an else a
+        B = (self.legs[bn], self.tot[bn], self.data[bn])
         lc, qc, c, _ = oc.contract(self.group, A, B, pa, pb)
         g = np.random.default_rng(i).standard_normal(c.size)
         oc.contract_grad(self.group, A, B, pa, pb, g)
         return (lc, qc, c)
+
+    def forward0(self):
+        """Forward of the first contraction (L.A) alone."""
+        from oracle import contract as oc
+        return oc.contract(self.group, (self.legs["L"], self.tot["L"], self.data["L"]),
+                           (self.legs["A"], self.tot["A"], self.data["A"]), [2], [0])
 
     def full_step(self):
         a = None
@@ -1178,8 +1198,8 @@ class OracleMPS:
         a = None
         for j in range(i):
             an, bn, pa, pb = self.steps[j]
-            A = (self.legs[an], 0, self.data[an]) if an else a
-            lc, qc, c, _ = oc.contract(self.group, A, (self.legs[bn], 0, self.data[bn]), pa, pb)
+            A = (self.legs[an], self.tot[an], self.data[an]) if an else a
+            lc, qc, c, _ = oc.contract(self.group, A, (self.legs[bn], self.tot[bn], self.data[bn]), pa, pb)
             a = (lc, qc, c)
         return a
 
@@ -1369,6 +1389,15 @@ def cpu_baseline(args, flops, steps):
         return {"value": round(n * per / dt / 1e12, 9), "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
                 "sample": f"{n} dense elements of C from embedded slices of A and B (FP64 numpy oracle), each "
                           f"credited the forward useful flops per block entry of C; {dt:.1f} s"}
+    if args.workload == "su2u1_mps_heff":
+        o = OracleMPS("su2u1")
+        f0 = contraction_flops_host("su2u1")[0]
+        t0 = time.perf_counter()
+        o.forward0()
+        dt = time.perf_counter() - t0
+        return {"value": round(f0 / dt / 1e12, 9), "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+                "sample": f"the forward of the first contraction (L.A) alone, dense FP64 oracle with CG trees, "
+                          f"credited its own useful flops; {dt:.1f} s"}
     o = OracleMPS("z2f" if args.workload == "z2f_mps_heff" else "u1")
     t0 = time.perf_counter()
     for _ in range(steps):
@@ -1493,15 +1522,46 @@ def run_reference(args, flops_by_contraction, group="u1"):
     }
 
 
+def run_reference_su2u1(args):
+    """Oracle reference arm for su2u1_mps_heff: each step is the forward of the
+    first contraction (L.A) (the dense CG-tree oracle takes seconds per step)."""
+    f0 = contraction_flops_host("su2u1")[0]
+    o = OracleMPS("su2u1")
+    for _ in range(args.warmup):
+        o.forward0()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.forward0()
+    dt = time.perf_counter() - t0
+    value = f0 * args.steps / dt / 1e12
+    sample = "step = forward of the first contraction (L.A), dense FP64 oracle with CG trees, its own useful flops"
+    return {
+        "metric": METRIC, "value": round(value, 9), "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": SU2U1MPSWorkload.describe, "sample": sample},
+        "cpu_baseline": {"value": round(value, 9), "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 9), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
 def contraction_flops_host(group="u1"):
     """Useful forward flops of each contraction of the chain (host planning only)."""
+    old = os.environ.get("SYM_PLAN_DRYRUN")
     os.environ["SYM_PLAN_DRYRUN"] = "1"
-    import paper_1203_2222_gb300 as P
-    m, S = mps_structures(P, group)
-    t1 = P.contract_plan(S["L"], S["A"], [2], [0], P.BF16X3)
-    t2 = P.contract_plan(t1.out, S["W"], [1, 2], [0, 2], P.BF16X3)
-    t3 = P.contract_plan(t2.out, S["R"], [1, 3], [2, 1], P.BF16X3)
-    return [t.stats()["flops_fwd"] for t in (t1, t2, t3)]
+    try:
+        import paper_1203_2222_gb300 as P
+        m, S = mps_structures(P, group)
+        t1 = P.contract_plan(S["L"], S["A"], [2], [0], P.BF16X3)
+        t2 = P.contract_plan(t1.out, S["W"], [1, 2], [0, 2], P.BF16X3)
+        t3 = P.contract_plan(t2.out, S["R"], [1, 3], [2, 1], P.BF16X3)
+        return [t.stats()["flops_fwd"] for t in (t1, t2, t3)]
+    finally:
+        if old is None:
+            del os.environ["SYM_PLAN_DRYRUN"]
+        else:
+            os.environ["SYM_PLAN_DRYRUN"] = old
 
 
 def main():
@@ -1525,6 +1585,8 @@ def main():
             out = run_reference_batch(args)
         elif args.workload == "u1_mera_grad":
             out = run_reference_mera(args)
+        elif args.workload == "su2u1_mps_heff":
+            out = run_reference_su2u1(args)
         else:
             g = "z2f" if args.workload == "z2f_mps_heff" else "u1"
             out = run_reference(args, contraction_flops_host(g), g)

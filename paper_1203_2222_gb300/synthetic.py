@@ -29,6 +29,9 @@ Workload shapes (all seeds are ``1234 + index``):
 * ``u1_two_site_svd``  the two-site tensor theta[a, s1, s2, b] of that chain
   (D = 2048, total charge 0) as the matrix (a, s1) x (s2, b), truncated to
   chi = 2048 singular values.
+* ``su2u1_mps_heff``  the MPS chain with SU(2) x U(1) legs (labels (q, 2j)):
+  a Hubbard-like site {(0,0), (1,1), (2,0)}, MPO {(-1,1):2, (0,0):3, (1,1):2},
+  about 1024 bond multiplets over q = -8..8, 2j = 0..4 (2j = q mod 2).
 * ``z2f_mps_heff``  the MPS chain above with fermion-parity legs: bond
   D = 2048 as {0: 1024, 1: 1024}, physical {0:1, 1:1}, MPO {0:3, 1:2}.
 * ``su2_recouple``  rank-4 SU(2) tensors, every leg with 2j = 0..8 and
@@ -118,6 +121,37 @@ def u1_two_site_svd(D=2048, qmax=20, sigma=6.0, seed=1240):
     phys_in = ([0, 1], [1, 1], -1)
     theta = [(qs, d, -1), phys_in, phys_in, (qs, d, 1)]
     return {"group": "u1", "theta": theta, "nrow": 2, "chi": D, "seed": seed, "D": D}
+
+
+def su2u1_mps_heff(D=1024, qmax=8, sigma=3.0, seed=1241):
+    """Legs of the MPS chain ((L.A).W).R with SU(2) x U(1) legs (labels (q, 2j)).
+
+    A Hubbard-like chain: physical leg {(0,0):1, (1,1):1, (2,0):1} (empty,
+    singly occupied with spin 1/2, doubly occupied), MPO leg
+    {(-1,1):2, (0,0):3, (1,1):2} (hopping channels carrying charge -1 or +1
+    and spin 1/2, and three scalar channels).  The bond carries labels
+    (q, 2j) for q = -qmax..qmax and 2j = 0..4 with 2j = q mod 2, degeneracy
+    max(1, round-half-even(D w / sum w)) with w = exp(-q^2 / (2 sigma^2)) s_j,
+    s = (1, 1, 0.6, 0.5, 0.25) for 2j = 0..4 (about D multiplets in all).
+    Directions and contraction order as ``u1_mps_heff``; totals 0.
+    """
+    sj = [1.0, 1.0, 0.6, 0.5, 0.25]
+    labs = [(q, j2) for q in range(-qmax, qmax + 1) for j2 in range(5) if (j2 - q) % 2 == 0]
+    w = [math.exp(-q * q / (2.0 * sigma * sigma)) * sj[j2] for q, j2 in labs]
+    tot = sum(w)
+    d = [max(1, int(round(D * x / tot))) for x in w]
+    bond_in, bond_out = (labs, d, -1), (labs, d, 1)
+    phys = [(0, 0), (1, 1), (2, 0)]
+    phys_in, phys_out = (phys, [1, 1, 1], -1), (phys, [1, 1, 1], 1)
+    wl, wd = [(-1, 1), (0, 0), (1, 1)], [2, 3, 2]
+    L = [bond_in, (wl, wd, -1), bond_out]
+    A = [bond_in, phys_in, bond_out]
+    W = [(wl, wd, 1), phys_in, phys_out, (wl, wd, -1)]
+    R = [bond_out, (wl, wd, 1), bond_in]
+    return {"group": "su2u1", "L": L, "A": A, "W": W, "R": R,
+            "steps": [((1, 2), (0, 2)), ((1, 3), (2, 1))],
+            "seeds": {"L": seed, "A": seed + 100, "W": seed + 200, "R": seed + 300},
+            "D": D}
 
 
 def z2f_mps_heff(D=2048, seed=1239):
