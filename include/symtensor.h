@@ -8,7 +8,8 @@
  * Data model (Ch. 5 "Tensors as linear maps", Ch. 6 "Tree decompositions"):
  *   - A leg is a list of n labels with degeneracies and a direction
  *     (+1 'out', -1 'in').  U(1): labels are integer charges.  SU(2): labels
- *     are doubled spins 2j.  Labels are strictly increasing.
+ *     are doubled spins 2j.  Fermion parity: 0 or 1.  SU(2) x U(1):
+ *     64 q + 2j (see sym_tensor_create).  Labels are strictly increasing.
  *   - U(1): a block (sector) is one charge per leg with
  *       sum_out q - sum_in q == total   (charge conservation).
  *   - SU(2): the tensor is a tree decomposition; a sector is one spin per leg
