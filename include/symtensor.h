@@ -380,9 +380,11 @@ int sym_device_status(void);
  *   block that has not converged after 64 FP64 sweeps sets the device error word
  *   (SYM_ERR_NUMERIC, see sym_device_status).
  * sym_svd_stats: per block of the last execute (ascending x; either array
- *   may be NULL): the sweeps it took (the last one found nothing to rotate)
- *   and the rotations it applied, of the FP64 sweeps (fp32 = 0) or of the
- *   FP32 sweeps (fp32 = 1).  Synchronizes the device.
+ *   may be NULL): the sweeps it took and the rotations it applied, of the
+ *   FP64 sweeps (fp32 = 0; the last one rotated no pair by more than 1e-8
+ *   of its columns' norms, so what it left is at the FP64 rounding level)
+ *   or of the FP32 sweeps (fp32 = 1; the last one rotated no pair by more
+ *   than 1e-4, or it is the 40th).  Synchronizes the device.
  * sym_svd_truncation: keep[b] from a host copy of execute's S (reading of
  *   the truncation the thesis leaves open): every singular value sorted in
  *   descending order (ties: smaller x first, then the block's own order);

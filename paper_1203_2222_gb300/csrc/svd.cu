@@ -14,9 +14,10 @@
 //   pairs, one warp per pair, a cluster barrier between rounds); a pair whose
 //   columns are not orthogonal to within sqrt(R) ulp is rotated so that they
 //   are, and the same rotation is applied to V (V = I at the start).  When a
-//   whole sweep rotates nothing, A V = W has orthogonal columns: S = their
-//   norms, U = W / S.  The sweeps run first in FP32, then, from the FP32
-//   result made orthogonal in FP64, in FP64 (see the kernel).  The FP64
+//   whole sweep rotates nothing by more than kBigRotation(32) relative,
+//   A V = W has orthogonal columns: S = their norms, U = W / S.  The sweeps
+//   run first in FP32, then, from the FP32 result made orthogonal in FP64,
+//   in FP64 (see the kernel).  The FP64
 //   sweeps are bounded (kMaxSweeps); a block that has not converged by then
 //   sets the device error word to SYM_ERR_NUMERIC.  The columns are then
 //   ranked by norm (descending, ties by index) into S and a permutation.
@@ -53,6 +54,15 @@ constexpr int kSvdWarps = kSvdThreads / 32;
 constexpr int kSvdCluster = 8;  // CTAs (SMs) per diagonal block
 constexpr int kMaxSweeps = 64;    // FP64 sweeps before a block counts as not converged
 constexpr int kMaxSweeps32 = 40;  // FP32 sweeps (their result only seeds the FP64 ones)
+// An FP64 sweep whose rotations all had |w_p.w_q| <= kBigRotation |w_p| |w_q|
+// ends the sweeps: what it leaves is of order kBigRotation^2 from the pairs'
+// coupling plus the rotation's own residual (the angle is formed to FP32
+// accuracy, about 6e-8 of kBigRotation), both near the FP64 rounding level,
+// so a further sweep would find nothing to rotate.
+constexpr double kBigRotation = 1e-8;
+// The FP32 sweeps stop on the same rule at 1e-4: what they leave (1e-8) is
+// below FP32's own rounding of the pair products.
+constexpr float kBigRotation32 = 1e-4f;
 
 struct SvdBlock {
   int m, n;    // M_x is m x n
@@ -96,8 +106,9 @@ struct JacobiArith;
 template <>
 struct JacobiArith<float> {
   static constexpr float kEps = FLT_EPSILON;
-  static __device__ __forceinline__ bool angle(float a, float bb, float g, float tol, float& c, float& s) {
-    if (!(fabsf(g) > tol * sqrtf(a) * sqrtf(bb))) return false;
+  static __device__ __forceinline__ bool angle(float a, float bb, float g, float sab, float tol, float& c,
+                                               float& s) {
+    if (!(fabsf(g) > tol * sab)) return false;
     const float zeta = (bb - a) / (2.0f * g);
     const float t = fabsf(zeta) > 1e18f ? 0.5f / zeta
                                         : copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
@@ -117,8 +128,9 @@ struct JacobiArith<double> {
   // FP32 after scaling d and h by a power of two, and c = (1 + t^2)^(-1/2)
   // by two Newton steps in FP64 from the FP32 estimate -- GB300's FP64 units
   // are few, and FP64 square roots and divisions cost many of their cycles.
-  static __device__ __forceinline__ bool angle(double a, double bb, double g, double tol, double& c, double& s) {
-    if (!(fabs(g) > tol * sqrt(a * bb))) return false;
+  static __device__ __forceinline__ bool angle(double a, double bb, double g, double sab, double tol, double& c,
+                                               double& s) {
+    if (!(fabs(g) > tol * sab)) return false;
     const double d = bb - a, h = 2.0 * g;
     const double m = fmax(fabs(d), fabs(h));
     const int ex = (__double2hiint(m) >> 20) & 0x7ff;  // biased exponent of m
@@ -149,7 +161,7 @@ struct JacobiArith<double> {
 // NR rows per lane held in registers (R <= 32 NR); V's columns are loaded
 // with W's, so a pair costs one round trip to L2.
 template <typename T, int NR>
-__device__ __forceinline__ bool rotate_pair(T* wp, T* wq, T* vp, T* vq, int R, int C, int lane, T tol) {
+__device__ __forceinline__ int rotate_pair(T* wp, T* wq, T* vp, T* vq, int R, int C, int lane, T tol, T big) {
   T xw[NR], yw[NR], xv[NR], yv[NR];
 #pragma unroll
   for (int u = 0; u < NR; ++u) {
@@ -169,8 +181,9 @@ __device__ __forceinline__ bool rotate_pair(T* wp, T* wq, T* vp, T* vq, int R, i
   a = warp_sum(a);
   bb = warp_sum(bb);
   g = warp_sum(g);
+  const T sab = sqrt(a * bb);
   T c, s;
-  if (!JacobiArith<T>::angle(a, bb, g, tol, c, s)) return false;
+  if (!JacobiArith<T>::angle(a, bb, g, sab, tol, c, s)) return 0;
 #pragma unroll
   for (int u = 0; u < NR; ++u) {
     const int i = lane + 32 * u;
@@ -183,12 +196,12 @@ __device__ __forceinline__ bool rotate_pair(T* wp, T* wq, T* vp, T* vq, int R, i
       __stcg(vq + i, s * xv[u] + c * yv[u]);
     }
   }
-  return true;
+  return fabs(g) > big * sab ? 2 : 1;
 }
 
 // Any R: the columns streamed twice (products, then the rotation).
 template <typename T>
-__device__ __noinline__ bool rotate_pair_stream(T* wp, T* wq, T* vp, T* vq, int R, int C, int lane, T tol) {
+__device__ __noinline__ int rotate_pair_stream(T* wp, T* wq, T* vp, T* vq, int R, int C, int lane, T tol, T big) {
   T a = 0, bb = 0, g = 0;
   for (int i = lane; i < R; i += 32) {
     const T x = __ldcg(wp + i), y = __ldcg(wq + i);
@@ -199,8 +212,9 @@ __device__ __noinline__ bool rotate_pair_stream(T* wp, T* wq, T* vp, T* vq, int 
   a = warp_sum(a);
   bb = warp_sum(bb);
   g = warp_sum(g);
+  const T sab = sqrt(a * bb);
   T c, s;
-  if (!JacobiArith<T>::angle(a, bb, g, tol, c, s)) return false;
+  if (!JacobiArith<T>::angle(a, bb, g, sab, tol, c, s)) return 0;
   for (int i = lane; i < R; i += 32) {
     const T x = __ldcg(wp + i), y = __ldcg(wq + i);
     __stcg(wp + i, c * x - s * y);
@@ -211,7 +225,7 @@ __device__ __noinline__ bool rotate_pair_stream(T* wp, T* wq, T* vp, T* vq, int 
     __stcg(vp + i, c * x - s * y);
     __stcg(vq + i, s * x + c * y);
   }
-  return true;
+  return fabs(g) > big * sab ? 2 : 1;
 }
 
 // Per-cluster state of the sweeps (shared memory of every CTA; rank 0's
@@ -228,17 +242,17 @@ struct SweepCtl {
 template <typename T>
 __device__ int jacobi_sweeps(T* W, T* V, int R, int C, int max_sweeps, T tol, cg::cluster_group& cluster,
                              SweepCtl* ctl, int* flag0, int crank, int cw, int lane, int& gsweep,
-                             unsigned long long& myrot, bool& conv) {
+                             unsigned long long& myrot, bool& conv, T big_tol) {
   constexpr int kCW = kSvdCluster * kSvdWarps;
   const int Ce = C + (C & 1);
   const int rpl = (R + 31) / 32;
-  const int nr = rpl <= 1 ? 1 : rpl <= 2 ? 2 : rpl <= 4 ? 4 : rpl <= 8 ? 8 : rpl <= 12 ? 12 : 0;
+  const int nr = rpl <= 1 ? 1 : rpl <= 2 ? 2 : rpl <= 4 ? 4 : rpl <= 8 ? 8 : rpl <= 9 ? 9 : rpl <= 12 ? 12 : 0;
   int sweeps = 0;
   conv = C < 2;
   while (!conv && sweeps < max_sweeps) {
     ++sweeps;
     const int gs = ++gsweep;  // sweeps so far over both precisions (same in every thread): picks the flag
-    int did = 0;
+    int did = 0, big = 0;
     for (int r = 0; r < Ce - 1; ++r) {
       for (int k = cw; k < Ce / 2; k += kCW) {
         int p = k == 0 ? r : (r + k) % (Ce - 1);
@@ -253,17 +267,19 @@ __device__ int jacobi_sweeps(T* W, T* V, int R, int C, int max_sweeps, T tol, cg
         T* wq = W + (int64_t)q * R;
         T* vp = V + (int64_t)p * C;
         T* vq = V + (int64_t)q * C;
-        bool rot;
+        int rot;
         switch (nr) {
-          case 1: rot = rotate_pair<T, 1>(wp, wq, vp, vq, R, C, lane, tol); break;
-          case 2: rot = rotate_pair<T, 2>(wp, wq, vp, vq, R, C, lane, tol); break;
-          case 4: rot = rotate_pair<T, 4>(wp, wq, vp, vq, R, C, lane, tol); break;
-          case 8: rot = rotate_pair<T, 8>(wp, wq, vp, vq, R, C, lane, tol); break;
-          case 12: rot = rotate_pair<T, 12>(wp, wq, vp, vq, R, C, lane, tol); break;
-          default: rot = rotate_pair_stream<T>(wp, wq, vp, vq, R, C, lane, tol); break;
+          case 1: rot = rotate_pair<T, 1>(wp, wq, vp, vq, R, C, lane, tol, big_tol); break;
+          case 2: rot = rotate_pair<T, 2>(wp, wq, vp, vq, R, C, lane, tol, big_tol); break;
+          case 4: rot = rotate_pair<T, 4>(wp, wq, vp, vq, R, C, lane, tol, big_tol); break;
+          case 8: rot = rotate_pair<T, 8>(wp, wq, vp, vq, R, C, lane, tol, big_tol); break;
+          case 9: rot = rotate_pair<T, 9>(wp, wq, vp, vq, R, C, lane, tol, big_tol); break;
+          case 12: rot = rotate_pair<T, 12>(wp, wq, vp, vq, R, C, lane, tol, big_tol); break;
+          default: rot = rotate_pair_stream<T>(wp, wq, vp, vq, R, C, lane, tol, big_tol); break;
         }
         if (rot) {
           did = 1;
+          big |= rot == 2;
           ++myrot;
         }
       }
@@ -271,14 +287,17 @@ __device__ int jacobi_sweeps(T* W, T* V, int R, int C, int max_sweeps, T tol, cg
     }
     // did any warp of the cluster rotate?  flags alternate between sweeps, so
     // the one read now is never the one being cleared for the next sweep
-    if (__syncthreads_or(did) && threadIdx.x == 0) atomicOr(flag0 + (gs & 1), 1);
+    const int f = (__syncthreads_or(did) ? 1 : 0) | (__syncthreads_or(big) ? 2 : 0);
+    if (f && threadIdx.x == 0) atomicOr(flag0 + (gs & 1), f);
     cluster.sync();
     if (threadIdx.x == 0) {
       ctl->any = flag0[gs & 1];
       if (crank == 0) ctl->flag[(gs + 1) & 1] = 0;
     }
     __syncthreads();
-    conv = ctl->any == 0;
+    // converged: nothing rotated by more than big_tol relative -- what
+    // remains is then of order big_tol^2
+    conv = !(ctl->any & 2);
     __syncthreads();  // any and gsweep are rewritten by the next sweep
   }
   return sweeps;
@@ -348,7 +367,7 @@ __device__ void newton_schulz_factor(const double* Q, int C, double* G, int cw, 
 // (an orthogonality error e becomes ~1.5 e^2 per step), W = A V is formed in
 // FP64, and FP64 sweeps polish W and V to FP64 convergence.  The result is
 // the FP64 Jacobi result; the FP32 part only chooses the starting point.
-__global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThreads, 1)
+__global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThreads, 2)
     svd_jacobi_kernel(const SvdBlock* __restrict__ blocks, const SvdPiece* __restrict__ pieces,
                       const double* __restrict__ T, double* __restrict__ work, double* __restrict__ S,
                       int* __restrict__ perm, int* __restrict__ sweeps, long long* __restrict__ rotations,
@@ -414,7 +433,7 @@ __global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThread
   bool conv32, conv;
   int gsweep = 0;
   const int sw32 = jacobi_sweeps<float>(W32, V32, R, C, kMaxSweeps32, sqrtf((float)R) * FLT_EPSILON, cluster,
-                                        &ctl, flag0, crank, cw, lane, gsweep, rot32, conv32);
+                                        &ctl, flag0, crank, cw, lane, gsweep, rot32, conv32, kBigRotation32);
 
   // V = V32 made orthogonal in FP64: two Newton-Schulz steps through the G
   // buffer, the first one's product in W's buffer (free until W = A V)
@@ -432,7 +451,7 @@ __global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThread
   cluster.sync();
 
   const int sw64 = jacobi_sweeps<double>(W, V, R, C, kMaxSweeps, sqrt((double)R) * DBL_EPSILON, cluster, &ctl,
-                                         flag0, crank, cw, lane, gsweep, rot64, conv);
+                                         flag0, crank, cw, lane, gsweep, rot64, conv, kBigRotation);
   if (lane == 0 && rot32) atomicAdd(cluster.map_shared_rank(&nrot[0], 0), rot32);
   if (lane == 0 && rot64) atomicAdd(cluster.map_shared_rank(&nrot[1], 0), rot64);
 
