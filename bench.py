@@ -464,7 +464,7 @@ TRAFFIC = {
         "direct": {"ratio": 0.97, "sha": "32a083d9660812bd"},
     },
     "u1_two_site_svd": {  # profiles/svd_u1_two_site_svd.md (full size, mean of 10 launches)
-        "svd_jacobi": {"bytes_per_launch": 8677017, "sha": "ed66c8ab431e4f85"},
+        "svd_jacobi": {"bytes_per_launch": 8650342, "sha": "dac386f91d8a6964"},
     },
     "z2f_mps_heff": {  # profiles/traffic_z2f_mps_heff_and_mera.md (full size, mean of 48 step launches)
         "gemm_tc": {"bytes_per_launch": 196125834, "sha": "17524e1d9ff325bc"},
