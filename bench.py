@@ -74,6 +74,23 @@ def parse():
 
 # ----------------------------------------------------------------- helpers ---
 
+def max_over_ranks(x, world, device=None):
+    """The largest of every rank's x (a job takes as long as its slowest
+    rank); x itself on one rank.  Every rank must call it."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step, steps, world, ms):
+    """Units per second of the whole job: every rank (a replica) processes
+    units_per_rank_step per step, and the job takes ms for `steps` steps."""
+    return units_per_rank_step * steps * world / (ms * 1e-3)
+
+
 def load_peaks():
     try:
         with open(PEAKS_PATH) as f:
@@ -692,12 +709,9 @@ def run_ours(args, rank, world):
         accumulate()
         for p in plans:
             p.profile(False)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     ms_per_step = ms / args.steps
-    value = flops * args.steps * world / (ms * 1e-3) / 1e12
+    value = whole_job_rate(flops, args.steps, world, ms) / 1e12
 
     # ---- accuracy against the FP64 path, and the FP64 GPU comparator
     launch_mode = "cuda graph replay" if graph is not None else "eager"
@@ -875,12 +889,9 @@ def run_svd(args, rank, world):
         torch.distributed.barrier()
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     ms_per_step = ms / args.steps
-    value = args.steps * world / (ms * 1e-3)
+    value = whole_job_rate(1.0, args.steps, world, ms)
 
     # per-kernel device times (the same launches, timed one by one)
     kms = {"svd_jacobi": 0.0, "svd_factor": 0.0}
