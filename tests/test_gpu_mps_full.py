@@ -1,0 +1,79 @@
+"""Full-size parity of the MPS effective-Hamiltonian step the bench times:
+Y = ((L.A).W).R and the gradients of <G, Y> with respect to L, A, W and R,
+through the public API, against the FP64 oracle chained the same way
+(oracle/contract.py: contract, then contract_grad in reverse order).  The
+inputs are the bench's (same seeds, same cotangent G); the split-BF16 case
+feeds the oracle the float32 values the GPU holds.  Bond D = 2048 over
+charges -20..20 (U(1)) and D = 2048 as {0: 1024, 1: 1024} (fermion parity).
+
+Tolerance (relative Frobenius error): 1e-12 on the FP64 path, 2e-5 on the
+split-BF16 x3 path.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float64: 1e-12, torch.float32: 2e-5}
+STEPS = [("L", "A", [2], [0]), (None, "W", [1, 2], [0, 2]), (None, "R", [1, 3], [2, 1])]
+
+
+def _rel(x, y):
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    return float(np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-300))
+
+
+def _oracle_chain(group, spec, host, G):
+    """(Y, {name: gradient}) of the chain in FP64 on the host."""
+    from oracle import contract as oc
+    from oracle import u1, z2f
+    mod = u1 if group == "u1" else z2f
+    T = {n: ([mod.Leg(*l) for l in spec[n]], 0, host[n]) for n in ("L", "A", "W", "R")}
+    ins, cur = [], None
+    for an, bn, pa, pb in STEPS:
+        A = T[an] if an else cur
+        lc, qc, c, resid = oc.contract(group, A, T[bn], pa, pb)
+        assert resid < 1e-10
+        ins.append((A, T[bn], pa, pb))
+        cur = (lc, qc, c)
+    grads = {}
+    g = G
+    for i in (2, 1, 0):
+        A, B, pa, pb = ins[i]
+        dA, dB, resid = oc.contract_grad(group, A, B, pa, pb, g)
+        assert resid < 1e-10
+        grads[STEPS[i][1]] = dB
+        if i == 0:
+            grads["L"] = dA
+        g = dA
+    return cur[2], grads
+
+
+@pytest.mark.parametrize("group", ["u1", "z2f"])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["float64", "float32"])
+def test_mps_step_full_size_against_oracle(group, dtype):
+    import paper_1203_2222_gb300 as P
+    from paper_1203_2222_gb300 import synthetic
+    spec = synthetic.u1_mps_heff() if group == "u1" else synthetic.z2f_mps_heff()
+    g = P.U1 if group == "u1" else P.Z2F
+    S = {n: P.Structure(g, spec[n]) for n in ("L", "A", "W", "R")}
+    data = {n: torch.as_tensor(synthetic.normal(spec["seeds"][n], S[n].numel)).to(dtype).cuda().requires_grad_(True)
+            for n in S}
+    T = {n: P.SymTensor(S[n], data[n]) for n in S}
+    T1 = P.contract(T["L"], T["A"], [2], [0])
+    T2 = P.contract(T1, T["W"], [1, 2], [0, 2])
+    Y = P.contract(T2, T["R"], [1, 3], [2, 1])
+    G = torch.as_tensor(synthetic.normal(4242, Y.structure.numel)).to(dtype).cuda()
+    grads = torch.autograd.grad(Y.data, [data[n] for n in ("L", "A", "W", "R")], grad_outputs=G)
+    torch.cuda.synchronize()
+    P.device_status()
+    host = {n: data[n].detach().double().cpu().numpy() for n in S}
+    y_ref, g_ref = _oracle_chain(group, spec, host, G.double().cpu().numpy())
+    assert Y.structure.numel == y_ref.size
+    errs = {"Y": _rel(Y.data.detach().double().cpu().numpy(), y_ref)}
+    for n, gr in zip(("L", "A", "W", "R"), grads):
+        errs["d" + n] = _rel(gr.double().cpu().numpy(), g_ref[n])
+    assert max(errs.values()) <= TOL[dtype], errs
