@@ -1093,6 +1093,9 @@ def _time_ms(fn, steps, warmup, flush, stream):
 def run_su2_micro(args, rank, world):
     """Every comparison of SU(2)-invariant and regular tensors the thesis plots,
     on the library's kernels; one JSON line with every series."""
+    import ctypes
+    import itertools
+
     import torch
     import paper_1203_2222_gb300 as P
     from paper_1203_2222_gb300 import _lib as L
@@ -1114,11 +1117,10 @@ def run_su2_micro(args, rank, world):
         plan = make_plan(S)
         x = torch.randn(S.numel, dtype=dtype, device=dev)
         y = torch.empty(plan.out.numel, dtype=dtype, device=dev)
-        ptr = lambda t: ctypes.c_void_p(t.data_ptr())
-        fn = lambda: L.check(L.lib.sym_plan_execute(plan._h, ptr(x), ptr(y), ctypes.c_void_p(stream.cuda_stream)))
-        return _time_ms(fn, K, W, flush, stream), S.numel
+        args_ = (plan._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                 ctypes.c_void_p(stream.cuda_stream))
+        return _time_ms(lambda: L.check(L.lib.sym_plan_execute(*args_)), K, W, flush, stream), S.numel
 
-    import ctypes
     series = {"permute": [], "fuse": [], "matmul": [], "svd": []}
     for d in (2, 4, 8, 12, 16, 20):
         row = {"d": d}
@@ -1177,7 +1179,6 @@ def run_su2_micro(args, rank, world):
             plan = P.permute_plan(S, [0, 2, 1] + list(range(3, k)), None, P.FP64)
             dt = time.perf_counter() - t0
             n = 0
-            import itertools
             for tup in itertools.product(sp, repeat=k):
                 G, _, _ = P.su2_gamma(list(tup), None, [0, 2, 1] + list(range(3, k)), None)
                 n += int(np.count_nonzero(np.abs(G) > 1e-12))  # exact zeros may round to ~1e-17
