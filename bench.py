@@ -31,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "useful TFLOP/s of symmetric block-sparse contraction fwd+bwd vs plain FP64 GPU"
+SPLIT_BF16_TOL = 2e-5  # relative error bar of the split-BF16 x3 path against FP64
 WORKLOAD = ("u1_mps_heff: ((L.A).W).R fwd+bwd, D=2048 over q=-20..20 (gaussian sigma=6), "
             "phys {0:1,1:1}, MPO w=5 {-1:1,0:3,+1:1}")
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -585,9 +586,20 @@ def run_ours(args, rank, world):
         t0 = time.time()
         space = autotune.SPACE if not args.tune_space else {k: autotune.SPACE[k] for k in args.tune_space.split(",")}
         known = autotune.load(args.workload, table)  # the search starts from the better of defaults and this
+        # a candidate must keep the step within the split-BF16 bar of the FP64 path
+        ref64 = wl.step(P, {n: v.detach().double().requires_grad_(True) for n, v in data.items()}, G.double())
+        ref64 = [ref64[0].detach()] + [g.detach() for g in ref64[1]]
+
+        def accurate():
+            y, gs = run_once(data, G)
+            outs = [y.detach()] + [g.detach() for g in gs]
+            return max(float((a.double() - b).norm() / b.norm()) for a, b in zip(outs, ref64)) <= SPLIT_BF16_TOL
+
         params, ms_t, hist = autotune.tune(lambda: run_once(data, G), space=space, graph=not args.no_graph,
                                            starts=list(autotune.PRESETS) + ([known] if known else []),
-                                           log=lambda m: print("# " + m, file=sys.stderr, flush=True))
+                                           log=lambda m: print("# " + m, file=sys.stderr, flush=True),
+                                           check=accurate)
+        del ref64
         autotune.save(args.workload, params, ms_t, hist[0]["ms"], len(hist), path=table)
         tuning = {"source": "autotuner search", "params": params, "evaluations": len(hist),
                   "ms_per_step_defaults": hist[0]["ms"], "ms_per_step_tuned": round(ms_t, 5),

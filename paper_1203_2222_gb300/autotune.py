@@ -11,7 +11,8 @@ candidate is timed on the caller's own step -- the step re-plans under the
 candidate parameters (plan caches are keyed by the tuning epoch), then CUDA
 events time ``reps`` replays of a CUDA graph of the step, each after an L2
 flush, following ``warmup`` eager steps, median of ``trials`` -- and a
-value replaces the incumbent only when it is faster by more than ``tol``.
+value replaces the incumbent only when it is faster by more than ``tol``
+and, given a ``check``, when its results stay accurate.
 The winner is stored per (device, workload) in a JSON table that later runs
 load (``load`` / ``save``); ``tune`` leaves it installed.
 """
@@ -98,7 +99,7 @@ def time_step(step, reps=5, warmup=2, trials=3, graph=True, flush_mb=256):
 
 
 def tune(step, space=None, start=None, reps=5, warmup=2, trials=3, rounds=2, tol=0.02, log=None, graph=True,
-         starts=PRESETS):
+         starts=PRESETS, check=None):
     """Coordinate descent over `space` from `start` (default: the current parameters).
 
     step() runs one step of the workload (it must plan through the cached
@@ -107,6 +108,10 @@ def tune(step, space=None, start=None, reps=5, warmup=2, trials=3, rounds=2, tol
     starting points, each applied over the first one (by default the presets
     above; a caller adds e.g. an earlier table entry): the descent begins at
     the fastest of them, so a search never ends worse than a known point.
+    check(), if given, runs with a faster candidate's parameters installed
+    and returns whether its results are still accurate enough; a candidate
+    it rejects never becomes the incumbent (the kernel choice changes the
+    rounding of the split-BF16 path).
     Returns (parameters, ms per step, history); the parameters are installed.
     """
     space = SPACE if space is None else space
@@ -125,13 +130,23 @@ def tune(step, space=None, start=None, reps=5, warmup=2, trials=3, rounds=2, tol
             log(f"tune {json.dumps(params)} -> {ms:.4f} ms")
         return ms
 
+    def accurate(params):
+        if check is None:
+            return True
+        st.tune_set(**params)  # measure() left them installed; set them again for clarity
+        ok = bool(check())
+        history[-1]["accurate"] = ok
+        if not ok and log:
+            log(f"tune {json.dumps(params)} rejected: results not accurate enough")
+        return ok
+
     best = measure(base)
     if best is None:
         raise ValueError("starting parameters are out of range")
     for other in starts:
         cand = dict(base, **other)
         ms = measure(cand)
-        if ms is not None and ms < best:
+        if ms is not None and ms < best and accurate(cand):
             base, best = cand, ms
     for _ in range(rounds):
         improved = False
@@ -141,7 +156,7 @@ def tune(step, space=None, start=None, reps=5, warmup=2, trials=3, rounds=2, tol
                     continue
                 cand = dict(base, **{name: v})
                 ms = measure(cand)
-                if ms is not None and ms < best * (1.0 - tol):
+                if ms is not None and ms < best * (1.0 - tol) and accurate(cand):
                     base, best, improved = cand, ms, True
         if not improved:
             break

@@ -82,3 +82,36 @@ def test_autotune_table_round_trip(tmp_path):
     autotune.save("other", {"tc_min_mn": 64}, 1.0, 1.0, 1, path=path, device="dev")
     assert autotune.load("w", path, device="dev") == p
     assert autotune.load("w", path, device="another device") is None
+
+
+CHECK_SCRIPT = r'''
+import paper_1203_2222_gb300 as P
+from paper_1203_2222_gb300 import autotune
+
+# timing stand-in: tc_all = 1 would be the fastest point, a lower tc_min_mn next
+def fake_time(step, reps, warmup, trials, graph=True):
+    t = P.tune_get()
+    return 1.0 - 0.5 * t["tc_all"] - 0.001 * (64 - t["tc_min_mn"])
+
+autotune.time_step = fake_time
+space = {"tc_all": [0, 1], "tc_min_mn": [16, 64]}
+base = dict(P.tune_get(), tc_all=0, tc_min_mn=64)
+# without a check the descent takes tc_all = 1
+params, ms, hist = autotune.tune(lambda: None, space=space, start=base, starts=())
+assert params["tc_all"] == 1, params
+# a check that rejects tc_all = 1 (as an accuracy bar would) keeps it off
+params, ms, hist = autotune.tune(lambda: None, space=space, start=base, starts=(),
+                                 check=lambda: P.tune_get()["tc_all"] == 0)
+assert params["tc_all"] == 0 and params["tc_min_mn"] == 16, params
+assert any(h.get("accurate") is False for h in hist)
+assert P.tune_get()["tc_all"] == 0
+print("CHECK OK")
+'''
+
+
+def test_search_rejects_candidates_the_accuracy_check_refuses():
+    env = dict(os.environ, SYM_PLAN_DRYRUN="1", PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-c", CHECK_SCRIPT], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "CHECK OK" in r.stdout
