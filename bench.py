@@ -1131,9 +1131,12 @@ def run_su2_micro(args, rank, world):
         y = torch.empty(plan.out.numel, dtype=dtype, device=dev)
         args_ = (plan._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                  ctypes.c_void_p(stream.cuda_stream))
-        return _time_ms(lambda: L.check(L.lib.sym_plan_execute(*args_)), K, W, flush, stream), S.numel
+        ms = _time_ms(lambda: L.check(L.lib.sym_plan_execute(*args_)), K, W, flush, stream)
+        launches[0] += K * plan.launches()
+        return ms, S.numel
 
     series = {"permute": [], "fuse": [], "matmul": [], "svd": []}
+    launches = [0]  # the library's kernels launched by the timed calls
     for d in (2, 4, 8, 12, 16, 20):
         row = {"d": d}
         for kind, leg, grp in (("su2", su2_leg, P.SU2), ("regular", reg_leg, P.U1)):
@@ -1162,6 +1165,7 @@ def run_su2_micro(args, rank, world):
             B = P.SymTensor(SB, torch.randn(SB.numel, device=dev))
             with torch.no_grad():
                 row[kind + "_ms"] = round(_time_ms(lambda: P.contract(A, B, [1], [0]), K, W, flush, stream), 4)
+            launches[0] += K * P.contract_plan(SA, SB, [1], [0], P.BF16X3).launches()
         row["ratio"] = round(row["regular_ms"] / row["su2_ms"], 3)
         row["dtype"] = "split-BF16 x3 (fp32 blocks)"
         series["matmul"].append(row)
@@ -1173,6 +1177,7 @@ def run_su2_micro(args, rank, world):
             S = P.Structure(grp, [leg(d, 1), leg(d, -1)])
             T = P.SymTensor(S, torch.randn(S.numel, dtype=torch.float64, device=dev))
             row[kind + "_ms"] = round(_time_ms(lambda: P.svd(T, 1), K, W, flush, stream), 4)
+            launches[0] += 2 * K  # the Jacobi and the factor launch
         Md = torch.randn(9 * d, 9 * d, dtype=torch.float64, device=dev)
         row["regular_library_ms"] = round(_time_ms(lambda: torch.linalg.svd(Md), K, W, flush, stream), 4)
         row["ratio"] = round(row["regular_ms"] / row["su2_ms"], 3)
@@ -1202,7 +1207,7 @@ def run_su2_micro(args, rank, world):
         "dtype": "f64 (permute, fuse, svd), bf16x3-f32acc (matmul)", "data": "synthetic",
         "config": {"workload": MicroWorkload.describe, "l2": "flushed before every timed call (256 MiB write)",
                    "timing": f"median of {K} calls after {W} warm-up calls, CUDA events"},
-        "series": series, "spin_networks": sn, "gpu_launches": None,
+        "series": series, "spin_networks": sn, "gpu_launches": launches[0],
     }
     return out
 

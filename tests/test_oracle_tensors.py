@@ -236,7 +236,7 @@ def test_su2_swap_factor_in_permute():
 
 
 def test_su2_fused_leg_example8():
-    # Ch. 5, Example 8 (with the reading of the survey: V^(A) = V_1, V^(B) = 2V_0 + V_1)
+    # Ch. 5, Example 8 (read with V^(A) = V_1, V^(B) = 2V_0 + V_1: the printed example is inconsistent)
     a = su2.Leg([2], [1], 1)
     b = su2.Leg([0, 2], [2, 1], 1)
     d, pairs = su2.fused_leg(a, b)
