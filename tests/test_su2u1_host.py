@@ -54,6 +54,15 @@ for l3 in ([(CQ, [2, 1, 1, 1, 1], 1), (CQ, [1, 2, 1, 1, 2], 1), (CQ, [1, 1, 2, 1
         assert fp.out.numel == ref.size
         assert P.split_plan(fp.out, 0, [l3[0], l3[1]], P.FP64).out.numel == S.numel
 
+# a batch of composite contractions is one plan; each problem's result
+# structure equals its single plan's
+As = [P.Structure(P.SU2U1, legs, total=q) for q in (0, 2, -2)]
+Bs = [P.Structure(P.SU2U1, lb, total=q) for q in (0, -2, 2)]
+bp = P.contract_batch_plan(As, Bs, [2, 3], [0, 1], P.BF16X3)
+for a, b, o in zip(As, Bs, bp.outs):
+    single = P.contract_plan(a, b, [2, 3], [0, 1], P.BF16X3).out
+    assert o.numel == single.numel and o.total == single.total and o.legs == single.legs
+
 try:
     P.SVDPlan(P.Structure(P.SU2U1, legs[:2] + [(CQ, [1] * 5, 1)], total=0), 1)
     raise SystemExit("SVD of a composite tensor accepted")
