@@ -100,6 +100,9 @@ GAMMA_CASES = [
     ([1, 1, 1, 1], None, [0, 1, 2, 3], [(1, 2), (4, 3), (0, 5)]),
     ([2, 1, 1, 2, 2], None, [4, 0, 3, 1, 2], [(0, 1), (2, 3), (6, 4), (5, 7)]),
     ([3, 3, 2, 2, 2], [(0, 1), (2, 3), (5, 6), (7, 4)], [1, 0, 2, 4, 3], None),
+    # rank 6 (the library's largest): comb to a balanced tree, and back through a permutation
+    ([1, 1, 1, 1, 2, 2], None, [0, 2, 1, 3, 5, 4], [(0, 1), (2, 3), (4, 5), (6, 7), (9, 8)]),
+    ([2, 1, 1, 2, 1, 1], [(0, 1), (2, 3), (4, 5), (6, 7), (9, 8)], [3, 0, 5, 1, 4, 2], None),
 ]
 
 
