@@ -63,6 +63,19 @@ for a, b, o in zip(As, Bs, bp.outs):
     single = P.contract_plan(a, b, [2, 3], [0, 1], P.BF16X3).out
     assert o.numel == single.numel and o.total == single.total and o.legs == single.legs
 
+# the bench's composite MPS chain: every plan builds, results have the oracle's legs
+from paper_1203_2222_gb300 import synthetic
+ms = synthetic.su2u1_mps_heff()
+Sm = {n: P.Structure(P.SU2U1, ms[n]) for n in ("L", "A", "W", "R")}
+cur_s, cur_o = Sm["L"], ([m.Leg(*l) for l in ms["L"]], (su2.left_comb(3), 0), None)
+for bn, pa, pb in (("A", [2], [0]), ("W", [1, 2], [0, 2]), ("R", [1, 3], [2, 1])):
+    plan = P.contract_plan(cur_s, Sm[bn], pa, pb, P.BF16X3)
+    lc = oc.result_legs(cur_o[0], [m.Leg(*l) for l in ms[bn]], pa, pb)
+    assert [tuple(l.labels) for l in lc] == [tuple(l[0]) for l in plan.out.legs]
+    assert plan.stats()["flops_fwd"] > 0
+    cur_s, cur_o = plan.out, (lc, None, None)
+assert cur_s.numel == Sm["A"].numel  # Y has A's legs
+
 try:
     P.SVDPlan(P.Structure(P.SU2U1, legs[:2] + [(CQ, [1] * 5, 1)], total=0), 1)
     raise SystemExit("SVD of a composite tensor accepted")
