@@ -1,17 +1,23 @@
 #!/usr/bin/env python
 """Benchmark: symmetric block-sparse contraction, forward + backward, on one GB300.
 
-Workload (the MPS effective-Hamiltonian apply with U(1) symmetry): bond
-D = 2048 over charges -20..20 (Gaussian degeneracies, sigma 6), physical leg
-{0:1, 1:1}, MPO leg {-1:1, 0:3, +1:1}; one step = Y = ((L.A).W).R forward and
-the gradients of <G, Y> with respect to L, A, W and R (autograd through the
-library's adjoint), all on synthetic N(0,1) blocks.
+Default workload (the large-sector configuration, SU(2) with recoupling):
+rank-4 SU(2)-invariant tensors whose legs carry 2j = 0..8 with degeneracies
+drawn uniformly in 1..32 (seeded); A (comb tree, all legs out) is recoupled
+by 6j coefficients into the matrix tree and its legs 1, 3 are contracted
+with the dual legs 0, 1 of B.  One step = C = contract(A, B) forward and the
+gradients of <G, C> with respect to A and B (autograd through the library's
+adjoint), on N(0,1) blocks.  Other workloads (--workload): the U(1) MPS
+effective-Hamiltonian apply, the 512-problem batch, the MERA gradient, the
+fermionic and SU(2) x U(1) MPS chains, the blockwise SVD and the SU(2)
+micro-benchmarks.
 
 Metric: useful TFLOP/s = block-sparse GEMM flops (sum over sectors of 2 m n k,
 forward + backward) / device time.  Reported for the split-BF16 x3 tcgen05
-path (the value), next to the plain FP64 GPU path and the FP64 CPU oracle.
+path (the value), next to the plain FP64 GPU path and the FP64 CPU oracle,
+with the relative error against both.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
 
 Rank 0 prints one JSON line.  Under torchrun (N > 1) every rank runs the same
 workload on its own GPU (replicas; weak scaling) and the slowest rank's time
@@ -43,14 +49,15 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--workload", choices=["u1_mps_heff", "su2_recouple", "u1_two_site_batch", "u1_mera_grad",
                                            "z2f_mps_heff", "su2u1_mps_heff", "u1_two_site_svd", "su2_micro"],
-                    default="u1_mps_heff",
-                    help="u1_mps_heff (default, the metric's configuration), the large-sector su2_recouple, "
-                         "the 512-problem u1_two_site_batch or the MERA gradient u1_mera_grad")
+                    default="su2_recouple",
+                    help="su2_recouple (default: the large-sector SU(2) recoupling contraction at full size), "
+                         "the U(1) MPS chain u1_mps_heff, the 512-problem u1_two_site_batch, the MERA gradient "
+                         "u1_mera_grad, ...")
     ap.add_argument("--su2-dmax", type=int, default=32,
                     help="su2_recouple: largest degeneracy (32 = the full configuration; smaller sizes serve "
                          "profiler captures of the same kernels)")
-    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 100; su2_recouple 5)")
-    ap.add_argument("--warmup", type=int, default=None, help="warm-up steps (default 5; su2_recouple 3)")
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 20 for su2_recouple)")
+    ap.add_argument("--warmup", type=int, default=None, help="warm-up steps (default 5)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=None, help="FP64 comparator steps (default 10; su2_recouple 1)")
     ap.add_argument("--cpu-sample-steps", type=int, default=1)
@@ -74,6 +81,12 @@ def parse():
 
 
 # ----------------------------------------------------------------- helpers ---
+
+def bench_config(describe):
+    """The `config` of both arms' JSON lines: the workload alone, so that the
+    two lines name the same configuration."""
+    return {"workload": describe}
+
 
 def max_over_ranks(x, world, device=None):
     """The largest of every rank's x (a job takes as long as its slowest
@@ -312,7 +325,9 @@ class SU2Workload:
     name = "su2_recouple"
     describe = ("su2_recouple: rank-4 SU(2), legs 2j=0..8 with degeneracies U{1..32} (seeded), "
                 "A comb tree recoupled (6j) to the matrix tree, contract A(1,3) with B(0,1); fwd+bwd")
-    default_steps, default_warmup, default_fp64_steps = 5, 3, 1
+    # 20 timed steps of ~86 ms: a timed region long enough for the clock
+    # sampler; one FP64 comparator step (~30 s on the CUDA cores' FP64 units)
+    default_steps, default_warmup, default_fp64_steps = 20, 5, 1
 
     dmax = 32
 
@@ -744,6 +759,12 @@ def run_ours(args, rank, world):
 
     err = max([rel(y32, y64)] + [rel(a, b) for a, b in zip(g32, g64)])
     del y64, g64
+    # inputs and results on the host for the oracle's sampled check (rank 0)
+    check = None
+    if args.workload == "su2_recouple" and args.su2_dmax == 32 and rank == 0 and not args.no_cpu_baseline:
+        check = {"A": data["A"].detach().cpu().numpy(), "B": data["B"].detach().cpu().numpy(),
+                 "G": G.detach().cpu().numpy(), "C": y32.cpu().numpy(),
+                 "dA": g32[0].cpu().numpy(), "dB": g32[1].cpu().numpy()}
     e64 = []
     for _ in range(args.fp64_steps):
         flush.fill_(1.0)
@@ -840,14 +861,14 @@ def run_ours(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16x3-f32acc", "data": "synthetic",
-        "config": {"workload": wl.describe + (f" [dmax {args.su2_dmax}]" if args.workload == "su2_recouple" and
-                                               args.su2_dmax != 32 else "")
-                   + (f" [{args.batch_n} problems]" if args.workload == "u1_two_site_batch" and args.batch_n != 512
-                      else ""), "precision": "split-BF16 x3 on tcgen05, FP32 accumulate, fp32 blocks",
-                   "useful_gflop_per_step": round(flops / 1e9, 4),
-                   "l2": "flushed between timed steps (256 MiB write)",
-                   "launch": launch_mode,
-                   "parallelism": f"replicas x{world}"},
+        "config": bench_config(wl.describe + (f" [dmax {args.su2_dmax}]" if args.workload == "su2_recouple" and
+                                              args.su2_dmax != 32 else "")
+                               + (f" [{args.batch_n} problems]" if args.workload == "u1_two_site_batch" and
+                                  args.batch_n != 512 else "")),
+        "precision": "split-BF16 x3 on tcgen05, FP32 accumulate, fp32 blocks",
+        "useful_gflop_per_step": round(flops / 1e9, 4),
+        "l2": "flushed between timed steps (256 MiB write)", "launch": launch_mode,
+        "parallelism": f"replicas x{world}",
         "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
         "fp64_gpu": ({"value": round(value64, 5), "unit": "TFLOP/s", "ms_per_step": round(ms64, 4)}
                      if value64 else None),
@@ -858,7 +879,7 @@ def run_ours(args, rank, world):
         "clocks": clk, "gpu_launches": launches_per_step * args.steps,
         "tuning": tuning,
     }
-    return out, flops
+    return out, flops, check
 
 
 # ------------------------------------------------------------- blockwise SVD ---
@@ -999,11 +1020,11 @@ def run_svd(args, rank, world):
         "metric": SVD_METRIC, "value": round(value, 4), "unit": "SVD/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": SVDWorkload.describe,
-                   "precision": "FP64 result: FP32 Jacobi sweeps seed FP64 Newton-Schulz + FP64 Jacobi sweeps",
-                   "blocks": plan.nblocks, "singular_values": plan.nsv, "chi": chi,
-                   "l2": "flushed between timed steps (256 MiB write)", "launch": "eager (host truncation)",
-                   "parallelism": f"replicas x{world}"},
+        "config": bench_config(SVDWorkload.describe),
+        "precision": "FP64 result: FP32 Jacobi sweeps seed FP64 Newton-Schulz + FP64 Jacobi sweeps",
+        "blocks": plan.nblocks, "singular_values": plan.nsv, "chi": chi,
+        "l2": "flushed between timed steps (256 MiB write)", "launch": "eager (host truncation)",
+        "parallelism": f"replicas x{world}",
         "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
         "e2e": {"value": round(1e3 / ms_e2e * world, 4), "unit": "SVD/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e, 4)},
@@ -1062,7 +1083,7 @@ def run_reference_svd(args):
         "metric": SVD_METRIC, "value": round(value, 4), "unit": "SVD/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": SVDWorkload.describe, "sample": sample},
+        "config": bench_config(SVDWorkload.describe), "sample": sample,
         "cpu_baseline": {"value": round(value, 4), "unit": "SVD/s", "cores": cpu_cores(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 4), "unit": "SVD/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -1205,8 +1226,8 @@ def run_su2_micro(args, rank, world):
         "metric": MICRO_METRIC, "value": last["ratio"], "unit": "x", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": last["su2_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64 (permute, fuse, svd), bf16x3-f32acc (matmul)", "data": "synthetic",
-        "config": {"workload": MicroWorkload.describe, "l2": "flushed before every timed call (256 MiB write)",
-                   "timing": f"median of {K} calls after {W} warm-up calls, CUDA events"},
+        "config": bench_config(MicroWorkload.describe), "l2": "flushed before every timed call (256 MiB write)",
+        "timing": f"median of {K} calls after {W} warm-up calls, CUDA events",
         "series": series, "spin_networks": sn, "gpu_launches": launches[0],
     }
     return out
@@ -1313,6 +1334,50 @@ class OracleSU2:
         sa = su2.embed_slice(self.la, su2.left_comb(4), self.a, {0: idx[0], 2: idx[1]})
         sb = su2.embed_slice(self.lb, su2.left_comb(4), self.b, {2: idx[2], 3: idx[3]})
         return float(np.sum(sa * sb))
+
+
+def su2_oracle_check(h, flops, n):
+    """The FP64 CPU oracle on the bench's own inputs and results: n dense
+    elements each of C, dA and dB (oracle.sample: slices of the embedded
+    inputs, summed), at indices drawn in uniformly chosen sectors, against
+    the embedding of the GPU's result blocks at the same indices.  Returns
+    the cpu_baseline (the oracle's elements timed on the host cores, each
+    credited the useful flops per block entry of its tensor) and the relative
+    error of each result over its sample."""
+    from oracle import contract as oc
+    from oracle import sample, su2
+    from paper_1203_2222_gb300 import synthetic
+    c = synthetic.su2_recouple(dmax=32, jmax2=8)
+    la = [su2.Leg(*l) for l in c["A"]]
+    lb = [su2.Leg(*l) for l in c["B"]]
+    pa, pb = c["pairsA"], c["pairsB"]
+    lc = oc.result_legs(la, lb, pa, pb)
+    comb, nodes_c = su2.left_comb(4), oc.comb_pair_tree(2, 2)
+    A, B, G = (la, comb, h["A"]), (lb, comb, h["B"]), (lc, nodes_c, h["G"])
+    rng = np.random.default_rng(0)
+
+    per_entry = {"C": flops / 3.0 / h["C"].size, "dA": flops / 3.0 / h["A"].size, "dB": flops / 3.0 / h["B"].size}
+    kinds = {
+        "C": (lambda i: sample.contraction_element(su2, A, B, pa, pb, i), (lc, nodes_c, h["C"]), (lc, nodes_c)),
+        "dA": (lambda i: sample.grad_a_element(su2, A, B, pa, pb, G, i), (la, comb, h["dA"]), (la, comb)),
+        "dB": (lambda i: sample.grad_b_element(su2, A, B, pa, pb, G, i), (lb, comb, h["dB"]), (lb, comb)),
+    }
+    t_ref, credited, errs = 0.0, 0.0, {}
+    for name, (ref_fn, got_t, lay) in kinds.items():
+        idxs = sample.draw_indices(su2, *lay, rng, n)
+        t0 = time.perf_counter()
+        ref = np.array([ref_fn(i) for i in idxs])
+        t_ref += time.perf_counter() - t0
+        credited += n * per_entry[name]
+        got = np.array([sample.element(su2, got_t, i) for i in idxs])
+        errs[name] = float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))
+    base = {"value": round(credited / t_ref / 1e12, 9), "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{n} dense elements each of C, dA and dB on the bench's own inputs (slices of the embedded "
+                      f"tensors, FP64 numpy oracle), each credited the useful flops per block entry of its tensor; "
+                      f"{t_ref:.1f} s"}
+    err = {"value": max(errs.values()), "per_result": errs,
+           "sample": f"relative Frobenius error over {n} sampled dense elements of each result"}
+    return base, err
 
 
 def su2_flops_per_entry():
@@ -1494,7 +1559,7 @@ def run_reference_mera(args):
         "metric": METRIC, "value": round(value, 9), "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": MeraWorkload.describe, "sample": sample},
+        "config": bench_config(MeraWorkload.describe), "sample": sample,
         "cpu_baseline": {"value": round(value, 9), "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 9), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -1523,7 +1588,7 @@ def run_reference_batch(args):
         "metric": METRIC, "value": round(value, 9), "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": BatchWorkload.describe, "sample": sample},
+        "config": bench_config(BatchWorkload.describe), "sample": sample,
         "cpu_baseline": {"value": round(value, 9), "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 9), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -1549,7 +1614,7 @@ def run_reference_su2(args):
         "metric": METRIC, "value": round(value, 9), "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": SU2Workload.describe, "sample": sample},
+        "config": bench_config(SU2Workload.describe), "sample": sample,
         "cpu_baseline": {"value": round(value, 9), "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 9), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -1573,8 +1638,8 @@ def run_reference(args, flops_by_contraction, group="u1"):
         "metric": METRIC, "value": round(value, 6), "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD if group == "u1" else Z2FMPSWorkload.describe,
-                   "sample": "step s = contraction (s mod 3) of the chain, fwd + grad"},
+        "config": bench_config(WORKLOAD if group == "u1" else Z2FMPSWorkload.describe),
+        "sample": "step s = contraction (s mod 3) of the chain, fwd + grad",
         "cpu_baseline": {"value": round(value, 6), "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
                          "sample": "one contraction of ((L.A).W).R per step, rotating, dense FP64 numpy oracle"},
         "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -1598,7 +1663,7 @@ def run_reference_su2u1(args):
         "metric": METRIC, "value": round(value, 9), "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": SU2U1MPSWorkload.describe, "sample": sample},
+        "config": bench_config(SU2U1MPSWorkload.describe), "sample": sample,
         "cpu_baseline": {"value": round(value, 9), "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 9), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -1663,9 +1728,13 @@ def main():
         if rank == 0 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_svd(args.cpu_sample_steps)
     else:
-        out, flops = run_ours(args, rank, world)
+        out, flops, check = run_ours(args, rank, world)
         if rank == 0 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(args, flops, args.cpu_sample_steps)
+            if check is not None:
+                out["cpu_baseline"], out["max_rel_err_vs_oracle"] = su2_oracle_check(
+                    check, flops, SU2_SAMPLE * max(args.cpu_sample_steps, 1))
+            else:
+                out["cpu_baseline"] = cpu_baseline(args, flops, args.cpu_sample_steps)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

@@ -327,12 +327,20 @@ int sym_su2_gamma(int rank, const int* spins, const int* tree_in, const int* per
  *   Asynchronous on `stream`.  The first call on a device looks up the
  *   array's device address (cudaGetSymbolAddress) with that device current;
  *   make that first call before any stream capture.  Every call copies its
- *   work lists into the shared array and clears the regions that must start
- *   at zero, so calls whose executions overlap on the GPU (other streams,
- *   other threads) race: serialize them.  Plans are cached on the host per
- *   (A, B, pairs, precision).  Errors: SYM_ERR_UNSUPPORTED (with the needed
- *   size) if the contraction needs more than 32 MiB of scratch, the argument
- *   errors of sym_contract_plan, SYM_ERR_CUDA if a copy or launch fails.     */
+ *   work lists into the shared array, which keeps the last call's contents
+ *   (nothing in it needs to start at zero: the call's own gathers and
+ *   zero-fill items write everything its GEMMs read), so calls whose
+ *   executions overlap on the GPU (other streams, other threads) race:
+ *   serialize them.  Plans are cached on the host under the contents of A's
+ *   and B's structures (legs, total, tree), the pairs, the precision and the
+ *   sym_tune epoch, so a destroyed handle whose address is reused never
+ *   reaches a stale plan and sym_tune_set takes effect on the next call; at
+ *   most 64 plans are kept, the oldest dropped first.  A bounded device-side
+ *   wait that expires sets a second static error word, which
+ *   sym_device_status reads and clears with the library's own.  Errors:
+ *   SYM_ERR_UNSUPPORTED (with the needed size) if the contraction needs more
+ *   than 32 MiB of scratch, the argument errors of sym_contract_plan,
+ *   SYM_ERR_CUDA if a copy or launch fails.                                  */
 int sym_contract_noalloc(sym_tensor A, sym_tensor B, int npairs,
                          const int* pairsA, const int* pairsB, int precision,
                          const void* a, const void* b, void* c, void* stream);

@@ -424,6 +424,7 @@ bool Plan::f64() const { return precision == SYM_PREC_FP64; }
 
 namespace {
 int* g_err_word = nullptr;
+std::vector<int*> g_extra_err_words;  // registered by sym_contract_noalloc (static device words)
 std::mutex g_err_mu;
 }  // namespace
 
@@ -440,13 +441,26 @@ int* device_error_word() {
   return g_err_word;
 }
 
+void register_device_error_word(int* w) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (std::find(g_extra_err_words.begin(), g_extra_err_words.end(), w) == g_extra_err_words.end())
+    g_extra_err_words.push_back(w);
+}
+
 int take_device_error() {
   std::lock_guard<std::mutex> lk(g_err_mu);
-  if (!g_err_word) return SYM_OK;
-  int h = 0;
-  if (cudaMemcpy(&h, g_err_word, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SYM_ERR_CUDA;
-  if (h != 0) cudaMemset(g_err_word, 0, sizeof(int));
-  return h != 0 ? h : SYM_OK;
+  std::vector<int*> words = g_extra_err_words;
+  if (g_err_word) words.insert(words.begin(), g_err_word);
+  int code = SYM_OK;
+  for (int* w : words) {
+    int h = 0;
+    if (cudaMemcpy(&h, w, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SYM_ERR_CUDA;
+    if (h != 0) {
+      cudaMemset(w, 0, sizeof(int));
+      if (code == SYM_OK) code = h;
+    }
+  }
+  return code;
 }
 
 void* DeviceArena::alloc(size_t bytes, bool zero) {

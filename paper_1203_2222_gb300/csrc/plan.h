@@ -154,6 +154,9 @@ int exec_contract_backward(Plan& p, const void* A, const void* B, const void* dC
 // take_device_error() reads and clears it.
 int* device_error_word();
 int take_device_error();
+// Another device error word (a static __device__ int) that take_device_error
+// also reads and clears.
+void register_device_error_word(int* w);
 
 // Structure helpers shared with the C ABI.
 Leg fused_leg(const Leg& a, const Leg& b, int group);

@@ -1,93 +1,98 @@
-"""SU(2) recoupling contraction at full size, checked on sampled dense elements.
+"""SU(2) recoupling contraction at full size: forward and backward checked
+against the oracle on sampled dense elements.
 
 The workload of the large-sector configuration: rank-4 SU(2) tensors whose
 legs carry 2j = 0..8 with degeneracies drawn in 1..32, A in the comb tree,
 its legs 1 and 3 contracted with the dual legs of B (the gather recouples A
 into the matrix tree by 6j coefficients).  At this size (A: 7.5e8 block
 entries, 1.3e13 useful flops per forward) the dense oracle cannot embed the
-tensors, so the test draws elements of the dense result and lets the oracle
-compute each one from two embedded slices (oracle.su2.embed_slice), and it
-embeds the GPU's result blocks at the same indices.  The backward pass is
-checked through the identity <dA, X> = <G, contract(X, B)> (C is linear in
-A), which holds at any size; the gradients are checked against the oracle
-and finite differences at small sizes in test_gpu_parity.py.
+tensors, so the test draws dense elements of C = contract(A, B) and of the
+gradients dA, dB of <G, C>, lets the oracle compute each one from slices of
+the embedded inputs (oracle.sample), and embeds the GPU's result blocks at
+the same indices.  Elements are drawn with J_z conserved (so none is a
+structural zero), at least 16 in every matrix-form sector of C (coupled spin
+2e = 0..16) plus the largest block of each result, and at least 256 per
+result.  The oracle's elements run in a pool of spawned host processes that
+read the tensors from memory-mapped files.
 
 Inputs are N(0,1) draws of a seeded torch generator on the device.
 """
+import os
+import shutil
+import tempfile
+
 import numpy as np
 import pytest
+
+import oracle_pool
 
 torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-
-def _sampled_elements(la, lb, lc, nodes_c, ah, bh, ch, nsamp, seed):
-    from oracle import su2
-    secs = su2.layout(lc, nodes_c)[0]
-    loffs = [l.offsets() for l in lc]
-    rng = np.random.default_rng(seed)
-    ref, got = [], []
-    for _ in range(nsamp):
-        sec = secs[int(rng.integers(len(secs)))]
-        idx = []
-        for l, p in enumerate(sec[0]):
-            j2, d = lc[l].labels[p], lc[l].degens[p]
-            idx.append(loffs[l][p] + int(rng.integers((j2 + 1) * d)))
-        sa = su2.embed_slice(la, su2.left_comb(4), ah, {0: idx[0], 2: idx[1]})
-        sb = su2.embed_slice(lb, su2.left_comb(4), bh, {2: idx[2], 3: idx[3]})
-        ref.append(float(np.sum(sa * sb)))
-        got.append(float(su2.embed_slice(lc, nodes_c, ch, dict(enumerate(idx)))))
-    return np.array(got), np.array(ref)
-
-
-@pytest.mark.parametrize("dmax,dtype,tol", [(32, torch.float32, 2e-5), (16, torch.float64, 1e-12)],
-                         ids=["full_bf16x3", "half_fp64"])
-def test_su2_recouple_contraction_sampled_against_oracle(dmax, dtype, tol):
-    import paper_1203_2222_gb300 as P
-    from paper_1203_2222_gb300 import synthetic
+def _tasks(c, dmax, per_e, per_tensor, seed):
+    """Sampled indices: C stratified by its matrix-form sector (coupled spin
+    e), dA and dB uniform over their sectors, plus the largest block of each."""
     from oracle import contract as oc
-    from oracle import su2
-    c = synthetic.su2_recouple(dmax=dmax, jmax2=8)
-    SA, SB = P.Structure(P.SU2, c["A"]), P.Structure(P.SU2, c["B"])
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(1236)
-    a = torch.randn(SA.numel, device="cuda", dtype=dtype, generator=gen)
-    b = torch.randn(SB.numel, device="cuda", dtype=dtype, generator=gen)
-    C = P.contract(P.SymTensor(SA, a), P.SymTensor(SB, b), c["pairsA"], c["pairsB"])
-    nodes_c = oc.comb_pair_tree(2, 2)
-    assert C.structure.tree == nodes_c
+    from oracle import sample, su2
     la = [su2.Leg(*l) for l in c["A"]]
     lb = [su2.Leg(*l) for l in c["B"]]
     lc = oc.result_legs(la, lb, c["pairsA"], c["pairsB"])
-    ah, bh, ch = a.cpu().numpy(), b.cpu().numpy(), C.data.cpu().numpy()
-    got, ref = _sampled_elements(la, lb, lc, nodes_c, ah, bh, ch, nsamp=24, seed=dmax)
-    assert np.linalg.norm(ref) > 0
-    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    assert rel <= tol, rel
+    comb, nodes_c = su2.left_comb(4), oc.comb_pair_tree(2, 2)
+    rng = np.random.default_rng(seed)
+    tasks = []
+    secs_c = su2.layout(lc, nodes_c)[0]
+    by_e = {}
+    for s in secs_c:
+        by_e.setdefault(s[1][0], []).append(s)  # the node spin of legs (0, 1) = that of (2, 3)
+    assert sorted(by_e) == list(range(0, 17)), sorted(by_e)
+    for e, secs in sorted(by_e.items()):
+        tasks += [("C", i) for i in sample.draw_indices(su2, lc, nodes_c, rng, per_e, sectors=secs)]
+    for name, legs, nodes in (("C", lc, nodes_c), ("dA", la, comb), ("dB", lb, comb)):
+        secs = su2.layout(legs, nodes)[0]
+        big = max(secs, key=lambda s: int(np.prod(su2.block_shape(legs, s))))
+        tasks += [(name, i) for i in sample.draw_indices(su2, legs, nodes, rng, 8, sectors=[big])]
+        if name != "C":
+            tasks += [(name, i) for i in sample.draw_indices(su2, legs, nodes, rng, per_tensor)]
+    return tasks
 
 
-def test_su2_recouple_backward_is_the_adjoint_at_full_size():
+def _check(dmax, dtype, per_e, per_tensor, tol):
     import paper_1203_2222_gb300 as P
     from paper_1203_2222_gb300 import synthetic
-    c = synthetic.su2_recouple(dmax=32, jmax2=8)
+    c = synthetic.su2_recouple(dmax=dmax, jmax2=8)
+    tasks = _tasks(c, dmax, per_e, per_tensor, seed=dmax)
     SA, SB = P.Structure(P.SU2, c["A"]), P.Structure(P.SU2, c["B"])
     gen = torch.Generator(device="cuda")
-    gen.manual_seed(77)
-    a = torch.randn(SA.numel, device="cuda", generator=gen).requires_grad_(True)
-    b = torch.randn(SB.numel, device="cuda", generator=gen).requires_grad_(True)
+    gen.manual_seed(1236)
+    a = torch.randn(SA.numel, device="cuda", dtype=dtype, generator=gen).requires_grad_(True)
+    b = torch.randn(SB.numel, device="cuda", dtype=dtype, generator=gen).requires_grad_(True)
     C = P.contract(P.SymTensor(SA, a), P.SymTensor(SB, b), c["pairsA"], c["pairsB"])
-    G = torch.randn(C.structure.numel, device="cuda", generator=gen)
+    G = torch.randn(C.structure.numel, device="cuda", dtype=dtype, generator=gen)
     da, db = torch.autograd.grad(C.data, [a, b], grad_outputs=G)
-    X = torch.randn(SA.numel, device="cuda", generator=gen)
-    Y = torch.randn(SB.numel, device="cuda", generator=gen)
-    with torch.no_grad():
-        cx = P.contract(P.SymTensor(SA, X), P.SymTensor(SB, b.detach()), c["pairsA"], c["pairsB"]).data
-        cy = P.contract(P.SymTensor(SA, a.detach()), P.SymTensor(SB, Y), c["pairsA"], c["pairsB"]).data
-    for g, x, cxy in ((da, X, cx), (db, Y, cy)):
-        lhs = float(torch.dot(g.double(), x.double()))
-        rhs = float(torch.dot(G.double(), cxy.double()))
-        # both sides are sums of ~1e9 products of N(0,1) numbers computed in
-        # split-BF16 with FP32 accumulation: compare against the scale of the terms
-        scale = float(G.double().norm() * cxy.double().norm())
-        assert abs(lhs - rhs) <= 2e-5 * scale, (lhs, rhs, scale)
+    torch.cuda.synchronize()
+    P.device_status()
+    d = tempfile.mkdtemp(prefix="su2full_")
+    try:
+        for n, t in (("A", a), ("B", b), ("G", G), ("C", C.data), ("dA", da), ("dB", db)):
+            np.save(os.path.join(d, n + ".npy"), t.detach().cpu().numpy())
+        del a, b, G, C, da, db
+        torch.cuda.empty_cache()
+        res = oracle_pool.su2_elements(d, c, tasks)
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
+    for kind in ("C", "dA", "dB"):
+        ref = np.array([r for k, r, _ in res if k == kind])
+        got = np.array([g for k, _, g in res if k == kind])
+        assert len(ref) >= (256 if per_tensor >= 256 else per_tensor)
+        assert np.count_nonzero(np.abs(ref) > 0) >= 0.9 * len(ref), kind  # not zero against zero
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert rel <= tol, (kind, rel)
+
+
+def test_su2_recouple_full_size_bf16x3_forward_and_backward_against_oracle():
+    _check(32, torch.float32, per_e=16, per_tensor=256, tol=2e-5)
+
+
+def test_su2_recouple_half_size_fp64_forward_and_backward_against_oracle():
+    _check(16, torch.float64, per_e=4, per_tensor=64, tol=1e-12)

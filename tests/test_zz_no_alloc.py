@@ -84,3 +84,60 @@ def test_noalloc_rejects_contractions_beyond_its_scratch():
                                     ctypes.c_void_p(c.data_ptr()), None)
     assert rc == L.SYM_ERR_UNSUPPORTED
     assert b"static limit" in L.lib.sym_last_error()
+
+
+def _case_structures(P, synthetic, case):
+    if case == "u1_ragged":
+        qs = [-1, 0, 1]
+        la = [(qs, [70, 150, 33], -1), (qs, [5, 9, 2], 1), (qs, [90, 140, 61], 1)]
+        lb = [(qs, [90, 140, 61], -1), (qs, [100, 131, 7], 1)]
+        return P.U1, la, lb, [2], [0]
+    c = synthetic.su2_recouple(dmax=3, jmax2=4)
+    return P.SU2, c["A"], c["B"], c["pairsA"], c["pairsB"]
+
+
+def test_noalloc_alternating_plans_share_the_array():
+    """Calls with different plans in a row on one stream: each call lays out
+    the shared array for its own plan over what the previous one left."""
+    import paper_1203_2222_gb300 as P
+    from paper_1203_2222_gb300 import _lib as L
+    from paper_1203_2222_gb300 import synthetic
+    rng = np.random.default_rng(5)
+    setups = {}
+    for case in ("u1_ragged", "su2_recouple"):
+        g, la, lb, pa, pb = _case_structures(P, synthetic, case)
+        SA, SB = P.Structure(g, la), P.Structure(g, lb)
+        a = torch.as_tensor(rng.standard_normal(SA.numel)).float().cuda()
+        b = torch.as_tensor(rng.standard_normal(SB.numel)).float().cuda()
+        ref = P.contract(P.SymTensor(SA, a), P.SymTensor(SB, b), pa, pb).data
+        setups[case] = (SA, SB, pa, pb, a, b, ref)
+    torch.cuda.synchronize()
+    for case in ("u1_ragged", "su2_recouple", "u1_ragged", "su2_recouple"):
+        SA, SB, pa, pb, a, b, ref = setups[case]
+        out = _run_noalloc(P, L, SA, SB, pa, pb, P.BF16X3, a, b, ref.numel())
+        assert _rel(out, ref) <= TOL[torch.float32], case
+    P.device_status()
+
+
+def test_noalloc_recreated_structures_get_their_own_plans():
+    """Destroying the structures and creating different ones (whose handles
+    may land at the same addresses) must not reuse the old plan."""
+    import gc
+
+    import paper_1203_2222_gb300 as P
+    from paper_1203_2222_gb300 import _lib as L
+    rng = np.random.default_rng(6)
+    qs = [-1, 0, 1]
+    for trial, (dk, dn) in enumerate([([40, 90, 30], [50, 70, 20]), ([200, 310, 120], [60, 140, 90]),
+                                      ([40, 90, 30], [50, 70, 20])]):
+        SA = P.Structure(P.U1, [(qs, [64, 100, 36], 1), (qs, dk, -1)])
+        SB = P.Structure(P.U1, [(qs, dk, 1), (qs, dn, -1)])
+        a = torch.as_tensor(rng.standard_normal(SA.numel)).cuda()
+        b = torch.as_tensor(rng.standard_normal(SB.numel)).cuda()
+        ref = P.contract(P.SymTensor(SA, a), P.SymTensor(SB, b), [1], [0]).data
+        torch.cuda.synchronize()
+        out = _run_noalloc(P, L, SA, SB, [1], [0], P.FP64, a, b, ref.numel())
+        assert _rel(out, ref) <= TOL[torch.float64], trial
+        del SA, SB
+        gc.collect()
+    P.device_status()
