@@ -74,6 +74,48 @@ def test_recoupling_F_matches_oracle():
             ocg.recoupling_F(jd, je, ja, jb, jc, J), abs=1e-14)
 
 
+def _workload_F_args(rng, n):
+    """Arguments (jd, je, ja, jb, jc, J) of F as the large-sector workload
+    uses them: legs ja, jb, jc with 2j <= 8, node spins jd, je, J <= 16."""
+    out = []
+    while len(out) < n:
+        ja, jb, jc = (int(x) for x in rng.integers(0, 9, size=3))
+        jd, je, J = (int(x) for x in rng.integers(0, 17, size=3))
+        if (ocg.triangle(ja, jb, jd) and ocg.triangle(jd, jc, J) and ocg.triangle(jb, jc, je)
+                and ocg.triangle(ja, je, J)):
+            out.append((jd, je, ja, jb, jc, J))
+    return out
+
+
+def test_recoupling_F_exact_at_workload_spins():
+    """The library's F (Racah's single sum over long-double factorials)
+    against exact values (sympy's 6j in rational arithmetic, Ch. 5 Eq. sixj
+    with the sign and normalisation of Eq. f) across the workload's spins,
+    including the largest coupled spins, where the sum's cancellation is
+    worst."""
+    wigner = pytest.importorskip("sympy.physics.wigner")
+    from sympy import Rational, sqrt as ssqrt
+    rng = np.random.default_rng(21)
+    args = _workload_F_args(rng, 400)
+    args += [a for a in itertools.product([14, 15, 16], [14, 15, 16], [7, 8], [7, 8], [7, 8], [14, 15, 16])
+             if ocg.triangle(a[2], a[3], a[0]) and ocg.triangle(a[0], a[4], a[5]) and ocg.triangle(a[3], a[4], a[1])
+             and ocg.triangle(a[2], a[1], a[5])]
+    for jd, je, ja, jb, jc, J in args:
+        six = wigner.wigner_6j(*(Rational(x, 2) for x in (ja, jb, jd, jc, J, je)))
+        exact = (-1) ** ((ja + jb + jc + J) // 2) * ssqrt((jd + 1) * (je + 1)) * six
+        want = float(exact.evalf(30))
+        assert su2_F(jd, je, ja, jb, jc, J) == pytest.approx(want, abs=1e-14), (jd, je, ja, jb, jc, J)
+
+
+def test_recoupling_F_matches_oracle_at_workload_spins():
+    """The library's F against the oracle's F (four CG tensors contracted,
+    Ch. 5 Eq. f with the fourth-factor reading) at the workload's spins."""
+    rng = np.random.default_rng(22)
+    for jd, je, ja, jb, jc, J in _workload_F_args(rng, 120):
+        assert su2_F(jd, je, ja, jb, jc, J) == pytest.approx(
+            ocg.recoupling_F(jd, je, ja, jb, jc, J), abs=1e-14), (jd, je, ja, jb, jc, J)
+
+
 def _brute_gamma(spins, tree_in, perm, tree_out):
     k = len(spins)
     legs = [osu2.Leg([s], [1], 1) for s in spins]
@@ -100,6 +142,10 @@ GAMMA_CASES = [
     ([1, 1, 1, 1], None, [0, 1, 2, 3], [(1, 2), (4, 3), (0, 5)]),
     ([2, 1, 1, 2, 2], None, [4, 0, 3, 1, 2], [(0, 1), (2, 3), (6, 4), (5, 7)]),
     ([3, 3, 2, 2, 2], [(0, 1), (2, 3), (5, 6), (7, 4)], [1, 0, 2, 4, 3], None),
+    # the large-sector workload's recoupling at its largest leg spins (2j = 8, node spins to 16)
+    ([8, 8, 8, 8], None, [0, 2, 1, 3], [(0, 1), (2, 3), (4, 5)]),
+    ([7, 8, 5, 6], None, [0, 2, 1, 3], [(0, 1), (2, 3), (4, 5)]),
+    ([8, 7, 8, 5], [(1, 2), (0, 4), (5, 3)], [3, 1, 2, 0], None),
     # rank 6 (the library's largest): comb to a balanced tree, and back through a permutation
     ([1, 1, 1, 1, 2, 2], None, [0, 2, 1, 3, 5, 4], [(0, 1), (2, 3), (4, 5), (6, 7), (9, 8)]),
     ([2, 1, 1, 2, 1, 1], [(0, 1), (2, 3), (4, 5), (6, 7), (9, 8)], [3, 0, 5, 1, 4, 2], None),

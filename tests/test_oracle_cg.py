@@ -185,3 +185,50 @@ def test_F_is_orthogonal_matrix():
         F = np.array([[cgm.recoupling_F(d, e, ja, jb, jc, J) for e in Es] for d in Ds])
         assert F.shape[0] == F.shape[1]
         assert np.allclose(F @ F.T, np.eye(len(Ds)), atol=1e-13)
+
+
+# The large-sector SU(2) workload couples leg spins 2j <= 8 into node spins
+# 2e <= 16: the recoupling coefficients it uses have three arguments <= 8
+# (the legs a, b and the spectator d) and three <= 16 (c, e, f).
+def _workload_sixj_args(rng, n):
+    out = []
+    while len(out) < n:
+        a, b, d = (int(x) for x in rng.integers(0, 9, size=3))
+        c, e, f = (int(x) for x in rng.integers(0, 17, size=3))
+        if _admissible(a, b, c, d, e, f):
+            out.append((a, b, c, d, e, f))
+    return out
+
+
+def test_sixj_zero_argument_closed_form_at_workload_spins():
+    for a, b, c in itertools.product(_spins(8), _spins(16), _spins(16)):
+        if not cgm.triangle(a, b, c):
+            continue
+        want = (-1) ** ((a + b + c) // 2) / sqrt((b + 1) * (c + 1))
+        assert _sixj(a, b, c, 0, c, b) == pytest.approx(want, abs=1e-14)
+
+
+def test_sixj_against_sympy_at_workload_spins():
+    wigner = pytest.importorskip("sympy.physics.wigner")
+    from sympy import S
+    rng = np.random.default_rng(12)
+    args = _workload_sixj_args(rng, 150) + [(8, 8, 16, 8, 8, 16), (7, 8, 15, 8, 7, 16), (8, 8, 16, 8, 16, 8)]
+    for a, b, c, d, e, f in args:
+        if not _admissible(a, b, c, d, e, f):
+            continue
+        ref = float(wigner.wigner_6j(*(S(x) / 2 for x in (a, b, c, d, e, f))).evalf(30))
+        assert _sixj(a, b, c, d, e, f) == pytest.approx(ref, abs=1e-14), (a, b, c, d, e, f)
+
+
+def test_sixj_orthogonality_at_workload_spins():
+    # sum_x (2x+1)(2f+1) {a b x; c d f}{a b x; c d f'} = delta_{f f'}, legs up to 2j = 8
+    rng = np.random.default_rng(13)
+    for _ in range(6):
+        a, b, c, d = (int(x) for x in rng.integers(0, 9, size=4))
+        if (a + b + c + d) % 2:
+            d = max(d - 1, 0) if d else 1
+        fs = [f for f in range(0, 17) if cgm.triangle(a, d, f) and cgm.triangle(c, b, f)]
+        xs = [x for x in range(0, 17) if cgm.triangle(a, b, x) and cgm.triangle(c, d, x)]
+        for f, f2 in itertools.product(fs, fs):
+            s = sum((x + 1) * (f + 1) * _sixj(a, b, x, c, d, f) * _sixj(a, b, x, c, d, f2) for x in xs)
+            assert s == pytest.approx(1.0 if f == f2 else 0.0, abs=1e-13)
