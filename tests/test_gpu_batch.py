@@ -132,3 +132,46 @@ def test_full_batch_matches_single_plans_and_oracle():
         got = t1[plans[0].off_c[i]:plans[0].off_c[i + 1]].cpu().numpy()
         assert _rel(got, c_ref) <= 1e-12
     P.device_status()
+
+
+def test_full_batch_bf16x3_chain_and_gradients_against_oracle():
+    """The bench's batched step at full size (512 problems, split-BF16 x3):
+    the whole four-contraction chain forward and the gradients of <G, Y>
+    with respect to L, theta, W (both uses) and R, for the three smallest
+    problems, a stratified sample across the bond dimension (the problems
+    at the 20/40/60/80% quantiles of D) and the largest, against the FP64
+    oracle's dense chain and its adjoint step by step."""
+    import paper_1203_2222_gb300 as P
+    from oracle import contract as oc
+    from paper_1203_2222_gb300 import synthetic
+    spec = synthetic.u1_two_site_batch()
+    S, plans, offs, data = _batch(P, spec, torch.float32)
+    Y = _chain(P, plans, data)
+    G = torch.as_tensor(synthetic.normal(4243, Y.numel())).to(torch.float32).cuda()
+    names = ("L", "theta", "W", "R")
+    grads = torch.autograd.grad(Y, [data[n] for n in names], grad_outputs=G)
+    torch.cuda.synchronize()
+    P.device_status()
+    yh, gh = Y.detach().double().cpu().numpy(), G.double().cpu().numpy()
+    gr = {n: g.double().cpu().numpy() for n, g in zip(names, grads)}
+    dh = {n: data[n].detach().double().cpu().numpy() for n in names}
+    pr = spec["problems"]
+    order = list(np.argsort([p["D"] for p in pr], kind="stable"))
+    n = len(order)
+    sample = order[:3] + [order[int(q * (n - 1))] for q in (0.2, 0.4, 0.6, 0.8)] + [order[-1]]
+    for i in sample:
+        sl = {k: slice(offs[k][i], offs[k][i + 1]) for k in offs}
+        host = {k: dh[k][sl[k]] for k in offs}
+        ins, (_, _, y_ref) = _oracle_chain(spec, i, host)
+        ys = slice(plans[3].off_c[i], plans[3].off_c[i + 1])
+        assert _rel(yh[ys], y_ref) <= 2e-5, (i, pr[i]["D"])
+        dc, ref = gh[ys], {}
+        for k in range(3, -1, -1):
+            a, b, pa, pb = ins[k]
+            da, db, _ = oc.contract_grad("u1", a, b, pa, pb, dc)
+            nb = spec["steps"][k][1]
+            ref[nb] = ref.get(nb, 0.0) + db
+            dc = da
+        ref["L"] = dc
+        for k in names:
+            assert _rel(gr[k][sl[k]], ref[k]) <= 2e-5, (i, pr[i]["D"], k)

@@ -75,3 +75,36 @@ def test_mera_gradients_against_oracle_finite_differences():
         an = float(np.dot(g.cpu().numpy(), delta))
         assert abs(an - fd) <= 1e-6 * max(abs(fd), np.linalg.norm(g.cpu().numpy())), (name, an, fd)
     P.device_status()
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-6), (torch.float32, 2e-5)], ids=["float64", "float32"])
+def test_mera_gradients_of_every_tensor_against_oracle_fd(dtype, tol):
+    """The gradient with respect to t, w and u (split-BF16 x3 and FP64, the
+    environment checkpointed as the bench runs it) against FP64 central
+    finite differences of the oracle's dense energy along several directions
+    per tensor: the gradient's own direction (so the check sees its norm)
+    and three random unit directions.  The error bar is relative to the
+    gradient's norm: a gradient with relative error r misses any unit
+    directional derivative by at most r |g|."""
+    P, networks, spec, S, d = _setup(dtype)
+    t = d["t"].clone().requires_grad_(True)
+    u = d["u"].clone().requires_grad_(True)
+    w = d["w"].clone().requires_grad_(True)
+    E = networks.mera_energy(S, t, w, u, d["h"], d["1"], checkpoint=True)
+    grads = dict(zip(("t", "w", "u"), (g.double().cpu().numpy() for g in torch.autograd.grad(E, [t, w, u]))))
+    torch.cuda.synchronize()
+    host = {n: d[n].double().cpu().numpy() for n in ("t", "w", "u")}
+    rng = np.random.default_rng(17)
+    eps = 1e-5
+    for name, g in grads.items():
+        gn = np.linalg.norm(g)
+        assert gn > 0
+        dirs = [g / gn] + [v / np.linalg.norm(v) for v in (rng.standard_normal(S[name].numel) for _ in range(3))]
+        for k, delta in enumerate(dirs):
+            plus, minus = dict(host), dict(host)
+            plus[name] = host[name] + eps * delta
+            minus[name] = host[name] - eps * delta
+            fd = (_oracle_energy(spec, S, plus) - _oracle_energy(spec, S, minus)) / (2 * eps)
+            an = float(np.dot(g, delta))
+            assert abs(an - fd) <= tol * gn, (name, k, an, fd, gn)
+    P.device_status()

@@ -120,22 +120,27 @@ def test_noalloc_alternating_plans_share_the_array():
 
 
 def test_noalloc_recreated_structures_get_their_own_plans():
-    """Destroying the structures and creating different ones (whose handles
-    may land at the same addresses) must not reuse the old plan."""
+    """Structures passed only to sym_contract_noalloc are destroyed after each
+    call and replaced by structures of other sizes, whose handles the host
+    allocator may place at the freed addresses: every call must run the plan
+    of its own structures (the references come from other, cached handles)."""
     import gc
 
     import paper_1203_2222_gb300 as P
     from paper_1203_2222_gb300 import _lib as L
     rng = np.random.default_rng(6)
     qs = [-1, 0, 1]
-    for trial, (dk, dn) in enumerate([([40, 90, 30], [50, 70, 20]), ([200, 310, 120], [60, 140, 90]),
-                                      ([40, 90, 30], [50, 70, 20])]):
-        SA = P.Structure(P.U1, [(qs, [64, 100, 36], 1), (qs, dk, -1)])
-        SB = P.Structure(P.U1, [(qs, dk, 1), (qs, dn, -1)])
-        a = torch.as_tensor(rng.standard_normal(SA.numel)).cuda()
-        b = torch.as_tensor(rng.standard_normal(SB.numel)).cuda()
-        ref = P.contract(P.SymTensor(SA, a), P.SymTensor(SB, b), [1], [0]).data
+    sizes = [([40, 90, 30], [50, 70, 20]), ([200, 310, 120], [60, 140, 90]), ([40, 90, 30], [50, 70, 20]),
+             ([7, 3, 11], [300, 5, 64])]
+    for trial, (dk, dn) in enumerate(sizes):
+        la = [(qs, [64, 100, 36], 1), (qs, dk, -1)]
+        lb = [(qs, dk, 1), (qs, dn, -1)]
+        RA, RB = P.Structure(P.U1, la), P.Structure(P.U1, lb)
+        a = torch.as_tensor(rng.standard_normal(RA.numel)).cuda()
+        b = torch.as_tensor(rng.standard_normal(RB.numel)).cuda()
+        ref = P.contract(P.SymTensor(RA, a), P.SymTensor(RB, b), [1], [0]).data
         torch.cuda.synchronize()
+        SA, SB = P.Structure(P.U1, la), P.Structure(P.U1, lb)  # seen by the no-allocation call only
         out = _run_noalloc(P, L, SA, SB, [1], [0], P.FP64, a, b, ref.numel())
         assert _rel(out, ref) <= TOL[torch.float64], trial
         del SA, SB
