@@ -27,6 +27,12 @@ non-Abelian Symmetries" (arXiv:1203.2222):
 * ``svd``       Blockwise singular value decomposition (Ch. 5, Eq. svd0 and
                 svd1): block-diagonal form, SVD of every block, truncation,
                 factors recast as tensors.
+* ``eig``       Blockwise symmetric eigendecomposition (Ch. 5, Eq. spectral,
+                by blocks as after Eq. svd1): the same block-diagonal form,
+                numpy's eigh of every block, truncation by |lambda|, factors.
+* ``sample``    Single dense elements of a contraction and of its gradients
+                (Ch. 5, Eq. tensormult at one index) for tensors too large to
+                embed.
 
 Every function works in float64 with no blocking, fusion or reordering beyond
 what the definition states.
