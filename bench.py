@@ -48,7 +48,8 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--workload", choices=["u1_mps_heff", "su2_recouple", "u1_two_site_batch", "u1_mera_grad",
-                                           "z2f_mps_heff", "su2u1_mps_heff", "u1_two_site_svd", "su2_micro"],
+                                           "z2f_mps_heff", "su2u1_mps_heff", "u1_two_site_svd", "u1_two_site_eig",
+                                           "su2_micro"],
                     default="su2_recouple",
                     help="su2_recouple (default: the large-sector SU(2) recoupling contraction at full size), "
                          "the U(1) MPS chain u1_mps_heff, the 512-problem u1_two_site_batch, the MERA gradient "
@@ -73,7 +74,8 @@ def parse():
     ap.add_argument("--tune-space", default=None,
                     help="comma-separated planning parameters the search varies (default: all of autotune.SPACE)")
     args = ap.parse_args()
-    wl = {"u1_two_site_svd": SVDWorkload, "su2_micro": MicroWorkload}.get(args.workload) or WORKLOADS[args.workload]
+    wl = ({"u1_two_site_svd": SVDWorkload, "u1_two_site_eig": EigWorkload, "su2_micro": MicroWorkload}
+          .get(args.workload) or WORKLOADS[args.workload])
     args.steps = wl.default_steps if args.steps is None else args.steps
     args.warmup = wl.default_warmup if args.warmup is None else args.warmup
     args.fp64_steps = wl.default_fp64_steps if args.fp64_steps is None else args.fp64_steps
@@ -900,6 +902,19 @@ class SVDWorkload:
     default_fp64_steps = 0
 
 
+EIG_METRIC = "blockwise FP64 symmetric eigendecomposition + truncation of the two-site density matrix, per second"
+
+
+class EigWorkload:
+    describe = ("u1_two_site_eig: rho = theta theta* over (a, s1) of the two-site tensor of u1_two_site_svd (D = 2048 "
+                "over q = -20..20, Gaussian profile sigma 6; phys {0:1, 1:1}), 41 diagonal blocks up to 272 x 272, "
+                "FP64 blockwise eigendecomposition, truncated to chi = 2048 eigenvalues of largest magnitude, "
+                "eigenvectors U and their transposes")
+    default_steps = 20
+    default_warmup = 3
+    default_fp64_steps = 0
+
+
 def _svd_inputs(P):
     from paper_1203_2222_gb300 import synthetic
     w = synthetic.u1_two_site_svd()
@@ -907,22 +922,44 @@ def _svd_inputs(P):
     return w, S, synthetic.normal(w["seed"], S.numel)
 
 
+def _eig_inputs(P, dev):
+    """rho = theta theta* contracted by the library in FP64 (not timed)."""
+    import torch
+    from paper_1203_2222_gb300 import networks, synthetic
+    w = synthetic.u1_two_site_eig()
+    S = P.Structure(P.U1, w["theta"])
+    Sc = P.Structure(P.U1, networks.reversed_legs(w["theta"]))
+    th = torch.as_tensor(synthetic.normal(w["seed"], S.numel)).to(dev)
+    with torch.no_grad():
+        rho = P.contract(P.SymTensor(S, th), P.SymTensor(Sc, th), *w["pairs"])
+    torch.cuda.synchronize()
+    return w, rho.structure, rho.data.contiguous()
+
+
 def run_svd(args, rank, world):
     """Blockwise FP64 SVD workload: one step = P.svd(theta, 2, chi) -- the
     Jacobi launch, the singular values to the host for the truncation, and
-    the factor launch writing U and S V."""
+    the factor launch writing U and S V.  With u1_two_site_eig, one step =
+    P.eig(rho, 2, chi) on the density matrix, through the same kernels."""
     import torch
     import paper_1203_2222_gb300 as P
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    w, S, vals = _svd_inputs(P)
-    T = P.SymTensor(S, torch.as_tensor(vals).to(dev))
+    is_eig = args.workload == "u1_two_site_eig"
+    if is_eig:
+        w, S, data = _eig_inputs(P, dev)
+        vals = data.cpu()
+        T = P.SymTensor(S, data)
+    else:
+        w, S, vals = _svd_inputs(P)
+        T = P.SymTensor(S, torch.as_tensor(vals).to(dev))
     chi, nrow = w["chi"], w["nrow"]
-    plan = P.svd_plan(S, nrow)
+    plan = P.eig_plan(S, nrow) if is_eig else P.svd_plan(S, nrow)
+    absorb = 0 if is_eig else 2
 
     def step(t):
-        return P.svd(t, nrow, chi=chi, absorb=2)
+        return (P.eig if is_eig else P.svd)(t, nrow, chi=chi, absorb=absorb)
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -958,7 +995,7 @@ def run_svd(args, rank, world):
         e0.record(stream)
         plan.execute(T.data)
         e1.record(stream)
-        plan.factors(2)
+        plan.factors(absorb)
         e2.record(stream)
         torch.cuda.synchronize()
         kms["svd_jacobi"] += e0.elapsed_time(e1)
@@ -974,7 +1011,7 @@ def run_svd(args, rank, world):
     peak32 = 152 * FP32_FLOPS_PER_SM_CLK * mhz * 1e6 / 1e12
     roof = {"bound": "alu", "kernel": "svd_jacobi", "symbol": "svd_jacobi_kernel",
             "achieved": round(f64 / jac_s / 1e12, 5), "peak": round(peak64, 4), "unit": "TFLOP/s",
-            "frac": round(f64 / jac_s / 1e12 / peak64, 4), "traffic": svd_traffic(),
+            "frac": round(f64 / jac_s / 1e12 / peak64, 4), "traffic": None if is_eig else svd_traffic(),
             "algorithmic_per_launch": f64, "fp32_flops_per_launch": f32,
             "avg_launch_us": round(jac_s * 1e6, 2), "launches_timed": args.steps,
             "peak_source": "FP64 ALU: 152 SMs x 4 flops/clk (1.25 TFLOP/s nominal at 2070 MHz) x sampled SM clock",
@@ -985,7 +1022,8 @@ def run_svd(args, rank, world):
                  "frac": round(t_roof / (ms_per_step * 1e-3), 4), "bound": "alu",
                  "fp64_flops": f64, "fp32_flops": f32}
 
-    # end to end: pinned host theta -> device, SVD, U, S and S V back to the host
+    # end to end: pinned host input -> device, the factorization, U, the values
+    # and the second factor back to the host
     host_in = torch.as_tensor(vals).pin_memory()
     dev_in = torch.empty_like(T.data)
     Us, Vs = plan.bond(plan.truncation(plan.execute(T.data).cpu().numpy(), chi))
@@ -1016,21 +1054,25 @@ def run_svd(args, rank, world):
     ms_e2e = sum(a.elapsed_time(b) for a, b in ee) / args.steps
     P.device_status()
 
+    unit = "eig/s" if is_eig else "SVD/s"
     out = {
-        "metric": SVD_METRIC, "value": round(value, 4), "unit": "SVD/s", "n_gpus": world,
+        "metric": EIG_METRIC if is_eig else SVD_METRIC, "value": round(value, 4), "unit": unit, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": bench_config(SVDWorkload.describe),
-        "precision": "FP64 result: FP32 Jacobi sweeps seed FP64 Newton-Schulz + FP64 Jacobi sweeps",
+        "config": bench_config(EigWorkload.describe if is_eig else SVDWorkload.describe),
+        "precision": "FP64 result: FP32 Jacobi sweeps seed FP64 Newton-Schulz + FP64 Jacobi sweeps"
+                     + (" on the block's symmetric part shifted by its Frobenius norm" if is_eig else ""),
         "blocks": plan.nblocks, "singular_values": plan.nsv, "chi": chi,
         "l2": "flushed between timed steps (256 MiB write)", "launch": "eager (host truncation)",
         "parallelism": f"replicas x{world}",
         "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
-        "e2e": {"value": round(1e3 / ms_e2e * world, 4), "unit": "SVD/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": round(1e3 / ms_e2e * world, 4), "unit": unit, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e, 4)},
         "clocks": clk, "gpu_launches": 2 * args.steps,
     }
-    return out
+    vals_gpu = plan.execute(T.data).cpu().numpy()  # every block's values, for the oracle's comparison
+    torch.cuda.synchronize()
+    return out, (plan.labels, plan.m if is_eig else [min(a, b) for a, b in zip(plan.m, plan.n)], vals_gpu)
 
 
 def svd_traffic():
@@ -1055,16 +1097,88 @@ def _oracle_svd_inputs():
     return w, (legs, 0, synthetic.normal(w["seed"], n))
 
 
-def cpu_baseline_svd(steps):
+def _values_error(check, fac):
+    """Largest difference of the GPU's values from the oracle's, block by
+    block (each sorted), relative to the largest magnitude."""
+    labels, sizes, vals = check
+    off, worst, vmax = 0, 0.0, 0.0
+    for x, k in zip(labels, sizes):
+        ref = np.sort(fac[x][1])
+        got = np.sort(vals[off:off + k])
+        off += k
+        worst = max(worst, float(np.max(np.abs(got - ref))))
+        vmax = max(vmax, float(np.max(np.abs(ref))))
+    return {"value": worst / vmax, "sample": "every value of every block, relative to the largest |value|"}
+
+
+def cpu_baseline_svd(steps, check=None):
     w, To = _oracle_svd_inputs()
     n = max(steps, 1) * 3
     t0 = time.perf_counter()
     for _ in range(n):
         fac = _oracle_svd_step(w, To)
     dt = time.perf_counter() - t0
-    return {"value": round(n / dt, 4), "unit": "SVD/s", "cores": cpu_cores(), "kind": "oracle",
+    base = {"value": round(n / dt, 4), "unit": "SVD/s", "cores": cpu_cores(), "kind": "oracle",
             "sample": f"{n} full steps of the same workload (numpy SVD of every block, truncation, factors), "
                       f"{dt:.1f} s"}
+    return base, (_values_error(check, fac) if check else None)
+
+
+def _oracle_eig_inputs():
+    """rho = theta theta* by the oracle's dense contraction of the same theta."""
+    from oracle import contract as oc
+    from oracle import u1
+    from paper_1203_2222_gb300 import synthetic
+    w = synthetic.u1_two_site_eig()
+    legs = [u1.Leg(*l) for l in w["theta"]]
+    legs_c = [u1.Leg(l.labels, l.degens, -l.dir) for l in legs]
+    th = synthetic.normal(w["seed"], u1.layout(legs, 0)[2])
+    lr, qr, rho, _ = oc.contract("u1", (legs, 0, th), (legs_c, 0, th), *w["pairs"])
+    return w, (lr, qr, rho)
+
+
+def _oracle_eig_step(w, To):
+    from oracle import eig as oeig
+    fac, _ = oeig.eig("u1", To, w["nrow"])
+    keep = oeig.truncation({x: f[1] for x, f in fac.items()}, w["chi"])
+    oeig.factors("u1", To, w["nrow"], keep, absorb=0, fac=fac)
+    return fac
+
+
+def cpu_baseline_eig(steps, check=None):
+    w, To = _oracle_eig_inputs()
+    n = max(steps, 1) * 3
+    t0 = time.perf_counter()
+    for _ in range(n):
+        fac = _oracle_eig_step(w, To)
+    dt = time.perf_counter() - t0
+    base = {"value": round(n / dt, 4), "unit": "eig/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{n} full steps of the same workload (numpy eigh of every block, truncation, factors; rho "
+                      f"formed once by the oracle's dense contraction, untimed), {dt:.1f} s"}
+    return base, (_values_error(check, fac) if check else None)
+
+
+def run_reference_eig(args):
+    """Oracle reference arm for u1_two_site_eig: each step is the oracle's blockwise
+    eigendecomposition, truncation and factors of the same density matrix."""
+    w, To = _oracle_eig_inputs()
+    for _ in range(args.warmup):
+        _oracle_eig_step(w, To)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_eig_step(w, To)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    sample = "step = the oracle's blockwise eigendecomposition (numpy eigh, FP64) + truncation + factors of rho"
+    return {
+        "metric": EIG_METRIC, "value": round(value, 4), "unit": "eig/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": bench_config(EigWorkload.describe), "sample": sample,
+        "cpu_baseline": {"value": round(value, 4), "unit": "eig/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "eig/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
 
 
 def run_reference_svd(args):
@@ -1703,6 +1817,8 @@ def main():
                                                       "library's own kernels; the thesis's MATLAB timings have no values"}
         elif args.workload == "u1_two_site_svd":
             out = run_reference_svd(args)
+        elif args.workload == "u1_two_site_eig":
+            out = run_reference_eig(args)
         elif args.workload == "su2_recouple":
             out = run_reference_su2(args)
         elif args.workload == "u1_two_site_batch":
@@ -1723,10 +1839,11 @@ def main():
         torch.distributed.init_process_group("nccl")
     if args.workload == "su2_micro":
         out = run_su2_micro(args, rank, world)
-    elif args.workload == "u1_two_site_svd":
-        out = run_svd(args, rank, world)
+    elif args.workload in ("u1_two_site_svd", "u1_two_site_eig"):
+        out, check = run_svd(args, rank, world)
         if rank == 0 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline_svd(args.cpu_sample_steps)
+            fn = cpu_baseline_eig if args.workload == "u1_two_site_eig" else cpu_baseline_svd
+            out["cpu_baseline"], out["max_rel_err_vs_oracle"] = fn(args.cpu_sample_steps, check)
     else:
         out, flops, check = run_ours(args, rank, world)
         if rank == 0 and not args.no_cpu_baseline:

@@ -427,6 +427,45 @@ int sym_svd_bond(sym_svd plan, const int* keep, sym_tensor* U, sym_tensor* V);
 int sym_svd_factors(sym_svd plan, int absorb, double* U, double* V, double* Sk, void* stream);
 int sym_svd_destroy(sym_svd plan);
 
+/* --------------------------------------- blockwise eigendecomposition (FP64) ---
+ * Spectral decomposition of a symmetric tensor seen as a square matrix
+ * (Ch. 5, "Factorization of a matrix", Eq. spectral; the thesis obtains it,
+ * like the SVD of Eq. svd0 / svd1, by factorizing every diagonal block on its
+ * own).  Rows = legs 0..nrow-1, columns = legs nrow..2 nrow-1, which must be
+ * the row legs reversed (same labels and degeneracies, opposite directions,
+ * same order; SYM_ERR_INCOMPATIBLE_LEGS otherwise) with total label 0
+ * (U(1), fermion parity), or an SU(2) tensor of rank 2 with one incoming and
+ * one outgoing leg.  The block-diagonal form is the SVD's (above); every
+ * block M_x is square and is taken as symmetric: the result is the
+ * eigendecomposition of (M_x + M_x^T) / 2 = Q diag(lambda) Q^T.  The kernel
+ * is the SVD's one-sided Jacobi applied to (M_x + M_x^T) / 2 + sigma I with
+ * sigma its Frobenius norm (a positive semidefinite matrix, whose singular
+ * vectors are its eigenvectors); lambda = singular value - sigma, so the
+ * eigenvalues carry an absolute error of a few ulp of sigma.  SU(2): the
+ * dense matrix is the direct sum of sgn_j M_x / sqrt(2j+1) (x) 1_{2j+1}, with
+ * sgn_j = (-1)^{2j} if the row leg is incoming, else 1; lambda reports the
+ * dense eigenvalues sgn_j lambda_x / sqrt(2j+1) (each standing for 2j+1 of
+ * them) and the factors are U = sqrt(2j+1) Q, V = sgn_j sqrt(2j+1) Q^T, so
+ * that U diag(lambda) V rebuilds T through the library's contraction and U
+ * is an isometry densely whose columns are the dense eigenvectors.
+ *
+ * sym_eig_plan: as sym_svd_plan; nev = sum over blocks of m_x.  The plan is
+ *   a sym_svd handle: sym_svd_blocks, sym_svd_stats, sym_svd_bond,
+ *   sym_svd_factors and sym_svd_destroy apply to it unchanged (U = the
+ *   eigenvectors with an incoming bond leg, V = their transposes with an
+ *   outgoing bond leg; absorb 1 / 2 multiplies lambda into U / V).
+ * sym_eig_execute: lambda (device, nev doubles, caller-owned) receives every
+ *   block's eigenvalues ordered by |lambda| descending (ties: the larger
+ *   lambda first, then the Jacobi column), blocks in ascending x.  Errors and
+ *   asynchrony as sym_svd_execute.
+ * sym_eig_truncation: keep[b] from a host copy of lambda: the rule of
+ *   sym_svd_truncation applied to |lambda| (the singular values of a
+ *   symmetric matrix), so that a truncation to chi keeps the best
+ *   approximation of that rank (Eckart-Young).  Host only.               */
+int sym_eig_plan(sym_tensor T, int nrow, sym_svd* out, int* nblocks, int64_t* nev);
+int sym_eig_execute(sym_svd plan, const double* T, double* lambda, void* stream);
+int sym_eig_truncation(sym_svd plan, const double* lambda, int64_t chi, double cutoff, int* keep);
+
 #ifdef __cplusplus
 }
 #endif

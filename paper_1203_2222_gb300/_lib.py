@@ -104,6 +104,9 @@ _SIGS = {
     "sym_svd_bond": ([_P, _IP, ctypes.POINTER(_P), ctypes.POINTER(_P)], _I),
     "sym_svd_factors": ([_P, _I, _P, _P, _P, _P], _I),
     "sym_svd_destroy": ([_P], _I),
+    "sym_eig_plan": ([_P, _I, ctypes.POINTER(_P), _IP, _LP], _I),
+    "sym_eig_execute": ([_P, _P, _P, _P], _I),
+    "sym_eig_truncation": ([_P, _DP, ctypes.c_int64, ctypes.c_double, _IP], _I),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(lib, _name)

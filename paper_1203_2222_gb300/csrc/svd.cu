@@ -24,6 +24,17 @@
 // svd_factor_kernel: one CTA per block writes the kept singular vectors into
 //   the blocks of U (row legs, bond) and V (bond, column legs), optionally
 //   scaled by S.
+//
+// The same two kernels give the blockwise eigendecomposition of a symmetric
+// tensor seen as a square matrix (Ch. 5, Eq. spectral, by blocks as the
+// thesis prescribes after Eq. svd1; blocks flagged `eig`): the block is
+// replaced by its symmetric part B = (M + M^T)/2 plus sigma I, where sigma is
+// B's Frobenius norm (>= its spectral norm), so that B + sigma I is positive
+// semidefinite.  For such a matrix the one-sided Jacobi result A V = W has
+// |w_j| = lambda_j + sigma and V's columns are the eigenvectors, so the
+// eigenvalues are |w_j| - sigma (absolute error ~ eps sigma, the backward
+// error of any FP64 symmetric eigensolver), ranked by |lambda| descending
+// (ties: the larger lambda, then the column), and U = V, V^T for the factors.
 // The workspace stays L2-resident for the sizes of tensor-network bonds
 // (a 300 x 300 block is 1.4 MB), so the sweeps run from L2, not HBM.
 #include <cooperative_groups.h>
@@ -75,6 +86,8 @@ struct SvdBlock {
   int slot;    // position of the block in ascending x
   int ks;      // first kept singular value of the block in the bond order
   double vscale;  // SU(2): sqrt(2j+1) (the factors carry it, S is divided by it), else 1
+  int eig;        // eigendecomposition of the symmetric part (square block) instead of the SVD
+  double sgn;     // eig, SU(2) with an incoming row leg: (-1)^{2j}, the sign of the dense block; else 1
   int64_t w;   // workspace offset: W (R x C, column-major), V (C x C), norms (C), sorted S (C), then
                // the Jacobi kernel's A (R x C), Newton-Schulz factor (C x C), FP32 W and V
   int64_t s;   // first singular value of the block in S and in the permutation
@@ -375,6 +388,8 @@ __global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThread
   __shared__ unsigned long long nrot[2];
   __shared__ unsigned long long amax;
   __shared__ SweepCtl ctl;
+  __shared__ double wsum[kSvdWarps];
+  __shared__ double fpart;  // eig: this CTA's part of the squared Frobenius norm
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
   const SvdBlock b = blocks[blockIdx.x / kSvdCluster];
@@ -414,6 +429,43 @@ __global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThread
       __stcg(b.trans ? A + c + r * R : A + r + c * R, v);
       mx = max(mx, (unsigned long long)__double_as_longlong(fabs(v)));  // |v| >= 0 orders as its bits
     }
+  }
+  double shift = 0.0;  // eig: sigma
+  if (b.eig) {
+    cluster.sync();  // the whole block is in A
+    // the symmetric part, in place (the thread of (r, c), r < c, writes both
+    // halves), and its squared Frobenius norm
+    double f2 = 0.0;
+    for (int64_t e = ct; e < RC; e += kCT) {
+      const int r = (int)(e % R), c = (int)(e / R);
+      if (r < c) {
+        const int64_t t = c + (int64_t)r * R;
+        const double v = 0.5 * (__ldcg(A + e) + __ldcg(A + t));
+        __stcg(A + e, v);
+        __stcg(A + t, v);
+        f2 = fma(2.0 * v, v, f2);
+      } else if (r == c) {
+        const double v = __ldcg(A + e);
+        f2 = fma(v, v, f2);
+      }
+    }
+    f2 = warp_sum(f2);
+    if (lane == 0) wsum[tid >> 5] = f2;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kSvdWarps; ++w) t += wsum[w];
+      fpart = t;
+    }
+    cluster.sync();  // every CTA's part and the symmetric part are written
+    double tot = 0.0;  // the same sum, in the same order, in every thread
+    for (int r = 0; r < kSvdCluster; ++r) tot += *cluster.map_shared_rank(&fpart, r);
+    shift = sqrt(tot);
+    for (int j = ct; j < C; j += kCT) __stcg(A + j + (int64_t)j * R, __ldcg(A + j + (int64_t)j * R) + shift);
+    cluster.sync();
+    mx = 0;
+    for (int64_t e = ct; e < RC; e += kCT)
+      mx = max(mx, (unsigned long long)__double_as_longlong(fabs(__ldcg(A + e))));
   }
   if (mx) atomicMax(cluster.map_shared_rank(&amax, 0), mx);
   cluster.sync();
@@ -479,12 +531,22 @@ __global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThread
   for (int j = ct; j < C; j += kCT) {
     const double v = __ldcg(nrm + j);
     int rank = 0;
-    for (int i = 0; i < C; ++i) {
-      const double u = __ldcg(nrm + i);
-      rank += (u > v) || (u == v && i < j);
+    if (!b.eig) {
+      for (int i = 0; i < C; ++i) {
+        const double u = __ldcg(nrm + i);
+        rank += (u > v) || (u == v && i < j);
+      }
+      S[b.s + rank] = v / b.vscale;
+      Ss[rank] = v;
+    } else {  // lambda = |w| - sigma, ranked by |lambda| (ties: larger lambda, then column)
+      const double lj = v - shift, aj = fabs(lj);
+      for (int i = 0; i < C; ++i) {
+        const double li = __ldcg(nrm + i) - shift, ai = fabs(li);
+        rank += (ai > aj) || (ai == aj && (li > lj || (li == lj && i < j)));
+      }
+      S[b.s + rank] = b.sgn * lj / b.vscale;
+      Ss[rank] = lj;
     }
-    S[b.s + rank] = v / b.vscale;
-    Ss[rank] = v;
     perm[b.s + rank] = j;
   }
 }
@@ -506,6 +568,29 @@ __global__ void __launch_bounds__(kSvdThreads)
   // SU(2): the factors are vscale times the orthonormal ones and the values
   // are divided by it; absorbing S gives the orthonormal factor times sigma
   const double vs = b.vscale;
+  if (b.eig) {  // M = Q diag(lambda) Q^T: U = vs Q, V = sgn vs Q^T, values sgn lambda / vs
+    const double sg = b.sgn;
+    if (Sk)
+      for (int j = tid; j < k; j += kSvdThreads) Sk[b.ks + j] = sg * Ss[j] / vs;
+    for (int q = 0; q < b.nu; ++q) {
+      const SvdPiece pc = pieces[b.u0 + q];
+      const int64_t n = (int64_t)pc.rows * k;
+      for (int64_t e = tid; e < n; e += kSvdThreads) {
+        const int i = (int)(e / k), j = (int)(e - (int64_t)i * k);
+        U[pc.off + e] = V[pc.r0 + i + (int64_t)pm[j] * C] * (absorb == 1 ? sg * Ss[j] : vs);
+      }
+    }
+    for (int q = 0; q < b.nv; ++q) {
+      const SvdPiece pc = pieces[b.v0 + q];
+      const int64_t n = (int64_t)k * pc.cols;
+      for (int64_t e = tid; e < n; e += kSvdThreads) {
+        const int j = (int)(e / pc.cols);
+        const int64_t c = pc.c0 + (e - (int64_t)j * pc.cols);
+        Vt[pc.off + e] = V[c + (int64_t)pm[j] * C] * (absorb == 2 ? Ss[j] : sg * vs);
+      }
+    }
+    return;
+  }
   if (Sk)
     for (int j = tid; j < k; j += kSvdThreads) Sk[b.ks + j] = Ss[j] / vs;
   for (int q = 0; q < b.nu; ++q) {
@@ -590,6 +675,7 @@ TupleMap enumerate_tuples(int group, const std::vector<Leg>& legs, int l0, int l
 struct SvdPlan {
   Tensor T;
   int nrow = 0;
+  bool eig = false;  // eigendecomposition plan (sym_eig_plan)
   std::vector<int> xs;            // block labels, ascending
   std::vector<SvdBlock> blocks;   // ascending x
   std::vector<SvdPiece> tpieces;  // grouped by block
@@ -640,14 +726,25 @@ struct SvdPlan {
   }
 };
 
-std::unique_ptr<SvdPlan> plan_svd(const Tensor& T, int nrow) {
-  if (T.group == SYM_SU2U1) fail(SYM_ERR_UNSUPPORTED, "blockwise SVD of SU(2) x U(1) tensors is not built");
+std::unique_ptr<SvdPlan> plan_svd(const Tensor& T, int nrow, bool eig) {
+  const char* what = eig ? "blockwise eigendecomposition" : "blockwise SVD";
+  if (T.group == SYM_SU2U1) fail(SYM_ERR_UNSUPPORTED, std::string(what) + " of SU(2) x U(1) tensors is not built");
   if (T.group == SYM_SU2 && T.rank != 2)
-    fail(SYM_ERR_UNSUPPORTED, "blockwise SVD of SU(2) tensors is built for rank 2 (the block-diagonal form)");
+    fail(SYM_ERR_UNSUPPORTED, std::string(what) + " of SU(2) tensors is built for rank 2 (the block-diagonal form)");
   if (T.rank < 2 || nrow < 1 || nrow >= T.rank) fail(SYM_ERR_ARG, "SVD needs rank >= 2 and 1 <= nrow < rank");
+  if (eig) {  // a square matrix: the column legs are the row legs reversed, total label 0
+    if (T.rank != 2 * nrow) fail(SYM_ERR_ARG, "eigendecomposition needs rank = 2 nrow");
+    for (int l = 0; l < nrow; ++l)
+      if (!T.legs[l].same_content(T.legs[nrow + l]) || T.legs[l].dir != -T.legs[nrow + l].dir)
+        fail(SYM_ERR_INCOMPATIBLE_LEGS,
+             "eigendecomposition: column leg " + std::to_string(nrow + l) + " must be row leg " + std::to_string(l) +
+                 " reversed (same labels and degeneracies, opposite direction)");
+    if (T.group != SYM_SU2 && T.total != 0) fail(SYM_ERR_ARG, "eigendecomposition needs total label 0");
+  }
   auto P = std::make_unique<SvdPlan>();
   P->T = T;
   P->nrow = nrow;
+  P->eig = eig;
   std::unordered_map<int, int64_t> mext, next;
   P->rows = enumerate_tuples(T.group, T.legs, 0, nrow, false, T.total, mext);
   P->cols = enumerate_tuples(T.group, T.legs, nrow, T.rank, true, T.total, next);
@@ -667,6 +764,10 @@ std::unique_ptr<SvdPlan> plan_svd(const Tensor& T, int nrow) {
     b.C = (int)std::min(m, n);
     b.slot = (int)P->blocks.size();
     b.vscale = T.group == SYM_SU2 ? std::sqrt((double)x + 1.0) : 1.0;
+    b.eig = eig ? 1 : 0;
+    // SU(2) with an incoming row leg: the dense block is (-1)^{2j} M_x / sqrt(2j+1) (x) 1
+    b.sgn = (eig && T.group == SYM_SU2 && T.legs[0].dir == -1 && (x & 1)) ? -1.0 : 1.0;
+    if (eig && m != n) fail(SYM_ERR_ARG, "internal: eigendecomposition block is not square");
     b.w = P->work_elems;
     b.s = P->nsv;
     // W, V, norms, sorted S, A, the Newton-Schulz factor (doubles), W and V in FP32
@@ -737,9 +838,20 @@ extern "C" {
 int sym_svd_plan(sym_tensor T, int nrow, sym_svd* out, int* nblocks, int64_t* nsv) {
   return sym::guard([&] {
     need(T != nullptr && out != nullptr, "T or out is NULL");
-    auto P = sym::plan_svd(T->t, nrow);
+    auto P = sym::plan_svd(T->t, nrow, false);
     if (nblocks) *nblocks = (int)P->blocks.size();
     if (nsv) *nsv = P->nsv;
+    *out = new sym_svd_s{std::move(P)};
+    return SYM_OK;
+  });
+}
+
+int sym_eig_plan(sym_tensor T, int nrow, sym_svd* out, int* nblocks, int64_t* nev) {
+  return sym::guard([&] {
+    need(T != nullptr && out != nullptr, "T or out is NULL");
+    auto P = sym::plan_svd(T->t, nrow, true);
+    if (nblocks) *nblocks = (int)P->blocks.size();
+    if (nev) *nev = P->nsv;
     *out = new sym_svd_s{std::move(P)};
     return SYM_OK;
   });
@@ -758,15 +870,31 @@ int sym_svd_blocks(sym_svd plan, int* x, int* m, int* n) {
   });
 }
 
+namespace {
+void launch_jacobi(sym::SvdPlan& P, const double* T, double* S, void* stream) {
+  if (P.dry) sym::fail(SYM_ERR_UNSUPPORTED, "plan was built with SYM_PLAN_DRYRUN=1 and cannot run");
+  sym::svd_jacobi_kernel<<<(unsigned)P.blocks.size() * sym::kSvdCluster, sym::kSvdThreads, 0,
+                           static_cast<cudaStream_t>(stream)>>>(
+      P.d_blocks, P.d_pieces, T, P.work, S, P.perm, P.sweeps, P.rotations, sym::device_error_word());
+  check_launch("svd_jacobi_kernel");
+}
+}  // namespace
+
+int sym_eig_execute(sym_svd plan, const double* T, double* lambda, void* stream) {
+  return sym::guard([&] {
+    need(plan != nullptr && T != nullptr && lambda != nullptr, "plan, T or lambda is NULL");
+    need(plan->p->eig, "not an eigendecomposition plan (sym_eig_plan)");
+    launch_jacobi(*plan->p, T, lambda, stream);
+    return SYM_OK;
+  });
+}
+
 int sym_svd_execute(sym_svd plan, const double* T, double* S, void* stream) {
   return sym::guard([&] {
     need(plan != nullptr && T != nullptr && S != nullptr, "plan, T or S is NULL");
     auto& P = *plan->p;
-    if (P.dry) sym::fail(SYM_ERR_UNSUPPORTED, "plan was built with SYM_PLAN_DRYRUN=1 and cannot run");
-    sym::svd_jacobi_kernel<<<(unsigned)P.blocks.size() * sym::kSvdCluster, sym::kSvdThreads, 0,
-                             static_cast<cudaStream_t>(stream)>>>(
-        P.d_blocks, P.d_pieces, T, P.work, S, P.perm, P.sweeps, P.rotations, sym::device_error_word());
-    check_launch("svd_jacobi_kernel");
+    need(!P.eig, "an eigendecomposition plan runs with sym_eig_execute");
+    launch_jacobi(P, T, S, stream);
     return SYM_OK;
   });
 }
@@ -875,38 +1003,56 @@ int sym_svd_factors(sym_svd plan, int absorb, double* U, double* V, double* Sk, 
   });
 }
 
+namespace {
+// keep[b] from the values' magnitudes (SVD: the singular values; eig: |lambda|)
+void truncate_values(const sym::SvdPlan& P, const double* S, int64_t chi, double cutoff, int* keep) {
+  need(cutoff >= 0.0, "cutoff must be >= 0");
+  struct Val {
+    double v;
+    int b, i;
+  };
+  std::vector<Val> vals;
+  vals.reserve(P.nsv);
+  for (size_t b = 0; b < P.blocks.size(); ++b)
+    for (int i = 0; i < P.blocks[b].C; ++i) {
+      const double s = S[P.blocks[b].s + i];
+      const double v = P.eig ? std::fabs(s) : s;
+      if (!(v >= 0.0) || !std::isfinite(v))
+        sym::fail(SYM_ERR_NUMERIC, P.eig ? "eigenvalues must be finite" : "singular values must be finite and >= 0");
+      vals.push_back(Val{v, (int)b, i});
+    }
+  // descending; ties: smaller x first, then the block's own order
+  std::sort(vals.begin(), vals.end(), [](const Val& a, const Val& c) {
+    if (a.v != c.v) return a.v > c.v;
+    return a.b != c.b ? a.b < c.b : a.i < c.i;
+  });
+  const double vmax = vals.empty() ? 0.0 : vals[0].v;
+  for (size_t b = 0; b < P.blocks.size(); ++b) keep[b] = 0;
+  int64_t n = 0;
+  for (const Val& x : vals) {
+    const int w = P.T.group == SYM_SU2 ? P.xs[x.b] + 1 : 1;  // dense values one value stands for
+    if (chi >= 0 && n + w > chi) break;
+    if (cutoff > 0.0 && x.v <= cutoff * vmax) break;
+    ++keep[x.b];
+    n += w;
+  }
+}
+}  // namespace
+
 int sym_svd_truncation(sym_svd plan, const double* S, int64_t chi, double cutoff, int* keep) {
   return sym::guard([&] {
     need(plan != nullptr && S != nullptr && keep != nullptr, "plan, S or keep is NULL");
-    need(cutoff >= 0.0, "cutoff must be >= 0");
-    const auto& P = *plan->p;
-    struct Val {
-      double v;
-      int b, i;
-    };
-    std::vector<Val> vals;
-    vals.reserve(P.nsv);
-    for (size_t b = 0; b < P.blocks.size(); ++b)
-      for (int i = 0; i < P.blocks[b].C; ++i) {
-        const double v = S[P.blocks[b].s + i];
-        if (!(v >= 0.0)) sym::fail(SYM_ERR_NUMERIC, "singular values must be finite and >= 0");
-        vals.push_back(Val{v, (int)b, i});
-      }
-    // descending; ties: smaller x first, then the block's own order
-    std::sort(vals.begin(), vals.end(), [](const Val& a, const Val& c) {
-      if (a.v != c.v) return a.v > c.v;
-      return a.b != c.b ? a.b < c.b : a.i < c.i;
-    });
-    const double vmax = vals.empty() ? 0.0 : vals[0].v;
-    for (size_t b = 0; b < P.blocks.size(); ++b) keep[b] = 0;
-    int64_t n = 0;
-    for (const Val& x : vals) {
-      const int w = P.T.group == SYM_SU2 ? P.xs[x.b] + 1 : 1;  // dense values one value stands for
-      if (chi >= 0 && n + w > chi) break;
-      if (cutoff > 0.0 && x.v <= cutoff * vmax) break;
-      ++keep[x.b];
-      n += w;
-    }
+    need(!plan->p->eig, "an eigendecomposition plan truncates with sym_eig_truncation");
+    truncate_values(*plan->p, S, chi, cutoff, keep);
+    return SYM_OK;
+  });
+}
+
+int sym_eig_truncation(sym_svd plan, const double* lambda, int64_t chi, double cutoff, int* keep) {
+  return sym::guard([&] {
+    need(plan != nullptr && lambda != nullptr && keep != nullptr, "plan, lambda or keep is NULL");
+    need(plan->p->eig, "not an eigendecomposition plan (sym_eig_plan)");
+    truncate_values(*plan->p, lambda, chi, cutoff, keep);
     return SYM_OK;
   });
 }

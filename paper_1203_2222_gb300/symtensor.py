@@ -445,9 +445,11 @@ class SVDPlan:
     """Blockwise SVD of tensors with structure ``S``, rows = legs 0..nrow-1
     (include/symtensor.h, sym_svd_*; Ch. 5, Eq. svd0 and svd1)."""
 
+    _plan_fn = "sym_svd_plan"
+
     def __init__(self, S, nrow):
         h, nb, ns = ctypes.c_void_p(), ctypes.c_int(), ctypes.c_int64()
-        L.check(L.lib.sym_svd_plan(S._h, int(nrow), _byref(h), _byref(nb), _byref(ns)))
+        L.check(getattr(L.lib, self._plan_fn)(S._h, int(nrow), _byref(h), _byref(nb), _byref(ns)))
         self._h = h
         self.structure, self.nrow = S, int(nrow)
         self.nblocks, self.nsv = nb.value, ns.value
@@ -526,7 +528,67 @@ class SVDPlan:
             self._h = None
 
 
+class EigPlan(SVDPlan):
+    """Blockwise symmetric eigendecomposition of tensors with structure ``S``
+    seen as a square matrix, rows = legs 0..nrow-1, columns = the row legs
+    reversed (include/symtensor.h, sym_eig_*; Ch. 5, Eq. spectral by blocks).
+    ``execute`` returns the eigenvalues (|lambda| descending per block);
+    ``bond`` / ``factors`` give U (eigenvectors) and V (their transposes)."""
+
+    _plan_fn = "sym_eig_plan"
+
+    def execute(self, data):
+        """lambda (device, float64, nev): every block's eigenvalues."""
+        if data.dtype != torch.float64 or not data.is_cuda or data.numel() != self.structure.numel:
+            raise TypeError("eigendecomposition input must be the tensor's float64 CUDA blocks")
+        lam = torch.empty(self.nsv, dtype=torch.float64, device=data.device)
+        L.check(L.lib.sym_eig_execute(self._h, _ptr(data.contiguous()), _ptr(lam), _stream()))
+        return lam
+
+    def truncation(self, lam_host, chi=None, cutoff=0.0):
+        """keep per block (ascending x) for a host copy of execute's lambda (by |lambda|)."""
+        lam_host = np.ascontiguousarray(lam_host, dtype=np.float64)
+        keep = (ctypes.c_int * self.nblocks)()
+        L.check(L.lib.sym_eig_truncation(self._h, lam_host.ctypes.data_as(L._DP), -1 if chi is None else int(chi),
+                                         float(cutoff), keep))
+        return list(keep)
+
+
 _SVD_PLANS = {}
+
+
+def eig_plan(S, nrow):
+    """Eigendecomposition plan (cached) of structure S with rows = legs 0..nrow-1."""
+    key = ("eig", id(S), int(nrow))
+    hit = _SVD_PLANS.get(key)
+    if hit is None or hit[1] is not S:
+        hit = (EigPlan(S, nrow), S)
+        _SVD_PLANS[key] = hit
+    return hit[0]
+
+
+def eig(T, nrow, chi=None, cutoff=0.0, absorb=0):
+    """Blockwise eigendecomposition T = U diag(lambda) V of a symmetric float64
+    tensor (rows = legs 0..nrow-1, columns = the row legs reversed; blocks
+    taken as symmetric), truncated to the ``chi`` eigenvalues of largest
+    magnitude above ``cutoff`` times the largest (include/symtensor.h,
+    sym_eig_truncation).
+
+    Returns (U, lambda, V): U has the row legs and an incoming bond leg (its
+    columns are the eigenvectors), V an outgoing bond leg and the column
+    legs, lambda the kept eigenvalues in bond order; absorb = 1 / 2 multiplies
+    lambda into U / V.  Without chi or cutoff nothing is truncated and no host
+    synchronisation happens.
+    """
+    plan = eig_plan(T.structure, nrow)
+    lam = plan.execute(T.data)
+    if chi is None and not cutoff:
+        keep = plan.full
+    else:
+        keep = plan.truncation(lam.cpu().numpy(), chi, cutoff)
+    Us, Vs = plan.bond(keep)
+    U, V, Lk = plan.factors(absorb)
+    return SymTensor(Us, U), Lk, SymTensor(Vs, V)
 
 
 def svd_plan(S, nrow):

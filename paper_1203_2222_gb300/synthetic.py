@@ -29,6 +29,8 @@ Workload shapes (all seeds are ``1234 + index``):
 * ``u1_two_site_svd``  the two-site tensor theta[a, s1, s2, b] of that chain
   (D = 2048, total charge 0) as the matrix (a, s1) x (s2, b), truncated to
   chi = 2048 singular values.
+* ``u1_two_site_eig``  the reduced density matrix theta theta* of that
+  tensor over (a, s1), eigendecomposed and truncated to chi = 2048.
 * ``su2u1_mps_heff``  the MPS chain with SU(2) x U(1) legs (labels (q, 2j)):
   a Hubbard-like site {(0,0), (1,1), (2,0)}, MPO {(-1,1):2, (0,0):3, (1,1):2},
   about 1024 bond multiplets over q = -8..8, 2j = 0..4 (2j = q mod 2).
@@ -121,6 +123,17 @@ def u1_two_site_svd(D=2048, qmax=20, sigma=6.0, seed=1240):
     phys_in = ([0, 1], [1, 1], -1)
     theta = [(qs, d, -1), phys_in, phys_in, (qs, d, 1)]
     return {"group": "u1", "theta": theta, "nrow": 2, "chi": D, "seed": seed, "D": D}
+
+
+def u1_two_site_eig(D=2048, qmax=20, sigma=6.0, seed=1240):
+    """Legs of the two-site tensor theta of ``u1_two_site_svd``; the workload
+    is the reduced density matrix rho[(a, s1), (a', s1')] = sum over (s2, b)
+    of theta theta* (legs a, s1 incoming, a', s1' outgoing, total 0), whose
+    eigendecomposition truncated to chi = D eigenvalues is the density-matrix
+    form of the same truncation step."""
+    w = u1_two_site_svd(D, qmax, sigma, seed)
+    w["pairs"] = ([2, 3], [2, 3])
+    return w
 
 
 def su2u1_mps_heff(D=1024, qmax=8, sigma=3.0, seed=1241):
