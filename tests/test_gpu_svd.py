@@ -88,10 +88,10 @@ def _check(group, legs, total, nrow, values, chi=None, cutoff=0.0):
         live = np.where(Sd > 1e-10 * Smax)[0]
         if absorb != 1:
             Ul = Um[:, live]
-            assert np.max(np.abs(Ul.T @ Ul - np.eye(len(live)))) <= 4 * TOL
+            assert np.max(np.abs(Ul.T @ Ul - np.eye(len(live)))) <= TOL
         if absorb != 2:
             Vl = Vm[live, :]
-            assert np.max(np.abs(Vl @ Vl.T - np.eye(len(live)))) <= 4 * TOL
+            assert np.max(np.abs(Vl @ Vl.T - np.eye(len(live)))) <= TOL
         # U and V carry nothing outside their blocks (their layouts are the library's own)
         for X in (U, V):
             legsX = [m.Leg(*l) for l in X.structure.legs]
