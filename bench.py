@@ -527,7 +527,7 @@ def kernel_source_sha(kern):
     return h.hexdigest()[:16]
 
 
-def roofline(prof, clk, sustained=False, workload="u1_mps_heff"):
+def roofline(prof, clk, sustained=False, workload="u1_mps_heff", full_size=True):
     """Roofline of the kernel with the largest summed device time.
 
     box kernels, the direct kernel and the rows / thin GEMMs: HBM-bound,
@@ -559,7 +559,7 @@ def roofline(prof, clk, sustained=False, workload="u1_mps_heff"):
         bound, unit, per = "alu", "TFLOP/s", d["flops"] / n
         achieved, peak = per / sec / 1e12, 152 * 128 * 2 * mhz * 1e6 / 1e12
         src = "152 SMs x 128 FP32 FMA/clk x 2 flops x sampled SM clock"
-    t = TRAFFIC.get(workload, {}).get(dom)
+    t = TRAFFIC.get(workload, {}).get(dom) if full_size else None  # the figures are the full-size launches
     traffic = None
     if t and t["sha"] == kernel_source_sha(dom):
         traffic = t["bytes_per_launch"] if "bytes_per_launch" in t else round(t["ratio"] * d["bytes"] / n)
@@ -842,7 +842,9 @@ def run_ours(args, rank, world):
     # the whole step: T_roof = max(useful flops / tensor peak, algorithmic
     # bytes / HBM bandwidth) against the measured step time
     long_step = ms_per_step > 20.0  # seconds-long timed region: the power cap applies
-    roof = roofline(prof, clk, sustained=long_step, workload=args.workload)
+    full_size = not ((args.workload == "su2_recouple" and args.su2_dmax != 32) or
+                     (args.workload == "u1_two_site_batch" and args.batch_n != 512))
+    roof = roofline(prof, clk, sustained=long_step, workload=args.workload, full_size=full_size)
     peaks, peak_src = load_peaks()
     p_tensor = (peaks["bf16_tflops_sustained"] if long_step else peaks["bf16_tflops"]) / 3.0
     t_flop = flops / (p_tensor * 1e12)
