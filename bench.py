@@ -642,7 +642,9 @@ def run_ours(args, rank, world):
     plans = P.cached_plans()
     # The library records a CUDA event pair around each of its own launches
     # (on the launch stream).  Captured into the graph, every replay re-records
-    # them with the kernels' own device times.
+    # them with the kernels' own device times.  While profiling, a phase's
+    # GEMM kinds run one after another instead of concurrently, so that every
+    # pair brackets one kernel alone (the timed graph keeps them concurrent).
     if use_graph:
         try:
             s = torch.cuda.Stream()

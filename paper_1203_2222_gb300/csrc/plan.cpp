@@ -2206,7 +2206,9 @@ int run_gemm(Plan& p, int ph0, int ph1, void* stream, int phase) {
       rs[n++] = r;
     }
   }
-  if (n <= 1 || !p.concurrent) {
+  // while profiling, the kinds run one after another: each launch's event
+  // pair then brackets that kernel alone (as a serialised profiler sees it)
+  if (n <= 1 || !p.concurrent || p.profiling) {
     for (int i = 0; i < n; ++i)
       if (int rc = run_gemm_kind(p, kinds[i], rs[i], stream, phase)) return rc;
     return SYM_OK;

@@ -12,6 +12,8 @@ phase of every problem runs in one launch per kernel.  Checks:
 import numpy as np
 import pytest
 
+import graph_replay
+
 torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
@@ -136,7 +138,8 @@ def test_full_batch_matches_single_plans_and_oracle():
 
 def test_full_batch_bf16x3_chain_and_gradients_against_oracle():
     """The bench's batched step at full size (512 problems, split-BF16 x3):
-    the whole four-contraction chain forward and the gradients of <G, Y>
+    the whole four-contraction chain forward and the gradients of <G, Y>,
+    replayed from a CUDA graph as the bench times it,
     with respect to L, theta, W (both uses) and R, for the three smallest
     problems, a stratified sample across the bond dimension (the problems
     at the 20/40/60/80% quantiles of D) and the largest, against the FP64
@@ -146,11 +149,15 @@ def test_full_batch_bf16x3_chain_and_gradients_against_oracle():
     from paper_1203_2222_gb300 import synthetic
     spec = synthetic.u1_two_site_batch()
     S, plans, offs, data = _batch(P, spec, torch.float32)
-    Y = _chain(P, plans, data)
-    G = torch.as_tensor(synthetic.normal(4243, Y.numel())).to(torch.float32).cuda()
+    G = torch.as_tensor(synthetic.normal(4243, plans[3].off_c[-1])).to(torch.float32).cuda()
     names = ("L", "theta", "W", "R")
-    grads = torch.autograd.grad(Y, [data[n] for n in names], grad_outputs=G)
-    torch.cuda.synchronize()
+
+    def step():
+        Y = _chain(P, plans, data)
+        return (Y,) + tuple(torch.autograd.grad(Y, [data[n] for n in names], grad_outputs=G))
+
+    # the bench's launch configuration: the autograd step replayed from a CUDA graph
+    (Y, *grads), graph = graph_replay.replay(step)
     P.device_status()
     yh, gh = Y.detach().double().cpu().numpy(), G.double().cpu().numpy()
     gr = {n: g.double().cpu().numpy() for n, g in zip(names, grads)}

@@ -6,11 +6,14 @@ inputs are the bench's (same seeds, same cotangent G); the split-BF16 case
 feeds the oracle the float32 values the GPU holds.  Bond D = 2048 over
 charges -20..20 (U(1)) and D = 2048 as {0: 1024, 1: 1024} (fermion parity).
 
-Tolerance (relative Frobenius error): 1e-12 on the FP64 path, 2e-5 on the
-split-BF16 x3 path.
+The split-BF16 step runs as the bench times it (the autograd step captured
+in a CUDA graph and replayed).  Tolerance (relative Frobenius error): 1e-12
+on the FP64 path, 2e-5 on the split-BF16 x3 path.
 """
 import numpy as np
 import pytest
+
+import graph_replay
 
 torch = pytest.importorskip("torch")
 
@@ -63,11 +66,23 @@ def test_mps_step_full_size_against_oracle(group, dtype):
     data = {n: torch.as_tensor(synthetic.normal(spec["seeds"][n], S[n].numel)).to(dtype).cuda().requires_grad_(True)
             for n in S}
     T = {n: P.SymTensor(S[n], data[n]) for n in S}
-    T1 = P.contract(T["L"], T["A"], [2], [0])
-    T2 = P.contract(T1, T["W"], [1, 2], [0, 2])
-    Y = P.contract(T2, T["R"], [1, 3], [2, 1])
-    G = torch.as_tensor(synthetic.normal(4242, Y.structure.numel)).to(dtype).cuda()
-    grads = torch.autograd.grad(Y.data, [data[n] for n in ("L", "A", "W", "R")], grad_outputs=G)
+
+    def step():
+        T1 = P.contract(T["L"], T["A"], [2], [0])
+        T2 = P.contract(T1, T["W"], [1, 2], [0, 2])
+        Y = P.contract(T2, T["R"], [1, 3], [2, 1])
+        gs = torch.autograd.grad(Y.data, [data[n] for n in ("L", "A", "W", "R")], grad_outputs=G)
+        return (Y,) + tuple(gs)
+
+    prec = P.FP64 if dtype == torch.float64 else P.BF16X3
+    t1 = P.contract_plan(S["L"], S["A"], [2], [0], prec).out
+    t2 = P.contract_plan(t1, S["W"], [1, 2], [0, 2], prec).out
+    ny = P.contract_plan(t2, S["R"], [1, 3], [2, 1], prec).out.numel
+    G = torch.as_tensor(synthetic.normal(4242, ny)).to(dtype).cuda()
+    if dtype == torch.float32:  # the bench's launch configuration: the step replayed from a CUDA graph
+        (Y, *grads), graph = graph_replay.replay(step)
+    else:
+        Y, *grads = step()
     torch.cuda.synchronize()
     P.device_status()
     host = {n: data[n].detach().double().cpu().numpy() for n in S}

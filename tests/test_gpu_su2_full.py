@@ -9,7 +9,9 @@ entries, 1.3e13 useful flops per forward) the dense oracle cannot embed the
 tensors, so the test draws dense elements of C = contract(A, B) and of the
 gradients dA, dB of <G, C>, lets the oracle compute each one from slices of
 the embedded inputs (oracle.sample), and embeds the GPU's result blocks at
-the same indices.  Elements are drawn with J_z conserved (so none is a
+the same indices.  The full-size split-BF16 step runs as the bench times
+it: the autograd step captured in a CUDA graph and replayed.  Elements are
+drawn with J_z conserved (so none is a
 structural zero), at least 16 in every matrix-form sector of C (coupled spin
 2e = 0..16) plus the largest block of each result, and at least 256 per
 result.  The oracle's elements run in a pool of spawned host processes that
@@ -24,6 +26,7 @@ import tempfile
 import numpy as np
 import pytest
 
+import graph_replay
 import oracle_pool
 
 torch = pytest.importorskip("torch")
@@ -57,7 +60,7 @@ def _tasks(c, dmax, per_e, per_tensor, seed):
     return tasks
 
 
-def _check(dmax, dtype, per_e, per_tensor, tol):
+def _check(dmax, dtype, per_e, per_tensor, tol, graph=False):
     import paper_1203_2222_gb300 as P
     from paper_1203_2222_gb300 import synthetic
     c = synthetic.su2_recouple(dmax=dmax, jmax2=8)
@@ -67,16 +70,27 @@ def _check(dmax, dtype, per_e, per_tensor, tol):
     gen.manual_seed(1236)
     a = torch.randn(SA.numel, device="cuda", dtype=dtype, generator=gen).requires_grad_(True)
     b = torch.randn(SB.numel, device="cuda", dtype=dtype, generator=gen).requires_grad_(True)
-    C = P.contract(P.SymTensor(SA, a), P.SymTensor(SB, b), c["pairsA"], c["pairsB"])
-    G = torch.randn(C.structure.numel, device="cuda", dtype=dtype, generator=gen)
-    da, db = torch.autograd.grad(C.data, [a, b], grad_outputs=G)
+    prec = P.FP64 if dtype == torch.float64 else P.BF16X3
+    nc = P.contract_plan(SA, SB, c["pairsA"], c["pairsB"], prec).out.numel
+    G = torch.randn(nc, device="cuda", dtype=dtype, generator=gen)
+
+    def step():
+        C = P.contract(P.SymTensor(SA, a), P.SymTensor(SB, b), c["pairsA"], c["pairsB"])
+        return (C.data,) + tuple(torch.autograd.grad(C.data, [a, b], grad_outputs=G))
+
+    if graph:  # the bench's launch configuration: the autograd step replayed from a CUDA graph
+        (cdata, da, db), g = graph_replay.replay(step)
+    else:
+        cdata, da, db = step()
     torch.cuda.synchronize()
     P.device_status()
     d = tempfile.mkdtemp(prefix="su2full_")
     try:
-        for n, t in (("A", a), ("B", b), ("G", G), ("C", C.data), ("dA", da), ("dB", db)):
+        for n, t in (("A", a), ("B", b), ("G", G), ("C", cdata), ("dA", da), ("dB", db)):
             np.save(os.path.join(d, n + ".npy"), t.detach().cpu().numpy())
-        del a, b, G, C, da, db
+        del a, b, G, cdata, da, db
+        if graph:
+            del g
         torch.cuda.empty_cache()
         res = oracle_pool.su2_elements(d, c, tasks)
     finally:
@@ -91,7 +105,7 @@ def _check(dmax, dtype, per_e, per_tensor, tol):
 
 
 def test_su2_recouple_full_size_bf16x3_forward_and_backward_against_oracle():
-    _check(32, torch.float32, per_e=16, per_tensor=256, tol=2e-5)
+    _check(32, torch.float32, per_e=16, per_tensor=256, tol=2e-5, graph=True)
 
 
 def test_su2_recouple_half_size_fp64_forward_and_backward_against_oracle():
