@@ -498,8 +498,11 @@ TRAFFIC = {
     "u1_two_site_batch": {  # profiles/direct_u1_two_site_batch.md (128 of the 512 problems)
         "direct": {"ratio": 0.97, "sha": "32a083d9660812bd"},
     },
-    "u1_two_site_svd": {  # profiles/svd_u1_two_site_svd.md (full size, mean of 10 launches)
-        "svd_jacobi": {"bytes_per_launch": 8650342, "sha": "dac386f91d8a6964"},
+    "u1_two_site_svd": {  # profiles/svd_u1_two_site_svd.md (full size, mean of 11 launches)
+        "svd_jacobi": {"bytes_per_launch": 8764230, "sha": "80768ec65c30971e"},
+    },
+    "u1_two_site_eig": {  # profiles/eig_u1_two_site_eig.md (full size, mean of 11 launches)
+        "svd_jacobi": {"bytes_per_launch": 8724596, "sha": "80768ec65c30971e"},
     },
     "z2f_mps_heff": {  # profiles/traffic_z2f_mps_heff_and_mera.md (full size, mean of 48 step launches)
         "gemm_tc": {"bytes_per_launch": 196125834, "sha": "17524e1d9ff325bc"},
@@ -911,7 +914,7 @@ EIG_METRIC = "blockwise FP64 symmetric eigendecomposition + truncation of the tw
 
 class EigWorkload:
     describe = ("u1_two_site_eig: rho = theta theta* over (a, s1) of the two-site tensor of u1_two_site_svd (D = 2048 "
-                "over q = -20..20, Gaussian profile sigma 6; phys {0:1, 1:1}), 41 diagonal blocks up to 272 x 272, "
+                "over q = -20..20, Gaussian profile sigma 6; phys {0:1, 1:1}), 42 diagonal blocks up to 272 x 272, "
                 "FP64 blockwise eigendecomposition, truncated to chi = 2048 eigenvalues of largest magnitude, "
                 "eigenvectors U and their transposes")
     default_steps = 20
@@ -1015,7 +1018,7 @@ def run_svd(args, rank, world):
     peak32 = 152 * FP32_FLOPS_PER_SM_CLK * mhz * 1e6 / 1e12
     roof = {"bound": "alu", "kernel": "svd_jacobi", "symbol": "svd_jacobi_kernel",
             "achieved": round(f64 / jac_s / 1e12, 5), "peak": round(peak64, 4), "unit": "TFLOP/s",
-            "frac": round(f64 / jac_s / 1e12 / peak64, 4), "traffic": None if is_eig else svd_traffic(),
+            "frac": round(f64 / jac_s / 1e12 / peak64, 4), "traffic": svd_traffic(args.workload),
             "algorithmic_per_launch": f64, "fp32_flops_per_launch": f32,
             "avg_launch_us": round(jac_s * 1e6, 2), "launches_timed": args.steps,
             "peak_source": "FP64 ALU: 152 SMs x 4 flops/clk (1.25 TFLOP/s nominal at 2070 MHz) x sampled SM clock",
@@ -1079,8 +1082,8 @@ def run_svd(args, rank, world):
     return out, (plan.labels, plan.m if is_eig else [min(a, b) for a, b in zip(plan.m, plan.n)], vals_gpu)
 
 
-def svd_traffic():
-    t = TRAFFIC["u1_two_site_svd"]["svd_jacobi"]
+def svd_traffic(workload="u1_two_site_svd"):
+    t = TRAFFIC[workload]["svd_jacobi"]
     return t["bytes_per_launch"] if t["sha"] == kernel_source_sha("svd_jacobi") else None
 
 
