@@ -41,3 +41,53 @@ def test_bad_legs_are_rejected():
         Structure(SU2, [([0, 1], [1, 1], 2)])         # direction +-1
     with pytest.raises(SymError):
         Structure(SU2, [([1], [1], 1)] * 3, tree=[(0, 2), (3, 1)])  # not planar
+
+
+def test_raw_abi_error_codes():
+    """Error paths of the C ABI called directly (independent binding; the
+    planner runs host-only with SYM_PLAN_DRYRUN=1, so no GPU is needed)."""
+    import ctypes
+
+    from tests import abi_raw as R
+    os.environ["SYM_PLAN_DRYRUN"] = "1"
+    try:
+        lib = R.load()
+        q = [-1, 0, 1]
+        rc, a = R.tensor(lib, R.SYM_U1, [(q, [2, 3, 1], 1), (q, [1, 2, 2], -1)])
+        assert rc == R.SYM_OK and R.numel(lib, a) == 2 * 1 + 3 * 2 + 1 * 2
+        rc, b = R.tensor(lib, R.SYM_U1, [(q, [1, 2, 3], 1), (q, [1, 1, 1], -1)])  # leg 0 differs from a's leg 1
+        assert rc == R.SYM_OK
+        c, p = ctypes.c_void_p(), ctypes.c_void_p()
+        # contracted legs must carry the same labels and degeneracies with opposite directions
+        rc = lib.sym_contract_plan(a, b, 1, R.ints([1]), R.ints([0]), None, R.SYM_PREC_FP64, ctypes.byref(c),
+                                   ctypes.byref(p))
+        assert rc == R.SYM_ERR_INCOMPATIBLE_LEGS and b"same labels" in lib.sym_last_error()
+        rc, d = R.tensor(lib, R.SYM_U1, [(q, [2, 3, 1], 1), (q, [2, 3, 1], -1)])  # d's leg 1 pairs with its leg 0
+        assert rc == R.SYM_OK
+        # bad precision, repeated pair, NULL outputs
+        assert lib.sym_contract_plan(d, d, 1, R.ints([1]), R.ints([0]), None, 9, ctypes.byref(c),
+                                     ctypes.byref(p)) == R.SYM_ERR_ARG
+        assert lib.sym_contract_plan(d, d, 2, R.ints([1, 1]), R.ints([0, 0]), None, R.SYM_PREC_FP64,
+                                     ctypes.byref(c), ctypes.byref(p)) == R.SYM_ERR_ARG
+        assert lib.sym_contract_plan(d, d, 1, R.ints([1]), R.ints([0]), None, R.SYM_PREC_FP64, None,
+                                     None) == R.SYM_ERR_ARG
+        # a valid plan built host-only refuses to run
+        assert lib.sym_contract_plan(d, d, 1, R.ints([1]), R.ints([0]), None, R.SYM_PREC_FP64, ctypes.byref(c),
+                                     ctypes.byref(p)) == R.SYM_OK
+        assert lib.sym_contract(p, None, None, None, None) == R.SYM_ERR_UNSUPPORTED
+        assert lib.sym_plan_destroy(p) == R.SYM_OK and lib.sym_tensor_destroy(c) == R.SYM_OK
+        # the eigendecomposition needs the column legs to be the row legs reversed
+        e, nb, nev = ctypes.c_void_p(), ctypes.c_int(), ctypes.c_int64()
+        assert lib.sym_eig_plan(b, 1, ctypes.byref(e), ctypes.byref(nb), ctypes.byref(nev)) == \
+            R.SYM_ERR_INCOMPATIBLE_LEGS
+        rc, s = R.tensor(lib, R.SYM_U1, [(q, [2, 3, 1], -1), (q, [2, 3, 1], 1)])
+        assert lib.sym_eig_plan(s, 1, ctypes.byref(e), ctypes.byref(nb), ctypes.byref(nev)) == R.SYM_OK
+        assert nb.value == 3 and nev.value == 6
+        assert lib.sym_svd_destroy(e) == R.SYM_OK
+        # SU(2): a tree that is not planar is refused
+        rc, _ = R.tensor(lib, R.SYM_SU2, [([1], [1], 1)] * 3, tree=[(0, 2), (3, 1)])
+        assert rc == R.SYM_ERR_ARG
+        for h in (a, b, d, s):
+            assert lib.sym_tensor_destroy(h) == R.SYM_OK
+    finally:
+        del os.environ["SYM_PLAN_DRYRUN"]
