@@ -128,3 +128,78 @@ def test_raw_eigendecomposition():
         off += k
     assert lib.sym_svd_destroy(plan) == R.SYM_OK
     assert lib.sym_tensor_destroy(T) == R.SYM_OK
+
+
+@pytest.mark.parametrize("prec,dtype", [(R.SYM_PREC_FP64, torch.float64), (R.SYM_PREC_BF16X3, torch.float32)],
+                         ids=["fp64", "bf16x3"])
+def test_raw_sectors_without_contributions_are_written_as_zeros(prec, dtype):
+    """C's sector (a = 1, b = 1) is allowed by charge conservation but no
+    block of A has a = 1, so nothing contributes to it: the library must
+    write it as zeros (the outputs start as NaN here), and likewise the
+    gradient blocks of A and B that receive nothing."""
+    from oracle import contract as oc
+    from oracle import u1
+    lib = R.load()
+    la = [([0, 1], [2, 3], 1), ([0], [2], -1)]   # A: only the block a = 0
+    lb = [([0], [2], 1), ([0, 1], [3, 2], -1)]   # B: only the block b = 0
+    rc, A = R.tensor(lib, R.SYM_U1, la)
+    assert rc == R.SYM_OK
+    rc, B = R.tensor(lib, R.SYM_U1, lb)
+    assert rc == R.SYM_OK
+    C, plan = ctypes.c_void_p(), ctypes.c_void_p()
+    assert lib.sym_contract_plan(A, B, 1, R.ints([1]), R.ints([0]), None, prec, ctypes.byref(C),
+                                 ctypes.byref(plan)) == R.SYM_OK
+    nc = R.numel(lib, C)
+    assert nc == 2 * 3 + 3 * 2  # sectors (0, 0) and (1, 1)
+    rng = np.random.default_rng(24)
+    a = torch.as_tensor(rng.standard_normal(R.numel(lib, A))).to(dtype).cuda()
+    b = torch.as_tensor(rng.standard_normal(R.numel(lib, B))).to(dtype).cuda()
+    c = torch.full((nc,), float("nan"), dtype=dtype, device="cuda")
+    assert lib.sym_contract(plan, _ptr(a), _ptr(b), _ptr(c), _stream()) == R.SYM_OK
+    dc = torch.as_tensor(rng.standard_normal(nc)).to(dtype).cuda()
+    da = torch.full_like(a, float("nan"))
+    db = torch.full_like(b, float("nan"))
+    assert lib.sym_contract_backward(plan, _ptr(a), _ptr(b), _ptr(dc), _ptr(da), _ptr(db), _stream()) == R.SYM_OK
+    torch.cuda.synchronize()
+    assert lib.sym_device_status() == R.SYM_OK
+    for t in (c, da, db):
+        assert not torch.isnan(t).any()
+    assert torch.all(c[6:] == 0)
+    oA = ([u1.Leg(*l) for l in la], 0, a.double().cpu().numpy())
+    oB = ([u1.Leg(*l) for l in lb], 0, b.double().cpu().numpy())
+    _, _, c_ref, _ = oc.contract("u1", oA, oB, [1], [0])
+    dA_ref, dB_ref, _ = oc.contract_grad("u1", oA, oB, [1], [0], dc.double().cpu().numpy())
+    tol = 1e-12 if dtype == torch.float64 else 2e-5
+    assert _rel(c.double().cpu().numpy(), c_ref) <= tol
+    assert _rel(da.double().cpu().numpy(), dA_ref) <= tol
+    assert _rel(db.double().cpu().numpy(), dB_ref) <= tol
+    assert lib.sym_plan_destroy(plan) == R.SYM_OK
+    for h in (A, B, C):
+        assert lib.sym_tensor_destroy(h) == R.SYM_OK
+
+
+def test_raw_empty_tensors():
+    """A tensor whose total charge no sector reaches has no blocks; its
+    contraction plans, runs (nothing to launch) and leaves the buffers alone."""
+    lib = R.load()
+    rc, A = R.tensor(lib, R.SYM_U1, [([0], [3], 1), ([0], [2], -1)], total=1)  # a - k = 1: impossible
+    assert rc == R.SYM_OK and R.numel(lib, A) == 0
+    rc, B = R.tensor(lib, R.SYM_U1, [([0], [2], 1), ([0], [4], -1)])
+    assert rc == R.SYM_OK and R.numel(lib, B) == 8
+    C, plan = ctypes.c_void_p(), ctypes.c_void_p()
+    assert lib.sym_contract_plan(A, B, 1, R.ints([1]), R.ints([0]), None, R.SYM_PREC_BF16X3, ctypes.byref(C),
+                                 ctypes.byref(plan)) == R.SYM_OK, lib.sym_last_error()
+    assert R.numel(lib, C) == 0
+    a = torch.full((1,), 7.0, device="cuda")
+    b = torch.ones(8, device="cuda")
+    c = torch.full((1,), 7.0, device="cuda")
+    db = torch.full((8,), 7.0, device="cuda")
+    assert lib.sym_contract(plan, _ptr(a), _ptr(b), _ptr(c), _stream()) == R.SYM_OK
+    assert lib.sym_contract_backward(plan, _ptr(a), _ptr(b), _ptr(c), _ptr(a), _ptr(db), _stream()) == R.SYM_OK
+    torch.cuda.synchronize()
+    assert lib.sym_device_status() == R.SYM_OK
+    assert float(c[0]) == 7.0 and float(a[0]) == 7.0
+    assert torch.all(db == 0)  # B's gradient is a real tensor: nothing reaches it, so it is zero
+    assert lib.sym_plan_destroy(plan) == R.SYM_OK
+    for h in (A, B, C):
+        assert lib.sym_tensor_destroy(h) == R.SYM_OK

@@ -373,3 +373,13 @@ def test_su2u1_permute_fuse_split(dtype):
             torch.cuda.synchronize()
             err = rel(back.data.double().cpu().numpy(), T.data.double().cpu().numpy())
             assert err <= (1e-13 if dtype == torch.float64 else 1e-6), err
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
+def test_su2_high_spins(dtype):
+    # legs of spin 7 to 8 (2j = 14..16, the largest the workloads use, node
+    # spins up to 2j = 32 inside A's comb tree), recoupled into the matrix tree
+    hi = [14, 15, 16]
+    la = [(hi, [1, 2, 1], 1), (hi, [2, 1, 1], 1), (hi, [1, 1, 2], 1), ([0, 1, 2], [1, 1, 1], 1)]
+    lb = [(hi, [2, 1, 1], -1), ([0, 1, 2], [1, 1, 1], -1), ([13, 14, 15, 16], [1, 1, 2, 1], 1)]
+    _contract_case("su2", la, lb, [1, 3], [0, 1], dtype)
