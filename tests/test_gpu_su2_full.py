@@ -84,7 +84,11 @@ def _check(dmax, dtype, per_e, per_tensor, tol, graph=False):
         cdata, da, db = step()
     torch.cuda.synchronize()
     P.device_status()
-    d = tempfile.mkdtemp(prefix="su2full_")
+    # the six tensors (about 18 GB at full size) go to a memory-backed
+    # directory when it has room, else to the default temporary directory
+    need = sum(t.numel() * t.element_size() for t in (a, b, G, cdata, da, db))
+    where = "/dev/shm" if os.path.isdir("/dev/shm") and shutil.disk_usage("/dev/shm").free > 2 * need else None
+    d = tempfile.mkdtemp(prefix="su2full_", dir=where)
     try:
         for n, t in (("A", a), ("B", b), ("G", G), ("C", cdata), ("dA", da), ("dB", db)):
             np.save(os.path.join(d, n + ".npy"), t.detach().cpu().numpy())
