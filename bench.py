@@ -85,10 +85,14 @@ def parse():
 
 # ----------------------------------------------------------------- helpers ---
 
+L2_POLICY = "flushed between timed steps (256 MiB write)"
+
+
 def bench_config(describe):
-    """The `config` of both arms' JSON lines: the workload alone, so that the
-    two lines name the same configuration."""
-    return {"workload": describe}
+    """The `config` of both arms' JSON lines (the same dict, so that the two
+    lines name the same configuration): the workload and the L2 policy of the
+    GPU arm's timed steps."""
+    return {"workload": describe, "l2": L2_POLICY}
 
 
 def max_over_ranks(x, world, device=None):
@@ -899,7 +903,7 @@ def run_ours(args, rank, world):
                                   args.batch_n != 512 else "")),
         "precision": "split-BF16 x3 on tcgen05, FP32 accumulate, fp32 blocks",
         "useful_gflop_per_step": round(flops / 1e9, 4),
-        "l2": "flushed between timed steps (256 MiB write)", "launch": launch_mode,
+        "launch": launch_mode,
         "parallelism": f"replicas x{world}",
         "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
         "fp64_gpu": ({"value": round(value64, 5), "unit": "TFLOP/s", "ms_per_step": round(ms64, 4)}
@@ -1093,7 +1097,7 @@ def run_svd(args, rank, world):
         "precision": "FP64 result: FP32 Jacobi sweeps seed FP64 Newton-Schulz + FP64 Jacobi sweeps"
                      + (" on the block's symmetric part shifted by its Frobenius norm" if is_eig else ""),
         "blocks": plan.nblocks, "singular_values": plan.nsv, "chi": chi,
-        "l2": "flushed between timed steps (256 MiB write)", "launch": "eager (host truncation)",
+        "launch": "eager (host truncation)",
         "parallelism": f"replicas x{world}",
         "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
         "e2e": {"value": round(1e3 / ms_e2e * world, 4), "unit": unit, "h2d_bytes_per_step": h2d,
@@ -1370,7 +1374,7 @@ def run_su2_micro(args, rank, world):
         "metric": MICRO_METRIC, "value": last["ratio"], "unit": "x", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": last["su2_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64 (permute, fuse, svd), bf16x3-f32acc (matmul)", "data": "synthetic",
-        "config": bench_config(MicroWorkload.describe), "l2": "flushed before every timed call (256 MiB write)",
+        "config": dict(bench_config(MicroWorkload.describe), l2="flushed before every timed call (256 MiB write)"),
         "timing": f"median of {K} calls after {W} warm-up calls, CUDA events",
         "series": series, "spin_networks": sn, "gpu_launches": launches[0],
     }
