@@ -139,6 +139,12 @@ int sym_tensor_sectors(sym_tensor t, int* labels, int64_t* offsets);
  *   (la, lb) are ordered with la slowest and (t_a, t_b) row-major).  For
  *   SU(2) the input is first taken to the tree where the two legs share a
  *   node (NEWTREE), the output tree is the left comb.
+ * sym_fuse_n_plan: legs first..first+nlegs-1 (nlegs >= 2, equal directions)
+ *   become one leg, fused pairwise from the left: ((l_f, l_f+1), l_f+2), ...
+ *   (the fused leg's labels and order are those of nlegs-1 sym_fuse_plan
+ *   steps).  For nlegs > 2 the plan runs the pairwise steps in order through
+ *   two device scratch buffers it allocates and owns (the largest
+ *   intermediate); its launches are not recorded by sym_plan_profile.
  * sym_split_plan: SPLIT of Ch. 6 -- leg `leg` is split into the two legs
  *   parts[0], parts[1], which must fuse exactly to it; SU(2) output tree is
  *   the left comb.
@@ -147,6 +153,8 @@ int sym_permute_plan(sym_tensor in, const int* perm, const int* tree_out,
                      int precision, sym_tensor* out, sym_plan* plan);
 int sym_fuse_plan(sym_tensor in, int first, int precision, sym_tensor* out,
                   sym_plan* plan);
+int sym_fuse_n_plan(sym_tensor in, int first, int nlegs, int precision,
+                    sym_tensor* out, sym_plan* plan);
 int sym_split_plan(sym_tensor in, int leg, const sym_leg* parts, int precision,
                    sym_tensor* out, sym_plan* plan);
 int sym_plan_execute(sym_plan plan, const void* in, void* out, void* stream);

@@ -75,6 +75,7 @@ _SIGS = {
     "sym_tensor_sectors": ([_P, _IP, _LP], _I),
     "sym_permute_plan": ([_P, _IP, _IP, _I, ctypes.POINTER(_P), ctypes.POINTER(_P)], _I),
     "sym_fuse_plan": ([_P, _I, _I, ctypes.POINTER(_P), ctypes.POINTER(_P)], _I),
+    "sym_fuse_n_plan": ([_P, _I, _I, _I, ctypes.POINTER(_P), ctypes.POINTER(_P)], _I),
     "sym_split_plan": ([_P, _I, ctypes.POINTER(sym_leg), _I, ctypes.POINTER(_P), ctypes.POINTER(_P)], _I),
     "sym_plan_execute": ([_P, _P, _P, _P], _I),
     "sym_contract_plan": ([_P, _P, _I, _IP, _IP, _IP, _I, ctypes.POINTER(_P), ctypes.POINTER(_P)], _I),

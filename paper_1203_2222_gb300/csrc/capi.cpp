@@ -94,6 +94,20 @@ sym::Tensor sym::contraction_result(const Tensor& a, const Tensor& b, const std:
   return make_tensor(a.group, legs, a.group == SYM_Z2F ? (a.total ^ b.total) : a.total + b.total, tr);
 }
 
+namespace {
+// FUSE of legs first and first+1 of T: the result structure and the plan
+std::pair<sym::Tensor, std::unique_ptr<sym::Plan>> fuse_pair(const sym::Tensor& T, int first, int precision) {
+  need(first >= 0 && first + 1 < T.rank, "fuse: first must be in 0..rank-2");
+  sym::Leg d = sym::fused_leg(T.legs[first], T.legs[first + 1], T.group);
+  std::vector<sym::Leg> legs(T.legs.begin(), T.legs.begin() + first);
+  legs.push_back(d);
+  legs.insert(legs.end(), T.legs.begin() + first + 2, T.legs.end());
+  sym::Tensor O = sym::make_tensor(T.group, legs, T.total, sym::Tree::comb((int)legs.size()));
+  auto P = sym::plan_transform(T, O, {}, precision, 1, first);
+  return {std::move(O), std::move(P)};
+}
+}  // namespace
+
 extern "C" {
 
 const char* sym_last_error(void) { return sym::last_error().c_str(); }
@@ -194,15 +208,30 @@ int sym_fuse_plan(sym_tensor in, int first, int precision, sym_tensor* out, sym_
   return guard([&] {
     need(in && out && plan, "NULL argument");
     check_precision(precision);
+    auto r = fuse_pair(in->t, first, precision);
+    *out = wrap(std::move(r.first));
+    *plan = new sym_plan_s{std::move(r.second)};
+    return SYM_OK;
+  });
+}
+
+int sym_fuse_n_plan(sym_tensor in, int first, int nlegs, int precision, sym_tensor* out, sym_plan* plan) {
+  return guard([&] {
+    need(in && out && plan, "NULL argument");
+    check_precision(precision);
     const sym::Tensor& T = in->t;
-    need(first >= 0 && first + 1 < T.rank, "fuse: first must be in 0..rank-2");
-    sym::Leg d = sym::fused_leg(T.legs[first], T.legs[first + 1], T.group);
-    std::vector<sym::Leg> legs(T.legs.begin(), T.legs.begin() + first);
-    legs.push_back(d);
-    legs.insert(legs.end(), T.legs.begin() + first + 2, T.legs.end());
-    sym::Tensor O = sym::make_tensor(T.group, legs, T.total, sym::Tree::comb((int)legs.size()));
-    auto P = sym::plan_transform(T, O, {}, precision, 1, first);
-    *out = wrap(std::move(O));
+    need(nlegs >= 2 && first >= 0 && first + nlegs <= T.rank, "fuse: legs first..first+nlegs-1 must exist, nlegs >= 2");
+    // ((l_first, l_first+1), l_first+2) ...: nlegs - 1 pairwise fuses at `first`
+    std::vector<std::unique_ptr<sym::Plan>> steps;
+    sym::Tensor cur = T;
+    for (int i = 0; i + 1 < nlegs; ++i) {
+      auto r = fuse_pair(cur, first, precision);
+      cur = std::move(r.first);
+      steps.push_back(std::move(r.second));
+    }
+    std::unique_ptr<sym::Plan> P =
+        steps.size() == 1 ? std::move(steps.front()) : sym::chain_transforms(std::move(steps), precision);
+    *out = wrap(std::move(cur));
     *plan = new sym_plan_s{std::move(P)};
     return SYM_OK;
   });

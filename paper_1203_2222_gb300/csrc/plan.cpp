@@ -2266,9 +2266,38 @@ BoxPtrs gather_ptrs(Plan& p, const void* A, const void* B, const void* dC) {
 
 }  // namespace
 
+std::unique_ptr<Plan> chain_transforms(std::vector<std::unique_ptr<Plan>> steps, int precision) {
+  if (steps.empty()) fail(SYM_ERR_ARG, "internal: empty transform chain");
+  auto P = std::make_unique<Plan>();
+  P->kind = Plan::TRANSFORM;
+  P->precision = precision;
+  P->numel_a = steps.front()->numel_a;
+  P->numel_c = steps.back()->numel_c;
+  P->dry = steps.front()->dry;
+  int64_t mid = 1;  // the largest intermediate
+  for (size_t i = 0; i + 1 < steps.size(); ++i) mid = std::max(mid, steps[i]->numel_c);
+  P->chain = std::move(steps);
+  if (!P->dry) {
+    const size_t es = precision == SYM_PREC_FP64 ? sizeof(double) : sizeof(float);
+    P->chain_buf[0] = P->arena.alloc((size_t)mid * es, false);
+    P->chain_buf[1] = P->arena.alloc((size_t)mid * es, false);
+  }
+  return P;
+}
+
 int exec_transform(Plan& p, const void* in, void* out, void* stream) {
   if (p.dry) fail(SYM_ERR_UNSUPPORTED, "plan was built with SYM_PLAN_DRYRUN=1 and cannot run");
   p.last_launches = 0;
+  if (!p.chain.empty()) {  // each step's output feeds the next, through the scratch pair
+    const void* src = in;
+    for (size_t i = 0; i < p.chain.size(); ++i) {
+      void* dst = i + 1 == p.chain.size() ? out : p.chain_buf[i & 1];
+      if (int rc = exec_transform(*p.chain[i], src, dst, stream)) return rc;
+      p.last_launches += p.chain[i]->last_launches;
+      src = dst;
+    }
+    return SYM_OK;
+  }
   BoxPtrs ptrs{};
   ptrs.src[0] = in;
   ptrs.dst[DST_OUT] = out;

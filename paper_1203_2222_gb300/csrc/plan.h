@@ -50,6 +50,10 @@ struct Plan {
   std::vector<BoxItem> items;
   std::vector<Term> terms;
   Range xform;                        // TRANSFORM: in -> out
+  // TRANSFORM made of several transforms run in order (a fuse of more than
+  // two legs: pairwise fuses), through two plan-owned scratch buffers
+  std::vector<std::unique_ptr<Plan>> chain;
+  void* chain_buf[2] = {nullptr, nullptr};
   Range fwd_gather, fwd_scatter;      // CONTRACT forward
   Range bwd_gather_a, bwd_gather_b;   // backward gathers needed for dA / dB
   Range bwd_scatter_a, bwd_scatter_b;
@@ -134,6 +138,9 @@ int tune_epoch();
 
 std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const std::vector<int>& perm,
                                      int precision, int mode_fuse_split, int leg);
+// a transform made of the given ones run in order (each one's output the
+// next one's input); owns two scratch buffers for the intermediates
+std::unique_ptr<Plan> chain_transforms(std::vector<std::unique_ptr<Plan>> steps, int precision);
 // device = false builds and validates the work lists on the host only (no
 // device allocation); such a plan runs only through sym_contract_noalloc.
 std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std::vector<int>& pairsA,

@@ -313,10 +313,14 @@ def permute_plan(S, perm, tree=None, precision=BF16X3):
         S._h, L.int_array(perm), L.tree_array(tree), int(precision), _byref(o), _byref(p))), S.total)[1])
 
 
-def fuse_plan(S, first, precision=BF16X3):
-    key = ("f", id(S), int(first), precision, S)
-    return _transform_plan(key, lambda o, p: (L.check(L.lib.sym_fuse_plan(
-        S._h, int(first), int(precision), _byref(o), _byref(p))), S.total)[1])
+def fuse_plan(S, first, precision=BF16X3, nlegs=2):
+    """Plan (cached) of fusing legs first..first+nlegs-1 of structure S."""
+    key = ("f", id(S), int(first), int(nlegs), precision, S)
+    if nlegs == 2:
+        return _transform_plan(key, lambda o, p: (L.check(L.lib.sym_fuse_plan(
+            S._h, int(first), int(precision), _byref(o), _byref(p))), S.total)[1])
+    return _transform_plan(key, lambda o, p: (L.check(L.lib.sym_fuse_n_plan(
+        S._h, int(first), int(nlegs), int(precision), _byref(o), _byref(p))), S.total)[1])
 
 
 def split_plan(S, leg, parts, precision=BF16X3):
@@ -403,9 +407,9 @@ def permute(T, perm, tree=None):
     return _run_transform(permute_plan(T.structure, perm, tree, _precision(T.data.dtype)), T)
 
 
-def fuse(T, first):
-    """FUSE legs (first, first+1) into one leg."""
-    return _run_transform(fuse_plan(T.structure, first, _precision(T.data.dtype)), T)
+def fuse(T, first, nlegs=2):
+    """FUSE legs first..first+nlegs-1 into one leg (pairwise from the left)."""
+    return _run_transform(fuse_plan(T.structure, first, _precision(T.data.dtype), nlegs), T)
 
 
 def split(T, leg, parts):

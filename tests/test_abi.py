@@ -91,3 +91,23 @@ def test_raw_abi_error_codes():
             assert lib.sym_tensor_destroy(h) == R.SYM_OK
     finally:
         del os.environ["SYM_PLAN_DRYRUN"]
+
+
+def test_fuse_of_several_legs_is_the_iterated_pairwise_fuse():
+    """The structure sym_fuse_n_plan returns equals that of n-1 pairwise
+    fuses, and a chained plan runs all of them (host-only plans)."""
+    import subprocess
+    import sys
+    code = (
+        "import paper_1203_2222_gb300 as P\n"
+        "for g, legs in ((P.U1, [([-1, 0, 1], [2, 1, 2], 1), ([0, 1], [1, 2], 1), ([-1, 0], [2, 1], 1), "
+        "([0], [3], -1)]), (P.SU2, [([0, 1, 2], [2, 1, 1], 1), ([0, 1], [1, 2], 1), ([1, 2], [2, 1], 1), "
+        "([0, 1, 2, 3], [1, 2, 1, 1], 1)])):\n"
+        "    S = P.Structure(g, legs)\n"
+        "    a = P.fuse_plan(S, 0, P.FP64, nlegs=3).out\n"
+        "    b = P.fuse_plan(P.fuse_plan(S, 0, P.FP64).out, 0, P.FP64).out\n"
+        "    assert a.legs == b.legs and a.numel == b.numel, (a.legs, b.legs)\n"
+        "print('ok')\n")
+    env = dict(os.environ, SYM_PLAN_DRYRUN="1", PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stderr

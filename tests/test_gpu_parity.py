@@ -383,3 +383,35 @@ def test_su2_high_spins(dtype):
     la = [(hi, [1, 2, 1], 1), (hi, [2, 1, 1], 1), (hi, [1, 1, 2], 1), ([0, 1, 2], [1, 1, 1], 1)]
     lb = [(hi, [2, 1, 1], -1), ([0, 1, 2], [1, 1, 1], -1), ([13, 14, 15, 16], [1, 1, 2, 1], 1)]
     _contract_case("su2", la, lb, [1, 3], [0, 1], dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
+def test_fuse_several_legs(dtype):
+    # sym_fuse_n_plan: legs first..first+n-1 fused pairwise from the left in
+    # one plan (its steps chained through plan-owned scratch), against the
+    # oracle's pairwise fuse applied n-1 times
+    P = _lib()
+    cases = [
+        ("u1", [([-1, 0, 1], [2, 1, 2], 1), ([0, 1], [1, 2], 1), ([-1, 0], [2, 1], 1), ([-2, 0, 2], [1, 2, 1], -1)],
+         0, 3),
+        ("u1", [([0, 1], [2, 1], -1), ([-1, 0, 1], [1, 2, 1], 1), ([0, 1], [1, 2], 1), ([0, 1], [2, 1], 1),
+                ([-1, 0, 1, 2, 3], [1, 1, 2, 1, 1], -1)], 1, 3),
+        ("su2", [([0, 1, 2], [2, 1, 1], 1), ([0, 1], [1, 2], 1), ([1, 2], [2, 1], 1), ([0, 1, 2, 3], [1, 2, 1, 1], 1)],
+         0, 3),
+        ("su2", [([0, 1, 2], [1, 1, 1], -1), ([0, 1, 2], [2, 1, 1], -1), ([0, 1], [1, 1], -1), ([1, 2], [1, 1], -1),
+                 ([0, 1, 2, 3, 4], [1, 1, 2, 1, 1], 1)], 0, 4),
+    ]
+    for group, legs, first, n in cases:
+        S, T, t = _make(group, legs, 31, dtype)
+        out = P.fuse(T, first, nlegs=n)
+        torch.cuda.synchronize()
+        oT = ([_oleg(group, l) for l in legs], _otree(group, S, legs), t)
+        for _ in range(n - 1):
+            lo, to, data, resid = oc.fuse(group, oT, first)
+            assert resid < 1e-10
+            oT = (lo, to, data)
+        assert [tuple(l.labels) for l in oT[0]] == [tuple(l[0]) for l in out.structure.legs]
+        assert [tuple(l.degens) for l in oT[0]] == [tuple(l[1]) for l in out.structure.legs]
+        err = rel(out.data.double().cpu().numpy(), oT[2])
+        assert err <= (TOL[dtype] if dtype == torch.float64 else 1e-6), (group, first, n, err)
+    P.device_status()
