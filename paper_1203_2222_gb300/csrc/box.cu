@@ -29,6 +29,15 @@
 namespace sym {
 namespace {
 
+#ifndef RC_VALS
+#define RC_VALS 24
+#endif
+#ifndef RC_HMAX
+#define RC_HMAX 8
+#endif
+#ifndef RC_MINB
+#define RC_MINB 4
+#endif
 constexpr int kThreads = 128;
 constexpr int kWarps = kThreads / 32;
 constexpr int kBatch = kBoxChunk / 32;  // elements per lane of a linear item
@@ -275,10 +284,43 @@ __device__ __forceinline__ void tile_item(const BoxItem& it, const TS* __restric
 // n_s source values are loaded once and the n_d destinations receive their
 // coefficient-weighted sums (Ch. 6, Eq. permsu2, all output labels of one
 // set of leg spins at once).  The coefficient matrix is staged in the warp's
-// shared-memory tile with rows padded to NS (a bound on n_s, 8 or 16) and
-// read back as 16-byte vectors, once per batch of H positions per lane; the
-// source and destination offsets are staged there too and read once per
-// column per batch.  ND is a bound on the box's dims (unused dims are unit).
+// shared-memory tile with rows padded to NS (a bound on n_s: 2, 4, 8 or 16)
+// and read back as 8- or 16-byte vectors; the (offset, ld) pairs of sources
+// and destinations are staged beside it.  A lane keeps H positions x NS
+// values in flight (H * NS = 32 registers of FP32), so items with few
+// sources load more positions per round trip; with NS <= 4 the source
+// offsets live in registers and every position's loads are issued as soon as
+// its index is split.  An item may hold more than 32 positions per lane (the
+// planner sizes it by n_s); the lane walks them H at a time.  ND is a bound
+// on the box's dims (unused dims are unit).
+template <int NS, typename TD>
+__device__ __forceinline__ void load_row(const TD* r, TD (&w)[NS]) {
+  if constexpr (sizeof(TD) == 4 && NS % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < NS; q += 4) {
+      const float4 x = *reinterpret_cast<const float4*>(r + q);
+      w[q] = x.x;
+      w[q + 1] = x.y;
+      w[q + 2] = x.z;
+      w[q + 3] = x.w;
+    }
+  } else if constexpr (sizeof(TD) == 4) {
+#pragma unroll
+    for (int q = 0; q < NS; q += 2) {
+      const float2 x = *reinterpret_cast<const float2*>(r + q);
+      w[q] = x.x;
+      w[q + 1] = x.y;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < NS; q += 2) {
+      const double2 x = *reinterpret_cast<const double2*>(r + q);
+      w[q] = x.x;
+      w[q + 1] = x.y;
+    }
+  }
+}
+
 template <int ND, int NS, typename TS, typename TD>
 __device__ __forceinline__ void recouple_item(const BoxItem& it, const Term* __restrict__ terms,
                                               const TS* __restrict__ src, void* dstv, int64_t lo_off, bool split,
@@ -286,85 +328,93 @@ __device__ __forceinline__ void recouple_item(const BoxItem& it, const Term* __r
   const int ns = it.nterm, nd = it.p0;
   const Term* T = terms + it.term0;
   TD* cf = &tile[0][0];  // [nd][NS], zero past n_s
-  int64_t* soff = reinterpret_cast<int64_t*>(cf + kMaxRecouple * 16);
-  int64_t* sld = soff + kMaxRecouple;
-  int64_t* doff = sld + kMaxRecouple;
-  int64_t* dld = doff + kMaxRecouple;
+  longlong2* sp = reinterpret_cast<longlong2*>(cf + kMaxRecouple * 16);  // (off, ld) of each source
+  longlong2* dp = sp + kMaxRecouple;                                       // (off, ld) of each destination
   for (int i = lane; i < nd * NS; i += 32) {
     const int d = i / NS, q = i - d * NS;
     cf[i] = q < ns ? coef<TD>(T[ns + nd + d * ns + q].coef, T[ns + nd + d * ns + q].coef_f) : TD(0);
   }
-  if (lane < ns) {
-    soff[lane] = T[lane].off;
-    sld[lane] = T[lane].ld;
-  }
-  if (lane < nd) {
-    doff[lane] = T[ns + lane].off;
-    dld[lane] = T[ns + lane].ld;
-  }
+  if (lane < ns) sp[lane] = make_longlong2(T[lane].off, T[lane].ld);
+  if (lane < nd) dp[lane] = make_longlong2(T[ns + lane].off, T[ns + lane].ld);
   __syncwarp();
   const Shape<ND> sh(it);
-  int sa[ND], sb[ND], da[ND], db[ND];
+  int sa[ND], sb[ND];
   load_strides(it.sa, sa);
   load_strides(it.sb, sb);
+  const int last = it.start + it.count - 1;
+  const int per_lane = (it.count + 31) >> 5;
+  int da[ND], db[ND];
   load_strides(it.da, da);
   load_strides(it.db, db);
-  const int last = it.start + it.count - 1;
-  constexpr int H = (sizeof(TD) == 4 && NS <= 8) ? 4 : ND > 4 ? 1 : 2;  // positions in flight per lane
-  constexpr int V = 16 / sizeof(TD);                       // coefficients per 16-byte read
+  // positions in flight per lane: H x NS values and H destination offsets in
+  // registers (fewer for 6-dim boxes, whose index split needs more)
+  constexpr int kVals = (sizeof(TD) == 4 ? RC_VALS : 16) / (ND > 4 ? 2 : 1);
+  constexpr int H = kVals / NS > RC_HMAX ? RC_HMAX : kVals / NS > 0 ? kVals / NS : 1;
 #pragma unroll 1
-  for (int u = 0; u < kBatch; u += H) {
-    int a[H], b[H], c[H], e[H];
-#pragma unroll
-    for (int h = 0; h < H; ++h) {
-      int t[ND];
-      sh.split(min(it.start + lane + 32 * (u + h), last), t);
-      a[h] = dot(t, sa);
-      b[h] = dot(t, sb);
-      c[h] = dot(t, da);
-      e[h] = dot(t, db);
-    }
+  for (int u = 0; u < per_lane; u += H) {
     TD v[H][NS];
+    int c[H], e[H];  // destination offset parts of each position
+    if constexpr (NS <= 4) {
+      int64_t so[NS];
+      int sl[NS];  // the planner keeps a recoupling item's ld below 2^31
 #pragma unroll
-    for (int q = 0; q < NS; ++q) {
-      if (q < ns) {
-        const TS* p = src + soff[q];
-        const int64_t l = sld[q];
+      for (int q = 0; q < NS; ++q) {
+        const longlong2 x = sp[q < ns ? q : 0];
+        so[q] = x.x;
+        sl[q] = (int)x.y;
+      }
 #pragma unroll
-        for (int h = 0; h < H; ++h) v[h][q] = TD(__ldg(p + l * a[h] + b[h]));
-      } else {
+      for (int h = 0; h < H; ++h) {
+        int t[ND];
+        sh.split(min(it.start + lane + 32 * (u + h), last), t);
+        const int a = dot(t, sa), b = dot(t, sb);
+        c[h] = dot(t, da);
+        e[h] = dot(t, db);
 #pragma unroll
-        for (int h = 0; h < H; ++h) v[h][q] = TD(0);
+        for (int q = 0; q < NS; ++q)
+          v[h][q] = q < ns && u + h < per_lane ? TD(__ldg(src + so[q] + (int64_t)sl[q] * a + b)) : TD(0);
+      }
+    } else {
+      int a[H], b[H];
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        int t[ND];
+        sh.split(min(it.start + lane + 32 * (u + h), last), t);
+        a[h] = dot(t, sa);
+        b[h] = dot(t, sb);
+        c[h] = dot(t, da);
+        e[h] = dot(t, db);
+      }
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        if (q < ns) {
+          const longlong2 x = sp[q];
+          const TS* p = src + x.x;
+#pragma unroll
+          for (int h = 0; h < H; ++h) v[h][q] = TD(__ldg(p + x.y * a[h] + b[h]));
+        } else {
+#pragma unroll
+          for (int h = 0; h < H; ++h) v[h][q] = TD(0);
+        }
       }
     }
 #pragma unroll 1
     for (int d = 0; d < nd; ++d) {
       TD w[NS];
-#pragma unroll
-      for (int q = 0; q < NS; q += V) {  // one 16-byte shared-memory read per V coefficients
-        if constexpr (V == 4) {
-          const float4 r = *reinterpret_cast<const float4*>(cf + d * NS + q);
-          w[q] = r.x;
-          w[q + 1] = r.y;
-          w[q + 2] = r.z;
-          w[q + 3] = r.w;
-        } else {
-          const double2 r = *reinterpret_cast<const double2*>(cf + d * NS + q);
-          w[q] = r.x;
-          w[q + 1] = r.y;
-        }
-      }
-      const int64_t o0 = doff[d], l = dld[d];
+      load_row<NS, TD>(cf + d * NS, w);
+      const longlong2 x = dp[d];
 #pragma unroll
       for (int h = 0; h < H; ++h) {
-        TD acc = TD(0);
+        if (u + h < per_lane) {  // the item's last positions (warp-uniform)
+          TD acc = TD(0);
 #pragma unroll
-        for (int q = 0; q < NS; ++q) acc = fma(w[q], v[h][q], acc);
-        const int64_t o = o0 + l * c[h] + e[h];
-        if (split)
-          store_split(static_cast<__nv_bfloat16*>(dstv), lo_off, o, (float)acc);
-        else
-          static_cast<TD*>(dstv)[o] = acc;
+          for (int q = 0; q < NS; ++q) acc = fma(w[q], v[h][q], acc);
+          const int64_t o = x.x + x.y * c[h] + e[h];
+          if (split)
+            store_split(static_cast<__nv_bfloat16*>(dstv), lo_off, o, (float)acc);
+          else
+            static_cast<TD*>(dstv)[o] = acc;
+        }
       }
     }
   }
@@ -439,6 +489,34 @@ __device__ __forceinline__ void run_flat(const BoxItem& it, const BoxPtrs& ptrs,
   }
 }
 
+// recoupling item: dims bound ND and source-count bound NS from the item
+template <typename TS, typename TD>
+__device__ __forceinline__ void recouple(const BoxItem& it, const Term* __restrict__ terms, const TS* sp, void* dp,
+                                         int64_t lo_off, bool split, TD (*tile)[33], int lane) {
+  const int ns = it.nterm;
+  if (it.ndim <= 4) {
+    if (ns <= 2) {
+      if (it.ndim <= 2)
+        recouple_item<2, 2, TS, TD>(it, terms, sp, dp, lo_off, split, tile, lane);
+      else
+        recouple_item<4, 2, TS, TD>(it, terms, sp, dp, lo_off, split, tile, lane);
+    } else if (ns <= 4) {
+      if (it.ndim <= 2)
+        recouple_item<2, 4, TS, TD>(it, terms, sp, dp, lo_off, split, tile, lane);
+      else
+        recouple_item<4, 4, TS, TD>(it, terms, sp, dp, lo_off, split, tile, lane);
+    } else if (ns <= 8) {
+      recouple_item<4, 8, TS, TD>(it, terms, sp, dp, lo_off, split, tile, lane);
+    } else {
+      recouple_item<4, 16, TS, TD>(it, terms, sp, dp, lo_off, split, tile, lane);
+    }
+  } else if (ns <= 8) {
+    recouple_item<kMaxDim, 8, TS, TD>(it, terms, sp, dp, lo_off, split, tile, lane);
+  } else {
+    recouple_item<kMaxDim, 16, TS, TD>(it, terms, sp, dp, lo_off, split, tile, lane);
+  }
+}
+
 template <typename TS, typename TD>
 __device__ __forceinline__ void run_item(const BoxItem& it, const Term* __restrict__ terms, const BoxPtrs& ptrs,
                                          TD (*tile)[33], int lane) {
@@ -449,16 +527,7 @@ __device__ __forceinline__ void run_item(const BoxItem& it, const Term* __restri
   const TS* sp = src_slot<TS, TD>(it, ptrs);
   void* dp = dst_slot(it, ptrs);
   if (it.sel & kSelRecouple) {
-    const bool split = ((it.sel >> 4) & 7) == DST_SPLIT;
-    const int k = (it.ndim <= 2 ? 0 : it.ndim <= 4 ? 1 : 2) * 2 + (it.nterm <= 8 ? 0 : 1);
-    switch (k) {
-      case 0: recouple_item<2, 8, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
-      case 1: recouple_item<2, 16, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
-      case 2: recouple_item<4, 8, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
-      case 3: recouple_item<4, 16, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
-      case 4: recouple_item<kMaxDim, 8, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
-      default: recouple_item<kMaxDim, 16, TS, TD>(it, terms, sp, dp, ptrs.split_lo, split, tile, lane); break;
-    }
+    recouple<TS, TD>(it, terms, sp, dp, ptrs.split_lo, ((it.sel >> 4) & 7) == DST_SPLIT, tile, lane);
     return;
   }
   Src<TS, TD> src;
@@ -487,10 +556,13 @@ __device__ __forceinline__ void run_item(const BoxItem& it, const Term* __restri
   }
 }
 
-// kFlat: every item of the launch is a flat linear item; this variant has
-// no tile buffer and a 64-register cap, so twice the warps stay resident.
-template <typename TS, typename TD, bool kFlat>
-__global__ void __launch_bounds__(kThreads, kFlat ? 8 : (sizeof(TD) == 4 ? 5 : 4))
+// Launch variants by the items a launch holds: kBoxGeneral any item;
+// kBoxFlat only flat linear items (no tile buffer and a 64-register cap, so
+// twice the warps stay resident); kBoxRecouple only flat linear and fused
+// recoupling items (no transposing tiles or general sums, so the recoupling
+// path is compiled on its own and keeps its loads in registers).
+template <typename TS, typename TD, int kMode>
+__global__ void __launch_bounds__(kThreads, kMode == kBoxFlat ? 8 : kMode == kBoxRecouple && sizeof(TD) == 4 ? RC_MINB : (sizeof(TD) == 4 ? 5 : 4))
     box_kernel(const BoxItem* __restrict__ items, int nitems, const Term* __restrict__ terms, const BoxPtrs ptrs) {
   __shared__ int64_t raw[kWarps][kItemWords];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -507,8 +579,15 @@ __global__ void __launch_bounds__(kThreads, kFlat ? 8 : (sizeof(TD) == 4 ? 5 : 4
     __syncwarp();
     const int next = item + nwarps;
     if (lane < kItemWords && next < nitems) word = __ldg(words + (int64_t)next * kItemWords + lane);
-    if constexpr (kFlat) {
+    if constexpr (kMode == kBoxFlat) {
       run_flat<TS, TD>(it, ptrs, lane);
+    } else if constexpr (kMode == kBoxRecouple) {
+      __shared__ __align__(16) TD stage[kWarps][32][33];
+      if (it.sel & kSelRecouple)
+        recouple<TS, TD>(it, terms, src_slot<TS, TD>(it, ptrs), dst_slot(it, ptrs), ptrs.split_lo,
+                         ((it.sel >> 4) & 7) == DST_SPLIT, stage[w], lane);
+      else
+        run_flat<TS, TD>(it, ptrs, lane);
     } else {
       __shared__ __align__(16) TD tiles[kWarps][32][33];
       run_item<TS, TD>(it, terms, ptrs, tiles[w], lane);
@@ -517,12 +596,12 @@ __global__ void __launch_bounds__(kThreads, kFlat ? 8 : (sizeof(TD) == 4 ? 5 : 4
   }
 }
 
-template <typename TS, typename TD, bool kFlat>
+template <typename TS, typename TD, int kMode>
 int launch_t(const BoxItem* items, int nitems, const Term* terms, const BoxPtrs& ptrs, cudaStream_t s) {
   static int slots = 0;  // resident warps of this instantiation on the device
   if (slots == 0) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, box_kernel<TS, TD, kFlat>, kThreads, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, box_kernel<TS, TD, kMode>, kThreads, 0) !=
             cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
@@ -533,21 +612,26 @@ int launch_t(const BoxItem* items, int nitems, const Term* terms, const BoxPtrs&
   }
   const int warps = nitems < slots ? nitems : slots;
   const int grid = (warps + kWarps - 1) / kWarps;
-  return (int)launch_pdl(box_kernel<TS, TD, kFlat>, dim3(grid), dim3(kThreads), 0, s, items, nitems, terms, ptrs);
+  return (int)launch_pdl(box_kernel<TS, TD, kMode>, dim3(grid), dim3(kThreads), 0, s, items, nitems, terms, ptrs);
+}
+
+template <typename T>
+int launch_mode(int mode, const BoxItem* items, int nitems, const Term* terms, const BoxPtrs& ptrs, cudaStream_t s) {
+  switch (mode) {
+    case kBoxFlat: return launch_t<T, T, kBoxFlat>(items, nitems, terms, ptrs, s);
+    case kBoxRecouple: return launch_t<T, T, kBoxRecouple>(items, nitems, terms, ptrs, s);
+    default: return launch_t<T, T, kBoxGeneral>(items, nitems, terms, ptrs, s);
+  }
 }
 
 }  // namespace
 
-int launch_box(bool src_f64, bool dst_f64, bool flat_only, const BoxItem* items, int nitems, const Term* terms,
+int launch_box(bool src_f64, bool dst_f64, int mode, const BoxItem* items, int nitems, const Term* terms,
                const BoxPtrs& ptrs, void* stream) {
   if (nitems <= 0) return 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (src_f64 && dst_f64)
-    return flat_only ? launch_t<double, double, true>(items, nitems, terms, ptrs, s)
-                     : launch_t<double, double, false>(items, nitems, terms, ptrs, s);
-  if (!src_f64 && !dst_f64)
-    return flat_only ? launch_t<float, float, true>(items, nitems, terms, ptrs, s)
-                     : launch_t<float, float, false>(items, nitems, terms, ptrs, s);
+  if (src_f64 && dst_f64) return launch_mode<double>(mode, items, nitems, terms, ptrs, s);
+  if (!src_f64 && !dst_f64) return launch_mode<float>(mode, items, nitems, terms, ptrs, s);
   return (int)cudaErrorInvalidValue;
 }
 

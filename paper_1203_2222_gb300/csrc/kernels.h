@@ -182,8 +182,11 @@ static_assert(sizeof(DirectItem) == 512, "DirectItem layout");
 enum SimtShape { SIMT_64x64 = 0, SIMT_256x16 = 1, SIMT_THIN = 2, SIMT_ROWS = 3, SIMT_SHAPES = 4 };
 
 // Launchers (return cudaError_t as int).
-// flat_only: every item is a flat linear item (kSelFlat without kSelTile)
-int launch_box(bool src_f64, bool dst_f64, bool flat_only, const BoxItem* items, int nitems, const Term* terms,
+// mode: the items the launch holds, which picks the kernel variant.
+// kBoxGeneral: any item; kBoxFlat: only flat linear items (kSelFlat without
+// kSelTile); kBoxRecouple: only flat linear and fused recoupling items.
+constexpr int kBoxGeneral = 0, kBoxFlat = 1, kBoxRecouple = 2;
+int launch_box(bool src_f64, bool dst_f64, int mode, const BoxItem* items, int nitems, const Term* terms,
                const BoxPtrs& ptrs, void* stream);
 int launch_gemm_simt(bool f64, int shape, const GemmSectorSimt* secs, const GemmTile* tiles, int ntiles,
                      const void* ops, void* outm, void* stream);

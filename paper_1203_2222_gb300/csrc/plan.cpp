@@ -216,12 +216,29 @@ bool emit_recouple(Plan& P, const Box& box0, const std::vector<std::pair<int64_t
                    int src_slot, int dst_slot) {
   const int ns = (int)srcs.size(), nd = (int)dsts.size();
   if (ns < 1 || nd < 1 || ns > kMaxRecouple || nd > kMaxRecouple) return false;
-  const Box box = simplify(box0);
+  // Walk the destination in memory order (dims by destination stride, ld
+  // multiplier first; the last dim is contiguous on both sides and stays
+  // last), so that an item writes whole runs of the destination: a 32-byte
+  // sector written in parts by items far apart in time is read back from
+  // DRAM by the L2 before the rest lands, reading in parts costs no such fill.
+  Box box = simplify(box0);
+  {
+    const int last = box.ndim - 1;
+    std::vector<int> ord(last);
+    for (int i = 0; i < last; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+      return box.da[x] != box.da[y] ? box.da[x] > box.da[y] : box.db[x] > box.db[y];
+    });
+    Box r;
+    for (int i : ord) r.push(box.dims[i], box.sa[i], box.sb[i], box.da[i], box.db[i]);
+    r.push(box.dims[last], box.sa[last], box.sb[last], box.da[last], box.db[last]);
+    box = simplify(r);
+  }
   const int q = box.ndim - 1;
   for (auto& x : srcs)
-    if (x.second * box.sa[q] + box.sb[q] != 1) return false;
+    if (x.second * box.sa[q] + box.sb[q] != 1 || x.second >= ((int64_t)1 << 31)) return false;
   for (auto& x : dsts)
-    if (x.second * box.da[q] + box.db[q] != 1) return false;
+    if (x.second * box.da[q] + box.db[q] != 1 || x.second >= ((int64_t)1 << 31)) return false;
   int64_t total = 1;
   for (int i = 0; i < box.ndim; ++i) total *= box.dims[i];
   if (total >= (int64_t)1 << 31) fail(SYM_ERR_UNSUPPORTED, "block larger than 2^31 elements");
@@ -230,15 +247,60 @@ bool emit_recouple(Plan& P, const Box& box0, const std::vector<std::pair<int64_t
   for (auto& x : dsts) P.terms.push_back(Term{x.first, x.second, 0.0, 0.0f, 0});
   for (double c : coef) P.terms.push_back(Term{0, 0, c, (float)c, 0});
   const std::vector<Term> none;
-  for (int64_t st = 0; st < total; st += kChunk) {
+  // items with few sources hold more positions (the kernel walks a lane's
+  // positions H = 32 / n_s at a time), so the coefficient staging of an item
+  // is shared by about four rounds of loads whatever n_s is
+  const int64_t chunk = ns <= 2 ? 4 * kChunk : ns <= 4 ? 2 * kChunk : kChunk;
+  for (int64_t st = 0; st < total; st += chunk) {
     BoxItem it = make_item(box, 0, 0, src_slot | (dst_slot << 4) | kSelRecouple, term0, none);
     it.nterm = ns;
     it.p0 = nd;
     it.start = (int)st;
-    it.count = (int)std::min<int64_t>(kChunk, total - st);
+    it.count = (int)std::min<int64_t>(chunk, total - st);
     P.items.push_back(it);
   }
   return true;
+}
+
+// Fused recoupling of one gather, scatter or permute (SU(2)): destinations
+// whose recoupling sums run over the same source sectors (the same leg
+// spins) and that write the same buffer form one group, emitted as fused
+// items; `done` (sized ndst by the caller) marks the destinations emitted
+// that way.  dst_of(d) gives the destination's (offset, ld) and slot,
+// src_of(s) a source's (offset, ld), box_of(d, s) the box every member of
+// the group shares (the same leg labels give the same block shape).
+using OffLd = std::pair<int64_t, int64_t>;
+void fuse_recoupling_items(Plan& P, int64_t ndst, const std::vector<TermList>& X, int src_slot,
+                           const std::function<bool(int64_t, OffLd&, int&)>& dst_of,
+                           const std::function<OffLd(int64_t)>& src_of,
+                           const std::function<Box(int64_t, int64_t)>& box_of, std::vector<char>& done) {
+  std::map<std::pair<std::vector<int64_t>, int>, std::vector<int64_t>> groups;
+  for (int64_t d = 0; d < ndst; ++d) {
+    OffLd o;
+    int slot;
+    if (X[d].size() < 2 || !dst_of(d, o, slot)) continue;
+    std::vector<int64_t> key;
+    for (auto& pc : X[d]) key.push_back(pc.first);
+    std::sort(key.begin(), key.end());
+    groups[{key, slot}].push_back(d);
+  }
+  for (auto& gr : groups) {
+    const std::vector<int64_t>& srcs = gr.first.first;
+    const std::vector<int64_t>& ds = gr.second;
+    std::vector<OffLd> so, dof;
+    for (int64_t sidx : srcs) so.push_back(src_of(sidx));
+    std::vector<double> coef(ds.size() * srcs.size(), 0.0);
+    for (size_t i = 0; i < ds.size(); ++i) {
+      OffLd o;
+      int slot;
+      dst_of(ds[i], o, slot);
+      dof.push_back(o);
+      for (auto& pc : X[ds[i]])
+        coef[i * srcs.size() + (std::lower_bound(srcs.begin(), srcs.end(), pc.first) - srcs.begin())] += pc.second;
+    }
+    if (emit_recouple(P, box_of(ds[0], srcs[0]), so, dof, coef, src_slot, gr.first.second))
+      for (int64_t d : ds) done[d] = 1;
+  }
 }
 
 void block_strides(const Tensor& T, int64_t s, int* st) {
@@ -604,8 +666,11 @@ void Plan::upload(bool device) {
   if (item_bytes_prefix.size() != items.size() + 1) item_bytes_prefix.assign(items.size() + 1, 0.0);
   for (size_t i = 0; i < items.size(); ++i) item_bytes_prefix[i + 1] += item_bytes_prefix[i];
   flat_prefix.assign(items.size() + 1, 0);
-  for (size_t i = 0; i < items.size(); ++i)
+  recouple_prefix.assign(items.size() + 1, 0);
+  for (size_t i = 0; i < items.size(); ++i) {
     flat_prefix[i + 1] = flat_prefix[i] + ((items[i].sel & (kSelFlat | kSelTile)) == kSelFlat ? 1 : 0);
+    recouple_prefix[i + 1] = recouple_prefix[i] + ((items[i].sel & kSelRecouple) ? 1 : 0);
+  }
   tile_flops_prefix.assign(tiles.size() + 1, 0.0);
   tile_bytes_prefix.assign(tiles.size() + 1, 0.0);
   for (size_t i = 0; i < tiles.size(); ++i) {
@@ -774,7 +839,26 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
     std::vector<int> pinv(k);
     for (int n = 0; n < k; ++n) pinv[perm[n]] = n;
     auto X = make_xform(in, perm, out);
+    std::vector<char> done(out.nsec(), 0);
+    if (su2_like(in.group))  // output labels sharing their sources: one fused item per position range
+      fuse_recoupling_items(
+          *P, out.nsec(), X, 0,
+          [&](int64_t s, OffLd& o, int& slot) {
+            o = {out.offs[s], 1};
+            slot = DST_OUT;
+            return true;
+          },
+          [&](int64_t si) { return OffLd{in.offs[si], 1}; },
+          [&](int64_t s, int64_t si) {
+            block_strides(out, s, ost);
+            block_strides(in, si, ist);
+            Box b;
+            for (int l = 0; l < k; ++l) b.push(out.dim(s, pinv[l]), ist[l], 0, ost[pinv[l]], 0);
+            return b;
+          },
+          done);
     for (int64_t s = 0; s < out.nsec(); ++s) {
+      if (done[s]) continue;
       block_strides(out, s, ost);
       std::vector<Term> terms;
       for (auto& pc : X[s]) terms.push_back({in.offs[pc.first], 1, pc.second});
@@ -802,7 +886,8 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
     std::vector<int> idp(k);
     for (int i = 0; i < k; ++i) idp[i] = i;
     if (tree) X = make_xform(in, idp, mid);
-    for (int64_t sm = 0; sm < mid.nsec(); ++sm) {
+    // out sector of mid sector sm and the row of the fused leg where it starts
+    auto place = [&](int64_t sm, int64_t& row0) {
       int c = fused_pair_label(in.group, la.labels[mid.p(sm, f)], lb.labels[mid.p(sm, f + 1)],
                                tree ? mid.inner_of(sm)[0] : 0);
       int iq = (int)(std::lower_bound(ld.labels.begin(), ld.labels.end(), c) - ld.labels.begin());
@@ -814,7 +899,45 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
       if (tree) key.insert(key.end(), mid.inner_of(sm) + 1, mid.inner_of(sm) + mid.nin);
       int64_t so = out.find(key);
       if (so < 0) fail(SYM_ERR_ARG, "internal: fused sector missing");
-      int64_t row0 = pair_offset(la, lb, in.group, c, mid.p(sm, f), mid.p(sm, f + 1));
+      row0 = pair_offset(la, lb, in.group, c, mid.p(sm, f), mid.p(sm, f + 1));
+      return so;
+    };
+    std::vector<char> done(mid.nsec(), 0);
+    if (tree)  // the mid sectors of one set of leg labels differ in the fused leg's label, so
+               // in its dimension D: out strides of legs before f are D x (strides without it),
+               // taken as the destination's ld
+      fuse_recoupling_items(
+          *P, mid.nsec(), X, 0,
+          [&](int64_t sm, OffLd& o, int& slot) {
+            int64_t row0;
+            const int64_t so = place(sm, row0);
+            block_strides(out, so, ost);
+            o = {out.offs[so] + row0 * ost[f], out.dim(so, f)};
+            slot = DST_OUT;
+            return true;
+          },
+          [&](int64_t si) { return OffLd{in.offs[si], 1}; },
+          [&](int64_t sm, int64_t si) {
+            int64_t row0;
+            const int64_t so = place(sm, row0);
+            block_strides(out, so, ost);
+            block_strides(in, si, ist);
+            const int D = out.dim(so, f), db_ = mid.dim(sm, f + 1);
+            Box b;
+            for (int l = 0; l < k; ++l) {
+              const int d = mid.dim(sm, l);
+              if (l < f)
+                b.push(d, ist[l], 0, ost[l] / D, 0);
+              else
+                b.push(d, ist[l], 0, 0, l == f ? db_ * ost[f] : l == f + 1 ? ost[f] : ost[l - 1]);
+            }
+            return b;
+          },
+          done);
+    for (int64_t sm = 0; sm < mid.nsec(); ++sm) {
+      if (done[sm]) continue;
+      int64_t row0;
+      const int64_t so = place(sm, row0);
       block_strides(out, so, ost);
       std::vector<Term> terms;
       if (!tree) {
@@ -860,7 +983,50 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
       if (m_in[sm] < 0) fail(SYM_ERR_ARG, "internal: split source sector missing");
       m_row[sm] = pair_offset(la, lb, in.group, c, mid.p(sm, f), mid.p(sm, f + 1));
     }
+    // source box of mid sector sm (the fused leg f of `in` seen as legs f, f+1)
+    auto src_box = [&](int64_t sm, int* sa_, int* sb_) {
+      const int64_t si = m_in[sm];
+      block_strides(in, si, ist);
+      const int64_t dfused = in.dim(si, f);
+      const int stf = ist[f];
+      for (int l = 0; l < f; ++l) {  // in legs l < f: stride = dfused * (stride without the fused dim)
+        sa_[l] = (int)(ist[l] / dfused);
+        sb_[l] = 0;
+      }
+      sa_[f] = 0;
+      sb_[f] = (int)(mid.dim(sm, f + 1) * stf);
+      sa_[f + 1] = 0;
+      sb_[f + 1] = stf;
+      for (int l = f + 2; l < ko; ++l) {
+        sa_[l] = 0;
+        sb_[l] = ist[l - 1];
+      }
+      return OffLd{in.offs[si] + m_row[sm] * stf, dfused};
+    };
+    std::vector<char> done(out.nsec(), 0);
+    if (tree)
+      fuse_recoupling_items(
+          *P, out.nsec(), X, 0,
+          [&](int64_t s, OffLd& o, int& slot) {
+            o = {out.offs[s], 1};
+            slot = DST_OUT;
+            return true;
+          },
+          [&](int64_t sm) {
+            int sa_[kMaxDim], sb_[kMaxDim];
+            return src_box(sm, sa_, sb_);
+          },
+          [&](int64_t s, int64_t sm) {
+            int sa_[kMaxDim], sb_[kMaxDim];
+            src_box(sm, sa_, sb_);
+            block_strides(out, s, ost);
+            Box b;
+            for (int l = 0; l < ko; ++l) b.push(out.dim(s, l), sa_[l], sb_[l], ost[l], 0);
+            return b;
+          },
+          done);
     for (int64_t s = 0; s < out.nsec(); ++s) {
+      if (done[s]) continue;
       block_strides(out, s, ost);
       TermList tl = !tree ? TermList{{s, 1.0}} : X[s];
       std::vector<Term> terms;
@@ -1669,46 +1835,13 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     emit(*P, b, off, (int)cols, 3, DST_OUTM, {});
   };
 
-  // Fused recoupling of one gather or scatter (SU(2)): destinations whose
-  // recoupling sums run over the same source sectors (the same leg spins)
-  // and that write the same buffer form one group, emitted as fused items;
-  // `done` marks the destinations emitted that way.  dst_of(d) gives the
-  // destination's (offset, ld) and slot, src_of(s) a source's (offset, ld),
-  // box_of(d, s) the shared box.
   using OffLd = std::pair<int64_t, int64_t>;
   auto fuse_recoupling = [&](int64_t ndst, const std::vector<TermList>& X, int src_slot,
                              const std::function<bool(int64_t, OffLd&, int&)>& dst_of,
                              const std::function<OffLd(int64_t)>& src_of,
                              const std::function<Box(int64_t, int64_t)>& box_of, std::vector<char>& done) {
     done.assign(ndst, 0);
-    if (!su2) return;
-    std::map<std::pair<std::vector<int64_t>, int>, std::vector<int64_t>> groups;
-    for (int64_t d = 0; d < ndst; ++d) {
-      OffLd o;
-      int slot;
-      if (X[d].size() < 2 || !dst_of(d, o, slot)) continue;
-      std::vector<int64_t> key;
-      for (auto& pc : X[d]) key.push_back(pc.first);
-      std::sort(key.begin(), key.end());
-      groups[{key, slot}].push_back(d);
-    }
-    for (auto& gr : groups) {
-      const std::vector<int64_t>& srcs = gr.first.first;
-      const std::vector<int64_t>& ds = gr.second;
-      std::vector<OffLd> so, dof;
-      for (int64_t sidx : srcs) so.push_back(src_of(sidx));
-      std::vector<double> coef(ds.size() * srcs.size(), 0.0);
-      for (size_t i = 0; i < ds.size(); ++i) {
-        OffLd o;
-        int slot;
-        dst_of(ds[i], o, slot);
-        dof.push_back(o);
-        for (auto& pc : X[ds[i]])
-          coef[i * srcs.size() + (std::lower_bound(srcs.begin(), srcs.end(), pc.first) - srcs.begin())] += pc.second;
-      }
-      if (emit_recouple(*P, box_of(ds[0], srcs[0]), so, dof, coef, src_slot, gr.first.second))
-        for (int64_t d : ds) done[d] = 1;
-    }
+    if (su2) fuse_recoupling_items(*P, ndst, X, src_slot, dst_of, src_of, box_of, done);
   };
 
   // ---- forward gather: A -> A operand, B -> B operand (+ zero fills)
@@ -2154,10 +2287,12 @@ struct ProfScope {
 int run_box(Plan& p, Range r, const BoxPtrs& ptrs, void* stream, int phase) {
   if (r.count <= 0) return SYM_OK;
   p.last_launches++;
-  const bool flat_only = p.flat_prefix[r.first + r.count] - p.flat_prefix[r.first] == r.count;
-  ProfScope ps(p, phase, flat_only ? SYM_KERNEL_BOX_FLAT : SYM_KERNEL_BOX, stream,
+  const int flat = p.flat_prefix[r.first + r.count] - p.flat_prefix[r.first];
+  const int rec = p.recouple_prefix[r.first + r.count] - p.recouple_prefix[r.first];
+  const int mode = flat == r.count ? kBoxFlat : flat + rec == r.count ? kBoxRecouple : kBoxGeneral;
+  ProfScope ps(p, phase, mode == kBoxFlat ? SYM_KERNEL_BOX_FLAT : SYM_KERNEL_BOX, stream,
                p.item_bytes_prefix[r.first + r.count] - p.item_bytes_prefix[r.first], 0.0);
-  return cuda_code(launch_box(p.f64(), p.f64(), flat_only, p.d_items + r.first, r.count, p.d_terms, ptrs, stream),
+  return cuda_code(launch_box(p.f64(), p.f64(), mode, p.d_items + r.first, r.count, p.d_terms, ptrs, stream),
                    "box kernel");
 }
 

@@ -90,7 +90,8 @@ struct Plan {
   // algorithmic bytes of every box item and useful flops of every tile,
   // as prefix sums (launch statistics for any range in O(1))
   std::vector<double> item_bytes_prefix, tile_flops_prefix, tile_bytes_prefix;
-  std::vector<int> flat_prefix;  // flat linear items among the first i (launch variant choice)
+  std::vector<int> flat_prefix;      // flat linear items among the first i (launch variant choice)
+  std::vector<int> recouple_prefix;  // fused recoupling items among the first i
   void set_item_bytes(Range r, int es_src, int es_dst);
   bool profiling = false;
   PhaseProfile prof[PH_COUNT];

@@ -178,7 +178,7 @@ PHASES = {"fwd_gather": 0, "fwd_gemm_tc": 1, "fwd_scatter": 2, "bwd_gather": 3, 
 # name of the CUDA kernel each one launches
 KERNELS = {"box": 0, "box_flat": 1, "gemm_tc": 2, "gemm_tile": 3, "gemm_wide": 4, "gemm_thin": 5, "gemm_rows": 6,
            "direct": 7}
-KERNEL_SYMBOLS = {"box": "box_kernel<T, T, false>", "box_flat": "box_kernel<T, T, true>",
+KERNEL_SYMBOLS = {"box": "box_kernel<T, T, 0 | 2>", "box_flat": "box_kernel<T, T, 1>",
                   "gemm_tc": "gemm_tc_kernel", "gemm_tile": "gemm_tile_kernel<T, 64, 64>",
                   "gemm_wide": "gemm_tile_kernel<T, 256, 16>", "gemm_thin": "gemm_thin_kernel<T>",
                   "gemm_rows": "gemm_rows_kernel<T>", "direct": "direct_kernel<T>"}

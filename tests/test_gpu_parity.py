@@ -292,6 +292,27 @@ def test_permute(dtype):
 
 
 @pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
+def test_su2_transforms_many_positions(dtype):
+    # standalone SU(2) permute, fuse and split whose blocks span several
+    # fused recoupling items (blocks up to 12^4 positions; items of 512 to
+    # 2048 positions with ragged last ones) and whose leg spins give 1 to 5
+    # source labels per set of legs; fuses of inner legs (1, 2) and (2, 3)
+    # take the destination's fused-leg dimension as its row stride
+    P = _lib()
+    sp = [0, 1, 2]
+    for legs in ([(sp, [12, 9, 7], 1), (sp, [9, 7, 12], -1), (sp, [7, 12, 9], -1), (sp, [12, 7, 9], -1)],
+                 [([3, 4], [6, 5], 1), ([2, 3, 4], [3, 6, 4], 1), ([3, 4], [5, 6], 1), ([2, 4], [6, 5], 1)]):
+        _transform_case("su2", legs, "permute", ([0, 2, 1, 3], [(0, 1), (2, 3), (4, 5)]), dtype)
+        _transform_case("su2", legs, "permute", ([3, 1, 0, 2], None), dtype)
+        for f in (1, 2):
+            S, T, F = _transform_case("su2", legs, "fuse", (f,), dtype)
+            back = P.split(F, f, [legs[f], legs[f + 1]])
+            torch.cuda.synchronize()
+            err = rel(back.data.double().cpu().numpy(), T.data.double().cpu().numpy())
+            assert err <= (1e-13 if dtype == torch.float64 else 1e-6), (f, err)
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=DTYPE_IDS)
 def test_fuse_then_split_roundtrip(dtype):
     P = _lib()
     for group, legs in [
