@@ -497,13 +497,13 @@ WORKLOADS = {"u1_mps_heff": MPSWorkload, "su2_recouple": SU2Workload, "u1_two_si
 # the captured launches, applied to the full launch's algorithmic bytes.
 TRAFFIC = {
     "u1_mps_heff": {  # profiles/traffic_u1_mps_heff.md
-        "gemm_tc": {"bytes_per_launch": 13768512, "sha": "17524e1d9ff325bc"},
-        "box_flat": {"bytes_per_launch": 5857248, "sha": "b7242e8ca118cb38"},
-        "box": {"bytes_per_launch": 13079040, "sha": "b7242e8ca118cb38"},
-        "direct": {"bytes_per_launch": 11909291, "sha": "32a083d9660812bd"},
+        "gemm_tc": {"bytes_per_launch": 13767680, "sha": "98131bfb98e11ffc"},
+        "box_flat": {"bytes_per_launch": 5859584, "sha": "0320d4c6c49f9616"},
+        "box": {"bytes_per_launch": 13080064, "sha": "0320d4c6c49f9616"},
+        "direct": {"bytes_per_launch": 11909291, "sha": "f5f2fc621ce84798"},
     },
     "su2_recouple": {  # profiles/gemm_tc_su2_recouple.md (full size, forward and backward launches)
-        "gemm_tc": {"bytes_per_launch": 60924806400, "sha": "17524e1d9ff325bc"},
+        "gemm_tc": {"bytes_per_launch": 61036485248, "sha": "98131bfb98e11ffc"},
     },
     "u1_two_site_batch": {  # profiles/direct_u1_two_site_batch.md (128 of the 512 problems)
         "direct": {"ratio": 0.97, "sha": "32a083d9660812bd"},
@@ -514,11 +514,11 @@ TRAFFIC = {
     "u1_two_site_eig": {  # profiles/eig_u1_two_site_eig.md (full size, mean of 11 launches)
         "svd_jacobi": {"bytes_per_launch": 8724596, "sha": "80768ec65c30971e"},
     },
-    "z2f_mps_heff": {  # profiles/traffic_z2f_mps_heff_and_mera.md (full size, mean of 48 step launches)
-        "gemm_tc": {"bytes_per_launch": 196125834, "sha": "17524e1d9ff325bc"},
+    "z2f_mps_heff": {  # profiles/traffic_z2f_mps_heff_and_mera.md (full size, mean of 54 step launches)
+        "gemm_tc": {"bytes_per_launch": 196313993, "sha": "98131bfb98e11ffc"},
     },
-    "u1_mera_grad": {  # profiles/traffic_z2f_mps_heff_and_mera.md (full size, mean of 507 launches)
-        "box_flat": {"bytes_per_launch": 2139185, "sha": "b7242e8ca118cb38"},
+    "u1_mera_grad": {  # profiles/traffic_z2f_mps_heff_and_mera.md (full size, mean of 585 launches)
+        "box_flat": {"bytes_per_launch": 2138954, "sha": "0320d4c6c49f9616"},
     },
 }
 KERNEL_SOURCES = {
