@@ -359,6 +359,18 @@ int sym_contract_noalloc(sym_tensor A, sym_tensor B, int npairs,
  * device. */
 int sym_device_status(void);
 
+/* Test of the failure detection (no counterpart in the thesis): runs, on the
+ * legacy default stream, one bounded mbarrier wait of the kind the
+ * tensor-core kernel's waits are, for a phase that nothing completes, and
+ * synchronizes.  The wait expires after limit_us microseconds (1 ..
+ * 2,000,000) and sets SYM_ERR_TIMEOUT in the library's device error word
+ * (word = 0) or in sym_contract_noalloc's static one (word = 1), which the
+ * next sym_device_status() then reports and clears; the context stays
+ * usable.  Nothing faults and nothing waits without a limit.  Errors:
+ * SYM_ERR_ARG for a limit or word out of range, SYM_ERR_CUDA if the launch
+ * or the synchronization fails. */
+int sym_wait_probe(int limit_us, int word);
+
 /* ------------------------------------------ blockwise factorization (SVD) ---
  * Singular value decomposition of a symmetric tensor seen as a matrix
  * (Ch. 5, "Factorization of a matrix", Eq. svd0 and svd1; Ch. 6, "Matrix

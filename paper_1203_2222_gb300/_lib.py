@@ -91,6 +91,7 @@ _SIGS = {
     "sym_plan_destroy": ([_P], _I),
     "sym_plan_gemm_shapes": ([_P, _IP, _IP], _I),
     "sym_device_status": ([], _I),
+    "sym_wait_probe": ([_I, _I], _I),
     "sym_su2_F": ([_I, _I, _I, _I, _I, _I, _DP], _I),
     "sym_contract_noalloc": ([_P, _P, _I, _IP, _IP, _I, _P, _P, _P, _P], _I),
     "sym_su2_gamma": ([_I, _IP, _IP, _IP, _IP, _IP, _IP, _DP, _IP, _IP], _I),

@@ -519,4 +519,16 @@ int sym_device_status(void) {
   });
 }
 
+int sym_wait_probe(int limit_us, int word) {
+  return guard([&] {
+    if (limit_us < 1 || limit_us > 2000000 || (word != 0 && word != 1))
+      sym::fail(SYM_ERR_ARG, "sym_wait_probe: limit_us in 1..2000000, word 0 or 1");
+    int* w = word == 0 ? sym::device_error_word() : sym::noalloc_error_word();
+    int e = sym::launch_wait_probe(w, (uint64_t)limit_us * 1000ull, nullptr);
+    if (e == 0) e = (int)cudaDeviceSynchronize();
+    if (e != 0) sym::fail(SYM_ERR_CUDA, std::string("wait probe: ") + cudaGetErrorString((cudaError_t)e));
+    return SYM_OK;
+  });
+}
+
 }  // extern "C"

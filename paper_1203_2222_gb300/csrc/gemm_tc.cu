@@ -180,7 +180,7 @@ struct Ctl {
 };
 
 // Bounded wait; false on timeout or when another role aborted.
-__device__ bool wait_bar(uint64_t* bar, uint32_t parity, Ctl* ctl, int* err) {
+__device__ bool wait_bar(uint64_t* bar, uint32_t parity, Ctl* ctl, int* err, uint64_t limit_ns = WAIT_NS) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = now_ns();
   while (true) {
@@ -188,7 +188,7 @@ __device__ bool wait_bar(uint64_t* bar, uint32_t parity, Ctl* ctl, int* err) {
     for (int i = 0; i < 32; ++i)
       if (mbar_try_wait(bar, parity)) return true;
     if (ctl->abort) return false;
-    if (now_ns() - t0 > WAIT_NS) {
+    if (now_ns() - t0 > limit_ns) {
       ctl->abort = 1;
       atomicExch(err, SYM_ERR_TIMEOUT);
       return false;
@@ -414,7 +414,29 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
 int g_num_sms = 0;
 
+// One bounded wait, on the path the kernel's waits take, for the phase of
+// an mbarrier that nothing arrives at: it expires after limit_ns and sets
+// SYM_ERR_TIMEOUT in *err.  Lets a test check the expiry path and the error
+// word without a fault or a hang.
+__global__ void wait_probe_kernel(int* err, uint64_t limit_ns) {
+  __shared__ uint64_t bar;
+  __shared__ Ctl ctl;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    ctl.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) wait_bar(&bar, 0u, &ctl, err, limit_ns);
+}
+
 }  // namespace
+
+int launch_wait_probe(int* err_word, uint64_t limit_ns, void* stream) {
+  if (limit_ns > WAIT_NS) limit_ns = WAIT_NS;
+  wait_probe_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(err_word, limit_ns);
+  return (int)cudaGetLastError();
+}
 
 int tc_num_sms() {
   if (g_num_sms == 0) {

@@ -194,6 +194,10 @@ int launch_gemm_simt(bool f64, int shape, const GemmSectorSimt* secs, const Gemm
 int launch_direct(bool f64, int op, const DirectItem* items, int nitems, const BoxPtrs& ptrs, void* stream);
 int launch_gemm_tc(const TcSector* secs, const GemmTile* tiles, int ntiles, const TensorMap* maps, float* C,
                    int* err_word, void* stream);
+// One bounded mbarrier wait that nothing completes (a test of the expiry
+// path): sets SYM_ERR_TIMEOUT in *err_word after limit_ns (at most the
+// kernels' own 2 s limit).
+int launch_wait_probe(int* err_word, uint64_t limit_ns, void* stream);
 // Tensor map of one operand whose hi plane starts at `hi` (bf16) and whose lo
 // plane is split_lo elements further; 0 or a CUDA driver error code.
 int encode_operand_map(TensorMap* out, const void* hi, const TcOperand& op, int64_t split_lo);

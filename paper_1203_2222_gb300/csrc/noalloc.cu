@@ -107,6 +107,9 @@ DeviceSyms device_syms() {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
+
+int* noalloc_error_word() { return device_syms().err; }
+
 }  // namespace sym
 
 extern "C" int sym_contract_noalloc(sym_tensor A, sym_tensor B, int npairs, const int* pairsA, const int* pairsB,

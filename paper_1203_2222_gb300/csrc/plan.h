@@ -165,6 +165,8 @@ int take_device_error();
 // Another device error word (a static __device__ int) that take_device_error
 // also reads and clears.
 void register_device_error_word(int* w);
+// sym_contract_noalloc's static error word on the current device (noalloc.cu).
+int* noalloc_error_word();
 
 // Structure helpers shared with the C ABI.
 Leg fused_leg(const Leg& a, const Leg& b, int group);
