@@ -29,15 +29,6 @@
 namespace sym {
 namespace {
 
-#ifndef RC_VALS
-#define RC_VALS 24
-#endif
-#ifndef RC_HMAX
-#define RC_HMAX 8
-#endif
-#ifndef RC_MINB
-#define RC_MINB 4
-#endif
 constexpr int kThreads = 128;
 constexpr int kWarps = kThreads / 32;
 constexpr int kBatch = kBoxChunk / 32;  // elements per lane of a linear item
@@ -287,12 +278,13 @@ __device__ __forceinline__ void tile_item(const BoxItem& it, const TS* __restric
 // shared-memory tile with rows padded to NS (a bound on n_s: 2, 4, 8 or 16)
 // and read back as 8- or 16-byte vectors; the (offset, ld) pairs of sources
 // and destinations are staged beside it.  A lane keeps H positions x NS
-// values in flight (H * NS = 32 registers of FP32), so items with few
-// sources load more positions per round trip; with NS <= 4 the source
-// offsets live in registers and every position's loads are issued as soon as
-// its index is split.  An item may hold more than 32 positions per lane (the
-// planner sizes it by n_s); the lane walks them H at a time.  ND is a bound
-// on the box's dims (unused dims are unit).
+// values in flight (H * NS about 24 registers of FP32, H at most 8) and the
+// destination offsets of its H positions, so items with few sources load
+// more positions per round trip; with NS <= 4 the source offsets live in
+// registers and every position's loads are issued as soon as its index is
+// split.  An item may hold more than 32 positions per lane (the planner
+// sizes it by n_s); the lane walks them H at a time.  ND is a bound on the
+// box's dims (unused dims are unit).
 template <int NS, typename TD>
 __device__ __forceinline__ void load_row(const TD* r, TD (&w)[NS]) {
   if constexpr (sizeof(TD) == 4 && NS % 4 == 0) {
@@ -348,8 +340,8 @@ __device__ __forceinline__ void recouple_item(const BoxItem& it, const Term* __r
   load_strides(it.db, db);
   // positions in flight per lane: H x NS values and H destination offsets in
   // registers (fewer for 6-dim boxes, whose index split needs more)
-  constexpr int kVals = (sizeof(TD) == 4 ? RC_VALS : 16) / (ND > 4 ? 2 : 1);
-  constexpr int H = kVals / NS > RC_HMAX ? RC_HMAX : kVals / NS > 0 ? kVals / NS : 1;
+  constexpr int kVals = (sizeof(TD) == 4 ? 24 : 16) / (ND > 4 ? 2 : 1);
+  constexpr int H = kVals / NS > 8 ? 8 : kVals / NS > 0 ? kVals / NS : 1;
 #pragma unroll 1
   for (int u = 0; u < per_lane; u += H) {
     TD v[H][NS];
@@ -562,7 +554,7 @@ __device__ __forceinline__ void run_item(const BoxItem& it, const Term* __restri
 // recoupling items (no transposing tiles or general sums, so the recoupling
 // path is compiled on its own and keeps its loads in registers).
 template <typename TS, typename TD, int kMode>
-__global__ void __launch_bounds__(kThreads, kMode == kBoxFlat ? 8 : kMode == kBoxRecouple && sizeof(TD) == 4 ? RC_MINB : (sizeof(TD) == 4 ? 5 : 4))
+__global__ void __launch_bounds__(kThreads, kMode == kBoxFlat ? 8 : kMode == kBoxRecouple && sizeof(TD) == 4 ? 4 : (sizeof(TD) == 4 ? 5 : 4))
     box_kernel(const BoxItem* __restrict__ items, int nitems, const Term* __restrict__ terms, const BoxPtrs ptrs) {
   __shared__ int64_t raw[kWarps][kItemWords];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
