@@ -7,7 +7,7 @@
 // from the tensor's blocks (each one a row-major sub-matrix of its M_x,
 // because the row legs lead), so there is no separate move into matrix form.
 //
-// svd_jacobi_kernel: one cluster of 8 CTAs per block, one-sided Jacobi
+// svd_jacobi_kernel: one cluster of 16 CTAs per block, one-sided Jacobi
 //   (Hestenes).  A = M_x (m >= n) or M_x^T, R x C with R >= C, is copied
 //   column-major into the workspace.  A sweep visits every column pair once,
 //   in the round-robin order of a tournament (C - 1 rounds of C/2 disjoint
@@ -17,7 +17,9 @@
 //   whole sweep rotates nothing by more than kBigRotation(32) relative,
 //   A V = W has orthogonal columns: S = their norms, U = W / S.  The sweeps
 //   run first in FP32, then, from the FP32 result made orthogonal in FP64,
-//   in FP64 (see the kernel).  The FP64
+//   in FP64 (see the kernel).  The FP32 sweeps of blocks with at least 32
+//   columns take the same pairs by column blocks, a block pair in a CTA's
+//   shared memory (jacobi_sweeps_blocked).  The FP64
 //   sweeps are bounded (kMaxSweeps); a block that has not converged by then
 //   sets the device error word to SYM_ERR_NUMERIC.  The columns are then
 //   ranked by norm (descending, ties by index) into S and a permutation.
@@ -62,7 +64,12 @@ namespace {
 
 constexpr int kSvdThreads = 256;
 constexpr int kSvdWarps = kSvdThreads / 32;
-constexpr int kSvdCluster = 8;  // CTAs (SMs) per diagonal block
+// CTAs per diagonal block (16: a cluster size above the portable 8, allowed
+// by a function attribute; two CTAs of the kernel fit on an SM)
+constexpr int kSvdCluster = 16;
+// dynamic shared memory a Jacobi CTA may take for the FP32 sweeps by column
+// blocks (two CTAs of 256 threads and 128 registers share an SM)
+constexpr int kSvdSmem32Max = 100 * 1024;
 constexpr int kMaxSweeps = 64;    // FP64 sweeps before a block counts as not converged
 constexpr int kMaxSweeps32 = 40;  // FP32 sweeps (their result only seeds the FP64 ones)
 // An FP64 sweep whose rotations all had |w_p.w_q| <= kBigRotation |w_p| |w_q|
@@ -88,6 +95,7 @@ struct SvdBlock {
   double vscale;  // SU(2): sqrt(2j+1) (the factors carry it, S is divided by it), else 1
   int eig;        // eigendecomposition of the symmetric part (square block) instead of the SVD
   double sgn;     // eig, SU(2) with an incoming row leg: (-1)^{2j}, the sign of the dense block; else 1
+  int bw;         // FP32 sweeps by column blocks of bw columns (0: by column pairs)
   int64_t w;   // workspace offset: W (R x C, column-major), V (C x C), norms (C), sorted S (C), then
                // the Jacobi kernel's A (R x C), Newton-Schulz factor (C x C), FP32 W and V
   int64_t s;   // first singular value of the block in S and in the permutation
@@ -316,6 +324,136 @@ __device__ int jacobi_sweeps(T* W, T* V, int R, int C, int max_sweeps, T tol, cg
   return sweeps;
 }
 
+// Rotate one column pair of W (length R) and V (length C) held in shared
+// memory; NR rows per lane.  Returns 0 (no rotation), 1, or 2 (a rotation
+// larger than big relative to the pair's norms).
+template <int NR>
+__device__ __forceinline__ int rotate_pair_smem(float* wp, float* wq, float* vp, float* vq, int R, int C, int lane,
+                                                float tol, float big) {
+  float xw[NR], yw[NR];
+  float a = 0.0f, bb = 0.0f, g = 0.0f;
+#pragma unroll
+  for (int u = 0; u < NR; ++u) {
+    const int i = lane + 32 * u;
+    xw[u] = i < R ? wp[i] : 0.0f;
+    yw[u] = i < R ? wq[i] : 0.0f;
+    a = fmaf(xw[u], xw[u], a);
+    bb = fmaf(yw[u], yw[u], bb);
+    g = fmaf(xw[u], yw[u], g);
+  }
+  a = warp_sum(a);
+  bb = warp_sum(bb);
+  g = warp_sum(g);
+  const float sab = sqrtf(a * bb);
+  float c, sn;
+  if (!JacobiArith<float>::angle(a, bb, g, sab, tol, c, sn)) return 0;
+#pragma unroll
+  for (int u = 0; u < NR; ++u) {
+    const int i = lane + 32 * u;
+    if (i < R) {
+      wp[i] = c * xw[u] - sn * yw[u];
+      wq[i] = sn * xw[u] + c * yw[u];
+    }
+    if (i < C) {
+      const float x = vp[i], y = vq[i];
+      vp[i] = c * x - sn * y;
+      vq[i] = sn * x + c * y;
+    }
+  }
+  return fabsf(g) > big * sab ? 2 : 1;
+}
+
+// FP32 sweeps by column blocks: the C columns form kColBlocks blocks of bw
+// (the last ones ragged or empty), and a sweep is the tournament over the
+// blocks (kColBlocks - 1 rounds of kSvdCluster disjoint block pairs).  In a
+// round, CTA k of the cluster takes block pair k -- the columns of W and V
+// -- into its shared memory, rotates every cross pair (p in P, q in Q; in
+// the first round also the pairs inside P and inside Q) in bw inner rounds
+// of disjoint pairs separated by CTA barriers, and writes the columns back;
+// a cluster barrier separates the rounds.  Every column pair is visited once
+// a sweep, as in the order by pairs, but a sweep needs kColBlocks - 1 cluster
+// barriers instead of C - 1, and the pairs' columns come from shared memory.
+constexpr int kColBlocks = 2 * kSvdCluster;
+template <int NR>
+__device__ int jacobi_sweeps_blocked(float* W, float* V, int R, int C, int bw, int max_sweeps, float tol,
+                                     cg::cluster_group& cluster, SweepCtl* ctl, int* flag0, int crank, int lane,
+                                     int& gsweep, unsigned long long& myrot, bool& conv, float big_tol, float* sm) {
+  const int warp = threadIdx.x >> 5;
+  float* Wp = sm;  // bw columns of R, then Q's, then V's columns of P and Q (C each)
+  float* Wq = Wp + (int64_t)bw * R;
+  float* Vp = Wq + (int64_t)bw * R;
+  float* Vq = Vp + (int64_t)bw * C;
+  const int bwe = bw + (bw & 1);  // a block's own tournament: bwe - 1 rounds of bwe / 2 pairs
+  int sweeps = 0;
+  conv = C < 2;
+  while (!conv && sweeps < max_sweeps) {
+    ++sweeps;
+    const int gs = ++gsweep;
+    int did = 0, big = 0;
+    auto rot = [&](float* wp, float* wq, float* vp, float* vq) {
+      const int r = rotate_pair_smem<NR>(wp, wq, vp, vq, R, C, lane, tol, big_tol);
+      if (r) {
+        did = 1;
+        big |= r == 2;
+        ++myrot;
+      }
+    };
+    for (int r = 0; r < kColBlocks - 1; ++r) {
+      const int k = crank;
+      const int P = k == 0 ? r : (r + k) % (kColBlocks - 1);
+      const int Q = k == 0 ? kColBlocks - 1 : (r - k + kColBlocks - 1) % (kColBlocks - 1);
+      const int p0 = P * bw, np = max(0, min(bw, C - p0));
+      const int q0 = Q * bw, nq = max(0, min(bw, C - q0));
+      // the two blocks' columns are contiguous in the column-major W and V
+      for (int i = threadIdx.x; i < np * R; i += kSvdThreads) Wp[i] = __ldcg(W + (int64_t)p0 * R + i);
+      for (int i = threadIdx.x; i < nq * R; i += kSvdThreads) Wq[i] = __ldcg(W + (int64_t)q0 * R + i);
+      for (int i = threadIdx.x; i < np * C; i += kSvdThreads) Vp[i] = __ldcg(V + (int64_t)p0 * C + i);
+      for (int i = threadIdx.x; i < nq * C; i += kSvdThreads) Vq[i] = __ldcg(V + (int64_t)q0 * C + i);
+      __syncthreads();
+      if (r == 0) {  // the pairs inside P and inside Q: each block's own tournament, side by side
+        for (int ir = 0; ir < bwe - 1; ++ir) {
+          for (int t = warp; t < bwe; t += kSvdWarps) {
+            const int side = t < bwe / 2 ? 0 : 1, kk = side ? t - bwe / 2 : t;
+            int a = kk == 0 ? ir : (ir + kk) % (bwe - 1);
+            int c = kk == 0 ? bwe - 1 : (ir - kk + bwe - 1) % (bwe - 1);
+            const int n = side ? nq : np;
+            if (a < n && c < n) {
+              float* w0 = side ? Wq : Wp;
+              float* v0 = side ? Vq : Vp;
+              rot(w0 + (int64_t)a * R, w0 + (int64_t)c * R, v0 + (int64_t)a * C, v0 + (int64_t)c * C);
+            }
+          }
+          __syncthreads();
+        }
+      }
+      for (int ir = 0; ir < bw; ++ir) {  // the cross pairs (i, (i + ir) mod bw)
+        for (int i = warp; i < bw; i += kSvdWarps) {
+          const int j = (i + ir) % bw;
+          if (i < np && j < nq)
+            rot(Wp + (int64_t)i * R, Wq + (int64_t)j * R, Vp + (int64_t)i * C, Vq + (int64_t)j * C);
+        }
+        __syncthreads();
+      }
+      for (int i = threadIdx.x; i < np * R; i += kSvdThreads) __stcg(W + (int64_t)p0 * R + i, Wp[i]);
+      for (int i = threadIdx.x; i < nq * R; i += kSvdThreads) __stcg(W + (int64_t)q0 * R + i, Wq[i]);
+      for (int i = threadIdx.x; i < np * C; i += kSvdThreads) __stcg(V + (int64_t)p0 * C + i, Vp[i]);
+      for (int i = threadIdx.x; i < nq * C; i += kSvdThreads) __stcg(V + (int64_t)q0 * C + i, Vq[i]);
+      cluster.sync();  // the next round reads columns this round wrote, on other CTAs
+    }
+    const int f = (__syncthreads_or(did) ? 1 : 0) | (__syncthreads_or(big) ? 2 : 0);
+    if (f && threadIdx.x == 0) atomicOr(flag0 + (gs & 1), f);
+    cluster.sync();
+    if (threadIdx.x == 0) {
+      ctl->any = flag0[gs & 1];
+      if (crank == 0) ctl->flag[(gs + 1) & 1] = 0;
+    }
+    __syncthreads();
+    conv = !(ctl->any & 2);
+    __syncthreads();
+  }
+  return sweeps;
+}
+
 // out[:, j] = scale * sum_i X[i, j] Aop[:, i]  (column-major: Aop rows x C,
 // X C x C, out rows x C); a warp per (column j, 128 rows).
 __device__ void gemm_cols(const double* Aop, int rows, int C, const double* X, double* out, double scale, int cw,
@@ -390,6 +528,7 @@ __global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThread
   __shared__ SweepCtl ctl;
   __shared__ double wsum[kSvdWarps];
   __shared__ double fpart;  // eig: this CTA's part of the squared Frobenius norm
+  extern __shared__ float sm32[];  // the FP32 sweeps by column blocks: a block pair of W and V
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
   const SvdBlock b = blocks[blockIdx.x / kSvdCluster];
@@ -484,8 +623,31 @@ __global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThread
   unsigned long long rot32 = 0, rot64 = 0;
   bool conv32, conv;
   int gsweep = 0;
-  const int sw32 = jacobi_sweeps<float>(W32, V32, R, C, kMaxSweeps32, sqrtf((float)R) * FLT_EPSILON, cluster,
-                                        &ctl, flag0, crank, cw, lane, gsweep, rot32, conv32, kBigRotation32);
+  const float tol32 = sqrtf((float)R) * FLT_EPSILON;
+  int sw32;
+  switch (b.bw ? (R + 31) / 32 : 0) {
+#define SYM_BLOCKED(NR)                                                                                           \
+  case NR:                                                                                                         \
+    sw32 = jacobi_sweeps_blocked<NR>(W32, V32, R, C, b.bw, kMaxSweeps32, tol32, cluster, &ctl, flag0, crank, lane, \
+                                     gsweep, rot32, conv32, kBigRotation32, sm32);                                 \
+    break;
+    SYM_BLOCKED(1)
+    SYM_BLOCKED(2)
+    SYM_BLOCKED(3)
+    SYM_BLOCKED(4)
+    SYM_BLOCKED(5)
+    SYM_BLOCKED(6)
+    SYM_BLOCKED(7)
+    SYM_BLOCKED(8)
+    SYM_BLOCKED(9)
+    SYM_BLOCKED(10)
+    SYM_BLOCKED(11)
+    SYM_BLOCKED(12)
+#undef SYM_BLOCKED
+    default:
+      sw32 = jacobi_sweeps<float>(W32, V32, R, C, kMaxSweeps32, tol32, cluster, &ctl, flag0, crank, cw, lane, gsweep,
+                                  rot32, conv32, kBigRotation32);
+  }
 
   // V = V32 made orthogonal in FP64: two Newton-Schulz steps through the G
   // buffer, the first one's product in W's buffer (free until W = A V)
@@ -681,6 +843,7 @@ struct SvdPlan {
   std::vector<SvdPiece> tpieces;  // grouped by block
   TupleMap rows, cols;
   int64_t nsv = 0, work_elems = 0;
+  int64_t smem32 = 0;      // dynamic shared memory of the Jacobi launch (FP32 sweeps by column blocks)
   std::vector<int> order;  // launch order: blocks by decreasing work
   bool dry = false;
   bool bonded = false;
@@ -768,6 +931,14 @@ std::unique_ptr<SvdPlan> plan_svd(const Tensor& T, int nrow, bool eig) {
     // SU(2) with an incoming row leg: the dense block is (-1)^{2j} M_x / sqrt(2j+1) (x) 1
     b.sgn = (eig && T.group == SYM_SU2 && T.legs[0].dir == -1 && (x & 1)) ? -1.0 : 1.0;
     if (eig && m != n) fail(SYM_ERR_ARG, "internal: eigendecomposition block is not square");
+    // FP32 sweeps by column blocks when a block pair of W and V fits the
+    // shared memory two CTAs of an SM can have, rows up to 12 per lane
+    {
+      const int bw = (b.C + kColBlocks - 1) / kColBlocks;
+      const int64_t bytes = 2 * (int64_t)bw * (b.R + b.C) * (int64_t)sizeof(float);
+      b.bw = (b.C >= kColBlocks * 2 && b.R <= 32 * 12 && bytes <= kSvdSmem32Max) ? bw : 0;
+      if (b.bw) P->smem32 = std::max<int64_t>(P->smem32, bytes);
+    }
     b.w = P->work_elems;
     b.s = P->nsv;
     // W, V, norms, sorted S, A, the Newton-Schulz factor (doubles), W and V in FP32
@@ -873,7 +1044,16 @@ int sym_svd_blocks(sym_svd plan, int* x, int* m, int* n) {
 namespace {
 void launch_jacobi(sym::SvdPlan& P, const double* T, double* S, void* stream) {
   if (P.dry) sym::fail(SYM_ERR_UNSUPPORTED, "plan was built with SYM_PLAN_DRYRUN=1 and cannot run");
-  sym::svd_jacobi_kernel<<<(unsigned)P.blocks.size() * sym::kSvdCluster, sym::kSvdThreads, 0,
+  static int attr_set = -1;  // dynamic shared memory the kernel is allowed (set once to the maximum)
+  if (attr_set < 0) {
+    cudaError_t e = cudaFuncSetAttribute(sym::svd_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         sym::kSvdSmem32Max);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(sym::svd_jacobi_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) sym::fail(SYM_ERR_CUDA, std::string("svd_jacobi_kernel attribute: ") + cudaGetErrorString(e));
+    attr_set = 1;
+  }
+  sym::svd_jacobi_kernel<<<(unsigned)P.blocks.size() * sym::kSvdCluster, sym::kSvdThreads, (size_t)P.smem32,
                            static_cast<cudaStream_t>(stream)>>>(
       P.d_blocks, P.d_pieces, T, P.work, S, P.perm, P.sweeps, P.rotations, sym::device_error_word());
   check_launch("svd_jacobi_kernel");
