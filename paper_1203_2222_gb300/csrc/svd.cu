@@ -96,6 +96,7 @@ struct SvdBlock {
   int eig;        // eigendecomposition of the symmetric part (square block) instead of the SVD
   double sgn;     // eig, SU(2) with an incoming row leg: (-1)^{2j}, the sign of the dense block; else 1
   int bw;         // FP32 sweeps by column blocks of bw columns (0: by column pairs)
+  int bw64;       // the same for the FP64 sweeps
   int64_t w;   // workspace offset: W (R x C, column-major), V (C x C), norms (C), sorted S (C), then
                // the Jacobi kernel's A (R x C), Newton-Schulz factor (C x C), FP32 W and V
   int64_t s;   // first singular value of the block in S and in the permutation
@@ -327,26 +328,25 @@ __device__ int jacobi_sweeps(T* W, T* V, int R, int C, int max_sweeps, T tol, cg
 // Rotate one column pair of W (length R) and V (length C) held in shared
 // memory; NR rows per lane.  Returns 0 (no rotation), 1, or 2 (a rotation
 // larger than big relative to the pair's norms).
-template <int NR>
-__device__ __forceinline__ int rotate_pair_smem(float* wp, float* wq, float* vp, float* vq, int R, int C, int lane,
-                                                float tol, float big) {
-  float xw[NR], yw[NR];
-  float a = 0.0f, bb = 0.0f, g = 0.0f;
+template <typename T, int NR>
+__device__ __forceinline__ int rotate_pair_smem(T* wp, T* wq, T* vp, T* vq, int R, int C, int lane, T tol, T big) {
+  T xw[NR], yw[NR];
+  T a = 0, bb = 0, g = 0;
 #pragma unroll
   for (int u = 0; u < NR; ++u) {
     const int i = lane + 32 * u;
-    xw[u] = i < R ? wp[i] : 0.0f;
-    yw[u] = i < R ? wq[i] : 0.0f;
-    a = fmaf(xw[u], xw[u], a);
-    bb = fmaf(yw[u], yw[u], bb);
-    g = fmaf(xw[u], yw[u], g);
+    xw[u] = i < R ? wp[i] : T(0);
+    yw[u] = i < R ? wq[i] : T(0);
+    a = fma(xw[u], xw[u], a);
+    bb = fma(yw[u], yw[u], bb);
+    g = fma(xw[u], yw[u], g);
   }
   a = warp_sum(a);
   bb = warp_sum(bb);
   g = warp_sum(g);
-  const float sab = sqrtf(a * bb);
-  float c, sn;
-  if (!JacobiArith<float>::angle(a, bb, g, sab, tol, c, sn)) return 0;
+  const T sab = sqrt(a * bb);
+  T c, sn;
+  if (!JacobiArith<T>::angle(a, bb, g, sab, tol, c, sn)) return 0;
 #pragma unroll
   for (int u = 0; u < NR; ++u) {
     const int i = lane + 32 * u;
@@ -355,12 +355,12 @@ __device__ __forceinline__ int rotate_pair_smem(float* wp, float* wq, float* vp,
       wq[i] = sn * xw[u] + c * yw[u];
     }
     if (i < C) {
-      const float x = vp[i], y = vq[i];
+      const T x = vp[i], y = vq[i];
       vp[i] = c * x - sn * y;
       vq[i] = sn * x + c * y;
     }
   }
-  return fabsf(g) > big * sab ? 2 : 1;
+  return fabs(g) > big * sab ? 2 : 1;
 }
 
 // FP32 sweeps by column blocks: the C columns form kColBlocks blocks of bw
@@ -374,15 +374,15 @@ __device__ __forceinline__ int rotate_pair_smem(float* wp, float* wq, float* vp,
 // a sweep, as in the order by pairs, but a sweep needs kColBlocks - 1 cluster
 // barriers instead of C - 1, and the pairs' columns come from shared memory.
 constexpr int kColBlocks = 2 * kSvdCluster;
-template <int NR>
-__device__ int jacobi_sweeps_blocked(float* W, float* V, int R, int C, int bw, int max_sweeps, float tol,
-                                     cg::cluster_group& cluster, SweepCtl* ctl, int* flag0, int crank, int lane,
-                                     int& gsweep, unsigned long long& myrot, bool& conv, float big_tol, float* sm) {
+template <typename T, int NR>
+__device__ int jacobi_sweeps_blocked(T* W, T* V, int R, int C, int bw, int max_sweeps, T tol, cg::cluster_group& cluster,
+                                     SweepCtl* ctl, int* flag0, int crank, int lane, int& gsweep,
+                                     unsigned long long& myrot, bool& conv, T big_tol, T* sm) {
   const int warp = threadIdx.x >> 5;
-  float* Wp = sm;  // bw columns of R, then Q's, then V's columns of P and Q (C each)
-  float* Wq = Wp + (int64_t)bw * R;
-  float* Vp = Wq + (int64_t)bw * R;
-  float* Vq = Vp + (int64_t)bw * C;
+  T* Wp = sm;  // bw columns of R, then Q's, then V's columns of P and Q (C each)
+  T* Wq = Wp + (int64_t)bw * R;
+  T* Vp = Wq + (int64_t)bw * R;
+  T* Vq = Vp + (int64_t)bw * C;
   const int bwe = bw + (bw & 1);  // a block's own tournament: bwe - 1 rounds of bwe / 2 pairs
   int sweeps = 0;
   conv = C < 2;
@@ -390,8 +390,8 @@ __device__ int jacobi_sweeps_blocked(float* W, float* V, int R, int C, int bw, i
     ++sweeps;
     const int gs = ++gsweep;
     int did = 0, big = 0;
-    auto rot = [&](float* wp, float* wq, float* vp, float* vq) {
-      const int r = rotate_pair_smem<NR>(wp, wq, vp, vq, R, C, lane, tol, big_tol);
+    auto rot = [&](T* wp, T* wq, T* vp, T* vq) {
+      const int r = rotate_pair_smem<T, NR>(wp, wq, vp, vq, R, C, lane, tol, big_tol);
       if (r) {
         did = 1;
         big |= r == 2;
@@ -418,8 +418,8 @@ __device__ int jacobi_sweeps_blocked(float* W, float* V, int R, int C, int bw, i
             int c = kk == 0 ? bwe - 1 : (ir - kk + bwe - 1) % (bwe - 1);
             const int n = side ? nq : np;
             if (a < n && c < n) {
-              float* w0 = side ? Wq : Wp;
-              float* v0 = side ? Vq : Vp;
+              T* w0 = side ? Wq : Wp;
+              T* v0 = side ? Vq : Vp;
               rot(w0 + (int64_t)a * R, w0 + (int64_t)c * R, v0 + (int64_t)a * C, v0 + (int64_t)c * C);
             }
           }
@@ -528,7 +528,7 @@ __global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThread
   __shared__ SweepCtl ctl;
   __shared__ double wsum[kSvdWarps];
   __shared__ double fpart;  // eig: this CTA's part of the squared Frobenius norm
-  extern __shared__ float sm32[];  // the FP32 sweeps by column blocks: a block pair of W and V
+  extern __shared__ double sm_pair[];  // the sweeps by column blocks: a block pair of W and V
   cg::cluster_group cluster = cg::this_cluster();
   const int crank = (int)cluster.block_rank();
   const SvdBlock b = blocks[blockIdx.x / kSvdCluster];
@@ -628,8 +628,9 @@ __global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThread
   switch (b.bw ? (R + 31) / 32 : 0) {
 #define SYM_BLOCKED(NR)                                                                                           \
   case NR:                                                                                                         \
-    sw32 = jacobi_sweeps_blocked<NR>(W32, V32, R, C, b.bw, kMaxSweeps32, tol32, cluster, &ctl, flag0, crank, lane, \
-                                     gsweep, rot32, conv32, kBigRotation32, sm32);                                 \
+    sw32 = jacobi_sweeps_blocked<float, NR>(W32, V32, R, C, b.bw, kMaxSweeps32, tol32, cluster, &ctl, flag0,     \
+                                            crank, lane, gsweep, rot32, conv32, kBigRotation32,                    \
+                                            reinterpret_cast<float*>(sm_pair));                                    \
     break;
     SYM_BLOCKED(1)
     SYM_BLOCKED(2)
@@ -664,8 +665,31 @@ __global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThread
   gemm_cols(A, R, C, V, W, sa, cw, lane);  // W = (sa A) V
   cluster.sync();
 
-  const int sw64 = jacobi_sweeps<double>(W, V, R, C, kMaxSweeps, sqrt((double)R) * DBL_EPSILON, cluster, &ctl,
-                                         flag0, crank, cw, lane, gsweep, rot64, conv, kBigRotation);
+  const double tol64 = sqrt((double)R) * DBL_EPSILON;
+  int sw64;
+  switch (b.bw64 ? (R + 31) / 32 : 0) {
+#define SYM_BLOCKED(NR)                                                                                          \
+  case NR:                                                                                                        \
+    sw64 = jacobi_sweeps_blocked<double, NR>(W, V, R, C, b.bw64, kMaxSweeps, tol64, cluster, &ctl, flag0, crank, \
+                                             lane, gsweep, rot64, conv, kBigRotation, sm_pair);                 \
+    break;
+    SYM_BLOCKED(1)
+    SYM_BLOCKED(2)
+    SYM_BLOCKED(3)
+    SYM_BLOCKED(4)
+    SYM_BLOCKED(5)
+    SYM_BLOCKED(6)
+    SYM_BLOCKED(7)
+    SYM_BLOCKED(8)
+    SYM_BLOCKED(9)
+    SYM_BLOCKED(10)
+    SYM_BLOCKED(11)
+    SYM_BLOCKED(12)
+#undef SYM_BLOCKED
+    default:
+      sw64 = jacobi_sweeps<double>(W, V, R, C, kMaxSweeps, tol64, cluster, &ctl, flag0, crank, cw, lane, gsweep, rot64,
+                                   conv, kBigRotation);
+  }
   if (lane == 0 && rot32) atomicAdd(cluster.map_shared_rank(&nrot[0], 0), rot32);
   if (lane == 0 && rot64) atomicAdd(cluster.map_shared_rank(&nrot[1], 0), rot64);
 
@@ -936,8 +960,14 @@ std::unique_ptr<SvdPlan> plan_svd(const Tensor& T, int nrow, bool eig) {
     {
       const int bw = (b.C + kColBlocks - 1) / kColBlocks;
       const int64_t bytes = 2 * (int64_t)bw * (b.R + b.C) * (int64_t)sizeof(float);
-      b.bw = (b.C >= kColBlocks * 2 && b.R <= 32 * 12 && bytes <= kSvdSmem32Max) ? bw : 0;
-      if (b.bw) P->smem32 = std::max<int64_t>(P->smem32, bytes);
+      const bool ok = b.C >= kColBlocks * 2 && b.R <= 32 * 12;
+      b.bw = (ok && bytes <= kSvdSmem32Max) ? bw : 0;
+      // FP64 by column blocks for the SVD only: on the shifted symmetric blocks of
+      // the eigendecomposition that order took up to 6 FP64 sweeps where the
+      // order by pairs takes 4 (two-site density matrix: 29.8 against 29.0 ms;
+      // two-site SVD: 20.4 against 22.3 ms)
+      b.bw64 = (ok && !eig && 2 * bytes <= kSvdSmem32Max) ? bw : 0;
+      if (b.bw) P->smem32 = std::max<int64_t>(P->smem32, b.bw64 ? 2 * bytes : bytes);
     }
     b.w = P->work_elems;
     b.s = P->nsv;
