@@ -159,6 +159,18 @@ def test_two_site_theta_full_size():
     _check("u1", legs, total, w["nrow"], vals, chi=w["chi"])
 
 
+def test_large_blocks_every_sweep_order():
+    # blocks of 320 x 320 (FP32 sweeps by column blocks, FP64 by pairs: the
+    # FP64 block pair would exceed the shared memory), 450 x 330 and
+    # 200 x 500 (more than 384 rows: every sweep by pairs, columns streamed),
+    # 272 x 272 (both by column blocks) and 40 x 20 (by pairs: too few columns)
+    legs = [([-2, -1, 0, 1], [40, 272, 320, 450], 1), ([-2, -1, 0, 1], [20, 272, 320, 330], -1)]
+    vals = _rand("u1", legs, 0, 24)
+    _check("u1", legs, 0, 1, vals)
+    legs = [([0], [200], 1), ([0], [500], -1)]
+    _check("u1", legs, 0, 1, _rand("u1", legs, 0, 25), chi=150)
+
+
 @pytest.mark.parametrize("dirs", [(1, -1), (1, 1), (-1, -1), (-1, 1)])
 def test_su2_rank2(dirs):
     # the block-diagonal form of Eq. svd0: integer and half-integer spins,
