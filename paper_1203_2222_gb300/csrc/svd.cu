@@ -183,8 +183,16 @@ struct JacobiArith<double> {
 // NR rows per lane held in registers (R <= 32 NR); V's columns are loaded
 // with W's, so a pair costs one round trip to L2.
 template <typename T, int NR>
-__device__ __forceinline__ int rotate_pair(T* wp, T* wq, T* vp, T* vq, int R, int C, int lane, T tol, T big) {
+// With na, nb (the pair's squared column norms, carried as in
+// rotate_pair_smem below) one dot product a pair instead of three.
+__device__ __forceinline__ int rotate_pair(T* wp, T* wq, T* vp, T* vq, T* na, T* nb, int R, int C, int lane, T tol,
+                                           T big) {
   T xw[NR], yw[NR], xv[NR], yv[NR];
+  T a = 0, bb = 0;
+  if (na) {
+    a = __ldcg(na);
+    bb = __ldcg(nb);
+  }
 #pragma unroll
   for (int u = 0; u < NR; ++u) {
     const int i = lane + 32 * u;
@@ -193,15 +201,18 @@ __device__ __forceinline__ int rotate_pair(T* wp, T* wq, T* vp, T* vq, int R, in
     xv[u] = i < C ? __ldcg(vp + i) : T(0);
     yv[u] = i < C ? __ldcg(vq + i) : T(0);
   }
-  T a = 0, bb = 0, g = 0;
+  T g = 0;
+  if (!na) {
 #pragma unroll
-  for (int u = 0; u < NR; ++u) {
-    a = fma(xw[u], xw[u], a);
-    bb = fma(yw[u], yw[u], bb);
-    g = fma(xw[u], yw[u], g);
+    for (int u = 0; u < NR; ++u) {
+      a = fma(xw[u], xw[u], a);
+      bb = fma(yw[u], yw[u], bb);
+    }
+    a = warp_sum(a);
+    bb = warp_sum(bb);
   }
-  a = warp_sum(a);
-  bb = warp_sum(bb);
+#pragma unroll
+  for (int u = 0; u < NR; ++u) g = fma(xw[u], yw[u], g);
   g = warp_sum(g);
   const T sab = sqrt(a * bb);
   T c, s;
@@ -217,6 +228,11 @@ __device__ __forceinline__ int rotate_pair(T* wp, T* wq, T* vp, T* vq, int R, in
       __stcg(vp + i, c * xv[u] - s * yv[u]);
       __stcg(vq + i, s * xv[u] + c * yv[u]);
     }
+  }
+  if (na && lane == 0) {
+    const T cs2g = T(2) * c * s * g, cc = c * c, ss = s * s;
+    __stcg(na, fma(cc, a, fma(ss, bb, -cs2g)));
+    __stcg(nb, fma(ss, a, fma(cc, bb, cs2g)));
   }
   return fabs(g) > big * sab ? 2 : 1;
 }
@@ -262,7 +278,7 @@ struct SweepCtl {
 // round (tournament order, an odd C playing against a bye) go to the
 // cluster's warps; cluster barriers separate the rounds.
 template <typename T>
-__device__ int jacobi_sweeps(T* W, T* V, int R, int C, int max_sweeps, T tol, cg::cluster_group& cluster,
+__device__ int jacobi_sweeps(T* W, T* V, T* nrm2, int R, int C, int max_sweeps, T tol, cg::cluster_group& cluster,
                              SweepCtl* ctl, int* flag0, int crank, int cw, int lane, int& gsweep,
                              unsigned long long& myrot, bool& conv, T big_tol) {
   constexpr int kCW = kSvdCluster * kSvdWarps;
@@ -275,6 +291,20 @@ __device__ int jacobi_sweeps(T* W, T* V, int R, int C, int max_sweeps, T tol, cg
     ++sweeps;
     const int gs = ++gsweep;  // sweeps so far over both precisions (same in every thread): picks the flag
     int did = 0, big = 0;
+    if (nrm2 && nr) {  // the squared column norms, exact at the sweep's start, carried by the rotations
+      for (int j = cw; j < C; j += kCW) {
+        const T* wj = W + (int64_t)j * R;
+        T a = 0;
+        for (int i = lane; i < R; i += 32) {
+          const T x = __ldcg(wj + i);
+          a = fma(x, x, a);
+        }
+        a = warp_sum(a);
+        if (lane == 0) __stcg(nrm2 + j, a);
+      }
+      cluster.sync();
+    }
+    T* const carry = nr ? nrm2 : nullptr;
     for (int r = 0; r < Ce - 1; ++r) {
       for (int k = cw; k < Ce / 2; k += kCW) {
         int p = k == 0 ? r : (r + k) % (Ce - 1);
@@ -290,13 +320,15 @@ __device__ int jacobi_sweeps(T* W, T* V, int R, int C, int max_sweeps, T tol, cg
         T* vp = V + (int64_t)p * C;
         T* vq = V + (int64_t)q * C;
         int rot;
+        T* na = carry ? carry + p : nullptr;
+        T* nb = carry ? carry + q : nullptr;
         switch (nr) {
-          case 1: rot = rotate_pair<T, 1>(wp, wq, vp, vq, R, C, lane, tol, big_tol); break;
-          case 2: rot = rotate_pair<T, 2>(wp, wq, vp, vq, R, C, lane, tol, big_tol); break;
-          case 4: rot = rotate_pair<T, 4>(wp, wq, vp, vq, R, C, lane, tol, big_tol); break;
-          case 8: rot = rotate_pair<T, 8>(wp, wq, vp, vq, R, C, lane, tol, big_tol); break;
-          case 9: rot = rotate_pair<T, 9>(wp, wq, vp, vq, R, C, lane, tol, big_tol); break;
-          case 12: rot = rotate_pair<T, 12>(wp, wq, vp, vq, R, C, lane, tol, big_tol); break;
+          case 1: rot = rotate_pair<T, 1>(wp, wq, vp, vq, na, nb, R, C, lane, tol, big_tol); break;
+          case 2: rot = rotate_pair<T, 2>(wp, wq, vp, vq, na, nb, R, C, lane, tol, big_tol); break;
+          case 4: rot = rotate_pair<T, 4>(wp, wq, vp, vq, na, nb, R, C, lane, tol, big_tol); break;
+          case 8: rot = rotate_pair<T, 8>(wp, wq, vp, vq, na, nb, R, C, lane, tol, big_tol); break;
+          case 9: rot = rotate_pair<T, 9>(wp, wq, vp, vq, na, nb, R, C, lane, tol, big_tol); break;
+          case 12: rot = rotate_pair<T, 12>(wp, wq, vp, vq, na, nb, R, C, lane, tol, big_tol); break;
           default: rot = rotate_pair_stream<T>(wp, wq, vp, vq, R, C, lane, tol, big_tol); break;
         }
         if (rot) {
@@ -326,24 +358,26 @@ __device__ int jacobi_sweeps(T* W, T* V, int R, int C, int max_sweeps, T tol, cg
 }
 
 // Rotate one column pair of W (length R) and V (length C) held in shared
-// memory; NR rows per lane.  Returns 0 (no rotation), 1, or 2 (a rotation
-// larger than big relative to the pair's norms).
+// memory; NR rows per lane.  The squared column norms *na, *nb are carried
+// from rotation to rotation (recomputed at every sweep's start), so a pair
+// costs one dot product (w_p . w_q), not three; the rotation updates them
+// exactly as it rotates the columns: |w_p'|^2 = c^2 a - 2 c s g + s^2 b,
+// |w_q'|^2 = s^2 a + 2 c s g + c^2 b.  Returns 0 (no rotation), 1, or 2 (a
+// rotation larger than big relative to the pair's norms).
 template <typename T, int NR>
-__device__ __forceinline__ int rotate_pair_smem(T* wp, T* wq, T* vp, T* vq, int R, int C, int lane, T tol, T big) {
+__device__ __forceinline__ int rotate_pair_smem(T* wp, T* wq, T* vp, T* vq, T* na, T* nb, int R, int C, int lane,
+                                                T tol, T big) {
   T xw[NR], yw[NR];
-  T a = 0, bb = 0, g = 0;
+  T g = 0;
 #pragma unroll
   for (int u = 0; u < NR; ++u) {
     const int i = lane + 32 * u;
     xw[u] = i < R ? wp[i] : T(0);
     yw[u] = i < R ? wq[i] : T(0);
-    a = fma(xw[u], xw[u], a);
-    bb = fma(yw[u], yw[u], bb);
     g = fma(xw[u], yw[u], g);
   }
-  a = warp_sum(a);
-  bb = warp_sum(bb);
   g = warp_sum(g);
+  const T a = *na, bb = *nb;
   const T sab = sqrt(a * bb);
   T c, sn;
   if (!JacobiArith<T>::angle(a, bb, g, sab, tol, c, sn)) return 0;
@@ -360,6 +394,12 @@ __device__ __forceinline__ int rotate_pair_smem(T* wp, T* wq, T* vp, T* vq, int 
       vq[i] = sn * x + c * y;
     }
   }
+  const T cs2g = T(2) * c * sn * g, cc = c * c, ss = sn * sn;
+  __syncwarp();  // every lane has read the old norms
+  if (lane == 0) {
+    *na = fma(cc, a, fma(ss, bb, -cs2g));
+    *nb = fma(ss, a, fma(cc, bb, cs2g));
+  }
   return fabs(g) > big * sab ? 2 : 1;
 }
 
@@ -375,14 +415,18 @@ __device__ __forceinline__ int rotate_pair_smem(T* wp, T* wq, T* vp, T* vq, int 
 // barriers instead of C - 1, and the pairs' columns come from shared memory.
 constexpr int kColBlocks = 2 * kSvdCluster;
 template <typename T, int NR>
-__device__ int jacobi_sweeps_blocked(T* W, T* V, int R, int C, int bw, int max_sweeps, T tol, cg::cluster_group& cluster,
-                                     SweepCtl* ctl, int* flag0, int crank, int lane, int& gsweep,
-                                     unsigned long long& myrot, bool& conv, T big_tol, T* sm) {
+__device__ int jacobi_sweeps_blocked(T* W, T* V, T* nrm2, int R, int C, int bw, int max_sweeps, T tol,
+                                     cg::cluster_group& cluster, SweepCtl* ctl, int* flag0, int crank, int lane,
+                                     int& gsweep, unsigned long long& myrot, bool& conv, T big_tol, T* sm) {
   const int warp = threadIdx.x >> 5;
-  T* Wp = sm;  // bw columns of R, then Q's, then V's columns of P and Q (C each)
+  constexpr int kCW = kSvdCluster * kSvdWarps;
+  const int cw = crank * kSvdWarps + warp;
+  T* Wp = sm;  // bw columns of R, then Q's, then V's columns of P and Q (C each), then their squared norms
   T* Wq = Wp + (int64_t)bw * R;
   T* Vp = Wq + (int64_t)bw * R;
   T* Vq = Vp + (int64_t)bw * C;
+  T* Np = Vq + (int64_t)bw * C;
+  T* Nq = Np + bw;
   const int bwe = bw + (bw & 1);  // a block's own tournament: bwe - 1 rounds of bwe / 2 pairs
   int sweeps = 0;
   conv = C < 2;
@@ -390,8 +434,19 @@ __device__ int jacobi_sweeps_blocked(T* W, T* V, int R, int C, int bw, int max_s
     ++sweeps;
     const int gs = ++gsweep;
     int did = 0, big = 0;
-    auto rot = [&](T* wp, T* wq, T* vp, T* vq) {
-      const int r = rotate_pair_smem<T, NR>(wp, wq, vp, vq, R, C, lane, tol, big_tol);
+    for (int j = cw; j < C; j += kCW) {  // the squared column norms, exact at the sweep's start
+      const T* wj = W + (int64_t)j * R;
+      T a = 0;
+      for (int i = lane; i < R; i += 32) {
+        const T x = __ldcg(wj + i);
+        a = fma(x, x, a);
+      }
+      a = warp_sum(a);
+      if (lane == 0) __stcg(nrm2 + j, a);
+    }
+    cluster.sync();
+    auto rot = [&](T* wp, T* wq, T* vp, T* vq, T* na, T* nb) {
+      const int r = rotate_pair_smem<T, NR>(wp, wq, vp, vq, na, nb, R, C, lane, tol, big_tol);
       if (r) {
         did = 1;
         big |= r == 2;
@@ -409,6 +464,8 @@ __device__ int jacobi_sweeps_blocked(T* W, T* V, int R, int C, int bw, int max_s
       for (int i = threadIdx.x; i < nq * R; i += kSvdThreads) Wq[i] = __ldcg(W + (int64_t)q0 * R + i);
       for (int i = threadIdx.x; i < np * C; i += kSvdThreads) Vp[i] = __ldcg(V + (int64_t)p0 * C + i);
       for (int i = threadIdx.x; i < nq * C; i += kSvdThreads) Vq[i] = __ldcg(V + (int64_t)q0 * C + i);
+      for (int i = threadIdx.x; i < np; i += kSvdThreads) Np[i] = __ldcg(nrm2 + p0 + i);
+      for (int i = threadIdx.x; i < nq; i += kSvdThreads) Nq[i] = __ldcg(nrm2 + q0 + i);
       __syncthreads();
       if (r == 0) {  // the pairs inside P and inside Q: each block's own tournament, side by side
         for (int ir = 0; ir < bwe - 1; ++ir) {
@@ -420,7 +477,8 @@ __device__ int jacobi_sweeps_blocked(T* W, T* V, int R, int C, int bw, int max_s
             if (a < n && c < n) {
               T* w0 = side ? Wq : Wp;
               T* v0 = side ? Vq : Vp;
-              rot(w0 + (int64_t)a * R, w0 + (int64_t)c * R, v0 + (int64_t)a * C, v0 + (int64_t)c * C);
+              T* n0 = side ? Nq : Np;
+              rot(w0 + (int64_t)a * R, w0 + (int64_t)c * R, v0 + (int64_t)a * C, v0 + (int64_t)c * C, n0 + a, n0 + c);
             }
           }
           __syncthreads();
@@ -430,7 +488,7 @@ __device__ int jacobi_sweeps_blocked(T* W, T* V, int R, int C, int bw, int max_s
         for (int i = warp; i < bw; i += kSvdWarps) {
           const int j = (i + ir) % bw;
           if (i < np && j < nq)
-            rot(Wp + (int64_t)i * R, Wq + (int64_t)j * R, Vp + (int64_t)i * C, Vq + (int64_t)j * C);
+            rot(Wp + (int64_t)i * R, Wq + (int64_t)j * R, Vp + (int64_t)i * C, Vq + (int64_t)j * C, Np + i, Nq + j);
         }
         __syncthreads();
       }
@@ -438,6 +496,8 @@ __device__ int jacobi_sweeps_blocked(T* W, T* V, int R, int C, int bw, int max_s
       for (int i = threadIdx.x; i < nq * R; i += kSvdThreads) __stcg(W + (int64_t)q0 * R + i, Wq[i]);
       for (int i = threadIdx.x; i < np * C; i += kSvdThreads) __stcg(V + (int64_t)p0 * C + i, Vp[i]);
       for (int i = threadIdx.x; i < nq * C; i += kSvdThreads) __stcg(V + (int64_t)q0 * C + i, Vq[i]);
+      for (int i = threadIdx.x; i < np; i += kSvdThreads) __stcg(nrm2 + p0 + i, Np[i]);
+      for (int i = threadIdx.x; i < nq; i += kSvdThreads) __stcg(nrm2 + q0 + i, Nq[i]);
       cluster.sync();  // the next round reads columns this round wrote, on other CTAs
     }
     const int f = (__syncthreads_or(did) ? 1 : 0) | (__syncthreads_or(big) ? 2 : 0);
@@ -628,9 +688,9 @@ __global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThread
   switch (b.bw ? (R + 31) / 32 : 0) {
 #define SYM_BLOCKED(NR)                                                                                           \
   case NR:                                                                                                         \
-    sw32 = jacobi_sweeps_blocked<float, NR>(W32, V32, R, C, b.bw, kMaxSweeps32, tol32, cluster, &ctl, flag0,     \
-                                            crank, lane, gsweep, rot32, conv32, kBigRotation32,                    \
-                                            reinterpret_cast<float*>(sm_pair));                                    \
+    sw32 = jacobi_sweeps_blocked<float, NR>(W32, V32, reinterpret_cast<float*>(nrm), R, C, b.bw, kMaxSweeps32,     \
+                                            tol32, cluster, &ctl, flag0, crank, lane, gsweep, rot32, conv32,       \
+                                            kBigRotation32, reinterpret_cast<float*>(sm_pair));                    \
     break;
     SYM_BLOCKED(1)
     SYM_BLOCKED(2)
@@ -646,8 +706,8 @@ __global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThread
     SYM_BLOCKED(12)
 #undef SYM_BLOCKED
     default:
-      sw32 = jacobi_sweeps<float>(W32, V32, R, C, kMaxSweeps32, tol32, cluster, &ctl, flag0, crank, cw, lane, gsweep,
-                                  rot32, conv32, kBigRotation32);
+      sw32 = jacobi_sweeps<float>(W32, V32, reinterpret_cast<float*>(nrm), R, C, kMaxSweeps32, tol32, cluster, &ctl,
+                                  flag0, crank, cw, lane, gsweep, rot32, conv32, kBigRotation32);
   }
 
   // V = V32 made orthogonal in FP64: two Newton-Schulz steps through the G
@@ -670,8 +730,8 @@ __global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThread
   switch (b.bw64 ? (R + 31) / 32 : 0) {
 #define SYM_BLOCKED(NR)                                                                                          \
   case NR:                                                                                                        \
-    sw64 = jacobi_sweeps_blocked<double, NR>(W, V, R, C, b.bw64, kMaxSweeps, tol64, cluster, &ctl, flag0, crank, \
-                                             lane, gsweep, rot64, conv, kBigRotation, sm_pair);                 \
+    sw64 = jacobi_sweeps_blocked<double, NR>(W, V, nrm, R, C, b.bw64, kMaxSweeps, tol64, cluster, &ctl, flag0,   \
+                                             crank, lane, gsweep, rot64, conv, kBigRotation, sm_pair);          \
     break;
     SYM_BLOCKED(1)
     SYM_BLOCKED(2)
@@ -687,8 +747,8 @@ __global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThread
     SYM_BLOCKED(12)
 #undef SYM_BLOCKED
     default:
-      sw64 = jacobi_sweeps<double>(W, V, R, C, kMaxSweeps, tol64, cluster, &ctl, flag0, crank, cw, lane, gsweep, rot64,
-                                   conv, kBigRotation);
+      sw64 = jacobi_sweeps<double>(W, V, nrm, R, C, kMaxSweeps, tol64, cluster, &ctl, flag0, crank, cw, lane, gsweep,
+                                   rot64, conv, kBigRotation);
   }
   if (lane == 0 && rot32) atomicAdd(cluster.map_shared_rank(&nrot[0], 0), rot32);
   if (lane == 0 && rot64) atomicAdd(cluster.map_shared_rank(&nrot[1], 0), rot64);
@@ -959,7 +1019,7 @@ std::unique_ptr<SvdPlan> plan_svd(const Tensor& T, int nrow, bool eig) {
     // shared memory two CTAs of an SM can have, rows up to 12 per lane
     {
       const int bw = (b.C + kColBlocks - 1) / kColBlocks;
-      const int64_t bytes = 2 * (int64_t)bw * (b.R + b.C) * (int64_t)sizeof(float);
+      const int64_t bytes = 2 * (int64_t)bw * (b.R + b.C + 1) * (int64_t)sizeof(float);
       const bool ok = b.C >= kColBlocks * 2 && b.R <= 32 * 12;
       b.bw = (ok && bytes <= kSvdSmem32Max) ? bw : 0;
       // FP64 by column blocks for the SVD only: on the shifted symmetric blocks of
