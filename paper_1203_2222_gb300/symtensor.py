@@ -482,17 +482,23 @@ class SVDPlan:
     def flops(self):
         """(FP64 flops, FP32 flops) of the last execute (synchronizes).
 
-        Per sweep 3 FMAs per row of every pair visited, per rotation 4
-        multiply-adds per row of W and V; in FP64 also the two Newton-Schulz
-        steps (2 C^3 FMAs each), W = A V (R C^2) and the column norms.  An
-        FMA counts 2."""
+        Per sweep one FMA per row of every pair visited and the squared
+        column norms (one FMA per element of W) when the kernel carries the
+        norms through the rotations (blocks of at most 384 rows), else three
+        FMAs per row of every pair visited; per rotation 4 multiply-adds per
+        row of W and V; in FP64 also the two Newton-Schulz steps (2 C^3 FMAs
+        each), W = A V (R C^2) and the column norms.  An FMA counts 2."""
         out = []
         for fp32 in (False, True):
             sweeps, rotations = self.stats(fp32)
             f = 0.0
             for m, n, sw, rot in zip(self.m, self.n, sweeps, rotations):
                 R, C = max(m, n), min(m, n)
-                f += sw * (C * (C - 1) // 2) * 6.0 * R + rot * 6.0 * (R + C)
+                if R <= 384:
+                    f += sw * ((C * (C - 1) // 2) * 2.0 * R + 2.0 * R * C)
+                else:
+                    f += sw * (C * (C - 1) // 2) * 6.0 * R
+                f += rot * 6.0 * (R + C)
                 if not fp32:
                     f += 2.0 * (4.0 * C ** 3 + R * C * C + R * C)
             out.append(f)
