@@ -796,79 +796,115 @@ def run_ours(args, rank, world):
     value64 = flops * world / (ms64 * 1e-3) / 1e12 if e64 else None
     del data64, G64
 
-    # ---- end to end through the public API: pinned host inputs -> result on host
+    # ---- end to end through the public API: pinned host inputs -> results on
+    # the host.  Two slots (device input buffers, a CUDA graph of the step
+    # captured on them, host result buffers) take turns, so that step i+1's
+    # inputs go to the device and step i's results to the host on copy
+    # streams while the next step computes; the host waits for every step's
+    # results, one step behind.
     names = list(data.keys())
     host_in = {n: v.detach().cpu().pin_memory() for n, v in data.items()}
-    dev_in = {n: torch.empty_like(v.detach()).requires_grad_(True) for n, v in data.items()}
-    host_y = torch.empty(y32.numel(), dtype=torch.float32).pin_memory()
-    host_g = {n: torch.empty(v.numel(), dtype=torch.float32).pin_memory() for n, v in data.items()}
     h2d = sum(v.numel() * 4 for v in host_in.values())
-    d2h = host_y.numel() * 4 + sum(v.numel() * 4 for v in host_g.values())
-
-    # the step as a caller replays it: a CUDA graph captured on the input
-    # buffers the host copies land in (eager launches if capture fails)
-    g_e2e, e2e_out, e2e_launch = None, None, "eager"
+    d2h = y32.numel() * 4 + sum(v.numel() * 4 for v in host_in.values())
     # workloads whose step exposes its forward result copy it to the host on
     # a side stream, forked inside the graph, while the backward runs
     overlap_y = "on_forward" in inspect.signature(wl.step).parameters
-    s_copy = torch.cuda.Stream() if overlap_y else None
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
 
-    def copy_y(y):
-        s_copy.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(s_copy):
-            host_y.copy_(y.detach(), non_blocking=True)
+    class Slot:
+        pass
 
-    if use_graph:
-        try:
-            s2 = torch.cuda.Stream()
-            s2.wait_stream(torch.cuda.current_stream())
-            with torch.cuda.stream(s2):
-                for _ in range(2):
-                    wl.step(P, dev_in, G)
-            torch.cuda.current_stream().wait_stream(s2)
-            torch.cuda.synchronize()
-            g_e2e = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g_e2e):
-                if overlap_y:
-                    e2e_out = wl.step(P, dev_in, G, on_forward=copy_y)
-                    torch.cuda.current_stream().wait_stream(s_copy)  # join the copy inside the graph
-                else:
-                    e2e_out = wl.step(P, dev_in, G)
-            e2e_launch = "cuda graph replay" + (" (result copied to the host during the backward)" if overlap_y
-                                                else "")
-        except Exception as e:
-            print(f"# e2e graph capture failed ({e}); eager launches", file=sys.stderr)
-            g_e2e = None
+    def make_slot():
+        sl = Slot()
+        sl.dev_in = {n: torch.empty_like(v.detach()).requires_grad_(True) for n, v in data.items()}
+        sl.host_y = torch.empty(y32.numel(), dtype=torch.float32).pin_memory()
+        sl.host_g = {n: torch.empty(v.numel(), dtype=torch.float32).pin_memory() for n, v in data.items()}
+        sl.s_copy = torch.cuda.Stream() if overlap_y else None
+        sl.graph, sl.out = None, None
+        sl.ev_in, sl.ev_done, sl.ev_out = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
+        for n in names:
+            sl.dev_in[n].detach().copy_(data[n].detach())
 
-    def e2e_step():
-        with torch.no_grad():
-            for n in dev_in:
-                dev_in[n].copy_(host_in[n], non_blocking=True)
-        if g_e2e is not None:
-            g_e2e.replay()  # with overlap_y the graph itself copies the result to host_y
-            yy, gg = e2e_out
-            if not overlap_y:
-                host_y.copy_(yy.detach(), non_blocking=True)
-        else:
-            yy, gg = wl.step(P, dev_in, G)
-            host_y.copy_(yy.detach(), non_blocking=True)
-        for n, gv in zip(names, gg):
-            host_g[n].copy_(gv, non_blocking=True)
+        def copy_y(y):
+            sl.s_copy.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(sl.s_copy):
+                sl.host_y.copy_(y.detach(), non_blocking=True)
 
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize()
-    ee = []
-    for _ in range(args.steps):
+        sl.copy_y = copy_y
+        if use_graph:
+            try:
+                s2 = torch.cuda.Stream()
+                s2.wait_stream(torch.cuda.current_stream())
+                with torch.cuda.stream(s2):
+                    for _ in range(2):
+                        wl.step(P, sl.dev_in, G)
+                torch.cuda.current_stream().wait_stream(s2)
+                torch.cuda.synchronize()
+                sl.graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(sl.graph):
+                    if overlap_y:
+                        sl.out = wl.step(P, sl.dev_in, G, on_forward=copy_y)
+                        torch.cuda.current_stream().wait_stream(sl.s_copy)  # join the copy inside the graph
+                    else:
+                        sl.out = wl.step(P, sl.dev_in, G)
+            except Exception as e:
+                print(f"# e2e graph capture failed ({e}); eager launches", file=sys.stderr)
+                sl.graph = None
+        sl.ev_done.record(stream)
+        return sl
+
+    slots = [make_slot(), make_slot()]
+    e2e_launch = ("cuda graph replay" if all(sl.graph is not None for sl in slots) else "eager") + \
+        ", two slots: the next step's inputs to the device and this step's results to the host on copy streams " \
+        "during the following step" + (", the forward result during the backward" if overlap_y else "")
+
+    def issue_in(sl):  # after the slot's previous step has finished with its inputs
+        s_in.wait_event(sl.ev_done)
+        with torch.cuda.stream(s_in), torch.no_grad():
+            for n in names:
+                sl.dev_in[n].copy_(host_in[n], non_blocking=True)
+        sl.ev_in.record(s_in)
+
+    def run(sl):
+        stream.wait_event(sl.ev_in)
         flush.fill_(1.0)
+        if sl.graph is not None:
+            sl.graph.replay()  # with overlap_y the graph itself copies the result to host_y
+            yy, gg = sl.out
+        else:
+            yy, gg = (wl.step(P, sl.dev_in, G, on_forward=sl.copy_y) if overlap_y else wl.step(P, sl.dev_in, G))
+            if overlap_y:
+                stream.wait_stream(sl.s_copy)
+        sl.ev_done.record(stream)
+        s_out.wait_event(sl.ev_done)
+        with torch.cuda.stream(s_out):
+            if not overlap_y:
+                sl.host_y.copy_(yy.detach(), non_blocking=True)
+            for n, gv in zip(names, gg):
+                sl.host_g[n].copy_(gv, non_blocking=True)
+        sl.ev_out.record(s_out)
+
+    def e2e_run(k):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        e2e_step()
+        s_in.wait_event(e0)
+        issue_in(slots[0])
+        for i in range(k):
+            run(slots[i % 2])
+            if i + 1 < k:
+                issue_in(slots[(i + 1) % 2])
+            if i >= 1:
+                slots[(i - 1) % 2].ev_out.synchronize()  # the host takes step i-1's results
+        stream.wait_event(slots[(k - 1) % 2].ev_out)
         e1.record(stream)
-        e1.synchronize()  # the host reads the result every step
-        ee.append((e0, e1))
-    ms_e2e = sum(a.elapsed_time(b) for a, b in ee) / args.steps
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    e2e_run(2)
+    torch.cuda.synchronize()
+    ms_e2e = e2e_run(args.steps) / args.steps
     e2e_value = flops * world / (ms_e2e * 1e-3) / 1e12
+    del slots
 
     # ---- roofline of the dominant kernel (largest summed device time), and of
     # the whole step: T_roof = max(useful flops / tensor peak, algorithmic
