@@ -497,28 +497,28 @@ WORKLOADS = {"u1_mps_heff": MPSWorkload, "su2_recouple": SU2Workload, "u1_two_si
 # the captured launches, applied to the full launch's algorithmic bytes.
 TRAFFIC = {
     "u1_mps_heff": {  # profiles/traffic_u1_mps_heff.md
-        "gemm_tc": {"bytes_per_launch": 13767680, "sha": "98131bfb98e11ffc"},
-        "box_flat": {"bytes_per_launch": 5859584, "sha": "0320d4c6c49f9616"},
-        "box": {"bytes_per_launch": 13080064, "sha": "0320d4c6c49f9616"},
-        "direct": {"bytes_per_launch": 11909291, "sha": "f5f2fc621ce84798"},
+        "gemm_tc": {"bytes_per_launch": 13768640, "sha": "e8b8ba59c26dc3b8"},
+        "box_flat": {"bytes_per_launch": 5856928, "sha": "b2745455cd736886"},
+        "box": {"bytes_per_launch": 13080064, "sha": "b2745455cd736886"},
+        "direct": {"bytes_per_launch": 11909291, "sha": "a481e530fd08e2e9"},
     },
     "su2_recouple": {  # profiles/gemm_tc_su2_recouple.md (full size, forward and backward launches)
-        "gemm_tc": {"bytes_per_launch": 61036485248, "sha": "98131bfb98e11ffc"},
+        "gemm_tc": {"bytes_per_launch": 61145753344, "sha": "e8b8ba59c26dc3b8"},
     },
     "u1_two_site_batch": {  # profiles/direct_u1_two_site_batch.md (128 of the 512 problems)
-        "direct": {"ratio": 0.97, "sha": "32a083d9660812bd"},
+        "direct": {"ratio": 0.96, "sha": "a481e530fd08e2e9"},
     },
     "u1_two_site_svd": {  # profiles/svd_u1_two_site_svd.md (full size, mean of 11 launches)
-        "svd_jacobi": {"bytes_per_launch": 8764230, "sha": "80768ec65c30971e"},
+        "svd_jacobi": {"bytes_per_launch": 9013271, "sha": "96f8106d63b42dfd"},
     },
     "u1_two_site_eig": {  # profiles/eig_u1_two_site_eig.md (full size, mean of 11 launches)
-        "svd_jacobi": {"bytes_per_launch": 8724596, "sha": "80768ec65c30971e"},
+        "svd_jacobi": {"bytes_per_launch": 8889972, "sha": "96f8106d63b42dfd"},
     },
-    "z2f_mps_heff": {  # profiles/traffic_z2f_mps_heff_and_mera.md (full size, mean of 54 step launches)
-        "gemm_tc": {"bytes_per_launch": 196313993, "sha": "98131bfb98e11ffc"},
+    "z2f_mps_heff": {  # profiles/traffic_z2f_mps_heff_and_mera.md (full size, mean of 62 step launches)
+        "gemm_tc": {"bytes_per_launch": 196322104, "sha": "e8b8ba59c26dc3b8"},
     },
-    "u1_mera_grad": {  # profiles/traffic_z2f_mps_heff_and_mera.md (full size, mean of 585 launches)
-        "box_flat": {"bytes_per_launch": 2138954, "sha": "0320d4c6c49f9616"},
+    "u1_mera_grad": {  # profiles/traffic_z2f_mps_heff_and_mera.md (full size, mean of 663 launches)
+        "box_flat": {"bytes_per_launch": 2139167, "sha": "b2745455cd736886"},
     },
 }
 KERNEL_SOURCES = {
