@@ -262,6 +262,33 @@ bool emit_recouple(Plan& P, const Box& box0, const std::vector<std::pair<int64_t
   return true;
 }
 
+// A launch of few items (small tensors) splits its fused recoupling items of
+// more than kChunk positions back into kChunk-position ones: more items keep
+// more warps busy, while a large launch keeps the long items, which share
+// one staging of their coefficients over several rounds of loads.
+constexpr int kFewItems = 4096;
+void split_few_recouple_items(Plan& P, int begin) {
+  const int end = (int)P.items.size();
+  if (end - begin >= kFewItems) return;
+  std::vector<BoxItem> out;
+  out.reserve(end - begin);
+  for (int i = begin; i < end; ++i) {
+    const BoxItem& it = P.items[i];
+    if (!(it.sel & kSelRecouple) || it.count <= kChunk) {
+      out.push_back(it);
+      continue;
+    }
+    for (int st = 0; st < it.count; st += kChunk) {
+      BoxItem c = it;
+      c.start = it.start + st;
+      c.count = std::min(kChunk, it.count - st);
+      out.push_back(c);
+    }
+  }
+  P.items.resize(begin);
+  P.items.insert(P.items.end(), out.begin(), out.end());
+}
+
 // Fused recoupling of one gather, scatter or permute (SU(2)): destinations
 // whose recoupling sums run over the same source sectors (the same leg
 // spins) and that write the same buffer form one group, emitted as fused
@@ -1061,6 +1088,7 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
       emit(*P, b, out.offs[s], 1, 0, DST_OUT, terms);
     }
   }
+  split_few_recouple_items(*P, 0);
   P->xform = {0, (int)P->items.size()};
   {
     const int es = precision == SYM_PREC_FP64 ? 8 : 4;
@@ -1886,6 +1914,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
   }
   for (auto& g : gs)
     if (g.split[0]) zero_fill(g.c, g.m, g.n);
+  split_few_recouple_items(*P, begin);
   P->fwd_gather = {begin, (int)P->items.size() - begin};
 
   // ---- forward scatter: C_x -> C blocks (SU(2): Gamma to the requested tree)
@@ -2028,6 +2057,7 @@ std::unique_ptr<Plan> plan_contract(const Tensor& A, const Tensor& B, const std:
     }
     emit(*P, b, A.offs[s], 1, 3, DST_DA, t);
   }
+  split_few_recouple_items(*P, begin);
   P->bwd_scatter_a = {begin, (int)P->items.size() - begin};
   begin = (int)P->items.size();
   for (int64_t s = 0; s < B.nsec(); ++s) {
