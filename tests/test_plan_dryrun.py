@@ -84,6 +84,25 @@ U = P.Structure(P.U1, [(qs, [2, 3, 1], 1), (qs, [1, 2, 2], 1), (qs, [3, 1, 2], -
 P.permute_plan(U, [2, 0, 1]); f = P.fuse_plan(U, 0); P.split_plan(f.out, 0, [U.legs[0], U.legs[1]])
 S = P.Structure(P.SU2, [([0, 1, 2], [2, 1, 1], 1), ([0, 1, 2], [1, 2, 1], 1), ([0, 1, 2, 3, 4], [1, 1, 2, 1, 1], 1)])
 P.permute_plan(S, [2, 0, 1]); f = P.fuse_plan(S, 0); P.split_plan(f.out, 0, [S.legs[0], S.legs[1]])
+# SU(2) transforms with fused recoupling items: blocks of many positions, the
+# permute into the matrix tree, inner-leg fuses (the destination's fused-leg
+# dimension as its row stride) and the splits back
+sp3 = [0, 1, 2]
+for legs in ([(sp3, [12, 9, 7], 1), (sp3, [9, 7, 12], -1), (sp3, [7, 12, 9], -1), (sp3, [12, 7, 9], -1)],
+             [([3, 4], [6, 5], 1), ([2, 3, 4], [3, 6, 4], 1), ([3, 4], [5, 6], 1), ([2, 4], [6, 5], 1)]):
+    S4 = P.Structure(P.SU2, legs)
+    P.permute_plan(S4, [0, 2, 1, 3], [(0, 1), (2, 3), (4, 5)])
+    P.permute_plan(S4, [3, 1, 0, 2])
+    for f in (1, 2):
+        fp = P.fuse_plan(S4, f)
+        P.split_plan(fp.out, f, [legs[f], legs[f + 1]])
+# a large recoupling permute (items of up to 2048 positions) and the
+# contraction whose gather recouples the same tensor
+c3 = synthetic.su2_recouple(dmax=12, jmax2=8)
+A3, B3 = P.Structure(P.SU2, c3["A"]), P.Structure(P.SU2, c3["B"])
+P.permute_plan(A3, [0, 2, 1, 3], [(0, 1), (2, 3), (4, 5)])
+for prec in (P.FP64, P.BF16X3):
+    P.contract_plan(A3, B3, c3["pairsA"], c3["pairsB"], prec)
 try:
     P.contract(None, None, [], [])
 except Exception:
