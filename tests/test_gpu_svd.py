@@ -171,6 +171,41 @@ def test_large_blocks_every_sweep_order():
     _check("u1", legs, 0, 1, _rand("u1", legs, 0, 25), chi=150)
 
 
+def test_su2_rank4_through_fuse_and_split():
+    # SU(2) above rank 2: fuse the row legs and the column legs (equal
+    # directions within each group), decompose the rank-2 form, split the
+    # factors' fused legs back.  The fusions are isometries, so the singular
+    # values are those of T's dense matrix (rows = legs 0, 1), and U S V
+    # rebuilds T.
+    P = _P()
+    sp = [0, 1, 2]
+    legs = [(sp, [2, 3, 1], 1), (sp, [1, 2, 2], 1), (sp, [2, 1, 2], -1), ([0, 1, 2, 3], [1, 2, 1, 1], -1)]
+    ol = [osu2.Leg(*l) for l in legs]
+    vals = np.random.default_rng(43).standard_normal(osu2.layout(ol, osu2.left_comb(4))[2])
+    S = P.Structure(P.SU2, legs)
+    assert S.numel == vals.size
+    T = P.SymTensor(S, torch.as_tensor(vals, dtype=torch.float64).cuda())
+    F = P.fuse(P.fuse(T, 0), 1)
+    plan = P.svd_plan(F.structure, 1)
+    Sg = plan.execute(F.data).cpu().numpy()
+    ks = [min(a, b) for a, b in zip(plan.m, plan.n)]
+    offs = np.cumsum([0] + ks)
+    Sd = np.sort(osvd.dense_values("su2", {x: Sg[o:o + k] for x, k, o in zip(plan.labels, ks, offs)}))[::-1]
+    dense = osu2.embed(ol, osu2.left_comb(4), vals)
+    sv = np.linalg.svd(dense.reshape(dense.shape[0] * dense.shape[1], -1), compute_uv=False)
+    assert np.max(np.abs(sv[:len(Sd)] - Sd)) <= TOL * sv[0]
+    assert np.all(sv[len(Sd):] <= TOL * sv[0])
+    U, Sk, V = P.svd(F, 1, absorb=1)
+    U4 = P.split(U, 0, [legs[0], legs[1]])
+    V4 = P.split(V, 1, [legs[2], legs[3]])
+    R = P.contract(U4, V4, [2], [0])
+    torch.cuda.synchronize()
+    Rl = [osu2.Leg(*l) for l in R.structure.legs]
+    Rd = osu2.embed(Rl, R.structure.tree, R.data.detach().cpu().numpy())
+    assert np.max(np.abs(Rd - dense)) <= TOL * sv[0]
+    P.device_status()
+
+
 @pytest.mark.parametrize("dirs", [(1, -1), (1, 1), (-1, -1), (-1, 1)])
 def test_su2_rank2(dirs):
     # the block-diagonal form of Eq. svd0: integer and half-integer spins,
