@@ -953,10 +953,12 @@ std::unique_ptr<Plan> plan_transform(const Tensor& in, const Tensor& out, const 
             Box b;
             for (int l = 0; l < k; ++l) {
               const int d = mid.dim(sm, l);
-              if (l < f)
+              if (l < f) {
+                if (ost[l] % D != 0) fail(SYM_ERR_ARG, "internal: fused leg's dimension does not divide a stride");
                 b.push(d, ist[l], 0, ost[l] / D, 0);
-              else
+              } else {
                 b.push(d, ist[l], 0, 0, l == f ? db_ * ost[f] : l == f + 1 ? ost[f] : ost[l - 1]);
+              }
             }
             return b;
           },
